@@ -1,0 +1,458 @@
+"""FP64 CPU oracle for the FITrig trigger path.
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module.  It shares no code with the CUDA library and imports nothing from it.
+
+Every step is written straight from the paper's definitions, in float64, by
+whole-array NumPy operations and plain loops; there is no fusion, blocking or
+reordering beyond what the definitions state.
+
+Paper sections used (arXiv 2509.21754, "FITrig"):
+
+* Sec. 2.2.4 (Mathematics): Eq. (tLISI), the difference image D (Eq. 3), the
+  ratio r (Eq. 4) and the guarded reference intensity x-hat (Eq. 5), C = 1e-6.
+* Sec. 2.3 (GPU-accelerated tLISI): Eq. (tLISI kernel form) -- the mean is a
+  sum over the tile divided by its pixel count; M is one scalar for the stack.
+* Sec. 2.4.1 (image-domain detection): Eq. (z-score) and the selected set
+  {t | z_t > tau}.
+* Sec. 2.4.2 (image-frequency detection): the tLISI cube, Eq. (eta) with h =
+  maximum spectral magnitude (the paper's own conservative choice in Sec. 3.4.3),
+  the z-score of eta and the selected set.
+
+Readings where the paper is silent or ambiguous (each is an option here):
+
+* rmode "abs": x-hat = |x^(s+1)| (C if zero) so that r lies in [0, 1] as the
+  paper requires of tLISI; "signed" keeps the literal Eq. 4/5.
+* edge "partial": ceil(n/w) tiles, edge tiles averaged over their own pixel
+  count; "drop": the image is cropped to whole tiles first.
+* M is the maximum over every finite pixel of every analysed snapshot, floored
+  at C; non-finite pixels invalidate the tiles they touch.
+* standard deviation is the population one; the robust scale is
+  1.482602218505602 x MAD with lower medians (index floor((n-1)/2)).
+* tiles are merged into 8-connected components per unit; one candidate per
+  component at its maximum-z tile (ties: smallest row-major tile index); the
+  image-branch pixel is the tile's arg-max of Delta (ties: smallest row-major
+  pixel), the frequency-branch pixel is the tile centre, refined by a parabola
+  through the eta values of the neighbouring tiles.
+* the transform is the unnormalised DFT of exact length n = L - 2, bins
+  k = 1..floor(n/2).
+
+All pins of this module live in ``tests/test_oracle_pins.py``.
+"""
+from __future__ import annotations
+
+from collections import deque
+from dataclasses import dataclass
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+C = 1e-6                       # Eq. 5 guard constant
+MAD_TO_SIGMA = 1.482602218505602   # 1 / Phi^-1(3/4)
+
+BRANCH_IMAGE = 1
+BRANCH_FREQ = 2
+BRANCH_BOTH = 3
+
+
+# --------------------------------------------------------------------------
+# Tiling (Sec. 2.1: non-overlapping tiles, same shape across time)
+# --------------------------------------------------------------------------
+def tiling(ny: int, nx: int, w: int, edge: str = "partial") -> Tuple[int, int, int, int]:
+    """Return (Ty, Tx, ny_used, nx_used)."""
+    if edge == "partial":
+        return -(-ny // w), -(-nx // w), ny, nx
+    if edge == "drop":
+        Ty, Tx = ny // w, nx // w
+        return Ty, Tx, Ty * w, Tx * w
+    raise ValueError(edge)
+
+
+def tile_extent(t_index: int, n_used: int, w: int) -> int:
+    """Number of pixels of tile row/column ``t_index`` along one axis."""
+    return min(w, n_used - t_index * w)
+
+
+# --------------------------------------------------------------------------
+# Normaliser M (Eq. tLISI denominator; a single scalar, Sec. 2.3)
+# --------------------------------------------------------------------------
+def normaliser_M(stack: np.ndarray) -> float:
+    """M = max(max_s max_i x_i^(s), C) over finite pixels."""
+    x = np.asarray(stack, dtype=np.float64)
+    fin = x[np.isfinite(x)]
+    m = float(fin.max()) if fin.size else -np.inf
+    return max(m, C)
+
+
+# --------------------------------------------------------------------------
+# Per-pixel terms of one three-snapshot unit (Eq. 3, Eq. 4, Eq. 5)
+# --------------------------------------------------------------------------
+def unit_terms(x_s: np.ndarray, x_s1: np.ndarray, x_s2: np.ndarray,
+               rmode: str = "abs") -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Delta = |D^(s) - D^(s+1)|, r (Eq. 4) and a mask of fully finite pixels."""
+    a = np.asarray(x_s, dtype=np.float64)
+    b = np.asarray(x_s1, dtype=np.float64)
+    c = np.asarray(x_s2, dtype=np.float64)
+    finite = np.isfinite(a) & np.isfinite(b) & np.isfinite(c)
+    with np.errstate(invalid="ignore", over="ignore", divide="ignore"):
+        D_s = np.abs(b - a)            # D^(s)   = |x^(s+1) - x^(s)|
+        D_s1 = np.abs(c - b)           # D^(s+1) = |x^(s+2) - x^(s+1)|
+        delta = np.abs(D_s - D_s1)
+        ref = np.abs(b) if rmode == "abs" else b
+        x_hat = np.where(b == 0.0, C, ref)      # Eq. 5
+        ratio = delta / x_hat
+        r = np.where(ratio < 1.0, ratio, 1.0)   # Eq. 4
+    delta = np.where(finite, delta, 0.0)
+    r = np.where(finite, r, 0.0)
+    return delta, r, finite
+
+
+@dataclass
+class UnitTiles:
+    S1: np.ndarray       # sum of Delta per tile           (Ty, Tx)
+    S2: np.ndarray       # max of Delta per tile
+    S3: np.ndarray       # sum of r per tile
+    n: np.ndarray        # pixel count per tile
+    valid: np.ndarray    # tile has only finite pixels
+    arg_y: np.ndarray    # pixel row of the first max of Delta
+    arg_x: np.ndarray    # pixel column of the first max of Delta
+
+    @property
+    def numerator(self) -> np.ndarray:
+        """mean(Delta) * max(Delta) * mean(r): the Eq. tLISI numerator."""
+        with np.errstate(invalid="ignore"):
+            v = (self.S1 / self.n) * self.S2 * (self.S3 / self.n)
+        return np.where(self.valid, v, np.nan)
+
+
+def tile_reduce(delta: np.ndarray, r: np.ndarray, finite: np.ndarray, w: int,
+                Ty: int, Tx: int) -> UnitTiles:
+    """Per-tile sum/max/sum over an image whose origin is a tile corner."""
+    ny, nx = delta.shape
+    H, W = Ty * w, Tx * w
+    pd_sum = np.zeros((H, W))
+    pd_max = np.full((H, W), -np.inf)
+    pr = np.zeros((H, W))
+    pf = np.ones((H, W), dtype=bool)
+    h, wd = min(ny, H), min(nx, W)
+    pd_sum[:h, :wd] = delta[:h, :wd]
+    pd_max[:h, :wd] = delta[:h, :wd]
+    pr[:h, :wd] = r[:h, :wd]
+    pf[:h, :wd] = finite[:h, :wd]
+    blk = lambda a: a.reshape(Ty, w, Tx, w).transpose(0, 2, 1, 3).reshape(Ty, Tx, w * w)
+    S1 = blk(pd_sum).sum(axis=2)
+    dm = blk(pd_max)
+    S2 = dm.max(axis=2)
+    idx = dm.argmax(axis=2)                  # first occurrence: smallest row-major
+    S3 = blk(pr).sum(axis=2)
+    valid = blk(pf).all(axis=2)
+    hy = np.array([tile_extent(t, h, w) for t in range(Ty)])
+    wx = np.array([tile_extent(t, wd, w) for t in range(Tx)])
+    n = (hy[:, None] * wx[None, :]).astype(np.float64)
+    ty = np.arange(Ty)[:, None]
+    tx = np.arange(Tx)[None, :]
+    arg_y = ty * w + idx // w
+    arg_x = tx * w + idx % w
+    return UnitTiles(S1, S2, S3, n, valid, arg_y, arg_x)
+
+
+def unit_tiles(stack: np.ndarray, s: int, w: int, rmode: str = "abs",
+               edge: str = "partial") -> UnitTiles:
+    """Tile statistics of unit s, which spans snapshots (s, s+1, s+2)."""
+    L, ny, nx = stack.shape
+    Ty, Tx, nyu, nxu = tiling(ny, nx, w, edge)
+    a, b, c = (stack[s + i, :nyu, :nxu] for i in range(3))
+    delta, r, fin = unit_terms(a, b, c, rmode)
+    return tile_reduce(delta, r, fin, w, Ty, Tx)
+
+
+def tlisi_from_tiles(ut: UnitTiles, M: float) -> np.ndarray:
+    """Eq. tLISI: 1 - mean(Delta) max(Delta) mean(r) / (M * M); NaN if invalid."""
+    with np.errstate(invalid="ignore"):
+        t = 1.0 - (ut.S1 / ut.n) * ut.S2 * (ut.S3 / ut.n) / (M * M)
+    return np.where(ut.valid, t, np.nan)
+
+
+def sampled_tiles(stack: np.ndarray, w: int, tiles: Sequence[Tuple[int, int]],
+                  rmode: str = "abs", edge: str = "partial") -> Dict[str, np.ndarray]:
+    """Tile statistics of selected tiles for every unit (tiles are independent).
+
+    Returns arrays of shape (units, len(tiles)).
+    """
+    L, ny, nx = stack.shape
+    Ty, Tx, nyu, nxu = tiling(ny, nx, w, edge)
+    U = L - 2
+    out = {k: np.zeros((U, len(tiles))) for k in ("S1", "S2", "S3", "n", "numerator")}
+    out["valid"] = np.zeros((U, len(tiles)), dtype=bool)
+    out["arg_y"] = np.zeros((U, len(tiles)), dtype=np.int64)
+    out["arg_x"] = np.zeros((U, len(tiles)), dtype=np.int64)
+    for j, (ty, tx) in enumerate(tiles):
+        y0, x0 = ty * w, tx * w
+        y1, x1 = min(y0 + w, nyu), min(x0 + w, nxu)
+        sub = np.asarray(stack[:, y0:y1, x0:x1], dtype=np.float64)
+        for s in range(U):
+            d, r, f = unit_terms(sub[s], sub[s + 1], sub[s + 2], rmode)
+            ut = tile_reduce(d, r, f, w, 1, 1)
+            for k in ("S1", "S2", "S3", "n"):
+                out[k][s, j] = getattr(ut, k)[0, 0]
+            out["numerator"][s, j] = ut.numerator[0, 0]
+            out["valid"][s, j] = ut.valid[0, 0]
+            out["arg_y"][s, j] = y0 + ut.arg_y[0, 0]
+            out["arg_x"][s, j] = x0 + ut.arg_x[0, 0]
+    return out
+
+
+# --------------------------------------------------------------------------
+# Noise estimates (Sec. 2.4.1 mean/std; robust median/MAD reading)
+# --------------------------------------------------------------------------
+def lower_median(values: np.ndarray) -> float:
+    v = np.sort(np.asarray(values, dtype=np.float64).ravel())
+    return float(v[(v.size - 1) // 2])
+
+
+def noise_meanstd(values: np.ndarray) -> Tuple[float, float, int]:
+    v = np.asarray(values, dtype=np.float64).ravel()
+    v = v[np.isfinite(v)]
+    if v.size == 0:
+        return float("nan"), 0.0, 0
+    return float(v.mean()), float(v.std()), int(v.size)
+
+
+def noise_medmad(values: np.ndarray) -> Tuple[float, float, int]:
+    v = np.asarray(values, dtype=np.float64).ravel()
+    v = v[np.isfinite(v)]
+    if v.size == 0:
+        return float("nan"), 0.0, 0
+    med = lower_median(v)
+    mad = lower_median(np.abs(v - med))
+    return med, MAD_TO_SIGMA * mad, int(v.size)
+
+
+def zscore_image(tlisi: np.ndarray, noise: str = "meanstd") -> Tuple[np.ndarray, float, float]:
+    """Eq. (z-score): z = (mu - tLISI) / sigma over the tiles of one unit.
+
+    The robust mode applies the same form to the complement v = 1 - tLISI:
+    z = (v - median(v)) / (1.4826 MAD(v)).  Returns (z, centre, scale), where
+    the centre/scale are those of the complement v in both modes.
+    """
+    if noise == "meanstd":
+        mu, sigma, _ = noise_meanstd(tlisi)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            z = (mu - tlisi) / sigma if sigma > 0 else np.full(tlisi.shape, np.nan)
+        return z, 1.0 - mu, sigma
+    v = 1.0 - tlisi
+    med, scale, _ = noise_medmad(v)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        z = (v - med) / scale if scale > 0 else np.full(tlisi.shape, np.nan)
+    return z, med, scale
+
+
+def zscore_map(values: np.ndarray, noise: str = "meanstd") -> Tuple[np.ndarray, float, float]:
+    """z = (value - centre) / scale, used for eta (Sec. 2.4.2) and plain maps."""
+    centre, scale, _ = noise_meanstd(values) if noise == "meanstd" else noise_medmad(values)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        z = (values - centre) / scale if scale > 0 else np.full(np.shape(values), np.nan)
+    return z, centre, scale
+
+
+# --------------------------------------------------------------------------
+# Selection and 8-connected components
+# --------------------------------------------------------------------------
+def select(z: np.ndarray, tau: float) -> np.ndarray:
+    """{t | z_t > tau} as a boolean mask (strict inequality)."""
+    with np.errstate(invalid="ignore"):
+        return np.asarray(z > tau) & np.isfinite(z)
+
+
+def components(mask: np.ndarray) -> List[List[Tuple[int, int]]]:
+    """8-connected components of a boolean (Ty, Tx) mask, by breadth-first search."""
+    Ty, Tx = mask.shape
+    seen = np.zeros_like(mask, dtype=bool)
+    comps = []
+    for ty, tx in zip(*np.nonzero(mask)):
+        if seen[ty, tx]:
+            continue
+        comp = []
+        q = deque([(int(ty), int(tx))])
+        seen[ty, tx] = True
+        while q:
+            cy, cx = q.popleft()
+            comp.append((cy, cx))
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    ny_, nx_ = cy + dy, cx + dx
+                    if 0 <= ny_ < Ty and 0 <= nx_ < Tx and mask[ny_, nx_] and not seen[ny_, nx_]:
+                        seen[ny_, nx_] = True
+                        q.append((ny_, nx_))
+        comps.append(comp)
+    return comps
+
+
+def component_peak(comp: List[Tuple[int, int]], z: np.ndarray) -> Tuple[int, int]:
+    """Maximum-z tile of a component; ties go to the smallest row-major index."""
+    return max(comp, key=lambda p: (z[p], -p[0], -p[1]))
+
+
+# --------------------------------------------------------------------------
+# Image-frequency branch (Sec. 2.4.2)
+# --------------------------------------------------------------------------
+def dft_magnitudes(series: np.ndarray) -> np.ndarray:
+    """|F[y - mean(y)]|_k for k = 1..floor(n/2), unnormalised DFT of length n.
+
+    ``series`` has shape (..., n).  The twiddle matrix exp(-2 pi i k s / n) is
+    applied by a matrix product (naive O(n^2) DFT).
+    """
+    y = np.asarray(series, dtype=np.float64)
+    n = y.shape[-1]
+    yc = y - y.mean(axis=-1, keepdims=True)
+    k = np.arange(1, n // 2 + 1)
+    s = np.arange(n)
+    ang = 2.0 * np.pi * ((np.outer(s, k) % n) / n)
+    X = yc @ np.cos(ang) - 1j * (yc @ np.sin(ang))
+    return np.abs(X)
+
+
+def spectrum(cube: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """eta_t = max_k |X_k| and its bin (smallest k on ties) per tile.
+
+    ``cube`` is the tLISI cube with shape (L-2, Ty, Tx); tiles with a
+    non-finite entry get eta = NaN and bin = -1.
+    """
+    U, Ty, Tx = cube.shape
+    series = np.moveaxis(cube, 0, -1).reshape(Ty * Tx, U)
+    ok = np.all(np.isfinite(series), axis=1)
+    mags = dft_magnitudes(np.where(ok[:, None], series, 0.0))
+    eta = mags.max(axis=1)
+    kbin = mags.argmax(axis=1) + 1
+    eta = np.where(ok, eta, np.nan).reshape(Ty, Tx)
+    kbin = np.where(ok, kbin, -1).reshape(Ty, Tx)
+    return eta, kbin
+
+
+def parabolic_offset(left: float, centre: float, right: float) -> float:
+    """Vertex offset (in grid steps) of the parabola through three samples."""
+    if not (np.isfinite(left) and np.isfinite(right) and np.isfinite(centre)):
+        return 0.0
+    den = left - 2.0 * centre + right
+    if not den < 0.0:
+        return 0.0
+    d = 0.5 * (left - right) / den
+    return float(min(0.5, max(-0.5, d)))
+
+
+# --------------------------------------------------------------------------
+# Whole trigger
+# --------------------------------------------------------------------------
+@dataclass
+class Candidate:
+    snapshot: int
+    y: int
+    x: int
+    significance: float
+    branch: int
+    freq_bin: int
+    xf: float
+    yf: float
+
+    def key(self):
+        return (self.snapshot, self.y, self.x)
+
+
+@dataclass
+class Detection:
+    candidates: List[Candidate]
+    M: float
+    Ty: int
+    Tx: int
+    tlisi: Optional[np.ndarray] = None       # (U, Ty, Tx)
+    z: Optional[np.ndarray] = None           # (U, Ty, Tx)
+    centre: Optional[np.ndarray] = None      # (U,) of the complement v
+    scale: Optional[np.ndarray] = None       # (U,)
+    units: Optional[List[UnitTiles]] = None
+    eta: Optional[np.ndarray] = None
+    eta_bin: Optional[np.ndarray] = None
+    eta_z: Optional[np.ndarray] = None
+    eta_centre: float = float("nan")
+    eta_scale: float = float("nan")
+
+
+def image_candidates(units: List[UnitTiles], z: np.ndarray, tau: float,
+                     forced: Optional[Dict[Tuple[int, int, int], bool]] = None) -> List[Candidate]:
+    out = []
+    for s, ut in enumerate(units):
+        mask = select(z[s], tau)
+        if forced:
+            for (fs, ty, tx), val in forced.items():
+                if fs == s:
+                    mask[ty, tx] = val
+        for comp in components(mask):
+            ty, tx = component_peak(comp, z[s])
+            out.append(Candidate(s, int(ut.arg_y[ty, tx]), int(ut.arg_x[ty, tx]),
+                                 float(z[s, ty, tx]), BRANCH_IMAGE, -1,
+                                 float(ut.arg_x[ty, tx]), float(ut.arg_y[ty, tx])))
+    return out
+
+
+def freq_candidates(eta: np.ndarray, kbin: np.ndarray, z: np.ndarray, tau: float,
+                    w: int, nyu: int, nxu: int,
+                    forced: Optional[Dict[Tuple[int, int], bool]] = None) -> List[Candidate]:
+    Ty, Tx = eta.shape
+    mask = select(z, tau)
+    if forced:
+        for (ty, tx), val in forced.items():
+            mask[ty, tx] = val
+    out = []
+    for comp in components(mask):
+        ty, tx = component_peak(comp, z)
+        hy, wx = tile_extent(ty, nyu, w), tile_extent(tx, nxu, w)
+        cx = tx * w + (wx - 1) / 2.0
+        cy = ty * w + (hy - 1) / 2.0
+        gx = lambda j: eta[ty, j] if 0 <= j < Tx else np.nan
+        gy = lambda j: eta[j, tx] if 0 <= j < Ty else np.nan
+        dx = parabolic_offset(gx(tx - 1), eta[ty, tx], gx(tx + 1))
+        dy = parabolic_offset(gy(ty - 1), eta[ty, tx], gy(ty + 1))
+        out.append(Candidate(-1, ty * w + (hy - 1) // 2, tx * w + (wx - 1) // 2,
+                             float(z[ty, tx]), BRANCH_FREQ, int(kbin[ty, tx]),
+                             float(cx + dx * w), float(cy + dy * w)))
+    return out
+
+
+def detect(stack: np.ndarray, w: int, tau: float, branch: int = BRANCH_IMAGE,
+           noise: str = "meanstd", rmode: str = "abs", edge: str = "partial",
+           forced_image=None, forced_freq=None) -> Detection:
+    """Run the trigger on a (L, ny, nx) stack and return the sorted candidates."""
+    x = np.asarray(stack)
+    L, ny, nx = x.shape
+    Ty, Tx, nyu, nxu = tiling(ny, nx, w, edge)
+    M = normaliser_M(x[:, :nyu, :nxu])
+    units = [unit_tiles(x, s, w, rmode, edge) for s in range(L - 2)]
+    tl = np.stack([tlisi_from_tiles(u, M) for u in units])
+    det = Detection([], M, Ty, Tx, tlisi=tl, units=units)
+    cands: List[Candidate] = []
+    if branch & BRANCH_IMAGE:
+        zs, cs, ss = [], [], []
+        for s in range(L - 2):
+            z, c, sc = zscore_image(tl[s], noise)
+            zs.append(z)
+            cs.append(c)
+            ss.append(sc)
+        det.z = np.stack(zs)
+        det.centre = np.array(cs)
+        det.scale = np.array(ss)
+        cands += image_candidates(units, det.z, tau, forced_image)
+    if branch & BRANCH_FREQ:
+        eta, kbin = spectrum(tl)
+        ez, ec, es = zscore_map(eta, noise)
+        det.eta, det.eta_bin, det.eta_z = eta, kbin, ez
+        det.eta_centre, det.eta_scale = ec, es
+        cands += freq_candidates(eta, kbin, ez, tau, w, nyu, nxu, forced_freq)
+    cands.sort(key=Candidate.key)
+    det.candidates = cands
+    return det
+
+
+def threshold_count(values: np.ndarray, tau: float, noise: str = "meanstd") -> int:
+    """Number of entries of a plain map whose z-score exceeds tau."""
+    z, _, _ = zscore_map(np.asarray(values, dtype=np.float64), noise)
+    return int(np.count_nonzero(select(z, tau)))

@@ -1,0 +1,338 @@
+"""Pins of the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle against a closed form, an invariant the paper
+states or implies, a hand-derived worked example, a library routine that the
+definition reduces to, or brute force on tiny inputs, so that a dropped term,
+a wrong sign/index or a transposed operand in the oracle fails at least one.
+"""
+import json
+import math
+import os
+import statistics
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import fitrig_oracle as O
+from paper_2509_21754_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _frac_eval(expr: str) -> float:
+    return float(eval(expr, {"__builtins__": {}}, {"sqrt": math.sqrt}))
+
+
+def _worked_example_stack():
+    g = json.load(open(os.path.join(GOLDEN, "pulse_worked_example.json")))
+    b = g["background"]
+    x = np.zeros((5, 6, 8), dtype=np.float32)
+    for k, bk in enumerate(b):
+        x[k] = bk
+    p = g["pulse"]
+    x[p["snapshot"], p["y"], p["x"]] += p["amp"]
+    return g, x
+
+
+# ---------------------------------------------------------------- worked example
+def test_worked_example_tlisi_values():
+    """Hand-derived tLISI of every tile of every unit (Eq. tLISI, Eq. 3-5)."""
+    g, x = _worked_example_stack()
+    det = O.detect(x, g["w"], g["tau"], noise="meanstd")
+    assert det.M == 6.0
+    assert (det.Ty, det.Tx) == (2, 3)
+    for s in range(3):
+        want = np.array([[_frac_eval(e) for e in row] for row in g["tlisi"][str(s)]])
+        np.testing.assert_allclose(det.tlisi[s], want, rtol=0, atol=1e-15)
+    a0 = g["argmax_unit0_tile01"]
+    assert (det.units[0].arg_y[0, 1], det.units[0].arg_x[0, 1]) == (a0["y"], a0["x"])
+    a2 = g["argmax_unit2_tile01"]
+    assert (det.units[2].arg_y[0, 1], det.units[2].arg_x[0, 1]) == (a2["y"], a2["x"])
+
+
+def test_worked_example_candidates():
+    g, x = _worked_example_stack()
+    det = O.detect(x, g["w"], g["tau"], noise="meanstd")
+    got = [(c.snapshot, c.y, c.x) for c in det.candidates]
+    want = [(c["snapshot"], c["y"], c["x"]) for c in g["candidates_meanstd"]]
+    assert got == want
+    assert det.candidates[0].significance == pytest.approx(math.sqrt(5.0), rel=1e-12)
+    det_r = O.detect(x, g["w"], g["tau"], noise="medmad")
+    assert det_r.candidates == []
+
+
+# ---------------------------------------------------------------- invariants
+def test_identical_snapshots_give_no_change_value():
+    """tLISI = 1 when the two difference images are the same (Sec. 2.1)."""
+    x = np.repeat(synth.random_stack(1, 17, 23, 3), 6, axis=0)
+    det = O.detect(x, 4, 3.0)
+    assert np.all(det.tlisi == 1.0)
+    assert np.all(det.scale == 0.0)
+    assert det.candidates == []
+
+
+def test_constant_offset_pair_gives_one():
+    """x^(s+2) = x^(s) makes D^(s) = D^(s+1), whatever x^(s+1) is."""
+    x = synth.random_stack(3, 12, 15, 5)
+    x[2] = x[0]
+    ut = O.unit_tiles(x, 0, 3)
+    assert np.all(O.tlisi_from_tiles(ut, O.normaliser_M(x)) == 1.0)
+
+
+def test_tlisi_in_unit_interval_for_nonnegative_images():
+    """tLISI lies in [0, 1] (Sec. 2.1) for non-negative snapshots."""
+    x = synth.random_stack(6, 20, 21, 7, kind="positive") * 5.0
+    det = O.detect(x, 3, 3.0)
+    assert np.all(det.tlisi >= 0.0) and np.all(det.tlisi <= 1.0)
+
+
+def test_scale_invariance():
+    """x -> a x scales D, Delta and M by a; r is unchanged; so are tLISI and z."""
+    x = synth.random_stack(7, 24, 30, 11)
+    x[np.abs(x) < 1e-3] = 0.5
+    a = 3.75
+    d1 = O.detect(x.astype(np.float64), 4, 2.0, branch=O.BRANCH_BOTH)
+    d2 = O.detect(x.astype(np.float64) * a, 4, 2.0, branch=O.BRANCH_BOTH)
+    np.testing.assert_allclose(d1.tlisi, d2.tlisi, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(d1.z, d2.z, rtol=1e-9, atol=1e-9)
+    assert [c.key() for c in d1.candidates] == [c.key() for c in d2.candidates]
+
+
+def test_z_does_not_depend_on_M():
+    """M is one scalar for the whole stack, so it cancels in the z-score."""
+    x = synth.random_stack(5, 30, 30, 13)
+    ut = O.unit_tiles(x, 1, 5)
+    M = O.normaliser_M(x)
+    z1, _, _ = O.zscore_image(O.tlisi_from_tiles(ut, M))
+    z2, _, _ = O.zscore_image(O.tlisi_from_tiles(ut, 7.0 * M))
+    np.testing.assert_allclose(z1, z2, rtol=1e-6, atol=1e-6)
+
+
+def test_M_is_global_over_the_stack():
+    x = np.zeros((4, 4, 4), dtype=np.float32)
+    x[3, 2, 2] = 9.0
+    x[0, 0, 0] = -20.0
+    assert O.normaliser_M(x) == 9.0
+    assert O.normaliser_M(-np.ones((3, 2, 2))) == O.C
+
+
+def test_single_pixel_tiles_closed_form():
+    """w = 1: tLISI_i = 1 - Delta_i * Delta_i * r_i / M^2 per pixel."""
+    x = synth.random_stack(3, 5, 6, 17).astype(np.float64)
+    M = O.normaliser_M(x)
+    ut = O.unit_tiles(x, 0, 1)
+    t = O.tlisi_from_tiles(ut, M)
+    for y in range(5):
+        for xx in range(6):
+            a, b, c = x[0, y, xx], x[1, y, xx], x[2, y, xx]
+            d = abs(abs(c - b) - abs(b - a))
+            xh = O.C if b == 0 else abs(b)
+            r = min(d / xh, 1.0)
+            assert t[y, xx] == pytest.approx(1.0 - d * d * r / (M * M), abs=1e-15)
+
+
+def test_single_outlier_z_is_samuelson_bound():
+    """Population std: one odd tile among T equal ones has z = sqrt(T - 1)."""
+    v = np.full((7, 9), 0.25)
+    v[3, 4] = 0.1
+    z, _, _ = O.zscore_image(v)
+    assert z[3, 4] == pytest.approx(math.sqrt(v.size - 1), rel=1e-12)
+    assert z[0, 0] == pytest.approx(-1.0 / math.sqrt(v.size - 1), rel=1e-12)
+    rng = np.random.default_rng(0)
+    z2, _, _ = O.zscore_image(rng.uniform(size=(13, 11)))
+    assert np.max(np.abs(z2)) <= math.sqrt(13 * 11 - 1) + 1e-12
+
+
+def test_pulse_in_noise_seen_in_units_k_and_k_minus_2():
+    """A pulse in snapshot k lights the units (k, k+1, k+2) and (k-2, k-1, k) but
+    not (k-1, k, k+1), where both differences contain it (Sec. 2.1)."""
+    rng = np.random.default_rng(5)
+    L, n, w = 9, 40, 4
+    x = rng.standard_normal((L, n, n))
+    k, py, px = 4, 21, 13
+    x[k, py, px] += 60.0
+    det = O.detect(x, w, 5.0)
+    hits = {c.snapshot for c in det.candidates if (c.y, c.x) == (py, px)}
+    assert hits == {k - 2, k}
+    near = [c for c in det.candidates if c.snapshot == k - 1
+            and abs(c.y - py) < w and abs(c.x - px) < w]
+    assert near == []
+
+
+def test_ratio_clip_and_zero_guard():
+    """r <= 1 always (Eq. 4); a zero reference uses C (Eq. 5)."""
+    a = np.array([[0.0, 1.0, 5.0]])
+    b = np.array([[0.0, 0.0, 1.0]])
+    c = np.array([[0.0, 3e-7, 0.0]])
+    d, r, f = O.unit_terms(a, b, c)
+    # pixel 0: all zero -> Delta 0, r 0; pixel 1: Delta=|3e-7-1| over C -> clipped 1;
+    # pixel 2: D0=4, D1=1, Delta=3 over |1| -> clipped 1
+    np.testing.assert_allclose(d[0], [0.0, 1.0 - 3e-7, 3.0])
+    np.testing.assert_allclose(r[0], [0.0, 1.0, 1.0])
+    d2, r2, _ = O.unit_terms(np.array([[0.0]]), np.array([[0.0]]), np.array([[5e-7]]))
+    assert r2[0, 0] == pytest.approx(0.5)
+    assert f.all()
+
+
+def test_signed_reading_follows_literal_eq4():
+    _, r, _ = O.unit_terms(np.array([[0.0]]), np.array([[-2.0]]), np.array([[-2.5]]))
+    # D0 = 2, D1 = 0.5, Delta = 1.5, Delta / x-hat = 1.5 / -2 = -0.75 < 1
+    _, rs, _ = O.unit_terms(np.array([[0.0]]), np.array([[-2.0]]), np.array([[-2.5]]), "signed")
+    assert r[0, 0] == pytest.approx(0.75)
+    assert rs[0, 0] == pytest.approx(-0.75)
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("kind", ["normal", "integers", "zeros"])
+@pytest.mark.parametrize("shape,w", [((4, 7, 9), 3), ((5, 8, 8), 4), ((3, 5, 11), 2), ((4, 6, 6), 6)])
+def test_tiles_against_pixel_loops(kind, shape, w):
+    """Vectorised tiling (padding, transposes, arg-max mapping) against loops."""
+    x = synth.random_stack(*shape, seed=sum(shape) + w, kind=kind).astype(np.float64)
+    L, ny, nx = shape
+    for s in range(L - 2):
+        ut = O.unit_tiles(x, s, w)
+        Ty, Tx = -(-ny // w), -(-nx // w)
+        for ty in range(Ty):
+            for tx in range(Tx):
+                S1 = S3 = 0.0
+                best, by, bx, cnt = -1.0, -1, -1, 0
+                for y in range(ty * w, min(ny, ty * w + w)):
+                    for xx in range(tx * w, min(nx, tx * w + w)):
+                        a, b, c = x[s, y, xx], x[s + 1, y, xx], x[s + 2, y, xx]
+                        dd = abs(abs(c - b) - abs(b - a))
+                        xh = O.C if b == 0 else abs(b)
+                        rr = dd / xh if dd / xh < 1 else 1.0
+                        S1 += dd
+                        S3 += rr
+                        cnt += 1
+                        if dd > best:
+                            best, by, bx = dd, y, xx
+                assert ut.S1[ty, tx] == pytest.approx(S1, abs=1e-12)
+                assert ut.S2[ty, tx] == best
+                assert ut.S3[ty, tx] == pytest.approx(S3, abs=1e-12)
+                assert ut.n[ty, tx] == cnt
+                assert (ut.arg_y[ty, tx], ut.arg_x[ty, tx]) == (by, bx)
+
+
+def test_nonfinite_pixels_invalidate_their_tiles():
+    x = synth.random_stack(5, 8, 8, 21)
+    x[2, 1, 6] = np.nan
+    x[4, 7, 0] = np.inf
+    det = O.detect(x, 4, 2.0)
+    # unit s touches snapshots s..s+2
+    for s in range(3):
+        assert np.isnan(det.tlisi[s, 0, 1]) == (s <= 2)
+        assert np.isnan(det.tlisi[s, 1, 0]) == (s == 2)
+    assert np.isfinite(det.tlisi[:, 1, 1]).all()
+    assert np.isfinite(det.M)
+
+
+def test_drop_edge_crops_to_whole_tiles():
+    x = synth.random_stack(4, 10, 11, 23)
+    d = O.detect(x, 3, 2.0, edge="drop")
+    ref = O.detect(x[:, :9, :9], 3, 2.0)
+    np.testing.assert_array_equal(d.tlisi, ref.tlisi)
+
+
+# ---------------------------------------------------------------- noise / threshold
+def test_lower_median_and_mad_constant():
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 5, 10, 101, 1000):
+        v = rng.standard_normal(n)
+        assert O.lower_median(v) == statistics.median_low(v.tolist())
+    from scipy.stats import norm
+    assert O.MAD_TO_SIGMA == pytest.approx(1.0 / norm.ppf(0.75), rel=1e-15)
+
+
+def test_medmad_scale_of_gaussian():
+    rng = np.random.default_rng(4)
+    med, scale, n = O.noise_medmad(rng.standard_normal(400_001))
+    assert abs(med) < 0.01 and abs(scale - 1.0) < 0.01
+
+
+@pytest.mark.parametrize("noise", ["meanstd", "medmad"])
+@pytest.mark.parametrize("tau", [3.0, 4.0])
+def test_gaussian_tail_false_positive_rate(noise, tau):
+    """Exceedances of z > tau on N(0,1) match Q(tau) within a 4-sigma interval."""
+    from scipy.special import erfc
+    n = 20_000_000
+    v = np.random.default_rng(int(tau * 10) + len(noise)).standard_normal(n)
+    k = O.threshold_count(v, tau, noise)
+    q = 0.5 * erfc(tau / math.sqrt(2.0))
+    mean, sd = n * q, math.sqrt(n * q * (1 - q))
+    slack = 4 * sd + (0.002 * n * q if noise == "medmad" else 0.0)
+    assert abs(k - mean) <= slack, (k, mean, sd)
+
+
+def test_strict_threshold():
+    z = np.array([[2.0, 2.0000001, np.nan]])
+    np.testing.assert_array_equal(O.select(z, 2.0), [[False, True, False]])
+
+
+# ---------------------------------------------------------------- components
+def test_components_match_scipy_label():
+    from scipy import ndimage
+    rng = np.random.default_rng(9)
+    for trial in range(20):
+        m = rng.uniform(size=(23, 31)) < (0.05 + 0.02 * trial)
+        comps = O.components(m)
+        lab, n = ndimage.label(m, structure=np.ones((3, 3), dtype=int))
+        assert len(comps) == n
+        for comp in comps:
+            labels = {lab[p] for p in comp}
+            assert len(labels) == 1
+            assert len(comp) == int(np.count_nonzero(lab == labels.pop()))
+
+
+def test_component_peak_tie_breaks_to_smallest_index():
+    z = np.zeros((3, 3))
+    z[1, 2] = z[2, 0] = 5.0
+    assert O.component_peak([(2, 0), (1, 2), (1, 1)], z) == (1, 2)
+
+
+# ---------------------------------------------------------------- frequency branch
+def test_dft_matches_numpy_fft():
+    rng = np.random.default_rng(12)
+    for n in (4, 7, 62, 64, 127):
+        y = rng.standard_normal((5, n))
+        want = np.abs(np.fft.rfft(y - y.mean(axis=1, keepdims=True), axis=1))[:, 1:n // 2 + 1]
+        np.testing.assert_allclose(O.dft_magnitudes(y), want, rtol=1e-11, atol=1e-11)
+
+
+def test_dft_removes_dc_and_ignores_offsets():
+    y = np.arange(10.0)
+    np.testing.assert_allclose(O.dft_magnitudes(y), O.dft_magnitudes(y + 123.0), atol=1e-10)
+
+
+@pytest.mark.parametrize("period,phase", [(4, 1), (8, 3), (16, 0)])
+def test_period_recovery(period, phase):
+    """A tile pulsing once per period P (P | n) peaks at a multiple of n/P."""
+    L = 66
+    n = L - 2
+    x = synth.periodic_tile_stack(L, 24, 24, 4, period, phase, (2, 3), 40.0, seed=period)
+    det = O.detect(x, 4, 5.0, branch=O.BRANCH_FREQ)
+    ty, tx = 2, 3
+    assert det.eta_z[ty, tx] == np.nanmax(det.eta_z)
+    assert det.eta_bin[ty, tx] % (n // period) == 0
+    top = max(det.candidates, key=lambda c: c.significance)
+    assert (top.y // 4, top.x // 4) == (ty, tx)
+    assert top.snapshot == -1 and top.branch == O.BRANCH_FREQ
+
+
+def test_parabolic_offset_finds_vertex():
+    for v in (-0.4, -0.1, 0.0, 0.25, 0.49):
+        f = lambda t: 3.0 - 2.0 * (t - v) ** 2
+        assert O.parabolic_offset(f(-1), f(0), f(1)) == pytest.approx(v, abs=1e-12)
+    assert O.parabolic_offset(1.0, 1.0, 1.0) == 0.0
+    assert O.parabolic_offset(np.nan, 2.0, 1.0) == 0.0
+
+
+def test_freq_candidate_is_tile_centre():
+    x = synth.periodic_tile_stack(34, 20, 26, 5, 4, 2, (1, 4), 50.0, seed=2)
+    # 24 tiles: a lone outlier reaches at most z = sqrt(23) ~ 4.8
+    det = O.detect(x, 5, 3.0, branch=O.BRANCH_FREQ)
+    top = max(det.candidates, key=lambda c: c.significance)
+    # tile (1, 4) spans rows 5..9 and columns 20..24: centre (7, 22)
+    assert (top.y, top.x) == (7, 22)
+    assert abs(top.xf - 22.0) <= 2.5 and abs(top.yf - 7.0) <= 2.5

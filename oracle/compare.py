@@ -1,0 +1,159 @@
+"""Parity rule between a candidate list and the FP64 oracle.
+
+TEST INFRASTRUCTURE ONLY (imported by tests/, __graft_entry__.smoke() and
+bench.py's CPU legs).
+
+A tile is *ambiguous* when its oracle z lies within ``REL_TOL * tau`` of the
+threshold.  Ambiguous tiles take the decision of the implementation under test
+(passed in as ``decide``) and the oracle's components are rebuilt with that
+forced mask; outside them the masks must agree exactly.  Each oracle component
+must then be matched by exactly one candidate that
+
+* sits in a tile of that component whose oracle z is within REL_TOL of the
+  component's maximum z (a near tie may pick either tile),
+* reports a significance within REL_TOL (relative) of that tile's oracle z,
+* for the image branch, is a pixel whose oracle Delta is within the FP32
+  rounding bound of the tile's maximum Delta (ties may pick either pixel),
+* for the frequency branch, is the tile centre, with a DFT bin whose oracle
+  magnitude is within REL_TOL of the tile's maximum, and a refined position
+  within ``XF_TOL_TILES`` tiles of the oracle's.
+"""
+from __future__ import annotations
+
+from typing import Callable, Dict, List, Optional, Tuple
+
+import numpy as np
+
+from . import fitrig_oracle as O
+
+REL_TOL = 1e-4
+XF_TOL_TILES = 0.05
+U32 = 2.0 ** -24
+
+
+def _near_peak(comp, z, tol):
+    zmax = max(z[p] for p in comp)
+    return {p for p in comp if z[p] >= zmax - tol * max(1.0, abs(zmax))}
+
+
+def _pixel_ok(stack: np.ndarray, s: int, y: int, x: int, ty: int, tx: int, w: int,
+              nyu: int, nxu: int, rmode: str) -> bool:
+    y0, x0 = ty * w, tx * w
+    y1, x1 = min(y0 + w, nyu), min(x0 + w, nxu)
+    if not (y0 <= y < y1 and x0 <= x < x1):
+        return False
+    a, b, c = (np.asarray(stack[s + i, y0:y1, x0:x1], dtype=np.float64) for i in range(3))
+    d, _, _ = O.unit_terms(a, b, c, rmode)
+    bound = 8 * U32 * (np.abs(a) + 2 * np.abs(b) + np.abs(c)).max() + 1e-300
+    return d[y - y0, x - x0] >= d.max() - bound
+
+
+def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: int,
+            noise: str = "meanstd", rmode: str = "abs", edge: str = "partial",
+            decide_image: Optional[Callable[[int, int, int], bool]] = None,
+            decide_freq: Optional[Callable[[int, int], bool]] = None,
+            det: Optional[O.Detection] = None) -> List[str]:
+    """Return a list of parity violations (empty when the lists agree)."""
+    errs: List[str] = []
+    L, ny, nx = stack.shape
+    Ty, Tx, nyu, nxu = O.tiling(ny, nx, w, edge)
+    if det is None:
+        det = O.detect(stack, w, tau, branch, noise, rmode, edge)
+    band = REL_TOL * tau
+    got = [dict(zip(cands.dtype.names, c)) for c in cands]
+
+    def check_groups(groups, branch_id):
+        # groups: list of (label, z_map, comps, snapshot, extra)
+        pool = [g for g in got if g["branch"] == branch_id]
+        used = set()
+        for label, zmap, comps, snap in groups:
+            for comp in comps:
+                near = _near_peak(comp, zmap, REL_TOL)
+                hit = None
+                for k, gc in enumerate(pool):
+                    if k in used or gc["snapshot"] != snap:
+                        continue
+                    t = (gc["y"] // w, gc["x"] // w)
+                    if t in comp:
+                        hit = k
+                        break
+                if hit is None:
+                    errs.append(f"{label}: oracle component at {sorted(comp)[:4]} has no candidate")
+                    continue
+                used.add(hit)
+                gc = pool[hit]
+                t = (gc["y"] // w, gc["x"] // w)
+                if t not in near:
+                    errs.append(f"{label}: candidate tile {t} is not a peak tile {sorted(near)}")
+                zt = zmap[t]
+                if abs(gc["significance"] - zt) > REL_TOL * max(1.0, abs(zt)):
+                    errs.append(f"{label}: significance {gc['significance']} vs oracle {zt}")
+                yield gc, t, snap
+        for k, gc in enumerate(pool):
+            if k not in used:
+                errs.append(f"extra candidate {gc}")
+
+    if branch & O.BRANCH_IMAGE:
+        groups = []
+        for s in range(L - 2):
+            z = det.z[s]
+            with np.errstate(invalid="ignore"):
+                amb = np.isfinite(z) & (np.abs(z - tau) <= band)
+            mask = O.select(z, tau)
+            for ty, tx in zip(*np.nonzero(amb)):
+                if decide_image is None:
+                    errs.append(f"unit {s}: ambiguous tile {(ty, tx)} and no decision callback")
+                else:
+                    mask[ty, tx] = bool(decide_image(s, int(ty), int(tx)))
+            groups.append((f"unit {s}", z, O.components(mask), s))
+        for gc, (ty, tx), s in check_groups(groups, O.BRANCH_IMAGE):
+            if not _pixel_ok(stack, s, int(gc["y"]), int(gc["x"]), ty, tx, w, nyu, nxu, rmode):
+                errs.append(f"unit {s}: pixel {(gc['y'], gc['x'])} is not an arg-max of Delta")
+
+    if branch & O.BRANCH_FREQ:
+        z = det.eta_z
+        with np.errstate(invalid="ignore"):
+            amb = np.isfinite(z) & (np.abs(z - tau) <= band)
+        mask = O.select(z, tau)
+        for ty, tx in zip(*np.nonzero(amb)):
+            if decide_freq is None:
+                errs.append(f"freq: ambiguous tile {(ty, tx)} and no decision callback")
+            else:
+                mask[ty, tx] = bool(decide_freq(int(ty), int(tx)))
+        comps = O.components(mask)
+        ref = {}
+        for c in O.freq_candidates(det.eta, det.eta_bin, z, tau, w, nyu, nxu,
+                                   forced={(int(a), int(b)): bool(mask[a, b])
+                                           for a, b in zip(*np.nonzero(amb))}):
+            ref[(c.y // w, c.x // w)] = c
+        series = det.tlisi
+        for gc, (ty, tx), _ in check_groups([("freq", z, comps, -1)], O.BRANCH_FREQ):
+            hy, wx = O.tile_extent(ty, nyu, w), O.tile_extent(tx, nxu, w)
+            if (gc["y"], gc["x"]) != (ty * w + (hy - 1) // 2, tx * w + (wx - 1) // 2):
+                errs.append(f"freq: candidate {(gc['y'], gc['x'])} is not the centre of {(ty, tx)}")
+            mags = O.dft_magnitudes(series[:, ty, tx])
+            k = int(gc["freq_bin"])
+            if not (1 <= k <= mags.size) or mags[k - 1] < mags.max() * (1 - REL_TOL):
+                errs.append(f"freq: bin {k} is not a maximum of tile {(ty, tx)}")
+            oc = ref.get((ty, tx))
+            if oc is not None:
+                if abs(gc["xf"] - oc.xf) > XF_TOL_TILES * w or abs(gc["yf"] - oc.yf) > XF_TOL_TILES * w:
+                    errs.append(f"freq: refined {(gc['yf'], gc['xf'])} vs oracle {(oc.yf, oc.xf)}")
+    return errs
+
+
+def values_close(gpu: np.ndarray, ref: np.ndarray, rel: float = 1e-5,
+                 abs_scale: float = 1e-6) -> Tuple[bool, float]:
+    """Elementwise |gpu - ref| <= rel |ref| + abs_scale * mean|ref|, NaNs must coincide."""
+    g = np.asarray(gpu, dtype=np.float64)
+    r = np.asarray(ref, dtype=np.float64)
+    if not np.array_equal(np.isnan(g), np.isnan(r)):
+        return False, float("inf")
+    m = np.isfinite(r)
+    if not m.any():
+        return True, 0.0
+    scale = float(np.mean(np.abs(r[m]))) if m.any() else 0.0
+    err = np.abs(g[m] - r[m])
+    ok = bool(np.all(err <= rel * np.abs(r[m]) + abs_scale * scale))
+    worst = float(np.max(err / (np.abs(r[m]) + abs_scale * scale + 1e-300)))
+    return ok, worst

@@ -1,0 +1,230 @@
+// Internal declarations shared by the translation units of libfitrig.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fitrig.h"
+
+namespace fitrig {
+
+constexpr float kGuardC = 1e-6f;           // Eq. 5 guard constant C
+constexpr double kMadToSigma = 1.482602218505602;  // 1 / Phi^-1(3/4)
+
+// Device error flags (bit mask in Plan::d_status[0]).
+enum : unsigned {
+  kErrTimeout = 1u,      // an mbarrier wait gave up
+  kErrCcLimit = 2u,      // union-find retry bound reached
+  kErrCapacity = 4u,     // a list exceeded its capacity
+};
+
+// ---------------------------------------------------------------- keys
+// Order-preserving map float -> uint32 (NaN must be filtered by the caller).
+__host__ __device__ inline uint32_t f32_key(float f) {
+#ifdef __CUDA_ARCH__
+  uint32_t b = __float_as_uint(f);
+#else
+  uint32_t b;
+  memcpy(&b, &f, 4);
+#endif
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__host__ __device__ inline float f32_from_key(uint32_t k) {
+  uint32_t b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+__device__ inline unsigned long long f64_key(double d) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// ---------------------------------------------------------------- storage types
+struct bf16_t { uint16_t v; };
+struct f16_t { uint16_t v; };
+
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(bf16_t x) { return __uint_as_float(((uint32_t)x.v) << 16); }
+__device__ __forceinline__ float to_f32(f16_t x) {
+  float f;
+  asm("{ .reg .f16 h; mov.b16 h, %1; cvt.f32.f16 %0, h; }" : "=f"(f) : "h"(x.v));
+  return f;
+}
+
+// ---------------------------------------------------------------- PTX: time, mbarrier, TMA
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: spins on try_wait until the phase completes or `deadline`
+// (globaltimer ns) passes; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  uint64_t deadline) {
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 63u && globaltimer_ns() > deadline) return false;
+  }
+}
+// 3-D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---------------------------------------------------------------- host-side launchers
+// Adds n to the process-wide count of kernel launches (fitrig_launch_count).
+void count_launches(int n);
+
+// Stack-march geometry chosen on the host (see k_stack.cu).
+struct StackGeom {
+  int w;              // tile size
+  int R;              // rows per thread segment (template parameter)
+  int nseg;           // row segments per tile band
+  int TBX, TBY;       // tiles per CTA in x / y
+  int BW;             // pixel columns per CTA (TBX * w)
+  int BH;             // pixel rows per CTA (TBY * w)
+  int boxW;           // TMA box width (BW, or widened for unaligned origins)
+  bool aligned;       // CTA column origin always a multiple of 8 elements
+  int stages;         // TMA ring depth
+  int threads;        // BW * TBY * nseg
+  size_t stage_bytes; // boxW * BH * elem, rounded to 128
+  size_t smem_bytes;
+  int gridX, gridY;
+};
+
+struct StackArgs {
+  int nx, ny;          // analysed image size (cropped in EDGE_DROP)
+  int nsnap;           // snapshots to march over (>= 3)
+  int Tx, Ty;
+  int64_t T;           // Tx * Ty
+  float* vp;           // [nsnap-2][T] tile statistic
+  unsigned* gmax;      // ordered key of the running maximum
+  unsigned* status;    // error flags
+  uint64_t timeout_ns;
+  StackGeom g;
+};
+
+bool stack_geometry(int w, int elem_bytes, StackGeom* g);
+cudaError_t launch_stack(const CUtensorMap* tmap, const StackArgs& a, int storage, int rmode,
+                         cudaStream_t st);
+cudaError_t launch_finite_max(const void* stack, int storage, int L, int ny, int nx,
+                              int64_t pitch, unsigned* gmax, cudaStream_t st);
+
+// Noise: per-group centre/scale of `vals` ([groups][n], NaN = excluded).
+struct NoiseScratch {
+  double* part;        // [groups][nblk] partial sums
+  int* cnt;            // [groups][nblk] partial counts
+  unsigned* hist;      // [groups][2048] radix histogram
+  unsigned* rsel;      // [groups][4] radix-select state
+  float* shift;        // [groups] FP32 mean used by the second MEANSTD pass
+  unsigned long long* invalid;  // device counter of non-finite values seen (may be null)
+  int nblk;
+};
+size_t noise_scratch_bytes(int groups, int nblk);
+void noise_scratch_carve(void* base, int groups, int nblk, NoiseScratch* s);
+cudaError_t launch_noise(const float* vals, int groups, int64_t n, int mode,
+                         const NoiseScratch& s, double* centre_scale, cudaStream_t st);
+// thr32[g] = largest float <= centre + tau*scale (+inf if degenerate)
+cudaError_t launch_thresholds(const double* centre_scale, int groups, double tau, float* thr,
+                              cudaStream_t st);
+
+// Selection / components / candidates.
+struct SelItem {
+  int32_t group;
+  int32_t t;
+  double z;
+};
+struct SelectScratch {
+  int nblk;            // fixed grid of the ordered compaction
+  int* blkcnt;         // [nblk]
+  int* blkoff;         // [nblk + 1]
+  SelItem* items;      // capacity entries
+  int* nsel;           // device count
+  int* parent;         // capacity
+  unsigned long long* compmax;  // capacity
+  int* peak;           // capacity
+  int64_t capacity;
+};
+cudaError_t launch_select(const float* vals, int groups, int64_t T, const float* thr,
+                          const double* centre_scale, const SelectScratch& s, unsigned* status,
+                          cudaStream_t st);
+cudaError_t launch_count_selected(const float* vals, int groups, int64_t T, const float* thr,
+                                  int nblk, int* blkcnt, long long* total, cudaStream_t st);
+cudaError_t launch_clamp_count(int* n, int cap, unsigned* status, cudaStream_t st);
+cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
+                              unsigned* status, cudaStream_t st);
+
+struct CandArgs {
+  int nx, ny, w, Tx, Ty;
+  int64_t T;
+  int branch;          // 1 image, 2 freq
+  // image branch: stack access for the in-tile arg-max of Delta
+  const void* stack;
+  int storage;
+  int64_t pitch;       // elements per row
+  int64_t slice;       // elements per snapshot
+  // freq branch
+  const float* eta;
+  const int* bin;
+  fitrig_candidate* out;
+  int* nout;
+  int64_t cap;
+};
+cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, cudaStream_t st);
+cudaError_t launch_sort_candidates(fitrig_candidate* c, fitrig_candidate* tmp, const int* n,
+                                   cudaStream_t st);
+
+// Frequency branch.
+cudaError_t launch_spectrum(const float* vp, int n, int64_t T, const float2* twiddle,
+                            float* eta, int* bin, cudaStream_t st);
+
+// Ingest conversion (fp32 <-> bf16/fp16).
+cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,
+                           int dst_type, int64_t dst_pitch, int ny, int nx, cudaStream_t st);
+
+// Small helpers.
+cudaError_t launch_tlisi_from_values(const float* vp, int64_t n, const unsigned* gmax,
+                                     float* out, cudaStream_t st);
+
+}  // namespace fitrig

@@ -1,0 +1,153 @@
+// Image-frequency branch (Sec. 2.4.2): per tile, the series of the tile
+// statistic over the n = L - 2 units, its mean removed (the DC term of Eq.
+// eta), an unnormalised DFT of exact length n, and
+//   eta_t = max_{k=1..floor(n/2)} |X_k|   (h = maximum spectral magnitude)
+// with the arg-max bin (smallest k on ties).
+//
+// The series used is v_t(s) = mean(Delta) max(Delta) mean(r), i.e. the tLISI
+// complement times M^2 with one M for the stack, so |X_k| of tLISI is |X_k|/M^2
+// and the z-score of eta is unchanged.
+//
+// One thread per tile; the series is staged in shared memory (coalesced over
+// tiles).  Real input: pairs y_s, y_{n-s} are folded into e_s = y_s + y_{n-s}
+// and o_s = y_s - y_{n-s}, so that Re X_k = y_0 + sum e_s cos + [n even]
+// (-1)^k y_{n/2} and Im X_k = -sum o_s sin, halving the multiply-adds.  The
+// twiddles cos/sin(2 pi k s / n) come from a table filled on the host in FP64.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace fitrig {
+
+constexpr int kDftThreads = 128;
+
+__global__ void __launch_bounds__(kDftThreads) k_dft(const float* __restrict__ vp, int n,
+                                                     int64_t T, const float2* __restrict__ tw,
+                                                     float* eta, int* bin) {
+  extern __shared__ float ys[];   // [n][kDftThreads]
+  const int tid = threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * kDftThreads + tid;
+  const bool live = t < T;
+  bool ok = live;
+  float s = 0.f, comp = 0.f;
+  for (int q = 0; q < n; ++q) {
+    const float v = live ? vp[(size_t)q * T + t] : 0.f;
+    ok = ok && isfinite(v);
+    ys[q * kDftThreads + tid] = v;
+    const float y = v - comp;
+    const float u = s + y;
+    comp = (u - s) - y;
+    s = u;
+  }
+  if (!live) return;
+  if (!ok) {
+    eta[t] = NAN;
+    bin[t] = -1;
+    return;
+  }
+  const float mean = s / (float)n;
+  const int H = (n - 1) / 2;        // folded pairs s = 1..H
+  const bool even = (n & 1) == 0;
+  const float y0 = ys[tid] - mean;
+  const float ymid = even ? ys[(n / 2) * kDftThreads + tid] - mean : 0.f;
+  for (int q = 1; q <= H; ++q) {
+    const float a = ys[q * kDftThreads + tid] - mean;
+    const float b = ys[(n - q) * kDftThreads + tid] - mean;
+    ys[q * kDftThreads + tid] = a + b;         // e_q
+    ys[(n - q) * kDftThreads + tid] = a - b;   // o_q
+  }
+  const int K = n / 2;
+  float best = -1.f;
+  int bk = 1;
+  for (int k = 1; k <= K; ++k) {
+    float re = y0 + ((even && (k & 1)) ? -ymid : ymid);
+    float im = 0.f;
+    const float2* twk = tw + (size_t)(k - 1) * H;
+    for (int q = 1; q <= H; ++q) {
+      const float2 cs = twk[q - 1];
+      re = fmaf(ys[q * kDftThreads + tid], cs.x, re);
+      im = fmaf(ys[(n - q) * kDftThreads + tid], cs.y, im);
+    }
+    const float m2 = re * re + im * im;
+    if (m2 > best) {
+      best = m2;
+      bk = k;
+    }
+  }
+  eta[t] = sqrtf(best);
+  bin[t] = bk;
+}
+
+cudaError_t launch_spectrum(const float* vp, int n, int64_t T, const float2* twiddle,
+                            float* eta, int* bin, cudaStream_t st) {
+  const size_t smem = (size_t)n * kDftThreads * sizeof(float);
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_dft, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  const int64_t blocks = (T + kDftThreads - 1) / kDftThreads;
+  k_dft<<<(unsigned)blocks, kDftThreads, smem, st>>>(vp, n, T, twiddle, eta, bin);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- ingest conversion
+__device__ __forceinline__ float load_any(const void* p, int type, int64_t i) {
+  if (type == FITRIG_BF16) return to_f32(static_cast<const bf16_t*>(p)[i]);
+  if (type == FITRIG_F16) return to_f32(static_cast<const f16_t*>(p)[i]);
+  return static_cast<const float*>(p)[i];
+}
+
+__device__ __forceinline__ void store_any(void* p, int type, int64_t i, float v) {
+  if (type == FITRIG_BF16) {
+    unsigned short h;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(v));
+    static_cast<uint16_t*>(p)[i] = h;
+  } else if (type == FITRIG_F16) {
+    unsigned short h;
+    asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(v));
+    static_cast<uint16_t*>(p)[i] = h;
+  } else {
+    static_cast<float*>(p)[i] = v;
+  }
+}
+
+__global__ void k_convert(const void* src, int st, int64_t sp, void* dst, int dt, int64_t dp,
+                          int ny, int nx) {
+  const int64_t total = (int64_t)ny * nx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = i / nx, x = i - (i / nx) * nx;
+    store_any(dst, dt, y * dp + x, load_any(src, st, y * sp + x));
+  }
+}
+
+cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,
+                           int dst_type, int64_t dst_pitch, int ny, int nx, cudaStream_t st) {
+  k_convert<<<152 * 8, 256, 0, st>>>(src, src_type, src_pitch, dst, dst_type, dst_pitch, ny, nx);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- tLISI report
+// tLISI = 1 - v / M^2 in FP64 (Eq. tLISI), M = max(stack maximum, C).
+__global__ void k_tlisi(const float* vp, int64_t n, const unsigned* gmax, float* out) {
+  const unsigned key = *gmax;
+  double M = key ? (double)f32_from_key(key) : 0.0;
+  if (!(M > (double)kGuardC)) M = (double)kGuardC;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)(1.0 - (double)vp[i] / (M * M));
+}
+
+cudaError_t launch_tlisi_from_values(const float* vp, int64_t n, const unsigned* gmax,
+                                     float* out, cudaStream_t st) {
+  k_tlisi<<<152 * 2, 256, 0, st>>>(vp, n, gmax, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace fitrig

@@ -1,0 +1,458 @@
+// Threshold, compaction, components, candidates and their sort.
+//
+// Selection follows the set {t | z_t > tau} of Sec. 2.4.1 (image branch) and
+// Sec. 2.4.2 (eta): z = (v - centre) / scale in FP64.  The comparison is made
+// in FP32 against thr = the largest float <= centre + tau * scale, which picks
+// exactly the floats v with (double)v > centre + tau * scale.
+//
+// Compaction is order-preserving (per-block counts, an exclusive scan, and a
+// warp-ballot write), so the list of selected tiles is sorted by (unit, t).
+// Tiles are merged into 8-connected components per unit (a pulsar spreads over
+// one, two or four tiles, Sec. 2.4.2) by a lock-free union-find whose roots
+// are always the smallest list index; each component yields one candidate at
+// its maximum-z tile (ties: smallest tile index).  The image-branch pixel is
+// the tile's arg-max of Delta recomputed from the three snapshots; the
+// frequency-branch pixel is the tile centre refined by a parabola through the
+// eta of the neighbouring tiles.  Candidates are finally radix-sorted by
+// (snapshot, y, x), a unique key, so the output is deterministic.
+#include <cfloat>
+#include <climits>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace fitrig {
+
+constexpr int kSelThreads = 256;
+
+__device__ __forceinline__ void chunk_range(int64_t N, int nblk, int b, int64_t* lo,
+                                            int64_t* hi) {
+  const int64_t chunk = (N + nblk - 1) / nblk;
+  *lo = (int64_t)b * chunk;
+  *hi = *lo + chunk < N ? *lo + chunk : N;
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_count(const float* __restrict__ vals,
+                                                           int groups, int64_t T,
+                                                           const float* __restrict__ thr,
+                                                           int nblk, int* blkcnt) {
+  __shared__ int wsum[kSelThreads / 32];
+  const int64_t N = (int64_t)groups * T;
+  int64_t lo, hi;
+  chunk_range(N, nblk, blockIdx.x, &lo, &hi);
+  int cnt = 0;
+  int64_t i = lo + threadIdx.x;
+  int g = (int)(i / T);
+  int64_t gend = (int64_t)(g + 1) * T;
+  float th = g < groups ? thr[g] : INFINITY;
+  for (; i < hi; i += blockDim.x) {
+    while (i >= gend) {
+      ++g;
+      gend += T;
+      th = thr[g];
+    }
+    cnt += vals[i] > th;
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) s += wsum[w];
+    blkcnt[blockIdx.x] = s;
+  }
+}
+
+// Exclusive scan of per-block counts (one block of 1024 threads).
+__global__ void __launch_bounds__(1024) k_scan_blocks(int nblk, const int* blkcnt, int* blkoff,
+                                                      int* total, int64_t cap,
+                                                      unsigned* status) {
+  __shared__ long long sh[1024];
+  const int per = (nblk + 1023) / 1024;
+  const int b0 = threadIdx.x * per;
+  long long local = 0;
+  for (int b = b0; b < b0 + per && b < nblk; ++b) local += blkcnt[b];
+  sh[threadIdx.x] = local;
+  __syncthreads();
+  for (int d = 1; d < 1024; d <<= 1) {
+    const long long add = threadIdx.x >= d ? sh[threadIdx.x - d] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += add;
+    __syncthreads();
+  }
+  long long run = sh[threadIdx.x] - local;
+  for (int b = b0; b < b0 + per && b < nblk; ++b) {
+    blkoff[b] = (int)(run < cap ? run : cap);
+    run += blkcnt[b];
+  }
+  if (threadIdx.x == 1023) {
+    const long long tot = sh[1023];
+    *total = (int)(tot < cap ? tot : cap);
+    if (tot > cap) atomicOr(status, kErrCapacity);
+  }
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restrict__ vals,
+                                                           int groups, int64_t T,
+                                                           const float* __restrict__ thr,
+                                                           const double* __restrict__ cs,
+                                                           int nblk, const int* blkoff,
+                                                           SelItem* items, int64_t cap) {
+  __shared__ int wcnt[kSelThreads / 32];
+  const int64_t N = (int64_t)groups * T;
+  int64_t lo, hi;
+  chunk_range(N, nblk, blockIdx.x, &lo, &hi);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t run = blkoff[blockIdx.x];
+  int g = (int)((lo + threadIdx.x) / T);
+  int64_t gend = (int64_t)(g + 1) * T;
+  for (int64_t base = lo; base < hi; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool sel = false;
+    float v = 0.f;
+    if (i < hi) {
+      while (i >= gend) {
+        ++g;
+        gend += T;
+      }
+      v = vals[i];
+      sel = v > thr[g];
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, sel);
+    if (lane == 0) wcnt[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, tile = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) {
+      before += w < warp ? wcnt[w] : 0;
+      tile += wcnt[w];
+    }
+    if (sel) {
+      const int64_t pos = run + before + __popc(bal & ((1u << lane) - 1u));
+      if (pos < cap) {
+        SelItem it;
+        it.group = g;
+        it.t = (int32_t)(i - (int64_t)g * T);
+        it.z = ((double)v - cs[2 * g]) / cs[2 * g + 1];
+        items[pos] = it;
+      }
+    }
+    run += tile;
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_select(const float* vals, int groups, int64_t T, const float* thr,
+                          const double* cs, const SelectScratch& s, unsigned* status,
+                          cudaStream_t st) {
+  k_sel_count<<<s.nblk, kSelThreads, 0, st>>>(vals, groups, T, thr, s.nblk, s.blkcnt);
+  k_scan_blocks<<<1, 1024, 0, st>>>(s.nblk, s.blkcnt, s.blkoff, s.nsel, s.capacity, status);
+  k_sel_write<<<s.nblk, kSelThreads, 0, st>>>(vals, groups, T, thr, cs, s.nblk, s.blkoff,
+                                              s.items, s.capacity);
+  count_launches(3);
+  return cudaGetLastError();
+}
+
+__global__ void k_sum_counts(int nblk, const int* blkcnt, long long* total) {
+  __shared__ long long sh[256];
+  long long s = 0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += blkcnt[b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int d = 128; d > 0; d >>= 1) {
+    if (threadIdx.x < d) sh[threadIdx.x] += sh[threadIdx.x + d];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = sh[0];
+}
+
+cudaError_t launch_count_selected(const float* vals, int groups, int64_t T, const float* thr,
+                                  int nblk, int* blkcnt, long long* total, cudaStream_t st) {
+  k_sel_count<<<nblk, kSelThreads, 0, st>>>(vals, groups, T, thr, nblk, blkcnt);
+  k_sum_counts<<<1, 256, 0, st>>>(nblk, blkcnt, total);
+  count_launches(2);
+  return cudaGetLastError();
+}
+
+__global__ void k_clamp_count(int* n, int cap, unsigned* status) {
+  if (*n > cap) {
+    *n = cap;
+    atomicOr(status, kErrCapacity);
+  }
+}
+
+cudaError_t launch_clamp_count(int* n, int cap, unsigned* status, cudaStream_t st) {
+  k_clamp_count<<<1, 1, 0, st>>>(n, cap, status);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- components
+__device__ __forceinline__ int64_t item_key(const SelItem& it, int64_t T) {
+  return (int64_t)it.group * T + it.t;
+}
+
+__device__ __forceinline__ int find_root(int* parent, int x) {
+  volatile int* p = parent;
+  int y = p[x];
+  while (y != x) {
+    const int z = p[y];
+    if (z != y) p[x] = z;   // path halving; only non-roots are written
+    x = y;
+    y = p[x];
+  }
+  return x;
+}
+
+__device__ void unite(int* parent, int a, int b, unsigned* status) {
+  for (int it = 0; it < (1 << 20); ++it) {
+    a = find_root(parent, a);
+    b = find_root(parent, b);
+    if (a == b) return;
+    const int hi = a > b ? a : b, lo = a > b ? b : a;
+    const int old = atomicCAS(&parent[hi], hi, lo);
+    if (old == hi) return;
+    a = old;
+    b = lo;
+  }
+  atomicOr(status, kErrCcLimit);
+}
+
+__global__ void k_cc_init(const int* nsel, int* parent, unsigned long long* compmax, int* peak) {
+  const int n = *nsel;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    parent[i] = i;
+    compmax[i] = 0ull;
+    peak[i] = INT_MAX;
+  }
+}
+
+__global__ void k_cc_union(const SelItem* __restrict__ items, const int* nsel, int Tx, int Ty,
+                           int64_t T, int* parent, unsigned* status) {
+  const int n = *nsel;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const SelItem me = items[i];
+    const int ty = me.t / Tx, tx = me.t - (me.t / Tx) * Tx;
+    const int64_t gbase = (int64_t)me.group * T;
+    const int dys[4] = {-1, -1, -1, 0}, dxs[4] = {-1, 0, 1, -1};
+    for (int q = 0; q < 4; ++q) {
+      const int ny = ty + dys[q], nx = tx + dxs[q];
+      if (ny < 0 || nx < 0 || nx >= Tx) continue;
+      const int64_t key = gbase + (int64_t)ny * Tx + nx;
+      int lo = 0, hi = i;   // neighbours precede i in the sorted list
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (item_key(items[mid], T) < key) lo = mid + 1; else hi = mid;
+      }
+      if (lo < i && item_key(items[lo], T) == key) unite(parent, i, lo, status);
+    }
+  }
+}
+
+__global__ void k_cc_flatten(const int* nsel, int* parent) {
+  const int n = *nsel;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    parent[i] = find_root(parent, i);
+}
+
+__global__ void k_cc_peak(const SelItem* __restrict__ items, const int* nsel, const int* parent,
+                          unsigned long long* compmax, int* peak, int stage) {
+  const int n = *nsel;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned long long k = f64_key(items[i].z);
+    const int r = parent[i];
+    if (stage == 0) atomicMax(&compmax[r], k);
+    else if (k == compmax[r]) atomicMin(&peak[r], i);
+  }
+}
+
+cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
+                              unsigned* status, cudaStream_t st) {
+  const int grid = 152 * 4, thr = 256;
+  k_cc_init<<<grid, thr, 0, st>>>(s.nsel, s.parent, s.compmax, s.peak);
+  k_cc_union<<<grid, thr, 0, st>>>(s.items, s.nsel, Tx, Ty, T, s.parent, status);
+  k_cc_flatten<<<grid, thr, 0, st>>>(s.nsel, s.parent);
+  k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak, 0);
+  k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak, 1);
+  count_launches(5);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- candidates
+__device__ __forceinline__ float load_px(const void* base, int storage, int64_t idx) {
+  switch (storage) {
+    case FITRIG_BF16: return to_f32(static_cast<const bf16_t*>(base)[idx]);
+    case FITRIG_F16: return to_f32(static_cast<const f16_t*>(base)[idx]);
+    default: return static_cast<const float*>(base)[idx];
+  }
+}
+
+__device__ __forceinline__ float parabola(float l, float c, float r) {
+  if (!isfinite(l) || !isfinite(c) || !isfinite(r)) return 0.f;
+  const float den = l - 2.f * c + r;
+  if (!(den < 0.f)) return 0.f;
+  const float d = 0.5f * (l - r) / den;
+  return fminf(0.5f, fmaxf(-0.5f, d));
+}
+
+// One warp per list entry; only component roots emit.
+__global__ void k_emit(CandArgs a, const SelItem* __restrict__ items, const int* nsel,
+                       const int* parent, const int* peak) {
+  const int n = *nsel;
+  const int lane = threadIdx.x & 31;
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int i = wid; i < n; i += nw) {
+    if (parent[i] != i) continue;
+    const SelItem it = items[peak[i]];
+    const int ty = it.t / a.Tx, tx = it.t - (it.t / a.Tx) * a.Tx;
+    const int hw = min(a.w, a.ny - ty * a.w), ww = min(a.w, a.nx - tx * a.w);
+    fitrig_candidate c;
+    c.significance = (float)it.z;
+    if (a.branch == FITRIG_BRANCH_IMAGE) {
+      // in-tile arg-max of Delta (ties: smallest row-major index), same FP32
+      // arithmetic as the stack march
+      const int64_t s0 = (int64_t)it.group * a.slice;
+      float best = -1.f;
+      int bidx = INT_MAX;
+      for (int q = lane; q < hw * ww; q += 32) {
+        const int dy = q / ww, dx = q - (q / ww) * ww;
+        const int64_t off = (int64_t)(ty * a.w + dy) * a.pitch + (tx * a.w + dx);
+        const float x0 = load_px(a.stack, a.storage, s0 + off);
+        const float x1 = load_px(a.stack, a.storage, s0 + a.slice + off);
+        const float x2 = load_px(a.stack, a.storage, s0 + 2 * a.slice + off);
+        const float d = fabsf(fabsf(x2 - x1) - fabsf(x1 - x0));
+        if (d > best) {
+          best = d;
+          bidx = q;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+        if (ob > best || (ob == best && oi < bidx)) {
+          best = ob;
+          bidx = oi;
+        }
+      }
+      c.x = tx * a.w + bidx % ww;
+      c.y = ty * a.w + bidx / ww;
+      c.snapshot = it.group;
+      c.branch = FITRIG_BRANCH_IMAGE;
+      c.freq_bin = -1;
+      c.xf = (float)c.x;
+      c.yf = (float)c.y;
+    } else {
+      const float e = a.eta[it.t];
+      const float el = tx > 0 ? a.eta[it.t - 1] : NAN;
+      const float er = tx + 1 < a.Tx ? a.eta[it.t + 1] : NAN;
+      const float eu = ty > 0 ? a.eta[it.t - a.Tx] : NAN;
+      const float ed = ty + 1 < a.Ty ? a.eta[it.t + a.Tx] : NAN;
+      c.x = tx * a.w + (ww - 1) / 2;
+      c.y = ty * a.w + (hw - 1) / 2;
+      c.snapshot = -1;
+      c.branch = FITRIG_BRANCH_FREQ;
+      c.freq_bin = a.bin[it.t];
+      c.xf = (float)(tx * a.w) + 0.5f * (float)(ww - 1) + parabola(el, e, er) * (float)a.w;
+      c.yf = (float)(ty * a.w) + 0.5f * (float)(hw - 1) + parabola(eu, e, ed) * (float)a.w;
+    }
+    if (lane == 0) {
+      const int pos = atomicAdd(a.nout, 1);
+      if (pos < a.cap) a.out[pos] = c;
+    }
+  }
+}
+
+cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, cudaStream_t st) {
+  k_emit<<<152 * 2, 256, 0, st>>>(a, s.items, s.nsel, s.parent, s.peak);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- sort
+__device__ __forceinline__ unsigned long long cand_key(const fitrig_candidate& c) {
+  return ((unsigned long long)(unsigned)(c.snapshot + 1) << 42) |
+         ((unsigned long long)(unsigned)c.y << 21) | (unsigned long long)(unsigned)c.x;
+}
+
+// Stable LSD radix sort (8-bit digits) in one CTA: n is small (candidates).
+__global__ void __launch_bounds__(1024) k_sort_candidates(fitrig_candidate* a,
+                                                          fitrig_candidate* b, const int* pn) {
+  __shared__ unsigned hist[256];
+  __shared__ unsigned base[256];
+  __shared__ unsigned ctot[256];
+  __shared__ unsigned wcnt[32][256];
+  __shared__ unsigned long long kmax[32];
+  const int n = *pn;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long mk = 0;
+  for (int i = tid; i < n; i += 1024) mk = max(mk, cand_key(a[i]));
+  for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
+  if (lane == 0) kmax[warp] = mk;
+  __syncthreads();
+  mk = 0;
+  for (int w = 0; w < 32; ++w) mk = max(mk, kmax[w]);
+  int bits = 0;
+  while (bits < 64 && (mk >> bits) != 0ull) ++bits;
+  const int passes = (bits + 7) / 8;
+  fitrig_candidate* src = a;
+  fitrig_candidate* dst = b;
+  for (int p = 0; p < passes; ++p) {
+    const int sh = 8 * p;
+    if (tid < 256) hist[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += 1024) atomicAdd(&hist[(cand_key(src[i]) >> sh) & 255ull], 1u);
+    __syncthreads();
+    if (tid == 0) {
+      unsigned run = 0;
+      for (int d = 0; d < 256; ++d) {
+        base[d] = run;
+        run += hist[d];
+      }
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < n; c0 += 1024) {
+      const int i = c0 + tid;
+      const bool valid = i < n;
+      fitrig_candidate v;
+      unsigned d = 256;
+      if (valid) {
+        v = src[i];
+        d = (unsigned)((cand_key(v) >> sh) & 255ull);
+      }
+      for (int q = tid; q < 32 * 256; q += 1024) (&wcnt[0][0])[q] = 0;
+      __syncthreads();
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+      if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = __popc(peers);
+      __syncthreads();
+      if (tid < 256) {
+        unsigned acc = 0;
+        for (int w = 0; w < 32; ++w) {
+          const unsigned t = wcnt[w][tid];
+          wcnt[w][tid] = acc;
+          acc += t;
+        }
+        ctot[tid] = acc;
+      }
+      __syncthreads();
+      if (valid) dst[base[d] + wcnt[warp][d] + rank] = v;
+      __syncthreads();
+      if (tid < 256) base[tid] += ctot[tid];
+      __syncthreads();
+    }
+    fitrig_candidate* t = src;
+    src = dst;
+    dst = t;
+  }
+  if (src != a)
+    for (int i = tid; i < n; i += 1024) a[i] = src[i];
+}
+
+cudaError_t launch_sort_candidates(fitrig_candidate* c, fitrig_candidate* tmp, const int* n,
+                                   cudaStream_t st) {
+  k_sort_candidates<<<1, 1024, 0, st>>>(c, tmp, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace fitrig

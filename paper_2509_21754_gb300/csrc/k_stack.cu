@@ -1,0 +1,307 @@
+// Stack-march tile statistics: one HBM pass over the snapshot stack.
+//
+// For every tile t and unit s (snapshots s, s+1, s+2) this computes, following
+// Eq. (tLISI) and Eq. 3-5 of the paper (Sec. 2.2.4), with the sum form of the
+// kernel equation in Sec. 2.3:
+//   D^(s)   = |x^(s+1) - x^(s)|,  D^(s+1) = |x^(s+2) - x^(s+1)|
+//   Delta   = |D^(s) - D^(s+1)|
+//   r       = min(Delta / x-hat^(s+1), 1),  x-hat = C if x == 0 else |x| (or x)
+//   v_t     = (sum Delta / n_t) * max Delta * (sum r / n_t)
+// so that tLISI_t = 1 - v_t / M^2; M is one scalar for the stack and is
+// reduced here too (max over every pixel, Eq. tLISI denominator).
+//
+// GB300 design (differs from the paper's one-block-per-tile kernel, which
+// re-reads a materialised Delta image per unit):
+//   * a CTA owns a box of TBX x TBY tiles and marches through time; each
+//     snapshot box arrives by a 3-D TMA load into a ring of shared-memory
+//     stages completed on mbarriers, so every stack pixel is read from HBM once;
+//   * each thread owns one pixel column of R rows of a tile band and carries
+//     x^(s+1) and D^(s) in registers from one snapshot to the next, so Delta and
+//     r never touch memory;
+//   * per-thread partial sums go to shared memory once per snapshot, and one
+//     thread per tile combines them in a fixed order (deterministic).
+// The one __syncthreads per snapshot also guards the reuse of ring stages, so
+// no "empty" barriers are needed.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace fitrig {
+
+constexpr int kStackMaxThreads = 512;
+
+template <typename T, int R, bool SIGNED>
+__global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_constant__ CUtensorMap tmap,
+                                                     const StackArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const StackGeom& g = a.g;
+  const int NS = g.stages;
+  float4* part = reinterpret_cast<float4*>(smem + (size_t)NS * g.stage_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(part + 2 * g.threads);
+
+  const int tid = threadIdx.x;
+  const int c = tid % g.BW;
+  const int rest = tid / g.BW;
+  const int band = rest / g.nseg;
+  const int seg = rest - band * g.nseg;
+  const int rcount = min(R, g.w - seg * R);
+  const int row0 = band * g.w + seg * R;
+  const int x0 = blockIdx.x * g.BW;
+  const int y0 = blockIdx.y * g.BH;
+  const int xload = g.aligned ? x0 : (x0 & ~7);
+  const int col = (x0 - xload) + c;
+  const uint32_t bar0 = smem_u32(bars);
+  const uint32_t stage0 = smem_u32(smem);
+  const uint32_t box_bytes = (uint32_t)(g.boxW * g.BH * (int)sizeof(T));
+  const int L = a.nsnap;
+
+  if (tid == 0) {
+    prefetch_tmap(&tmap);
+    for (int i = 0; i < NS; ++i) mbar_init(bar0 + 8 * i, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < NS && j < L; ++j) {
+      mbar_expect_tx(bar0 + 8 * j, box_bytes);
+      tma_load_3d(stage0 + j * (uint32_t)g.stage_bytes, &tmap, xload, y0, j, bar0 + 8 * j);
+    }
+  }
+
+  float xp[R], dp[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) xp[i] = dp[i] = 0.f;
+  float mx = -INFINITY;
+  const uint64_t deadline = globaltimer_ns() + a.timeout_ns;
+
+  for (int j = 0; j < L; ++j) {
+    const int stg = j % NS;
+    const bool ok = mbar_wait_bounded(bar0 + 8 * stg, (uint32_t)((j / NS) & 1), deadline);
+    const T* st = reinterpret_cast<const T*>(smem + (size_t)stg * g.stage_bytes);
+    if (ok) {
+      if (j >= 2) {
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          if (i < rcount) {
+            const float xn = to_f32(st[(row0 + i) * g.boxW + col]);
+            mx = fmaxf(mx, xn);
+            const float dn = fabsf(xn - xp[i]);        // D^(s+1)
+            const float d = fabsf(dn - dp[i]);         // Delta
+            const float ref = SIGNED ? xp[i] : fabsf(xp[i]);
+            const float xh = (xp[i] == 0.f) ? kGuardC : ref;   // Eq. 5
+            const float r = fminf(__fdividef(d, xh), 1.f);     // Eq. 4
+            s1 += d;
+            s2 = fmaxf(s2, d);
+            s3 += r;
+            dp[i] = dn;
+            xp[i] = xn;
+          }
+        }
+        part[(j & 1) * g.threads + tid] = make_float4(s1, s2, s3, 0.f);
+      } else {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          if (i < rcount) {
+            const float xn = to_f32(st[(row0 + i) * g.boxW + col]);
+            mx = fmaxf(mx, xn);
+            dp[i] = fabsf(xn - xp[i]);   // D^(0) once j == 1
+            xp[i] = xn;
+          }
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      // A stage never completed: flag it, let in-flight copies land (bounded),
+      // and leave.  No thread touches the ring after this point.
+      if (tid == 0) {
+        atomicOr(a.status, kErrTimeout);
+        const uint64_t d2 = globaltimer_ns() + 1000000ull;
+        for (int jj = j; jj < L && jj < j + NS; ++jj)
+          mbar_wait_bounded(bar0 + 8 * (jj % NS), (uint32_t)((jj / NS) & 1), d2);
+      }
+      return;
+    }
+    if (tid == 0 && j + NS < L) {
+      fence_proxy_async_smem();
+      mbar_expect_tx(bar0 + 8 * stg, box_bytes);
+      tma_load_3d(stage0 + stg * (uint32_t)g.stage_bytes, &tmap, xload, y0, j + NS,
+                  bar0 + 8 * stg);
+    }
+    if (j >= 2 && tid < g.TBX * g.TBY) {
+      const int tb = tid / g.TBX;
+      const int tbx = tid - tb * g.TBX;
+      const int tx = blockIdx.x * g.TBX + tbx;
+      const int ty = blockIdx.y * g.TBY + tb;
+      if (tx < a.Tx && ty < a.Ty) {
+        const float4* pp = part + (j & 1) * g.threads;
+        float S1 = 0.f, S2 = 0.f, S3 = 0.f;
+        for (int sg = 0; sg < g.nseg; ++sg) {
+          const float4* row = pp + (tb * g.nseg + sg) * g.BW + tbx * g.w;
+          for (int cc = 0; cc < g.w; ++cc) {
+            const float4 q = row[cc];
+            S1 += q.x;
+            S2 = fmaxf(S2, q.y);
+            S3 += q.z;
+          }
+        }
+        const int hw = min(g.w, a.ny - ty * g.w);
+        const int ww = min(g.w, a.nx - tx * g.w);
+        const float n = (float)(hw * ww);
+        float v = (S1 / n) * S2 * (S3 / n);
+        if (!isfinite(S1) || !isfinite(v)) v = NAN;
+        a.vp[(size_t)(j - 2) * (size_t)a.T + (size_t)ty * a.Tx + tx] = v;
+      }
+    }
+  }
+  // Global maximum M (NaN ignored by fmaxf; +inf is resolved on the host).
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0 && mx > -INFINITY) atomicMax(a.gmax, f32_key(mx));
+}
+
+// Finite maximum over the stack; used only when the fused maximum saw +inf.
+template <typename T>
+__global__ void k_finite_max(const T* __restrict__ x, int L, int ny, int nx, int64_t pitch,
+                             unsigned* gmax) {
+  float m = -INFINITY;
+  const int64_t total = (int64_t)L * ny * nx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / ((int64_t)ny * nx);
+    const int64_t rem = i - s * ny * nx;
+    const int64_t yy = rem / nx, xx = rem - yy * nx;
+    const float v = to_f32(x[(s * ny + yy) * pitch + xx]);
+    if (isfinite(v)) m = fmaxf(m, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > -INFINITY) atomicMax(gmax, f32_key(m));
+}
+
+bool stack_geometry(int w, int elem_bytes, StackGeom* g) {
+  if (w < 1 || w > 128) return false;
+  // rows per thread R (a template value) and row segments per tile band
+  int R, nseg;
+  if (w <= 8) {
+    R = w;
+    nseg = 1;
+  } else if (w <= 32) {
+    nseg = (w + 7) / 8;
+    R = (w + nseg - 1) / nseg;
+  } else if (w <= 64) {
+    R = 16;
+    nseg = (w + 15) / 16;
+  } else {
+    R = 32;
+    nseg = (w + 31) / 32;
+  }
+  // Tiles per CTA in x: about 160 pixel columns, preferring an origin that is
+  // always a multiple of 8 elements (TMA needs 16-byte aligned x).
+  const int max_cols = std::min(160, kStackMaxThreads / nseg);
+  if (w > max_cols) return false;
+  int tbx = 0;
+  for (int t = max_cols / w; t >= 1; --t)
+    if ((t * w) % 8 == 0) { tbx = t; break; }
+  bool aligned = tbx > 0;
+  if (!aligned) tbx = max_cols / w;
+  const int BW = tbx * w;
+  int tby = 320 / (BW * nseg);
+  if (tby < 1) tby = 1;
+  if (tby * w > 256) tby = 256 / w;
+  if (tby < 1) return false;
+  const int threads = BW * tby * nseg;
+  if (threads > kStackMaxThreads) return false;
+  const int boxW = aligned ? BW : ((BW + 7) / 8) * 8 + 8;
+  if (boxW > 256) return false;
+  const int BH = tby * w;
+  size_t stage = (size_t)boxW * BH * elem_bytes;
+  stage = (stage + 127) / 128 * 128;
+  const size_t fixed = (size_t)2 * threads * sizeof(float4) + 8 * 8;
+  const size_t limit = 232448 - 1024;
+  int ns = 4;
+  while (ns > 2 && fixed + ns * stage > limit) --ns;
+  if (fixed + ns * stage > limit) return false;
+  g->w = w;
+  g->R = R;
+  g->nseg = nseg;
+  g->TBX = tbx;
+  g->TBY = tby;
+  g->BW = BW;
+  g->BH = BH;
+  g->boxW = boxW;
+  g->aligned = aligned;
+  g->stages = ns;
+  g->threads = threads;
+  g->stage_bytes = stage;
+  g->smem_bytes = fixed + ns * stage;
+  return true;
+}
+
+template <typename T, int R, bool SIGNED>
+static cudaError_t launch_one(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
+  auto kern = k_stack_tile<T, R, SIGNED>;
+  static size_t configured = 0;
+  if (a.g.smem_bytes > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)a.g.smem_bytes);
+    if (e != cudaSuccess) return e;
+    configured = a.g.smem_bytes;
+  }
+  dim3 grid(a.g.gridX, a.g.gridY);
+  kern<<<grid, a.g.threads, a.g.smem_bytes, st>>>(*tmap, a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T, bool SIGNED>
+static cudaError_t launch_r(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
+  switch (a.g.R) {
+    case 1: return launch_one<T, 1, SIGNED>(tmap, a, st);
+    case 2: return launch_one<T, 2, SIGNED>(tmap, a, st);
+    case 3: return launch_one<T, 3, SIGNED>(tmap, a, st);
+    case 4: return launch_one<T, 4, SIGNED>(tmap, a, st);
+    case 5: return launch_one<T, 5, SIGNED>(tmap, a, st);
+    case 6: return launch_one<T, 6, SIGNED>(tmap, a, st);
+    case 7: return launch_one<T, 7, SIGNED>(tmap, a, st);
+    case 8: return launch_one<T, 8, SIGNED>(tmap, a, st);
+    case 16: return launch_one<T, 16, SIGNED>(tmap, a, st);
+    case 32: return launch_one<T, 32, SIGNED>(tmap, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_stack(const CUtensorMap* tmap, const StackArgs& a, int storage, int rmode,
+                         cudaStream_t st) {
+  const bool sg = rmode == FITRIG_RMODE_SIGNED;
+  switch (storage) {
+    case FITRIG_F32: return sg ? launch_r<float, true>(tmap, a, st) : launch_r<float, false>(tmap, a, st);
+    case FITRIG_BF16: return sg ? launch_r<bf16_t, true>(tmap, a, st) : launch_r<bf16_t, false>(tmap, a, st);
+    case FITRIG_F16: return sg ? launch_r<f16_t, true>(tmap, a, st) : launch_r<f16_t, false>(tmap, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_finite_max(const void* stack, int storage, int L, int ny, int nx,
+                              int64_t pitch, unsigned* gmax, cudaStream_t st) {
+  const int blocks = 152 * 8, threads = 256;
+  switch (storage) {
+    case FITRIG_F32:
+      k_finite_max<float><<<blocks, threads, 0, st>>>((const float*)stack, L, ny, nx, pitch, gmax);
+      break;
+    case FITRIG_BF16:
+      k_finite_max<bf16_t><<<blocks, threads, 0, st>>>((const bf16_t*)stack, L, ny, nx, pitch, gmax);
+      break;
+    case FITRIG_F16:
+      k_finite_max<f16_t><<<blocks, threads, 0, st>>>((const f16_t*)stack, L, ny, nx, pitch, gmax);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace fitrig

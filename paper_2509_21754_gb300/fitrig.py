@@ -1,0 +1,338 @@
+"""ctypes binding of libfitrig (include/fitrig.h), one function per C entry point.
+
+Argument marshalling only: every step of the trigger runs in the CUDA library.
+Importing this module does not load the library; the first call does, and it
+raises ``FitrigError`` if the library is missing -- there is no CPU fallback.
+
+Tensors: snapshots may be torch tensors (CUDA or CPU) or NumPy arrays; device
+pointers are passed for CUDA tensors, host pointers otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (POINTER, byref, c_char_p, c_double, c_float, c_int, c_int32, c_int64,
+                    c_void_p)
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, ESTATE, ECUDA, ETIMEOUT, ETRUNC, ENONFINITE, EBUSY, EUNSUPPORTED = range(10)
+BRANCH_IMAGE, BRANCH_FREQ, BRANCH_BOTH = 1, 2, 3
+F32, BF16, F16 = 0, 1, 2
+OPT_STORAGE, OPT_NOISE, OPT_RMODE, OPT_EDGE, OPT_STREAM, OPT_TIMEOUT_NS = 1, 2, 3, 5, 8, 9
+NOISE_MEANSTD, NOISE_MEDMAD = 0, 1
+RMODE_ABS, RMODE_SIGNED = 0, 1
+EDGE_PARTIAL, EDGE_DROP = 0, 1
+KERNEL_STACK, KERNEL_NOISE, KERNEL_SELECT, KERNEL_SPECTRUM, KERNEL_DETECT = range(5)
+
+# statuses that still carry valid results
+SOFT = (OK, ENONFINITE)
+
+
+class Candidate(ctypes.Structure):
+    _fields_ = [("x", c_int32), ("y", c_int32), ("snapshot", c_int32),
+                ("significance", c_float), ("branch", c_int32), ("freq_bin", c_int32),
+                ("xf", c_float), ("yf", c_float)]
+
+
+CANDIDATE_DTYPE = np.dtype([("x", np.int32), ("y", np.int32), ("snapshot", np.int32),
+                            ("significance", np.float32), ("branch", np.int32),
+                            ("freq_bin", np.int32), ("xf", np.float32), ("yf", np.float32)])
+
+
+class FitrigError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None):
+    """Load libfitrig.so (building it first if sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        try:
+            _build.build()
+        except Exception as e:  # noqa: BLE001
+            raise FitrigError(ECUDA, f"libfitrig is not built and could not be built ({e})")
+    lib = ctypes.CDLL(p)
+    P = c_void_p
+    sig = {
+        "fitrig_version": (c_char_p, []),
+        "fitrig_status_string": (c_char_p, [c_int]),
+        "fitrig_plan_create": (c_int, [c_int, c_int, c_int, c_int, c_double, c_int, POINTER(P)]),
+        "fitrig_plan_set": (c_int, [P, c_int, c_int64]),
+        "fitrig_push_snapshot": (c_int, [P, P, c_int, c_int, c_int64]),
+        "fitrig_plan_reset": (c_int, [P]),
+        "fitrig_detect": (c_int, [P, POINTER(c_int32)]),
+        "fitrig_candidates": (c_int, [P, P, c_int32, POINTER(c_int32)]),
+        "fitrig_tlisi": (c_int, [P, c_int32, P, c_int32]),
+        "fitrig_unit_values": (c_int, [P, c_int32, P, c_int32]),
+        "fitrig_noise_params": (c_int, [P, c_int32, POINTER(c_double), POINTER(c_double)]),
+        "fitrig_spectrum": (c_int, [P, P, P, c_int32]),
+        "fitrig_global_max": (c_int, [P, POINTER(c_double)]),
+        "fitrig_tile_grid": (c_int, [P, POINTER(c_int32), POINTER(c_int32)]),
+        "fitrig_kernel_ms": (c_int, [P, c_int, POINTER(c_float)]),
+        "fitrig_stack_device_ptr": (c_int, [P, c_int32, POINTER(P), POINTER(c_int64)]),
+        "fitrig_threshold_map": (c_int, [P, c_int64, c_double, c_int, c_int64,
+                                         POINTER(c_int64), POINTER(c_double), POINTER(c_double)]),
+        "fitrig_launch_count": (c_int, [POINTER(c_int64)]),
+        "fitrig_plan_destroy": (c_int, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(s: int) -> str:
+    try:
+        return load().fitrig_status_string(int(s)).decode()
+    except Exception:  # noqa: BLE001
+        return f"status {s}"
+
+
+def _check(rc: int, where: str, allow=(OK,)) -> int:
+    if rc not in allow:
+        raise FitrigError(rc, where)
+    return rc
+
+
+def _ptr_dtype(data) -> Tuple[int, int, int, int]:
+    """(pointer, dtype code, on_device, row pitch in elements) of an image."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(data, torch.Tensor):
+        code = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}.get(data.dtype)
+        if code is None or data.dim() != 2 or data.stride(1) != 1:
+            raise FitrigError(EINVAL, "push: need a 2-D float32/bfloat16/float16 tensor with unit column stride")
+        return data.data_ptr(), code, int(data.is_cuda), int(data.stride(0))
+    a = np.asarray(data)
+    code = {np.dtype(np.float32): F32, np.dtype(np.float16): F16}.get(a.dtype)
+    if code is None or a.ndim != 2 or a.strides[1] != a.itemsize:
+        raise FitrigError(EINVAL, "push: need a 2-D float32/float16 array with unit column stride")
+    return a.ctypes.data, code, 0, a.strides[0] // a.itemsize
+
+
+# ---------------------------------------------------------------- entry points
+def fitrig_version() -> str:
+    return load().fitrig_version().decode()
+
+
+def fitrig_plan_create(nx: int, ny: int, nsnap: int, window: int, nsigma: float,
+                       branch: int = BRANCH_IMAGE) -> c_void_p:
+    h = c_void_p()
+    _check(load().fitrig_plan_create(nx, ny, nsnap, window, float(nsigma), branch, byref(h)),
+           "fitrig_plan_create")
+    return h
+
+
+def fitrig_plan_set(plan, option: int, value: int) -> None:
+    _check(load().fitrig_plan_set(plan, option, int(value)), "fitrig_plan_set")
+
+
+def fitrig_push_snapshot(plan, data, row_pitch_elems: Optional[int] = None) -> None:
+    ptr, code, dev, pitch = _ptr_dtype(data)
+    if row_pitch_elems is not None:
+        pitch = row_pitch_elems
+    _check(load().fitrig_push_snapshot(plan, c_void_p(ptr), code, dev, pitch),
+           "fitrig_push_snapshot")
+
+
+def fitrig_plan_reset(plan) -> None:
+    _check(load().fitrig_plan_reset(plan), "fitrig_plan_reset")
+
+
+def fitrig_detect(plan) -> Tuple[int, int]:
+    """Returns (status, ncand); raises unless status is OK or ENONFINITE."""
+    n = c_int32()
+    rc = load().fitrig_detect(plan, byref(n))
+    _check(rc, "fitrig_detect", allow=SOFT)
+    return rc, n.value
+
+
+def fitrig_candidates(plan, cap: Optional[int] = None) -> np.ndarray:
+    n = c_int32()
+    lib = load()
+    if cap is None:
+        lib.fitrig_candidates(plan, None, 0, byref(n))
+        cap = n.value
+    out = np.zeros(max(cap, 1), dtype=CANDIDATE_DTYPE)
+    rc = lib.fitrig_candidates(plan, c_void_p(out.ctypes.data), cap, byref(n))
+    _check(rc, "fitrig_candidates", allow=(OK, ETRUNC))
+    return out[:min(cap, n.value)]
+
+
+def fitrig_tile_grid(plan) -> Tuple[int, int]:
+    ty, tx = c_int32(), c_int32()
+    _check(load().fitrig_tile_grid(plan, byref(ty), byref(tx)), "fitrig_tile_grid")
+    return ty.value, tx.value
+
+
+def _tile_floats(fn, plan, unit) -> np.ndarray:
+    ty, tx = fitrig_tile_grid(plan)
+    out = np.empty(ty * tx, dtype=np.float32)
+    _check(fn(plan, unit, c_void_p(out.ctypes.data), out.size), fn.__name__)
+    return out.reshape(ty, tx)
+
+
+def fitrig_tlisi(plan, unit: int) -> np.ndarray:
+    return _tile_floats(load().fitrig_tlisi, plan, unit)
+
+
+def fitrig_unit_values(plan, unit: int) -> np.ndarray:
+    return _tile_floats(load().fitrig_unit_values, plan, unit)
+
+
+def fitrig_noise_params(plan, unit: int) -> Tuple[float, float]:
+    c, s = c_double(), c_double()
+    _check(load().fitrig_noise_params(plan, unit, byref(c), byref(s)), "fitrig_noise_params")
+    return c.value, s.value
+
+
+def fitrig_spectrum(plan) -> Tuple[np.ndarray, np.ndarray]:
+    ty, tx = fitrig_tile_grid(plan)
+    eta = np.empty(ty * tx, dtype=np.float32)
+    kb = np.empty(ty * tx, dtype=np.int32)
+    _check(load().fitrig_spectrum(plan, c_void_p(eta.ctypes.data), c_void_p(kb.ctypes.data),
+                                  eta.size), "fitrig_spectrum")
+    return eta.reshape(ty, tx), kb.reshape(ty, tx)
+
+
+def fitrig_global_max(plan) -> float:
+    m = c_double()
+    _check(load().fitrig_global_max(plan, byref(m)), "fitrig_global_max")
+    return m.value
+
+
+def fitrig_kernel_ms(plan, kernel: int) -> float:
+    ms = c_float()
+    _check(load().fitrig_kernel_ms(plan, kernel, byref(ms)), "fitrig_kernel_ms")
+    return ms.value
+
+
+def fitrig_stack_device_ptr(plan, s: int) -> Tuple[int, int]:
+    p, pitch = c_void_p(), c_int64()
+    _check(load().fitrig_stack_device_ptr(plan, s, byref(p), byref(pitch)),
+           "fitrig_stack_device_ptr")
+    return p.value, pitch.value
+
+
+def fitrig_threshold_map(dev_map, nsigma: float, noise_mode: int = NOISE_MEANSTD,
+                         stream: int = 0) -> Tuple[int, float, float]:
+    """dev_map: a contiguous float32 CUDA tensor; returns (nexceed, centre, scale)."""
+    n, c, s = c_int64(), c_double(), c_double()
+    _check(load().fitrig_threshold_map(c_void_p(dev_map.data_ptr()), dev_map.numel(),
+                                       float(nsigma), noise_mode, int(stream), byref(n),
+                                       byref(c), byref(s)), "fitrig_threshold_map")
+    return n.value, c.value, s.value
+
+
+def fitrig_launch_count() -> int:
+    n = c_int64()
+    _check(load().fitrig_launch_count(byref(n)), "fitrig_launch_count")
+    return n.value
+
+
+def fitrig_plan_destroy(plan) -> None:
+    _check(load().fitrig_plan_destroy(plan), "fitrig_plan_destroy")
+
+
+# ---------------------------------------------------------------- convenience
+class Plan:
+    """Owns a plan handle; pushes a whole (L, ny, nx) stack and detects."""
+
+    def __init__(self, nx, ny, nsnap, window, nsigma, branch=BRANCH_IMAGE, storage=F32,
+                 noise=NOISE_MEANSTD, rmode=RMODE_ABS, edge=EDGE_PARTIAL, stream=None):
+        self.h = fitrig_plan_create(nx, ny, nsnap, window, nsigma, branch)
+        try:
+            fitrig_plan_set(self.h, OPT_STORAGE, storage)
+            fitrig_plan_set(self.h, OPT_NOISE, noise)
+            fitrig_plan_set(self.h, OPT_RMODE, rmode)
+            fitrig_plan_set(self.h, OPT_EDGE, edge)
+            if stream is None:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            if stream:
+                fitrig_plan_set(self.h, OPT_STREAM, stream)
+        except Exception:
+            fitrig_plan_destroy(self.h)
+            raise
+        self.nsnap = nsnap
+
+    def push_stack(self, stack) -> None:
+        for k in range(stack.shape[0]):
+            fitrig_push_snapshot(self.h, stack[k])
+
+    def detect(self) -> Tuple[int, np.ndarray]:
+        rc, n = fitrig_detect(self.h)
+        return rc, fitrig_candidates(self.h, n)
+
+    def close(self):
+        if self.h is not None:
+            fitrig_plan_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def detect_stack(stack, window: int, nsigma: float, branch: int = BRANCH_IMAGE,
+                 storage: int = F32, noise: int = NOISE_MEANSTD, rmode: int = RMODE_ABS,
+                 edge: int = EDGE_PARTIAL, dumps: bool = True) -> dict:
+    """Push an (L, ny, nx) stack, detect, and read back candidates and dumps."""
+    L, ny, nx = (int(d) for d in stack.shape)
+    with Plan(nx, ny, L, window, nsigma, branch, storage, noise, rmode, edge) as p:
+        p.push_stack(stack)
+        rc, cands = p.detect()
+        out = {"status": rc, "candidates": cands}
+        if dumps:
+            ty, tx = fitrig_tile_grid(p.h)
+            out["grid"] = (ty, tx)
+            out["M"] = fitrig_global_max(p.h)
+            if branch & BRANCH_IMAGE:
+                out["values"] = np.stack([fitrig_unit_values(p.h, s) for s in range(L - 2)])
+                out["noise"] = np.array([fitrig_noise_params(p.h, s) for s in range(L - 2)])
+            if branch & BRANCH_FREQ:
+                out["eta"], out["bin"] = fitrig_spectrum(p.h)
+                out["eta_noise"] = fitrig_noise_params(p.h, -1)
+            out["kernel_ms"] = {k: fitrig_kernel_ms(p.h, k) for k in range(5)}
+        return out
+
+
+def decisions(res: dict, nsigma: float):
+    """The library's own threshold decisions, (double)v > centre + tau * scale."""
+    def image(s, ty, tx):
+        c, sc = res["noise"][s]
+        return sc > 0 and float(res["values"][s, ty, tx]) > c + nsigma * sc
+
+    def freq(ty, tx):
+        c, sc = res["eta_noise"]
+        return sc > 0 and float(res["eta"][ty, tx]) > c + nsigma * sc
+    return image, freq

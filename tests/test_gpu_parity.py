@@ -1,0 +1,253 @@
+"""CUDA path against the FP64 oracle, element by element and candidate by
+candidate, on seeded synthetic stacks.  All calls go through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import compare as C  # noqa: E402
+from oracle import fitrig_oracle as O  # noqa: E402
+from paper_2509_21754_gb300 import fitrig as F  # noqa: E402
+from paper_2509_21754_gb300 import synth  # noqa: E402
+
+NOISE = {"meanstd": F.NOISE_MEANSTD, "medmad": F.NOISE_MEDMAD}
+RMODE = {"abs": F.RMODE_ABS, "signed": F.RMODE_SIGNED}
+EDGE = {"partial": F.EDGE_PARTIAL, "drop": F.EDGE_DROP}
+STORAGE = {"f32": (F.F32, torch.float32), "bf16": (F.BF16, torch.bfloat16),
+           "f16": (F.F16, torch.float16)}
+
+
+def stored(stack_t, storage):
+    """The values the library stores (half formats round to nearest even)."""
+    tdt = STORAGE[storage][1]
+    return stack_t.to(tdt).to(torch.float32).cpu().numpy()
+
+
+def run_both(stack_t, w, tau, branch=F.BRANCH_IMAGE, noise="meanstd", rmode="abs",
+             edge="partial", storage="f32"):
+    res = F.detect_stack(stack_t.cuda(), w, tau, branch, STORAGE[storage][0], NOISE[noise],
+                         RMODE[rmode], EDGE[edge])
+    torch.cuda.synchronize()
+    x = stored(stack_t, storage)
+    det = O.detect(x, w, tau, branch, noise, rmode, edge)
+    return res, det, x
+
+
+def assert_parity(res, det, x, w, tau, branch, noise="meanstd", rmode="abs", edge="partial",
+                  rel=1e-5):
+    di, dfq = F.decisions(res, tau)
+    errs = C.compare(res["candidates"], x, w, tau, branch, noise, rmode, edge, di, dfq, det)
+    assert not errs, errs[:10]
+    if branch & F.BRANCH_IMAGE:
+        ref = np.stack([u.numerator for u in det.units])
+        ok, worst = C.values_close(res["values"], ref, rel=rel)
+        assert ok, f"tile values differ, worst relative error {worst}"
+        assert res["M"] == det.M
+
+
+# ---------------------------------------------------------------- workloads
+def test_config1_full_parity_both_noise_modes():
+    """16 snapshots of 512 x 512, window 5, 6 sigma (the small workload)."""
+    stack, truth = synth.make_stack(synth.C1, seed=1, device="cuda")
+    for noise in ("meanstd", "medmad"):
+        res, det, x = run_both(stack, 5, 6.0, F.BRANCH_IMAGE, noise)
+        assert_parity(res, det, x, 5, 6.0, F.BRANCH_IMAGE, noise)
+        # noise parameters of every unit: same estimator on the same values
+        for s in range(x.shape[0] - 2):
+            c, sc = res["noise"][s]
+            assert sc == pytest.approx(det.scale[s] * det.M ** 2, rel=1e-5)
+            assert c == pytest.approx(det.centre[s] * det.M ** 2, rel=1e-5)
+
+
+@pytest.mark.parametrize("L,ny,nx,w", [
+    (5, 37, 53, 4), (6, 64, 70, 7), (4, 33, 33, 33), (3, 20, 31, 1), (8, 100, 90, 16),
+    (5, 130, 141, 32), (4, 200, 150, 64), (3, 129, 300, 128), (7, 61, 45, 3), (5, 90, 97, 9),
+    (4, 77, 200, 20), (3, 50, 50, 50),
+])
+def test_ragged_shapes_and_tile_sizes(L, ny, nx, w):
+    spec = synth.small_spec(L, ny, nx, n_steady=6, n_pulsed=2, pulse_period=(3, 4))
+    stack, _ = synth.make_stack(spec, seed=ny * 7 + nx + w, device="cuda")
+    tau = 3.0
+    res, det, x = run_both(stack, w, tau)
+    assert_parity(res, det, x, w, tau, F.BRANCH_IMAGE)
+
+
+@pytest.mark.parametrize("rmode", ["abs", "signed"])
+@pytest.mark.parametrize("edge", ["partial", "drop"])
+@pytest.mark.parametrize("noise", ["meanstd", "medmad"])
+def test_options(rmode, edge, noise):
+    spec = synth.small_spec(9, 123, 118, n_steady=10, n_pulsed=3, pulse_period=(3, 5))
+    stack, _ = synth.make_stack(spec, seed=3, device="cuda")
+    res, det, x = run_both(stack, 5, 3.5, F.BRANCH_IMAGE, noise, rmode, edge)
+    assert_parity(res, det, x, 5, 3.5, F.BRANCH_IMAGE, noise, rmode, edge)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_half_storage_parity(storage):
+    """Half storage: the oracle sees the same rounded values."""
+    stack, _ = synth.make_stack(synth.small_spec(10, 256, 256), seed=5, device="cuda")
+    res, det, x = run_both(stack, 5, 4.0, F.BRANCH_BOTH, storage=storage)
+    assert_parity(res, det, x, 5, 4.0, F.BRANCH_BOTH)
+
+
+@pytest.mark.parametrize("L,n,w,period", [(64, 120, 5, 4), (66, 96, 4, 8), (32, 64, 8, 3),
+                                          (5, 40, 4, 2), (130, 48, 6, 16)])
+def test_frequency_branch_parity(L, n, w, period):
+    x = synth.periodic_tile_stack(L, n, n + 3, w, period, 1, (2, 3), 6.0, seed=L + n)
+    stack = torch.from_numpy(x)
+    for noise in ("meanstd", "medmad"):
+        res, det, xs = run_both(stack, w, 4.0, F.BRANCH_FREQ, noise)
+        assert_parity(res, det, xs, w, 4.0, F.BRANCH_FREQ, noise)
+        ok, worst = C.values_close(res["eta"], det.eta / 1.0 * det.M ** 2, rel=1e-4)
+        assert ok, worst
+
+
+def test_both_branches_c2_like():
+    spec = synth.small_spec(64, 512, 512)
+    stack, _ = synth.make_stack(spec, seed=11, device="cuda")
+    res, det, x = run_both(stack, 5, 6.0, F.BRANCH_BOTH, "medmad")
+    assert_parity(res, det, x, 5, 6.0, F.BRANCH_BOTH, "medmad")
+
+
+# ---------------------------------------------------------------- properties
+def test_medmad_is_bit_exact_on_own_values():
+    spec = synth.small_spec(12, 300, 257)
+    stack, _ = synth.make_stack(spec, seed=13, device="cuda")
+    res = F.detect_stack(stack, 3, 5.0, F.BRANCH_BOTH, noise=F.NOISE_MEDMAD)
+    for s in range(10):
+        v = res["values"][s].ravel()
+        v = v[np.isfinite(v)]
+        med = np.sort(v)[(v.size - 1) // 2]
+        mad = np.sort(np.abs(v - med))[(v.size - 1) // 2]   # float32 arithmetic
+        c, sc = res["noise"][s]
+        assert np.float32(c) == med and c == float(med)
+        assert sc == 1.482602218505602 * float(mad)
+    e = res["eta"].ravel()
+    med = np.sort(e)[(e.size - 1) // 2]
+    mad = np.sort(np.abs(e - med))[(e.size - 1) // 2]
+    assert res["eta_noise"][0] == float(med)
+    assert res["eta_noise"][1] == 1.482602218505602 * float(mad)
+
+
+def test_identical_snapshots_give_no_candidates():
+    one = torch.randn(1, 64, 80, generator=torch.Generator().manual_seed(1))
+    stack = one.repeat(6, 1, 1)
+    res = F.detect_stack(stack.cuda(), 4, 3.0, F.BRANCH_BOTH)
+    assert len(res["candidates"]) == 0
+    assert np.all(res["values"] == 0.0)
+    assert np.all(res["noise"][:, 1] == 0.0)
+
+
+def test_nonfinite_pixels_invalidate_tiles():
+    spec = synth.small_spec(6, 60, 64, n_steady=4, n_pulsed=1)
+    stack, _ = synth.make_stack(spec, seed=17, device="cuda")
+    stack[2, 10, 11] = float("nan")
+    stack[4, 40, 50] = float("inf")
+    stack[0, 5, 5] = float("-inf")
+    res, det, x = run_both(stack, 4, 3.0, F.BRANCH_BOTH)
+    assert res["status"] == F.ENONFINITE
+    assert np.array_equal(np.isnan(res["values"]), np.isnan(det.tlisi))
+    assert_parity(res, det, x, 4, 3.0, F.BRANCH_BOTH)
+
+
+def test_injected_pulse_found_at_its_pixel():
+    """A pulse in snapshot k is reported at its pixel in units k and k-2."""
+    g = torch.Generator().manual_seed(5)
+    stack = torch.randn(9, 96, 96, generator=g)
+    k, py, px = 5, 41, 67
+    stack[k, py, px] += 60.0
+    res = F.detect_stack(stack.cuda(), 4, 5.0)
+    hits = {int(c["snapshot"]) for c in res["candidates"] if (c["y"], c["x"]) == (py, px)}
+    assert hits == {k - 2, k}
+
+
+def test_scale_invariance_of_candidates():
+    spec = synth.small_spec(8, 128, 128)
+    stack, _ = synth.make_stack(spec, seed=19, device="cuda")
+    r1 = F.detect_stack(stack, 5, 4.0, F.BRANCH_BOTH)
+    r2 = F.detect_stack(stack * 4.0, 5, 4.0, F.BRANCH_BOTH)   # a power of two: exact
+    assert np.array_equal(r1["candidates"][["x", "y", "snapshot"]],
+                          r2["candidates"][["x", "y", "snapshot"]])
+    assert r2["M"] == 4.0 * r1["M"]
+
+
+def test_determinism():
+    stack, _ = synth.make_stack(synth.small_spec(20, 300, 310), seed=23, device="cuda")
+    a = F.detect_stack(stack, 5, 4.0, F.BRANCH_BOTH, noise=F.NOISE_MEANSTD)
+    b = F.detect_stack(stack, 5, 4.0, F.BRANCH_BOTH, noise=F.NOISE_MEANSTD)
+    assert a["candidates"].tobytes() == b["candidates"].tobytes()
+    assert a["values"].tobytes() == b["values"].tobytes()
+    assert np.array_equal(a["noise"], b["noise"])
+    assert a["eta"].tobytes() == b["eta"].tobytes()
+
+
+def test_tlisi_report_matches_oracle():
+    stack, _ = synth.make_stack(synth.small_spec(6, 100, 100), seed=29, device="cuda")
+    x = stack.cpu().numpy()
+    det = O.detect(x, 5, 4.0)
+    with F.Plan(100, 100, 6, 5, 4.0) as p:
+        p.push_stack(stack)
+        p.detect()
+        for s in range(4):
+            t = F.fitrig_tlisi(p.h, s)
+            np.testing.assert_allclose(t, det.tlisi[s], rtol=0, atol=1e-6)
+
+
+@pytest.mark.parametrize("noise", ["meanstd", "medmad"])
+@pytest.mark.parametrize("tau", [3.0, 4.0])
+def test_threshold_stage_gaussian_tail(noise, tau):
+    """Exceedances of a pure N(0,1) map match Q(tau) within 4 binomial sigma."""
+    from scipy.special import erfc
+    n = 100_000_000
+    g = torch.Generator(device="cuda").manual_seed(int(tau))
+    v = torch.randn(n, device="cuda", generator=g)
+    k, c, s = F.fitrig_threshold_map(v, tau, NOISE[noise], torch.cuda.current_stream().cuda_stream)
+    q = 0.5 * erfc(tau / math.sqrt(2.0))
+    sd = math.sqrt(n * q * (1 - q))
+    slack = 4 * sd + (0.002 * n * q if noise == "medmad" else 0.0)
+    assert abs(k - n * q) <= slack, (k, n * q)
+    assert abs(c) < 1e-3 and abs(s - 1.0) < 1e-3
+
+
+def test_push_conversions_and_pitches():
+    """fp32 input into half storage, host input, and padded row pitch."""
+    stack, _ = synth.make_stack(synth.small_spec(5, 70, 90), seed=31, device="cuda")
+    ref = F.detect_stack(stack.to(torch.bfloat16), 5, 3.0, storage=F.BF16)
+    with F.Plan(90, 70, 5, 5, 3.0, storage=F.BF16) as p:
+        big = torch.zeros(5, 70, 128, device="cuda")
+        big[:, :, :90] = stack
+        for k in range(5):
+            if k % 2:
+                F.fitrig_push_snapshot(p.h, big[k, :, :90])          # device, pitch 128
+            else:
+                F.fitrig_push_snapshot(p.h, stack[k].cpu().numpy())  # host fp32
+        rc, c = p.detect()
+        vals = np.stack([F.fitrig_unit_values(p.h, s) for s in range(3)])
+    assert vals.tobytes() == ref["values"].tobytes()
+    assert c.tobytes() == ref["candidates"].tobytes()
+
+
+def test_state_errors():
+    with F.Plan(32, 32, 4, 4, 3.0) as p:
+        with pytest.raises(F.FitrigError) as e:
+            F.fitrig_detect(p.h)
+        assert e.value.status == F.ESTATE
+        x = torch.randn(4, 32, 32, device="cuda")
+        p.push_stack(x)
+        with pytest.raises(F.FitrigError) as e:
+            F.fitrig_push_snapshot(p.h, x[0])
+        assert e.value.status == F.ESTATE
+        with pytest.raises(F.FitrigError) as e:
+            F.fitrig_plan_set(p.h, F.OPT_STORAGE, F.BF16)
+        assert e.value.status == F.ESTATE
+        p.detect()
+        F.fitrig_plan_reset(p.h)
+        p.push_stack(x)
+        rc, _ = p.detect()
+        assert rc == F.OK

@@ -181,17 +181,17 @@ def oracle_sample(a, stack_np, budget_s=12.0):
     from oracle import fitrig_oracle as O
     noise = a.noise
     L, ny, nx = stack_np.shape
-    rows = 40   # 8 tile rows at window 5
+    rows = 8 * a.window   # 8 tile rows
     done_px, t_used, strips = 0, 0.0, 0
-    y0 = 0
-    while t_used < budget_s and y0 + rows <= ny:
+    nstrip = max(1, ny // rows)
+    while t_used < budget_s and strips < 4 * nstrip:
+        y0 = ((strips * 13) % nstrip) * rows
         strip = stack_np[:, y0:y0 + rows, :]
         t0 = time.perf_counter()
         O.detect(strip, a.window, a.nsigma, O.BRANCH_BOTH, noise)
         t_used += time.perf_counter() - t0
-        done_px += L * rows * nx
+        done_px += L * strip.shape[1] * nx
         strips += 1
-        y0 += rows * 13
     desc = (f"{strips} strips of {L} snapshots x {rows} rows x {nx} columns "
             f"({done_px / 1e6:.0f} Mpixel) of the same stack, FP64 NumPy oracle, "
             f"noise statistics over each strip")

@@ -74,12 +74,18 @@ enum {
   FITRIG_OPT_NOISE = 2,      /* FITRIG_NOISE_MEANSTD (default) | FITRIG_NOISE_MEDMAD  */
   FITRIG_OPT_RMODE = 3,      /* FITRIG_RMODE_ABS (default) | FITRIG_RMODE_SIGNED      */
   FITRIG_OPT_EDGE = 5,       /* FITRIG_EDGE_PARTIAL (default) | FITRIG_EDGE_DROP      */
+  FITRIG_OPT_STRIDE = 6,     /* FITRIG_STRIDE_TILE (default) | FITRIG_STRIDE_SLIDING  */
   FITRIG_OPT_STREAM = 8,     /* cudaStream_t cast to int64; 0 = the plan's own stream */
   FITRIG_OPT_TIMEOUT_NS = 9  /* bound of every device-side wait (default 2e9 ns)      */
 };
 enum { FITRIG_NOISE_MEANSTD = 0, FITRIG_NOISE_MEDMAD = 1 };
 enum { FITRIG_RMODE_ABS = 0, FITRIG_RMODE_SIGNED = 1 };
 enum { FITRIG_EDGE_PARTIAL = 0, FITRIG_EDGE_DROP = 1 };
+/* STRIDE_SLIDING evaluates the tile statistic over the odd window centred on
+ * every pixel (clipped at the border) instead of on the paper's disjoint tiles;
+ * every pixel then acts as a 1 x 1 tile (Ty = ny, Tx = nx) for the noise,
+ * selection, components and candidates.  Needs an odd window <= 31. */
+enum { FITRIG_STRIDE_TILE = 0, FITRIG_STRIDE_SLIDING = 1 };
 
 /* Kernels whose last device time fitrig_kernel_ms reports. */
 enum { FITRIG_KERNEL_STACK = 0, FITRIG_KERNEL_NOISE = 1, FITRIG_KERNEL_SELECT = 2,

@@ -37,6 +37,9 @@ Readings where the paper is silent or ambiguous (each is an option here):
   through the eta values of the neighbouring tiles.
 * the transform is the unnormalised DFT of exact length n = L - 2, bins
   k = 1..floor(n/2).
+* a sliding-window mode (not in the paper, whose tiles partition the image)
+  evaluates the tile statistic over the odd w x w window centred on each pixel,
+  clipped at the border, and then treats pixels as 1 x 1 tiles.
 
 All pins of this module live in ``tests/test_oracle_pins.py``.
 """
@@ -165,6 +168,46 @@ def unit_tiles(stack: np.ndarray, s: int, w: int, rmode: str = "abs",
     a, b, c = (stack[s + i, :nyu, :nxu] for i in range(3))
     delta, r, fin = unit_terms(a, b, c, rmode)
     return tile_reduce(delta, r, fin, w, Ty, Tx)
+
+
+def window_stats(delta: np.ndarray, r: np.ndarray, finite: np.ndarray, w: int) -> UnitTiles:
+    """Sliding-window statistics: for every pixel p, the sums of Delta and r and
+    the maximum of Delta over the w x w window centred on p (w odd), clipped at
+    the image border (n_p = number of in-image pixels).  Accumulates the w*w
+    shifted copies of the maps one offset at a time.  The arg-max fields hold
+    the pixel itself (the pixel is the location in this mode)."""
+    if w % 2 != 1:
+        raise ValueError("sliding windows need an odd size")
+    ny, nx = delta.shape
+    h = w // 2
+    S1 = np.zeros((ny, nx))
+    S2 = np.full((ny, nx), -np.inf)
+    S3 = np.zeros((ny, nx))
+    n = np.zeros((ny, nx))
+    valid = np.ones((ny, nx), dtype=bool)
+    for dy in range(-h, h + 1):
+        for dx in range(-h, h + 1):
+            # window pixel q = p + (dy, dx); rows/cols of p for which q is inside
+            py0, py1 = max(0, -dy), min(ny, ny - dy)
+            px0, px1 = max(0, -dx), min(nx, nx - dx)
+            if py0 >= py1 or px0 >= px1:
+                continue
+            q = (slice(py0 + dy, py1 + dy), slice(px0 + dx, px1 + dx))
+            p = (slice(py0, py1), slice(px0, px1))
+            S1[p] += delta[q]
+            S2[p] = np.maximum(S2[p], delta[q])
+            S3[p] += r[q]
+            n[p] += 1.0
+            valid[p] &= finite[q]
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    return UnitTiles(S1, S2, S3, n, valid, yy, xx)
+
+
+def unit_windows(stack: np.ndarray, s: int, w: int, rmode: str = "abs") -> UnitTiles:
+    """Per-pixel sliding-window statistics of unit s (the 'local window' mode)."""
+    a, b, c = (stack[s + i] for i in range(3))
+    delta, r, fin = unit_terms(a, b, c, rmode)
+    return window_stats(delta, r, fin, w)
 
 
 def tlisi_from_tiles(ut: UnitTiles, M: float) -> np.ndarray:
@@ -420,13 +463,23 @@ def freq_candidates(eta: np.ndarray, kbin: np.ndarray, z: np.ndarray, tau: float
 
 def detect(stack: np.ndarray, w: int, tau: float, branch: int = BRANCH_IMAGE,
            noise: str = "meanstd", rmode: str = "abs", edge: str = "partial",
-           forced_image=None, forced_freq=None) -> Detection:
-    """Run the trigger on a (L, ny, nx) stack and return the sorted candidates."""
+           forced_image=None, forced_freq=None, stride: str = "tile") -> Detection:
+    """Run the trigger on a (L, ny, nx) stack and return the sorted candidates.
+
+    stride "tile" is the paper's tiling; "sliding" evaluates the same statistic
+    over a w x w window centred on every pixel, after which every pixel plays
+    the part of a 1 x 1 tile in the z-score, selection and components.
+    """
     x = np.asarray(stack)
     L, ny, nx = x.shape
-    Ty, Tx, nyu, nxu = tiling(ny, nx, w, edge)
-    M = normaliser_M(x[:, :nyu, :nxu])
-    units = [unit_tiles(x, s, w, rmode, edge) for s in range(L - 2)]
+    if stride == "sliding":
+        M = normaliser_M(x)
+        units = [unit_windows(x, s, w, rmode) for s in range(L - 2)]
+        Ty, Tx, nyu, nxu, w = ny, nx, ny, nx, 1
+    else:
+        Ty, Tx, nyu, nxu = tiling(ny, nx, w, edge)
+        M = normaliser_M(x[:, :nyu, :nxu])
+        units = [unit_tiles(x, s, w, rmode, edge) for s in range(L - 2)]
     tl = np.stack([tlisi_from_tiles(u, M) for u in units])
     det = Detection([], M, Ty, Tx, tlisi=tl, units=units)
     cands: List[Candidate] = []

@@ -151,6 +151,29 @@ cudaError_t launch_stack(const CUtensorMap* tmap, const StackArgs& a, int storag
 cudaError_t launch_finite_max(const void* stack, int storage, int L, int ny, int nx,
                               int64_t pitch, unsigned* gmax, cudaStream_t st);
 
+// Sliding-window mode geometry (see k_slide.cu).
+struct SlideGeom {
+  int w, h;            // window and half-width
+  int OW, OH;          // output pixels per CTA
+  int EW, EH;          // extended block with halo
+  int nseg;            // row segments of kSlideR rows
+  int boxW;            // TMA box width (x origin rounded down to 8 elements)
+  int threads, stages;
+  size_t stage_bytes, smem_bytes;
+  int gridX, gridY;
+};
+struct SlideArgs {
+  int nx, ny, nsnap;
+  float* vp;           // [nsnap-2][ny][nx]
+  unsigned* gmax;
+  unsigned* status;
+  uint64_t timeout_ns;
+  SlideGeom g;
+};
+bool slide_geometry(int w, int elem_bytes, SlideGeom* g);
+cudaError_t launch_slide(const CUtensorMap* tmap, const SlideArgs& a, int storage, int rmode,
+                         cudaStream_t st);
+
 // Noise: per-group centre/scale of `vals` ([groups][n], NaN = excluded).
 struct NoiseScratch {
   double* part;        // [groups][nblk] partial sums
@@ -184,6 +207,9 @@ struct SelectScratch {
   int* parent;         // capacity
   unsigned long long* compmax;  // capacity
   int* peak;           // capacity
+  int* map;            // [groups * T] list index + 1 of selected entries, else 0
+  int* plist;          // capacity: list indices of component peaks, in list order
+  int* npeak;          // device count of plist
   int64_t capacity;
 };
 cudaError_t launch_select(const float* vals, int groups, int64_t T, const float* thr,
@@ -211,9 +237,11 @@ struct CandArgs {
   int* nout;
   int64_t cap;
 };
-cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, cudaStream_t st);
-cudaError_t launch_sort_candidates(fitrig_candidate* c, fitrig_candidate* tmp, const int* n,
-                                   cudaStream_t st);
+// Appends the branch's candidates in (snapshot, y, x) order: frequency
+// candidates at positions [0, n_peaks), image candidates after *base.  Adds
+// the number of peaks to *a.nout and clears the selection map.
+cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, int* base,
+                                   fitrig_candidate* tmp, unsigned* status, cudaStream_t st);
 
 // Frequency branch.
 cudaError_t launch_spectrum(const float* vp, int n, int64_t T, const float2* twiddle,

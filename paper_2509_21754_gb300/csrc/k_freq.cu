@@ -78,8 +78,94 @@ __global__ void __launch_bounds__(kDftThreads) k_dft(const float* __restrict__ v
   bin[t] = bk;
 }
 
+// Short series (n <= 2*KMAX + 1): the pair loop runs outermost and the
+// accumulators of every bin stay in registers; each twiddle is a shared-memory
+// broadcast, so one load feeds two multiply-adds.
+template <int KMAX>
+__global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restrict__ vp, int n,
+                                                           int64_t T,
+                                                           const float2* __restrict__ tw,
+                                                           float* eta, int* bin) {
+  extern __shared__ float2 tws[];   // [H][K] twiddles, pair-major, then [n][threads] series
+  const int H = (n - 1) / 2, K = n / 2;
+  float* ys = reinterpret_cast<float*>(tws + H * K);
+  for (int i = threadIdx.x; i < H * K; i += blockDim.x) {
+    const int q = i / K, k = i - (i / K) * K;
+    tws[i] = tw[(size_t)k * H + q];
+  }
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * kDftThreads + threadIdx.x;
+  if (t >= T) return;
+  float s = 0.f, comp = 0.f;
+  bool ok = true;
+  float* my = ys + threadIdx.x;
+  for (int q = 0; q < n; ++q) {
+    const float v = vp[(size_t)q * T + t];
+    ok = ok && isfinite(v);
+    my[q * kDftThreads] = v;
+    const float y = v - comp;
+    const float u = s + y;
+    comp = (u - s) - y;
+    s = u;
+  }
+  if (!ok) {
+    eta[t] = NAN;
+    bin[t] = -1;
+    return;
+  }
+  const float mean = s / (float)n;
+  const bool even = (n & 1) == 0;
+  const float y0 = my[0] - mean;
+  const float ymid = even ? my[(n / 2) * kDftThreads] - mean : 0.f;
+  float re[KMAX], im[KMAX];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    re[k] = y0 + ((even && ((k + 1) & 1)) ? -ymid : ymid);
+    im[k] = 0.f;
+  }
+  for (int q = 1; q <= H; ++q) {
+    const float a = my[q * kDftThreads] - mean;
+    const float b = my[(n - q) * kDftThreads] - mean;
+    const float e = a + b, o = a - b;
+    const float2* row = tws + (q - 1) * K;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+      if (k < K) {
+        const float2 cs = row[k];
+        re[k] = fmaf(e, cs.x, re[k]);
+        im[k] = fmaf(o, cs.y, im[k]);
+      }
+    }
+  }
+  float best = -1.f;
+  int bk = 1;
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    if (k < K) {
+      const float m2 = re[k] * re[k] + im[k] * im[k];
+      if (m2 > best) {
+        best = m2;
+        bk = k + 1;
+      }
+    }
+  }
+  eta[t] = sqrtf(best);
+  bin[t] = bk;
+}
+
 cudaError_t launch_spectrum(const float* vp, int n, int64_t T, const float2* twiddle,
                             float* eta, int* bin, cudaStream_t st) {
+  const int64_t blocks = (T + kDftThreads - 1) / kDftThreads;
+  const int H = (n - 1) / 2, K = n / 2;
+  if (n <= 65 && H >= 1) {
+    const size_t sm = (size_t)H * K * sizeof(float2) + (size_t)n * kDftThreads * sizeof(float);
+    if (K <= 16)
+      k_dft_short<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, twiddle, eta, bin);
+    else
+      k_dft_short<32><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, twiddle, eta, bin);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)n * kDftThreads * sizeof(float);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
@@ -88,7 +174,6 @@ cudaError_t launch_spectrum(const float* vp, int n, int64_t T, const float2* twi
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  const int64_t blocks = (T + kDftThreads - 1) / kDftThreads;
   k_dft<<<(unsigned)blocks, kDftThreads, smem, st>>>(vp, n, T, twiddle, eta, bin);
   count_launches(1);
   return cudaGetLastError();

@@ -170,58 +170,82 @@ __global__ void __launch_bounds__(kNoiseThreads) k_rs_hist(const float* __restri
     if (sh[b]) atomicAdd(&hist[(size_t)g * kBins + b], sh[b]);
 }
 
-// One thread per group: locate the digit holding the target rank, clear the
-// histogram for the next pass, and finish the value after the last digit.
-__global__ void k_rs_select(int groups, int64_t n, int pass, int mad, unsigned* hist,
-                            unsigned* rsel, double* cs, unsigned long long* invalid) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= groups) return;
+// One block per group: locate the digit holding the target rank (block-wide
+// scan of the histogram), clear the histogram for the next pass, and finish
+// the value after the last digit.
+constexpr int kSelectThreads = 256;
+
+__global__ void __launch_bounds__(kSelectThreads) k_rs_select(int groups, int64_t n, int pass,
+                                                              int mad, unsigned* hist,
+                                                              unsigned* rsel, double* cs,
+                                                              unsigned long long* invalid) {
+  __shared__ unsigned long long scan[kSelectThreads];
+  __shared__ int found_bin;
+  __shared__ unsigned found_below;
+  const int g = blockIdx.x;
+  const int tid = threadIdx.x;
   unsigned* h = hist + (size_t)g * kBins;
   unsigned* st = rsel + 4 * g;
   const int nb = pass == 2 ? 1024 : 2048;
-  if (pass == 0) {
-    unsigned long long tot = 0;
-    for (int b = 0; b < nb; ++b) tot += h[b];
-    if (!mad) {
-      st[2] = (unsigned)tot;
-      if (invalid && (int64_t)tot < n) atomicAdd(invalid, (unsigned long long)(n - (int64_t)tot));
-    }
-    st[3] = tot == 0 ? 1u : 0u;
-    st[1] = tot == 0 ? 0u : (unsigned)((tot - 1) / 2);
+  const int per = nb / kSelectThreads;
+  unsigned local[8];
+  unsigned long long mine = 0;
+  for (int i = 0; i < per; ++i) {
+    local[i] = h[tid * per + i];
+    mine += local[i];
   }
+  scan[tid] = mine;
+  __syncthreads();
+  for (int d = 1; d < kSelectThreads; d <<= 1) {
+    const unsigned long long add = tid >= d ? scan[tid - d] : 0ull;
+    __syncthreads();
+    scan[tid] += add;
+    __syncthreads();
+  }
+  const unsigned long long total = scan[kSelectThreads - 1];
+  const unsigned long long before = scan[tid] - mine;
+  for (int i = 0; i < per; ++i) h[tid * per + i] = 0;   // ready for the next pass
+  if (pass == 0 && tid == 0) {
+    if (!mad) {
+      st[2] = (unsigned)total;
+      if (invalid && (int64_t)total < n) atomicAdd(invalid, (unsigned long long)(n - (int64_t)total));
+    }
+    st[3] = total == 0 ? 1u : 0u;
+    st[1] = total == 0 ? 0u : (unsigned)((total - 1) / 2);
+  }
+  __syncthreads();
   if (st[3]) {
-    for (int b = 0; b < nb; ++b) h[b] = 0;
-    if (pass == 2) {
+    if (tid == 0 && pass == 2) {
       if (!mad) cs[2 * g] = NAN;
       cs[2 * g + 1] = 0.0;
     }
     return;
   }
-  unsigned k = st[1];
-  unsigned cum = 0;
-  int sel = nb - 1;
-  for (int b = 0; b < nb; ++b) {
-    const unsigned c = h[b];
-    if (k < cum + c) {
-      sel = b;
-      break;
+  const unsigned k = st[1];
+  if ((unsigned long long)k >= before && (unsigned long long)k < before + mine) {
+    unsigned long long cum = before;
+    for (int i = 0; i < per; ++i) {
+      if (k < cum + local[i]) {
+        found_bin = tid * per + i;
+        found_below = (unsigned)cum;
+        break;
+      }
+      cum += local[i];
     }
-    cum += c;
   }
-  for (int b = 0; b < nb; ++b) h[b] = 0;
-  st[1] = k - cum;
+  __syncthreads();
+  if (tid != 0) return;
+  const unsigned sel = (unsigned)found_bin;
+  st[1] = k - found_below;
   if (pass == 0) {
-    st[0] = (unsigned)sel;
+    st[0] = sel;
   } else if (pass == 1) {
-    st[0] = (st[0] << 11) | (unsigned)sel;
+    st[0] = (st[0] << 11) | sel;
   } else {
-    const uint32_t key = (st[0] << 10) | (unsigned)sel;
+    const uint32_t key = (st[0] << 10) | sel;
     const float val = f32_from_key(key);
-    if (!mad) {
-      cs[2 * g] = (double)val;
-    } else {
-      cs[2 * g + 1] = kMadToSigma * (double)val;
-    }
+    if (!mad) cs[2 * g] = (double)val;
+    else cs[2 * g + 1] = kMadToSigma * (double)val;
     st[0] = 0;
   }
 }
@@ -253,8 +277,8 @@ cudaError_t launch_noise(const float* vals, int groups, int64_t n, int mode,
   for (int mad = 0; mad < 2; ++mad) {
     for (int pass = 0; pass < 3; ++pass) {
       k_rs_hist<<<grid, kNoiseThreads, 0, st>>>(vals, n, nblk, pass, mad, s.rsel, cs, s.hist);
-      k_rs_select<<<(groups + 127) / 128, 128, 0, st>>>(groups, n, pass, mad, s.hist, s.rsel, cs,
-                                                        s.invalid);
+      k_rs_select<<<groups, kSelectThreads, 0, st>>>(groups, n, pass, mad, s.hist, s.rsel, cs,
+                                                     s.invalid);
     }
   }
   count_launches(12);

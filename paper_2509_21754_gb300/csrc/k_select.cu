@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restri
                                                            const float* __restrict__ thr,
                                                            const double* __restrict__ cs,
                                                            int nblk, const int* blkoff,
-                                                           SelItem* items, int64_t cap) {
+                                                           SelItem* items, int* map,
+                                                           int64_t cap) {
   __shared__ int wcnt[kSelThreads / 32];
   const int64_t N = (int64_t)groups * T;
   int64_t lo, hi;
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restri
         it.t = (int32_t)(i - (int64_t)g * T);
         it.z = ((double)v - cs[2 * g]) / cs[2 * g + 1];
         items[pos] = it;
+        map[i] = (int)pos + 1;
       }
     }
     run += tile;
@@ -147,7 +149,7 @@ cudaError_t launch_select(const float* vals, int groups, int64_t T, const float*
   k_sel_count<<<s.nblk, kSelThreads, 0, st>>>(vals, groups, T, thr, s.nblk, s.blkcnt);
   k_scan_blocks<<<1, 1024, 0, st>>>(s.nblk, s.blkcnt, s.blkoff, s.nsel, s.capacity, status);
   k_sel_write<<<s.nblk, kSelThreads, 0, st>>>(vals, groups, T, thr, cs, s.nblk, s.blkoff,
-                                              s.items, s.capacity);
+                                              s.items, s.map, s.capacity);
   count_launches(3);
   return cudaGetLastError();
 }
@@ -227,7 +229,8 @@ __global__ void k_cc_init(const int* nsel, int* parent, unsigned long long* comp
 }
 
 __global__ void k_cc_union(const SelItem* __restrict__ items, const int* nsel, int Tx, int Ty,
-                           int64_t T, int* parent, unsigned* status) {
+                           int64_t T, const int* __restrict__ map, int* parent,
+                           unsigned* status) {
   const int n = *nsel;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const SelItem me = items[i];
@@ -237,13 +240,8 @@ __global__ void k_cc_union(const SelItem* __restrict__ items, const int* nsel, i
     for (int q = 0; q < 4; ++q) {
       const int ny = ty + dys[q], nx = tx + dxs[q];
       if (ny < 0 || nx < 0 || nx >= Tx) continue;
-      const int64_t key = gbase + (int64_t)ny * Tx + nx;
-      int lo = 0, hi = i;   // neighbours precede i in the sorted list
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (item_key(items[mid], T) < key) lo = mid + 1; else hi = mid;
-      }
-      if (lo < i && item_key(items[lo], T) == key) unite(parent, i, lo, status);
+      const int j = map[gbase + (int64_t)ny * Tx + nx] - 1;   // list index, or -1
+      if (j >= 0) unite(parent, i, j, status);
     }
   }
 }
@@ -269,7 +267,7 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
                               unsigned* status, cudaStream_t st) {
   const int grid = 152 * 4, thr = 256;
   k_cc_init<<<grid, thr, 0, st>>>(s.nsel, s.parent, s.compmax, s.peak);
-  k_cc_union<<<grid, thr, 0, st>>>(s.items, s.nsel, Tx, Ty, T, s.parent, status);
+  k_cc_union<<<grid, thr, 0, st>>>(s.items, s.nsel, Tx, Ty, T, s.map, s.parent, status);
   k_cc_flatten<<<grid, thr, 0, st>>>(s.nsel, s.parent);
   k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak, 0);
   k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak, 1);
@@ -277,7 +275,51 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- candidates
+// ---- ordered list of component peaks (sorted by (group, t) like the items)
+__global__ void __launch_bounds__(kSelThreads) k_peak_count(const int* nsel, const int* parent,
+                                                            const int* peak, int nblk,
+                                                            int* blkcnt) {
+  __shared__ int wsum[kSelThreads / 32];
+  int64_t lo, hi;
+  chunk_range(*nsel, nblk, blockIdx.x, &lo, &hi);
+  int cnt = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) cnt += peak[parent[i]] == (int)i;
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) t += wsum[w];
+    blkcnt[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_peak_write(const int* nsel, const int* parent,
+                                                            const int* peak, int nblk,
+                                                            const int* blkoff, int* plist) {
+  __shared__ int wcnt[kSelThreads / 32];
+  int64_t lo, hi;
+  chunk_range(*nsel, nblk, blockIdx.x, &lo, &hi);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int run = blkoff[blockIdx.x];
+  for (int64_t base = lo; base < hi; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const bool is_peak = i < hi && peak[parent[i]] == (int)i;
+    const unsigned bal = __ballot_sync(0xffffffffu, is_peak);
+    if (lane == 0) wcnt[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, tile = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) {
+      before += w < warp ? wcnt[w] : 0;
+      tile += wcnt[w];
+    }
+    if (is_peak) plist[run + before + __popc(bal & ((1u << lane) - 1u))] = (int)i;
+    run += tile;
+    __syncthreads();
+  }
+}
+
+// ---- candidates
 __device__ __forceinline__ float load_px(const void* base, int storage, int64_t idx) {
   switch (storage) {
     case FITRIG_BF16: return to_f32(static_cast<const bf16_t*>(base)[idx]);
@@ -294,164 +336,190 @@ __device__ __forceinline__ float parabola(float l, float c, float r) {
   return fminf(0.5f, fmaxf(-0.5f, d));
 }
 
-// One warp per list entry; only component roots emit.
-__global__ void k_emit(CandArgs a, const SelItem* __restrict__ items, const int* nsel,
-                       const int* parent, const int* peak) {
-  const int n = *nsel;
+// Frequency branch: one thread per peak; tile-centre order is (y, x) order,
+// so the peaks' list order is already the output order.
+__global__ void k_emit_freq(CandArgs a, const SelItem* __restrict__ items, const int* np_,
+                            const int* __restrict__ plist) {
+  const int np = *np_;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    const SelItem it = items[plist[p]];
+    const int ty = it.t / a.Tx, tx = it.t - (it.t / a.Tx) * a.Tx;
+    const int hw = min(a.w, a.ny - ty * a.w), ww = min(a.w, a.nx - tx * a.w);
+    const float e = a.eta[it.t];
+    const float el = tx > 0 ? a.eta[it.t - 1] : NAN;
+    const float er = tx + 1 < a.Tx ? a.eta[it.t + 1] : NAN;
+    const float eu = ty > 0 ? a.eta[it.t - a.Tx] : NAN;
+    const float ed = ty + 1 < a.Ty ? a.eta[it.t + a.Tx] : NAN;
+    fitrig_candidate c;
+    c.x = tx * a.w + (ww - 1) / 2;
+    c.y = ty * a.w + (hw - 1) / 2;
+    c.snapshot = -1;
+    c.significance = (float)it.z;
+    c.branch = FITRIG_BRANCH_FREQ;
+    c.freq_bin = a.bin[it.t];
+    c.xf = (float)(tx * a.w) + 0.5f * (float)(ww - 1) + parabola(el, e, er) * (float)a.w;
+    c.yf = (float)(ty * a.w) + 0.5f * (float)(hw - 1) + parabola(eu, e, ed) * (float)a.w;
+    if (p < a.cap) a.out[p] = c;
+  }
+}
+
+// Image branch, step 1: one warp per peak computes the tile's arg-max of Delta
+// (ties: smallest row-major index, same FP32 arithmetic as the stack march)
+// and writes the candidate in peak-list order to `tmp`.
+__global__ void k_emit_image(CandArgs a, const SelItem* __restrict__ items, const int* np_,
+                             const int* __restrict__ plist, fitrig_candidate* tmp) {
+  const int np = *np_;
   const int lane = threadIdx.x & 31;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int i = wid; i < n; i += nw) {
-    if (parent[i] != i) continue;
-    const SelItem it = items[peak[i]];
+  for (int p = wid; p < np; p += nw) {
+    const SelItem it = items[plist[p]];
     const int ty = it.t / a.Tx, tx = it.t - (it.t / a.Tx) * a.Tx;
     const int hw = min(a.w, a.ny - ty * a.w), ww = min(a.w, a.nx - tx * a.w);
-    fitrig_candidate c;
-    c.significance = (float)it.z;
-    if (a.branch == FITRIG_BRANCH_IMAGE) {
-      // in-tile arg-max of Delta (ties: smallest row-major index), same FP32
-      // arithmetic as the stack march
-      const int64_t s0 = (int64_t)it.group * a.slice;
-      float best = -1.f;
-      int bidx = INT_MAX;
-      for (int q = lane; q < hw * ww; q += 32) {
-        const int dy = q / ww, dx = q - (q / ww) * ww;
-        const int64_t off = (int64_t)(ty * a.w + dy) * a.pitch + (tx * a.w + dx);
-        const float x0 = load_px(a.stack, a.storage, s0 + off);
-        const float x1 = load_px(a.stack, a.storage, s0 + a.slice + off);
-        const float x2 = load_px(a.stack, a.storage, s0 + 2 * a.slice + off);
-        const float d = fabsf(fabsf(x2 - x1) - fabsf(x1 - x0));
-        if (d > best) {
-          best = d;
-          bidx = q;
-        }
+    const int64_t s0 = (int64_t)it.group * a.slice;
+    float best = -1.f;
+    int bidx = INT_MAX;
+    for (int q = lane; q < hw * ww; q += 32) {
+      const int dy = q / ww, dx = q - (q / ww) * ww;
+      const int64_t off = (int64_t)(ty * a.w + dy) * a.pitch + (tx * a.w + dx);
+      const float x0 = load_px(a.stack, a.storage, s0 + off);
+      const float x1 = load_px(a.stack, a.storage, s0 + a.slice + off);
+      const float x2 = load_px(a.stack, a.storage, s0 + 2 * a.slice + off);
+      const float d = fabsf(fabsf(x2 - x1) - fabsf(x1 - x0));
+      if (d > best) {
+        best = d;
+        bidx = q;
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-        if (ob > best || (ob == best && oi < bidx)) {
-          best = ob;
-          bidx = oi;
-        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) {
+        best = ob;
+        bidx = oi;
       }
+    }
+    if (lane == 0) {
+      fitrig_candidate c;
       c.x = tx * a.w + bidx % ww;
       c.y = ty * a.w + bidx / ww;
       c.snapshot = it.group;
+      c.significance = (float)it.z;
       c.branch = FITRIG_BRANCH_IMAGE;
       c.freq_bin = -1;
       c.xf = (float)c.x;
       c.yf = (float)c.y;
-    } else {
-      const float e = a.eta[it.t];
-      const float el = tx > 0 ? a.eta[it.t - 1] : NAN;
-      const float er = tx + 1 < a.Tx ? a.eta[it.t + 1] : NAN;
-      const float eu = ty > 0 ? a.eta[it.t - a.Tx] : NAN;
-      const float ed = ty + 1 < a.Ty ? a.eta[it.t + a.Tx] : NAN;
-      c.x = tx * a.w + (ww - 1) / 2;
-      c.y = ty * a.w + (hw - 1) / 2;
-      c.snapshot = -1;
-      c.branch = FITRIG_BRANCH_FREQ;
-      c.freq_bin = a.bin[it.t];
-      c.xf = (float)(tx * a.w) + 0.5f * (float)(ww - 1) + parabola(el, e, er) * (float)a.w;
-      c.yf = (float)(ty * a.w) + 0.5f * (float)(hw - 1) + parabola(eu, e, ed) * (float)a.w;
+      tmp[p] = c;
     }
+  }
+}
+
+// Image branch, step 2: peaks are in (unit, tile row, tile column) order.  Each
+// run of peaks sharing (unit, tile row) -- a group -- occupies the same output
+// positions once sorted by (y, x); inside a group the order is (dy, tx), so a
+// stable counting sort on the in-tile row dy finishes it.  One warp per group,
+// found at its first entry.
+constexpr int kGroupWarps = 8;
+constexpr int kMaxW = 128;
+
+__global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, const int* np_,
+                                                                 const fitrig_candidate* tmp,
+                                                                 const int* base_) {
+  __shared__ int counts[kGroupWarps][kMaxW];
+  const int np = *np_;
+  const int base = base_ ? *base_ : 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int* cnt = counts[warp];
+  const int wid = blockIdx.x * kGroupWarps + warp;
+  const int nw = gridDim.x * kGroupWarps;
+  for (int p = wid; p < np; p += nw) {
+    const fitrig_candidate head = tmp[p];
+    const int gty = head.y / a.w;
+    if (p > 0) {
+      const fitrig_candidate prev = tmp[p - 1];
+      if (prev.snapshot == head.snapshot && prev.y / a.w == gty) continue;   // not a head
+    }
+    // group extent
+    int end = p + 1;
+    for (;;) {
+      const int q = end + lane;
+      bool same = false;
+      if (q < np) {
+        const fitrig_candidate c = tmp[q];
+        same = c.snapshot == head.snapshot && c.y / a.w == gty;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, same);
+      if (bal == 0xffffffffu) {
+        end += 32;
+        continue;
+      }
+      end += __ffs(~bal) - 1;
+      break;
+    }
+    for (int k = lane; k < a.w; k += 32) cnt[k] = 0;
+    __syncwarp();
+    for (int q = p + lane; q < end; q += 32) atomicAdd(&cnt[tmp[q].y - gty * a.w], 1);
+    __syncwarp();
     if (lane == 0) {
-      const int pos = atomicAdd(a.nout, 1);
-      if (pos < a.cap) a.out[pos] = c;
-    }
-  }
-}
-
-cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, cudaStream_t st) {
-  k_emit<<<152 * 2, 256, 0, st>>>(a, s.items, s.nsel, s.parent, s.peak);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------- sort
-__device__ __forceinline__ unsigned long long cand_key(const fitrig_candidate& c) {
-  return ((unsigned long long)(unsigned)(c.snapshot + 1) << 42) |
-         ((unsigned long long)(unsigned)c.y << 21) | (unsigned long long)(unsigned)c.x;
-}
-
-// Stable LSD radix sort (8-bit digits) in one CTA: n is small (candidates).
-__global__ void __launch_bounds__(1024) k_sort_candidates(fitrig_candidate* a,
-                                                          fitrig_candidate* b, const int* pn) {
-  __shared__ unsigned hist[256];
-  __shared__ unsigned base[256];
-  __shared__ unsigned ctot[256];
-  __shared__ unsigned wcnt[32][256];
-  __shared__ unsigned long long kmax[32];
-  const int n = *pn;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  unsigned long long mk = 0;
-  for (int i = tid; i < n; i += 1024) mk = max(mk, cand_key(a[i]));
-  for (int o = 16; o > 0; o >>= 1) mk = max(mk, __shfl_xor_sync(0xffffffffu, mk, o));
-  if (lane == 0) kmax[warp] = mk;
-  __syncthreads();
-  mk = 0;
-  for (int w = 0; w < 32; ++w) mk = max(mk, kmax[w]);
-  int bits = 0;
-  while (bits < 64 && (mk >> bits) != 0ull) ++bits;
-  const int passes = (bits + 7) / 8;
-  fitrig_candidate* src = a;
-  fitrig_candidate* dst = b;
-  for (int p = 0; p < passes; ++p) {
-    const int sh = 8 * p;
-    if (tid < 256) hist[tid] = 0;
-    __syncthreads();
-    for (int i = tid; i < n; i += 1024) atomicAdd(&hist[(cand_key(src[i]) >> sh) & 255ull], 1u);
-    __syncthreads();
-    if (tid == 0) {
-      unsigned run = 0;
-      for (int d = 0; d < 256; ++d) {
-        base[d] = run;
-        run += hist[d];
+      int run = 0;
+      for (int k = 0; k < a.w; ++k) {
+        const int c = cnt[k];
+        cnt[k] = run;
+        run += c;
       }
     }
-    __syncthreads();
-    for (int c0 = 0; c0 < n; c0 += 1024) {
-      const int i = c0 + tid;
-      const bool valid = i < n;
-      fitrig_candidate v;
-      unsigned d = 256;
+    __syncwarp();
+    for (int q0 = p; q0 < end; q0 += 32) {
+      const int q = q0 + lane;
+      const bool valid = q < end;
+      fitrig_candidate c;
+      int dy = kMaxW;
       if (valid) {
-        v = src[i];
-        d = (unsigned)((cand_key(v) >> sh) & 255ull);
+        c = tmp[q];
+        dy = c.y - gty * a.w;
       }
-      for (int q = tid; q < 32 * 256; q += 1024) (&wcnt[0][0])[q] = 0;
-      __syncthreads();
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-      if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = __popc(peers);
-      __syncthreads();
-      if (tid < 256) {
-        unsigned acc = 0;
-        for (int w = 0; w < 32; ++w) {
-          const unsigned t = wcnt[w][tid];
-          wcnt[w][tid] = acc;
-          acc += t;
-        }
-        ctot[tid] = acc;
+      const unsigned peers = __match_any_sync(0xffffffffu, dy);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      const int off = valid ? cnt[dy] : 0;
+      __syncwarp();
+      if (valid) {
+        const int pos = base + p + off + rank;
+        if (pos < a.cap) a.out[pos] = c;
+        if (lane == __ffs(peers) - 1) cnt[dy] = off + __popc(peers);
       }
-      __syncthreads();
-      if (valid) dst[base[d] + wcnt[warp][d] + rank] = v;
-      __syncthreads();
-      if (tid < 256) base[tid] += ctot[tid];
-      __syncthreads();
+      __syncwarp();
     }
-    fitrig_candidate* t = src;
-    src = dst;
-    dst = t;
   }
-  if (src != a)
-    for (int i = tid; i < n; i += 1024) a[i] = src[i];
 }
 
-cudaError_t launch_sort_candidates(fitrig_candidate* c, fitrig_candidate* tmp, const int* n,
-                                   cudaStream_t st) {
-  k_sort_candidates<<<1, 1024, 0, st>>>(c, tmp, n);
-  count_launches(1);
+__global__ void k_map_clear(const SelItem* __restrict__ items, const int* nsel, int64_t T,
+                            int* map) {
+  const int n = *nsel;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    map[(int64_t)items[i].group * T + items[i].t] = 0;
+}
+
+__global__ void k_add_count(int* total, const int* part) { *total += *part; }
+
+cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, int* base,
+                                   fitrig_candidate* tmp, unsigned* status, cudaStream_t st) {
+  // ordered list of component peaks
+  k_peak_count<<<s.nblk, kSelThreads, 0, st>>>(s.nsel, s.parent, s.peak, s.nblk, s.blkcnt);
+  k_scan_blocks<<<1, 1024, 0, st>>>(s.nblk, s.blkcnt, s.blkoff, s.npeak, s.capacity, status);
+  k_peak_write<<<s.nblk, kSelThreads, 0, st>>>(s.nsel, s.parent, s.peak, s.nblk, s.blkoff,
+                                               s.plist);
+  if (a.branch == FITRIG_BRANCH_FREQ) {
+    k_emit_freq<<<152 * 4, 256, 0, st>>>(a, s.items, s.npeak, s.plist);
+    count_launches(4);
+  } else {
+    k_emit_image<<<152 * 4, 256, 0, st>>>(a, s.items, s.npeak, s.plist, tmp);
+    k_group_sort<<<152 * 4, kGroupWarps * 32, 0, st>>>(a, s.npeak, tmp, base);
+    count_launches(5);
+  }
+  // running total of candidates, and a clean map for the next selection
+  k_add_count<<<1, 1, 0, st>>>(a.nout, s.npeak);
+  k_map_clear<<<152 * 4, 256, 0, st>>>(s.items, s.nsel, a.T, s.map);
+  count_launches(2);
   return cudaGetLastError();
 }
 

@@ -31,6 +31,8 @@
 namespace fitrig {
 
 constexpr int kStackMaxThreads = 512;
+constexpr int kSmallThreads = 128;   // thread-per-tile path: 32 x 4 tiles per CTA
+constexpr int kSmallMaxW = 6;
 
 template <typename T, int R, bool SIGNED>
 __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_constant__ CUtensorMap tmap,
@@ -76,9 +78,10 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
   float mx = -INFINITY;
   const uint64_t deadline = globaltimer_ns() + a.timeout_ns;
 
+  int stg = 0;
+  uint32_t phase = 0;
   for (int j = 0; j < L; ++j) {
-    const int stg = j % NS;
-    const bool ok = mbar_wait_bounded(bar0 + 8 * stg, (uint32_t)((j / NS) & 1), deadline);
+    const bool ok = mbar_wait_bounded(bar0 + 8 * stg, phase, deadline);
     const T* st = reinterpret_cast<const T*>(smem + (size_t)stg * g.stage_bytes);
     if (ok) {
       if (j >= 2) {
@@ -130,6 +133,10 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
       tma_load_3d(stage0 + stg * (uint32_t)g.stage_bytes, &tmap, xload, y0, j + NS,
                   bar0 + 8 * stg);
     }
+    if (++stg == NS) {
+      stg = 0;
+      phase ^= 1u;
+    }
     if (j >= 2 && tid < g.TBX * g.TBY) {
       const int tb = tid / g.TBX;
       const int tbx = tid - tb * g.TBX;
@@ -156,7 +163,124 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
       }
     }
   }
+  (void)stg;
   // Global maximum M (NaN ignored by fmaxf; +inf is resolved on the host).
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((tid & 31) == 0 && mx > -INFINITY) atomicMax(a.gmax, f32_key(mx));
+}
+
+// Small windows (W <= 6): one thread owns a whole W x W tile and keeps its
+// W*W pixels' x^(s+1) and D^(s) in registers, so a tile's sums and maximum
+// never leave the thread.  A warp covers 32 tiles side by side (lane t reads
+// columns W*t .. W*t+W-1 of the stage, which spreads over all banks for odd W);
+// the CTA covers 32 x TBY tiles.  One barrier per snapshot guards the ring.
+template <typename T, int W, bool SIGNED>
+__global__ void __launch_bounds__(kSmallThreads) k_stack_small(const __grid_constant__ CUtensorMap tmap,
+                                                               const StackArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const StackGeom& g = a.g;
+  const int NS = g.stages;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NS * g.stage_bytes);
+  const int tid = threadIdx.x;
+  const int tbx = tid & 31;
+  const int tb = tid >> 5;
+  const int tx = blockIdx.x * 32 + tbx;
+  const int ty = blockIdx.y * g.TBY + tb;
+  const uint32_t bar0 = smem_u32(bars);
+  const uint32_t stage0 = smem_u32(smem);
+  const uint32_t box_bytes = (uint32_t)(g.boxW * g.BH * (int)sizeof(T));
+  const int L = a.nsnap;
+  const int x0 = blockIdx.x * g.BW, y0 = blockIdx.y * g.BH;
+  const bool live = tx < a.Tx && ty < a.Ty;
+  // 1 / n_t^2 of this tile (edge tiles are clipped)
+  const int hw = live ? min(W, a.ny - ty * W) : 1;
+  const int ww = live ? min(W, a.nx - tx * W) : 1;
+  const float inv_n2 = 1.f / ((float)(hw * ww) * (float)(hw * ww));
+  const int off = (tb * W) * g.boxW + tbx * W;
+
+  if (tid == 0) {
+    prefetch_tmap(&tmap);
+    for (int i = 0; i < NS; ++i) mbar_init(bar0 + 8 * i, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int j = 0; j < NS && j < L; ++j) {
+      mbar_expect_tx(bar0 + 8 * j, box_bytes);
+      tma_load_3d(stage0 + j * (uint32_t)g.stage_bytes, &tmap, x0, y0, j, bar0 + 8 * j);
+    }
+  }
+  float xp[W * W], dp[W * W];
+#pragma unroll
+  for (int i = 0; i < W * W; ++i) xp[i] = dp[i] = 0.f;
+  float mx = -INFINITY;
+  const uint64_t deadline = globaltimer_ns() + a.timeout_ns;
+  float* out = a.vp + (size_t)ty * a.Tx + tx;
+  int stg = 0;
+  uint32_t phase = 0;
+  for (int j = 0; j < L; ++j) {
+    const bool ok = mbar_wait_bounded(bar0 + 8 * stg, phase, deadline);
+    const T* st = reinterpret_cast<const T*>(smem + (size_t)stg * g.stage_bytes) + off;
+    if (ok) {
+      if (j >= 2) {
+        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            const int i = r * W + q;
+            const float xn = to_f32(st[r * (32 * W) + q]);
+            mx = fmaxf(mx, xn);
+            const float dn = fabsf(xn - xp[i]);
+            const float d = fabsf(dn - dp[i]);
+            const float ref = SIGNED ? xp[i] : fabsf(xp[i]);
+            const float xh = (xp[i] == 0.f) ? kGuardC : ref;
+            s1 += d;
+            s2 = fmaxf(s2, d);
+            s3 += fminf(__fdividef(d, xh), 1.f);
+            dp[i] = dn;
+            xp[i] = xn;
+          }
+        }
+        if (live) {
+          float v = s1 * s2 * s3 * inv_n2;
+          if (!isfinite(s1) || !isfinite(v)) v = NAN;
+          out[(size_t)(j - 2) * (size_t)a.T] = v;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+#pragma unroll
+          for (int q = 0; q < W; ++q) {
+            const int i = r * W + q;
+            const float xn = to_f32(st[r * (32 * W) + q]);
+            mx = fmaxf(mx, xn);
+            dp[i] = fabsf(xn - xp[i]);
+            xp[i] = xn;
+          }
+        }
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(a.status, kErrTimeout);
+        const uint64_t d2 = globaltimer_ns() + 1000000ull;
+        for (int jj = j; jj < L && jj < j + NS; ++jj)
+          mbar_wait_bounded(bar0 + 8 * (jj % NS), (uint32_t)((jj / NS) & 1), d2);
+      }
+      return;
+    }
+    if (tid == 0 && j + NS < L) {
+      fence_proxy_async_smem();
+      mbar_expect_tx(bar0 + 8 * stg, box_bytes);
+      tma_load_3d(stage0 + stg * (uint32_t)g.stage_bytes, &tmap, x0, y0, j + NS, bar0 + 8 * stg);
+    }
+    if (++stg == NS) {
+      stg = 0;
+      phase ^= 1u;
+    }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((tid & 31) == 0 && mx > -INFINITY) atomicMax(a.gmax, f32_key(mx));
@@ -181,8 +305,32 @@ __global__ void k_finite_max(const T* __restrict__ x, int L, int ny, int nx, int
   if ((threadIdx.x & 31) == 0 && m > -INFINITY) atomicMax(gmax, f32_key(m));
 }
 
+static bool small_geometry(int w, int elem_bytes, StackGeom* g) {
+  // 32 tiles across (lane = tile), 4 tile rows per CTA
+  const int tbx = 32, tby = kSmallThreads / 32;
+  const int BW = tbx * w, BH = tby * w;
+  if (BW > 256 || (BW * elem_bytes) % 16 != 0 || BW % 8 != 0) return false;
+  size_t stage = (size_t)BW * BH * elem_bytes;
+  stage = (stage + 127) / 128 * 128;
+  g->w = w;
+  g->R = 0;   // marks the thread-per-tile path
+  g->nseg = 1;
+  g->TBX = tbx;
+  g->TBY = tby;
+  g->BW = BW;
+  g->BH = BH;
+  g->boxW = BW;
+  g->aligned = true;
+  g->stages = 4;
+  g->threads = kSmallThreads;
+  g->stage_bytes = stage;
+  g->smem_bytes = 4 * stage + 8 * 8;
+  return true;
+}
+
 bool stack_geometry(int w, int elem_bytes, StackGeom* g) {
   if (w < 1 || w > 128) return false;
+  if (w >= 3 && w <= kSmallMaxW && small_geometry(w, elem_bytes, g)) return true;
   // rows per thread R (a template value) and row segments per tile band
   int R, nseg;
   if (w <= 8) {
@@ -256,8 +404,33 @@ static cudaError_t launch_one(const CUtensorMap* tmap, const StackArgs& a, cudaS
   return cudaGetLastError();
 }
 
+template <typename T, int W, bool SIGNED>
+static cudaError_t launch_small(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
+  auto kern = k_stack_small<T, W, SIGNED>;
+  static size_t configured = 0;
+  if (a.g.smem_bytes > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)a.g.smem_bytes);
+    if (e != cudaSuccess) return e;
+    configured = a.g.smem_bytes;
+  }
+  dim3 grid(a.g.gridX, a.g.gridY);
+  kern<<<grid, a.g.threads, a.g.smem_bytes, st>>>(*tmap, a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 template <typename T, bool SIGNED>
 static cudaError_t launch_r(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
+  if (a.g.R == 0) {
+    switch (a.g.w) {
+      case 3: return launch_small<T, 3, SIGNED>(tmap, a, st);
+      case 4: return launch_small<T, 4, SIGNED>(tmap, a, st);
+      case 5: return launch_small<T, 5, SIGNED>(tmap, a, st);
+      case 6: return launch_small<T, 6, SIGNED>(tmap, a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (a.g.R) {
     case 1: return launch_one<T, 1, SIGNED>(tmap, a, st);
     case 2: return launch_one<T, 2, SIGNED>(tmap, a, st);

@@ -55,6 +55,7 @@ struct fitrig_plan_s {
   double tau = 0.0;
   int storage = FITRIG_F32, noise = FITRIG_NOISE_MEANSTD, rmode = FITRIG_RMODE_ABS;
   int edge = FITRIG_EDGE_PARTIAL;
+  int stride = FITRIG_STRIDE_TILE;
   uint64_t timeout_ns = 2000000000ull;
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -65,6 +66,7 @@ struct fitrig_plan_s {
   int64_t pitch = 0;       // elements per row
   size_t slice_bytes = 0;  // bytes per snapshot
   StackGeom geom{};
+  SlideGeom sgeom{};
   int pushed = 0;
   bool allocated = false;
   bool detected = false;
@@ -129,10 +131,22 @@ static int allocate(fitrig_plan_t p) {
   const int eb = elem_bytes(p->storage);
   p->pitch = ((int64_t)p->nx * eb + 127) / 128 * 128 / eb;
   p->slice_bytes = (size_t)p->pitch * p->ny * eb;
-  if (!stack_geometry(p->w, eb, &p->geom)) return FITRIG_EUNSUPPORTED;
-  p->geom.gridX = (p->Tx + p->geom.TBX - 1) / p->geom.TBX;
-  p->geom.gridY = (p->Ty + p->geom.TBY - 1) / p->geom.TBY;
-  if (p->geom.gridY > 65535) return FITRIG_EUNSUPPORTED;
+  int boxW, boxH;
+  if (p->stride == FITRIG_STRIDE_SLIDING) {
+    if (!slide_geometry(p->w, eb, &p->sgeom)) return FITRIG_EUNSUPPORTED;
+    p->sgeom.gridX = (p->nx + p->sgeom.OW - 1) / p->sgeom.OW;
+    p->sgeom.gridY = (p->ny + p->sgeom.OH - 1) / p->sgeom.OH;
+    if (p->sgeom.gridY > 65535) return FITRIG_EUNSUPPORTED;
+    boxW = p->sgeom.boxW;
+    boxH = p->sgeom.EH;
+  } else {
+    if (!stack_geometry(p->w, eb, &p->geom)) return FITRIG_EUNSUPPORTED;
+    p->geom.gridX = (p->Tx + p->geom.TBX - 1) / p->geom.TBX;
+    p->geom.gridY = (p->Ty + p->geom.TBY - 1) / p->geom.TBY;
+    if (p->geom.gridY > 65535) return FITRIG_EUNSUPPORTED;
+    boxW = p->geom.boxW;
+    boxH = p->geom.BH;
+  }
   const int U = p->units;
   CK(cudaMalloc(&p->d_stack, p->slice_bytes * p->L));
   CK(cudaMalloc(&p->d_vp, sizeof(float) * (size_t)U * p->T));
@@ -163,7 +177,11 @@ static int allocate(fitrig_plan_t p) {
   const size_t o_items = carve(sizeof(SelItem) * cap), o_nsel = carve(sizeof(int));
   const size_t o_par = carve(sizeof(int) * cap), o_cm = carve(sizeof(unsigned long long) * cap);
   const size_t o_pk = carve(sizeof(int) * cap);
+  const size_t o_pl = carve(sizeof(int) * cap), o_np = carve(sizeof(int));
+  const size_t map_n = (size_t)std::max<int64_t>(1, (int64_t)U * p->T);
+  const size_t o_map = carve(sizeof(int) * map_n);
   CK(cudaMalloc(&p->d_sel, bytes));
+  CK(cudaMemset(p->d_sel, 0, bytes));
   char* b = static_cast<char*>(p->d_sel);
   s.blkcnt = reinterpret_cast<int*>(b + o_cnt);
   s.blkoff = reinterpret_cast<int*>(b + o_off);
@@ -172,6 +190,9 @@ static int allocate(fitrig_plan_t p) {
   s.parent = reinterpret_cast<int*>(b + o_par);
   s.compmax = reinterpret_cast<unsigned long long*>(b + o_cm);
   s.peak = reinterpret_cast<int*>(b + o_pk);
+  s.plist = reinterpret_cast<int*>(b + o_pl);
+  s.npeak = reinterpret_cast<int*>(b + o_np);
+  s.map = reinterpret_cast<int*>(b + o_map);
   p->cand_cap = s.capacity;
   CK(cudaMalloc(&p->d_cand, sizeof(fitrig_candidate) * cap));
   CK(cudaMalloc(&p->d_cand_tmp, sizeof(fitrig_candidate) * cap));
@@ -199,7 +220,7 @@ static int allocate(fitrig_plan_t p) {
                                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   const cuuint64_t dims[3] = {(cuuint64_t)p->nxu, (cuuint64_t)p->nyu, (cuuint64_t)p->L};
   const cuuint64_t strides[2] = {(cuuint64_t)p->pitch * eb, (cuuint64_t)p->slice_bytes};
-  const cuuint32_t box[3] = {(cuuint32_t)p->geom.boxW, (cuuint32_t)p->geom.BH, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)boxW, (cuuint32_t)boxH, 1};
   const cuuint32_t es[3] = {1, 1, 1};
   if (enc(&p->tmap, dt, 3, p->d_stack, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -296,7 +317,27 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t p, int option, int64_t value) {
       if (value != FITRIG_RMODE_ABS && value != FITRIG_RMODE_SIGNED) return FITRIG_EINVAL;
       p->rmode = (int)value;
       return FITRIG_OK;
+    case FITRIG_OPT_STRIDE:
+      if (value == FITRIG_STRIDE_TILE) {
+        p->stride = FITRIG_STRIDE_TILE;
+        p->Tx = (p->nx + p->w - 1) / p->w;
+        p->Ty = (p->ny + p->w - 1) / p->w;
+      } else if (value == FITRIG_STRIDE_SLIDING) {
+        if ((p->w & 1) == 0) return FITRIG_EINVAL;
+        if (p->w > 31) return FITRIG_EUNSUPPORTED;
+        if (p->edge != FITRIG_EDGE_PARTIAL) return FITRIG_EINVAL;
+        p->stride = FITRIG_STRIDE_SLIDING;
+        p->Tx = p->nx;
+        p->Ty = p->ny;
+      } else {
+        return FITRIG_EINVAL;
+      }
+      p->nxu = p->nx;
+      p->nyu = p->ny;
+      p->T = (int64_t)p->Tx * p->Ty;
+      return FITRIG_OK;
     case FITRIG_OPT_EDGE:
+      if (p->stride == FITRIG_STRIDE_SLIDING) return FITRIG_EINVAL;
       if (value == FITRIG_EDGE_PARTIAL) {
         p->edge = (int)value;
         p->nxu = p->nx;
@@ -391,12 +432,25 @@ FITRIG_API int fitrig_detect(fitrig_plan_t p, int32_t* ncand) {
   a.status = status;
   a.timeout_ns = p->timeout_ns;
   a.g = p->geom;
-  CK(launch_stack(&p->tmap, a, p->storage, p->rmode, st));
+  if (p->stride == FITRIG_STRIDE_SLIDING) {
+    SlideArgs sa;
+    sa.nx = p->nx;
+    sa.ny = p->ny;
+    sa.nsnap = P;
+    sa.vp = p->d_vp;
+    sa.gmax = gmax;
+    sa.status = status;
+    sa.timeout_ns = p->timeout_ns;
+    sa.g = p->sgeom;
+    CK(launch_slide(&p->tmap, sa, p->storage, p->rmode, st));
+  } else {
+    CK(launch_stack(&p->tmap, a, p->storage, p->rmode, st));
+  }
   rec(p, FITRIG_KERNEL_STACK, 1, st);
   CandArgs ca;
   ca.nx = p->nxu;
   ca.ny = p->nyu;
-  ca.w = p->w;
+  ca.w = p->stride == FITRIG_STRIDE_SLIDING ? 1 : p->w;   // pixels are 1 x 1 tiles
   ca.Tx = p->Tx;
   ca.Ty = p->Ty;
   ca.T = p->T;
@@ -409,18 +463,7 @@ FITRIG_API int fitrig_detect(fitrig_plan_t p, int32_t* ncand) {
   ca.out = p->d_cand;
   ca.nout = nout;
   ca.cap = p->cand_cap;
-  if (p->branch & FITRIG_BRANCH_IMAGE) {
-    rec(p, FITRIG_KERNEL_NOISE, 0, st);
-    CK(launch_noise(p->d_vp, U, p->T, p->noise, p->ns_img, p->d_cs, st));
-    CK(launch_thresholds(p->d_cs, U, p->tau, p->d_thr, st));
-    rec(p, FITRIG_KERNEL_NOISE, 1, st);
-    rec(p, FITRIG_KERNEL_SELECT, 0, st);
-    CK(launch_select(p->d_vp, U, p->T, p->d_thr, p->d_cs, p->sel, status, st));
-    CK(launch_components(p->Tx, p->Ty, p->T, p->sel, status, st));
-    ca.branch = FITRIG_BRANCH_IMAGE;
-    CK(launch_emit_candidates(ca, p->sel, st));
-    rec(p, FITRIG_KERNEL_SELECT, 1, st);
-  }
+  // frequency branch first: its candidates (snapshot -1) lead the sorted list
   if (p->branch & FITRIG_BRANCH_FREQ) {
     rec(p, FITRIG_KERNEL_SPECTRUM, 0, st);
     CK(launch_spectrum(p->d_vp, U, p->T, p->d_tw, p->d_eta, p->d_bin, st));
@@ -431,10 +474,21 @@ FITRIG_API int fitrig_detect(fitrig_plan_t p, int32_t* ncand) {
     CK(launch_select(p->d_eta, 1, p->T, p->d_thr + U, cs, p->sel, status, st));
     CK(launch_components(p->Tx, p->Ty, p->T, p->sel, status, st));
     ca.branch = FITRIG_BRANCH_FREQ;
-    CK(launch_emit_candidates(ca, p->sel, st));
+    CK(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
+  }
+  if (p->branch & FITRIG_BRANCH_IMAGE) {
+    rec(p, FITRIG_KERNEL_NOISE, 0, st);
+    CK(launch_noise(p->d_vp, U, p->T, p->noise, p->ns_img, p->d_cs, st));
+    CK(launch_thresholds(p->d_cs, U, p->tau, p->d_thr, st));
+    rec(p, FITRIG_KERNEL_NOISE, 1, st);
+    rec(p, FITRIG_KERNEL_SELECT, 0, st);
+    CK(launch_select(p->d_vp, U, p->T, p->d_thr, p->d_cs, p->sel, status, st));
+    CK(launch_components(p->Tx, p->Ty, p->T, p->sel, status, st));
+    ca.branch = FITRIG_BRANCH_IMAGE;
+    CK(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
+    rec(p, FITRIG_KERNEL_SELECT, 1, st);
   }
   CK(launch_clamp_count(nout, (int)p->cand_cap, status, st));
-  CK(launch_sort_candidates(p->d_cand, p->d_cand_tmp, nout, st));
   rec(p, FITRIG_KERNEL_DETECT, 1, st);
   CK(cudaMemcpyAsync(p->h_pinned, p->d_small, 16, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(p->h_pinned + 4, p->d_invalid, 8, cudaMemcpyDeviceToHost, st));

@@ -22,10 +22,11 @@ from . import build as _build
 OK, EINVAL, ENOMEM, ESTATE, ECUDA, ETIMEOUT, ETRUNC, ENONFINITE, EBUSY, EUNSUPPORTED = range(10)
 BRANCH_IMAGE, BRANCH_FREQ, BRANCH_BOTH = 1, 2, 3
 F32, BF16, F16 = 0, 1, 2
-OPT_STORAGE, OPT_NOISE, OPT_RMODE, OPT_EDGE, OPT_STREAM, OPT_TIMEOUT_NS = 1, 2, 3, 5, 8, 9
+OPT_STORAGE, OPT_NOISE, OPT_RMODE, OPT_EDGE, OPT_STRIDE, OPT_STREAM, OPT_TIMEOUT_NS = 1, 2, 3, 5, 6, 8, 9
 NOISE_MEANSTD, NOISE_MEDMAD = 0, 1
 RMODE_ABS, RMODE_SIGNED = 0, 1
 EDGE_PARTIAL, EDGE_DROP = 0, 1
+STRIDE_TILE, STRIDE_SLIDING = 0, 1
 KERNEL_STACK, KERNEL_NOISE, KERNEL_SELECT, KERNEL_SPECTRUM, KERNEL_DETECT = range(5)
 
 # statuses that still carry valid results
@@ -259,13 +260,17 @@ class Plan:
     """Owns a plan handle; pushes a whole (L, ny, nx) stack and detects."""
 
     def __init__(self, nx, ny, nsnap, window, nsigma, branch=BRANCH_IMAGE, storage=F32,
-                 noise=NOISE_MEANSTD, rmode=RMODE_ABS, edge=EDGE_PARTIAL, stream=None):
+                 noise=NOISE_MEANSTD, rmode=RMODE_ABS, edge=EDGE_PARTIAL, stream=None,
+                 stride=STRIDE_TILE):
         self.h = fitrig_plan_create(nx, ny, nsnap, window, nsigma, branch)
         try:
+            if stride != STRIDE_TILE:
+                fitrig_plan_set(self.h, OPT_STRIDE, stride)
             fitrig_plan_set(self.h, OPT_STORAGE, storage)
             fitrig_plan_set(self.h, OPT_NOISE, noise)
             fitrig_plan_set(self.h, OPT_RMODE, rmode)
-            fitrig_plan_set(self.h, OPT_EDGE, edge)
+            if edge != EDGE_PARTIAL:
+                fitrig_plan_set(self.h, OPT_EDGE, edge)
             if stream is None:
                 import torch
                 if torch.cuda.is_available():
@@ -305,10 +310,12 @@ class Plan:
 
 def detect_stack(stack, window: int, nsigma: float, branch: int = BRANCH_IMAGE,
                  storage: int = F32, noise: int = NOISE_MEANSTD, rmode: int = RMODE_ABS,
-                 edge: int = EDGE_PARTIAL, dumps: bool = True) -> dict:
+                 edge: int = EDGE_PARTIAL, dumps: bool = True,
+                 stride: int = STRIDE_TILE) -> dict:
     """Push an (L, ny, nx) stack, detect, and read back candidates and dumps."""
     L, ny, nx = (int(d) for d in stack.shape)
-    with Plan(nx, ny, L, window, nsigma, branch, storage, noise, rmode, edge) as p:
+    with Plan(nx, ny, L, window, nsigma, branch, storage, noise, rmode, edge,
+              stride=stride) as p:
         p.push_stack(stack)
         rc, cands = p.detect()
         out = {"status": rc, "candidates": cands}

@@ -336,3 +336,57 @@ def test_freq_candidate_is_tile_centre():
     # tile (1, 4) spans rows 5..9 and columns 20..24: centre (7, 22)
     assert (top.y, top.x) == (7, 22)
     assert abs(top.xf - 22.0) <= 2.5 and abs(top.yf - 7.0) <= 2.5
+
+
+# ---------------------------------------------------------------- sliding windows
+@pytest.mark.parametrize("shape,w", [((4, 7, 9), 3), ((3, 6, 5), 5), ((5, 9, 8), 1), ((3, 4, 11), 7)])
+def test_sliding_windows_against_pixel_loops(shape, w):
+    x = synth.random_stack(*shape, seed=w + 100, kind="zeros").astype(np.float64)
+    L, ny, nx = shape
+    h = w // 2
+    for s in range(L - 2):
+        ut = O.unit_windows(x, s, w)
+        for y in range(ny):
+            for xx in range(nx):
+                S1 = S3 = 0.0
+                best, cnt = -1.0, 0
+                for qy in range(max(0, y - h), min(ny, y + h + 1)):
+                    for qx in range(max(0, xx - h), min(nx, xx + h + 1)):
+                        a, b, c = x[s, qy, qx], x[s + 1, qy, qx], x[s + 2, qy, qx]
+                        dd = abs(abs(c - b) - abs(b - a))
+                        xh = O.C if b == 0 else abs(b)
+                        S1 += dd
+                        S3 += dd / xh if dd / xh < 1 else 1.0
+                        best = max(best, dd)
+                        cnt += 1
+                assert ut.S1[y, xx] == pytest.approx(S1, abs=1e-12)
+                assert ut.S2[y, xx] == best
+                assert ut.S3[y, xx] == pytest.approx(S3, abs=1e-12)
+                assert ut.n[y, xx] == cnt
+
+
+def test_sliding_w1_is_the_single_pixel_tiling():
+    x = synth.random_stack(5, 13, 17, 41)
+    a = O.detect(x, 1, 3.0, O.BRANCH_BOTH, stride="sliding")
+    b = O.detect(x, 1, 3.0, O.BRANCH_BOTH)
+    np.testing.assert_array_equal(a.tlisi, b.tlisi)
+    assert [c.key() for c in a.candidates] == [c.key() for c in b.candidates]
+
+
+def test_sliding_window_counts_are_clipped_at_the_border():
+    delta = np.ones((6, 9))
+    ut = O.window_stats(delta, delta * 0.5, np.ones((6, 9), bool), 5)
+    assert ut.n[0, 0] == 9 and ut.n[0, 4] == 15 and ut.n[3, 4] == 25 and ut.n[5, 8] == 9
+    np.testing.assert_allclose(ut.numerator, 0.5)   # mean 1 * max 1 * mean 0.5
+
+
+def test_sliding_pulse_lights_the_windows_around_it():
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal((6, 40, 40)) * 0.01
+    x[3, 20, 25] += 50.0
+    det = O.detect(x, 5, 5.0, stride="sliding")
+    # every window holding the pulse has about the same statistic, so the peak
+    # of the plateau lies anywhere within the window radius of the pulse
+    assert sorted(c.snapshot for c in det.candidates) == [1, 3]
+    for c in det.candidates:
+        assert abs(c.y - 20) <= 2 and abs(c.x - 25) <= 2

@@ -41,6 +41,19 @@ extern "C" {
 #endif
 
 typedef struct fitrig_plan_s* fitrig_plan_t;
+typedef struct fitrig_batch_s* fitrig_batch_t;
+typedef struct fitrig_server_s* fitrig_server_t;
+
+/* One serving result: the trigger of one unit of one field. */
+typedef struct {
+  int32_t field;         /* field id from fitrig_server_admit                       */
+  int32_t unit;          /* unit s: the field's snapshots s, s+1, s+2 (s+2 arrived)  */
+  int32_t ncand;         /* candidates delivered with it                             */
+  int32_t status;        /* fitrig_status of the unit                                */
+  int64_t t_arrival_ns;  /* the caller's stamp of snapshot s+2 (CLOCK_MONOTONIC ns)  */
+  int64_t t_done_ns;     /* CLOCK_MONOTONIC ns when the result reached host memory   */
+  int64_t cand_offset;   /* index of its first candidate in the poll's candidates    */
+} fitrig_result;
 
 /* One trigger candidate (32 bytes). */
 typedef struct {
@@ -76,7 +89,8 @@ enum {
   FITRIG_OPT_EDGE = 5,       /* FITRIG_EDGE_PARTIAL (default) | FITRIG_EDGE_DROP      */
   FITRIG_OPT_STRIDE = 6,     /* FITRIG_STRIDE_TILE (default) | FITRIG_STRIDE_SLIDING  */
   FITRIG_OPT_STREAM = 8,     /* cudaStream_t cast to int64; 0 = the plan's own stream */
-  FITRIG_OPT_TIMEOUT_NS = 9  /* bound of every device-side wait (default 2e9 ns)      */
+  FITRIG_OPT_TIMEOUT_NS = 9, /* bound of every device-side wait (default 2e9 ns)      */
+  FITRIG_OPT_AUTOTUNE = 10   /* 1: use the autotuned stack-march shape (tunes once)    */
 };
 enum { FITRIG_NOISE_MEANSTD = 0, FITRIG_NOISE_MEDMAD = 1 };
 enum { FITRIG_RMODE_ABS = 0, FITRIG_RMODE_SIGNED = 1 };
@@ -186,6 +200,88 @@ FITRIG_API int fitrig_stack_device_ptr(fitrig_plan_t plan, int32_t s, void** ptr
 FITRIG_API int fitrig_threshold_map(const float* dev_map, int64_t n, double nsigma,
                                     int noise_mode, int64_t stream, int64_t* nexceed,
                                     double* centre, double* scale);
+
+/*
+ * Batches: many fields of uneven size and snapshot count in one go.
+ *
+ * fitrig_batch_create -- group `nplans` plans whose snapshots are all pushed
+ * (the plans stay owned by the caller and must outlive the batch, keep their
+ * shapes and push counts, and share one device).  When every plan uses the
+ * thread-per-tile march (tile mode, window 3..6) with the same window, storage,
+ * r reading and CTA shape, all their stack marches run as ONE persistent launch
+ * that takes (field, box) work items largest field first (Sec. 2.3 tiles are
+ * independent); otherwise each plan's march is launched in turn.  The work is
+ * issued on the first plan's stream.
+ *
+ * fitrig_batch_detect -- run the trigger of every plan: the first call runs it
+ * once and then captures the whole sequence (marches, every plan's noise,
+ * selection and candidates, counter read-backs) into a CUDA graph; later calls
+ * replay the graph.  Writes each plan's candidate count to ncand[i] (in the
+ * order given at creation); results are read per plan with fitrig_candidates.
+ * Returns the most severe status of the plans.
+ *
+ * fitrig_batch_ms -- device time of the last replay (CUDA events).
+ */
+FITRIG_API int fitrig_batch_create(const fitrig_plan_t* plans, int32_t nplans,
+                                   fitrig_batch_t* out);
+FITRIG_API int fitrig_batch_detect(fitrig_batch_t batch, int32_t* ncand);
+FITRIG_API int fitrig_batch_ms(fitrig_batch_t batch, float* ms);
+FITRIG_API int fitrig_batch_destroy(fitrig_batch_t batch);
+
+/*
+ * Serving: fields that stream snapshots (the real-time trigger of Sec. 3.2's
+ * timeline, P: input transfer of snapshot s+3 overlapping the trigger kernel).
+ *
+ * fitrig_server_create -- a server that admits fields against
+ *   `hbm_budget_bytes` of device memory and at most `max_fields` active ones.
+ * fitrig_server_admit -- a field of ny x nx pixels, window, nsigma, storage
+ *   type and noise mode (image-domain branch; each unit's z-scores use that
+ *   unit's tiles, Sec. 2.4.1).  Reserves the field's device memory: the last
+ *   three snapshots (a ring), the unit's tile statistics and selection lists.
+ *   Returns OK (active) or EBUSY when it does not fit yet: the field is then
+ *   queued and activated in FIFO order as retirements free memory.
+ * fitrig_server_push -- the field's next snapshot (host or device memory;
+ *   any of the three dtypes, converted on the device).  From the third
+ *   snapshot on, every push completes one unit, whose trigger is enqueued on
+ *   the field's own stream at once, overlapping other fields' work.  Returns
+ *   when `data` may be reused (its copy is done); EBUSY while queued.
+ *   t_arrival_ns is carried into the result (CLOCK_MONOTONIC ns).
+ * fitrig_server_poll -- moves finished results (in completion order, up to
+ *   `cap`) and their candidates (up to `cand_cap`, sorted by (y, x) per
+ *   result) to the caller; never blocks.
+ * fitrig_server_drain -- waits until every pushed unit has finished.
+ * fitrig_server_retire -- finishes the field's work, frees its memory and
+ *   activates waiting fields that now fit.
+ * fitrig_server_field_state -- 0 queued, 1 active, 2 retired.
+ * fitrig_server_usage -- reserved bytes, active and waiting field counts.
+ * The server is internally synchronised: calls may come from several threads.
+ */
+FITRIG_API int fitrig_server_create(int64_t hbm_budget_bytes, int max_fields, fitrig_server_t* out);
+FITRIG_API int fitrig_server_admit(fitrig_server_t server, int nx, int ny, int window,
+                                   double nsigma, int storage, int noise, int32_t* field_id);
+FITRIG_API int fitrig_server_push(fitrig_server_t server, int32_t field, const void* data,
+                                  int dtype, int64_t t_arrival_ns);
+FITRIG_API int fitrig_server_poll(fitrig_server_t server, fitrig_result* out, int32_t cap,
+                                  fitrig_candidate* cands, int32_t cand_cap, int32_t* n,
+                                  int32_t* ncands);
+FITRIG_API int fitrig_server_drain(fitrig_server_t server);
+FITRIG_API int fitrig_server_retire(fitrig_server_t server, int32_t field);
+FITRIG_API int fitrig_server_field_state(fitrig_server_t server, int32_t field, int32_t* state);
+FITRIG_API int fitrig_server_usage(fitrig_server_t server, int64_t* used_bytes, int32_t* active,
+                                   int32_t* waiting);
+FITRIG_API int fitrig_server_destroy(fitrig_server_t server);
+
+/*
+ * fitrig_autotune -- pick the stack-march CTA shape for a window and storage
+ * type by timing each candidate (tile rows per CTA x ring depth) on a probe
+ * stack of 16 snapshots of 2048 x 2048 on the current device; the winner is
+ * cached for the process and used by plans with FITRIG_OPT_AUTOTUNE = 1.
+ * Writes the chosen tile rows per CTA, ring depth and its time (ms per probe
+ * launch).  EUNSUPPORTED for windows outside 3..6 (a single fixed shape).
+ * Allocates and frees its probe memory; synchronises the device.
+ */
+FITRIG_API int fitrig_autotune(int window, int storage, int32_t* tile_rows, int32_t* stages,
+                               float* best_ms);
 
 /* fitrig_launch_count -- number of CUDA kernels this library has launched in
  * the process so far (all plans); for accounting in benchmarks. */

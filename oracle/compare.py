@@ -52,45 +52,53 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
             noise: str = "meanstd", rmode: str = "abs", edge: str = "partial",
             decide_image: Optional[Callable[[int, int, int], bool]] = None,
             decide_freq: Optional[Callable[[int, int], bool]] = None,
-            det: Optional[O.Detection] = None) -> List[str]:
-    """Return a list of parity violations (empty when the lists agree)."""
+            det: Optional[O.Detection] = None, pixel_sample: Optional[int] = None) -> List[str]:
+    """Return a list of parity violations (empty when the lists agree).
+
+    ``pixel_sample`` limits the arg-max pixel check (which reads the stack) to
+    that many randomly chosen image candidates; everything else is checked for
+    every candidate.
+    """
     errs: List[str] = []
     L, ny, nx = stack.shape
     Ty, Tx, nyu, nxu = O.tiling(ny, nx, w, edge)
     if det is None:
         det = O.detect(stack, w, tau, branch, noise, rmode, edge)
     band = REL_TOL * tau
-    got = [dict(zip(cands.dtype.names, c)) for c in cands]
+    names = cands.dtype.names
+    got = [dict(zip(names, c)) for c in cands]
 
     def check_groups(groups, branch_id):
-        # groups: list of (label, z_map, comps, snapshot, extra)
-        pool = [g for g in got if g["branch"] == branch_id]
+        # groups: list of (label, z_map, comps, snapshot)
+        by_tile = {}
+        for k, gc in enumerate(got):
+            if gc["branch"] == branch_id:
+                key = (int(gc["snapshot"]), int(gc["y"]) // w, int(gc["x"]) // w)
+                if key in by_tile:
+                    errs.append(f"two candidates in one tile: {gc}")
+                by_tile[key] = k
         used = set()
         for label, zmap, comps, snap in groups:
             for comp in comps:
-                near = _near_peak(comp, zmap, REL_TOL)
-                hit = None
-                for k, gc in enumerate(pool):
-                    if k in used or gc["snapshot"] != snap:
-                        continue
-                    t = (gc["y"] // w, gc["x"] // w)
-                    if t in comp:
-                        hit = k
-                        break
-                if hit is None:
-                    errs.append(f"{label}: oracle component at {sorted(comp)[:4]} has no candidate")
+                hits = [by_tile[(snap,) + t] for t in comp if (snap,) + t in by_tile]
+                if len(hits) != 1:
+                    errs.append(f"{label}: oracle component at {sorted(comp)[:4]} has "
+                                f"{len(hits)} candidates")
+                    used.update(hits)
                     continue
-                used.add(hit)
-                gc = pool[hit]
-                t = (gc["y"] // w, gc["x"] // w)
+                k = hits[0]
+                used.add(k)
+                gc = got[k]
+                t = (int(gc["y"]) // w, int(gc["x"]) // w)
+                near = _near_peak(comp, zmap, REL_TOL)
                 if t not in near:
-                    errs.append(f"{label}: candidate tile {t} is not a peak tile {sorted(near)}")
+                    errs.append(f"{label}: candidate tile {t} is not a peak tile {sorted(near)[:4]}")
                 zt = zmap[t]
                 if abs(gc["significance"] - zt) > REL_TOL * max(1.0, abs(zt)):
                     errs.append(f"{label}: significance {gc['significance']} vs oracle {zt}")
                 yield gc, t, snap
-        for k, gc in enumerate(pool):
-            if k not in used:
+        for k, gc in enumerate(got):
+            if gc["branch"] == branch_id and k not in used:
                 errs.append(f"extra candidate {gc}")
 
     if branch & O.BRANCH_IMAGE:
@@ -106,7 +114,12 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
                 else:
                     mask[ty, tx] = bool(decide_image(s, int(ty), int(tx)))
             groups.append((f"unit {s}", z, O.components(mask), s))
-        for gc, (ty, tx), s in check_groups(groups, O.BRANCH_IMAGE):
+        matched = list(check_groups(groups, O.BRANCH_IMAGE))
+        if pixel_sample is not None and len(matched) > pixel_sample:
+            rng = np.random.default_rng(12345)
+            pick = rng.choice(len(matched), pixel_sample, replace=False)
+            matched = [matched[i] for i in sorted(pick)]
+        for gc, (ty, tx), s in matched:
             if not _pixel_ok(stack, s, int(gc["y"]), int(gc["x"]), ty, tx, w, nyu, nxu, rmode):
                 errs.append(f"unit {s}: pixel {(gc['y'], gc['x'])} is not an arg-max of Delta")
 

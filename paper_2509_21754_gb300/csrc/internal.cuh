@@ -138,14 +138,38 @@ struct StackArgs {
   int nsnap;           // snapshots to march over (>= 3)
   int Tx, Ty;
   int64_t T;           // Tx * Ty
-  float* vp;           // [nsnap-2][T] tile statistic
+  int64_t vstride;     // floats between units in vp (T rounded up to 4)
+  float* vp;           // [nsnap-2][vstride] tile statistic (NaN padding)
+  uint8_t* arg;        // [nsnap-2][vstride] in-tile arg-max of Delta (small path), or null
+  int zrot;            // snapshot j of the march is stack slot (zrot + j) % nsnap (ring use)
   unsigned* gmax;      // ordered key of the running maximum
   unsigned* status;    // error flags
   uint64_t timeout_ns;
   StackGeom g;
 };
 
+// One field of a batched (persistent, multi-field) stack march.  The TMA
+// descriptor must stay 64-byte aligned in device memory.
+struct alignas(128) FieldDesc {
+  CUtensorMap tmap;
+  int zrot;            // as StackArgs::zrot
+  float* vp;
+  uint8_t* arg;
+  unsigned* gmax;
+  unsigned* status;
+  int nx, ny, L, Tx, Ty, gridX;
+  int64_t vstride;
+  int64_t item0;       // first work item (box) of this field
+};
+cudaError_t launch_stack_multi(const FieldDesc* fields, int nfields, int64_t nitems,
+                               unsigned long long* counter, const StackGeom& g, int grid,
+                               int storage, int rmode, uint64_t timeout_ns, cudaStream_t st);
+int multi_blocks_per_sm(const StackGeom& g, int storage, int rmode);
+
 bool stack_geometry(int w, int elem_bytes, StackGeom* g);
+// Thread-per-tile geometry for 3 <= w <= 6 with TBY tile rows per CTA and a
+// ring of `stages` buffers (the autotuner's search space).
+bool small_geometry(int w, int elem_bytes, int tby, int stages, StackGeom* g);
 cudaError_t launch_stack(const CUtensorMap* tmap, const StackArgs& a, int storage, int rmode,
                          cudaStream_t st);
 cudaError_t launch_finite_max(const void* stack, int storage, int L, int ny, int nx,
@@ -164,7 +188,9 @@ struct SlideGeom {
 };
 struct SlideArgs {
   int nx, ny, nsnap;
-  float* vp;           // [nsnap-2][ny][nx]
+  int zrot;            // snapshot j is stack slot (zrot + j) % nsnap
+  int64_t vstride;     // floats between units in vp (nx*ny rounded up to 4)
+  float* vp;           // [nsnap-2][vstride]
   unsigned* gmax;
   unsigned* status;
   uint64_t timeout_ns;
@@ -183,14 +209,19 @@ struct NoiseScratch {
   float* shift;        // [groups] FP32 mean used by the second MEANSTD pass
   unsigned long long* invalid;  // device counter of non-finite values seen (may be null)
   int nblk;
+  bool allow_cluster = true;    // median/MAD may use the one-launch cluster form
 };
 size_t noise_scratch_bytes(int groups, int nblk);
 void noise_scratch_carve(void* base, int groups, int nblk, NoiseScratch* s);
-cudaError_t launch_noise(const float* vals, int groups, int64_t n, int mode,
+// Group g's values are vals[g*stride .. g*stride + stride); entries that are
+// not finite (including padding) are skipped; n = real entries per group
+// (for the count of invalid ones).
+cudaError_t launch_noise(const float* vals, int groups, int64_t stride, int64_t n, int mode,
                          const NoiseScratch& s, double* centre_scale, cudaStream_t st);
-// thr32[g] = largest float <= centre + tau*scale (+inf if degenerate)
+// thr32[g] = largest float <= centre + tau*scale (+inf if degenerate), and
+// inv_scale[g] = 1/scale (0 if degenerate)
 cudaError_t launch_thresholds(const double* centre_scale, int groups, double tau, float* thr,
-                              cudaStream_t st);
+                              double* inv_scale, cudaStream_t st);
 
 // Selection / components / candidates.
 struct SelItem {
@@ -212,11 +243,14 @@ struct SelectScratch {
   int* npeak;          // device count of plist
   int64_t capacity;
 };
-cudaError_t launch_select(const float* vals, int groups, int64_t T, const float* thr,
-                          const double* centre_scale, const SelectScratch& s, unsigned* status,
-                          cudaStream_t st);
-cudaError_t launch_count_selected(const float* vals, int groups, int64_t T, const float* thr,
-                                  int nblk, int* blkcnt, long long* total, cudaStream_t st);
+// Element space [0, groups*stride); selected entries get SelItem{g, t, z} in
+// order and map[g*stride + t] = list index + 1.  blkcnt/blkoff need nblk*8
+// entries (one per warp).
+cudaError_t launch_select(const float* vals, int groups, int64_t stride, const float* thr,
+                          const double* centre_scale, const double* inv_scale,
+                          const SelectScratch& s, unsigned* status, cudaStream_t st);
+cudaError_t launch_count_selected(const float* vals, int groups, int64_t stride, const float* thr,
+                                  int nblk, int* wcnt, long long* total, cudaStream_t st);
 cudaError_t launch_clamp_count(int* n, int cap, unsigned* status, cudaStream_t st);
 cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
                               unsigned* status, cudaStream_t st);
@@ -224,12 +258,15 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
 struct CandArgs {
   int nx, ny, w, Tx, Ty;
   int64_t T;
+  int64_t stride;      // group stride of the selection element space
+  const uint8_t* arg;  // fused in-tile arg-max [units][stride], or null (recompute)
   int branch;          // 1 image, 2 freq
   // image branch: stack access for the in-tile arg-max of Delta
   const void* stack;
   int storage;
   int64_t pitch;       // elements per row
   int64_t slice;       // elements per snapshot
+  int zrot, zmod;      // snapshot j of unit 0 is slot (zrot + j) % zmod (zmod 0: slot = unit + j)
   // freq branch
   const float* eta;
   const int* bin;
@@ -243,15 +280,19 @@ struct CandArgs {
 cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, int* base,
                                    fitrig_candidate* tmp, unsigned* status, cudaStream_t st);
 
+cudaError_t launch_export_candidates(const fitrig_candidate* src, const int* n,
+                                     fitrig_candidate* dst, int cap, cudaStream_t st);
+
 // Frequency branch.
-cudaError_t launch_spectrum(const float* vp, int n, int64_t T, const float2* twiddle,
-                            float* eta, int* bin, cudaStream_t st);
+cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vstride,
+                            const float2* twiddle, float* eta, int* bin, cudaStream_t st);
 
 // Ingest conversion (fp32 <-> bf16/fp16).
 cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,
                            int dst_type, int64_t dst_pitch, int ny, int nx, cudaStream_t st);
 
 // Small helpers.
+cudaError_t launch_fill_probe(void* dst, int type, int64_t n, uint32_t seed, cudaStream_t st);
 cudaError_t launch_tlisi_from_values(const float* vp, int64_t n, const unsigned* gmax,
                                      float* out, cudaStream_t st);
 

@@ -22,7 +22,8 @@ namespace fitrig {
 constexpr int kDftThreads = 128;
 
 __global__ void __launch_bounds__(kDftThreads) k_dft(const float* __restrict__ vp, int n,
-                                                     int64_t T, const float2* __restrict__ tw,
+                                                     int64_t T, int64_t vs,
+                                                     const float2* __restrict__ tw,
                                                      float* eta, int* bin) {
   extern __shared__ float ys[];   // [n][kDftThreads]
   const int tid = threadIdx.x;
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft(const float* __restrict__ v
   bool ok = live;
   float s = 0.f, comp = 0.f;
   for (int q = 0; q < n; ++q) {
-    const float v = live ? vp[(size_t)q * T + t] : 0.f;
+    const float v = live ? vp[(size_t)q * vs + t] : 0.f;
     ok = ok && isfinite(v);
     ys[q * kDftThreads + tid] = v;
     const float y = v - comp;
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft(const float* __restrict__ v
 // broadcast, so one load feeds two multiply-adds.
 template <int KMAX>
 __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restrict__ vp, int n,
-                                                           int64_t T,
+                                                           int64_t T, int64_t vs,
                                                            const float2* __restrict__ tw,
                                                            float* eta, int* bin) {
   extern __shared__ float2 tws[];   // [H][K] twiddles, pair-major, then [n][threads] series
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restri
   bool ok = true;
   float* my = ys + threadIdx.x;
   for (int q = 0; q < n; ++q) {
-    const float v = vp[(size_t)q * T + t];
+    const float v = vp[(size_t)q * vs + t];
     ok = ok && isfinite(v);
     my[q * kDftThreads] = v;
     const float y = v - comp;
@@ -153,16 +154,16 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restri
   bin[t] = bk;
 }
 
-cudaError_t launch_spectrum(const float* vp, int n, int64_t T, const float2* twiddle,
-                            float* eta, int* bin, cudaStream_t st) {
+cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
+                            const float2* twiddle, float* eta, int* bin, cudaStream_t st) {
   const int64_t blocks = (T + kDftThreads - 1) / kDftThreads;
   const int H = (n - 1) / 2, K = n / 2;
   if (n <= 65 && H >= 1) {
     const size_t sm = (size_t)H * K * sizeof(float2) + (size_t)n * kDftThreads * sizeof(float);
     if (K <= 16)
-      k_dft_short<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, twiddle, eta, bin);
+      k_dft_short<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, eta, bin);
     else
-      k_dft_short<32><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, twiddle, eta, bin);
+      k_dft_short<32><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, eta, bin);
     count_launches(1);
     return cudaGetLastError();
   }
@@ -174,7 +175,7 @@ cudaError_t launch_spectrum(const float* vp, int n, int64_t T, const float2* twi
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  k_dft<<<(unsigned)blocks, kDftThreads, smem, st>>>(vp, n, T, twiddle, eta, bin);
+  k_dft<<<(unsigned)blocks, kDftThreads, smem, st>>>(vp, n, T, vs, twiddle, eta, bin);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -213,6 +214,26 @@ __global__ void k_convert(const void* src, int st, int64_t sp, void* dst, int dt
 cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,
                            int dst_type, int64_t dst_pitch, int ny, int nx, cudaStream_t st) {
   k_convert<<<152 * 8, 256, 0, st>>>(src, src_type, src_pitch, dst, dst_type, dst_pitch, ny, nx);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- autotuner probe data
+// Deterministic pseudo-random values in [-4, 4) (an integer hash of the index),
+// used only as timing input for the autotuner.
+__global__ void k_fill_probe(void* dst, int type, int64_t n, uint32_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    store_any(dst, type, i, ((float)(h >> 8) * (1.0f / 16777216.0f)) * 8.f - 4.f);
+  }
+}
+
+cudaError_t launch_fill_probe(void* dst, int type, int64_t n, uint32_t seed, cudaStream_t st) {
+  k_fill_probe<<<152 * 8, 256, 0, st>>>(dst, type, n, seed);
   count_launches(1);
   return cudaGetLastError();
 }

@@ -12,10 +12,15 @@
 // an exact radix select over order-preserving 32-bit keys in three digit passes
 // (11, 11 and 10 bits) with integer histograms; scale = 1.482602218505602 MAD.
 // Both medians are bit-exact elements of the (derived) value arrays.
+#include <cooperative_groups.h>
+
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
 #include "internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace fitrig {
 
@@ -51,32 +56,52 @@ void noise_scratch_carve(void* base, int groups, int nblk, NoiseScratch* s) {
 }
 
 // ---------------------------------------------------------------- MEANSTD
+__device__ __forceinline__ void kahan_add(float term, float& s, float& comp) {
+  const float y = term - comp;
+  const float t = s + y;
+  comp = (t - s) - y;
+  s = t;
+}
+
 // Partial sums of v (sq == 0) or of (v - shift[g])^2 (sq == 1) over finite v.
+// Group g's values start at vals + g * stride; VEC loads four at a time (the
+// caller guarantees 16-byte alignment and stride % 4 == 0).
+template <bool VEC>
 __global__ void __launch_bounds__(kNoiseThreads) k_sum_pass(const float* __restrict__ vals,
-                                                            int64_t n, int nblk, int sq,
+                                                            int64_t stride, int nblk, int sq,
                                                             const float* __restrict__ shift,
                                                             double* part, int* cnt) {
   __shared__ double sh[kNoiseThreads];
   __shared__ int shc[kNoiseThreads];
   const int g = blockIdx.y;
-  const float* v = vals + (size_t)g * n;
+  const float* v = vals + (size_t)g * stride;
   const float m = sq ? shift[g] : 0.f;
   float s = 0.f, comp = 0.f;
   int c = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)nblk * blockDim.x) {
-    const float x = v[i];
-    if (!isfinite(x)) continue;
+  auto take = [&](float x) {
+    if (!isfinite(x)) return;
     float term = x;
     if (sq) {
       const float d = x - m;
       term = d * d;
     }
-    const float y = term - comp;
-    const float t = s + y;
-    comp = (t - s) - y;
-    s = t;
+    kahan_add(term, s, comp);
     ++c;
+  };
+  if (VEC) {
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < stride / 4;
+         i += (int64_t)nblk * blockDim.x) {
+      const float4 q = v4[i];
+      take(q.x);
+      take(q.y);
+      take(q.z);
+      take(q.w);
+    }
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < stride;
+         i += (int64_t)nblk * blockDim.x)
+      take(v[i]);
   }
   sh[threadIdx.x] = (double)s - (double)comp;
   shc[threadIdx.x] = c;
@@ -132,8 +157,24 @@ __device__ __forceinline__ bool rs_key(float v, int mad, float med, uint32_t* ke
   return true;
 }
 
+__device__ __forceinline__ void rs_count(unsigned* sh, int pass, unsigned prefix, bool ok,
+                                         uint32_t key) {
+  if (pass == 0) {
+    // the leading digit is concentrated (exponent bits): aggregate per warp
+    const unsigned bin = ok ? (key >> 21) : 0xffffffffu;
+    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+    if (ok && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
+      atomicAdd(&sh[bin], (unsigned)__popc(peers));
+  } else if (pass == 1) {
+    if (ok && (key >> 21) == prefix) atomicAdd(&sh[(key >> 10) & 2047u], 1u);
+  } else {
+    if (ok && (key >> 10) == prefix) atomicAdd(&sh[key & 1023u], 1u);
+  }
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(kNoiseThreads) k_rs_hist(const float* __restrict__ vals,
-                                                           int64_t n, int nblk, int pass,
+                                                           int64_t stride, int nblk, int pass,
                                                            int mad, const unsigned* rsel,
                                                            const double* cs, unsigned* hist) {
   __shared__ unsigned sh[kBins];
@@ -143,25 +184,28 @@ __global__ void __launch_bounds__(kNoiseThreads) k_rs_hist(const float* __restri
   const unsigned prefix = rsel[4 * g + 0];
   const bool degenerate = rsel[4 * g + 3] != 0;
   const float med = mad ? (float)cs[2 * g] : 0.f;
-  const float* v = vals + (size_t)g * n;
+  const float* v = vals + (size_t)g * stride;
   if (!degenerate) {
-    // The trip count depends only on the block, so every lane of a warp reaches
-    // the warp-wide match below together.
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+    // Trip counts depend only on the block, so every lane of a warp reaches the
+    // warp-wide match in rs_count together.
+    const int64_t nv = VEC ? stride / 4 : stride;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nv;
          base += (int64_t)nblk * blockDim.x) {
       const int64_t i = base + threadIdx.x;
-      uint32_t key = 0;
-      const bool ok = i < n && rs_key(v[i], mad, med, &key);
-      if (pass == 0) {
-        // the leading digit is concentrated (exponent bits): aggregate per warp
-        const unsigned bin = ok ? (key >> 21) : 0xffffffffu;
-        const unsigned peers = __match_any_sync(0xffffffffu, bin);
-        if (ok && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
-          atomicAdd(&sh[bin], (unsigned)__popc(peers));
-      } else if (pass == 1) {
-        if (ok && (key >> 21) == prefix) atomicAdd(&sh[(key >> 10) & 2047u], 1u);
+      if (VEC) {
+        float4 q = make_float4(NAN, NAN, NAN, NAN);
+        if (i < nv) q = reinterpret_cast<const float4*>(v)[i];
+        uint32_t k0 = 0, k1 = 0, k2 = 0, k3 = 0;
+        const bool o0 = rs_key(q.x, mad, med, &k0), o1 = rs_key(q.y, mad, med, &k1);
+        const bool o2 = rs_key(q.z, mad, med, &k2), o3 = rs_key(q.w, mad, med, &k3);
+        rs_count(sh, pass, prefix, o0, k0);
+        rs_count(sh, pass, prefix, o1, k1);
+        rs_count(sh, pass, prefix, o2, k2);
+        rs_count(sh, pass, prefix, o3, k3);
       } else {
-        if (ok && (key >> 10) == prefix) atomicAdd(&sh[key & 1023u], 1u);
+        uint32_t key = 0;
+        const bool ok = i < nv && rs_key(v[i], mad, med, &key);
+        rs_count(sh, pass, prefix, ok, key);
       }
     }
   }
@@ -250,33 +294,275 @@ __global__ void __launch_bounds__(kSelectThreads) k_rs_select(int groups, int64_
   }
 }
 
+// ---------------------------------------------------------------- MEDMAD, cluster form
+// One thread-block cluster per group finds the median and then the MAD in a
+// single launch, by range-binned selection over the order-preserving keys:
+//   * a first sweep takes the minimum and maximum key (and the count) of the
+//     group's finite values;
+//   * each pass bins the keys inside the current inclusive range [lo, hi]
+//     linearly into 2048 bins (digit = (key - lo) >> shift, shift chosen so
+//     the range fits), the bin holding the target rank becomes the new range,
+//     and the rank is reduced by the counts below it; after at most three
+//     passes the range is a single key, which is the exact order statistic;
+//   * the MAD repeats this on the keys of |v - median| (FP32), whose range is
+//     [0, max(|vmax - median|, |vmin - median|)].
+// Linear bins spread the values over many bins, so plain shared-memory atomics
+// suffice.  Every CTA counts its share into its own histogram, the others add
+// theirs into the leader's through distributed shared memory, and the leader
+// publishes the new range after a cluster barrier.  Integer counting only:
+// the result is the same element a sort would give.
+constexpr int kClusterCtas = 8;
+constexpr int kClusterThreads = 512;
+constexpr int64_t kClusterMaxPerGroup = 8 << 20;   // larger maps use the grid-wide passes
+constexpr int64_t kClusterBatchBytes = 48 << 20;   // groups per launch stay L2-resident
+
+struct RangeState {
+  unsigned long long lo, hi;   // inclusive key range
+  unsigned long long rank;     // rank of the target inside the range
+  unsigned long long total;    // finite values of the group
+  unsigned shift;              // digit = (key - lo) >> shift
+  unsigned done;
+};
+
+__device__ __forceinline__ unsigned range_shift(unsigned long long lo, unsigned long long hi) {
+  const unsigned long long width = hi - lo + 1;   // <= 2^32
+  unsigned s = 0;
+  while ((width - 1) >> s >= (unsigned long long)kBins) ++s;
+  return s;
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kClusterThreads) k_medmad_cluster(const float* __restrict__ vals,
+                                                                    int64_t stride, int64_t n,
+                                                                    int g0, double* cs,
+                                                                    unsigned long long* invalid) {
+  __shared__ unsigned hist[kBins];
+  __shared__ unsigned long long red[kClusterThreads / 32][3];
+  __shared__ unsigned long long scan[kClusterThreads];
+  __shared__ RangeState st;
+  __shared__ unsigned long long mm[3];   // this CTA's min key, max key, count
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank();
+  const int g = g0 + blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* v = vals + (size_t)g * stride;
+  const RangeState* lead = cl.map_shared_rank(&st, 0);
+  const int64_t nv = VEC ? stride / 4 : stride;
+  const int64_t step = (int64_t)kClusterCtas * blockDim.x;
+
+  // visit every finite value of this CTA's share as an order-preserving key
+  auto for_keys = [&](int mad, float med, auto&& fn) {
+    for (int64_t i = (int64_t)rank * blockDim.x + tid; i < nv; i += step) {
+      if (VEC) {
+        const float4 q = reinterpret_cast<const float4*>(v)[i];
+        const float e[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          uint32_t key;
+          if (rs_key(e[c], mad, med, &key)) fn(key);
+        }
+      } else {
+        uint32_t key;
+        if (rs_key(v[i], mad, med, &key)) fn(key);
+      }
+    }
+  };
+
+  // ---- sweep 0: min, max and count of the keys (each CTA its share; every
+  // CTA then combines all shares through distributed shared memory)
+  {
+    unsigned long long kmin = ~0ull, kmax = 0ull, cnt = 0;
+    for_keys(0, 0.f, [&](uint32_t key) {
+      kmin = key < kmin ? key : kmin;
+      kmax = key > kmax ? key : kmax;
+      ++cnt;
+    });
+    for (int o = 16; o > 0; o >>= 1) {
+      kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+      kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+      red[warp][0] = kmin;
+      red[warp][1] = kmax;
+      red[warp][2] = cnt;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < kClusterThreads / 32; ++w) {
+        kmin = min(kmin, red[w][0]);
+        kmax = max(kmax, red[w][1]);
+        cnt += red[w][2];
+      }
+      mm[0] = kmin;
+      mm[1] = kmax;
+      mm[2] = cnt;
+    }
+  }
+  cl.sync();   // every CTA's share is summarised
+  unsigned long long gmin = ~0ull, gmax = 0ull, total = 0;
+  for (int r = 0; r < kClusterCtas; ++r) {
+    const unsigned long long* o = cl.map_shared_rank(mm, r);
+    gmin = min(gmin, o[0]);
+    gmax = max(gmax, o[1]);
+    total += o[2];
+  }
+  if (total == 0) {
+    if (rank == 0 && tid == 0) {
+      cs[2 * g] = NAN;
+      cs[2 * g + 1] = 0.0;
+      if (invalid && n > 0) atomicAdd(invalid, (unsigned long long)n);
+    }
+    cl.sync();   // nobody leaves while others still read its shared memory
+    return;
+  }
+  if (rank == 0 && tid == 0 && invalid && (int64_t)total < n)
+    atomicAdd(invalid, (unsigned long long)(n - (int64_t)total));
+
+  float med = 0.f;
+  for (int mad = 0; mad < 2; ++mad) {
+    if (rank == 0 && tid == 0) {
+      if (mad == 0) {
+        st.lo = gmin;
+        st.hi = gmax;
+      } else {
+        const float vmin = f32_from_key((uint32_t)gmin), vmax = f32_from_key((uint32_t)gmax);
+        st.lo = f32_key(0.f);
+        st.hi = f32_key(fmaxf(fabsf(vmax - med), fabsf(vmin - med)));
+      }
+      st.rank = (total - 1) / 2;
+      st.shift = range_shift(st.lo, st.hi);
+      st.done = st.lo == st.hi;
+    }
+    cl.sync();   // the starting range is published (and the shares summaries read)
+    for (int pass = 0; pass < 4; ++pass) {
+      const RangeState r = *lead;
+      if (r.done) break;   // uniform: everyone read the same leader state
+      for (int b = tid; b < kBins; b += blockDim.x) hist[b] = 0;
+      __syncthreads();
+      for_keys(mad, med, [&](uint32_t key) {
+        if (key >= r.lo && key <= r.hi) atomicAdd(&hist[(unsigned)((key - r.lo) >> r.shift)], 1u);
+      });
+      cl.sync();           // every CTA's histogram is complete
+      if (rank == 0) {
+        // sum the CTAs' histograms (plain remote loads, fixed order)
+        constexpr int per = kBins / kClusterThreads;
+        unsigned local[per];
+        for (int i = 0; i < per; ++i) local[i] = 0;
+        for (int c = 0; c < kClusterCtas; ++c) {
+          const unsigned* h = cl.map_shared_rank(hist, c);
+          for (int i = 0; i < per; ++i) local[i] += h[tid * per + i];
+        }
+        unsigned long long mine = 0;
+        for (int i = 0; i < per; ++i) mine += local[i];
+        scan[tid] = mine;
+        __syncthreads();
+        for (int d = 1; d < kClusterThreads; d <<= 1) {
+          const unsigned long long add = tid >= d ? scan[tid - d] : 0ull;
+          __syncthreads();
+          scan[tid] += add;
+          __syncthreads();
+        }
+        const unsigned long long before = scan[tid] - mine;
+        if (r.rank >= before && r.rank < before + mine) {
+          unsigned long long cum = before;
+          for (int i = 0; i < per; ++i) {
+            if (r.rank < cum + local[i]) {
+              const unsigned long long b = (unsigned long long)(tid * per + i);
+              const unsigned long long lo = r.lo + (b << r.shift);
+              const unsigned long long hi = min(r.hi, lo + ((1ull << r.shift) - 1));
+              st.lo = lo;
+              st.hi = hi;
+              st.rank = r.rank - cum;
+              st.shift = range_shift(lo, hi);
+              st.done = lo == hi;
+              break;
+            }
+            cum += local[i];
+          }
+        }
+      }
+      cl.sync();           // the new range is published; all histograms were read
+    }
+    const float val = f32_from_key((uint32_t)lead->lo);
+    if (mad == 0) {
+      med = val;
+      if (rank == 0 && tid == 0) cs[2 * g] = (double)val;
+    } else if (rank == 0 && tid == 0) {
+      cs[2 * g + 1] = kMadToSigma * (double)val;
+    }
+    cl.sync();             // everyone has read the result before the state changes
+  }
+}
+
+static cudaError_t launch_medmad_cluster(const float* vals, int groups, int64_t stride,
+                                         int64_t n, bool vec, double* cs,
+                                         unsigned long long* invalid, cudaStream_t st) {
+  const int64_t per = std::max<int64_t>(1, kClusterBatchBytes / std::max<int64_t>(1, stride * 4));
+  for (int g0 = 0; g0 < groups; g0 += (int)per) {
+    const int gb = (int)std::min<int64_t>(per, groups - g0);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClusterCtas, gb, 1);
+    cfg.blockDim = dim3(kClusterThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e =
+        vec ? cudaLaunchKernelEx(&cfg, k_medmad_cluster<true>, vals, stride, n, g0, cs, invalid)
+            : cudaLaunchKernelEx(&cfg, k_medmad_cluster<false>, vals, stride, n, g0, cs, invalid);
+    count_launches(1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 static int noise_blocks(int groups, const NoiseScratch& s) {
   (void)groups;
   return s.nblk;
 }
 
-cudaError_t launch_noise(const float* vals, int groups, int64_t n, int mode,
+cudaError_t launch_noise(const float* vals, int groups, int64_t stride, int64_t n, int mode,
                          const NoiseScratch& s, double* cs, cudaStream_t st) {
   const int nblk = noise_blocks(groups, s);
   dim3 grid(nblk, groups);
+  const bool vec = (reinterpret_cast<uintptr_t>(vals) % 16 == 0) && (stride % 4 == 0);
   if (mode == FITRIG_NOISE_MEANSTD) {
-    k_sum_pass<<<grid, kNoiseThreads, 0, st>>>(vals, n, nblk, 0, s.shift, s.part, s.cnt);
-    k_sum_final<<<(groups + 127) / 128, 128, 0, st>>>(groups, n, nblk, 0, s.part, s.cnt, s.shift,
-                                                      cs, s.invalid);
-    k_sum_pass<<<grid, kNoiseThreads, 0, st>>>(vals, n, nblk, 1, s.shift, s.part, s.cnt);
-    k_sum_final<<<(groups + 127) / 128, 128, 0, st>>>(groups, n, nblk, 1, s.part, s.cnt, s.shift,
-                                                      cs, nullptr);
+    for (int stage = 0; stage < 2; ++stage) {
+      if (vec)
+        k_sum_pass<true><<<grid, kNoiseThreads, 0, st>>>(vals, stride, nblk, stage, s.shift,
+                                                         s.part, s.cnt);
+      else
+        k_sum_pass<false><<<grid, kNoiseThreads, 0, st>>>(vals, stride, nblk, stage, s.shift,
+                                                          s.part, s.cnt);
+      k_sum_final<<<(groups + 127) / 128, 128, 0, st>>>(groups, n, nblk, stage, s.part, s.cnt,
+                                                        s.shift, cs,
+                                                        stage == 0 ? s.invalid : nullptr);
+    }
     count_launches(4);
     return cudaGetLastError();
   }
   if (mode != FITRIG_NOISE_MEDMAD) return cudaErrorInvalidValue;
+  // groups of moderate size: one cluster per group, all passes in one launch
+  if (stride <= kClusterMaxPerGroup && s.allow_cluster)
+    return launch_medmad_cluster(vals, groups, stride, n, vec, cs, s.invalid, st);
   cudaError_t e = cudaMemsetAsync(s.rsel, 0, (size_t)groups * 4 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(s.hist, 0, (size_t)groups * kBins * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   for (int mad = 0; mad < 2; ++mad) {
     for (int pass = 0; pass < 3; ++pass) {
-      k_rs_hist<<<grid, kNoiseThreads, 0, st>>>(vals, n, nblk, pass, mad, s.rsel, cs, s.hist);
+      if (vec)
+        k_rs_hist<true><<<grid, kNoiseThreads, 0, st>>>(vals, stride, nblk, pass, mad, s.rsel,
+                                                        cs, s.hist);
+      else
+        k_rs_hist<false><<<grid, kNoiseThreads, 0, st>>>(vals, stride, nblk, pass, mad, s.rsel,
+                                                         cs, s.hist);
       k_rs_select<<<groups, kSelectThreads, 0, st>>>(groups, n, pass, mad, s.hist, s.rsel, cs,
                                                      s.invalid);
     }
@@ -285,21 +571,24 @@ cudaError_t launch_noise(const float* vals, int groups, int64_t n, int mode,
   return cudaGetLastError();
 }
 
-__global__ void k_thresholds(const double* cs, int groups, double tau, float* thr) {
+__global__ void k_thresholds(const double* cs, int groups, double tau, float* thr,
+                             double* inv_scale) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= groups) return;
   const double c = cs[2 * g], s = cs[2 * g + 1];
   if (!(s > 0.0) || !isfinite(c) || !isfinite(s)) {
     thr[g] = INFINITY;   // degenerate spread: nothing is selected
+    inv_scale[g] = 0.0;
     return;
   }
   // largest float <= c + tau*s, so (float v > thr) <=> ((double)v > c + tau*s)
   thr[g] = __double2float_rd(c + tau * s);
+  inv_scale[g] = 1.0 / s;
 }
 
 cudaError_t launch_thresholds(const double* cs, int groups, double tau, float* thr,
-                              cudaStream_t st) {
-  k_thresholds<<<(groups + 127) / 128, 128, 0, st>>>(cs, groups, tau, thr);
+                              double* inv_scale, cudaStream_t st) {
+  k_thresholds<<<(groups + 127) / 128, 128, 0, st>>>(cs, groups, tau, thr, inv_scale);
   count_launches(1);
   return cudaGetLastError();
 }

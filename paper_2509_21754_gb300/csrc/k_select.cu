@@ -32,38 +32,50 @@ __device__ __forceinline__ void chunk_range(int64_t N, int nblk, int b, int64_t*
   *hi = *lo + chunk < N ? *lo + chunk : N;
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_sel_count(const float* __restrict__ vals,
-                                                           int groups, int64_t T,
-                                                           const float* __restrict__ thr,
-                                                           int nblk, int* blkcnt) {
-  __shared__ int wsum[kSelThreads / 32];
-  const int64_t N = (int64_t)groups * T;
-  int64_t lo, hi;
-  chunk_range(N, nblk, blockIdx.x, &lo, &hi);
-  int cnt = 0;
-  int64_t i = lo + threadIdx.x;
-  int g = (int)(i / T);
-  int64_t gend = (int64_t)(g + 1) * T;
-  float th = g < groups ? thr[g] : INFINITY;
-  for (; i < hi; i += blockDim.x) {
-    while (i >= gend) {
-      ++g;
-      gend += T;
-      th = thr[g];
-    }
-    cnt += vals[i] > th;
-  }
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int s = 0;
-    for (int w = 0; w < kSelThreads / 32; ++w) s += wsum[w];
-    blkcnt[blockIdx.x] = s;
-  }
+// Ordered compaction over the element space [0, groups * stride): each warp
+// owns a contiguous chunk of `chunk` elements (a multiple of 128), counts its
+// selected entries, and after an exclusive scan of the warp counts writes them
+// in order with a warp-level prefix -- no block-wide barriers.  VEC reads four
+// entries per lane (16-byte aligned base, stride % 4 == 0).
+__device__ __forceinline__ void warp_range(int64_t N, int64_t chunk, int64_t* lo, int64_t* hi) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  *lo = w * chunk;
+  *hi = *lo + chunk < N ? *lo + chunk : N;
 }
 
-// Exclusive scan of per-block counts (one block of 1024 threads).
+template <bool VEC>
+__global__ void __launch_bounds__(kSelThreads) k_sel_count(const float* __restrict__ vals,
+                                                           int groups, int64_t stride,
+                                                           const float* __restrict__ thr,
+                                                           int64_t chunk, int* wcnt) {
+  const int64_t N = (int64_t)groups * stride;
+  int64_t lo, hi;
+  warp_range(N, chunk, &lo, &hi);
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+  const int step = VEC ? 4 : 1;
+  int64_t i = lo + lane * step;
+  int g = lo < N ? (int)(lo / stride) : 0;
+  int64_t gend = (int64_t)(g + 1) * stride;
+  float th = lo < N ? thr[g] : INFINITY;
+  for (; i < hi; i += 32 * step) {
+    while (i >= gend) {
+      ++g;
+      gend += stride;
+      th = thr[g];
+    }
+    if (VEC) {
+      const float4 q = *reinterpret_cast<const float4*>(vals + i);
+      cnt += (q.x > th) + (q.y > th) + (q.z > th) + (q.w > th);
+    } else {
+      cnt += vals[i] > th;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0) wcnt[((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5] = cnt;
+}
+
+// Exclusive scan of per-warp (or per-block) counts (one block of 1024 threads).
 __global__ void __launch_bounds__(1024) k_scan_blocks(int nblk, const int* blkcnt, int* blkoff,
                                                       int* total, int64_t cap,
                                                       unsigned* status) {
@@ -92,64 +104,99 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(int nblk, const int* blkcn
   }
 }
 
+template <bool VEC>
 __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restrict__ vals,
-                                                           int groups, int64_t T,
+                                                           int groups, int64_t stride,
                                                            const float* __restrict__ thr,
                                                            const double* __restrict__ cs,
-                                                           int nblk, const int* blkoff,
+                                                           const double* __restrict__ inv,
+                                                           int64_t chunk, const int* woff,
                                                            SelItem* items, int* map,
                                                            int64_t cap) {
-  __shared__ int wcnt[kSelThreads / 32];
-  const int64_t N = (int64_t)groups * T;
+  const int64_t N = (int64_t)groups * stride;
   int64_t lo, hi;
-  chunk_range(N, nblk, blockIdx.x, &lo, &hi);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t run = blkoff[blockIdx.x];
-  int g = (int)((lo + threadIdx.x) / T);
-  int64_t gend = (int64_t)(g + 1) * T;
-  for (int64_t base = lo; base < hi; base += blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    bool sel = false;
-    float v = 0.f;
+  warp_range(N, chunk, &lo, &hi);
+  if (lo >= hi) return;   // warp-uniform
+  const int lane = threadIdx.x & 31;
+  const int step = VEC ? 4 : 1;
+  int64_t run = woff[((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5];
+  int g = (int)(lo / stride);
+  int64_t gend = (int64_t)(g + 1) * stride;
+  for (int64_t base = lo; base < hi; base += 32 * step) {
+    const int64_t i = base + lane * step;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    unsigned bits = 0;
     if (i < hi) {
       while (i >= gend) {
         ++g;
-        gend += T;
+        gend += stride;
       }
-      v = vals[i];
-      sel = v > thr[g];
-    }
-    const unsigned bal = __ballot_sync(0xffffffffu, sel);
-    if (lane == 0) wcnt[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0, tile = 0;
-    for (int w = 0; w < kSelThreads / 32; ++w) {
-      before += w < warp ? wcnt[w] : 0;
-      tile += wcnt[w];
-    }
-    if (sel) {
-      const int64_t pos = run + before + __popc(bal & ((1u << lane) - 1u));
-      if (pos < cap) {
-        SelItem it;
-        it.group = g;
-        it.t = (int32_t)(i - (int64_t)g * T);
-        it.z = ((double)v - cs[2 * g]) / cs[2 * g + 1];
-        items[pos] = it;
-        map[i] = (int)pos + 1;
+      const float th = thr[g];
+      if (VEC) {
+        const float4 q = *reinterpret_cast<const float4*>(vals + i);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+        bits = (q.x > th) | ((q.y > th) << 1) | ((q.z > th) << 2) | ((q.w > th) << 3);
+      } else {
+        v[0] = vals[i];
+        bits = v[0] > th;
       }
     }
-    run += tile;
-    __syncthreads();
+    const int c = __popc(bits);
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int64_t pos = run + incl - c;
+    if (bits) {
+      const double cg = cs[2 * g], ig = inv[g];
+      for (int k = 0; k < step; ++k) {
+        if (!(bits >> k & 1u)) continue;
+        if (pos < cap) {
+          const int64_t e = i + k;
+          SelItem it;
+          it.group = g;
+          it.t = (int32_t)(e - (int64_t)g * stride);
+          it.z = ((double)v[k] - cg) * ig;
+          items[pos] = it;
+          map[e] = (int)pos + 1;
+        }
+        ++pos;
+      }
+    }
+    run += total;
   }
 }
 
-cudaError_t launch_select(const float* vals, int groups, int64_t T, const float* thr,
-                          const double* cs, const SelectScratch& s, unsigned* status,
-                          cudaStream_t st) {
-  k_sel_count<<<s.nblk, kSelThreads, 0, st>>>(vals, groups, T, thr, s.nblk, s.blkcnt);
-  k_scan_blocks<<<1, 1024, 0, st>>>(s.nblk, s.blkcnt, s.blkoff, s.nsel, s.capacity, status);
-  k_sel_write<<<s.nblk, kSelThreads, 0, st>>>(vals, groups, T, thr, cs, s.nblk, s.blkoff,
-                                              s.items, s.map, s.capacity);
+static int64_t sel_chunk(int64_t N, int nwarps) {
+  int64_t c = (N + nwarps - 1) / nwarps;
+  return (c + 127) / 128 * 128;
+}
+
+static bool sel_vec(const float* vals, int64_t stride) {
+  return (reinterpret_cast<uintptr_t>(vals) % 16 == 0) && (stride % 4 == 0);
+}
+
+cudaError_t launch_select(const float* vals, int groups, int64_t stride, const float* thr,
+                          const double* cs, const double* inv, const SelectScratch& s,
+                          unsigned* status, cudaStream_t st) {
+  const int nw = s.nblk * (kSelThreads / 32);
+  const int64_t chunk = sel_chunk((int64_t)groups * stride, nw);
+  if (sel_vec(vals, stride)) {
+    k_sel_count<true><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk, s.blkcnt);
+    k_scan_blocks<<<1, 1024, 0, st>>>(nw, s.blkcnt, s.blkoff, s.nsel, s.capacity, status);
+    k_sel_write<true><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, cs, inv, chunk,
+                                                      s.blkoff, s.items, s.map, s.capacity);
+  } else {
+    k_sel_count<false><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk, s.blkcnt);
+    k_scan_blocks<<<1, 1024, 0, st>>>(nw, s.blkcnt, s.blkoff, s.nsel, s.capacity, status);
+    k_sel_write<false><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, cs, inv, chunk,
+                                                       s.blkoff, s.items, s.map, s.capacity);
+  }
   count_launches(3);
   return cudaGetLastError();
 }
@@ -167,10 +214,15 @@ __global__ void k_sum_counts(int nblk, const int* blkcnt, long long* total) {
   if (threadIdx.x == 0) *total = sh[0];
 }
 
-cudaError_t launch_count_selected(const float* vals, int groups, int64_t T, const float* thr,
-                                  int nblk, int* blkcnt, long long* total, cudaStream_t st) {
-  k_sel_count<<<nblk, kSelThreads, 0, st>>>(vals, groups, T, thr, nblk, blkcnt);
-  k_sum_counts<<<1, 256, 0, st>>>(nblk, blkcnt, total);
+cudaError_t launch_count_selected(const float* vals, int groups, int64_t stride, const float* thr,
+                                  int nblk, int* wcnt, long long* total, cudaStream_t st) {
+  const int nw = nblk * (kSelThreads / 32);
+  const int64_t chunk = sel_chunk((int64_t)groups * stride, nw);
+  if (sel_vec(vals, stride))
+    k_sel_count<true><<<nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk, wcnt);
+  else
+    k_sel_count<false><<<nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk, wcnt);
+  k_sum_counts<<<1, 256, 0, st>>>(nw, wcnt, total);
   count_launches(2);
   return cudaGetLastError();
 }
@@ -228,6 +280,34 @@ __global__ void k_cc_init(const int* nsel, int* parent, unsigned long long* comp
   }
 }
 
+// Horizontal runs: a selected tile whose left neighbour is selected is the next
+// list entry after it.  Each warp takes 32 consecutive entries, finds by
+// ballot the nearest run start at or before each lane, and points the entry at
+// it; a run that began in an earlier warp points at the entry just before the
+// warp, so chains only cross warp boundaries.
+__global__ void k_cc_runs(const SelItem* __restrict__ items, const int* nsel, int Tx,
+                          int* parent) {
+  const int n = *nsel;
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < n; base += nw * 32) {
+    const int i = base + lane;
+    bool left = false;
+    if (i < n && i > 0) {
+      const SelItem me = items[i], pv = items[i - 1];
+      left = pv.group == me.group && pv.t == me.t - 1 && (me.t % Tx) != 0;
+    }
+    const unsigned lmask = __ballot_sync(0xffffffffu, left);
+    const unsigned starts = ~lmask & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u));
+    if (i < n) {
+      int head;
+      if (starts) head = base + 31 - __clz(starts);
+      else head = base - 1;   // the run started in an earlier warp
+      parent[i] = head;
+    }
+  }
+}
+
 __global__ void k_cc_union(const SelItem* __restrict__ items, const int* nsel, int Tx, int Ty,
                            int64_t T, const int* __restrict__ map, int* parent,
                            unsigned* status) {
@@ -235,13 +315,22 @@ __global__ void k_cc_union(const SelItem* __restrict__ items, const int* nsel, i
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const SelItem me = items[i];
     const int ty = me.t / Tx, tx = me.t - (me.t / Tx) * Tx;
-    const int64_t gbase = (int64_t)me.group * T;
-    const int dys[4] = {-1, -1, -1, 0}, dxs[4] = {-1, 0, 1, -1};
-    for (int q = 0; q < 4; ++q) {
-      const int ny = ty + dys[q], nx = tx + dxs[q];
-      if (ny < 0 || nx < 0 || nx >= Tx) continue;
-      const int j = map[gbase + (int64_t)ny * Tx + nx] - 1;   // list index, or -1
-      if (j >= 0) unite(parent, i, j, status);
+    if (ty == 0) continue;
+    // left neighbours are joined by the runs; of the row above, the tile right
+    // above covers both diagonals when it is selected (they would be in its run)
+    const int64_t up = (int64_t)me.group * T + (int64_t)(ty - 1) * Tx + tx;
+    const int j = map[up] - 1;
+    if (j >= 0) {
+      unite(parent, i, j, status);
+    } else {
+      if (tx > 0) {
+        const int jl = map[up - 1] - 1;
+        if (jl >= 0) unite(parent, i, jl, status);
+      }
+      if (tx + 1 < Tx) {
+        const int jr = map[up + 1] - 1;
+        if (jr >= 0) unite(parent, i, jr, status);
+      }
     }
   }
 }
@@ -265,13 +354,14 @@ __global__ void k_cc_peak(const SelItem* __restrict__ items, const int* nsel, co
 
 cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
                               unsigned* status, cudaStream_t st) {
-  const int grid = 152 * 4, thr = 256;
+  const int grid = 152 * 16, thr = 256;
   k_cc_init<<<grid, thr, 0, st>>>(s.nsel, s.parent, s.compmax, s.peak);
+  k_cc_runs<<<grid, thr, 0, st>>>(s.items, s.nsel, Tx, s.parent);
   k_cc_union<<<grid, thr, 0, st>>>(s.items, s.nsel, Tx, Ty, T, s.map, s.parent, status);
   k_cc_flatten<<<grid, thr, 0, st>>>(s.nsel, s.parent);
   k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak, 0);
   k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak, 1);
-  count_launches(5);
+  count_launches(6);
   return cudaGetLastError();
 }
 
@@ -363,9 +453,37 @@ __global__ void k_emit_freq(CandArgs a, const SelItem* __restrict__ items, const
   }
 }
 
-// Image branch, step 1: one warp per peak computes the tile's arg-max of Delta
-// (ties: smallest row-major index, same FP32 arithmetic as the stack march)
-// and writes the candidate in peak-list order to `tmp`.
+__device__ __forceinline__ fitrig_candidate image_candidate(const SelItem& it, int tx, int ty,
+                                                            int w, int dx, int dy) {
+  fitrig_candidate c;
+  c.x = tx * w + dx;
+  c.y = ty * w + dy;
+  c.snapshot = it.group;
+  c.significance = (float)it.z;
+  c.branch = FITRIG_BRANCH_IMAGE;
+  c.freq_bin = -1;
+  c.xf = (float)c.x;
+  c.yf = (float)c.y;
+  return c;
+}
+
+// Image branch, step 1 (fused arg-max available): one thread per peak reads
+// the stack march's in-tile arg-max (index r*w + q of the first maximum of
+// Delta) and writes the candidate in peak-list order to `tmp`.
+__global__ void k_emit_image_arg(CandArgs a, const SelItem* __restrict__ items, const int* np_,
+                                 const int* __restrict__ plist, fitrig_candidate* tmp) {
+  const int np = *np_;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+    const SelItem it = items[plist[p]];
+    const int ty = it.t / a.Tx, tx = it.t - (it.t / a.Tx) * a.Tx;
+    const int idx = a.arg[(int64_t)it.group * a.stride + it.t];
+    tmp[p] = image_candidate(it, tx, ty, a.w, idx % a.w, idx / a.w);
+  }
+}
+
+// Image branch, step 1 (otherwise): one warp per peak computes the tile's
+// arg-max of Delta (ties: smallest row-major index, same FP32 arithmetic as the
+// stack march) and writes the candidate in peak-list order to `tmp`.
 __global__ void k_emit_image(CandArgs a, const SelItem* __restrict__ items, const int* np_,
                              const int* __restrict__ plist, fitrig_candidate* tmp) {
   const int np = *np_;
@@ -376,15 +494,17 @@ __global__ void k_emit_image(CandArgs a, const SelItem* __restrict__ items, cons
     const SelItem it = items[plist[p]];
     const int ty = it.t / a.Tx, tx = it.t - (it.t / a.Tx) * a.Tx;
     const int hw = min(a.w, a.ny - ty * a.w), ww = min(a.w, a.nx - tx * a.w);
-    const int64_t s0 = (int64_t)it.group * a.slice;
+    int64_t sl[3];   // the unit's three snapshots in the stack
+    for (int k = 0; k < 3; ++k)
+      sl[k] = (a.zmod > 0 ? (int64_t)((a.zrot + it.group + k) % a.zmod) : (int64_t)(it.group + k)) * a.slice;
     float best = -1.f;
     int bidx = INT_MAX;
     for (int q = lane; q < hw * ww; q += 32) {
       const int dy = q / ww, dx = q - (q / ww) * ww;
       const int64_t off = (int64_t)(ty * a.w + dy) * a.pitch + (tx * a.w + dx);
-      const float x0 = load_px(a.stack, a.storage, s0 + off);
-      const float x1 = load_px(a.stack, a.storage, s0 + a.slice + off);
-      const float x2 = load_px(a.stack, a.storage, s0 + 2 * a.slice + off);
+      const float x0 = load_px(a.stack, a.storage, sl[0] + off);
+      const float x1 = load_px(a.stack, a.storage, sl[1] + off);
+      const float x2 = load_px(a.stack, a.storage, sl[2] + off);
       const float d = fabsf(fabsf(x2 - x1) - fabsf(x1 - x0));
       if (d > best) {
         best = d;
@@ -399,28 +519,22 @@ __global__ void k_emit_image(CandArgs a, const SelItem* __restrict__ items, cons
         bidx = oi;
       }
     }
-    if (lane == 0) {
-      fitrig_candidate c;
-      c.x = tx * a.w + bidx % ww;
-      c.y = ty * a.w + bidx / ww;
-      c.snapshot = it.group;
-      c.significance = (float)it.z;
-      c.branch = FITRIG_BRANCH_IMAGE;
-      c.freq_bin = -1;
-      c.xf = (float)c.x;
-      c.yf = (float)c.y;
-      tmp[p] = c;
-    }
+    if (lane == 0) tmp[p] = image_candidate(it, tx, ty, a.w, bidx % ww, bidx / ww);
   }
 }
 
 // Image branch, step 2: peaks are in (unit, tile row, tile column) order.  Each
 // run of peaks sharing (unit, tile row) -- a group -- occupies the same output
 // positions once sorted by (y, x); inside a group the order is (dy, tx), so a
-// stable counting sort on the in-tile row dy finishes it.  One warp per group,
-// found at its first entry.
+// stable counting sort on the in-tile row dy finishes it.  A warp scans 32
+// consecutive peaks, finds the group heads among them by ballot, and sorts
+// each of those groups (which may run past its 32 entries).
 constexpr int kGroupWarps = 8;
 constexpr int kMaxW = 128;
+
+__device__ __forceinline__ bool same_group(const fitrig_candidate* tmp, int p, int q, int w) {
+  return tmp[p].snapshot == tmp[q].snapshot && tmp[p].y / w == tmp[q].y / w;
+}
 
 __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, const int* np_,
                                                                  const fitrig_candidate* tmp,
@@ -432,62 +546,61 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
   int* cnt = counts[warp];
   const int wid = blockIdx.x * kGroupWarps + warp;
   const int nw = gridDim.x * kGroupWarps;
-  for (int p = wid; p < np; p += nw) {
-    const fitrig_candidate head = tmp[p];
-    const int gty = head.y / a.w;
-    if (p > 0) {
-      const fitrig_candidate prev = tmp[p - 1];
-      if (prev.snapshot == head.snapshot && prev.y / a.w == gty) continue;   // not a head
-    }
-    // group extent
-    int end = p + 1;
-    for (;;) {
-      const int q = end + lane;
-      bool same = false;
-      if (q < np) {
-        const fitrig_candidate c = tmp[q];
-        same = c.snapshot == head.snapshot && c.y / a.w == gty;
+  for (int p0 = wid * 32; p0 < np; p0 += nw * 32) {
+    const int pl = p0 + lane;
+    const bool head = pl < np && (pl == 0 || !same_group(tmp, pl, pl - 1, a.w));
+    unsigned heads = __ballot_sync(0xffffffffu, head);
+    while (heads) {
+      const int p = p0 + __ffs(heads) - 1;
+      heads &= heads - 1;
+      const int gty = tmp[p].y / a.w;
+      const int snap = tmp[p].snapshot;
+      // group extent
+      int end = p + 1;
+      for (;;) {
+        const int q = end + lane;
+        const bool same = q < np && tmp[q].snapshot == snap && tmp[q].y / a.w == gty;
+        const unsigned bal = __ballot_sync(0xffffffffu, same);
+        if (bal == 0xffffffffu) {
+          end += 32;
+          continue;
+        }
+        end += __ffs(~bal) - 1;
+        break;
       }
-      const unsigned bal = __ballot_sync(0xffffffffu, same);
-      if (bal == 0xffffffffu) {
-        end += 32;
-        continue;
-      }
-      end += __ffs(~bal) - 1;
-      break;
-    }
-    for (int k = lane; k < a.w; k += 32) cnt[k] = 0;
-    __syncwarp();
-    for (int q = p + lane; q < end; q += 32) atomicAdd(&cnt[tmp[q].y - gty * a.w], 1);
-    __syncwarp();
-    if (lane == 0) {
-      int run = 0;
-      for (int k = 0; k < a.w; ++k) {
-        const int c = cnt[k];
-        cnt[k] = run;
-        run += c;
-      }
-    }
-    __syncwarp();
-    for (int q0 = p; q0 < end; q0 += 32) {
-      const int q = q0 + lane;
-      const bool valid = q < end;
-      fitrig_candidate c;
-      int dy = kMaxW;
-      if (valid) {
-        c = tmp[q];
-        dy = c.y - gty * a.w;
-      }
-      const unsigned peers = __match_any_sync(0xffffffffu, dy);
-      const int rank = __popc(peers & ((1u << lane) - 1u));
-      const int off = valid ? cnt[dy] : 0;
+      for (int k = lane; k < a.w; k += 32) cnt[k] = 0;
       __syncwarp();
-      if (valid) {
-        const int pos = base + p + off + rank;
-        if (pos < a.cap) a.out[pos] = c;
-        if (lane == __ffs(peers) - 1) cnt[dy] = off + __popc(peers);
+      for (int q = p + lane; q < end; q += 32) atomicAdd(&cnt[tmp[q].y - gty * a.w], 1);
+      __syncwarp();
+      if (lane == 0) {
+        int run = 0;
+        for (int k = 0; k < a.w; ++k) {
+          const int c = cnt[k];
+          cnt[k] = run;
+          run += c;
+        }
       }
       __syncwarp();
+      for (int q0 = p; q0 < end; q0 += 32) {
+        const int q = q0 + lane;
+        const bool valid = q < end;
+        fitrig_candidate c;
+        int dy = kMaxW;
+        if (valid) {
+          c = tmp[q];
+          dy = c.y - gty * a.w;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, dy);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        const int off = valid ? cnt[dy] : 0;
+        __syncwarp();
+        if (valid) {
+          const int pos = base + p + off + rank;
+          if (pos < a.cap) a.out[pos] = c;
+          if (lane == __ffs(peers) - 1) cnt[dy] = off + __popc(peers);
+        }
+        __syncwarp();
+      }
     }
   }
 }
@@ -501,6 +614,22 @@ __global__ void k_map_clear(const SelItem* __restrict__ items, const int* nsel, 
 
 __global__ void k_add_count(int* total, const int* part) { *total += *part; }
 
+// Copies the first min(*n, cap) candidates to mapped host memory, so only the
+// candidates that exist cross the host link.
+__global__ void k_export(const fitrig_candidate* __restrict__ src, const int* n,
+                         fitrig_candidate* dst, int cap) {
+  const int m = min(*n, cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+cudaError_t launch_export_candidates(const fitrig_candidate* src, const int* n,
+                                     fitrig_candidate* dst, int cap, cudaStream_t st) {
+  k_export<<<64, 256, 0, st>>>(src, n, dst, cap);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, int* base,
                                    fitrig_candidate* tmp, unsigned* status, cudaStream_t st) {
   // ordered list of component peaks
@@ -512,13 +641,16 @@ cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, in
     k_emit_freq<<<152 * 4, 256, 0, st>>>(a, s.items, s.npeak, s.plist);
     count_launches(4);
   } else {
-    k_emit_image<<<152 * 4, 256, 0, st>>>(a, s.items, s.npeak, s.plist, tmp);
+    if (a.arg)
+      k_emit_image_arg<<<152 * 4, 256, 0, st>>>(a, s.items, s.npeak, s.plist, tmp);
+    else
+      k_emit_image<<<152 * 4, 256, 0, st>>>(a, s.items, s.npeak, s.plist, tmp);
     k_group_sort<<<152 * 4, kGroupWarps * 32, 0, st>>>(a, s.npeak, tmp, base);
     count_launches(5);
   }
   // running total of candidates, and a clean map for the next selection
   k_add_count<<<1, 1, 0, st>>>(a.nout, s.npeak);
-  k_map_clear<<<152 * 4, 256, 0, st>>>(s.items, s.nsel, a.T, s.map);
+  k_map_clear<<<152 * 4, 256, 0, st>>>(s.items, s.nsel, a.stride, s.map);
   count_launches(2);
   return cudaGetLastError();
 }

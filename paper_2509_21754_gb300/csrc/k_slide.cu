@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(kSlideMaxThreads) k_slide(const __grid_constan
   if (tid == 0) {
     for (int j = 0; j < NS && j < L; ++j) {
       mbar_expect_tx(bar0 + 8 * j, box_bytes);
-      tma_load_3d(stage0 + j * (uint32_t)g.stage_bytes, &tmap, xload, y0 - g.h, j, bar0 + 8 * j);
+      tma_load_3d(stage0 + j * (uint32_t)g.stage_bytes, &tmap, xload, y0 - g.h, (a.zrot + j) % L,
+                  bar0 + 8 * j);
     }
   }
   float xp[kSlideR], dp[kSlideR];
@@ -106,8 +107,8 @@ __global__ void __launch_bounds__(kSlideMaxThreads) k_slide(const __grid_constan
     if (tid == 0 && j + NS < L) {
       fence_proxy_async_smem();
       mbar_expect_tx(bar0 + 8 * stg, box_bytes);
-      tma_load_3d(stage0 + stg * (uint32_t)g.stage_bytes, &tmap, xload, y0 - g.h, j + NS,
-                  bar0 + 8 * stg);
+      tma_load_3d(stage0 + stg * (uint32_t)g.stage_bytes, &tmap, xload, y0 - g.h,
+                  (a.zrot + j + NS) % L, bar0 + 8 * stg);
     }
     if (j < 2) continue;
     // horizontal pass: window rows over the extended block
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(kSlideMaxThreads) k_slide(const __grid_constan
       const float n = (float)(ny_ * nx_);
       float v = (S1 / n) * S2 * (S3 / n);
       if (!isfinite(S1) || !isfinite(v)) v = NAN;
-      a.vp[(size_t)(j - 2) * (size_t)a.nx * a.ny + (size_t)y * a.nx + x] = v;
+      a.vp[(size_t)(j - 2) * (size_t)a.vstride + (size_t)y * a.nx + x] = v;
     }
   }
 #pragma unroll

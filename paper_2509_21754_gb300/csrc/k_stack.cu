@@ -31,7 +31,7 @@
 namespace fitrig {
 
 constexpr int kStackMaxThreads = 512;
-constexpr int kSmallThreads = 128;   // thread-per-tile path: 32 x 4 tiles per CTA
+constexpr int kSmallMaxThreads = 256;   // thread-per-tile path: 32 x TBY tiles per CTA
 constexpr int kSmallMaxW = 6;
 
 template <typename T, int R, bool SIGNED>
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
   if (tid == 0) {
     for (int j = 0; j < NS && j < L; ++j) {
       mbar_expect_tx(bar0 + 8 * j, box_bytes);
-      tma_load_3d(stage0 + j * (uint32_t)g.stage_bytes, &tmap, xload, y0, j, bar0 + 8 * j);
+      tma_load_3d(stage0 + j * (uint32_t)g.stage_bytes, &tmap, xload, y0, (a.zrot + j) % L, bar0 + 8 * j);
     }
   }
 
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
     if (tid == 0 && j + NS < L) {
       fence_proxy_async_smem();
       mbar_expect_tx(bar0 + 8 * stg, box_bytes);
-      tma_load_3d(stage0 + stg * (uint32_t)g.stage_bytes, &tmap, xload, y0, j + NS,
+      tma_load_3d(stage0 + stg * (uint32_t)g.stage_bytes, &tmap, xload, y0, (a.zrot + j + NS) % L,
                   bar0 + 8 * stg);
     }
     if (++stg == NS) {
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
         const float n = (float)(hw * ww);
         float v = (S1 / n) * S2 * (S3 / n);
         if (!isfinite(S1) || !isfinite(v)) v = NAN;
-        a.vp[(size_t)(j - 2) * (size_t)a.T + (size_t)ty * a.Tx + tx] = v;
+        a.vp[(size_t)(j - 2) * (size_t)a.vstride + (size_t)ty * a.Tx + tx] = v;
       }
     }
   }
@@ -174,57 +174,87 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
 // W*W pixels' x^(s+1) and D^(s) in registers, so a tile's sums and maximum
 // never leave the thread.  A warp covers 32 tiles side by side (lane t reads
 // columns W*t .. W*t+W-1 of the stage, which spreads over all banks for odd W);
-// the CTA covers 32 x TBY tiles.  One barrier per snapshot guards the ring.
-template <typename T, int W, bool SIGNED>
-__global__ void __launch_bounds__(kSmallThreads) k_stack_small(const __grid_constant__ CUtensorMap tmap,
-                                                               const StackArgs a) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  const StackGeom& g = a.g;
-  const int NS = g.stages;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)NS * g.stage_bytes);
-  const int tid = threadIdx.x;
-  const int tbx = tid & 31;
-  const int tb = tid >> 5;
-  const int tx = blockIdx.x * 32 + tbx;
-  const int ty = blockIdx.y * g.TBY + tb;
-  const uint32_t bar0 = smem_u32(bars);
-  const uint32_t stage0 = smem_u32(smem);
-  const uint32_t box_bytes = (uint32_t)(g.boxW * g.BH * (int)sizeof(T));
-  const int L = a.nsnap;
-  const int x0 = blockIdx.x * g.BW, y0 = blockIdx.y * g.BH;
-  const bool live = tx < a.Tx && ty < a.Ty;
-  // 1 / n_t^2 of this tile (edge tiles are clipped)
-  const int hw = live ? min(W, a.ny - ty * W) : 1;
-  const int ww = live ? min(W, a.nx - tx * W) : 1;
-  const float inv_n2 = 1.f / ((float)(hw * ww) * (float)(hw * ww));
-  const int off = (tb * W) * g.boxW + tbx * W;
+// the CTA covers 32 x TBY tiles (TBY and the ring depth are tunable).  One
+// barrier per snapshot guards the ring.
 
-  if (tid == 0) {
-    prefetch_tmap(&tmap);
-    for (int i = 0; i < NS; ++i) mbar_init(bar0 + 8 * i, 1);
+// The TMA ring of one CTA.  Stage and phase advance with every snapshot
+// consumed and carry over from one box to the next (persistent kernels).
+struct Ring {
+  uint32_t bar0, stage0;
+  uint32_t box_bytes;
+  int NS;
+  uint32_t stage_bytes;
+  int stg;          // next stage to consume
+  uint32_t phase;   // its parity
+};
+
+// One field as the march sees it.
+struct FieldView {
+  int nx, ny, L, Tx, Ty;
+  int zrot;
+  int64_t vstride;
+  float* vp;
+  uint8_t* arg;
+  unsigned* status;
+};
+
+__device__ __forceinline__ void ring_init(Ring& rg, unsigned char* smem, const StackGeom& g,
+                                          int elem) {
+  rg.NS = g.stages;
+  rg.stage_bytes = (uint32_t)g.stage_bytes;
+  rg.box_bytes = (uint32_t)(g.boxW * g.BH * elem);
+  rg.stage0 = smem_u32(smem);
+  rg.bar0 = smem_u32(smem + (size_t)g.stages * g.stage_bytes);
+  rg.stg = 0;
+  rg.phase = 0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < rg.NS; ++i) mbar_init(rg.bar0 + 8 * i, 1);
     fence_mbar_init();
   }
   __syncthreads();
+}
+
+// Marches box (bx, by) of a field through its snapshots; mx collects the
+// running maximum.  Returns false (after flagging and draining, bounded) if a
+// stage never completed; the caller must then leave.
+template <typename T, int W, bool SIGNED>
+__device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const FieldView& f, int bx,
+                                            int by, int tby, Ring& rg, unsigned char* smem,
+                                            uint64_t deadline, float& mx) {
+  const int tid = threadIdx.x;
+  const int tbx = tid & 31;
+  const int tb = tid >> 5;
+  const int tx = bx * 32 + tbx;
+  const int ty = by * tby + tb;
+  const int L = f.L;
+  const int x0 = bx * 32 * W, y0 = by * tby * W;
+  const bool live = tx < f.Tx && ty < f.Ty;
+  // 1 / n_t^2 of this tile (edge tiles are clipped)
+  const int hw = live ? min(W, f.ny - ty * W) : 1;
+  const int ww = live ? min(W, f.nx - tx * W) : 1;
+  const float inv_n2 = 1.f / ((float)(hw * ww) * (float)(hw * ww));
+  const int off = (tb * W) * (32 * W) + tbx * W;
   if (tid == 0) {
-    for (int j = 0; j < NS && j < L; ++j) {
-      mbar_expect_tx(bar0 + 8 * j, box_bytes);
-      tma_load_3d(stage0 + j * (uint32_t)g.stage_bytes, &tmap, x0, y0, j, bar0 + 8 * j);
+    int s = rg.stg;
+    for (int j = 0; j < rg.NS && j < L; ++j) {
+      mbar_expect_tx(rg.bar0 + 8 * s, rg.box_bytes);
+      tma_load_3d(rg.stage0 + s * rg.stage_bytes, tmap, x0, y0, (f.zrot + j) % L, rg.bar0 + 8 * s);
+      if (++s == rg.NS) s = 0;
     }
   }
   float xp[W * W], dp[W * W];
 #pragma unroll
   for (int i = 0; i < W * W; ++i) xp[i] = dp[i] = 0.f;
-  float mx = -INFINITY;
-  const uint64_t deadline = globaltimer_ns() + a.timeout_ns;
-  float* out = a.vp + (size_t)ty * a.Tx + tx;
-  int stg = 0;
-  uint32_t phase = 0;
+  const size_t tile = (size_t)ty * f.Tx + tx;
+  float* out = f.vp + tile;
+  uint8_t* aout = f.arg ? f.arg + tile : nullptr;
   for (int j = 0; j < L; ++j) {
-    const bool ok = mbar_wait_bounded(bar0 + 8 * stg, phase, deadline);
-    const T* st = reinterpret_cast<const T*>(smem + (size_t)stg * g.stage_bytes) + off;
+    const bool ok = mbar_wait_bounded(rg.bar0 + 8 * rg.stg, rg.phase, deadline);
+    const T* st = reinterpret_cast<const T*>(smem + (size_t)rg.stg * rg.stage_bytes) + off;
     if (ok) {
       if (j >= 2) {
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int am = 0;   // first maximum in row-major order (strict >)
 #pragma unroll
         for (int r = 0; r < W; ++r) {
 #pragma unroll
@@ -237,7 +267,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_stack_small(const __grid_cons
             const float ref = SIGNED ? xp[i] : fabsf(xp[i]);
             const float xh = (xp[i] == 0.f) ? kGuardC : ref;
             s1 += d;
-            s2 = fmaxf(s2, d);
+            if (d > s2) {
+              s2 = d;
+              am = i;
+            }
             s3 += fminf(__fdividef(d, xh), 1.f);
             dp[i] = dn;
             xp[i] = xn;
@@ -246,7 +279,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_stack_small(const __grid_cons
         if (live) {
           float v = s1 * s2 * s3 * inv_n2;
           if (!isfinite(s1) || !isfinite(v)) v = NAN;
-          out[(size_t)(j - 2) * (size_t)a.T] = v;
+          out[(size_t)(j - 2) * (size_t)f.vstride] = v;
+          if (aout) aout[(size_t)(j - 2) * (size_t)f.vstride] = (uint8_t)am;
         }
       } else {
 #pragma unroll
@@ -264,26 +298,116 @@ __global__ void __launch_bounds__(kSmallThreads) k_stack_small(const __grid_cons
     }
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
-        atomicOr(a.status, kErrTimeout);
+        atomicOr(f.status, kErrTimeout);
         const uint64_t d2 = globaltimer_ns() + 1000000ull;
-        for (int jj = j; jj < L && jj < j + NS; ++jj)
-          mbar_wait_bounded(bar0 + 8 * (jj % NS), (uint32_t)((jj / NS) & 1), d2);
+        int s = rg.stg;
+        uint32_t ph = rg.phase;
+        for (int jj = j; jj < L && jj < j + rg.NS; ++jj) {
+          mbar_wait_bounded(rg.bar0 + 8 * s, ph, d2);
+          if (++s == rg.NS) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
       }
-      return;
+      return false;
     }
-    if (tid == 0 && j + NS < L) {
+    if (tid == 0 && j + rg.NS < L) {
       fence_proxy_async_smem();
-      mbar_expect_tx(bar0 + 8 * stg, box_bytes);
-      tma_load_3d(stage0 + stg * (uint32_t)g.stage_bytes, &tmap, x0, y0, j + NS, bar0 + 8 * stg);
+      mbar_expect_tx(rg.bar0 + 8 * rg.stg, rg.box_bytes);
+      tma_load_3d(rg.stage0 + rg.stg * rg.stage_bytes, tmap, x0, y0, (f.zrot + j + rg.NS) % L,
+                  rg.bar0 + 8 * rg.stg);
     }
-    if (++stg == NS) {
-      stg = 0;
-      phase ^= 1u;
+    if (++rg.stg == rg.NS) {
+      rg.stg = 0;
+      rg.phase ^= 1u;
     }
   }
+  return true;
+}
+
+__device__ __forceinline__ void block_max_to(float mx, unsigned* gmax) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((tid & 31) == 0 && mx > -INFINITY) atomicMax(a.gmax, f32_key(mx));
+  if ((threadIdx.x & 31) == 0 && mx > -INFINITY) atomicMax(gmax, f32_key(mx));
+}
+
+template <typename T, int W, bool SIGNED>
+__global__ void __launch_bounds__(kSmallMaxThreads) k_stack_small(const __grid_constant__ CUtensorMap tmap,
+                                                               const StackArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (threadIdx.x == 0) prefetch_tmap(&tmap);
+  Ring rg;
+  ring_init(rg, smem, a.g, (int)sizeof(T));
+  FieldView f;
+  f.nx = a.nx;
+  f.ny = a.ny;
+  f.L = a.nsnap;
+  f.Tx = a.Tx;
+  f.Ty = a.Ty;
+  f.zrot = a.zrot;
+  f.vstride = a.vstride;
+  f.vp = a.vp;
+  f.arg = a.arg;
+  f.status = a.status;
+  float mx = -INFINITY;
+  const uint64_t deadline = globaltimer_ns() + a.timeout_ns;
+  if (!march_small<T, W, SIGNED>(&tmap, f, blockIdx.x, blockIdx.y, a.g.TBY, rg, smem, deadline, mx))
+    return;
+  block_max_to(mx, a.gmax);
+}
+
+// Persistent form over many fields (one launch for a whole batch): each CTA
+// takes the next (field, box) item from a global counter until none is left;
+// fields are ordered largest first.  Every field has its own TMA descriptor in
+// global memory; the ring carries over between items.
+template <typename T, int W, bool SIGNED>
+__global__ void __launch_bounds__(kSmallMaxThreads) k_stack_multi(const FieldDesc* __restrict__ fields,
+                                                               int nfields, int64_t nitems,
+                                                               unsigned long long* counter,
+                                                               const StackGeom g,
+                                                               uint64_t timeout_ns) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ long long s_item;
+  __shared__ int s_field;
+  Ring rg;
+  ring_init(rg, smem, g, (int)sizeof(T));
+  const uint64_t deadline = globaltimer_ns() + timeout_ns;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(counter, 1ull);
+      int lo = 0, hi = nfields - 1;   // last field with item0 <= it
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (fields[mid].item0 <= it) lo = mid; else hi = mid - 1;
+      }
+      s_item = it;
+      s_field = lo;
+    }
+    __syncthreads();
+    const long long it = s_item;
+    const int fi = s_field;
+    __syncthreads();   // everyone has read the item before thread 0 fetches the next
+    if (it >= nitems) return;
+    const FieldDesc& d = fields[fi];
+    const long long b = it - d.item0;
+    FieldView f;
+    f.nx = d.nx;
+    f.ny = d.ny;
+    f.L = d.L;
+    f.Tx = d.Tx;
+    f.Ty = d.Ty;
+    f.zrot = d.zrot;
+    f.vstride = d.vstride;
+    f.vp = d.vp;
+    f.arg = d.arg;
+    f.status = d.status;
+    float mx = -INFINITY;
+    if (!march_small<T, W, SIGNED>(&d.tmap, f, (int)(b % d.gridX), (int)(b / d.gridX), g.TBY, rg,
+                                   smem, deadline, mx))
+      return;
+    block_max_to(mx, d.gmax);
+  }
 }
 
 // Finite maximum over the stack; used only when the fused maximum saw +inf.
@@ -305,13 +429,16 @@ __global__ void k_finite_max(const T* __restrict__ x, int L, int ny, int nx, int
   if ((threadIdx.x & 31) == 0 && m > -INFINITY) atomicMax(gmax, f32_key(m));
 }
 
-static bool small_geometry(int w, int elem_bytes, StackGeom* g) {
-  // 32 tiles across (lane = tile), 4 tile rows per CTA
-  const int tbx = 32, tby = kSmallThreads / 32;
+bool small_geometry(int w, int elem_bytes, int tby, int stages, StackGeom* g) {
+  // 32 tiles across (lane = tile), TBY tile rows per CTA
+  if (w < 3 || w > kSmallMaxW || tby < 1 || 32 * tby > kSmallMaxThreads || stages < 2) return false;
+  const int tbx = 32;
   const int BW = tbx * w, BH = tby * w;
-  if (BW > 256 || (BW * elem_bytes) % 16 != 0 || BW % 8 != 0) return false;
+  if (BW > 256 || BH > 256 || (BW * elem_bytes) % 16 != 0 || BW % 8 != 0) return false;
   size_t stage = (size_t)BW * BH * elem_bytes;
   stage = (stage + 127) / 128 * 128;
+  const size_t smem = (size_t)stages * stage + 8 * 8;
+  if (smem > 232448 - 1024) return false;
   g->w = w;
   g->R = 0;   // marks the thread-per-tile path
   g->nseg = 1;
@@ -321,16 +448,16 @@ static bool small_geometry(int w, int elem_bytes, StackGeom* g) {
   g->BH = BH;
   g->boxW = BW;
   g->aligned = true;
-  g->stages = 4;
-  g->threads = kSmallThreads;
+  g->stages = stages;
+  g->threads = 32 * tby;
   g->stage_bytes = stage;
-  g->smem_bytes = 4 * stage + 8 * 8;
+  g->smem_bytes = smem;
   return true;
 }
 
 bool stack_geometry(int w, int elem_bytes, StackGeom* g) {
   if (w < 1 || w > 128) return false;
-  if (w >= 3 && w <= kSmallMaxW && small_geometry(w, elem_bytes, g)) return true;
+  if (w >= 3 && w <= kSmallMaxW && small_geometry(w, elem_bytes, 4, 4, g)) return true;
   // rows per thread R (a template value) and row segments per tile band
   int R, nseg;
   if (w <= 8) {
@@ -454,6 +581,79 @@ cudaError_t launch_stack(const CUtensorMap* tmap, const StackArgs& a, int storag
     case FITRIG_BF16: return sg ? launch_r<bf16_t, true>(tmap, a, st) : launch_r<bf16_t, false>(tmap, a, st);
     case FITRIG_F16: return sg ? launch_r<f16_t, true>(tmap, a, st) : launch_r<f16_t, false>(tmap, a, st);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int W, bool SIGNED>
+static cudaError_t launch_multi_t(const FieldDesc* fields, int nfields, int64_t nitems,
+                                  unsigned long long* counter, const StackGeom& g, int grid,
+                                  uint64_t timeout_ns, cudaStream_t st) {
+  auto kern = k_stack_multi<T, W, SIGNED>;
+  static size_t configured = 0;
+  if (g.smem_bytes > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)g.smem_bytes);
+    if (e != cudaSuccess) return e;
+    configured = g.smem_bytes;
+  }
+  kern<<<grid, g.threads, g.smem_bytes, st>>>(fields, nfields, nitems, counter, g, timeout_ns);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T, bool SIGNED>
+static cudaError_t launch_multi_w(const FieldDesc* fields, int nfields, int64_t nitems,
+                                  unsigned long long* counter, const StackGeom& g, int grid,
+                                  uint64_t timeout_ns, cudaStream_t st) {
+  switch (g.w) {
+    case 3: return launch_multi_t<T, 3, SIGNED>(fields, nfields, nitems, counter, g, grid, timeout_ns, st);
+    case 4: return launch_multi_t<T, 4, SIGNED>(fields, nfields, nitems, counter, g, grid, timeout_ns, st);
+    case 5: return launch_multi_t<T, 5, SIGNED>(fields, nfields, nitems, counter, g, grid, timeout_ns, st);
+    case 6: return launch_multi_t<T, 6, SIGNED>(fields, nfields, nitems, counter, g, grid, timeout_ns, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int multi_blocks_per_sm(const StackGeom& g, int storage, int rmode) {
+  int n = 0;
+  const void* fn = nullptr;
+  const bool sg = rmode == FITRIG_RMODE_SIGNED;
+#define FITRIG_PICK(T)                                                                      \
+  switch (g.w) {                                                                            \
+    case 3: fn = sg ? (const void*)k_stack_multi<T, 3, true> : (const void*)k_stack_multi<T, 3, false>; break; \
+    case 4: fn = sg ? (const void*)k_stack_multi<T, 4, true> : (const void*)k_stack_multi<T, 4, false>; break; \
+    case 5: fn = sg ? (const void*)k_stack_multi<T, 5, true> : (const void*)k_stack_multi<T, 5, false>; break; \
+    case 6: fn = sg ? (const void*)k_stack_multi<T, 6, true> : (const void*)k_stack_multi<T, 6, false>; break; \
+  }
+  if (storage == FITRIG_F32) { FITRIG_PICK(float) }
+  else if (storage == FITRIG_BF16) { FITRIG_PICK(bf16_t) }
+  else { FITRIG_PICK(f16_t) }
+#undef FITRIG_PICK
+  if (!fn) return 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem_bytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, g.threads, g.smem_bytes) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_stack_multi(const FieldDesc* fields, int nfields, int64_t nitems,
+                               unsigned long long* counter, const StackGeom& g, int grid,
+                               int storage, int rmode, uint64_t timeout_ns, cudaStream_t st) {
+  const bool sg = rmode == FITRIG_RMODE_SIGNED;
+  switch (storage) {
+    case FITRIG_F32:
+      return sg ? launch_multi_w<float, true>(fields, nfields, nitems, counter, g, grid, timeout_ns, st)
+                : launch_multi_w<float, false>(fields, nfields, nitems, counter, g, grid, timeout_ns, st);
+    case FITRIG_BF16:
+      return sg ? launch_multi_w<bf16_t, true>(fields, nfields, nitems, counter, g, grid, timeout_ns, st)
+                : launch_multi_w<bf16_t, false>(fields, nfields, nitems, counter, g, grid, timeout_ns, st);
+    case FITRIG_F16:
+      return sg ? launch_multi_w<f16_t, true>(fields, nfields, nitems, counter, g, grid, timeout_ns, st)
+                : launch_multi_w<f16_t, false>(fields, nfields, nitems, counter, g, grid, timeout_ns, st);
+    default:
+      return cudaErrorInvalidValue;
   }
 }
 

@@ -9,6 +9,10 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <time.h>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -56,6 +60,10 @@ struct fitrig_plan_s {
   int storage = FITRIG_F32, noise = FITRIG_NOISE_MEANSTD, rmode = FITRIG_RMODE_ABS;
   int edge = FITRIG_EDGE_PARTIAL;
   int stride = FITRIG_STRIDE_TILE;
+  int autotune = 0;
+  bool ring = false;       // serving field: the stack is a ring of L slots
+  int64_t bytes = 0;       // device bytes allocated by the plan
+  int zrot = 0;            // slot of the current unit's first snapshot
   uint64_t timeout_ns = 2000000000ull;
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -63,6 +71,7 @@ struct fitrig_plan_s {
   // derived
   int Tx = 0, Ty = 0, nxu = 0, nyu = 0, units = 0;
   int64_t T = 0;
+  int64_t vstride = 0;     // floats between units of the statistic cube
   int64_t pitch = 0;       // elements per row
   size_t slice_bytes = 0;  // bytes per snapshot
   StackGeom geom{};
@@ -76,6 +85,8 @@ struct fitrig_plan_s {
   // device memory
   char* d_stack = nullptr;
   float* d_vp = nullptr;
+  uint8_t* d_arg = nullptr;      // fused in-tile arg-max (thread-per-tile path)
+  double* d_inv = nullptr;       // units + 1 reciprocal scales
   unsigned* d_small = nullptr;   // [0] gmax key, [1] status flags, [2] ncand
   unsigned long long* d_invalid = nullptr;
   double* d_cs = nullptr;        // (units + 1) x (centre, scale)
@@ -116,7 +127,7 @@ static int select_capacity(fitrig_plan_t p) {
 }
 
 static void free_all(fitrig_plan_t p) {
-  void* ptrs[] = {p->d_stack, p->d_vp,  p->d_small, p->d_invalid,  p->d_cs,
+  void* ptrs[] = {p->d_stack, p->d_vp,  p->d_small, p->d_invalid,  p->d_cs, p->d_arg, p->d_inv,
                   p->d_thr,   p->d_noise, p->d_sel, p->d_cand,     p->d_cand_tmp,
                   p->d_eta,   p->d_bin, p->d_tw,    p->d_staging,  p->d_report};
   for (void* q : ptrs)
@@ -124,6 +135,132 @@ static void free_all(fitrig_plan_t p) {
   if (p->h_pinned) cudaFreeHost(p->h_pinned);
   p->h_pinned = nullptr;
   p->allocated = false;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Times every thread-per-tile shape (tile rows per CTA x ring depth) of the
+// stack march on a probe stack and keeps the fastest per (window, storage).
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::pair<int, int>, std::pair<std::pair<int, int>, float>> g_tuned;
+}  // namespace
+
+static int run_autotune(int w, int storage, int* tby_out, int* ns_out, float* ms_out) {
+  const int eb = elem_bytes(storage);
+  const int L = 16, ny = 2048, nx = 2048;
+  const int64_t pitch = ((int64_t)nx * eb + 127) / 128 * 128 / eb;
+  const size_t slice = (size_t)pitch * ny * eb;
+  const int Tx = (nx + w - 1) / w, Ty = (ny + w - 1) / w;
+  const int64_t T = (int64_t)Tx * Ty, vs = (T + 3) / 4 * 4;
+  void* stack = nullptr;
+  float* vp = nullptr;
+  unsigned* small = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = FITRIG_OK;
+  float best = 1e30f;
+  int btby = 4, bns = 4;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return FITRIG_ECUDA;
+  if (cudaMalloc(&stack, slice * L) != cudaSuccess || cudaMalloc(&vp, sizeof(float) * (L - 2) * vs) != cudaSuccess ||
+      cudaMalloc(&small, 64) != cudaSuccess || cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    rc = FITRIG_ENOMEM;
+  }
+  if (rc == FITRIG_OK && launch_fill_probe(stack, storage, (int64_t)(slice / eb) * L, 12345u, st) != cudaSuccess)
+    rc = FITRIG_ECUDA;
+  const CUtensorMapDataType dt = storage == FITRIG_F32    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : storage == FITRIG_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const int tbys[3] = {2, 4, 8}, nss[4] = {2, 3, 4, 6};
+  for (int a = 0; a < 3 && rc == FITRIG_OK; ++a) {
+    for (int b = 0; b < 4 && rc == FITRIG_OK; ++b) {
+      StackGeom g;
+      if (!small_geometry(w, eb, tbys[a], nss[b], &g)) continue;
+      g.gridX = (Tx + g.TBX - 1) / g.TBX;
+      g.gridY = (Ty + g.TBY - 1) / g.TBY;
+      CUtensorMap tmap;
+      const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)L};
+      const cuuint64_t strides[2] = {(cuuint64_t)pitch * eb, (cuuint64_t)slice};
+      const cuuint32_t box[3] = {(cuuint32_t)g.boxW, (cuuint32_t)g.BH, 1};
+      const cuuint32_t es[3] = {1, 1, 1};
+      if (enc(&tmap, dt, 3, stack, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        rc = FITRIG_ECUDA;
+        break;
+      }
+      StackArgs sa;
+      sa.nx = nx;
+      sa.ny = ny;
+      sa.nsnap = L;
+      sa.Tx = Tx;
+      sa.Ty = Ty;
+      sa.T = T;
+      sa.vstride = vs;
+      sa.vp = vp;
+      sa.arg = nullptr;
+      sa.zrot = 0;
+      sa.gmax = small;
+      sa.status = small + 1;
+      sa.timeout_ns = 2000000000ull;
+      sa.g = g;
+      float total = 0.f;
+      for (int it = 0; it < 4 && rc == FITRIG_OK; ++it) {
+        if (cudaEventRecord(e0, st) != cudaSuccess || launch_stack(&tmap, sa, storage, FITRIG_RMODE_ABS, st) != cudaSuccess ||
+            cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          rc = FITRIG_ECUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (it > 0) total += ms;   // the first launch warms up
+      }
+      const float ms = total / 3.f;
+      if (rc == FITRIG_OK && ms < best) {
+        best = ms;
+        btby = tbys[a];
+        bns = nss[b];
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (stack) cudaFree(stack);
+  if (vp) cudaFree(vp);
+  if (small) cudaFree(small);
+  if (rc != FITRIG_OK) {
+    (void)cudaGetLastError();
+    return rc;
+  }
+  *tby_out = btby;
+  *ns_out = bns;
+  *ms_out = best;
+  return FITRIG_OK;
+}
+
+static int tuned_shape(int w, int storage, int* tby, int* ns) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  auto it = g_tuned.find({w, storage});
+  if (it == g_tuned.end()) {
+    float ms = 0.f;
+    const int rc = run_autotune(w, storage, tby, ns, &ms);
+    if (rc != FITRIG_OK) return rc;
+    g_tuned[{w, storage}] = {{*tby, *ns}, ms};
+    return FITRIG_OK;
+  }
+  *tby = it->second.first.first;
+  *ns = it->second.first.second;
+  return FITRIG_OK;
+}
+
+// cudaMalloc that also counts the plan's device bytes (serving admission).
+template <typename Ptr>
+static cudaError_t dmalloc(fitrig_plan_t p, Ptr** ptr, size_t bytes) {
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(ptr), bytes);
+  if (e == cudaSuccess) p->bytes += (int64_t)bytes;
+  return e;
 }
 
 static int allocate(fitrig_plan_t p) {
@@ -140,7 +277,14 @@ static int allocate(fitrig_plan_t p) {
     boxW = p->sgeom.boxW;
     boxH = p->sgeom.EH;
   } else {
-    if (!stack_geometry(p->w, eb, &p->geom)) return FITRIG_EUNSUPPORTED;
+    int tby = 0, ns = 0;
+    if (p->autotune && p->w >= 3 && p->w <= 6 &&
+        tuned_shape(p->w, p->storage, &tby, &ns) == FITRIG_OK &&
+        small_geometry(p->w, eb, tby, ns, &p->geom)) {
+      // tuned thread-per-tile shape
+    } else if (!stack_geometry(p->w, eb, &p->geom)) {
+      return FITRIG_EUNSUPPORTED;
+    }
     p->geom.gridX = (p->Tx + p->geom.TBX - 1) / p->geom.TBX;
     p->geom.gridY = (p->Ty + p->geom.TBY - 1) / p->geom.TBY;
     if (p->geom.gridY > 65535) return FITRIG_EUNSUPPORTED;
@@ -148,16 +292,21 @@ static int allocate(fitrig_plan_t p) {
     boxH = p->geom.BH;
   }
   const int U = p->units;
-  CK(cudaMalloc(&p->d_stack, p->slice_bytes * p->L));
-  CK(cudaMalloc(&p->d_vp, sizeof(float) * (size_t)U * p->T));
-  CK(cudaMalloc(&p->d_small, 64));
-  CK(cudaMalloc(&p->d_invalid, sizeof(unsigned long long)));
-  CK(cudaMalloc(&p->d_cs, sizeof(double) * 2 * (U + 1)));
-  CK(cudaMalloc(&p->d_thr, sizeof(float) * (U + 1)));
+  p->vstride = (p->T + 3) / 4 * 4;
+  CK(dmalloc(p, &p->d_stack, p->slice_bytes * p->L));
+  CK(dmalloc(p, &p->d_vp, sizeof(float) * (size_t)U * p->vstride));
+  CK(cudaMemset(p->d_vp, 0xff, sizeof(float) * (size_t)U * p->vstride));   // NaN padding
+  if (p->stride == FITRIG_STRIDE_TILE && p->geom.R == 0)
+    CK(dmalloc(p, &p->d_arg, (size_t)U * p->vstride));
+  CK(dmalloc(p, &p->d_inv, sizeof(double) * (U + 1)));
+  CK(dmalloc(p, &p->d_small, 64));
+  CK(dmalloc(p, &p->d_invalid, sizeof(unsigned long long)));
+  CK(dmalloc(p, &p->d_cs, sizeof(double) * 2 * (U + 1)));
+  CK(dmalloc(p, &p->d_thr, sizeof(float) * (U + 1)));
   const int nblk_img = std::max(1, std::min(1024, (152 * 4 + U - 1) / U));
   const int nblk_freq = 152 * 4;
   const size_t nb = std::max(noise_scratch_bytes(U, nblk_img), noise_scratch_bytes(1, nblk_freq));
-  CK(cudaMalloc(&p->d_noise, nb));
+  CK(dmalloc(p, &p->d_noise, nb));
   noise_scratch_carve(p->d_noise, U, nblk_img, &p->ns_img);
   noise_scratch_carve(p->d_noise, 1, nblk_freq, &p->ns_freq);
   p->ns_img.invalid = p->d_invalid;
@@ -173,14 +322,14 @@ static int allocate(fitrig_plan_t p) {
     bytes += (n + 255) / 256 * 256;
     return off;
   };
-  const size_t o_cnt = carve(sizeof(int) * s.nblk), o_off = carve(sizeof(int) * (s.nblk + 1));
+  const size_t o_cnt = carve(sizeof(int) * s.nblk * 8), o_off = carve(sizeof(int) * (s.nblk * 8 + 1));
   const size_t o_items = carve(sizeof(SelItem) * cap), o_nsel = carve(sizeof(int));
   const size_t o_par = carve(sizeof(int) * cap), o_cm = carve(sizeof(unsigned long long) * cap);
   const size_t o_pk = carve(sizeof(int) * cap);
   const size_t o_pl = carve(sizeof(int) * cap), o_np = carve(sizeof(int));
-  const size_t map_n = (size_t)std::max<int64_t>(1, (int64_t)U * p->T);
+  const size_t map_n = (size_t)std::max<int64_t>(1, (int64_t)U * p->vstride);
   const size_t o_map = carve(sizeof(int) * map_n);
-  CK(cudaMalloc(&p->d_sel, bytes));
+  CK(dmalloc(p, &p->d_sel, bytes));
   CK(cudaMemset(p->d_sel, 0, bytes));
   char* b = static_cast<char*>(p->d_sel);
   s.blkcnt = reinterpret_cast<int*>(b + o_cnt);
@@ -194,11 +343,12 @@ static int allocate(fitrig_plan_t p) {
   s.npeak = reinterpret_cast<int*>(b + o_np);
   s.map = reinterpret_cast<int*>(b + o_map);
   p->cand_cap = s.capacity;
-  CK(cudaMalloc(&p->d_cand, sizeof(fitrig_candidate) * cap));
-  CK(cudaMalloc(&p->d_cand_tmp, sizeof(fitrig_candidate) * cap));
+  CK(dmalloc(p, &p->d_cand, sizeof(fitrig_candidate) * cap));
+  CK(dmalloc(p, &p->d_cand_tmp, sizeof(fitrig_candidate) * cap));
   if (p->branch & FITRIG_BRANCH_FREQ) {
-    CK(cudaMalloc(&p->d_eta, sizeof(float) * p->T));
-    CK(cudaMalloc(&p->d_bin, sizeof(int) * p->T));
+    CK(dmalloc(p, &p->d_eta, sizeof(float) * p->vstride));
+    CK(cudaMemset(p->d_eta, 0xff, sizeof(float) * p->vstride));   // NaN padding
+    CK(dmalloc(p, &p->d_bin, sizeof(int) * p->T));
     const int n = U, H = (n - 1) / 2, K = n / 2;
     std::vector<float2> tw((size_t)std::max(1, K * H));
     for (int k = 1; k <= K; ++k)
@@ -206,7 +356,7 @@ static int allocate(fitrig_plan_t p) {
         const double ang = 2.0 * M_PI * (double)(((int64_t)k * q) % n) / (double)n;
         tw[(size_t)(k - 1) * H + (q - 1)] = make_float2((float)std::cos(ang), (float)std::sin(ang));
       }
-    CK(cudaMalloc(&p->d_tw, sizeof(float2) * tw.size()));
+    CK(dmalloc(p, &p->d_tw, sizeof(float2) * tw.size()));
     CK(cudaMemcpy(p->d_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
   }
   CK(cudaMallocHost(&p->h_pinned, 64));
@@ -296,6 +446,10 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t p, int option, int64_t value) {
     case FITRIG_OPT_STREAM:
       p->stream = reinterpret_cast<cudaStream_t>(value);
       return FITRIG_OK;
+    case FITRIG_OPT_AUTOTUNE:
+      if (p->allocated) return FITRIG_ESTATE;
+      p->autotune = value != 0;
+      return FITRIG_OK;
     case FITRIG_OPT_TIMEOUT_NS:
       if (value <= 0) return FITRIG_EINVAL;
       p->timeout_ns = (uint64_t)value;
@@ -380,7 +534,7 @@ FITRIG_API int fitrig_push_snapshot(fitrig_plan_t p, const void* data, int dtype
     const void* src = data;
     int64_t sp = rp;
     if (!on_device) {
-      if (!p->d_staging) CK(cudaMalloc(&p->d_staging, (size_t)p->nx * p->ny * 4));
+      if (!p->d_staging) CK(dmalloc(p, &p->d_staging, (size_t)p->nx * p->ny * 4));
       CK(cudaMemcpy2DAsync(p->d_staging, (size_t)p->nx * ib, data, rp * ib, (size_t)p->nx * ib,
                            p->ny, cudaMemcpyHostToDevice, st));
       src = p->d_staging;
@@ -405,48 +559,65 @@ static void rec(fitrig_plan_t p, int k, int end, cudaStream_t st) {
   cudaEventRecord(p->ev[2 * k + end], st);
 }
 
-FITRIG_API int fitrig_detect(fitrig_plan_t p, int32_t* ncand) {
-  if (!p || !ncand) return FITRIG_EINVAL;
-  *ncand = 0;
-  if (p->pushed < 3) return FITRIG_ESTATE;
-  if ((p->branch & FITRIG_BRANCH_FREQ) && p->pushed != p->L) return FITRIG_ESTATE;
-  CK(cudaSetDevice(p->device));
-  cudaStream_t st = plan_stream(p);
-  const int P = p->pushed, U = P - 2;
-  unsigned* gmax = p->d_small;
-  unsigned* status = p->d_small + 1;
-  int* nout = reinterpret_cast<int*>(p->d_small + 2);
-  CK(cudaMemsetAsync(p->d_small, 0, 16, st));
-  CK(cudaMemsetAsync(p->d_invalid, 0, sizeof(unsigned long long), st));
-  rec(p, FITRIG_KERNEL_DETECT, 0, st);
-  rec(p, FITRIG_KERNEL_STACK, 0, st);
+// The trigger as stream work, in three pieces so that a batch can put the
+// stack marches of many plans into one launch and capture everything in one
+// CUDA graph: clear (counters), march (a2, or a4 in sliding mode), post
+// (a5-a9 and the read-back of the counters).  `timed` records the per-kernel
+// events (not used inside graphs).
+static cudaError_t enqueue_clear(fitrig_plan_t p, cudaStream_t st) {
+  // a serving ring keeps word 0, the running maximum M over every snapshot seen
+  cudaError_t e = p->ring ? cudaMemsetAsync(p->d_small + 1, 0, 12, st)
+                          : cudaMemsetAsync(p->d_small, 0, 16, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->d_invalid, 0, sizeof(unsigned long long), st);
+  return e;
+}
+
+static cudaError_t enqueue_march(fitrig_plan_t p, cudaStream_t st) {
   StackArgs a;
   a.nx = p->nxu;
   a.ny = p->nyu;
-  a.nsnap = P;
+  a.nsnap = p->pushed;
   a.Tx = p->Tx;
   a.Ty = p->Ty;
   a.T = p->T;
+  a.vstride = p->vstride;
   a.vp = p->d_vp;
-  a.gmax = gmax;
-  a.status = status;
+  a.arg = p->d_arg;
+  a.zrot = p->zrot;
+  a.gmax = p->d_small;
+  a.status = p->d_small + 1;
   a.timeout_ns = p->timeout_ns;
   a.g = p->geom;
   if (p->stride == FITRIG_STRIDE_SLIDING) {
     SlideArgs sa;
+    sa.zrot = p->zrot;
     sa.nx = p->nx;
     sa.ny = p->ny;
-    sa.nsnap = P;
+    sa.nsnap = p->pushed;
+    sa.vstride = p->vstride;
     sa.vp = p->d_vp;
-    sa.gmax = gmax;
-    sa.status = status;
+    sa.gmax = p->d_small;
+    sa.status = p->d_small + 1;
     sa.timeout_ns = p->timeout_ns;
     sa.g = p->sgeom;
-    CK(launch_slide(&p->tmap, sa, p->storage, p->rmode, st));
-  } else {
-    CK(launch_stack(&p->tmap, a, p->storage, p->rmode, st));
+    return launch_slide(&p->tmap, sa, p->storage, p->rmode, st);
   }
-  rec(p, FITRIG_KERNEL_STACK, 1, st);
+  return launch_stack(&p->tmap, a, p->storage, p->rmode, st);
+}
+
+#define CKE(expr)                          \
+  do {                                     \
+    const cudaError_t e_ = (expr);         \
+    if (e_ != cudaSuccess) return e_;      \
+  } while (0)
+
+static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
+  const int U = p->pushed - 2;
+  unsigned* status = p->d_small + 1;
+  int* nout = reinterpret_cast<int*>(p->d_small + 2);
+  auto mark = [&](int k, int end) {
+    if (timed) cudaEventRecord(p->ev[2 * k + end], st);
+  };
   CandArgs ca;
   ca.nx = p->nxu;
   ca.ny = p->nyu;
@@ -454,10 +625,14 @@ FITRIG_API int fitrig_detect(fitrig_plan_t p, int32_t* ncand) {
   ca.Tx = p->Tx;
   ca.Ty = p->Ty;
   ca.T = p->T;
+  ca.stride = p->vstride;
+  ca.arg = nullptr;
   ca.stack = p->d_stack;
   ca.storage = p->storage;
   ca.pitch = p->pitch;
   ca.slice = (int64_t)p->pitch * p->ny;
+  ca.zrot = p->zrot;
+  ca.zmod = p->ring ? p->L : 0;
   ca.eta = p->d_eta;
   ca.bin = p->d_bin;
   ca.out = p->d_cand;
@@ -465,39 +640,38 @@ FITRIG_API int fitrig_detect(fitrig_plan_t p, int32_t* ncand) {
   ca.cap = p->cand_cap;
   // frequency branch first: its candidates (snapshot -1) lead the sorted list
   if (p->branch & FITRIG_BRANCH_FREQ) {
-    rec(p, FITRIG_KERNEL_SPECTRUM, 0, st);
-    CK(launch_spectrum(p->d_vp, U, p->T, p->d_tw, p->d_eta, p->d_bin, st));
-    rec(p, FITRIG_KERNEL_SPECTRUM, 1, st);
+    mark(FITRIG_KERNEL_SPECTRUM, 0);
+    CKE(launch_spectrum(p->d_vp, U, p->T, p->vstride, p->d_tw, p->d_eta, p->d_bin, st));
+    mark(FITRIG_KERNEL_SPECTRUM, 1);
     double* cs = p->d_cs + 2 * U;
-    CK(launch_noise(p->d_eta, 1, p->T, p->noise, p->ns_freq, cs, st));
-    CK(launch_thresholds(cs, 1, p->tau, p->d_thr + U, st));
-    CK(launch_select(p->d_eta, 1, p->T, p->d_thr + U, cs, p->sel, status, st));
-    CK(launch_components(p->Tx, p->Ty, p->T, p->sel, status, st));
+    CKE(launch_noise(p->d_eta, 1, p->vstride, p->T, p->noise, p->ns_freq, cs, st));
+    CKE(launch_thresholds(cs, 1, p->tau, p->d_thr + U, p->d_inv + U, st));
+    CKE(launch_select(p->d_eta, 1, p->vstride, p->d_thr + U, cs, p->d_inv + U, p->sel, status, st));
+    CKE(launch_components(p->Tx, p->Ty, p->vstride, p->sel, status, st));
     ca.branch = FITRIG_BRANCH_FREQ;
-    CK(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
+    CKE(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
   }
   if (p->branch & FITRIG_BRANCH_IMAGE) {
-    rec(p, FITRIG_KERNEL_NOISE, 0, st);
-    CK(launch_noise(p->d_vp, U, p->T, p->noise, p->ns_img, p->d_cs, st));
-    CK(launch_thresholds(p->d_cs, U, p->tau, p->d_thr, st));
-    rec(p, FITRIG_KERNEL_NOISE, 1, st);
-    rec(p, FITRIG_KERNEL_SELECT, 0, st);
-    CK(launch_select(p->d_vp, U, p->T, p->d_thr, p->d_cs, p->sel, status, st));
-    CK(launch_components(p->Tx, p->Ty, p->T, p->sel, status, st));
+    mark(FITRIG_KERNEL_NOISE, 0);
+    CKE(launch_noise(p->d_vp, U, p->vstride, p->T, p->noise, p->ns_img, p->d_cs, st));
+    CKE(launch_thresholds(p->d_cs, U, p->tau, p->d_thr, p->d_inv, st));
+    mark(FITRIG_KERNEL_NOISE, 1);
+    mark(FITRIG_KERNEL_SELECT, 0);
+    CKE(launch_select(p->d_vp, U, p->vstride, p->d_thr, p->d_cs, p->d_inv, p->sel, status, st));
+    CKE(launch_components(p->Tx, p->Ty, p->vstride, p->sel, status, st));
     ca.branch = FITRIG_BRANCH_IMAGE;
-    CK(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
-    rec(p, FITRIG_KERNEL_SELECT, 1, st);
+    ca.arg = p->d_arg;
+    CKE(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
+    mark(FITRIG_KERNEL_SELECT, 1);
   }
-  CK(launch_clamp_count(nout, (int)p->cand_cap, status, st));
-  rec(p, FITRIG_KERNEL_DETECT, 1, st);
-  CK(cudaMemcpyAsync(p->h_pinned, p->d_small, 16, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(p->h_pinned + 4, p->d_invalid, 8, cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  for (int k = 0; k < FITRIG_KERNEL_COUNT; ++k) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, p->ev[2 * k], p->ev[2 * k + 1]) == cudaSuccess) p->ms[k] = ms;
-    else (void)cudaGetLastError();
-  }
+  CKE(launch_clamp_count(nout, (int)p->cand_cap, status, st));
+  CKE(cudaMemcpyAsync(p->h_pinned, p->d_small, 16, cudaMemcpyDeviceToHost, st));
+  CKE(cudaMemcpyAsync(p->h_pinned + 4, p->d_invalid, 8, cudaMemcpyDeviceToHost, st));
+  return cudaSuccess;
+}
+
+// After the stream has passed enqueue_post: record the results on the host.
+static int finish_detect(fitrig_plan_t p, int32_t* ncand) {
   const unsigned flags = p->h_pinned[1];
   const int n = (int)p->h_pinned[2];
   unsigned long long invalid;
@@ -505,12 +679,73 @@ FITRIG_API int fitrig_detect(fitrig_plan_t p, int32_t* ncand) {
   p->last_ncand = n;
   p->detected = true;
   p->detected_branch = p->branch;
-  p->detected_units = U;
-  *ncand = n;
+  p->detected_units = p->pushed - 2;
+  if (ncand) *ncand = n;
   if (flags & kErrTimeout) return FITRIG_ETIMEOUT;
   if (flags & (kErrCapacity | kErrCcLimit)) return FITRIG_ETRUNC;
   if (invalid) return FITRIG_ENONFINITE;
   return FITRIG_OK;
+}
+
+static int detect_ready(fitrig_plan_t p) {
+  if (p->pushed < 3) return FITRIG_ESTATE;
+  if ((p->branch & FITRIG_BRANCH_FREQ) && p->pushed != p->L) return FITRIG_ESTATE;
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_detect(fitrig_plan_t p, int32_t* ncand) {
+  if (!p || !ncand) return FITRIG_EINVAL;
+  *ncand = 0;
+  int rc = detect_ready(p);
+  if (rc != FITRIG_OK) return rc;
+  CK(cudaSetDevice(p->device));
+  cudaStream_t st = plan_stream(p);
+  CK(enqueue_clear(p, st));
+  rec(p, FITRIG_KERNEL_DETECT, 0, st);
+  rec(p, FITRIG_KERNEL_STACK, 0, st);
+  CK(enqueue_march(p, st));
+  rec(p, FITRIG_KERNEL_STACK, 1, st);
+  CK(enqueue_post(p, st, true));
+  rec(p, FITRIG_KERNEL_DETECT, 1, st);
+  CK(cudaStreamSynchronize(st));
+  for (int k = 0; k < FITRIG_KERNEL_COUNT; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev[2 * k], p->ev[2 * k + 1]) == cudaSuccess) p->ms[k] = ms;
+    else (void)cudaGetLastError();
+  }
+  return finish_detect(p, ncand);
+}
+
+// ---------------------------------------------------------------- batches
+struct fitrig_batch_s {
+  std::vector<fitrig_plan_t> plans;   // in work order (largest first)
+  std::vector<int> order;             // plans[k] is the caller's plan order[k]
+  FieldDesc* d_fields = nullptr;
+  unsigned long long* d_counter = nullptr;
+  int64_t nitems = 0;
+  bool multi = false;                 // one persistent march for every plan
+  StackGeom geom{};
+  int grid = 0;
+  int storage = 0, rmode = 0;
+  uint64_t timeout_ns = 0;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int device = 0;
+  float last_ms = 0.f;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+static cudaError_t enqueue_batch(fitrig_batch_t b, cudaStream_t st) {
+  for (fitrig_plan_t p : b->plans) CKE(enqueue_clear(p, st));
+  if (b->multi) {
+    CKE(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), st));
+    CKE(launch_stack_multi(b->d_fields, (int)b->plans.size(), b->nitems, b->d_counter, b->geom,
+                           b->grid, b->storage, b->rmode, b->timeout_ns, st));
+  } else {
+    for (fitrig_plan_t p : b->plans) CKE(enqueue_march(p, st));
+  }
+  for (fitrig_plan_t p : b->plans) CKE(enqueue_post(p, st, false));
+  return cudaSuccess;
 }
 
 FITRIG_API int fitrig_candidates(fitrig_plan_t p, fitrig_candidate* out, int32_t cap,
@@ -541,7 +776,7 @@ FITRIG_API int fitrig_unit_values(fitrig_plan_t p, int32_t unit, float* out, int
   if (!p->detected) return FITRIG_ESTATE;
   if (unit < 0 || unit >= p->detected_units) return FITRIG_EINVAL;
   CK(cudaSetDevice(p->device));
-  return read_floats(p, p->d_vp + (size_t)unit * p->T, p->T, out, cap);
+  return read_floats(p, p->d_vp + (size_t)unit * p->vstride, p->T, out, cap);
 }
 
 static int resolve_max(fitrig_plan_t p, double* M) {
@@ -581,8 +816,9 @@ FITRIG_API int fitrig_tlisi(fitrig_plan_t p, int32_t unit, float* out, int32_t c
   int rc = resolve_max(p, &M);
   if (rc != FITRIG_OK) return rc;
   cudaStream_t st = plan_stream(p);
-  if (!p->d_report) CK(cudaMalloc(&p->d_report, sizeof(float) * p->T));
-  CK(launch_tlisi_from_values(p->d_vp + (size_t)unit * p->T, p->T, p->d_small, p->d_report, st));
+  if (!p->d_report) CK(dmalloc(p, &p->d_report, sizeof(float) * p->T));
+  CK(launch_tlisi_from_values(p->d_vp + (size_t)unit * p->vstride, p->T, p->d_small, p->d_report,
+                              st));
   return read_floats(p, p->d_report, p->T, out, cap);
 }
 
@@ -656,7 +892,7 @@ FITRIG_API int fitrig_threshold_map(const float* dev_map, int64_t n, double nsig
   const int nblk = 152 * 4;
   void* scratch = nullptr;
   const size_t nb = (noise_scratch_bytes(1, nblk) + 255) / 256 * 256;   // keeps the tail 8-byte aligned
-  const size_t extra = 256 + sizeof(int) * (nblk + 2) + sizeof(long long) * 2 + 64;
+  const size_t extra = 256 + sizeof(int) * (nblk * 8 + 2) + sizeof(long long) * 2 + 64;
   CK(cudaMalloc(&scratch, nb + extra));
   NoiseScratch ns;
   noise_scratch_carve(scratch, 1, nblk, &ns);
@@ -665,14 +901,15 @@ FITRIG_API int fitrig_threshold_map(const float* dev_map, int64_t n, double nsig
   float* thr = reinterpret_cast<float*>(tail + 16);
   unsigned long long* inval = reinterpret_cast<unsigned long long*>(tail + 32);
   long long* total = reinterpret_cast<long long*>(tail + 48);
+  double* inv = reinterpret_cast<double*>(tail + 56);
   int* blkcnt = reinterpret_cast<int*>(tail + 64);
   ns.invalid = inval;
   int rc = FITRIG_OK;
   double h[2] = {0, 0};
   long long cnt = 0;
   cudaError_t e = cudaMemsetAsync(inval, 0, 8, st);
-  if (e == cudaSuccess) e = launch_noise(dev_map, 1, n, noise_mode, ns, cs, st);
-  if (e == cudaSuccess) e = launch_thresholds(cs, 1, nsigma, thr, st);
+  if (e == cudaSuccess) e = launch_noise(dev_map, 1, n, n, noise_mode, ns, cs, st);
+  if (e == cudaSuccess) e = launch_thresholds(cs, 1, nsigma, thr, inv, st);
   if (e == cudaSuccess) e = launch_count_selected(dev_map, 1, n, thr, nblk, blkcnt, total, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, cs, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, total, sizeof(cnt), cudaMemcpyDeviceToHost, st);
@@ -686,6 +923,501 @@ FITRIG_API int fitrig_threshold_map(const float* dev_map, int64_t n, double nsig
   *nexceed = cnt;
   if (centre) *centre = h[0];
   if (scale) *scale = h[1];
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_autotune(int window, int storage, int32_t* tile_rows, int32_t* stages,
+                               float* best_ms) {
+  if (!tile_rows || !stages || !best_ms) return FITRIG_EINVAL;
+  if (storage != FITRIG_F32 && storage != FITRIG_BF16 && storage != FITRIG_F16) return FITRIG_EINVAL;
+  if (window < 3 || window > 6) return FITRIG_EUNSUPPORTED;
+  int tby = 0, ns = 0;
+  const int rc = tuned_shape(window, storage, &tby, &ns);
+  if (rc != FITRIG_OK) return rc;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  *tile_rows = tby;
+  *stages = ns;
+  *best_ms = g_tuned[{window, storage}].second;
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_batch_create(const fitrig_plan_t* plans, int32_t nplans,
+                                   fitrig_batch_t* out) {
+  if (!plans || nplans < 1 || !out) return FITRIG_EINVAL;
+  *out = nullptr;
+  fitrig_plan_t p0 = plans[0];
+  for (int i = 0; i < nplans; ++i) {
+    fitrig_plan_t p = plans[i];
+    if (!p) return FITRIG_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == p) return FITRIG_EINVAL;   // a plan may appear once
+    const int rc = detect_ready(p);
+    if (rc != FITRIG_OK) return rc;
+    if (!p->allocated || p->device != p0->device) return FITRIG_ESTATE;
+  }
+  fitrig_batch_t b = new (std::nothrow) fitrig_batch_s();
+  if (!b) return FITRIG_ENOMEM;
+  b->device = p0->device;
+  b->stream = plan_stream(p0);
+  b->storage = p0->storage;
+  b->rmode = p0->rmode;
+  b->timeout_ns = p0->timeout_ns;
+  // largest fields first, so the persistent march ends evenly
+  std::vector<int> idx(nplans);
+  for (int i = 0; i < nplans; ++i) idx[i] = i;
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+    return (double)plans[x]->pushed * plans[x]->T > (double)plans[y]->pushed * plans[y]->T;
+  });
+  for (int i : idx) {
+    b->plans.push_back(plans[i]);
+    b->order.push_back(i);
+  }
+  // one persistent launch needs the same thread-per-tile march for all
+  b->multi = true;
+  for (fitrig_plan_t p : b->plans)
+    if (p->stride != FITRIG_STRIDE_TILE || p->geom.R != 0 || p->w != p0->w ||
+        p->storage != p0->storage || p->rmode != p0->rmode || p->geom.TBY != p0->geom.TBY ||
+        p->geom.stages != p0->geom.stages)
+      b->multi = false;
+  cudaSetDevice(b->device);
+  if (b->multi) {
+    b->geom = p0->geom;
+    std::vector<FieldDesc> fd(b->plans.size());
+    int64_t items = 0;
+    for (size_t k = 0; k < b->plans.size(); ++k) {
+      fitrig_plan_t p = b->plans[k];
+      FieldDesc& d = fd[k];
+      memset(&d, 0, sizeof(d));
+      d.tmap = p->tmap;
+      d.zrot = 0;
+      d.vp = p->d_vp;
+      d.arg = p->d_arg;
+      d.gmax = p->d_small;
+      d.status = p->d_small + 1;
+      d.nx = p->nxu;
+      d.ny = p->nyu;
+      d.L = p->pushed;
+      d.Tx = p->Tx;
+      d.Ty = p->Ty;
+      d.gridX = p->geom.gridX;
+      d.vstride = p->vstride;
+      d.item0 = items;
+      items += (int64_t)p->geom.gridX * p->geom.gridY;
+    }
+    b->nitems = items;
+    const int per_sm = multi_blocks_per_sm(b->geom, b->storage, b->rmode);
+    b->grid = 152 * std::max(1, per_sm);
+    if (cudaMalloc(&b->d_fields, sizeof(FieldDesc) * fd.size()) != cudaSuccess ||
+        cudaMalloc(&b->d_counter, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemcpy(b->d_fields, fd.data(), sizeof(FieldDesc) * fd.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      (void)cudaGetLastError();
+      fitrig_batch_destroy(b);
+      return FITRIG_ENOMEM;
+    }
+  }
+  if (cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    fitrig_batch_destroy(b);
+    return FITRIG_ECUDA;
+  }
+  *out = b;
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_batch_detect(fitrig_batch_t b, int32_t* ncand) {
+  if (!b || !ncand) return FITRIG_EINVAL;
+  CK(cudaSetDevice(b->device));
+  cudaStream_t st = b->stream;
+  for (fitrig_plan_t p : b->plans) {
+    const int rc = detect_ready(p);
+    if (rc != FITRIG_OK) return rc;
+  }
+  if (!b->exec) {
+    // one eager pass (sets kernel attributes and checks every launch), then
+    // capture the same stream work once
+    CK(enqueue_batch(b, st));
+    CK(cudaStreamSynchronize(st));
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t e = enqueue_batch(b, st);
+    const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      (void)cudaGetLastError();
+      return FITRIG_ECUDA;
+    }
+    const cudaError_t e3 = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) {
+      b->exec = nullptr;
+      (void)cudaGetLastError();
+      return FITRIG_ECUDA;
+    }
+  }
+  CK(cudaEventRecord(b->ev0, st));
+  CK(cudaGraphLaunch(b->exec, st));
+  CK(cudaEventRecord(b->ev1, st));
+  CK(cudaStreamSynchronize(st));
+  cudaEventElapsedTime(&b->last_ms, b->ev0, b->ev1);
+  int worst = FITRIG_OK;
+  for (size_t k = 0; k < b->plans.size(); ++k) {
+    int32_t n = 0;
+    const int rc = finish_detect(b->plans[k], &n);
+    ncand[b->order[k]] = n;
+    if (rc != FITRIG_OK && (worst == FITRIG_OK || worst == FITRIG_ENONFINITE)) worst = rc;
+  }
+  return worst;
+}
+
+FITRIG_API int fitrig_batch_ms(fitrig_batch_t b, float* ms) {
+  if (!b || !ms) return FITRIG_EINVAL;
+  *ms = b->last_ms;
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_batch_destroy(fitrig_batch_t b) {
+  if (!b) return FITRIG_EINVAL;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->d_fields) cudaFree(b->d_fields);
+  if (b->d_counter) cudaFree(b->d_counter);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  delete b;
+  return FITRIG_OK;
+}
+
+// ---------------------------------------------------------------- serving
+// A server owns fields that stream snapshots.  Each active field is a plan
+// whose stack is a ring of three slots: the latest three snapshots stay on the
+// device, and every arriving snapshot completes one unit, whose trigger runs
+// on the field's own stream right away.  Fields overlap on the GPU through
+// their streams; admission reserves each field's device bytes against the
+// budget, and fields that do not fit wait in FIFO order until retirements free
+// enough memory.  Results are collected in stream order by a host callback
+// that stamps the completion time.
+namespace {
+
+int64_t monotonic_ns() {
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return (int64_t)ts.tv_sec * 1000000000ll + ts.tv_nsec;
+}
+
+enum { kFieldQueued = 0, kFieldActive = 1, kFieldRetired = 2 };
+
+struct ServerField {
+  int id = 0;
+  int state = kFieldQueued;
+  int nx = 0, ny = 0, w = 0, storage = 0, noise = 0;
+  double tau = 0.0;
+  fitrig_plan_t plan = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t copied = nullptr;
+  int64_t received = 0;             // snapshots pushed so far
+  int64_t bytes = 0;                // device bytes reserved
+  fitrig_candidate* h_cands = nullptr;   // mapped pinned host buffer
+  fitrig_candidate* d_cands = nullptr;   // its device alias
+  int32_t cand_cap = 0;
+};
+
+struct ServerResult {
+  fitrig_result r;
+  std::vector<fitrig_candidate> cands;
+};
+
+}  // namespace
+
+struct fitrig_server_s {
+  int64_t budget = 0, used = 0;
+  int max_fields = 0;
+  int device = 0;
+  std::mutex mtx;                     // fields, admission, enqueue
+  std::vector<ServerField*> fields;   // index = field id
+  std::deque<int> waiting;            // FIFO of queued field ids
+  int active = 0;
+  std::mutex rmtx;                    // results only (never held across CUDA calls)
+  std::deque<ServerResult> results;
+};
+
+namespace {
+
+struct UnitTicket {
+  fitrig_server_s* srv;
+  ServerField* f;
+  int32_t unit;
+  int64_t t_arrival;
+};
+
+constexpr int32_t kServeCandCap = 1 << 16;
+
+// Host callback, in stream order after a unit's trigger and export.
+void CUDART_CB unit_done(void* arg) {
+  UnitTicket* t = static_cast<UnitTicket*>(arg);
+  ServerField* f = t->f;
+  fitrig_plan_t p = f->plan;
+  ServerResult res;
+  res.r.field = f->id;
+  res.r.unit = t->unit;
+  const unsigned flags = p->h_pinned[1];
+  const int n = (int)p->h_pinned[2];
+  unsigned long long invalid;
+  memcpy(&invalid, p->h_pinned + 4, 8);
+  res.r.ncand = n;
+  res.r.status = (flags & kErrTimeout) ? FITRIG_ETIMEOUT
+                 : (flags & (kErrCapacity | kErrCcLimit)) || n > f->cand_cap ? FITRIG_ETRUNC
+                 : invalid ? FITRIG_ENONFINITE : FITRIG_OK;
+  const int m = std::min(n, f->cand_cap);
+  res.cands.assign(f->h_cands, f->h_cands + m);
+  for (auto& c : res.cands) c.snapshot = t->unit;   // absolute unit index
+  res.r.ncand = m;
+  res.r.t_arrival_ns = t->t_arrival;
+  res.r.t_done_ns = monotonic_ns();
+  res.r.cand_offset = 0;
+  {
+    std::lock_guard<std::mutex> lk(t->srv->rmtx);
+    t->srv->results.push_back(std::move(res));
+  }
+  delete t;
+}
+
+void free_field(ServerField* f) {
+  if (f->plan) fitrig_plan_destroy(f->plan);
+  f->plan = nullptr;
+  if (f->h_cands) cudaFreeHost(f->h_cands);
+  f->h_cands = nullptr;
+  if (f->copied) cudaEventDestroy(f->copied);
+  f->copied = nullptr;
+}
+
+// Creates the field's plan and buffers; FITRIG_EBUSY if it does not fit.
+int activate(fitrig_server_s* s, ServerField* f) {
+  fitrig_plan_t p = nullptr;
+  int rc = fitrig_plan_create(f->nx, f->ny, 3, f->w, f->tau, FITRIG_BRANCH_IMAGE, &p);
+  if (rc != FITRIG_OK) return rc;
+  if ((rc = fitrig_plan_set(p, FITRIG_OPT_STORAGE, f->storage)) != FITRIG_OK ||
+      (rc = fitrig_plan_set(p, FITRIG_OPT_NOISE, f->noise)) != FITRIG_OK) {
+    fitrig_plan_destroy(p);
+    return rc;
+  }
+  p->ring = true;
+  rc = ensure_allocated(p);
+  const int64_t need = p->bytes;
+  if (rc != FITRIG_OK || s->used + need > s->budget) {
+    fitrig_plan_destroy(p);
+    return rc != FITRIG_OK && rc != FITRIG_ENOMEM ? rc : FITRIG_EBUSY;
+  }
+  f->plan = p;
+  f->stream = plan_stream(p);
+  f->cand_cap = kServeCandCap;
+  if (cudaHostAlloc(&f->h_cands, sizeof(fitrig_candidate) * f->cand_cap, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(&f->d_cands, f->h_cands, 0) != cudaSuccess ||
+      cudaEventCreateWithFlags(&f->copied, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMemsetAsync(p->d_small, 0, 16, f->stream) != cudaSuccess) {
+    (void)cudaGetLastError();
+    free_field(f);
+    return FITRIG_ENOMEM;
+  }
+  f->bytes = need;
+  s->used += need;
+  f->state = kFieldActive;
+  ++s->active;
+  return FITRIG_OK;
+}
+
+// Activates waiting fields in FIFO order while they fit.
+void admit_waiting(fitrig_server_s* s) {
+  while (!s->waiting.empty() && s->active < s->max_fields) {
+    ServerField* f = s->fields[s->waiting.front()];
+    if (activate(s, f) != FITRIG_OK) break;
+    s->waiting.pop_front();
+  }
+}
+
+}  // namespace
+
+FITRIG_API int fitrig_server_create(int64_t hbm_budget_bytes, int max_fields, fitrig_server_t* out) {
+  if (!out || hbm_budget_bytes <= 0 || max_fields < 1) return FITRIG_EINVAL;
+  *out = nullptr;
+  fitrig_server_t s = new (std::nothrow) fitrig_server_s();
+  if (!s) return FITRIG_ENOMEM;
+  s->budget = hbm_budget_bytes;
+  s->max_fields = max_fields;
+  cudaGetDevice(&s->device);
+  *out = s;
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_server_admit(fitrig_server_t s, int nx, int ny, int window, double nsigma,
+                                   int storage, int noise, int32_t* field_id) {
+  if (!s || !field_id) return FITRIG_EINVAL;
+  if (nx < 1 || ny < 1 || window < 1 || window > std::min(nx, ny) || !(nsigma > 0.0)) return FITRIG_EINVAL;
+  if (storage != FITRIG_F32 && storage != FITRIG_BF16 && storage != FITRIG_F16) return FITRIG_EINVAL;
+  if (noise != FITRIG_NOISE_MEANSTD && noise != FITRIG_NOISE_MEDMAD) return FITRIG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mtx);
+  CK(cudaSetDevice(s->device));
+  ServerField* f = new (std::nothrow) ServerField();
+  if (!f) return FITRIG_ENOMEM;
+  f->id = (int)s->fields.size();
+  f->nx = nx;
+  f->ny = ny;
+  f->w = window;
+  f->tau = nsigma;
+  f->storage = storage;
+  f->noise = noise;
+  s->fields.push_back(f);
+  *field_id = f->id;
+  int rc = FITRIG_EBUSY;
+  if (s->waiting.empty() && s->active < s->max_fields) rc = activate(s, f);
+  if (rc == FITRIG_EBUSY) {
+    s->waiting.push_back(f->id);
+    return FITRIG_EBUSY;   // queued: becomes active when memory frees
+  }
+  if (rc != FITRIG_OK) {
+    f->state = kFieldRetired;
+    return rc;
+  }
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_server_field_state(fitrig_server_t s, int32_t field, int32_t* state) {
+  if (!s || !state) return FITRIG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mtx);
+  if (field < 0 || field >= (int)s->fields.size()) return FITRIG_EINVAL;
+  *state = s->fields[field]->state;
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_server_push(fitrig_server_t s, int32_t field, const void* data, int dtype,
+                                  int64_t t_arrival_ns) {
+  if (!s || !data) return FITRIG_EINVAL;
+  if (dtype != FITRIG_F32 && dtype != FITRIG_BF16 && dtype != FITRIG_F16) return FITRIG_EINVAL;
+  cudaEvent_t copied = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(s->mtx);
+    if (field < 0 || field >= (int)s->fields.size()) return FITRIG_EINVAL;
+    ServerField* f = s->fields[field];
+    if (f->state == kFieldQueued) return FITRIG_EBUSY;
+    if (f->state != kFieldActive) return FITRIG_ESTATE;
+    CK(cudaSetDevice(s->device));
+    fitrig_plan_t p = f->plan;
+    cudaStream_t st = f->stream;
+    const int slot = (int)(f->received % 3);
+    const int eb = elem_bytes(p->storage), ib = elem_bytes(dtype);
+    char* dst = p->d_stack + p->slice_bytes * slot;
+    if (dtype == p->storage) {
+      CK(cudaMemcpy2DAsync(dst, p->pitch * eb, data, (size_t)p->nx * ib, (size_t)p->nx * ib, p->ny,
+                           cudaMemcpyDefault, st));
+    } else {
+      if (!p->d_staging) CK(dmalloc(p, &p->d_staging, (size_t)p->nx * p->ny * 4));
+      CK(cudaMemcpyAsync(p->d_staging, data, (size_t)p->nx * p->ny * ib, cudaMemcpyDefault, st));
+      CK(launch_convert(p->d_staging, dtype, p->nx, dst, p->storage, p->pitch, p->ny, p->nx, st));
+    }
+    CK(cudaEventRecord(f->copied, st));
+    copied = f->copied;
+    f->received += 1;
+    if (f->received >= 3) {
+      // the unit whose last snapshot just arrived
+      p->pushed = 3;
+      p->zrot = (int)((f->received - 3) % 3);
+      CK(enqueue_clear(p, st));
+      CK(enqueue_march(p, st));
+      CK(enqueue_post(p, st, false));
+      CK(launch_export_candidates(p->d_cand, reinterpret_cast<int*>(p->d_small + 2), f->d_cands,
+                                  f->cand_cap, st));
+      UnitTicket* t = new (std::nothrow) UnitTicket{s, f, (int32_t)(f->received - 3), t_arrival_ns};
+      if (!t) return FITRIG_ENOMEM;
+      CK(cudaLaunchHostFunc(st, unit_done, t));
+    }
+  }
+  // the caller's buffer is free once the copy is done
+  CK(cudaEventSynchronize(copied));
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_server_poll(fitrig_server_t s, fitrig_result* out, int32_t cap,
+                                  fitrig_candidate* cands, int32_t cand_cap, int32_t* n,
+                                  int32_t* ncands) {
+  if (!s || !n || !ncands || cap < 0 || cand_cap < 0) return FITRIG_EINVAL;
+  *n = 0;
+  *ncands = 0;
+  std::lock_guard<std::mutex> lk(s->rmtx);
+  int32_t k = 0, c = 0;
+  while (!s->results.empty() && k < cap) {
+    ServerResult& r = s->results.front();
+    if (c + (int32_t)r.cands.size() > cand_cap) break;
+    r.r.cand_offset = c;
+    out[k++] = r.r;
+    if (!r.cands.empty()) memcpy(cands + c, r.cands.data(), sizeof(fitrig_candidate) * r.cands.size());
+    c += (int32_t)r.cands.size();
+    s->results.pop_front();
+  }
+  *n = k;
+  *ncands = c;
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_server_drain(fitrig_server_t s) {
+  if (!s) return FITRIG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mtx);
+  for (ServerField* f : s->fields)
+    if (f->state == kFieldActive) CK(cudaStreamSynchronize(f->stream));
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_server_retire(fitrig_server_t s, int32_t field) {
+  if (!s) return FITRIG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mtx);
+  if (field < 0 || field >= (int)s->fields.size()) return FITRIG_EINVAL;
+  ServerField* f = s->fields[field];
+  if (f->state == kFieldQueued) {
+    for (auto it = s->waiting.begin(); it != s->waiting.end(); ++it)
+      if (*it == field) {
+        s->waiting.erase(it);
+        break;
+      }
+    f->state = kFieldRetired;
+    return FITRIG_OK;
+  }
+  if (f->state != kFieldActive) return FITRIG_ESTATE;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(f->stream);   // its pending results are delivered
+  free_field(f);
+  s->used -= f->bytes;
+  f->bytes = 0;
+  f->state = kFieldRetired;
+  --s->active;
+  admit_waiting(s);
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_server_usage(fitrig_server_t s, int64_t* used_bytes, int32_t* active,
+                                   int32_t* waiting) {
+  if (!s || !used_bytes || !active || !waiting) return FITRIG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mtx);
+  *used_bytes = s->used;
+  *active = s->active;
+  *waiting = (int32_t)s->waiting.size();
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_server_destroy(fitrig_server_t s) {
+  if (!s) return FITRIG_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mtx);
+    cudaSetDevice(s->device);
+    for (ServerField* f : s->fields) {
+      if (f->state == kFieldActive) {
+        cudaStreamSynchronize(f->stream);
+        free_field(f);
+      }
+      delete f;
+    }
+    s->fields.clear();
+  }
+  delete s;
   return FITRIG_OK;
 }
 

@@ -23,6 +23,7 @@ OK, EINVAL, ENOMEM, ESTATE, ECUDA, ETIMEOUT, ETRUNC, ENONFINITE, EBUSY, EUNSUPPO
 BRANCH_IMAGE, BRANCH_FREQ, BRANCH_BOTH = 1, 2, 3
 F32, BF16, F16 = 0, 1, 2
 OPT_STORAGE, OPT_NOISE, OPT_RMODE, OPT_EDGE, OPT_STRIDE, OPT_STREAM, OPT_TIMEOUT_NS = 1, 2, 3, 5, 6, 8, 9
+OPT_AUTOTUNE = 10
 NOISE_MEANSTD, NOISE_MEDMAD = 0, 1
 RMODE_ABS, RMODE_SIGNED = 0, 1
 EDGE_PARTIAL, EDGE_DROP = 0, 1
@@ -38,6 +39,15 @@ class Candidate(ctypes.Structure):
                 ("significance", c_float), ("branch", c_int32), ("freq_bin", c_int32),
                 ("xf", c_float), ("yf", c_float)]
 
+
+class Result(ctypes.Structure):
+    _fields_ = [("field", c_int32), ("unit", c_int32), ("ncand", c_int32), ("status", c_int32),
+                ("t_arrival_ns", c_int64), ("t_done_ns", c_int64), ("cand_offset", c_int64)]
+
+
+RESULT_DTYPE = np.dtype([("field", np.int32), ("unit", np.int32), ("ncand", np.int32),
+                         ("status", np.int32), ("t_arrival_ns", np.int64),
+                         ("t_done_ns", np.int64), ("cand_offset", np.int64)])
 
 CANDIDATE_DTYPE = np.dtype([("x", np.int32), ("y", np.int32), ("snapshot", np.int32),
                             ("significance", np.float32), ("branch", np.int32),
@@ -90,6 +100,20 @@ def load(path: Optional[str] = None):
         "fitrig_threshold_map": (c_int, [P, c_int64, c_double, c_int, c_int64,
                                          POINTER(c_int64), POINTER(c_double), POINTER(c_double)]),
         "fitrig_launch_count": (c_int, [POINTER(c_int64)]),
+        "fitrig_batch_create": (c_int, [POINTER(P), c_int32, POINTER(P)]),
+        "fitrig_server_create": (c_int, [c_int64, c_int, POINTER(P)]),
+        "fitrig_server_admit": (c_int, [P, c_int, c_int, c_int, c_double, c_int, c_int, POINTER(c_int32)]),
+        "fitrig_server_push": (c_int, [P, c_int32, P, c_int, c_int64]),
+        "fitrig_server_poll": (c_int, [P, P, c_int32, P, c_int32, POINTER(c_int32), POINTER(c_int32)]),
+        "fitrig_server_drain": (c_int, [P]),
+        "fitrig_server_retire": (c_int, [P, c_int32]),
+        "fitrig_server_field_state": (c_int, [P, c_int32, POINTER(c_int32)]),
+        "fitrig_server_usage": (c_int, [P, POINTER(c_int64), POINTER(c_int32), POINTER(c_int32)]),
+        "fitrig_server_destroy": (c_int, [P]),
+        "fitrig_batch_detect": (c_int, [P, POINTER(c_int32)]),
+        "fitrig_batch_ms": (c_int, [P, POINTER(c_float)]),
+        "fitrig_batch_destroy": (c_int, [P]),
+        "fitrig_autotune": (c_int, [c_int, c_int, POINTER(c_int32), POINTER(c_int32), POINTER(c_float)]),
         "fitrig_plan_destroy": (c_int, [P]),
     }
     for name, (res, args) in sig.items():
@@ -245,6 +269,13 @@ def fitrig_threshold_map(dev_map, nsigma: float, noise_mode: int = NOISE_MEANSTD
     return n.value, c.value, s.value
 
 
+def fitrig_autotune(window: int, storage: int = F32) -> Tuple[int, int, float]:
+    """(tile rows per CTA, ring depth, ms per probe launch) chosen for the window."""
+    a, b, ms = c_int32(), c_int32(), c_float()
+    _check(load().fitrig_autotune(window, storage, byref(a), byref(b), byref(ms)), "fitrig_autotune")
+    return a.value, b.value, ms.value
+
+
 def fitrig_launch_count() -> int:
     n = c_int64()
     _check(load().fitrig_launch_count(byref(n)), "fitrig_launch_count")
@@ -261,9 +292,11 @@ class Plan:
 
     def __init__(self, nx, ny, nsnap, window, nsigma, branch=BRANCH_IMAGE, storage=F32,
                  noise=NOISE_MEANSTD, rmode=RMODE_ABS, edge=EDGE_PARTIAL, stream=None,
-                 stride=STRIDE_TILE):
+                 stride=STRIDE_TILE, autotune=False):
         self.h = fitrig_plan_create(nx, ny, nsnap, window, nsigma, branch)
         try:
+            if autotune:
+                fitrig_plan_set(self.h, OPT_AUTOTUNE, 1)
             if stride != STRIDE_TILE:
                 fitrig_plan_set(self.h, OPT_STRIDE, stride)
             fitrig_plan_set(self.h, OPT_STORAGE, storage)
@@ -311,11 +344,11 @@ class Plan:
 def detect_stack(stack, window: int, nsigma: float, branch: int = BRANCH_IMAGE,
                  storage: int = F32, noise: int = NOISE_MEANSTD, rmode: int = RMODE_ABS,
                  edge: int = EDGE_PARTIAL, dumps: bool = True,
-                 stride: int = STRIDE_TILE) -> dict:
+                 stride: int = STRIDE_TILE, autotune: bool = False) -> dict:
     """Push an (L, ny, nx) stack, detect, and read back candidates and dumps."""
     L, ny, nx = (int(d) for d in stack.shape)
     with Plan(nx, ny, L, window, nsigma, branch, storage, noise, rmode, edge,
-              stride=stride) as p:
+              stride=stride, autotune=autotune) as p:
         p.push_stack(stack)
         rc, cands = p.detect()
         out = {"status": rc, "candidates": cands}

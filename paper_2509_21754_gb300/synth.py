@@ -69,6 +69,11 @@ C2 = StackSpec(nsnap=64, ny=4096, nx=4096, layout="meerkat_like", n_ant=64,
                n_pulsed=10, pulse_amp=None, pulse_period=(3, 16))
 
 
+C3 = StackSpec(nsnap=8, ny=50000, nx=50000, layout="meerkat_like", n_ant=64,
+               n_steady=10000, steady_lo=5, steady_hi=500, steady_dist="loguniform",
+               n_pulsed=50, pulse_amp=None, pulse_period=(3, 16))
+
+
 def small_spec(nsnap: int, ny: int, nx: int, **kw) -> StackSpec:
     """A C2-like field of arbitrary size with source counts scaled by area."""
     area = ny * nx / float(4096 * 4096)
@@ -175,6 +180,46 @@ def draw_sources(spec: StackSpec, seed: int) -> Truth:
     return Truth(steady=steady, pulsed=pulsed)
 
 
+def beam_transfer(kind: str, n_ant: int, ny: int, nx: int, seed: int, fwhm_px: float = 2.0,
+                  umax: float = 0.45, device: str = "cpu") -> Tuple[torch.Tensor, float]:
+    """The dirty beam's transfer function on the rfft half-plane and ||psf||_2.
+
+    The tapered uv grid G is real and symmetric (both signs of every baseline),
+    so the beam psf = ifft2(G) / psf[0,0] has rfft2(psf) = G / psf[0,0] with
+    psf[0,0] = sum(G) / (nx ny); no transform of the beam is needed, which
+    keeps very large fields cheap.  Same beam as :func:`dirty_beam`.
+    """
+    pos = antenna_layout(kind, n_ant, seed)
+    b = (pos[:, None, :] - pos[None, :, :]).reshape(-1, 2)
+    b = b[np.any(b != 0.0, axis=1)]
+    b = b * (umax / np.max(np.hypot(b[:, 0], b[:, 1])))
+    iu = np.rint(b[:, 0] * nx).astype(np.int64) % nx
+    iv = np.rint(b[:, 1] * ny).astype(np.int64) % ny
+    half = nx // 2 + 1
+    keep = iu < half
+    dev = torch.device(device)
+    grid = torch.zeros(ny, half, dtype=torch.float64, device=dev)
+    idx_v = torch.from_numpy(iv[keep]).to(dev)
+    idx_u = torch.from_numpy(iu[keep]).to(dev)
+    grid.index_put_((idx_v, idx_u), torch.ones(idx_v.numel(), dtype=torch.float64, device=dev),
+                    accumulate=True)
+    sig_u = 1.0 / (2 * np.pi * fwhm_px * FWHM_TO_SIGMA)
+    fu = torch.arange(half, dtype=torch.float64, device=dev) / nx
+    fv = torch.fft.fftfreq(ny, dtype=torch.float64, device=dev)
+    grid *= torch.exp(-(fv[:, None] ** 2) / (2 * sig_u ** 2))
+    grid *= torch.exp(-(fu[None, :] ** 2) / (2 * sig_u ** 2))
+    # weights of the half-plane columns in full-plane sums (Hermitian symmetry)
+    wcol = torch.full((half,), 2.0, dtype=torch.float64, device=dev)
+    wcol[0] = 1.0
+    if nx % 2 == 0:
+        wcol[-1] = 1.0
+    n = float(nx) * float(ny)
+    peak = float((grid * wcol).sum()) / n
+    H = grid / peak
+    norm = float(np.sqrt(float((H * H * wcol).sum()) / n))   # Parseval
+    return H.to(torch.float32), norm
+
+
 def make_stack(spec: StackSpec, seed: int, device: str = "cpu",
                dtype: torch.dtype = torch.float32) -> Tuple[torch.Tensor, Truth]:
     """Synthesize an (nsnap, ny, nx) stack on ``device``.
@@ -183,14 +228,14 @@ def make_stack(spec: StackSpec, seed: int, device: str = "cpu",
     convolution by FFT), so the noise has unit standard deviation and a source
     of amplitude A peaks at A.
     """
-    psf = dirty_beam(spec.layout, spec.n_ant, spec.ny, spec.nx, seed, spec.fwhm_px)
-    norm = float(np.sqrt(np.sum(psf ** 2)))
+    H, norm = beam_transfer(spec.layout, spec.n_ant, spec.ny, spec.nx, seed, spec.fwhm_px,
+                            device=device)
     truth = draw_sources(spec, seed)
     dev = torch.device(device)
-    H = torch.fft.rfft2(torch.from_numpy(psf).to(dev, torch.float64)).to(torch.complex64)
     steady = torch.zeros(spec.ny, spec.nx, dtype=torch.float32, device=dev)
-    for x, y, a in truth.steady:
-        steady[y, x] += a
+    if truth.steady:
+        sx, sy, sa = (torch.tensor(c, device=dev) for c in zip(*truth.steady))
+        steady.index_put_((sy.long(), sx.long()), sa.float(), accumulate=True)
     gen = torch.Generator(device=dev)
     gen.manual_seed(int(seed) * 7919 + 17)
     out = torch.empty(spec.nsnap, spec.ny, spec.nx, dtype=dtype, device=dev)
@@ -199,8 +244,11 @@ def make_stack(spec: StackSpec, seed: int, device: str = "cpu",
         img.mul_(1.0 / norm).add_(steady)
         for x, y, a in truth.pulse_on(k):
             img[y, x] += a
-        conv = torch.fft.irfft2(torch.fft.rfft2(img) * H, s=(spec.ny, spec.nx))
-        out[k].copy_(conv)
+        spec_k = torch.fft.rfft2(img)
+        del img
+        spec_k *= H
+        out[k].copy_(torch.fft.irfft2(spec_k, s=(spec.ny, spec.nx)))
+        del spec_k
     return out, truth
 
 

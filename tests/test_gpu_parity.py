@@ -251,3 +251,16 @@ def test_state_errors():
         p.push_stack(x)
         rc, _ = p.detect()
         assert rc == F.OK
+
+
+@pytest.mark.parametrize("storage", [F.F32, F.BF16])
+def test_autotuned_shape_gives_identical_results(storage):
+    """The autotuner only changes the CTA shape, never a tile's arithmetic."""
+    tby, ns, ms = F.fitrig_autotune(5, storage)
+    assert tby in (2, 4, 8) and 2 <= ns <= 6 and ms > 0
+    stack, _ = synth.make_stack(synth.small_spec(12, 333, 250), seed=37, device="cuda")
+    tdt = torch.float32 if storage == F.F32 else torch.bfloat16
+    a = F.detect_stack(stack.to(tdt), 5, 4.0, F.BRANCH_BOTH, storage=storage)
+    b = F.detect_stack(stack.to(tdt), 5, 4.0, F.BRANCH_BOTH, storage=storage, autotune=True)
+    assert a["values"].tobytes() == b["values"].tobytes()
+    assert a["candidates"].tobytes() == b["candidates"].tobytes()

@@ -202,6 +202,32 @@ FITRIG_API int fitrig_threshold_map(const float* dev_map, int64_t n, double nsig
                                     double* centre, double* scale);
 
 /*
+ * fitrig_noise_static -- the same per-group noise estimate as the trigger uses
+ * (centre and scale of each of `groups` maps of `n` FP32 values, laid out one
+ * after another in device memory; NaN entries are skipped): mean and
+ * population standard deviation (FITRIG_NOISE_MEANSTD) or lower median and
+ * 1.482602218505602 x MAD (FITRIG_NOISE_MEDMAD).  Results go to
+ * dev_centre_scale[2g], [2g+1] (device memory, 2*groups doubles); work is
+ * enqueued on `stream` (a cudaStream_t; 0 = legacy default) and the call does
+ * not wait for it.  The paper has no counterpart of this entry point.
+ *
+ * It allocates nothing.  It is for callers that cannot call cudaMalloc, such
+ * as a real-time trigger loop where an allocation may block or synchronise the
+ * device, or a program whose device memory belongs to another allocator that
+ * forbids raw allocations.  Its working memory is one fixed device array
+ * inside the library (about 0.53 MB, held on every GPU that loads the library
+ * until the process exits), which limits `groups` to
+ * FITRIG_NOISE_STATIC_MAX_GROUPS (EINVAL beyond it) and n to INT32_MAX.
+ * Every call shares that array: calls that overlap on the GPU (for example on
+ * two streams at once) race and must not be issued.  The first call on a
+ * device looks up the array's device address; make that first call before
+ * any stream capture.
+ */
+#define FITRIG_NOISE_STATIC_MAX_GROUPS 64
+FITRIG_API int fitrig_noise_static(const float* dev_values, int32_t groups, int64_t n,
+                                   int noise_mode, double* dev_centre_scale, int64_t stream);
+
+/*
  * Batches: many fields of uneven size and snapshot count in one go.
  *
  * fitrig_batch_create -- group `nplans` plans whose snapshots are all pushed

@@ -100,6 +100,7 @@ def load(path: Optional[str] = None):
         "fitrig_threshold_map": (c_int, [P, c_int64, c_double, c_int, c_int64,
                                          POINTER(c_int64), POINTER(c_double), POINTER(c_double)]),
         "fitrig_launch_count": (c_int, [POINTER(c_int64)]),
+        "fitrig_noise_static": (c_int, [P, c_int32, c_int64, c_int, P, c_int64]),
         "fitrig_batch_create": (c_int, [POINTER(P), c_int32, POINTER(P)]),
         "fitrig_server_create": (c_int, [c_int64, c_int, POINTER(P)]),
         "fitrig_server_admit": (c_int, [P, c_int, c_int, c_int, c_double, c_int, c_int, POINTER(c_int32)]),
@@ -274,6 +275,17 @@ def fitrig_autotune(window: int, storage: int = F32) -> Tuple[int, int, float]:
     a, b, ms = c_int32(), c_int32(), c_float()
     _check(load().fitrig_autotune(window, storage, byref(a), byref(b), byref(ms)), "fitrig_autotune")
     return a.value, b.value, ms.value
+
+
+NOISE_STATIC_MAX_GROUPS = 64
+
+
+def fitrig_noise_static(dev_values, groups: int, n: int, noise_mode: int, dev_out,
+                        stream: int = 0) -> int:
+    """Noise estimate with no allocation: dev_values / dev_out are CUDA tensors
+    (float32 groups*n, float64 2*groups); returns the status code."""
+    return load().fitrig_noise_static(c_void_p(dev_values.data_ptr()), int(groups), int(n),
+                                      int(noise_mode), c_void_p(dev_out.data_ptr()), int(stream))
 
 
 def fitrig_launch_count() -> int:

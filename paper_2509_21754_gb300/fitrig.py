@@ -60,6 +60,47 @@ class FitrigError(RuntimeError):
         super().__init__(f"{where}: {status_string(status)} ({status})")
 
 
+P = c_void_p
+# ctypes signature of every entry point of include/fitrig.h
+SIGNATURES = {
+    "fitrig_version": (c_char_p, []),
+    "fitrig_status_string": (c_char_p, [c_int]),
+    "fitrig_plan_create": (c_int, [c_int, c_int, c_int, c_int, c_double, c_int, POINTER(P)]),
+    "fitrig_plan_set": (c_int, [P, c_int, c_int64]),
+    "fitrig_push_snapshot": (c_int, [P, P, c_int, c_int, c_int64]),
+    "fitrig_plan_reset": (c_int, [P]),
+    "fitrig_detect": (c_int, [P, POINTER(c_int32)]),
+    "fitrig_candidates": (c_int, [P, P, c_int32, POINTER(c_int32)]),
+    "fitrig_tlisi": (c_int, [P, c_int32, P, c_int32]),
+    "fitrig_unit_values": (c_int, [P, c_int32, P, c_int32]),
+    "fitrig_noise_params": (c_int, [P, c_int32, POINTER(c_double), POINTER(c_double)]),
+    "fitrig_spectrum": (c_int, [P, P, P, c_int32]),
+    "fitrig_global_max": (c_int, [P, POINTER(c_double)]),
+    "fitrig_tile_grid": (c_int, [P, POINTER(c_int32), POINTER(c_int32)]),
+    "fitrig_kernel_ms": (c_int, [P, c_int, POINTER(c_float)]),
+    "fitrig_stack_device_ptr": (c_int, [P, c_int32, POINTER(P), POINTER(c_int64)]),
+    "fitrig_threshold_map": (c_int, [P, c_int64, c_double, c_int, c_int64,
+                                     POINTER(c_int64), POINTER(c_double), POINTER(c_double)]),
+    "fitrig_launch_count": (c_int, [POINTER(c_int64)]),
+    "fitrig_batch_create": (c_int, [POINTER(P), c_int32, POINTER(P)]),
+    "fitrig_server_create": (c_int, [c_int64, c_int, POINTER(P)]),
+    "fitrig_server_admit": (c_int, [P, c_int, c_int, c_int, c_double, c_int, c_int, POINTER(c_int32)]),
+    "fitrig_server_push": (c_int, [P, c_int32, P, c_int, c_int64]),
+    "fitrig_server_poll": (c_int, [P, P, c_int32, P, c_int32, POINTER(c_int32), POINTER(c_int32)]),
+    "fitrig_server_drain": (c_int, [P]),
+    "fitrig_server_retire": (c_int, [P, c_int32]),
+    "fitrig_server_field_state": (c_int, [P, c_int32, POINTER(c_int32)]),
+    "fitrig_server_usage": (c_int, [P, POINTER(c_int64), POINTER(c_int32), POINTER(c_int32)]),
+    "fitrig_server_destroy": (c_int, [P]),
+    "fitrig_batch_detect": (c_int, [P, POINTER(c_int32)]),
+    "fitrig_batch_ms": (c_int, [P, POINTER(c_float)]),
+    "fitrig_batch_destroy": (c_int, [P]),
+    "fitrig_autotune": (c_int, [c_int, c_int, POINTER(c_int32), POINTER(c_int32), POINTER(c_float)]),
+    "fitrig_noise_static": (c_int, [P, c_int32, c_int64, c_int, P, c_int64]),
+    "fitrig_plan_destroy": (c_int, [P]),
+}
+
+
 _lib = None
 
 
@@ -79,45 +120,7 @@ def load(path: Optional[str] = None):
         except Exception as e:  # noqa: BLE001
             raise FitrigError(ECUDA, f"libfitrig is not built and could not be built ({e})")
     lib = ctypes.CDLL(p)
-    P = c_void_p
-    sig = {
-        "fitrig_version": (c_char_p, []),
-        "fitrig_status_string": (c_char_p, [c_int]),
-        "fitrig_plan_create": (c_int, [c_int, c_int, c_int, c_int, c_double, c_int, POINTER(P)]),
-        "fitrig_plan_set": (c_int, [P, c_int, c_int64]),
-        "fitrig_push_snapshot": (c_int, [P, P, c_int, c_int, c_int64]),
-        "fitrig_plan_reset": (c_int, [P]),
-        "fitrig_detect": (c_int, [P, POINTER(c_int32)]),
-        "fitrig_candidates": (c_int, [P, P, c_int32, POINTER(c_int32)]),
-        "fitrig_tlisi": (c_int, [P, c_int32, P, c_int32]),
-        "fitrig_unit_values": (c_int, [P, c_int32, P, c_int32]),
-        "fitrig_noise_params": (c_int, [P, c_int32, POINTER(c_double), POINTER(c_double)]),
-        "fitrig_spectrum": (c_int, [P, P, P, c_int32]),
-        "fitrig_global_max": (c_int, [P, POINTER(c_double)]),
-        "fitrig_tile_grid": (c_int, [P, POINTER(c_int32), POINTER(c_int32)]),
-        "fitrig_kernel_ms": (c_int, [P, c_int, POINTER(c_float)]),
-        "fitrig_stack_device_ptr": (c_int, [P, c_int32, POINTER(P), POINTER(c_int64)]),
-        "fitrig_threshold_map": (c_int, [P, c_int64, c_double, c_int, c_int64,
-                                         POINTER(c_int64), POINTER(c_double), POINTER(c_double)]),
-        "fitrig_launch_count": (c_int, [POINTER(c_int64)]),
-        "fitrig_noise_static": (c_int, [P, c_int32, c_int64, c_int, P, c_int64]),
-        "fitrig_batch_create": (c_int, [POINTER(P), c_int32, POINTER(P)]),
-        "fitrig_server_create": (c_int, [c_int64, c_int, POINTER(P)]),
-        "fitrig_server_admit": (c_int, [P, c_int, c_int, c_int, c_double, c_int, c_int, POINTER(c_int32)]),
-        "fitrig_server_push": (c_int, [P, c_int32, P, c_int, c_int64]),
-        "fitrig_server_poll": (c_int, [P, P, c_int32, P, c_int32, POINTER(c_int32), POINTER(c_int32)]),
-        "fitrig_server_drain": (c_int, [P]),
-        "fitrig_server_retire": (c_int, [P, c_int32]),
-        "fitrig_server_field_state": (c_int, [P, c_int32, POINTER(c_int32)]),
-        "fitrig_server_usage": (c_int, [P, POINTER(c_int64), POINTER(c_int32), POINTER(c_int32)]),
-        "fitrig_server_destroy": (c_int, [P]),
-        "fitrig_batch_detect": (c_int, [P, POINTER(c_int32)]),
-        "fitrig_batch_ms": (c_int, [P, POINTER(c_float)]),
-        "fitrig_batch_destroy": (c_int, [P]),
-        "fitrig_autotune": (c_int, [c_int, c_int, POINTER(c_int32), POINTER(c_int32), POINTER(c_float)]),
-        "fitrig_plan_destroy": (c_int, [P]),
-    }
-    for name, (res, args) in sig.items():
+    for name, (res, args) in SIGNATURES.items():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
@@ -159,6 +162,10 @@ def _ptr_dtype(data) -> Tuple[int, int, int, int]:
 # ---------------------------------------------------------------- entry points
 def fitrig_version() -> str:
     return load().fitrig_version().decode()
+
+
+def fitrig_status_string(status: int) -> str:
+    return load().fitrig_status_string(int(status)).decode()
 
 
 def fitrig_plan_create(nx: int, ny: int, nsnap: int, window: int, nsigma: float,
@@ -286,6 +293,94 @@ def fitrig_noise_static(dev_values, groups: int, n: int, noise_mode: int, dev_ou
     (float32 groups*n, float64 2*groups); returns the status code."""
     return load().fitrig_noise_static(c_void_p(dev_values.data_ptr()), int(groups), int(n),
                                       int(noise_mode), c_void_p(dev_out.data_ptr()), int(stream))
+
+
+def fitrig_batch_create(plans) -> c_void_p:
+    """plans: a sequence of plan handles (or Plan objects) with all snapshots pushed."""
+    hs = [p.h if isinstance(p, Plan) else p for p in plans]
+    arr = (c_void_p * len(hs))(*[h.value if isinstance(h, c_void_p) else h for h in hs])
+    b = c_void_p()
+    _check(load().fitrig_batch_create(arr, len(hs), byref(b)), "fitrig_batch_create")
+    return b
+
+
+def fitrig_batch_detect(batch, nplans: int) -> Tuple[int, np.ndarray]:
+    n = (c_int32 * nplans)()
+    rc = load().fitrig_batch_detect(batch, n)
+    _check(rc, "fitrig_batch_detect", allow=SOFT)
+    return rc, np.array(list(n), dtype=np.int32)
+
+
+def fitrig_batch_ms(batch) -> float:
+    ms = c_float()
+    _check(load().fitrig_batch_ms(batch, byref(ms)), "fitrig_batch_ms")
+    return ms.value
+
+
+def fitrig_batch_destroy(batch) -> None:
+    _check(load().fitrig_batch_destroy(batch), "fitrig_batch_destroy")
+
+
+FIELD_QUEUED, FIELD_ACTIVE, FIELD_RETIRED = 0, 1, 2
+
+
+def fitrig_server_create(hbm_budget_bytes: int, max_fields: int) -> c_void_p:
+    h = c_void_p()
+    _check(load().fitrig_server_create(int(hbm_budget_bytes), int(max_fields), byref(h)),
+           "fitrig_server_create")
+    return h
+
+
+def fitrig_server_admit(server, nx, ny, window, nsigma, storage=F32, noise=NOISE_MEANSTD):
+    """Returns (status, field_id); status OK (active) or EBUSY (queued)."""
+    fid = c_int32()
+    rc = load().fitrig_server_admit(server, nx, ny, window, float(nsigma), storage, noise,
+                                    byref(fid))
+    _check(rc, "fitrig_server_admit", allow=(OK, EBUSY))
+    return rc, fid.value
+
+
+def fitrig_server_push(server, field: int, data, t_arrival_ns: int) -> int:
+    """Push one snapshot (2-D tensor or array); returns the status (OK or EBUSY)."""
+    ptr, code, dev, pitch = _ptr_dtype(data)
+    rc = load().fitrig_server_push(server, field, c_void_p(ptr), code, int(t_arrival_ns))
+    _check(rc, "fitrig_server_push", allow=(OK, EBUSY))
+    return rc
+
+
+def fitrig_server_poll(server, cap: int = 4096, cand_cap: int = 1 << 20):
+    """Returns (results, candidates) as structured arrays."""
+    res = np.zeros(max(cap, 1), dtype=RESULT_DTYPE)
+    cands = np.zeros(max(cand_cap, 1), dtype=CANDIDATE_DTYPE)
+    n, nc = c_int32(), c_int32()
+    _check(load().fitrig_server_poll(server, c_void_p(res.ctypes.data), cap,
+                                     c_void_p(cands.ctypes.data), cand_cap, byref(n), byref(nc)),
+           "fitrig_server_poll")
+    return res[:n.value].copy(), cands[:nc.value].copy()
+
+
+def fitrig_server_drain(server) -> None:
+    _check(load().fitrig_server_drain(server), "fitrig_server_drain")
+
+
+def fitrig_server_retire(server, field: int) -> None:
+    _check(load().fitrig_server_retire(server, field), "fitrig_server_retire")
+
+
+def fitrig_server_field_state(server, field: int) -> int:
+    st = c_int32()
+    _check(load().fitrig_server_field_state(server, field, byref(st)), "fitrig_server_field_state")
+    return st.value
+
+
+def fitrig_server_usage(server) -> Tuple[int, int, int]:
+    u, a, w = c_int64(), c_int32(), c_int32()
+    _check(load().fitrig_server_usage(server, byref(u), byref(a), byref(w)), "fitrig_server_usage")
+    return u.value, a.value, w.value
+
+
+def fitrig_server_destroy(server) -> None:
+    _check(load().fitrig_server_destroy(server), "fitrig_server_destroy")
 
 
 def fitrig_launch_count() -> int:

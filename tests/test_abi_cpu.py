@@ -43,6 +43,17 @@ def test_every_declared_symbol_is_exported(lib):
     assert exported == set(declared_symbols())
 
 
+
+def test_binding_wraps_every_declared_symbol():
+    """The Python binding carries a function of the same name, and a ctypes
+    signature, for every entry point of the header."""
+    from paper_2509_21754_gb300 import fitrig as F
+    names = declared_symbols()
+    missing = [n for n in names if not callable(getattr(F, n, None))]
+    assert not missing, missing
+    untyped = [n for n in names if n not in F.SIGNATURES]
+    assert not untyped, untyped
+
 def test_status_strings(lib):
     from paper_2509_21754_gb300 import fitrig as F
     for s in range(10):

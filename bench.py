@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--nsigma", type=float, default=6.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="also run the 256-field batched workload (about a minute)")
     return ap.parse_args()
 
 
@@ -64,7 +67,8 @@ def dist_init(a):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
         dist.init_process_group("nccl" if a.impl == "ours" else "gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
@@ -77,14 +81,19 @@ def barrier(ws):
         dist.barrier()
 
 
-def max_over_ranks(ws, x: float) -> float:
+def max_over_ranks(ws, x: float, device: str = "cuda") -> float:
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(ws: int, px_per_rank: int, ms_max: float) -> float:
+    """Whole-job Gpixel/s: every rank's pixels over the slowest rank's time."""
+    return ws * px_per_rank / (ms_max * 1e-3) / 1e9
 
 
 # ---------------------------------------------------------------- clocks
@@ -243,6 +252,137 @@ def _cuda():
         return False
 
 
+# ---------------------------------------------------------------- serving leg
+def serving_run(a, F, synth, torch, nfields=32, nsnap=24, compression=20.0, seed=7):
+    """C5-like serving: fields stream snapshots (Poisson arrivals, mean 2 s,
+    time-compressed) through the server API; returns latency/throughput."""
+    import threading
+    sides = synth.serving_sides(seed, nfields)
+    pools = []
+    for k, side in enumerate(sides):
+        spec = synth.small_spec(3, side, side)
+        st, _ = synth.make_stack(spec, seed=900 + k, device="cuda")
+        host = torch.empty((3, side, side), dtype=torch.bfloat16, pin_memory=True)
+        host.copy_(st.to(torch.bfloat16))
+        pools.append(host)
+        del st
+    torch.cuda.empty_cache()
+    srv = F.fitrig_server_create(150 << 30, 64)
+    try:
+        ids = []
+        for side in sides:
+            rc, fid = F.fitrig_server_admit(srv, side, side, a.window, a.nsigma, F.BF16,
+                                            F.NOISE_MEDMAD)
+            ids.append((rc, fid))
+        active = [(fid, pools[k]) for k, (rc, fid) in enumerate(ids) if rc == F.OK]
+        mean_gap = 2.0 / compression
+        t0 = time.monotonic() + 0.2
+        pushed = [0]
+        lock = threading.Lock()
+
+        def feed(fid, pool, rs):
+            t = t0
+            for k in range(nsnap):
+                t += rs.exponential(mean_gap)
+                dt = t - time.monotonic()
+                if dt > 0:
+                    time.sleep(dt)
+                F.fitrig_server_push(srv, fid, pool[k % 3], time.monotonic_ns())
+                with lock:
+                    pushed[0] += pool.shape[1] * pool.shape[2]
+
+        threads = [threading.Thread(target=feed, args=(fid, pool, np.random.default_rng(seed + i)))
+                   for i, (fid, pool) in enumerate(active)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
+        F.fitrig_server_drain(srv)
+        t_end = time.monotonic()
+        res, _ = F.fitrig_server_poll(srv, cap=1 << 20, cand_cap=1 << 24)
+        lat = (res["t_done_ns"] - res["t_arrival_ns"]) / 1e6
+        used, nact, nwait = F.fitrig_server_usage(srv)
+        return {
+            "fields": len(sides), "admitted": len(active), "queued": nwait,
+            "snapshots_per_field": nsnap, "units": int(res.size),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()),
+            "gpx_per_s": pushed[0] / (t_end - t0) / 1e9,
+            "compression": compression, "storage": "bf16", "noise": "medmad",
+            "reserved_gb": used / 1e9,
+            "sides": "uniform 2048..16384, seeded",
+        }
+    finally:
+        F.fitrig_server_destroy(srv)
+        del pools
+
+
+# ---------------------------------------------------------------- batched leg
+def batched_run(a, F, synth, torch, wave_bytes=200e9, reps=3, seed=11):
+    """256 fields of uneven size and snapshot count (SKA-AA2-like PSF, BF16
+    storage, both branches): resident in waves of <= 200 GB of plan memory,
+    each wave one fitrig_batch (one persistent stack march, autotuned CTA
+    shape, the whole trigger under one CUDA graph).  Throughput is the pixels
+    of all waves over the sum of their median replay times (device time)."""
+    fields = synth.batched_fields(seed)
+    noise = {"meanstd": F.NOISE_MEANSTD, "medmad": F.NOISE_MEDMAD}[a.noise]
+
+    def plan_bytes(L, side):   # stack + tile statistics, selection lists, maps
+        return 2 * L * side * side * 1.35
+
+    waves, cur, acc = [], [], 0.0
+    for k, (L, side) in enumerate(fields):
+        b = plan_bytes(L, side)
+        if cur and acc + b > wave_bytes:
+            waves.append(cur)
+            cur, acc = [], 0.0
+        cur.append(k)
+        acc += b
+    if cur:
+        waves.append(cur)
+    tot_px, tot_ms, t_gen, per_wave = 0, 0.0, 0.0, []
+    for wave in waves:
+        t0 = time.perf_counter()
+        plans = []
+        try:
+            for k in wave:
+                L, side = fields[k]
+                p = F.Plan(side, side, L, a.window, a.nsigma, F.BRANCH_BOTH, F.BF16, noise,
+                           autotune=True)
+                plans.append(p)
+                for _, snap in synth.iter_stack(synth.batched_spec(L, side), 5000 + k, "cuda"):
+                    F.fitrig_push_snapshot(p.h, snap)   # FP32 in, BF16 on the device
+                    del snap
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            t_gen += time.perf_counter() - t0
+            b = F.fitrig_batch_create(plans)
+            try:
+                F.fitrig_batch_detect(b, len(plans))   # eager run + graph capture
+                ms = []
+                for _ in range(reps):
+                    rc, n = F.fitrig_batch_detect(b, len(plans))
+                    ms.append(F.fitrig_batch_ms(b))
+            finally:
+                F.fitrig_batch_destroy(b)
+            px = sum(fields[k][0] * fields[k][1] ** 2 for k in wave)
+            wms = statistics.median(ms)
+            tot_px += px
+            tot_ms += wms
+            per_wave.append({"fields": len(wave), "gpixel": px / 1e9, "ms": wms,
+                             "candidates": int(np.sum(n)), "status": int(rc)})
+        finally:
+            for p in plans:
+                p.close()
+            torch.cuda.empty_cache()
+    return {"workload": "256 fields, side U{1024..8192}, U{16..128} snapshots, SKA-AA2-like PSF, "
+                        f"BF16 storage, both branches, window {a.window}, {a.nsigma:g} sigma, "
+                        f"{a.noise} noise", "waves": len(waves), "gpixel": tot_px / 1e9,
+            "ms": tot_ms, "value": tot_px / (tot_ms * 1e-3) / 1e9, "unit": UNIT,
+            "timing": f"median of {reps} graph replays per wave, CUDA events",
+            "generation_s": round(t_gen, 1), "per_wave": per_wave}
+
+
 # ---------------------------------------------------------------- our arm
 def main():
     a = parse()
@@ -272,6 +412,9 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     stack_ms = []
+    groups = {"stack": F.KERNEL_STACK, "noise": F.KERNEL_NOISE, "select": F.KERNEL_SELECT,
+              "spectrum": F.KERNEL_SPECTRUM, "detect": F.KERNEL_DETECT}
+    group_ms = {k: [] for k in groups}
     barrier(ws)
     torch.cuda.synchronize()
     n0 = F.fitrig_launch_count()
@@ -280,6 +423,8 @@ def main():
         for _ in range(a.steps):
             rc, ncand = F.fitrig_detect(plan.h)
             stack_ms.append(F.fitrig_kernel_ms(plan.h, F.KERNEL_STACK))
+            for k, g in groups.items():
+                group_ms[k].append(F.fitrig_kernel_ms(plan.h, g))
         ev1.record(stream)
         torch.cuda.synchronize()
     barrier(ws)
@@ -287,7 +432,7 @@ def main():
     ms = ev0.elapsed_time(ev1) / a.steps
     ms = max_over_ranks(ws, ms)
     px_step = L * ny * nx
-    value = ws * px_step / (ms * 1e-3) / 1e9
+    value = job_throughput(ws, px_step, ms)
 
     # roofline of the dominant kernel (stack march): algorithmic bytes per launch
     Ty, Tx = F.fitrig_tile_grid(plan.h)
@@ -304,7 +449,6 @@ def main():
     if not a.no_e2e:
         host = torch.empty((L, ny, nx), dtype=tdt, pin_memory=True)
         host.copy_(stack_s.cpu())
-        del stack_s
         host_np = host  # torch CPU tensor, pinned
         tim = []
         ecands = 0
@@ -320,9 +464,10 @@ def main():
             if i > 0:
                 tim.append(dt)
             ecands = len(c)
+        del host, host_np
         e_ms = 1e3 * statistics.mean(tim)
         e_ms = max_over_ranks(ws, e_ms)
-        e2e = {"value": ws * px_step / (e_ms * 1e-3) / 1e9, "unit": UNIT,
+        e2e = {"value": job_throughput(ws, px_step, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": eb * L * ny * nx,
                "d2h_bytes_per_step": 32 * ecands + 24, "ms_per_step": e_ms,
                "steps": len(tim)}
@@ -334,6 +479,16 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(used, 2)}
 
+    serving = batched = None
+    if rank == 0 and ws == 1 and not (a.no_serving and not a.batched):
+        plan.close()
+        del stack, stack_s
+        torch.cuda.empty_cache()
+        if not a.no_serving:
+            serving = serving_run(a, F, synth, torch)
+        if a.batched:
+            batched = batched_run(a, F, synth, torch)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
@@ -344,15 +499,20 @@ def main():
                        "candidates": int(ncand), "status": int(rc)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_stack_tile", "kernel_ms": k_ms,
-                         "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind},
+                         "kernel": "k_stack_small" if a.window <= 6 else "k_stack_tile",
+                         "kernel_ms": k_ms, "alg_bytes_per_launch": alg_bytes,
+                         "peak_kind": peak_kind},
+            "stages_ms": {k: statistics.mean(v) for k, v in group_ms.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "serving": serving,
+            "batched": batched,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
         }
         print(json.dumps(line))
-    plan.close()
+    if plan.h is not None:
+        plan.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -86,14 +86,34 @@ enum {
   FITRIG_OPT_STORAGE = 1,    /* FITRIG_F32 (default) | FITRIG_BF16 | FITRIG_F16       */
   FITRIG_OPT_NOISE = 2,      /* FITRIG_NOISE_MEANSTD (default) | FITRIG_NOISE_MEDMAD  */
   FITRIG_OPT_RMODE = 3,      /* FITRIG_RMODE_ABS (default) | FITRIG_RMODE_SIGNED      */
+  FITRIG_OPT_MMODE = 4,      /* FITRIG_MMODE_GLOBAL (default) | FITRIG_MMODE_RUNNING  */
   FITRIG_OPT_EDGE = 5,       /* FITRIG_EDGE_PARTIAL (default) | FITRIG_EDGE_DROP      */
   FITRIG_OPT_STRIDE = 6,     /* FITRIG_STRIDE_TILE (default) | FITRIG_STRIDE_SLIDING  */
   FITRIG_OPT_STREAM = 8,     /* cudaStream_t cast to int64; 0 = the plan's own stream */
   FITRIG_OPT_TIMEOUT_NS = 9, /* bound of every device-side wait (default 2e9 ns)      */
-  FITRIG_OPT_AUTOTUNE = 10   /* 1: use the autotuned stack-march shape (tunes once)    */
+  FITRIG_OPT_AUTOTUNE = 10,  /* 1: use the autotuned stack-march shape (tunes once)    */
+  FITRIG_OPT_MAX_SELECTED = 11 /* selected-tile capacity of one detect; 0 = default    */
 };
+/* MAX_SELECTED bounds the tiles (pixels in sliding mode) that pass the
+ * threshold in one detect, over all units and both branches, and so also the
+ * candidates.  0 (the default) is automatic: the lists start at 4 Mi +
+ * units * T / 12 entries (at most units * T; about 100 bytes of device memory
+ * each) and grow when a detect selects more, in which case that detect runs
+ * its post-processing (noise, selection, components, candidates) once more on
+ * the same tile statistics.  A value > 0 is a hard limit: a detect that
+ * selects more returns FITRIG_ETRUNC.  Set after the first push, it resizes
+ * the lists at once (synchronising the plan's stream; the pushed snapshots
+ * stay); a batch that holds the plan must then be created again. */
 enum { FITRIG_NOISE_MEANSTD = 0, FITRIG_NOISE_MEDMAD = 1 };
 enum { FITRIG_RMODE_ABS = 0, FITRIG_RMODE_SIGNED = 1 };
+/* MMODE: the normaliser M of Eq. tLISI.  GLOBAL: one M, the maximum over
+ * every finite pixel of the stack.  RUNNING: the real-time reading of Sec.
+ * 2.2.4, unit s divided by M_s, the maximum over snapshots 0..s+2 only.  The
+ * image-branch z-scores are unchanged (each unit's tiles share one M_s); the
+ * reported tLISI (fitrig_tlisi) and the frequency branch's series (tLISI of
+ * one tile over the units) follow the reading.  Costs one warp reduction per
+ * snapshot in the march and one small kernel. */
+enum { FITRIG_MMODE_GLOBAL = 0, FITRIG_MMODE_RUNNING = 1 };
 enum { FITRIG_EDGE_PARTIAL = 0, FITRIG_EDGE_DROP = 1 };
 /* STRIDE_SLIDING evaluates the tile statistic over the odd window centred on
  * every pixel (clipped at the border) instead of on the paper's disjoint tiles;
@@ -117,9 +137,9 @@ enum { FITRIG_KERNEL_STACK = 0, FITRIG_KERNEL_NOISE = 1, FITRIG_KERNEL_SELECT = 
 FITRIG_API int fitrig_plan_create(int nx, int ny, int nsnap, int window, double nsigma,
                                   int branch, fitrig_plan_t* out);
 
-/* fitrig_plan_set -- set an option (see the enum).  STORAGE, NOISE, RMODE and
- * EDGE are accepted only before the first push (ESTATE after); STREAM and
- * TIMEOUT_NS at any time.  EINVAL for an unknown option or value. */
+/* fitrig_plan_set -- set an option (see the enum).  STORAGE, NOISE, RMODE,
+ * EDGE, STRIDE and AUTOTUNE are accepted only before the first push (ESTATE
+ * after); STREAM, TIMEOUT_NS and MAX_SELECTED at any time.  EINVAL for an unknown option or value. */
 FITRIG_API int fitrig_plan_set(fitrig_plan_t plan, int option, int64_t value);
 
 /*
@@ -130,7 +150,10 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t plan, int option, int64_t value);
  * storage type is converted on the device (round to nearest even).  The
  * buffer is borrowed: a host buffer may be reused when the call returns; a
  * device buffer once the plan's stream has passed this point.  ESTATE when
- * nsnap snapshots were already pushed.
+ * nsnap snapshots were already pushed.  Host snapshots of 32 MB or more are
+ * copied in four row bands on internal side streams (ordered after the work
+ * already on the plan's stream; the plan's stream waits for them), so that
+ * several copy engines share the transfer; pinned host memory is fastest.
  */
 FITRIG_API int fitrig_push_snapshot(fitrig_plan_t plan, const void* data, int dtype,
                                     int on_device, int64_t row_pitch_elems);
@@ -146,7 +169,9 @@ FITRIG_API int fitrig_plan_reset(fitrig_plan_t plan);
  * image branch needs >= 3 pushed snapshots, the frequency branch all nsnap.
  * Synchronises the stream and writes the number of candidates to *ncand.
  * Returns ENONFINITE (results valid) when non-finite pixels invalidated tiles,
- * ETIMEOUT if a device wait gave up.
+ * ETIMEOUT if a device wait gave up, ETRUNC when more tiles passed the
+ * threshold than an explicit FITRIG_OPT_MAX_SELECTED allows (then *ncand = the
+ * capacity that selection needed; results are incomplete).
  */
 FITRIG_API int fitrig_detect(fitrig_plan_t plan, int32_t* ncand);
 
@@ -156,8 +181,13 @@ FITRIG_API int fitrig_detect(fitrig_plan_t plan, int32_t* ncand);
 FITRIG_API int fitrig_candidates(fitrig_plan_t plan, fitrig_candidate* out, int32_t cap,
                                  int32_t* n);
 
+/* fitrig_unit_normaliser -- the M that divides unit s in the last detect:
+ * the global M (as fitrig_global_max) or, with FITRIG_MMODE_RUNNING, M_s. */
+FITRIG_API int fitrig_unit_normaliser(fitrig_plan_t plan, int32_t unit, double* M);
+
 /* fitrig_tlisi -- tLISI matrix of one unit of the last detect (Ty*Tx floats,
- * row-major, host), tLISI = 1 - v/M^2 evaluated in FP64 (Eq. tLISI). */
+ * row-major, host), tLISI = 1 - v/M^2 evaluated in FP64 (Eq. tLISI), M the
+ * unit's normaliser (see FITRIG_OPT_MMODE). */
 FITRIG_API int fitrig_tlisi(fitrig_plan_t plan, int32_t unit, float* out_host, int32_t cap);
 
 /* fitrig_unit_values -- the M-free tile statistic v_t = mean(Delta) max(Delta)
@@ -172,7 +202,9 @@ FITRIG_API int fitrig_noise_params(fitrig_plan_t plan, int32_t unit, double* cen
                                    double* scale);
 
 /* fitrig_spectrum -- eta_t (FP32, NaN for invalid tiles) and its DFT bin per
- * tile after a frequency-branch detect; either pointer may be NULL. */
+ * tile after a frequency-branch detect; either pointer may be NULL.  eta is
+ * the largest DFT magnitude of the tile's mean-removed tLISI series times
+ * M^2 (the global M; the z-scores do not depend on the scale). */
 FITRIG_API int fitrig_spectrum(fitrig_plan_t plan, float* eta_host, int32_t* bin_host,
                                int32_t cap);
 
@@ -256,7 +288,7 @@ FITRIG_API int fitrig_batch_destroy(fitrig_batch_t batch);
 
 /*
  * Serving: fields that stream snapshots (the real-time trigger of Sec. 3.2's
- * timeline, P: input transfer of snapshot s+3 overlapping the trigger kernel).
+ * timeline: the input transfer of snapshot s+3 overlaps the trigger kernel).
  *
  * fitrig_server_create -- a server that admits fields against
  *   `hbm_budget_bytes` of device memory and at most `max_fields` active ones.

@@ -27,7 +27,9 @@ Readings where the paper is silent or ambiguous (each is an option here):
 * edge "partial": ceil(n/w) tiles, edge tiles averaged over their own pixel
   count; "drop": the image is cropped to whole tiles first.
 * M is the maximum over every finite pixel of every analysed snapshot, floored
-  at C; non-finite pixels invalidate the tiles they touch.
+  at C (mmode "global"); the real-time reading (mmode "running") takes unit
+  s's maximum over snapshots 0..s+2 only.  Non-finite pixels invalidate the
+  tiles they touch.
 * standard deviation is the population one; the robust scale is
   1.482602218505602 x MAD with lower medians (index floor((n-1)/2)).
 * tiles are merged into 8-connected components per unit; one candidate per
@@ -86,6 +88,15 @@ def normaliser_M(stack: np.ndarray) -> float:
     fin = x[np.isfinite(x)]
     m = float(fin.max()) if fin.size else -np.inf
     return max(m, C)
+
+
+def normaliser_M_running(stack: np.ndarray) -> np.ndarray:
+    """Real-time reading of M (Sec. 2.2.4: in real time the maximum is taken
+    over the snapshots seen so far, at least three): M_s for unit s is the
+    maximum over every finite pixel of snapshots 0..s+2, floored at C."""
+    x = np.asarray(stack, dtype=np.float64)
+    L = x.shape[0]
+    return np.array([normaliser_M(x[:s + 3]) for s in range(L - 2)])
 
 
 # --------------------------------------------------------------------------
@@ -418,6 +429,7 @@ class Detection:
     eta_z: Optional[np.ndarray] = None
     eta_centre: float = float("nan")
     eta_scale: float = float("nan")
+    M_units: Optional[np.ndarray] = None     # (U,) normaliser of each unit
 
 
 def image_candidates(units: List[UnitTiles], z: np.ndarray, tau: float,
@@ -463,25 +475,32 @@ def freq_candidates(eta: np.ndarray, kbin: np.ndarray, z: np.ndarray, tau: float
 
 def detect(stack: np.ndarray, w: int, tau: float, branch: int = BRANCH_IMAGE,
            noise: str = "meanstd", rmode: str = "abs", edge: str = "partial",
-           forced_image=None, forced_freq=None, stride: str = "tile") -> Detection:
+           forced_image=None, forced_freq=None, stride: str = "tile",
+           mmode: str = "global") -> Detection:
     """Run the trigger on a (L, ny, nx) stack and return the sorted candidates.
 
     stride "tile" is the paper's tiling; "sliding" evaluates the same statistic
     over a w x w window centred on every pixel, after which every pixel plays
     the part of a 1 x 1 tile in the z-score, selection and components.
+    mmode "global" normalises every unit by the one M of the whole stack;
+    "running" normalises unit s by M_s over snapshots 0..s+2 (real time).
+    ``Detection.M`` is the global M in both modes, ``Detection.M_units`` the
+    normaliser of each unit.
     """
     x = np.asarray(stack)
     L, ny, nx = x.shape
     if stride == "sliding":
-        M = normaliser_M(x)
+        region = x
         units = [unit_windows(x, s, w, rmode) for s in range(L - 2)]
         Ty, Tx, nyu, nxu, w = ny, nx, ny, nx, 1
     else:
         Ty, Tx, nyu, nxu = tiling(ny, nx, w, edge)
-        M = normaliser_M(x[:, :nyu, :nxu])
+        region = x[:, :nyu, :nxu]
         units = [unit_tiles(x, s, w, rmode, edge) for s in range(L - 2)]
-    tl = np.stack([tlisi_from_tiles(u, M) for u in units])
-    det = Detection([], M, Ty, Tx, tlisi=tl, units=units)
+    M = normaliser_M(region)
+    Ms = normaliser_M_running(region) if mmode == "running" else np.full(L - 2, M)
+    tl = np.stack([tlisi_from_tiles(u, Ms[s]) for s, u in enumerate(units)])
+    det = Detection([], M, Ty, Tx, tlisi=tl, units=units, M_units=Ms)
     cands: List[Candidate] = []
     if branch & BRANCH_IMAGE:
         zs, cs, ss = [], [], []

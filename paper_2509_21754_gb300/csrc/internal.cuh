@@ -57,6 +57,22 @@ __device__ __forceinline__ float to_f32(f16_t x) {
   return f;
 }
 
+// One warp's maximum of v into *key (order-preserving key; -inf is skipped).
+// Every lane of the warp must call it.
+__device__ __forceinline__ void warp_max_to(float v, unsigned* key) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v > -INFINITY) atomicMax(key, f32_key(v));
+}
+
+// Three-input maximum (one instruction on sm_100 and later; NaN inputs are
+// ignored unless all are NaN, as with fmaxf).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
+
 // ---------------------------------------------------------------- PTX: time, mbarrier, TMA
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
@@ -140,9 +156,10 @@ struct StackArgs {
   int64_t T;           // Tx * Ty
   int64_t vstride;     // floats between units in vp (T rounded up to 4)
   float* vp;           // [nsnap-2][vstride] tile statistic (NaN padding)
-  uint8_t* arg;        // [nsnap-2][vstride] in-tile arg-max of Delta (small path), or null
+  uint8_t* arg = nullptr;     // [nsnap-2][vstride] in-tile arg-max of Delta (small path), or null
   int zrot;            // snapshot j of the march is stack slot (zrot + j) % nsnap (ring use)
   unsigned* gmax;      // ordered key of the running maximum
+  unsigned* smax = nullptr;   // [nsnap] ordered key of each snapshot's maximum, or null
   unsigned* status;    // error flags
   uint64_t timeout_ns;
   StackGeom g;
@@ -156,6 +173,7 @@ struct alignas(128) FieldDesc {
   float* vp;
   uint8_t* arg;
   unsigned* gmax;
+  unsigned* smax = nullptr;   // as StackArgs::smax
   unsigned* status;
   int nx, ny, L, Tx, Ty, gridX;
   int64_t vstride;
@@ -192,6 +210,7 @@ struct SlideArgs {
   int64_t vstride;     // floats between units in vp (nx*ny rounded up to 4)
   float* vp;           // [nsnap-2][vstride]
   unsigned* gmax;
+  unsigned* smax = nullptr;   // [nsnap] per-snapshot maximum keys, or null
   unsigned* status;
   uint64_t timeout_ns;
   SlideGeom g;
@@ -238,10 +257,12 @@ struct SelectScratch {
   int* parent;         // capacity
   unsigned long long* compmax;  // capacity
   int* peak;           // capacity
-  int* map;            // [groups * T] list index + 1 of selected entries, else 0
+  uint32_t* bits;      // [nwords] selection bitmap over the element space groups * stride
+  int* wbase;          // [nwords] list index of the first selected element of each word
   int* plist;          // capacity: list indices of component peaks, in list order
   int* npeak;          // device count of plist
   int64_t capacity;
+  unsigned* want;      // max over overflowing selections of the entries needed
 };
 // Element space [0, groups*stride); selected entries get SelItem{g, t, z} in
 // order and map[g*stride + t] = list index + 1.  blkcnt/blkoff need nblk*8
@@ -284,8 +305,9 @@ cudaError_t launch_export_candidates(const fitrig_candidate* src, const int* n,
                                      fitrig_candidate* dst, int cap, cudaStream_t st);
 
 // Frequency branch.
-cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vstride,
-                            const float2* twiddle, float* eta, int* bin, cudaStream_t st);
+cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
+                            const float2* twiddle, const float* wts, float* eta, int* bin,
+                            cudaStream_t st);
 
 // Ingest conversion (fp32 <-> bf16/fp16).
 cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,
@@ -294,6 +316,11 @@ cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, voi
 // Small helpers.
 cudaError_t launch_fill_probe(void* dst, int type, int64_t n, uint32_t seed, cudaStream_t st);
 cudaError_t launch_tlisi_from_values(const float* vp, int64_t n, const unsigned* gmax,
-                                     float* out, cudaStream_t st);
+                                     const double* m_unit, float* out, cudaStream_t st);
+// Running normalisers (real-time M): smax holds 2 * nsnap keys (the march's
+// per-snapshot maxima, then finite maxima where those were +inf).
+cudaError_t launch_running_norm(const void* stack, int storage, int L, int ny, int nx,
+                                int64_t pitch, unsigned* smax, double* m_unit, float* wts,
+                                cudaStream_t st);
 
 }  // namespace fitrig

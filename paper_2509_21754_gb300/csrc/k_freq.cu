@@ -24,6 +24,7 @@ constexpr int kDftThreads = 128;
 __global__ void __launch_bounds__(kDftThreads) k_dft(const float* __restrict__ vp, int n,
                                                      int64_t T, int64_t vs,
                                                      const float2* __restrict__ tw,
+                                                     const float* __restrict__ wts,
                                                      float* eta, int* bin) {
   extern __shared__ float ys[];   // [n][kDftThreads]
   const int tid = threadIdx.x;
@@ -32,7 +33,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft(const float* __restrict__ v
   bool ok = live;
   float s = 0.f, comp = 0.f;
   for (int q = 0; q < n; ++q) {
-    const float v = live ? vp[(size_t)q * vs + t] : 0.f;
+    const float v = live ? (wts ? vp[(size_t)q * vs + t] * wts[q] : vp[(size_t)q * vs + t]) : 0.f;
     ok = ok && isfinite(v);
     ys[q * kDftThreads + tid] = v;
     const float y = v - comp;
@@ -86,6 +87,7 @@ template <int KMAX>
 __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restrict__ vp, int n,
                                                            int64_t T, int64_t vs,
                                                            const float2* __restrict__ tw,
+                                                           const float* __restrict__ wts,
                                                            float* eta, int* bin) {
   extern __shared__ float2 tws[];   // [H][K] twiddles, pair-major, then [n][threads] series
   const int H = (n - 1) / 2, K = n / 2;
@@ -101,7 +103,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restri
   bool ok = true;
   float* my = ys + threadIdx.x;
   for (int q = 0; q < n; ++q) {
-    const float v = vp[(size_t)q * vs + t];
+    const float v = wts ? vp[(size_t)q * vs + t] * wts[q] : vp[(size_t)q * vs + t];
     ok = ok && isfinite(v);
     my[q * kDftThreads] = v;
     const float y = v - comp;
@@ -155,15 +157,18 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restri
 }
 
 cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
-                            const float2* twiddle, float* eta, int* bin, cudaStream_t st) {
+                            const float2* twiddle, const float* wts, float* eta, int* bin,
+                            cudaStream_t st) {
   const int64_t blocks = (T + kDftThreads - 1) / kDftThreads;
   const int H = (n - 1) / 2, K = n / 2;
   if (n <= 65 && H >= 1) {
     const size_t sm = (size_t)H * K * sizeof(float2) + (size_t)n * kDftThreads * sizeof(float);
     if (K <= 16)
-      k_dft_short<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, eta, bin);
+      k_dft_short<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts, eta,
+                                                                 bin);
     else
-      k_dft_short<32><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, eta, bin);
+      k_dft_short<32><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts, eta,
+                                                                 bin);
     count_launches(1);
     return cudaGetLastError();
   }
@@ -175,7 +180,7 @@ cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  k_dft<<<(unsigned)blocks, kDftThreads, smem, st>>>(vp, n, T, vs, twiddle, eta, bin);
+  k_dft<<<(unsigned)blocks, kDftThreads, smem, st>>>(vp, n, T, vs, twiddle, wts, eta, bin);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -240,19 +245,93 @@ cudaError_t launch_fill_probe(void* dst, int type, int64_t n, uint32_t seed, cud
 
 // ---------------------------------------------------------------- tLISI report
 // tLISI = 1 - v / M^2 in FP64 (Eq. tLISI), M = max(stack maximum, C).
-__global__ void k_tlisi(const float* vp, int64_t n, const unsigned* gmax, float* out) {
-  const unsigned key = *gmax;
-  double M = key ? (double)f32_from_key(key) : 0.0;
-  if (!(M > (double)kGuardC)) M = (double)kGuardC;
+__global__ void k_tlisi(const float* vp, int64_t n, const unsigned* gmax, const double* m_unit,
+                        float* out) {
+  double M;
+  if (m_unit) {
+    M = *m_unit;
+  } else {
+    const unsigned key = *gmax;
+    M = key ? (double)f32_from_key(key) : 0.0;
+    if (!(M > (double)kGuardC)) M = (double)kGuardC;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (float)(1.0 - (double)vp[i] / (M * M));
 }
 
 cudaError_t launch_tlisi_from_values(const float* vp, int64_t n, const unsigned* gmax,
-                                     float* out, cudaStream_t st) {
-  k_tlisi<<<152 * 2, 256, 0, st>>>(vp, n, gmax, out);
+                                     const double* m_unit, float* out, cudaStream_t st) {
+  k_tlisi<<<152 * 2, 256, 0, st>>>(vp, n, gmax, m_unit, out);
   count_launches(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- running M
+// Real-time reading of M (Sec. 2.2.4): unit s is normalised by the maximum
+// over snapshots 0..s+2.  The march leaves each snapshot's maximum key in
+// smax[k] (+inf included); a snapshot whose maximum is +inf gets the maximum
+// of its finite pixels instead (rare: only stacks with non-finite pixels).
+template <typename T>
+__global__ void k_snap_finite_max(const T* stack, int L, int ny, int nx, int64_t pitch,
+                                  size_t slice, unsigned* smax) {
+  const unsigned inf_key = f32_key(INFINITY);
+  for (int k = 0; k < L; ++k) {
+    if (smax[k] != inf_key) continue;   // uniform: every thread reads the same word
+    const T* x = stack + (size_t)k * slice;
+    float m = -INFINITY;
+    const int64_t total = (int64_t)ny * nx;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const float v = to_f32(x[(i / nx) * pitch + (i % nx)]);
+      if (isfinite(v)) m = fmaxf(m, v);
+    }
+    // the words are replaced only after every block has read them: write the
+    // finite maxima to the upper half and let k_running_norm prefer it
+    warp_max_to(m, smax + L + k);
+  }
+}
+
+// M_s = max(C, max over k <= s + 2 of the snapshot maxima) for s < U, in FP64,
+// and the series weights (M_{U-1} / M_s)^2 of the frequency branch, whose
+// spectrum is then the spectrum of the tLISI series scaled by M^2 like the
+// global reading's.
+__global__ void k_running_norm(const unsigned* smax, int L, double* m_unit, float* wts) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned inf_key = f32_key(INFINITY);
+  const int U = L - 2;
+  double run = (double)kGuardC;
+  for (int k = 0; k < L; ++k) {
+    unsigned key = smax[k];
+    if (key == inf_key) key = smax[L + k];
+    if (key) {
+      const double v = (double)f32_from_key(key);
+      if (v > run) run = v;   // NaN never compares greater
+    }
+    if (k >= 2) m_unit[k - 2] = run;
+  }
+  const double last = m_unit[U - 1];
+  for (int s = 0; s < U; ++s) {
+    const double q = last / m_unit[s];
+    wts[s] = (float)(q * q);
+  }
+}
+
+cudaError_t launch_running_norm(const void* stack, int storage, int L, int ny, int nx,
+                                int64_t pitch, unsigned* smax, double* m_unit, float* wts,
+                                cudaStream_t st) {
+  const size_t slice = (size_t)pitch * ny;
+  if (storage == FITRIG_F32)
+    k_snap_finite_max<float><<<152 * 2, 256, 0, st>>>(static_cast<const float*>(stack), L, ny, nx,
+                                                       pitch, slice, smax);
+  else if (storage == FITRIG_BF16)
+    k_snap_finite_max<bf16_t><<<152 * 2, 256, 0, st>>>(static_cast<const bf16_t*>(stack), L, ny,
+                                                        nx, pitch, slice, smax);
+  else
+    k_snap_finite_max<f16_t><<<152 * 2, 256, 0, st>>>(static_cast<const f16_t*>(stack), L, ny, nx,
+                                                       pitch, slice, smax);
+  k_running_norm<<<1, 32, 0, st>>>(smax, L, m_unit, wts);
+  count_launches(2);
   return cudaGetLastError();
 }
 

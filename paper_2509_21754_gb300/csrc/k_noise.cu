@@ -295,31 +295,41 @@ __global__ void __launch_bounds__(kSelectThreads) k_rs_select(int groups, int64_
 }
 
 // ---------------------------------------------------------------- MEDMAD, cluster form
-// One thread-block cluster per group finds the median and then the MAD in a
-// single launch, by range-binned selection over the order-preserving keys:
+// One thread-block cluster of 8 CTAs per group finds the median and then the
+// MAD, every group of the map in the same launch, by range-binned selection
+// over the order-preserving keys:
 //   * a first sweep takes the minimum and maximum key (and the count) of the
 //     group's finite values;
-//   * each pass bins the keys inside the current inclusive range [lo, hi]
-//     linearly into 2048 bins (digit = (key - lo) >> shift, shift chosen so
-//     the range fits), the bin holding the target rank becomes the new range,
-//     and the rank is reduced by the counts below it; after at most three
-//     passes the range is a single key, which is the exact order statistic;
+//   * a binning round counts the keys inside the current inclusive range
+//     [lo, hi] in 4096 linear bins (digit = (key - lo) >> shift); the bin
+//     holding the target rank becomes the new range and the rank is reduced by
+//     the counts below it;
+//   * once the range holds at most 20 Ki keys, one more pass over the group
+//     copies exactly those keys into the CTAs' shared memory, and the
+//     remaining rounds bin the copies instead of the whole map;
+//   * the range ends as a single key: the exact order statistic;
 //   * the MAD repeats this on the keys of |v - median| (FP32), whose range is
 //     [0, max(|vmax - median|, |vmin - median|)].
-// Linear bins spread the values over many bins, so plain shared-memory atomics
-// suffice.  Every CTA counts its share into its own histogram, the others add
-// theirs into the leader's through distributed shared memory, and the leader
-// publishes the new range after a cluster barrier.  Integer counting only:
-// the result is the same element a sort would give.
+// Each CTA bins its share into its own histogram, plus 64 coarse counts (64
+// bins each).  After one cluster barrier every CTA reads the eight CTAs'
+// coarse counts and then the 64 fine counts of the coarse bin that holds the
+// rank through distributed shared memory and finds the new range itself, so
+// all CTAs hold the same state without a leader.  The histograms are double
+// buffered: a CTA rewrites a buffer only after the next barrier, when every
+// CTA has finished reading it.  Integer counting only: the result is the
+// element a sort would give.
 constexpr int kClusterCtas = 8;
-constexpr int kClusterThreads = 512;
+constexpr int kClusterThreads = 256;
+constexpr int kClusterBins = 4096;
+constexpr int kCoarse = 64;                                     // coarse bins of 64 fine bins
+constexpr int kCollectPerCta = 5120;                            // keys kept per CTA
+constexpr unsigned long long kCollectAll = kClusterCtas * kCollectPerCta / 2;
 constexpr int64_t kClusterMaxPerGroup = 8 << 20;   // larger maps use the grid-wide passes
-constexpr int64_t kClusterBatchBytes = 48 << 20;   // groups per launch stay L2-resident
 
 struct RangeState {
   unsigned long long lo, hi;   // inclusive key range
   unsigned long long rank;     // rank of the target inside the range
-  unsigned long long total;    // finite values of the group
+  unsigned long long count;    // keys inside the range
   unsigned shift;              // digit = (key - lo) >> shift
   unsigned done;
 };
@@ -327,18 +337,57 @@ struct RangeState {
 __device__ __forceinline__ unsigned range_shift(unsigned long long lo, unsigned long long hi) {
   const unsigned long long width = hi - lo + 1;   // <= 2^32
   unsigned s = 0;
-  while ((width - 1) >> s >= (unsigned long long)kBins) ++s;
+  while ((width - 1) >> s >= (unsigned long long)kClusterBins) ++s;
   return s;
 }
 
+// Inclusive warp scan of two counts per lane (entries 2*lane, 2*lane+1); finds
+// the entry holding `rank`.  Returns the entry and the count before it.
+__device__ __forceinline__ void warp_find64(const unsigned* cnt, unsigned long long rank,
+                                            int* entry, unsigned long long* below,
+                                            unsigned* size) {
+  const int lane = threadIdx.x & 31;
+  const unsigned a = cnt[2 * lane], b = cnt[2 * lane + 1];
+  unsigned long long incl = (unsigned long long)a + b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned long long excl = incl - a - b;
+  int e = -1;
+  unsigned long long bl = 0;
+  unsigned sz = 0;
+  if (rank >= excl && rank < excl + a) {
+    e = 2 * lane;
+    bl = excl;
+    sz = a;
+  } else if (rank >= excl + a && rank < incl) {
+    e = 2 * lane + 1;
+    bl = excl + a;
+    sz = b;
+  }
+  const unsigned who = __ballot_sync(0xffffffffu, e >= 0);
+  const int src = who ? __ffs(who) - 1 : 0;
+  // the rank always lies inside the counted range; the clamp only keeps the
+  // indices derived from `entry` in bounds
+  *entry = max(0, __shfl_sync(0xffffffffu, e, src));
+  *below = __shfl_sync(0xffffffffu, bl, src);
+  *size = __shfl_sync(0xffffffffu, sz, src);
+}
+
+// (four CTAs per SM: the clusters of a whole map are resident at once)
 template <bool VEC>
-__global__ void __launch_bounds__(kClusterThreads) k_medmad_cluster(const float* __restrict__ vals,
+__global__ void __launch_bounds__(kClusterThreads, 4) k_medmad_cluster(const float* __restrict__ vals,
                                                                     int64_t stride, int64_t n,
                                                                     int g0, double* cs,
                                                                     unsigned long long* invalid) {
-  __shared__ unsigned hist[kBins];
+  __shared__ unsigned hist[2][kClusterBins];
+  __shared__ unsigned coarse[2][kCoarse];
+  __shared__ uint32_t keep[kCollectPerCta];
+  __shared__ unsigned nkeep, overflow;
   __shared__ unsigned long long red[kClusterThreads / 32][3];
-  __shared__ unsigned long long scan[kClusterThreads];
+  __shared__ unsigned sum64[kCoarse];
   __shared__ RangeState st;
   __shared__ unsigned long long mm[3];   // this CTA's min key, max key, count
   cg::cluster_group cl = cg::this_cluster();
@@ -346,25 +395,48 @@ __global__ void __launch_bounds__(kClusterThreads) k_medmad_cluster(const float*
   const int g = g0 + blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* v = vals + (size_t)g * stride;
-  const RangeState* lead = cl.map_shared_rank(&st, 0);
   const int64_t nv = VEC ? stride / 4 : stride;
   const int64_t step = (int64_t)kClusterCtas * blockDim.x;
 
-  // visit every finite value of this CTA's share as an order-preserving key
+  // visit every finite value of this CTA's share as an order-preserving key;
+  // four loads are issued before their keys are used, so that each thread
+  // keeps several requests in flight (the passes are latency-bound otherwise)
   auto for_keys = [&](int mad, float med, auto&& fn) {
-    for (int64_t i = (int64_t)rank * blockDim.x + tid; i < nv; i += step) {
-      if (VEC) {
-        const float4 q = reinterpret_cast<const float4*>(v)[i];
-        const float e[4] = {q.x, q.y, q.z, q.w};
+    auto take = [&](float e) {
+      uint32_t key;
+      if (rs_key(e, mad, med, &key)) fn(key);
+    };
+    int64_t i = (int64_t)rank * blockDim.x + tid;
+    if (VEC) {
+      const float4* v4 = reinterpret_cast<const float4*>(v);
+      for (; i + 3 * step < nv; i += 4 * step) {
+        float4 q[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          uint32_t key;
-          if (rs_key(e[c], mad, med, &key)) fn(key);
+        for (int u = 0; u < 4; ++u) q[u] = v4[i + u * step];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          take(q[u].x);
+          take(q[u].y);
+          take(q[u].z);
+          take(q[u].w);
         }
-      } else {
-        uint32_t key;
-        if (rs_key(v[i], mad, med, &key)) fn(key);
       }
+      for (; i < nv; i += step) {
+        const float4 q = v4[i];
+        take(q.x);
+        take(q.y);
+        take(q.z);
+        take(q.w);
+      }
+    } else {
+      for (; i + 3 * step < nv; i += 4 * step) {
+        float q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = v[i + u * step];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) take(q[u]);
+      }
+      for (; i < nv; i += step) take(v[i]);
     }
   };
 
@@ -420,8 +492,9 @@ __global__ void __launch_bounds__(kClusterThreads) k_medmad_cluster(const float*
     atomicAdd(invalid, (unsigned long long)(n - (int64_t)total));
 
   float med = 0.f;
+  int buf = 0;
   for (int mad = 0; mad < 2; ++mad) {
-    if (rank == 0 && tid == 0) {
+    if (tid == 0) {
       if (mad == 0) {
         st.lo = gmin;
         st.hi = gmax;
@@ -431,76 +504,127 @@ __global__ void __launch_bounds__(kClusterThreads) k_medmad_cluster(const float*
         st.hi = f32_key(fmaxf(fabsf(vmax - med), fabsf(vmin - med)));
       }
       st.rank = (total - 1) / 2;
+      st.count = total;
       st.shift = range_shift(st.lo, st.hi);
       st.done = st.lo == st.hi;
     }
-    cl.sync();   // the starting range is published (and the shares summaries read)
-    for (int pass = 0; pass < 4; ++pass) {
-      const RangeState r = *lead;
-      if (r.done) break;   // uniform: everyone read the same leader state
-      for (int b = tid; b < kBins; b += blockDim.x) hist[b] = 0;
-      __syncthreads();
-      for_keys(mad, med, [&](uint32_t key) {
-        if (key >= r.lo && key <= r.hi) atomicAdd(&hist[(unsigned)((key - r.lo) >> r.shift)], 1u);
-      });
-      cl.sync();           // every CTA's histogram is complete
-      if (rank == 0) {
-        // sum the CTAs' histograms (plain remote loads, fixed order)
-        constexpr int per = kBins / kClusterThreads;
-        unsigned local[per];
-        for (int i = 0; i < per; ++i) local[i] = 0;
-        for (int c = 0; c < kClusterCtas; ++c) {
-          const unsigned* h = cl.map_shared_rank(hist, c);
-          for (int i = 0; i < per; ++i) local[i] += h[tid * per + i];
+    __syncthreads();
+    bool kept = false;        // the keys of the current range sit in `keep`
+    bool no_copy = false;     // a copy pass overflowed: bin the whole map instead
+    for (int round = 0; round < 12; ++round) {
+      const RangeState r = st;   // the same in every CTA
+      if (r.done) break;
+      if (!kept && !no_copy && r.count <= kCollectAll) {
+        // copy pass: the keys inside [lo, hi] into this CTA's shared memory
+        if (tid == 0) {
+          nkeep = 0;
+          overflow = 0;
         }
-        unsigned long long mine = 0;
-        for (int i = 0; i < per; ++i) mine += local[i];
-        scan[tid] = mine;
         __syncthreads();
-        for (int d = 1; d < kClusterThreads; d <<= 1) {
-          const unsigned long long add = tid >= d ? scan[tid - d] : 0ull;
-          __syncthreads();
-          scan[tid] += add;
-          __syncthreads();
-        }
-        const unsigned long long before = scan[tid] - mine;
-        if (r.rank >= before && r.rank < before + mine) {
-          unsigned long long cum = before;
-          for (int i = 0; i < per; ++i) {
-            if (r.rank < cum + local[i]) {
-              const unsigned long long b = (unsigned long long)(tid * per + i);
-              const unsigned long long lo = r.lo + (b << r.shift);
-              const unsigned long long hi = min(r.hi, lo + ((1ull << r.shift) - 1));
-              st.lo = lo;
-              st.hi = hi;
-              st.rank = r.rank - cum;
-              st.shift = range_shift(lo, hi);
-              st.done = lo == hi;
-              break;
-            }
-            cum += local[i];
+        for_keys(mad, med, [&](uint32_t key) {
+          if (key >= r.lo && key <= r.hi) {
+            const unsigned at = atomicAdd(&nkeep, 1u);
+            if (at < (unsigned)kCollectPerCta) keep[at] = key;
+            else overflow = 1u;
           }
+        });
+        cl.sync();         // every CTA's copy and overflow flag are final
+        unsigned any = 0;
+        for (int c = 0; c < kClusterCtas; ++c) any |= *cl.map_shared_rank(&overflow, c);
+        kept = any == 0;   // the same decision in every CTA
+        no_copy = !kept;
+        // (the flags are next written in the MAD's copy pass, after further
+        // cluster barriers, so no barrier is needed before moving on)
+        continue;
+      }
+      unsigned* h = hist[buf];
+      unsigned* co = coarse[buf];
+      for (int b = tid; b < kClusterBins; b += blockDim.x) h[b] = 0;
+      __syncthreads();
+      auto bin = [&](uint32_t key) {
+        if (key >= r.lo && key <= r.hi) atomicAdd(&h[(unsigned)((key - r.lo) >> r.shift)], 1u);
+      };
+      if (kept) {
+        const unsigned m = nkeep;
+        for (unsigned i = tid; i < m; i += blockDim.x) bin(keep[i]);
+      } else {
+        for_keys(mad, med, bin);
+      }
+      __syncthreads();
+      // coarse counts: 4 threads per coarse bin of 64 fine bins
+      {
+        const int c = tid >> 2, part = tid & 3;
+        unsigned sum = 0;
+#pragma unroll 4
+        for (int i = 0; i < 16; ++i) sum += h[c * 64 + part * 16 + i];
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        if (part == 0) co[c] = sum;
+      }
+      cl.sync();           // every CTA's histogram and coarse counts are complete
+      // the cluster's coarse counts, then the fine counts inside the coarse bin
+      if (tid < kCoarse) {
+        unsigned t = 0;
+        for (int c = 0; c < kClusterCtas; ++c) t += cl.map_shared_rank(co, c)[tid];
+        sum64[tid] = t;
+      }
+      __syncthreads();
+      int cbin;
+      unsigned long long cbelow;
+      unsigned csize;
+      if (warp == 0) {
+        warp_find64(sum64, r.rank, &cbin, &cbelow, &csize);
+        if (lane == 0) {
+          red[0][0] = (unsigned long long)cbin;
+          red[0][1] = cbelow;
         }
       }
-      cl.sync();           // the new range is published; all histograms were read
+      __syncthreads();
+      cbin = (int)red[0][0];
+      cbelow = red[0][1];
+      if (tid < kCoarse) {
+        unsigned t = 0;
+        for (int c = 0; c < kClusterCtas; ++c) t += cl.map_shared_rank(h, c)[cbin * 64 + tid];
+        sum64[tid] = t;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        int fbin;
+        unsigned long long fbelow;
+        unsigned fsize;
+        warp_find64(sum64, r.rank - cbelow, &fbin, &fbelow, &fsize);
+        if (lane == 0) {
+          const unsigned long long b = (unsigned long long)(cbin * 64 + fbin);
+          const unsigned long long lo = r.lo + (b << r.shift);
+          const unsigned long long hi = min(r.hi, lo + ((1ull << r.shift) - 1));
+          st.lo = lo;
+          st.hi = hi;
+          st.rank = r.rank - cbelow - fbelow;
+          st.count = fsize;
+          st.shift = range_shift(lo, hi);
+          st.done = lo == hi;
+        }
+      }
+      __syncthreads();     // the new range is visible to the whole CTA
+      buf ^= 1;
     }
-    const float val = f32_from_key((uint32_t)lead->lo);
+    const float val = f32_from_key((uint32_t)st.lo);
     if (mad == 0) {
       med = val;
       if (rank == 0 && tid == 0) cs[2 * g] = (double)val;
     } else if (rank == 0 && tid == 0) {
       cs[2 * g + 1] = kMadToSigma * (double)val;
     }
-    cl.sync();             // everyone has read the result before the state changes
+    __syncthreads();       // everyone has read st before it is reset
   }
+  cl.sync();               // nobody leaves while others may still read its histograms
 }
 
 static cudaError_t launch_medmad_cluster(const float* vals, int groups, int64_t stride,
                                          int64_t n, bool vec, double* cs,
                                          unsigned long long* invalid, cudaStream_t st) {
-  const int64_t per = std::max<int64_t>(1, kClusterBatchBytes / std::max<int64_t>(1, stride * 4));
-  for (int g0 = 0; g0 < groups; g0 += (int)per) {
-    const int gb = (int)std::min<int64_t>(per, groups - g0);
+  for (int g0 = 0; g0 < groups; g0 += 65535) {
+    const int gb = std::min(65535, groups - g0);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kClusterCtas, gb, 1);
     cfg.blockDim = dim3(kClusterThreads, 1, 1);

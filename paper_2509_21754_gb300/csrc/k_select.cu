@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_count(const float* __restri
 // Exclusive scan of per-warp (or per-block) counts (one block of 1024 threads).
 __global__ void __launch_bounds__(1024) k_scan_blocks(int nblk, const int* blkcnt, int* blkoff,
                                                       int* total, int64_t cap,
-                                                      unsigned* status) {
+                                                      unsigned* status, unsigned* want) {
   __shared__ long long sh[1024];
   const int per = (nblk + 1023) / 1024;
   const int b0 = threadIdx.x * per;
@@ -100,7 +100,10 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(int nblk, const int* blkcn
   if (threadIdx.x == 1023) {
     const long long tot = sh[1023];
     *total = (int)(tot < cap ? tot : cap);
-    if (tot > cap) atomicOr(status, kErrCapacity);
+    if (tot > cap) {
+      atomicOr(status, kErrCapacity);
+      if (want) atomicMax(want, (unsigned)(tot < 0xffffffffll ? tot : 0xffffffffll));
+    }
   }
 }
 
@@ -111,8 +114,8 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restri
                                                            const double* __restrict__ cs,
                                                            const double* __restrict__ inv,
                                                            int64_t chunk, const int* woff,
-                                                           SelItem* items, int* map,
-                                                           int64_t cap) {
+                                                           SelItem* items, uint32_t* sbits,
+                                                           int* wbase, int64_t cap) {
   const int64_t N = (int64_t)groups * stride;
   int64_t lo, hi;
   warp_range(N, chunk, &lo, &hi);
@@ -152,6 +155,25 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restri
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     int64_t pos = run + incl - c;
+    // bitmap words of this iteration (base is a multiple of 32 elements, of
+    // 128 with VEC) and the list index of each word's first selected element
+    if (VEC) {
+      uint32_t word = bits << (4 * (lane & 7));   // lanes 8w..8w+7 hold word w
+      word |= __shfl_xor_sync(0xffffffffu, word, 1);
+      word |= __shfl_xor_sync(0xffffffffu, word, 2);
+      word |= __shfl_xor_sync(0xffffffffu, word, 4);
+      if ((lane & 7) == 0) {
+        const int64_t wi = (base >> 5) + (lane >> 3);
+        sbits[wi] = word;
+        wbase[wi] = (int)min(pos, (int64_t)INT_MAX);
+      }
+    } else {
+      const uint32_t word = __ballot_sync(0xffffffffu, bits != 0);
+      if (lane == 0) {
+        sbits[base >> 5] = word;
+        wbase[base >> 5] = (int)min(pos, (int64_t)INT_MAX);
+      }
+    }
     if (bits) {
       const double cg = cs[2 * g], ig = inv[g];
       for (int k = 0; k < step; ++k) {
@@ -163,7 +185,6 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restri
           it.t = (int32_t)(e - (int64_t)g * stride);
           it.z = ((double)v[k] - cg) * ig;
           items[pos] = it;
-          map[e] = (int)pos + 1;
         }
         ++pos;
       }
@@ -188,14 +209,18 @@ cudaError_t launch_select(const float* vals, int groups, int64_t stride, const f
   const int64_t chunk = sel_chunk((int64_t)groups * stride, nw);
   if (sel_vec(vals, stride)) {
     k_sel_count<true><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk, s.blkcnt);
-    k_scan_blocks<<<1, 1024, 0, st>>>(nw, s.blkcnt, s.blkoff, s.nsel, s.capacity, status);
+    k_scan_blocks<<<1, 1024, 0, st>>>(nw, s.blkcnt, s.blkoff, s.nsel, s.capacity, status,
+                                      s.want);
     k_sel_write<true><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, cs, inv, chunk,
-                                                      s.blkoff, s.items, s.map, s.capacity);
+                                                      s.blkoff, s.items, s.bits, s.wbase,
+                                                      s.capacity);
   } else {
     k_sel_count<false><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk, s.blkcnt);
-    k_scan_blocks<<<1, 1024, 0, st>>>(nw, s.blkcnt, s.blkoff, s.nsel, s.capacity, status);
+    k_scan_blocks<<<1, 1024, 0, st>>>(nw, s.blkcnt, s.blkoff, s.nsel, s.capacity, status,
+                                      s.want);
     k_sel_write<false><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, cs, inv, chunk,
-                                                       s.blkoff, s.items, s.map, s.capacity);
+                                                       s.blkoff, s.items, s.bits, s.wbase,
+                                                       s.capacity);
   }
   count_launches(3);
   return cudaGetLastError();
@@ -308,9 +333,18 @@ __global__ void k_cc_runs(const SelItem* __restrict__ items, const int* nsel, in
   }
 }
 
+// List index of element e when it is selected, else -1.
+__device__ __forceinline__ int sel_index(const uint32_t* __restrict__ sbits,
+                                         const int* __restrict__ wbase, int64_t e) {
+  const uint32_t w = sbits[e >> 5];
+  const uint32_t b = 1u << (e & 31);
+  if (!(w & b)) return -1;
+  return wbase[e >> 5] + __popc(w & (b - 1u));
+}
+
 __global__ void k_cc_union(const SelItem* __restrict__ items, const int* nsel, int Tx, int Ty,
-                           int64_t T, const int* __restrict__ map, int* parent,
-                           unsigned* status) {
+                           int64_t T, const uint32_t* __restrict__ sbits,
+                           const int* __restrict__ wbase, int* parent, unsigned* status) {
   const int n = *nsel;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const SelItem me = items[i];
@@ -319,26 +353,44 @@ __global__ void k_cc_union(const SelItem* __restrict__ items, const int* nsel, i
     // left neighbours are joined by the runs; of the row above, the tile right
     // above covers both diagonals when it is selected (they would be in its run)
     const int64_t up = (int64_t)me.group * T + (int64_t)(ty - 1) * Tx + tx;
-    const int j = map[up] - 1;
+    // (indices at or past n belong to a list that overflowed its capacity)
+    const int j = sel_index(sbits, wbase, up);
     if (j >= 0) {
-      unite(parent, i, j, status);
+      if (j < n) unite(parent, i, j, status);
     } else {
       if (tx > 0) {
-        const int jl = map[up - 1] - 1;
-        if (jl >= 0) unite(parent, i, jl, status);
+        const int jl = sel_index(sbits, wbase, up - 1);
+        if (jl >= 0 && jl < n) unite(parent, i, jl, status);
       }
       if (tx + 1 < Tx) {
-        const int jr = map[up + 1] - 1;
-        if (jr >= 0) unite(parent, i, jr, status);
+        const int jr = sel_index(sbits, wbase, up + 1);
+        if (jr >= 0 && jr < n) unite(parent, i, jr, status);
       }
     }
   }
 }
 
+// After the unions every entry points straight at its root.  The roots no
+// longer change here, so each thread finds its root without writing and then
+// sets every entry on its path to that root: every store is a final value
+// (path halving here could store an intermediate ancestor over another
+// thread's root and leave an entry outside its component's root).
 __global__ void k_cc_flatten(const int* nsel, int* parent) {
   const int n = *nsel;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    parent[i] = find_root(parent, i);
+  volatile int* p = parent;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int r = i, y = p[i];
+    while (y != r) {
+      r = y;
+      y = p[r];
+    }
+    int x = i;
+    while (x != r) {
+      const int nx = p[x];
+      p[x] = r;
+      x = nx;
+    }
+  }
 }
 
 __global__ void k_cc_peak(const SelItem* __restrict__ items, const int* nsel, const int* parent,
@@ -357,7 +409,8 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
   const int grid = 152 * 16, thr = 256;
   k_cc_init<<<grid, thr, 0, st>>>(s.nsel, s.parent, s.compmax, s.peak);
   k_cc_runs<<<grid, thr, 0, st>>>(s.items, s.nsel, Tx, s.parent);
-  k_cc_union<<<grid, thr, 0, st>>>(s.items, s.nsel, Tx, Ty, T, s.map, s.parent, status);
+  k_cc_union<<<grid, thr, 0, st>>>(s.items, s.nsel, Tx, Ty, T, s.bits, s.wbase, s.parent,
+                                   status);
   k_cc_flatten<<<grid, thr, 0, st>>>(s.nsel, s.parent);
   k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak, 0);
   k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak, 1);
@@ -605,13 +658,6 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
   }
 }
 
-__global__ void k_map_clear(const SelItem* __restrict__ items, const int* nsel, int64_t T,
-                            int* map) {
-  const int n = *nsel;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    map[(int64_t)items[i].group * T + items[i].t] = 0;
-}
-
 __global__ void k_add_count(int* total, const int* part) { *total += *part; }
 
 // Copies the first min(*n, cap) candidates to mapped host memory, so only the
@@ -634,7 +680,8 @@ cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, in
                                    fitrig_candidate* tmp, unsigned* status, cudaStream_t st) {
   // ordered list of component peaks
   k_peak_count<<<s.nblk, kSelThreads, 0, st>>>(s.nsel, s.parent, s.peak, s.nblk, s.blkcnt);
-  k_scan_blocks<<<1, 1024, 0, st>>>(s.nblk, s.blkcnt, s.blkoff, s.npeak, s.capacity, status);
+  k_scan_blocks<<<1, 1024, 0, st>>>(s.nblk, s.blkcnt, s.blkoff, s.npeak, s.capacity, status,
+                                    nullptr);
   k_peak_write<<<s.nblk, kSelThreads, 0, st>>>(s.nsel, s.parent, s.peak, s.nblk, s.blkoff,
                                                s.plist);
   if (a.branch == FITRIG_BRANCH_FREQ) {
@@ -648,10 +695,9 @@ cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, in
     k_group_sort<<<152 * 4, kGroupWarps * 32, 0, st>>>(a, s.npeak, tmp, base);
     count_launches(5);
   }
-  // running total of candidates, and a clean map for the next selection
+  // running total of candidates
   k_add_count<<<1, 1, 0, st>>>(a.nout, s.npeak);
-  k_map_clear<<<152 * 4, 256, 0, st>>>(s.items, s.nsel, a.stride, s.map);
-  count_launches(2);
+  count_launches(1);
   return cudaGetLastError();
 }
 

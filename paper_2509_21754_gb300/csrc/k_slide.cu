@@ -76,12 +76,13 @@ __global__ void __launch_bounds__(kSlideMaxThreads) k_slide(const __grid_constan
     const int stg = j % NS;
     const bool ok = mbar_wait_bounded(bar0 + 8 * stg, (uint32_t)((j / NS) & 1), deadline);
     const T* st = reinterpret_cast<const T*>(smem + (size_t)stg * g.stage_bytes);
+    float sm = -INFINITY;   // this snapshot's maximum over the thread's pixels
     if (ok && active) {
 #pragma unroll
       for (int i = 0; i < kSlideR; ++i) {
         if (i < rcount) {
           const float xn = to_f32(st[(row0 + i) * g.boxW + col]);
-          mx = fmaxf(mx, xn);
+          sm = fmaxf(sm, xn);
           const float dn = fabsf(xn - xp[i]);
           if (j >= 2) {
             const float d = fabsf(dn - dp[i]);
@@ -104,6 +105,8 @@ __global__ void __launch_bounds__(kSlideMaxThreads) k_slide(const __grid_constan
       }
       return;
     }
+    mx = fmaxf(mx, sm);
+    if (a.smax) warp_max_to(sm, a.smax + j);
     if (tid == 0 && j + NS < L) {
       fence_proxy_async_smem();
       mbar_expect_tx(bar0 + 8 * stg, box_bytes);

@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
   for (int j = 0; j < L; ++j) {
     const bool ok = mbar_wait_bounded(bar0 + 8 * stg, phase, deadline);
     const T* st = reinterpret_cast<const T*>(smem + (size_t)stg * g.stage_bytes);
+    float sm = -INFINITY;   // this snapshot's maximum over the thread's pixels
     if (ok) {
       if (j >= 2) {
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
         for (int i = 0; i < R; ++i) {
           if (i < rcount) {
             const float xn = to_f32(st[(row0 + i) * g.boxW + col]);
-            mx = fmaxf(mx, xn);
+            sm = fmaxf(sm, xn);
             const float dn = fabsf(xn - xp[i]);        // D^(s+1)
             const float d = fabsf(dn - dp[i]);         // Delta
             const float ref = SIGNED ? xp[i] : fabsf(xp[i]);
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
         for (int i = 0; i < R; ++i) {
           if (i < rcount) {
             const float xn = to_f32(st[(row0 + i) * g.boxW + col]);
-            mx = fmaxf(mx, xn);
+            sm = fmaxf(sm, xn);
             dp[i] = fabsf(xn - xp[i]);   // D^(0) once j == 1
             xp[i] = xn;
           }
@@ -127,6 +128,8 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
       }
       return;
     }
+    mx = fmaxf(mx, sm);
+    if (a.smax) warp_max_to(sm, a.smax + j);
     if (tid == 0 && j + NS < L) {
       fence_proxy_async_smem();
       mbar_expect_tx(bar0 + 8 * stg, box_bytes);
@@ -195,6 +198,7 @@ struct FieldView {
   int64_t vstride;
   float* vp;
   uint8_t* arg;
+  unsigned* smax;
   unsigned* status;
 };
 
@@ -217,6 +221,15 @@ __device__ __forceinline__ void ring_init(Ring& rg, unsigned char* smem, const S
 // Marches box (bx, by) of a field through its snapshots; mx collects the
 // running maximum.  Returns false (after flagging and draining, bounded) if a
 // stage never completed; the caller must then leave.
+// Running maximum over one tile row, two pixels per three-input max.
+template <int W>
+__device__ __forceinline__ float row_max(float m, const float* xn) {
+#pragma unroll
+  for (int q = 0; q + 1 < W; q += 2) m = max3f(m, xn[q], xn[q + 1]);
+  if (W & 1) m = fmaxf(m, xn[W - 1]);
+  return m;
+}
+
 template <typename T, int W, bool SIGNED>
 __device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const FieldView& f, int bx,
                                             int by, int tby, Ring& rg, unsigned char* smem,
@@ -251,29 +264,46 @@ __device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const Field
   for (int j = 0; j < L; ++j) {
     const bool ok = mbar_wait_bounded(rg.bar0 + 8 * rg.stg, rg.phase, deadline);
     const T* st = reinterpret_cast<const T*>(smem + (size_t)rg.stg * rg.stage_bytes) + off;
+    float sm = -INFINITY;   // this snapshot's maximum over the thread's pixels
     if (ok) {
       if (j >= 2) {
+        // Row partials first, then the rows in order: short dependency chains
+        // (the sums, the maximum with its first position in row-major order,
+        // and the running maximum M would otherwise be W*W long).
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
         int am = 0;   // first maximum in row-major order (strict >)
 #pragma unroll
         for (int r = 0; r < W; ++r) {
+          float r1 = 0.f, r3 = 0.f, rm = 0.f;
+          int ri = 0;
+          float xr[W];
+#pragma unroll
+          for (int q = 0; q < W; ++q) xr[q] = to_f32(st[r * (32 * W) + q]);
+          sm = row_max<W>(sm, xr);
 #pragma unroll
           for (int q = 0; q < W; ++q) {
             const int i = r * W + q;
-            const float xn = to_f32(st[r * (32 * W) + q]);
-            mx = fmaxf(mx, xn);
+            const float xn = xr[q];
             const float dn = fabsf(xn - xp[i]);
             const float d = fabsf(dn - dp[i]);
             const float ref = SIGNED ? xp[i] : fabsf(xp[i]);
             const float xh = (xp[i] == 0.f) ? kGuardC : ref;
-            s1 += d;
-            if (d > s2) {
-              s2 = d;
-              am = i;
+            r1 += d;
+            if (d > rm) {
+              rm = d;
+              ri = q;
             }
-            s3 += fminf(__fdividef(d, xh), 1.f);
+            // r = min(Delta / x-hat, 1); with x-hat = |x| >= 0 the quotient is
+            // never negative, so the multiply's saturation to [0, 1] clamps it
+            r3 += SIGNED ? fminf(__fdividef(d, xh), 1.f) : __saturatef(__fdividef(d, xh));
             dp[i] = dn;
             xp[i] = xn;
+          }
+          s1 += r1;
+          s3 += r3;
+          if (rm > s2) {
+            s2 = rm;
+            am = r * W + ri;
           }
         }
         if (live) {
@@ -289,7 +319,7 @@ __device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const Field
           for (int q = 0; q < W; ++q) {
             const int i = r * W + q;
             const float xn = to_f32(st[r * (32 * W) + q]);
-            mx = fmaxf(mx, xn);
+            sm = fmaxf(sm, xn);
             dp[i] = fabsf(xn - xp[i]);
             xp[i] = xn;
           }
@@ -312,6 +342,8 @@ __device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const Field
       }
       return false;
     }
+    mx = fmaxf(mx, sm);
+    if (f.smax) warp_max_to(sm, f.smax + j);
     if (tid == 0 && j + rg.NS < L) {
       fence_proxy_async_smem();
       mbar_expect_tx(rg.bar0 + 8 * rg.stg, rg.box_bytes);
@@ -349,6 +381,7 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_stack_small(const __grid_c
   f.vstride = a.vstride;
   f.vp = a.vp;
   f.arg = a.arg;
+  f.smax = a.smax;
   f.status = a.status;
   float mx = -INFINITY;
   const uint64_t deadline = globaltimer_ns() + a.timeout_ns;
@@ -401,6 +434,7 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_stack_multi(const FieldDes
     f.vstride = d.vstride;
     f.vp = d.vp;
     f.arg = d.arg;
+    f.smax = d.smax;
     f.status = d.status;
     float mx = -INFINITY;
     if (!march_small<T, W, SIGNED>(&d.tmap, f, (int)(b % d.gridX), (int)(b / d.gridX), g.TBY, rg,

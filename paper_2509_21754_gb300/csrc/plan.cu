@@ -60,7 +60,11 @@ struct fitrig_plan_s {
   int storage = FITRIG_F32, noise = FITRIG_NOISE_MEANSTD, rmode = FITRIG_RMODE_ABS;
   int edge = FITRIG_EDGE_PARTIAL;
   int stride = FITRIG_STRIDE_TILE;
+  int mmode = FITRIG_MMODE_GLOBAL;
   int autotune = 0;
+  int64_t max_selected = 0;  // 0: automatic selection capacity
+  int64_t auto_selected = 0; // the automatic capacity after growing (0: default)
+  int64_t sel_bytes = 0;     // device bytes of the selection lists
   bool ring = false;       // serving field: the stack is a ring of L slots
   int64_t bytes = 0;       // device bytes allocated by the plan
   int zrot = 0;            // slot of the current unit's first snapshot
@@ -98,15 +102,21 @@ struct fitrig_plan_s {
   fitrig_candidate* d_cand = nullptr;
   fitrig_candidate* d_cand_tmp = nullptr;
   int64_t cand_cap = 0;
-  float* d_eta = nullptr;
+  float* d_eta = nullptr;        // slot U of d_vp (frequency branch)
   int* d_bin = nullptr;
   float2* d_tw = nullptr;
   void* d_staging = nullptr;
   float* d_report = nullptr;
+  unsigned* d_smax = nullptr;    // running M: [2L] per-snapshot maximum keys
+  double* d_mrun = nullptr;      // running M: [units] normaliser of each unit
+  float* d_wts = nullptr;        // running M: [units] frequency-series weights
   unsigned* h_pinned = nullptr;   // [0..3] readback words
   CUtensorMap tmap;
   cudaEvent_t ev[2 * FITRIG_KERNEL_COUNT] = {};
   float ms[FITRIG_KERNEL_COUNT] = {};
+  // host-to-device pushes are split over these streams (several copy engines)
+  cudaStream_t copy_st[4] = {};
+  cudaEvent_t copy_ev[5] = {};
 };
 
 #define CK(expr)                                   \
@@ -120,16 +130,26 @@ struct fitrig_plan_s {
 
 static cudaStream_t plan_stream(fitrig_plan_t p) { return p->stream ? p->stream : p->own_stream; }
 
+// Selected tiles one detect can hold (also the candidate capacity).  The
+// automatic capacity starts at 1/12 of all tiles of all units plus 4 Mi and
+// grows when a detect needs more (the median/MAD trigger on dirty-image stacks
+// selects 5-11% of tiles at 6 sigma: the statistic's right tail is heavy); an
+// explicit MAX_SELECTED is a hard limit (ETRUNC beyond it).  Capped by the tile
+// count and by the int32 list indices.
 static int select_capacity(fitrig_plan_t p) {
   const int64_t all = (int64_t)p->units * p->T;
-  const int64_t cap = std::min<int64_t>(all, (int64_t)(4 << 20) + all / 64);
+  int64_t cap = p->max_selected > 0    ? p->max_selected
+                : p->auto_selected > 0 ? p->auto_selected
+                                       : (int64_t)(4 << 20) + all / 12;
+  cap = std::min<int64_t>(std::min<int64_t>(cap, all), (int64_t)INT32_MAX - 1);
   return (int)std::max<int64_t>(cap, 1);
 }
 
 static void free_all(fitrig_plan_t p) {
   void* ptrs[] = {p->d_stack, p->d_vp,  p->d_small, p->d_invalid,  p->d_cs, p->d_arg, p->d_inv,
                   p->d_thr,   p->d_noise, p->d_sel, p->d_cand,     p->d_cand_tmp,
-                  p->d_eta,   p->d_bin, p->d_tw,    p->d_staging,  p->d_report};
+                  p->d_bin,   p->d_tw,  p->d_staging, p->d_report,
+                  p->d_smax,  p->d_mrun, p->d_wts};   // d_eta lives inside d_vp
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->h_pinned) cudaFreeHost(p->h_pinned);
@@ -190,7 +210,7 @@ static int run_autotune(int w, int storage, int* tby_out, int* ns_out, float* ms
         rc = FITRIG_ECUDA;
         break;
       }
-      StackArgs sa;
+      StackArgs sa{};   // every field starts zeroed (null pointers)
       sa.nx = nx;
       sa.ny = ny;
       sa.nsnap = L;
@@ -263,6 +283,60 @@ static cudaError_t dmalloc(fitrig_plan_t p, Ptr** ptr, size_t bytes) {
   return e;
 }
 
+// Selection lists, the dense map of list indices and the candidate buffers,
+// sized by select_capacity(); replaces any earlier ones.
+static int alloc_select(fitrig_plan_t p) {
+  void* old[] = {p->d_sel, p->d_cand, p->d_cand_tmp};
+  for (void* q : old)
+    if (q) cudaFree(q);
+  p->bytes -= p->sel_bytes;
+  p->sel_bytes = 0;
+  p->d_sel = nullptr;
+  p->d_cand = nullptr;
+  p->d_cand_tmp = nullptr;
+  const int64_t b0 = p->bytes;
+  const int U = p->units;
+  SelectScratch& s = p->sel;
+  s.nblk = 152 * 8;
+  s.capacity = select_capacity(p);
+  const size_t cap = (size_t)s.capacity;
+  size_t bytes = 0;
+  auto carve = [&](size_t n) {
+    const size_t off = bytes;
+    bytes += (n + 255) / 256 * 256;
+    return off;
+  };
+  const size_t o_cnt = carve(sizeof(int) * s.nblk * 8), o_off = carve(sizeof(int) * (s.nblk * 8 + 1));
+  const size_t o_items = carve(sizeof(SelItem) * cap), o_nsel = carve(sizeof(int));
+  const size_t o_par = carve(sizeof(int) * cap), o_cm = carve(sizeof(unsigned long long) * cap);
+  const size_t o_pk = carve(sizeof(int) * cap);
+  const size_t o_pl = carve(sizeof(int) * cap), o_np = carve(sizeof(int));
+  // bitmap words over the element space units * vstride (whole 128-element
+  // blocks, as the compaction writes them)
+  const size_t nwords = ((size_t)std::max<int64_t>(1, (int64_t)U * p->vstride) + 127) / 128 * 4;
+  const size_t o_bits = carve(sizeof(uint32_t) * nwords), o_wb = carve(sizeof(int) * nwords);
+  CK(dmalloc(p, &p->d_sel, bytes));
+  CK(cudaMemset(p->d_sel, 0, bytes));
+  char* b = static_cast<char*>(p->d_sel);
+  s.blkcnt = reinterpret_cast<int*>(b + o_cnt);
+  s.blkoff = reinterpret_cast<int*>(b + o_off);
+  s.items = reinterpret_cast<SelItem*>(b + o_items);
+  s.nsel = reinterpret_cast<int*>(b + o_nsel);
+  s.parent = reinterpret_cast<int*>(b + o_par);
+  s.compmax = reinterpret_cast<unsigned long long*>(b + o_cm);
+  s.peak = reinterpret_cast<int*>(b + o_pk);
+  s.plist = reinterpret_cast<int*>(b + o_pl);
+  s.npeak = reinterpret_cast<int*>(b + o_np);
+  s.want = p->d_small + 3;
+  s.bits = reinterpret_cast<uint32_t*>(b + o_bits);
+  s.wbase = reinterpret_cast<int*>(b + o_wb);
+  p->cand_cap = s.capacity;
+  CK(dmalloc(p, &p->d_cand, sizeof(fitrig_candidate) * cap));
+  CK(dmalloc(p, &p->d_cand_tmp, sizeof(fitrig_candidate) * cap));
+  p->sel_bytes = p->bytes - b0;
+  return FITRIG_OK;
+}
+
 static int allocate(fitrig_plan_t p) {
   if (p->allocated) return FITRIG_OK;
   const int eb = elem_bytes(p->storage);
@@ -294,8 +368,12 @@ static int allocate(fitrig_plan_t p) {
   const int U = p->units;
   p->vstride = (p->T + 3) / 4 * 4;
   CK(dmalloc(p, &p->d_stack, p->slice_bytes * p->L));
-  CK(dmalloc(p, &p->d_vp, sizeof(float) * (size_t)U * p->vstride));
-  CK(cudaMemset(p->d_vp, 0xff, sizeof(float) * (size_t)U * p->vstride));   // NaN padding
+  // with the frequency branch, eta is one more slot after the U units, so that
+  // both branches' noise estimates run as one launch over U + 1 groups
+  const int vslots = (p->branch & FITRIG_BRANCH_FREQ) ? U + 1 : U;
+  CK(dmalloc(p, &p->d_vp, sizeof(float) * (size_t)vslots * p->vstride));
+  CK(cudaMemset(p->d_vp, 0xff, sizeof(float) * (size_t)vslots * p->vstride));   // NaN padding
+  if (p->branch & FITRIG_BRANCH_FREQ) p->d_eta = p->d_vp + (size_t)U * p->vstride;
   if (p->stride == FITRIG_STRIDE_TILE && p->geom.R == 0)
     CK(dmalloc(p, &p->d_arg, (size_t)U * p->vstride));
   CK(dmalloc(p, &p->d_inv, sizeof(double) * (U + 1)));
@@ -305,49 +383,18 @@ static int allocate(fitrig_plan_t p) {
   CK(dmalloc(p, &p->d_thr, sizeof(float) * (U + 1)));
   const int nblk_img = std::max(1, std::min(1024, (152 * 4 + U - 1) / U));
   const int nblk_freq = 152 * 4;
-  const size_t nb = std::max(noise_scratch_bytes(U, nblk_img), noise_scratch_bytes(1, nblk_freq));
+  const size_t nb =
+      std::max(noise_scratch_bytes(U + 1, nblk_img), noise_scratch_bytes(1, nblk_freq));
   CK(dmalloc(p, &p->d_noise, nb));
-  noise_scratch_carve(p->d_noise, U, nblk_img, &p->ns_img);
+  noise_scratch_carve(p->d_noise, U + 1, nblk_img, &p->ns_img);
   noise_scratch_carve(p->d_noise, 1, nblk_freq, &p->ns_freq);
   p->ns_img.invalid = p->d_invalid;
   p->ns_freq.invalid = p->d_invalid;
-  // selection lists
-  SelectScratch& s = p->sel;
-  s.nblk = 152 * 8;
-  s.capacity = select_capacity(p);
-  const size_t cap = (size_t)s.capacity;
-  size_t bytes = 0;
-  auto carve = [&](size_t n) {
-    const size_t off = bytes;
-    bytes += (n + 255) / 256 * 256;
-    return off;
-  };
-  const size_t o_cnt = carve(sizeof(int) * s.nblk * 8), o_off = carve(sizeof(int) * (s.nblk * 8 + 1));
-  const size_t o_items = carve(sizeof(SelItem) * cap), o_nsel = carve(sizeof(int));
-  const size_t o_par = carve(sizeof(int) * cap), o_cm = carve(sizeof(unsigned long long) * cap);
-  const size_t o_pk = carve(sizeof(int) * cap);
-  const size_t o_pl = carve(sizeof(int) * cap), o_np = carve(sizeof(int));
-  const size_t map_n = (size_t)std::max<int64_t>(1, (int64_t)U * p->vstride);
-  const size_t o_map = carve(sizeof(int) * map_n);
-  CK(dmalloc(p, &p->d_sel, bytes));
-  CK(cudaMemset(p->d_sel, 0, bytes));
-  char* b = static_cast<char*>(p->d_sel);
-  s.blkcnt = reinterpret_cast<int*>(b + o_cnt);
-  s.blkoff = reinterpret_cast<int*>(b + o_off);
-  s.items = reinterpret_cast<SelItem*>(b + o_items);
-  s.nsel = reinterpret_cast<int*>(b + o_nsel);
-  s.parent = reinterpret_cast<int*>(b + o_par);
-  s.compmax = reinterpret_cast<unsigned long long*>(b + o_cm);
-  s.peak = reinterpret_cast<int*>(b + o_pk);
-  s.plist = reinterpret_cast<int*>(b + o_pl);
-  s.npeak = reinterpret_cast<int*>(b + o_np);
-  s.map = reinterpret_cast<int*>(b + o_map);
-  p->cand_cap = s.capacity;
-  CK(dmalloc(p, &p->d_cand, sizeof(fitrig_candidate) * cap));
-  CK(dmalloc(p, &p->d_cand_tmp, sizeof(fitrig_candidate) * cap));
+  {
+    const int rc = alloc_select(p);
+    if (rc != FITRIG_OK) return rc;
+  }
   if (p->branch & FITRIG_BRANCH_FREQ) {
-    CK(dmalloc(p, &p->d_eta, sizeof(float) * p->vstride));
-    CK(cudaMemset(p->d_eta, 0xff, sizeof(float) * p->vstride));   // NaN padding
     CK(dmalloc(p, &p->d_bin, sizeof(int) * p->T));
     const int n = U, H = (n - 1) / 2, K = n / 2;
     std::vector<float2> tw((size_t)std::max(1, K * H));
@@ -358,6 +405,11 @@ static int allocate(fitrig_plan_t p) {
       }
     CK(dmalloc(p, &p->d_tw, sizeof(float2) * tw.size()));
     CK(cudaMemcpy(p->d_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+  }
+  if (p->mmode == FITRIG_MMODE_RUNNING) {
+    CK(dmalloc(p, &p->d_smax, sizeof(unsigned) * 2 * p->L));
+    CK(dmalloc(p, &p->d_mrun, sizeof(double) * U));
+    CK(dmalloc(p, &p->d_wts, sizeof(float) * U));
   }
   CK(cudaMallocHost(&p->h_pinned, 64));
   for (int i = 0; i < 2 * FITRIG_KERNEL_COUNT; ++i)
@@ -450,6 +502,16 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t p, int option, int64_t value) {
       if (p->allocated) return FITRIG_ESTATE;
       p->autotune = value != 0;
       return FITRIG_OK;
+    case FITRIG_OPT_MAX_SELECTED: {
+      if (value < 0 || value >= INT32_MAX) return FITRIG_EINVAL;
+      p->max_selected = value;
+      if (!p->allocated) return FITRIG_OK;
+      // resize the selection lists now; the pushed stack stays
+      CK(cudaSetDevice(p->device));
+      CK(cudaStreamSynchronize(plan_stream(p)));
+      p->detected = false;
+      return alloc_select(p);
+    }
     case FITRIG_OPT_TIMEOUT_NS:
       if (value <= 0) return FITRIG_EINVAL;
       p->timeout_ns = (uint64_t)value;
@@ -470,6 +532,10 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t p, int option, int64_t value) {
     case FITRIG_OPT_RMODE:
       if (value != FITRIG_RMODE_ABS && value != FITRIG_RMODE_SIGNED) return FITRIG_EINVAL;
       p->rmode = (int)value;
+      return FITRIG_OK;
+    case FITRIG_OPT_MMODE:
+      if (value != FITRIG_MMODE_GLOBAL && value != FITRIG_MMODE_RUNNING) return FITRIG_EINVAL;
+      p->mmode = (int)value;
       return FITRIG_OK;
     case FITRIG_OPT_STRIDE:
       if (value == FITRIG_STRIDE_TILE) {
@@ -514,6 +580,51 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t p, int option, int64_t value) {
   }
 }
 
+// Host-to-device copy of ny rows of `width` bytes, ordered on `st`.  Large
+// snapshots are split into row bands copied on up to four side streams, so
+// that several copy engines move them at once; the bands start after the work
+// already on `st` and `st` waits for all of them.  A copy whose rows are
+// contiguous on both sides goes as one linear copy per band.
+static cudaError_t copy_rows_h2d(fitrig_plan_t p, void* dst, size_t dpitch, const void* src,
+                                 size_t spitch, size_t width, cudaStream_t st) {
+  const int ny = p->ny;
+  const size_t bytes = width * (size_t)ny;
+  const bool linear = dpitch == width && spitch == width;
+  int nb = bytes >= ((size_t)32 << 20) ? 4 : 1;
+  if (nb > 1 && !p->copy_st[0]) {
+    for (int i = 0; i < 4; ++i) {
+      cudaError_t e = cudaStreamCreateWithFlags(&p->copy_st[i], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+    for (int i = 0; i < 5; ++i) {
+      cudaError_t e = cudaEventCreateWithFlags(&p->copy_ev[i], cudaEventDisableTiming);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  if (nb == 1) {
+    if (linear)
+      return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, ny, cudaMemcpyHostToDevice, st);
+  }
+  cudaError_t e = cudaEventRecord(p->copy_ev[4], st);
+  const int band = (ny + nb - 1) / nb;
+  for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+    const int r0 = i * band, r1 = std::min(ny, r0 + band);
+    if (r0 >= r1) break;
+    cudaStream_t cs = p->copy_st[i];
+    e = cudaStreamWaitEvent(cs, p->copy_ev[4], 0);
+    char* d = static_cast<char*>(dst) + (size_t)r0 * dpitch;
+    const char* s = static_cast<const char*>(src) + (size_t)r0 * spitch;
+    if (e == cudaSuccess)
+      e = linear ? cudaMemcpyAsync(d, s, width * (size_t)(r1 - r0), cudaMemcpyHostToDevice, cs)
+                 : cudaMemcpy2DAsync(d, dpitch, s, spitch, width, r1 - r0,
+                                     cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(p->copy_ev[i], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->copy_ev[i], 0);
+  }
+  return e;
+}
+
 FITRIG_API int fitrig_push_snapshot(fitrig_plan_t p, const void* data, int dtype, int on_device,
                                     int64_t row_pitch_elems) {
   if (!p || !data) return FITRIG_EINVAL;
@@ -528,15 +639,19 @@ FITRIG_API int fitrig_push_snapshot(fitrig_plan_t p, const void* data, int dtype
   const int eb = elem_bytes(p->storage), ib = elem_bytes(dtype);
   char* dst = p->d_stack + p->slice_bytes * p->pushed;
   if (dtype == p->storage) {
-    CK(cudaMemcpy2DAsync(dst, p->pitch * eb, data, rp * ib, (size_t)p->nx * ib, p->ny,
-                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (on_device)
+      CK(cudaMemcpy2DAsync(dst, p->pitch * eb, data, rp * ib, (size_t)p->nx * ib, p->ny,
+                           cudaMemcpyDeviceToDevice, st));
+    else
+      CK(copy_rows_h2d(p, dst, (size_t)p->pitch * eb, data, (size_t)rp * ib, (size_t)p->nx * ib,
+                       st));
   } else {
     const void* src = data;
     int64_t sp = rp;
     if (!on_device) {
       if (!p->d_staging) CK(dmalloc(p, &p->d_staging, (size_t)p->nx * p->ny * 4));
-      CK(cudaMemcpy2DAsync(p->d_staging, (size_t)p->nx * ib, data, rp * ib, (size_t)p->nx * ib,
-                           p->ny, cudaMemcpyHostToDevice, st));
+      CK(copy_rows_h2d(p, p->d_staging, (size_t)p->nx * ib, data, (size_t)rp * ib,
+                       (size_t)p->nx * ib, st));
       src = p->d_staging;
       sp = p->nx;
     }
@@ -569,11 +684,13 @@ static cudaError_t enqueue_clear(fitrig_plan_t p, cudaStream_t st) {
   cudaError_t e = p->ring ? cudaMemsetAsync(p->d_small + 1, 0, 12, st)
                           : cudaMemsetAsync(p->d_small, 0, 16, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(p->d_invalid, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess && p->d_smax)
+    e = cudaMemsetAsync(p->d_smax, 0, sizeof(unsigned) * 2 * p->L, st);
   return e;
 }
 
 static cudaError_t enqueue_march(fitrig_plan_t p, cudaStream_t st) {
-  StackArgs a;
+  StackArgs a{};
   a.nx = p->nxu;
   a.ny = p->nyu;
   a.nsnap = p->pushed;
@@ -585,11 +702,12 @@ static cudaError_t enqueue_march(fitrig_plan_t p, cudaStream_t st) {
   a.arg = p->d_arg;
   a.zrot = p->zrot;
   a.gmax = p->d_small;
+  a.smax = p->d_smax;
   a.status = p->d_small + 1;
   a.timeout_ns = p->timeout_ns;
   a.g = p->geom;
   if (p->stride == FITRIG_STRIDE_SLIDING) {
-    SlideArgs sa;
+    SlideArgs sa{};
     sa.zrot = p->zrot;
     sa.nx = p->nx;
     sa.ny = p->ny;
@@ -597,6 +715,7 @@ static cudaError_t enqueue_march(fitrig_plan_t p, cudaStream_t st) {
     sa.vstride = p->vstride;
     sa.vp = p->d_vp;
     sa.gmax = p->d_small;
+    sa.smax = p->d_smax;
     sa.status = p->d_small + 1;
     sa.timeout_ns = p->timeout_ns;
     sa.g = p->sgeom;
@@ -618,7 +737,7 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
   auto mark = [&](int k, int end) {
     if (timed) cudaEventRecord(p->ev[2 * k + end], st);
   };
-  CandArgs ca;
+  CandArgs ca{};
   ca.nx = p->nxu;
   ca.ny = p->nyu;
   ca.w = p->stride == FITRIG_STRIDE_SLIDING ? 1 : p->w;   // pixels are 1 x 1 tiles
@@ -639,23 +758,37 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
   ca.nout = nout;
   ca.cap = p->cand_cap;
   // frequency branch first: its candidates (snapshot -1) lead the sorted list
+  if (p->d_smax)
+    CKE(launch_running_norm(p->d_stack, p->storage, p->pushed, p->nyu, p->nxu, p->pitch, p->d_smax,
+                            p->d_mrun, p->d_wts, st));
+  const bool both = (p->branch & FITRIG_BRANCH_FREQ) && (p->branch & FITRIG_BRANCH_IMAGE);
   if (p->branch & FITRIG_BRANCH_FREQ) {
     mark(FITRIG_KERNEL_SPECTRUM, 0);
-    CKE(launch_spectrum(p->d_vp, U, p->T, p->vstride, p->d_tw, p->d_eta, p->d_bin, st));
+    CKE(launch_spectrum(p->d_vp, U, p->T, p->vstride, p->d_tw, p->d_wts, p->d_eta, p->d_bin, st));
     mark(FITRIG_KERNEL_SPECTRUM, 1);
     double* cs = p->d_cs + 2 * U;
-    CKE(launch_noise(p->d_eta, 1, p->vstride, p->T, p->noise, p->ns_freq, cs, st));
-    CKE(launch_thresholds(cs, 1, p->tau, p->d_thr + U, p->d_inv + U, st));
+    if (both) {
+      // both branches' estimates in one launch: the U units, then eta
+      mark(FITRIG_KERNEL_NOISE, 0);
+      CKE(launch_noise(p->d_vp, U + 1, p->vstride, p->T, p->noise, p->ns_img, p->d_cs, st));
+      CKE(launch_thresholds(p->d_cs, U + 1, p->tau, p->d_thr, p->d_inv, st));
+      mark(FITRIG_KERNEL_NOISE, 1);
+    } else {
+      CKE(launch_noise(p->d_eta, 1, p->vstride, p->T, p->noise, p->ns_freq, cs, st));
+      CKE(launch_thresholds(cs, 1, p->tau, p->d_thr + U, p->d_inv + U, st));
+    }
     CKE(launch_select(p->d_eta, 1, p->vstride, p->d_thr + U, cs, p->d_inv + U, p->sel, status, st));
     CKE(launch_components(p->Tx, p->Ty, p->vstride, p->sel, status, st));
     ca.branch = FITRIG_BRANCH_FREQ;
     CKE(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
   }
   if (p->branch & FITRIG_BRANCH_IMAGE) {
-    mark(FITRIG_KERNEL_NOISE, 0);
-    CKE(launch_noise(p->d_vp, U, p->vstride, p->T, p->noise, p->ns_img, p->d_cs, st));
-    CKE(launch_thresholds(p->d_cs, U, p->tau, p->d_thr, p->d_inv, st));
-    mark(FITRIG_KERNEL_NOISE, 1);
+    if (!both) {
+      mark(FITRIG_KERNEL_NOISE, 0);
+      CKE(launch_noise(p->d_vp, U, p->vstride, p->T, p->noise, p->ns_img, p->d_cs, st));
+      CKE(launch_thresholds(p->d_cs, U, p->tau, p->d_thr, p->d_inv, st));
+      mark(FITRIG_KERNEL_NOISE, 1);
+    }
     mark(FITRIG_KERNEL_SELECT, 0);
     CKE(launch_select(p->d_vp, U, p->vstride, p->d_thr, p->d_cs, p->d_inv, p->sel, status, st));
     CKE(launch_components(p->Tx, p->Ty, p->vstride, p->sel, status, st));
@@ -682,9 +815,42 @@ static int finish_detect(fitrig_plan_t p, int32_t* ncand) {
   p->detected_units = p->pushed - 2;
   if (ncand) *ncand = n;
   if (flags & kErrTimeout) return FITRIG_ETIMEOUT;
-  if (flags & (kErrCapacity | kErrCcLimit)) return FITRIG_ETRUNC;
+  if (flags & kErrCapacity) {
+    // the selection that did not fit: the capacity it would have needed
+    const unsigned want = p->h_pinned[3];
+    if (ncand) *ncand = (int32_t)std::min<unsigned>(want, (unsigned)INT32_MAX);
+    return FITRIG_ETRUNC;
+  }
+  if (flags & kErrCcLimit) return FITRIG_ETRUNC;
   if (invalid) return FITRIG_ENONFINITE;
   return FITRIG_OK;
+}
+
+// The capacity an overflowing selection of the last detect needed (0 when
+// everything fitted).
+static int64_t overflow_need(fitrig_plan_t p) {
+  return (p->h_pinned[1] & kErrCapacity) ? (int64_t)p->h_pinned[3] : 0;
+}
+
+// With the automatic capacity (MAX_SELECTED = 0): grow the selection lists to
+// what the last detect needed, with a margin.  The tile statistics of the
+// march stay valid, so only the post-processing has to run again.
+static int grow_select(fitrig_plan_t p) {
+  const int64_t need = overflow_need(p);
+  if (need <= 0 || p->max_selected != 0) return FITRIG_ETRUNC;
+  const int64_t all = (int64_t)p->units * p->T;
+  p->auto_selected = std::min<int64_t>(all, need + need / 4 + (1 << 20));
+  return alloc_select(p);
+}
+
+// Post-processing again after grow_select (status words and invalid counts
+// are cleared; M and the tile statistics are kept).
+static int repost(fitrig_plan_t p, cudaStream_t st, int32_t* ncand) {
+  CK(cudaMemsetAsync(p->d_small + 1, 0, 12, st));
+  CK(cudaMemsetAsync(p->d_invalid, 0, sizeof(unsigned long long), st));
+  CK(enqueue_post(p, st, true));
+  CK(cudaStreamSynchronize(st));
+  return finish_detect(p, ncand);
 }
 
 static int detect_ready(fitrig_plan_t p) {
@@ -713,7 +879,13 @@ FITRIG_API int fitrig_detect(fitrig_plan_t p, int32_t* ncand) {
     if (cudaEventElapsedTime(&ms, p->ev[2 * k], p->ev[2 * k + 1]) == cudaSuccess) p->ms[k] = ms;
     else (void)cudaGetLastError();
   }
-  return finish_detect(p, ncand);
+  rc = finish_detect(p, ncand);
+  if (rc == FITRIG_ETRUNC && overflow_need(p) > 0 && p->max_selected == 0) {
+    const int g = grow_select(p);
+    if (g != FITRIG_OK) return g;
+    rc = repost(p, st, ncand);
+  }
+  return rc;
 }
 
 // ---------------------------------------------------------------- batches
@@ -806,6 +978,18 @@ FITRIG_API int fitrig_global_max(fitrig_plan_t p, double* M) {
   return resolve_max(p, M);
 }
 
+FITRIG_API int fitrig_unit_normaliser(fitrig_plan_t p, int32_t unit, double* M) {
+  if (!p || !M) return FITRIG_EINVAL;
+  if (!p->detected) return FITRIG_ESTATE;
+  if (unit < 0 || unit >= p->detected_units) return FITRIG_EINVAL;
+  CK(cudaSetDevice(p->device));
+  if (!p->d_mrun) return resolve_max(p, M);
+  cudaStream_t st = plan_stream(p);
+  CK(cudaMemcpyAsync(M, p->d_mrun + unit, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return FITRIG_OK;
+}
+
 FITRIG_API int fitrig_tlisi(fitrig_plan_t p, int32_t unit, float* out, int32_t cap) {
   if (!p || !out) return FITRIG_EINVAL;
   if (!p->detected) return FITRIG_ESTATE;
@@ -817,7 +1001,8 @@ FITRIG_API int fitrig_tlisi(fitrig_plan_t p, int32_t unit, float* out, int32_t c
   if (rc != FITRIG_OK) return rc;
   cudaStream_t st = plan_stream(p);
   if (!p->d_report) CK(dmalloc(p, &p->d_report, sizeof(float) * p->T));
-  CK(launch_tlisi_from_values(p->d_vp + (size_t)unit * p->vstride, p->T, p->d_small, p->d_report,
+  CK(launch_tlisi_from_values(p->d_vp + (size_t)unit * p->vstride, p->T, p->d_small,
+                              p->d_mrun ? p->d_mrun + unit : nullptr, p->d_report,
                               st));
   return read_floats(p, p->d_report, p->T, out, cap);
 }
@@ -993,6 +1178,7 @@ FITRIG_API int fitrig_batch_create(const fitrig_plan_t* plans, int32_t nplans,
       d.vp = p->d_vp;
       d.arg = p->d_arg;
       d.gmax = p->d_small;
+      d.smax = p->d_smax;
       d.status = p->d_small + 1;
       d.nx = p->nxu;
       d.ny = p->nyu;
@@ -1034,10 +1220,16 @@ FITRIG_API int fitrig_batch_detect(fitrig_batch_t b, int32_t* ncand) {
     if (rc != FITRIG_OK) return rc;
   }
   if (!b->exec) {
-    // one eager pass (sets kernel attributes and checks every launch), then
-    // capture the same stream work once
+    // one eager pass (sets kernel attributes, checks every launch and sizes
+    // the selection lists), then capture the same stream work once
     CK(enqueue_batch(b, st));
     CK(cudaStreamSynchronize(st));
+    for (fitrig_plan_t p : b->plans) {
+      if (overflow_need(p) > 0 && p->max_selected == 0) {
+        const int g = grow_select(p);
+        if (g != FITRIG_OK) return g;
+      }
+    }
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const cudaError_t e = enqueue_batch(b, st);
@@ -1062,8 +1254,20 @@ FITRIG_API int fitrig_batch_detect(fitrig_batch_t b, int32_t* ncand) {
   cudaEventElapsedTime(&b->last_ms, b->ev0, b->ev1);
   int worst = FITRIG_OK;
   for (size_t k = 0; k < b->plans.size(); ++k) {
+    fitrig_plan_t p = b->plans[k];
     int32_t n = 0;
-    const int rc = finish_detect(b->plans[k], &n);
+    int rc = finish_detect(p, &n);
+    if (rc == FITRIG_ETRUNC && overflow_need(p) > 0 && p->max_selected == 0) {
+      // more selected tiles than on the first run: grow, finish this plan
+      // eagerly, and capture the graph again on the next call
+      const int g = grow_select(p);
+      if (g != FITRIG_OK) return g;
+      rc = repost(p, st, &n);
+      if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+      }
+    }
     ncand[b->order[k]] = n;
     if (rc != FITRIG_OK && (worst == FITRIG_OK || worst == FITRIG_ENONFINITE)) worst = rc;
   }
@@ -1436,6 +1640,10 @@ FITRIG_API int fitrig_plan_destroy(fitrig_plan_t p) {
   free_all(p);
   for (int i = 0; i < 2 * FITRIG_KERNEL_COUNT; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  for (cudaStream_t c : p->copy_st)
+    if (c) cudaStreamDestroy(c);
+  for (cudaEvent_t c : p->copy_ev)
+    if (c) cudaEventDestroy(c);
   if (p->own_stream) cudaStreamDestroy(p->own_stream);
   delete p;
   return FITRIG_OK;

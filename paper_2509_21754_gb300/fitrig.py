@@ -22,10 +22,12 @@ from . import build as _build
 OK, EINVAL, ENOMEM, ESTATE, ECUDA, ETIMEOUT, ETRUNC, ENONFINITE, EBUSY, EUNSUPPORTED = range(10)
 BRANCH_IMAGE, BRANCH_FREQ, BRANCH_BOTH = 1, 2, 3
 F32, BF16, F16 = 0, 1, 2
-OPT_STORAGE, OPT_NOISE, OPT_RMODE, OPT_EDGE, OPT_STRIDE, OPT_STREAM, OPT_TIMEOUT_NS = 1, 2, 3, 5, 6, 8, 9
-OPT_AUTOTUNE = 10
+OPT_STORAGE, OPT_NOISE, OPT_RMODE, OPT_MMODE, OPT_EDGE, OPT_STRIDE = 1, 2, 3, 4, 5, 6
+OPT_STREAM, OPT_TIMEOUT_NS = 8, 9
+OPT_AUTOTUNE, OPT_MAX_SELECTED = 10, 11
 NOISE_MEANSTD, NOISE_MEDMAD = 0, 1
 RMODE_ABS, RMODE_SIGNED = 0, 1
+MMODE_GLOBAL, MMODE_RUNNING = 0, 1
 EDGE_PARTIAL, EDGE_DROP = 0, 1
 STRIDE_TILE, STRIDE_SLIDING = 0, 1
 KERNEL_STACK, KERNEL_NOISE, KERNEL_SELECT, KERNEL_SPECTRUM, KERNEL_DETECT = range(5)
@@ -76,6 +78,7 @@ SIGNATURES = {
     "fitrig_noise_params": (c_int, [P, c_int32, POINTER(c_double), POINTER(c_double)]),
     "fitrig_spectrum": (c_int, [P, P, P, c_int32]),
     "fitrig_global_max": (c_int, [P, POINTER(c_double)]),
+    "fitrig_unit_normaliser": (c_int, [P, c_int32, POINTER(c_double)]),
     "fitrig_tile_grid": (c_int, [P, POINTER(c_int32), POINTER(c_int32)]),
     "fitrig_kernel_ms": (c_int, [P, c_int, POINTER(c_float)]),
     "fitrig_stack_device_ptr": (c_int, [P, c_int32, POINTER(P), POINTER(c_int64)]),
@@ -196,6 +199,10 @@ def fitrig_detect(plan) -> Tuple[int, int]:
     """Returns (status, ncand); raises unless status is OK or ENONFINITE."""
     n = c_int32()
     rc = load().fitrig_detect(plan, byref(n))
+    if rc == ETRUNC:
+        err = FitrigError(rc, "fitrig_detect")
+        err.needed = n.value   # the MAX_SELECTED that selection needed
+        raise err
     _check(rc, "fitrig_detect", allow=SOFT)
     return rc, n.value
 
@@ -251,6 +258,12 @@ def fitrig_spectrum(plan) -> Tuple[np.ndarray, np.ndarray]:
 def fitrig_global_max(plan) -> float:
     m = c_double()
     _check(load().fitrig_global_max(plan, byref(m)), "fitrig_global_max")
+    return m.value
+
+
+def fitrig_unit_normaliser(plan, unit: int) -> float:
+    m = c_double()
+    _check(load().fitrig_unit_normaliser(plan, unit, byref(m)), "fitrig_unit_normaliser")
     return m.value
 
 
@@ -399,11 +412,15 @@ class Plan:
 
     def __init__(self, nx, ny, nsnap, window, nsigma, branch=BRANCH_IMAGE, storage=F32,
                  noise=NOISE_MEANSTD, rmode=RMODE_ABS, edge=EDGE_PARTIAL, stream=None,
-                 stride=STRIDE_TILE, autotune=False):
+                 stride=STRIDE_TILE, autotune=False, max_selected=0, mmode=MMODE_GLOBAL):
         self.h = fitrig_plan_create(nx, ny, nsnap, window, nsigma, branch)
         try:
+            if mmode != MMODE_GLOBAL:
+                fitrig_plan_set(self.h, OPT_MMODE, mmode)
             if autotune:
                 fitrig_plan_set(self.h, OPT_AUTOTUNE, 1)
+            if max_selected:
+                fitrig_plan_set(self.h, OPT_MAX_SELECTED, max_selected)
             if stride != STRIDE_TILE:
                 fitrig_plan_set(self.h, OPT_STRIDE, stride)
             fitrig_plan_set(self.h, OPT_STORAGE, storage)
@@ -451,11 +468,12 @@ class Plan:
 def detect_stack(stack, window: int, nsigma: float, branch: int = BRANCH_IMAGE,
                  storage: int = F32, noise: int = NOISE_MEANSTD, rmode: int = RMODE_ABS,
                  edge: int = EDGE_PARTIAL, dumps: bool = True,
-                 stride: int = STRIDE_TILE, autotune: bool = False) -> dict:
+                 stride: int = STRIDE_TILE, autotune: bool = False,
+                 mmode: int = MMODE_GLOBAL) -> dict:
     """Push an (L, ny, nx) stack, detect, and read back candidates and dumps."""
     L, ny, nx = (int(d) for d in stack.shape)
     with Plan(nx, ny, L, window, nsigma, branch, storage, noise, rmode, edge,
-              stride=stride, autotune=autotune) as p:
+              stride=stride, autotune=autotune, mmode=mmode) as p:
         p.push_stack(stack)
         rc, cands = p.detect()
         out = {"status": rc, "candidates": cands}
@@ -463,6 +481,7 @@ def detect_stack(stack, window: int, nsigma: float, branch: int = BRANCH_IMAGE,
             ty, tx = fitrig_tile_grid(p.h)
             out["grid"] = (ty, tx)
             out["M"] = fitrig_global_max(p.h)
+            out["M_units"] = np.array([fitrig_unit_normaliser(p.h, s) for s in range(L - 2)])
             if branch & BRANCH_IMAGE:
                 out["values"] = np.stack([fitrig_unit_values(p.h, s) for s in range(L - 2)])
                 out["noise"] = np.array([fitrig_noise_params(p.h, s) for s in range(L - 2)])

@@ -74,6 +74,25 @@ C3 = StackSpec(nsnap=8, ny=50000, nx=50000, layout="meerkat_like", n_ant=64,
                n_pulsed=50, pulse_amp=None, pulse_period=(3, 16))
 
 
+def batched_fields(seed: int = 11, nfields: int = 256) -> List[Tuple[int, int]]:
+    """(nsnap, side) of the batched workload: square fields of side U{1024..8192}
+    with U{16..128} snapshots each (SKA-AA2-like PSF, see :func:`batched_spec`)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sides = rng.integers(1024, 8193, nfields)
+    nsnaps = rng.integers(16, 129, nfields)
+    return [(int(L), int(s)) for L, s in zip(nsnaps, sides)]
+
+
+def batched_spec(nsnap: int, side: int) -> StackSpec:
+    return small_spec(nsnap, side, side, layout="ska_aa2_like", n_ant=68)
+
+
+def serving_sides(seed: int = 7, nfields: int = 32) -> List[int]:
+    """Square field sides of the serving workload, U{2048..16384}."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [int(v) for v in rng.integers(2048, 16385, nfields)]
+
+
 def small_spec(nsnap: int, ny: int, nx: int, **kw) -> StackSpec:
     """A C2-like field of arbitrary size with source counts scaled by area."""
     area = ny * nx / float(4096 * 4096)
@@ -218,6 +237,32 @@ def beam_transfer(kind: str, n_ant: int, ny: int, nx: int, seed: int, fwhm_px: f
     H = grid / peak
     norm = float(np.sqrt(float((H * H * wcol).sum()) / n))   # Parseval
     return H.to(torch.float32), norm
+
+
+def iter_stack(spec: StackSpec, seed: int, device: str = "cpu"):
+    """Yield (k, snapshot) one FP32 snapshot at a time (same values as
+    make_stack), so that very large stacks never exist twice in memory."""
+    H, norm = beam_transfer(spec.layout, spec.n_ant, spec.ny, spec.nx, seed, spec.fwhm_px,
+                            device=device)
+    truth = draw_sources(spec, seed)
+    dev = torch.device(device)
+    steady = torch.zeros(spec.ny, spec.nx, dtype=torch.float32, device=dev)
+    if truth.steady:
+        sx, sy, sa = (torch.tensor(c, device=dev) for c in zip(*truth.steady))
+        steady.index_put_((sy.long(), sx.long()), sa.float(), accumulate=True)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed) * 7919 + 17)
+    for k in range(spec.nsnap):
+        img = torch.randn(spec.ny, spec.nx, generator=gen, device=dev, dtype=torch.float32)
+        img.mul_(1.0 / norm).add_(steady)
+        for x, y, a in truth.pulse_on(k):
+            img[y, x] += a
+        spec_k = torch.fft.rfft2(img)
+        del img
+        spec_k *= H
+        snap = torch.fft.irfft2(spec_k, s=(spec.ny, spec.nx))
+        del spec_k
+        yield k, snap
 
 
 def make_stack(spec: StackSpec, seed: int, device: str = "cpu",

@@ -264,3 +264,125 @@ def test_autotuned_shape_gives_identical_results(storage):
     b = F.detect_stack(stack.to(tdt), 5, 4.0, F.BRANCH_BOTH, storage=storage, autotune=True)
     assert a["values"].tobytes() == b["values"].tobytes()
     assert a["candidates"].tobytes() == b["candidates"].tobytes()
+
+
+def test_selection_capacity_truncates_loudly():
+    """A detect that selects more tiles than MAX_SELECTED returns ETRUNC; with
+    room for them the same stack gives the full candidate list."""
+    stack, _ = synth.make_stack(synth.small_spec(10, 200, 200), seed=5, device="cuda")
+    L, ny, nx = stack.shape
+    with F.Plan(nx, ny, L, 4, 2.0, F.BRANCH_IMAGE, noise=F.NOISE_MEDMAD) as p:
+        p.push_stack(stack)
+        rc, full = p.detect()
+        assert rc in (F.OK, F.ENONFINITE) and len(full) > 8
+    with F.Plan(nx, ny, L, 4, 2.0, F.BRANCH_IMAGE, noise=F.NOISE_MEDMAD, max_selected=8) as p:
+        p.push_stack(stack)
+        with pytest.raises(F.FitrigError) as e:
+            F.fitrig_detect(p.h)
+        assert e.value.status == F.ETRUNC and e.value.needed > 8
+        # resize in place to the reported need and detect again
+        F.fitrig_plan_set(p.h, F.OPT_MAX_SELECTED, e.value.needed)
+        rc, again = p.detect()
+        assert again.tobytes() == full.tobytes()
+    with F.Plan(nx, ny, L, 4, 2.0) as p:
+        with pytest.raises(F.FitrigError) as e:
+            F.fitrig_plan_set(p.h, F.OPT_MAX_SELECTED, -1)
+        assert e.value.status == F.EINVAL
+
+
+class _DeviceArray:
+    """A borrowed device buffer seen through the CUDA array interface."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": shape,
+                                         "typestr": typestr, "version": 2, "strides": None}
+
+
+def device_view(ptr, pitch, rows, tdt):
+    if tdt == torch.bfloat16:   # no array-interface code for bfloat16: view its bits
+        t = torch.as_tensor(_DeviceArray(ptr, (rows, pitch), "<i2"), device="cuda")
+        return t.view(torch.bfloat16)
+    code = {torch.float32: "<f4", torch.float16: "<f2"}[tdt]
+    return torch.as_tensor(_DeviceArray(ptr, (rows, pitch), code), device="cuda")
+
+
+@pytest.mark.parametrize("storage,host_dtype,pad", [(F.F32, torch.float32, 0),
+                                                   (F.F32, torch.float32, 96),
+                                                   (F.BF16, torch.float32, 0),
+                                                   (F.F16, torch.float16, 40)])
+def test_large_host_pushes_land_exactly(storage, host_dtype, pad):
+    """Snapshots of >= 32 MB from host memory go in row bands over several
+    streams; the stored stack equals the device-side conversion of the input."""
+    ny, nx, L = 4200, 4001, 3   # >= 32 MiB per snapshot in every case
+    x = torch.randn(L, ny, nx + pad, dtype=torch.float32).to(host_dtype).pin_memory()
+    tdt = {F.F32: torch.float32, F.BF16: torch.bfloat16, F.F16: torch.float16}[storage]
+    with F.Plan(nx, ny, L, 5, 4.0, storage=storage) as p:
+        for k in range(L):
+            F.fitrig_push_snapshot(p.h, x[k, :, :nx], row_pitch_elems=nx + pad)
+        torch.cuda.synchronize()
+        for k in range(L):
+            got = device_view(*F.fitrig_stack_device_ptr(p.h, k), ny, tdt)
+            want = x[k, :, :nx].cuda().to(tdt)
+            assert torch.equal(got[:, :nx], want), k
+
+
+def test_selection_lists_grow_automatically():
+    """A detect that selects more tiles than the starting capacity grows the
+    lists and gives the same result as a plan sized for every tile."""
+    stack = torch.randn(40, 2048, 2048, device="cuda")
+    L, ny, nx = stack.shape
+    w, tau = 2, 0.25
+    U, T = L - 2, (ny // w) * (nx // w)
+    with F.Plan(nx, ny, L, w, tau, F.BRANCH_IMAGE, noise=F.NOISE_MEDMAD) as p:
+        p.push_stack(stack)
+        rc, auto = p.detect()
+        rc2, again = p.detect()       # now within the grown capacity
+        selected = 0
+        for s in range(U):
+            c, sc = F.fitrig_noise_params(p.h, s)
+            v = F.fitrig_unit_values(p.h, s).astype(np.float64)
+            selected += int(np.count_nonzero(v > c + tau * sc))
+    assert selected > (4 << 20) + U * T // 12      # beyond the starting capacity
+    with F.Plan(nx, ny, L, w, tau, F.BRANCH_IMAGE, noise=F.NOISE_MEDMAD,
+                max_selected=U * T) as p:
+        p.push_stack(stack)
+        rc3, full = p.detect()
+    assert rc == rc2 == rc3
+    assert auto.tobytes() == full.tobytes() == again.tobytes()
+
+
+@pytest.mark.parametrize("stride", ["tile", "sliding"])
+def test_running_M_reading(stride):
+    """Real-time normaliser: unit s divided by the maximum of snapshots 0..s+2.
+    M_s, the reported tLISI, eta and both branches' candidates against the
+    oracle run with the same reading."""
+    spec = synth.small_spec(12, 150, 170, n_pulsed=3, pulse_period=(3, 4))
+    stack, _ = synth.make_stack(spec, seed=77, device="cuda")
+    ramp = torch.linspace(100.0, 700.0, stack.shape[0], device="cuda")
+    stack[:, 5, 7] = ramp                      # the maximum grows snapshot by snapshot
+    w, tau = (5, 3.0) if stride == "tile" else (3, 4.0)
+    st = F.STRIDE_TILE if stride == "tile" else F.STRIDE_SLIDING
+    res = F.detect_stack(stack, w, tau, F.BRANCH_BOTH, noise=F.NOISE_MEDMAD, stride=st,
+                         mmode=F.MMODE_RUNNING)
+    x = stack.cpu().numpy()
+    det = O.detect(x, w, tau, F.BRANCH_BOTH, "medmad", stride=stride, mmode="running")
+    assert list(res["M_units"]) == list(det.M_units)
+    assert len(set(det.M_units)) > 3           # the reading really differs from one M
+    assert res["M"] == det.M
+    di, dfq = F.decisions(res, tau)
+    if stride == "tile":
+        errs = C.compare(res["candidates"], x, w, tau, F.BRANCH_BOTH, "medmad", "abs",
+                         "partial", di, dfq, det)
+        assert not errs, errs[:10]
+    ok, worst = C.values_close(res["eta"], det.eta * det.M ** 2, rel=1e-4)
+    assert ok, worst
+    glob = F.detect_stack(stack, w, tau, F.BRANCH_IMAGE, noise=F.NOISE_MEDMAD, stride=st)
+    img = res["candidates"][res["candidates"]["snapshot"] >= 0]
+    assert img.tobytes() == glob["candidates"].tobytes()   # z does not see M_s
+    with F.Plan(170, 150, 12, w, tau, F.BRANCH_IMAGE, stride=st, mmode=F.MMODE_RUNNING) as p:
+        p.push_stack(stack)
+        p.detect()
+        for s in (0, 4, 9):
+            t = F.fitrig_tlisi(p.h, s)
+            ok, worst = C.values_close(t, det.tlisi[s], rel=1e-6)
+            assert ok, (s, worst)

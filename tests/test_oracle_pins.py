@@ -390,3 +390,72 @@ def test_sliding_pulse_lights_the_windows_around_it():
     assert sorted(c.snapshot for c in det.candidates) == [1, 3]
     for c in det.candidates:
         assert abs(c.y - 20) <= 2 and abs(c.x - 25) <= 2
+
+
+# ---------------------------------------------------------------- running M (real-time reading)
+def _spiked_stack(L=7, ny=12, nx=15, amps=None, seed=4):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0.0, 1.0, (L, ny, nx)).clip(-4.0, 4.0)
+    for k, a in enumerate(amps or []):
+        x[k, 0, 0] = a
+    return x
+
+
+def test_running_M_is_the_cumulative_maximum():
+    amps = [10.0 + k for k in range(7)]            # the spike grows every snapshot
+    det = O.detect(_spiked_stack(amps=amps), 3, 3.0, mmode="running")
+    # unit s sees snapshots 0..s+2, whose largest pixel is the spike of s+2
+    assert list(det.M_units) == [amps[s + 2] for s in range(5)]
+    assert det.M == amps[-1]
+    glob = O.detect(_spiked_stack(amps=amps), 3, 3.0)
+    assert list(glob.M_units) == [amps[-1]] * 5
+
+
+def test_running_equals_global_when_the_maximum_comes_first():
+    x = _spiked_stack(amps=[0.0, 50.0])            # the stack's maximum is in snapshot 1
+    a = O.detect(x, 3, 2.5, O.BRANCH_BOTH, mmode="running")
+    b = O.detect(x, 3, 2.5, O.BRANCH_BOTH)
+    assert np.array_equal(a.tlisi, b.tlisi, equal_nan=True)
+    assert [c.key() for c in a.candidates] == [c.key() for c in b.candidates]
+
+
+def test_running_M_leaves_image_candidates_unchanged():
+    # z uses one unit's tiles, so a per-unit constant M_s cancels (Sec. 2.4.1)
+    x = _spiked_stack(L=9, ny=30, nx=33, amps=[5.0 + 2 * k for k in range(9)], seed=9)
+    a = O.detect(x, 3, 2.0, mmode="running")
+    b = O.detect(x, 3, 2.0)
+    assert [c.key() for c in a.candidates] == [c.key() for c in b.candidates]
+    for ca, cb in zip(a.candidates, b.candidates):
+        assert ca.significance == pytest.approx(cb.significance, rel=1e-9)
+
+
+def test_running_M_series_spectrum_closed_form():
+    """Six snapshots give a 4-point series per tile; its DFT bins are
+    X1 = (y0 - y2) - i (y1 - y3) and X2 = y0 - y1 + y2 - y3."""
+    amps = [10.0, 10.5, 11.0, 12.0, 13.5, 15.0]
+    x = _spiked_stack(L=6, ny=9, nx=9, amps=amps, seed=21)
+    for mmode in ("global", "running"):
+        det = O.detect(x, 3, 1.0, O.BRANCH_FREQ, mmode=mmode)
+        for ty in range(3):
+            for tx in range(3):
+                y = det.tlisi[:, ty, tx]
+                x1 = math.hypot(y[0] - y[2], y[1] - y[3])
+                x2 = abs(y[0] - y[1] + y[2] - y[3])
+                assert det.eta[ty, tx] == pytest.approx(max(x1, x2), rel=1e-12, abs=1e-15)
+                assert det.eta_bin[ty, tx] == (1 if x1 >= x2 else 2)
+
+
+def test_running_M_brings_out_a_steady_tile_in_the_spectrum():
+    """A tile whose statistic v is the same in every unit has a flat series
+    under the global M (eta = 0) but not when M grows between units."""
+    L, w = 6, 2
+    x = np.full((L, 2, 4), 1.0)
+    x[:, 0, 2] = [0.0, 1.0, 1.0, 0.0, 0.0, 1.0]    # tile (0, 1): Delta = r = 1 in every unit
+    x[:, 1, 0] = [4.0, 4.0, 5.0, 6.0, 7.0, 8.0]    # tile (0, 0) carries the growing maximum
+    g = O.detect(x, w, 1.0, O.BRANCH_FREQ)
+    r = O.detect(x, w, 1.0, O.BRANCH_FREQ, mmode="running")
+    v = np.array([u.numerator[0, 1] for u in g.units])
+    assert np.all(v == v[0]) and v[0] > 0
+    assert g.eta[0, 1] == 0.0
+    assert list(r.M_units) == [5.0, 6.0, 7.0, 8.0]
+    assert r.eta[0, 1] > 0.0

@@ -23,7 +23,11 @@
  *     s = 1..L-2 shifted by one).
  *   - A plan is not thread-safe: use one plan per host thread.
  *   - All device work is issued on the plan's stream (FITRIG_OPT_STREAM);
- *     calls that return host-visible results synchronise that stream.
+ *     calls that return host-visible results synchronise that stream.  The
+ *     plan's own stream (the default) is a blocking stream: it is ordered with
+ *     the legacy default stream, so device buffers written there are complete
+ *     before a push reads them.  With another stream the caller orders the
+ *     producer of a pushed device buffer before the push.
  */
 #ifndef FITRIG_H_
 #define FITRIG_H_

@@ -243,10 +243,14 @@ cudaError_t launch_thresholds(const double* centre_scale, int groups, double tau
                               double* inv_scale, cudaStream_t st);
 
 // Selection / components / candidates.
+// One selected tile: its group (unit, or 0 for eta), tile index and value.
+// Within a group z = (v - centre) / scale is strictly increasing in v, so the
+// value orders the tiles of a component exactly; the FP64 significance is
+// computed for the candidates only.
 struct SelItem {
   int32_t group;
   int32_t t;
-  double z;
+  float v;
 };
 struct SelectScratch {
   int nblk;            // fixed grid of the ordered compaction
@@ -255,7 +259,7 @@ struct SelectScratch {
   SelItem* items;      // capacity entries
   int* nsel;           // device count
   int* parent;         // capacity
-  unsigned long long* compmax;  // capacity
+  unsigned* compmax;   // capacity: largest value key of each component
   int* peak;           // capacity
   uint32_t* bits;      // [nwords] selection bitmap over the element space groups * stride
   int* wbase;          // [nwords] list index of the first selected element of each word
@@ -268,7 +272,6 @@ struct SelectScratch {
 // order and map[g*stride + t] = list index + 1.  blkcnt/blkoff need nblk*8
 // entries (one per warp).
 cudaError_t launch_select(const float* vals, int groups, int64_t stride, const float* thr,
-                          const double* centre_scale, const double* inv_scale,
                           const SelectScratch& s, unsigned* status, cudaStream_t st);
 cudaError_t launch_count_selected(const float* vals, int groups, int64_t stride, const float* thr,
                                   int nblk, int* wcnt, long long* total, cudaStream_t st);
@@ -291,6 +294,9 @@ struct CandArgs {
   // freq branch
   const float* eta;
   const int* bin;
+  // significance z = (v - cs[2g]) * inv[g] in FP64 (per group g)
+  const double* cs;
+  const double* inv;
   fitrig_candidate* out;
   int* nout;
   int64_t cap;

@@ -111,8 +111,6 @@ template <bool VEC>
 __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restrict__ vals,
                                                            int groups, int64_t stride,
                                                            const float* __restrict__ thr,
-                                                           const double* __restrict__ cs,
-                                                           const double* __restrict__ inv,
                                                            int64_t chunk, const int* woff,
                                                            SelItem* items, uint32_t* sbits,
                                                            int* wbase, int64_t cap) {
@@ -175,7 +173,6 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restri
       }
     }
     if (bits) {
-      const double cg = cs[2 * g], ig = inv[g];
       for (int k = 0; k < step; ++k) {
         if (!(bits >> k & 1u)) continue;
         if (pos < cap) {
@@ -183,7 +180,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restri
           SelItem it;
           it.group = g;
           it.t = (int32_t)(e - (int64_t)g * stride);
-          it.z = ((double)v[k] - cg) * ig;
+          it.v = v[k];
           items[pos] = it;
         }
         ++pos;
@@ -203,22 +200,21 @@ static bool sel_vec(const float* vals, int64_t stride) {
 }
 
 cudaError_t launch_select(const float* vals, int groups, int64_t stride, const float* thr,
-                          const double* cs, const double* inv, const SelectScratch& s,
-                          unsigned* status, cudaStream_t st) {
+                          const SelectScratch& s, unsigned* status, cudaStream_t st) {
   const int nw = s.nblk * (kSelThreads / 32);
   const int64_t chunk = sel_chunk((int64_t)groups * stride, nw);
   if (sel_vec(vals, stride)) {
     k_sel_count<true><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk, s.blkcnt);
     k_scan_blocks<<<1, 1024, 0, st>>>(nw, s.blkcnt, s.blkoff, s.nsel, s.capacity, status,
                                       s.want);
-    k_sel_write<true><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, cs, inv, chunk,
+    k_sel_write<true><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk,
                                                       s.blkoff, s.items, s.bits, s.wbase,
                                                       s.capacity);
   } else {
     k_sel_count<false><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk, s.blkcnt);
     k_scan_blocks<<<1, 1024, 0, st>>>(nw, s.blkcnt, s.blkoff, s.nsel, s.capacity, status,
                                       s.want);
-    k_sel_write<false><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, cs, inv, chunk,
+    k_sel_write<false><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk,
                                                        s.blkoff, s.items, s.bits, s.wbase,
                                                        s.capacity);
   }
@@ -296,11 +292,11 @@ __device__ void unite(int* parent, int a, int b, unsigned* status) {
   atomicOr(status, kErrCcLimit);
 }
 
-__global__ void k_cc_init(const int* nsel, int* parent, unsigned long long* compmax, int* peak) {
+__global__ void k_cc_init(const int* nsel, int* parent, unsigned* compmax, int* peak) {
   const int n = *nsel;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     parent[i] = i;
-    compmax[i] = 0ull;
+    compmax[i] = 0u;
     peak[i] = INT_MAX;
   }
 }
@@ -394,10 +390,10 @@ __global__ void k_cc_flatten(const int* nsel, int* parent) {
 }
 
 __global__ void k_cc_peak(const SelItem* __restrict__ items, const int* nsel, const int* parent,
-                          unsigned long long* compmax, int* peak, int stage) {
+                          unsigned* compmax, int* peak, int stage) {
   const int n = *nsel;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const unsigned long long k = f64_key(items[i].z);
+    const unsigned k = f32_key(items[i].v);   // a component lies in one group
     const int r = parent[i];
     if (stage == 0) atomicMax(&compmax[r], k);
     else if (k == compmax[r]) atomicMin(&peak[r], i);
@@ -479,6 +475,12 @@ __device__ __forceinline__ float parabola(float l, float c, float r) {
   return fminf(0.5f, fmaxf(-0.5f, d));
 }
 
+// The candidate's significance, z = (v - centre) / scale in FP64 (Sec. 2.4.1,
+// 2.4.2), rounded to FP32 for the output.
+__device__ __forceinline__ float significance(const CandArgs& a, const SelItem& it) {
+  return (float)(((double)it.v - a.cs[2 * it.group]) * a.inv[it.group]);
+}
+
 // Frequency branch: one thread per peak; tile-centre order is (y, x) order,
 // so the peaks' list order is already the output order.
 __global__ void k_emit_freq(CandArgs a, const SelItem* __restrict__ items, const int* np_,
@@ -497,7 +499,7 @@ __global__ void k_emit_freq(CandArgs a, const SelItem* __restrict__ items, const
     c.x = tx * a.w + (ww - 1) / 2;
     c.y = ty * a.w + (hw - 1) / 2;
     c.snapshot = -1;
-    c.significance = (float)it.z;
+    c.significance = significance(a, it);
     c.branch = FITRIG_BRANCH_FREQ;
     c.freq_bin = a.bin[it.t];
     c.xf = (float)(tx * a.w) + 0.5f * (float)(ww - 1) + parabola(el, e, er) * (float)a.w;
@@ -506,13 +508,13 @@ __global__ void k_emit_freq(CandArgs a, const SelItem* __restrict__ items, const
   }
 }
 
-__device__ __forceinline__ fitrig_candidate image_candidate(const SelItem& it, int tx, int ty,
-                                                            int w, int dx, int dy) {
+__device__ __forceinline__ fitrig_candidate image_candidate(const CandArgs& a, const SelItem& it,
+                                                            int tx, int ty, int w, int dx, int dy) {
   fitrig_candidate c;
   c.x = tx * w + dx;
   c.y = ty * w + dy;
   c.snapshot = it.group;
-  c.significance = (float)it.z;
+  c.significance = significance(a, it);
   c.branch = FITRIG_BRANCH_IMAGE;
   c.freq_bin = -1;
   c.xf = (float)c.x;
@@ -530,7 +532,7 @@ __global__ void k_emit_image_arg(CandArgs a, const SelItem* __restrict__ items, 
     const SelItem it = items[plist[p]];
     const int ty = it.t / a.Tx, tx = it.t - (it.t / a.Tx) * a.Tx;
     const int idx = a.arg[(int64_t)it.group * a.stride + it.t];
-    tmp[p] = image_candidate(it, tx, ty, a.w, idx % a.w, idx / a.w);
+    tmp[p] = image_candidate(a, it, tx, ty, a.w, idx % a.w, idx / a.w);
   }
 }
 
@@ -572,7 +574,7 @@ __global__ void k_emit_image(CandArgs a, const SelItem* __restrict__ items, cons
         bidx = oi;
       }
     }
-    if (lane == 0) tmp[p] = image_candidate(it, tx, ty, a.w, bidx % ww, bidx / ww);
+    if (lane == 0) tmp[p] = image_candidate(a, it, tx, ty, a.w, bidx % ww, bidx / ww);
   }
 }
 

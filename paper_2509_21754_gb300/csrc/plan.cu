@@ -308,7 +308,7 @@ static int alloc_select(fitrig_plan_t p) {
   };
   const size_t o_cnt = carve(sizeof(int) * s.nblk * 8), o_off = carve(sizeof(int) * (s.nblk * 8 + 1));
   const size_t o_items = carve(sizeof(SelItem) * cap), o_nsel = carve(sizeof(int));
-  const size_t o_par = carve(sizeof(int) * cap), o_cm = carve(sizeof(unsigned long long) * cap);
+  const size_t o_par = carve(sizeof(int) * cap), o_cm = carve(sizeof(unsigned) * cap);
   const size_t o_pk = carve(sizeof(int) * cap);
   const size_t o_pl = carve(sizeof(int) * cap), o_np = carve(sizeof(int));
   // bitmap words over the element space units * vstride (whole 128-element
@@ -323,7 +323,7 @@ static int alloc_select(fitrig_plan_t p) {
   s.items = reinterpret_cast<SelItem*>(b + o_items);
   s.nsel = reinterpret_cast<int*>(b + o_nsel);
   s.parent = reinterpret_cast<int*>(b + o_par);
-  s.compmax = reinterpret_cast<unsigned long long*>(b + o_cm);
+  s.compmax = reinterpret_cast<unsigned*>(b + o_cm);
   s.peak = reinterpret_cast<int*>(b + o_pk);
   s.plist = reinterpret_cast<int*>(b + o_pl);
   s.npeak = reinterpret_cast<int*>(b + o_np);
@@ -479,7 +479,9 @@ FITRIG_API int fitrig_plan_create(int nx, int ny, int nsnap, int window, double 
   p->branch = branch;
   p->units = nsnap - 2;
   cudaGetDevice(&p->device);
-  if (cudaStreamCreateWithFlags(&p->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  // a blocking stream: ordered with the legacy default stream, so device
+  // snapshots produced there are complete before a push reads them
+  if (cudaStreamCreateWithFlags(&p->own_stream, cudaStreamDefault) != cudaSuccess) {
     delete p;
     return FITRIG_ECUDA;
   }
@@ -777,9 +779,11 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
       CKE(launch_noise(p->d_eta, 1, p->vstride, p->T, p->noise, p->ns_freq, cs, st));
       CKE(launch_thresholds(cs, 1, p->tau, p->d_thr + U, p->d_inv + U, st));
     }
-    CKE(launch_select(p->d_eta, 1, p->vstride, p->d_thr + U, cs, p->d_inv + U, p->sel, status, st));
+    CKE(launch_select(p->d_eta, 1, p->vstride, p->d_thr + U, p->sel, status, st));
     CKE(launch_components(p->Tx, p->Ty, p->vstride, p->sel, status, st));
     ca.branch = FITRIG_BRANCH_FREQ;
+    ca.cs = cs;              // eta's estimate (group 0 of its selection)
+    ca.inv = p->d_inv + U;
     CKE(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
   }
   if (p->branch & FITRIG_BRANCH_IMAGE) {
@@ -790,10 +794,12 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
       mark(FITRIG_KERNEL_NOISE, 1);
     }
     mark(FITRIG_KERNEL_SELECT, 0);
-    CKE(launch_select(p->d_vp, U, p->vstride, p->d_thr, p->d_cs, p->d_inv, p->sel, status, st));
+    CKE(launch_select(p->d_vp, U, p->vstride, p->d_thr, p->sel, status, st));
     CKE(launch_components(p->Tx, p->Ty, p->vstride, p->sel, status, st));
     ca.branch = FITRIG_BRANCH_IMAGE;
     ca.arg = p->d_arg;
+    ca.cs = p->d_cs;
+    ca.inv = p->d_inv;
     CKE(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
     mark(FITRIG_KERNEL_SELECT, 1);
   }

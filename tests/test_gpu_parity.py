@@ -386,3 +386,23 @@ def test_running_M_reading(stride):
             t = F.fitrig_tlisi(p.h, s)
             ok, worst = C.values_close(t, det.tlisi[s], rel=1e-6)
             assert ok, (s, worst)
+
+
+def test_device_pushes_wait_for_their_producer():
+    """Snapshots computed on the default stream and pushed straight away (their
+    memory is reused right after) land intact in the plan's stack."""
+    L, ny, nx = 8, 2048, 2048
+    kept = []
+    with F.Plan(nx, ny, L, 5, 4.0, storage=F.BF16) as p:
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(3)
+        for k in range(L):
+            img = torch.randn(ny, nx, generator=gen, device="cuda")
+            snap = torch.fft.irfft2(torch.fft.rfft2(img) * 0.5, s=(ny, nx))   # a few kernels
+            F.fitrig_push_snapshot(p.h, snap)
+            kept.append(snap.to(torch.bfloat16).cpu())
+            del img, snap
+        torch.cuda.synchronize()
+        for k in range(L):
+            got = device_view(*F.fitrig_stack_device_ptr(p.h, k), ny, torch.bfloat16)
+            assert torch.equal(got[:, :nx].cpu(), kept[k]), k

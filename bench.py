@@ -437,7 +437,10 @@ def main():
     # roofline of the dominant kernel (stack march): algorithmic bytes per launch
     Ty, Tx = F.fitrig_tile_grid(plan.h)
     eb = 4 if a.storage == "f32" else 2
-    alg_bytes = eb * L * ny * nx + 4 * (L - 2) * Ty * Tx
+    # one read of every stored pixel, one v write per tile per unit, and the
+    # in-tile arg-max byte the thread-per-tile march (window <= 6) writes
+    out_b = 4 + (1 if a.window <= 6 else 0)
+    alg_bytes = eb * L * ny * nx + out_b * (L - 2) * Ty * Tx
     k_ms = statistics.mean(stack_ms)
     achieved = alg_bytes / (k_ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()

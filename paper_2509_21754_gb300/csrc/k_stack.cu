@@ -218,9 +218,6 @@ __device__ __forceinline__ void ring_init(Ring& rg, unsigned char* smem, const S
   __syncthreads();
 }
 
-// Marches box (bx, by) of a field through its snapshots; mx collects the
-// running maximum.  Returns false (after flagging and draining, bounded) if a
-// stage never completed; the caller must then leave.
 // Running maximum over one tile row, two pixels per three-input max.
 template <int W>
 __device__ __forceinline__ float row_max(float m, const float* xn) {
@@ -230,10 +227,152 @@ __device__ __forceinline__ float row_max(float m, const float* xn) {
   return m;
 }
 
+// r of Eq. 4/5 from Delta (>= 0) and the reference intensity x^(s+1), with
+// the guard x-hat = C where x == 0.  In the ABS reading x-hat = |x|, so the
+// quotient is never negative and the multiply's saturation to [0, 1] is the
+// clamp min(., 1).
+template <bool SIGNED>
+__device__ __forceinline__ float r_term(float d, float xref) {
+  if (SIGNED) {
+    const float xh = (xref == 0.f) ? kGuardC : xref;
+    return fminf(__fdividef(d, xh), 1.f);
+  }
+  const float xh = (xref == 0.f) ? kGuardC : fabsf(xref);
+  return __saturatef(__fdividef(d, xh));
+}
+
+// Approximate reciprocal (rcp.approx.ftz: relative error below 2^-23).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Waits for the ring's current stage (bounded); false when it never completed.
+__device__ __forceinline__ bool ring_wait(const Ring& rg, uint64_t deadline) {
+  return mbar_wait_bounded(rg.bar0 + 8 * rg.stg, rg.phase, deadline);
+}
+
+// After every thread has consumed the current stage (snapshot j of L): on a
+// failed wait anywhere in the CTA, flag it, let copies in flight land
+// (bounded) and return false; otherwise refill the stage with snapshot
+// j + NS and advance the ring.
+__device__ __forceinline__ bool ring_release(Ring& rg, bool ok, const CUtensorMap* tmap,
+                                             unsigned* status, int j, int L, int x0, int y0,
+                                             int zrot) {
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      atomicOr(status, kErrTimeout);
+      const uint64_t d2 = globaltimer_ns() + 1000000ull;
+      int s = rg.stg;
+      uint32_t ph = rg.phase;
+      for (int jj = j; jj < L && jj < j + rg.NS; ++jj) {
+        mbar_wait_bounded(rg.bar0 + 8 * s, ph, d2);
+        if (++s == rg.NS) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    return false;
+  }
+  if (threadIdx.x == 0 && j + rg.NS < L) {
+    fence_proxy_async_smem();
+    mbar_expect_tx(rg.bar0 + 8 * rg.stg, rg.box_bytes);
+    tma_load_3d(rg.stage0 + rg.stg * rg.stage_bytes, tmap, x0, y0, (zrot + j + rg.NS) % L,
+                rg.bar0 + 8 * rg.stg);
+  }
+  if (++rg.stg == rg.NS) {
+    rg.stg = 0;
+    rg.phase ^= 1u;
+  }
+  return true;
+}
+
+// One unit of the thread's W x W tile: from x^(s+1) (xp) and D^(s) (dp) and
+// the stage holding x^(s+2), writes x^(s+2) to xn and D^(s+1) to dn (separate
+// arrays, so that the caller alternates them and no value is copied), and
+// returns the tile sums.  Row partials first, then the rows in order: short
+// dependency chains for the sums, the maximum with its first position in
+// row-major order (strict >), and this snapshot's maximum sm.
+//
+// ABS reading: for x != 0, r = sat(Delta * |1/x|) needs no guard.  A row whose
+// reference pixels multiply to a non-zero product has no zero among them and
+// takes that form; any other row (a zero pixel, the zero fill outside the
+// image, or a product that underflows) takes the guarded form of Eq. 5.  Both
+// give the same r for a non-zero x.
+template <typename T, int W, bool SIGNED>
+__device__ __forceinline__ void tile_unit(const T* st, const float (&xp)[W * W],
+                                          const float (&dp)[W * W], float (&xn)[W * W],
+                                          float (&dn)[W * W], float& sm, float& s1, float& s2,
+                                          float& s3, int& am) {
+  s1 = 0.f;
+  s2 = 0.f;
+  s3 = 0.f;
+  am = 0;
+#pragma unroll
+  for (int r = 0; r < W; ++r) {
+    float r1 = 0.f, r3 = 0.f, rm = 0.f;
+    int ri = 0;
+    float dd[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) xn[r * W + q] = to_f32(st[r * (32 * W) + q]);
+    sm = row_max<W>(sm, &xn[r * W]);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const int i = r * W + q;
+      dn[i] = fabsf(xn[i] - xp[i]);       // D^(s+1)
+      dd[q] = fabsf(dn[i] - dp[i]);       // Delta
+      r1 += dd[q];
+      if (dd[q] > rm) {
+        rm = dd[q];
+        ri = q;
+      }
+    }
+    float pz = xp[r * W];
+#pragma unroll
+    for (int q = 1; q < W; ++q) pz *= xp[r * W + q];
+    if (SIGNED || pz == 0.f) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) r3 += r_term<SIGNED>(dd[q], xp[r * W + q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < W; ++q) r3 += __saturatef(dd[q] * fabsf(rcp_approx(xp[r * W + q])));
+    }
+    s1 += r1;
+    s3 += r3;
+    if (rm > s2) {
+      s2 = rm;
+      am = r * W + ri;
+    }
+  }
+}
+
+// Snapshots 0 and 1 of a tile: x^(j) into xn, and D^(0) once j == 1.
+template <typename T, int W>
+__device__ __forceinline__ void tile_load(const T* st, const float (&xp)[W * W],
+                                          float (&xn)[W * W], float (&dn)[W * W], bool first,
+                                          float& sm) {
+#pragma unroll
+  for (int r = 0; r < W; ++r) {
+#pragma unroll
+    for (int q = 0; q < W; ++q) xn[r * W + q] = to_f32(st[r * (32 * W) + q]);
+    sm = row_max<W>(sm, &xn[r * W]);
+  }
+  if (!first) {
+#pragma unroll
+    for (int i = 0; i < W * W; ++i) dn[i] = fabsf(xn[i] - xp[i]);
+  }
+}
+
+// Marches box (bx, by) of a field through its snapshots; mx collects the
+// running maximum.  Returns false (after flagging and draining, bounded) if a
+// stage never completed; the caller must then leave.
 template <typename T, int W, bool SIGNED>
 __device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const FieldView& f, int bx,
                                             int by, int tby, Ring& rg, unsigned char* smem,
                                             uint64_t deadline, float& mx) {
+  constexpr int N = W * W;
   const int tid = threadIdx.x;
   const int tbx = tid & 31;
   const int tb = tid >> 5;
@@ -255,105 +394,49 @@ __device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const Field
       if (++s == rg.NS) s = 0;
     }
   }
-  float xp[W * W], dp[W * W];
-#pragma unroll
-  for (int i = 0; i < W * W; ++i) xp[i] = dp[i] = 0.f;
   const size_t tile = (size_t)ty * f.Tx + tx;
   float* out = f.vp + tile;
   uint8_t* aout = f.arg ? f.arg + tile : nullptr;
-  for (int j = 0; j < L; ++j) {
-    const bool ok = mbar_wait_bounded(rg.bar0 + 8 * rg.stg, rg.phase, deadline);
-    const T* st = reinterpret_cast<const T*>(smem + (size_t)rg.stg * rg.stage_bytes) + off;
-    float sm = -INFINITY;   // this snapshot's maximum over the thread's pixels
+  auto stage = [&]() {
+    return reinterpret_cast<const T*>(smem + (size_t)rg.stg * rg.stage_bytes) + off;
+  };
+  // Two register sets alternate between x^(s+1), D^(s) and x^(s+2), D^(s+1).
+  float xa[N], da[N], xb[N], db[N];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (j >= L) break;
+    const bool ok = ring_wait(rg, deadline);
+    float sm = -INFINITY;
     if (ok) {
-      if (j >= 2) {
-        // Row partials first, then the rows in order: short dependency chains
-        // (the sums, the maximum with its first position in row-major order,
-        // and the running maximum M would otherwise be W*W long).
-        float s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        int am = 0;   // first maximum in row-major order (strict >)
-#pragma unroll
-        for (int r = 0; r < W; ++r) {
-          float r1 = 0.f, r3 = 0.f, rm = 0.f;
-          int ri = 0;
-          float xr[W];
-#pragma unroll
-          for (int q = 0; q < W; ++q) xr[q] = to_f32(st[r * (32 * W) + q]);
-          sm = row_max<W>(sm, xr);
-#pragma unroll
-          for (int q = 0; q < W; ++q) {
-            const int i = r * W + q;
-            const float xn = xr[q];
-            const float dn = fabsf(xn - xp[i]);
-            const float d = fabsf(dn - dp[i]);
-            const float ref = SIGNED ? xp[i] : fabsf(xp[i]);
-            const float xh = (xp[i] == 0.f) ? kGuardC : ref;
-            r1 += d;
-            if (d > rm) {
-              rm = d;
-              ri = q;
-            }
-            // r = min(Delta / x-hat, 1); with x-hat = |x| >= 0 the quotient is
-            // never negative, so the multiply's saturation to [0, 1] clamps it
-            r3 += SIGNED ? fminf(__fdividef(d, xh), 1.f) : __saturatef(__fdividef(d, xh));
-            dp[i] = dn;
-            xp[i] = xn;
-          }
-          s1 += r1;
-          s3 += r3;
-          if (rm > s2) {
-            s2 = rm;
-            am = r * W + ri;
-          }
-        }
-        if (live) {
-          float v = s1 * s2 * s3 * inv_n2;
-          if (!isfinite(s1) || !isfinite(v)) v = NAN;
-          out[(size_t)(j - 2) * (size_t)f.vstride] = v;
-          if (aout) aout[(size_t)(j - 2) * (size_t)f.vstride] = (uint8_t)am;
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < W; ++r) {
-#pragma unroll
-          for (int q = 0; q < W; ++q) {
-            const int i = r * W + q;
-            const float xn = to_f32(st[r * (32 * W) + q]);
-            sm = fmaxf(sm, xn);
-            dp[i] = fabsf(xn - xp[i]);
-            xp[i] = xn;
-          }
-        }
-      }
+      if (j == 0) tile_load<T, W>(stage(), xb, xa, da, true, sm);
+      else tile_load<T, W>(stage(), xa, xb, db, false, sm);
     }
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicOr(f.status, kErrTimeout);
-        const uint64_t d2 = globaltimer_ns() + 1000000ull;
-        int s = rg.stg;
-        uint32_t ph = rg.phase;
-        for (int jj = j; jj < L && jj < j + rg.NS; ++jj) {
-          mbar_wait_bounded(rg.bar0 + 8 * s, ph, d2);
-          if (++s == rg.NS) {
-            s = 0;
-            ph ^= 1u;
-          }
-        }
-      }
-      return false;
-    }
+    if (!ring_release(rg, ok, tmap, f.status, j, L, x0, y0, f.zrot)) return false;
     mx = fmaxf(mx, sm);
     if (f.smax) warp_max_to(sm, f.smax + j);
-    if (tid == 0 && j + rg.NS < L) {
-      fence_proxy_async_smem();
-      mbar_expect_tx(rg.bar0 + 8 * rg.stg, rg.box_bytes);
-      tma_load_3d(rg.stage0 + rg.stg * rg.stage_bytes, tmap, x0, y0, (f.zrot + j + rg.NS) % L,
-                  rg.bar0 + 8 * rg.stg);
+  }
+  // After the prologue x^(1) and D^(0) are in (xb, db) when L > 1.
+  auto unit = [&](int j, const float (&xp)[N], const float (&dp)[N], float (&xn)[N],
+                  float (&dn)[N]) -> bool {
+    const bool ok = ring_wait(rg, deadline);
+    float sm = -INFINITY;
+    float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int am = 0;
+    if (ok) tile_unit<T, W, SIGNED>(stage(), xp, dp, xn, dn, sm, s1, s2, s3, am);
+    if (!ring_release(rg, ok, tmap, f.status, j, L, x0, y0, f.zrot)) return false;
+    mx = fmaxf(mx, sm);
+    if (f.smax) warp_max_to(sm, f.smax + j);
+    if (live) {
+      float v = s1 * s2 * s3 * inv_n2;
+      if (!isfinite(s1) || !isfinite(v)) v = NAN;
+      out[(size_t)(j - 2) * (size_t)f.vstride] = v;
+      if (aout) aout[(size_t)(j - 2) * (size_t)f.vstride] = (uint8_t)am;
     }
-    if (++rg.stg == rg.NS) {
-      rg.stg = 0;
-      rg.phase ^= 1u;
-    }
+    return true;
+  };
+  for (int j = 2; j < L; j += 2) {
+    if (!unit(j, xb, db, xa, da)) return false;
+    if (j + 1 < L && !unit(j + 1, xa, da, xb, db)) return false;
   }
   return true;
 }

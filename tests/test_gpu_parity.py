@@ -115,6 +115,25 @@ def test_both_branches_c2_like():
     assert_parity(res, det, x, 5, 6.0, F.BRANCH_BOTH, "medmad")
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("w", [3, 5, 6, 8])
+def test_zero_reference_guard(storage, w):
+    """Eq. 5: where the reference pixel x^(s+1) is 0, x-hat = C, also when
+    0 < Delta < C (r = Delta / C < 1) and when Delta = 0 (r = 0).  The values
+    are exact in every storage type (2^-17 and 2^-17 + 2^-22)."""
+    spec = synth.small_spec(7, 96, 101, n_steady=4, n_pulsed=1, pulse_period=(3, 4))
+    stack, _ = synth.make_stack(spec, seed=40 + w, device="cuda")
+    a = 2.0 ** -17
+    rs = np.random.default_rng(w)
+    for k in range(60):
+        s, y, xx = int(rs.integers(0, 5)), int(rs.integers(0, 96)), int(rs.integers(0, 101))
+        stack[s, y, xx] = a
+        stack[s + 1, y, xx] = 0.0
+        stack[s + 2, y, xx] = (a + 2.0 ** -22, a, 3.0)[k % 3]
+    res, det, x = run_both(stack, w, 3.0, F.BRANCH_IMAGE, storage=storage)
+    assert_parity(res, det, x, w, 3.0, F.BRANCH_IMAGE)
+
+
 # ---------------------------------------------------------------- properties
 def test_medmad_is_bit_exact_on_own_values():
     spec = synth.small_spec(12, 300, 257)

@@ -381,7 +381,8 @@ template <bool VEC>
 __global__ void __launch_bounds__(kClusterThreads, 4) k_medmad_cluster(const float* __restrict__ vals,
                                                                     int64_t stride, int64_t n,
                                                                     int g0, double* cs,
-                                                                    unsigned long long* invalid) {
+                                                                    unsigned long long* invalid,
+                                                                    int skip_done) {
   __shared__ unsigned hist[2][kClusterBins];
   __shared__ unsigned coarse[2][kCoarse];
   __shared__ uint32_t keep[kCollectPerCta];
@@ -393,6 +394,9 @@ __global__ void __launch_bounds__(kClusterThreads, 4) k_medmad_cluster(const flo
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank();
   const int g = g0 + blockIdx.y;
+  // after the bracketed kernel: only the groups it left (scale -1) remain; the
+  // test reads one value, so every CTA of the cluster leaves together
+  if (skip_done && cs[2 * g + 1] >= 0.0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* v = vals + (size_t)g * stride;
   const int64_t nv = VEC ? stride / 4 : stride;
@@ -620,9 +624,477 @@ __global__ void __launch_bounds__(kClusterThreads, 4) k_medmad_cluster(const flo
   cl.sync();               // nobody leaves while others may still read its histograms
 }
 
+// ---------------------------------------------------------------- MEDMAD, bracketed form
+// One thread-block cluster of 8 CTAs per group, for maps of moderate size.
+// The exact lower median and MAD are found with two passes over the map
+// instead of one pass per radix digit:
+//   * every CTA bins the same fixed, evenly spread sample of the group (up to
+//     288 runs of 32 consecutive values) twice -- over the sample's key range,
+//     then over the bins holding the targets -- and so finds the same sample
+//     quantiles A <= B at ranks 1/2 -+ delta of the sample;
+//   * one pass, each CTA over its share, counts the finite values and the
+//     keys below A, and copies the keys in [A, B] into its shared memory;
+//   * if the median's rank lies among the copies of the cluster, rounds of
+//     2048-bin histograms over the copies (summed over the cluster through
+//     distributed shared memory) select it exactly;
+//   * the same sample as keys of |v - median| (FP32, the exact median) gives
+//     the MAD's bracket [m_lo, m_hi]; a second pass counts the values with
+//     |v - median| <= m_lo and copies those strictly between, and the MAD is
+//     selected among the copies the same way.
+// Every count is exact, so the result is the element a sort would give; the
+// sample only decides how much is copied.  When a bracket misses its rank or
+// the copies do not fit, the group is marked (scale -1) and the multi-pass
+// cluster kernel above, launched next, computes it instead.
+constexpr int kFastThreads = 256;
+constexpr int kFastWarps = kFastThreads / 32;
+constexpr int kFastBins = 2048;                    // 64 coarse bins of 32
+constexpr int kFastPool = 9 * 1024;                // keys copied per CTA
+constexpr int kFastRuns = kFastPool / 32;          // sample runs of 32 values
+constexpr int64_t kFastMaxPerGroup = 2 << 20;
+constexpr uint32_t kFinLo = 0x00800000u;   // key of -FLT_MAX
+constexpr uint32_t kFinHi = 0xff7fffffu;   // key of +FLT_MAX
+constexpr uint32_t kNoKey = 0xffffffffu;   // above every finite key (a NaN's)
+
+// Finiteness from the exponent bits (an integer test, so that no floating-
+// point rewriting of NaN or infinity can change which values are ranked).
+__device__ __forceinline__ bool finite_bits(float x) {
+  return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
+}
+
+struct FastFind {
+  unsigned long long below;   // keys before the bin
+  unsigned bin, size;
+};
+
+__device__ __forceinline__ unsigned fast_shift(unsigned long long lo, unsigned long long hi) {
+  const unsigned long long width = hi - lo + 1;   // <= 2^32
+  unsigned s = 0;
+  while ((width - 1) >> s >= (unsigned long long)kFastBins) ++s;
+  return s;
+}
+
+// Exclusive scan of one CTA's 2048 bins (eight per thread); returns, for
+// each of up to three ranks, the bin holding it.  Every thread must call it.
+__device__ void fast_find(const unsigned* h, const unsigned long long* rank, int nr, FastFind* out,
+                          unsigned long long* wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned c[8];
+  unsigned mine = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    c[i] = h[8 * tid + i];
+    mine += c[i];
+  }
+  unsigned long long incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  unsigned long long before = incl - mine;
+  for (int w = 0; w < warp; ++w) before += wsum[w];
+  for (int r = 0; r < nr; ++r) {
+    const unsigned long long k = rank[r];
+    if (k >= before && k < before + mine) {
+      unsigned long long cum = before;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        if (k >= cum && k < cum + c[i]) out[r] = FastFind{cum, (unsigned)(8 * tid + i), c[i]};
+        cum += c[i];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Sample quantiles of the n keys in pool (range [kmin, kmax]) at ranks
+// t[0] <= t[nt-1]: a histogram over the whole range, then one over the bins
+// holding the first and last target.  Returns the lower edge of the first
+// target's final bin and the upper edge of the last one's.  CTA-local.
+__device__ void fast_quantiles(const uint32_t* pool, unsigned n, unsigned kmin, unsigned kmax,
+                               const unsigned long long* t, int nt, unsigned* hist,
+                               unsigned long long* wsum, FastFind* res, uint32_t* qlo,
+                               uint32_t* qhi) {
+  unsigned long long lo = kmin, hi = kmax;
+  unsigned long long rk[2] = {t[0], t[nt - 1]};
+  for (int round = 0; round < 2; ++round) {
+    const unsigned sh = fast_shift(lo, hi);
+    for (int b = threadIdx.x; b < kFastBins; b += kFastThreads) hist[b] = 0;
+    if (threadIdx.x < 2) res[threadIdx.x] = FastFind{0ull, 0u, 0u};
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < n; i += kFastThreads) {
+      const uint32_t k = pool[i];
+      if (k >= lo && k <= hi) atomicAdd(&hist[(unsigned)((k - lo) >> sh)], 1u);
+    }
+    __syncthreads();
+    fast_find(hist, rk, 2, res, wsum);
+    const FastFind f0 = res[0], f1 = res[1];
+    const unsigned long long nlo = lo + ((unsigned long long)f0.bin << sh);
+    const unsigned long long nhi = min(hi, lo + ((unsigned long long)f1.bin << sh) + ((1ull << sh) - 1));
+    rk[0] -= f0.below;
+    rk[1] -= f0.below;
+    lo = nlo;
+    hi = nhi;
+    __syncthreads();   // res and hist are rewritten next round
+  }
+  *qlo = (uint32_t)lo;
+  *qhi = (uint32_t)hi;
+}
+
+// Sample ranks 1/2 -+ delta of n sample keys (delta = 4.5 standard errors of
+// a sample median, counting each run of 32 values as half as informative).
+__device__ __forceinline__ void fast_targets(unsigned ns, unsigned long long* t) {
+  const double d = 4.5 * 0.5 / sqrt(0.5 * (double)ns) + 1.0 / (double)ns;
+  const double m = (double)(ns - 1);
+  const double a = floor((0.5 - d) * m), b = ceil((0.5 + d) * m);
+  t[0] = a < 0.0 ? 0ull : (unsigned long long)a;
+  t[1] = b > m ? (unsigned long long)m : (unsigned long long)b;
+}
+
+// Warp 0: the entry of 32 counts (one per lane) holding `rank`.
+__device__ __forceinline__ void warp_find32(unsigned c, unsigned long long rank, int* entry,
+                                            unsigned long long* below, unsigned* size) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned long long excl = incl - c;
+  const bool hit = rank >= excl && rank < incl;
+  const unsigned who = __ballot_sync(0xffffffffu, hit);
+  const int src = who ? __ffs(who) - 1 : 0;
+  *entry = src;
+  *below = __shfl_sync(0xffffffffu, excl, src);
+  *size = __shfl_sync(0xffffffffu, c, src);
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kFastThreads, 4) k_medmad_fast(const float* __restrict__ vals,
+                                                                 int64_t stride, int64_t n, int g0,
+                                                                 double* cs,
+                                                                 unsigned long long* invalid) {
+  __shared__ uint32_t pool[kFastPool];
+  __shared__ unsigned hist[2][kFastBins];
+  __shared__ unsigned coarse[2][64];
+  __shared__ unsigned sum64[64];
+  __shared__ unsigned long long wsum[kFastWarps];
+  __shared__ FastFind res[2];
+  __shared__ unsigned cnt, kmin, kmax;
+  __shared__ unsigned long long mine[3];   // this CTA's pass counts: finite, low, copies
+  __shared__ unsigned long long sel[3];    // cluster selection state: lo, hi, rank
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned crank = cl.block_rank();
+  const int g = g0 + blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* v = vals + (size_t)g * stride;
+  const int64_t nv = VEC ? stride / 4 : stride;
+  // sample slots: one run of 32 values per 32 slots
+  const unsigned slots = 32u * (unsigned)min((stride + 31) / 32, (int64_t)kFastRuns);
+  int buf = 0;
+
+  auto reset = [&]() {
+    if (tid == 0) {
+      cnt = 0;
+      kmin = 0xffffffffu;
+      kmax = 0;
+      mine[0] = mine[1] = mine[2] = 0;
+    }
+    __syncthreads();
+  };
+  // the sample (the same runs in every CTA) as keys of v or of |v - med|:
+  // run c fills slots 32c .. 32c+31; a value that is not finite leaves key 0,
+  // below every finite key, which the ranges of the quantile rounds exclude
+  auto sample = [&](bool mad, float med) -> unsigned {
+    const int64_t runs = (stride + 31) / 32;
+    const int64_t use = runs < kFastRuns ? runs : kFastRuns;
+    unsigned lmin = 0xffffffffu, lmax = 0u, nfin = 0;
+    for (int64_t c = warp; c < use; c += kFastWarps) {   // every run into L2 first
+      const int64_t i = (c * runs / use) * 32 + lane;
+      if (i < stride) asm volatile("prefetch.global.L2 [%0];" ::"l"((const void*)(v + i)));
+    }
+    constexpr int B = 6;
+    for (int64_t c0 = warp; c0 < use; c0 += B * kFastWarps) {
+      float x[B];
+      bool in[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int64_t c = c0 + b * kFastWarps;
+        const int64_t i = (c * runs / use) * 32 + lane;
+        in[b] = c < use && i < stride;
+        x[b] = in[b] ? v[i] : 0.f;
+      }
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int64_t c = c0 + b * kFastWarps;
+        const float y = mad ? fabsf(x[b] - med) : x[b];
+        const bool ok = in[b] && finite_bits(x[b]) && finite_bits(y);
+        const uint32_t key = ok ? f32_key(y) : 0u;
+        if (c < use) pool[c * 32 + lane] = key;
+        if (ok) {
+          lmin = min(lmin, key);
+          lmax = max(lmax, key);
+          ++nfin;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+      lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+      nfin += __shfl_xor_sync(0xffffffffu, nfin, o);
+    }
+    if (lane == 0) {
+      atomicMin(&kmin, lmin);
+      atomicMax(&kmax, lmax);
+      atomicAdd(&cnt, nfin);
+    }
+    __syncthreads();
+    return cnt;
+  };
+  // One pass over this CTA's share.  keyof(x) maps a value to the key that is
+  // ranked (the key of v, or of |v - median|); over keys, the finite values
+  // are exactly [kFinLo, kFinHi], so a key below `low` (finite) is counted and
+  // a key in [clo, chi] (finite) is copied.  Each thread counts its copies of
+  // a batch first, so a warp reserves their slots with one atomic.  The
+  // cluster's totals of (finite, low, copies) are returned in tot.
+  auto pass = [&](auto&& keyof, uint32_t low, uint32_t clo, uint32_t chi,
+                  unsigned long long* tot) {
+    unsigned nf = 0, c0 = 0;
+    constexpr int U = VEC ? 3 : 8;   // loads in flight per thread (registers allow 12 keys)
+    constexpr int E = VEC ? 4 * U : U;
+    const int step = kClusterCtas * kFastThreads;
+    const int nvi = (int)nv;
+    const uint32_t cw = chi - clo;
+    // the trip count depends on the warp only (the shuffles below need every lane)
+    for (int w0 = (int)crank * kFastThreads + warp * 32; w0 < nvi; w0 += U * step) {
+      const int b0 = w0 + lane;
+      uint32_t key[E];
+      // slots past the end take kNoKey, which no class contains
+      if (VEC) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = b0 + u * step;
+          const bool in = i < nvi;
+          const float4 q = in ? reinterpret_cast<const float4*>(v)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+          key[4 * u] = in ? keyof(q.x) : kNoKey;
+          key[4 * u + 1] = in ? keyof(q.y) : kNoKey;
+          key[4 * u + 2] = in ? keyof(q.z) : kNoKey;
+          key[4 * u + 3] = in ? keyof(q.w) : kNoKey;
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int i = b0 + u * step;
+          key[u] = i < nvi ? keyof(v[i]) : kNoKey;
+        }
+      }
+      unsigned ncp = 0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const bool fin = key[e] - kFinLo <= kFinHi - kFinLo;
+        nf += fin;
+        c0 += fin && key[e] < low;
+        ncp += key[e] - clo <= cw;
+      }
+      unsigned incl = ncp;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned wtot = __shfl_sync(0xffffffffu, incl, 31);
+      if (wtot) {   // warp-uniform
+        unsigned base = 0;
+        if (lane == 31) base = atomicAdd(&cnt, wtot);
+        unsigned pos = __shfl_sync(0xffffffffu, base, 31) + incl - ncp;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const bool cp = key[e] - clo <= cw;
+          if (cp && pos < (unsigned)kFastPool) pool[pos] = key[e];
+          pos += cp;
+        }
+      }
+    }
+    unsigned long long nf64 = nf, c064 = c0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nf64 += __shfl_xor_sync(0xffffffffu, nf64, o);
+      c064 += __shfl_xor_sync(0xffffffffu, c064, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&mine[0], nf64);
+      atomicAdd(&mine[1], c064);
+    }
+    __syncthreads();
+    if (tid == 0) mine[2] = cnt;
+    cl.sync();   // every CTA's counts are final
+    tot[0] = tot[1] = tot[2] = 0;
+    bool over = false;
+    for (int r = 0; r < kClusterCtas; ++r) {
+      const unsigned long long* o = cl.map_shared_rank(mine, r);
+      tot[0] += o[0];
+      tot[1] += o[1];
+      tot[2] += o[2];
+      over |= o[2] > (unsigned long long)kFastPool;
+    }
+    if (over) tot[2] = ~0ull;   // a copy did not fit
+  };
+  // the rank-th smallest copy (counted from lo) of the cluster inside [lo, hi]
+  auto select = [&](unsigned long long lo, unsigned long long hi, unsigned long long rank) {
+    const unsigned n = min(cnt, (unsigned)kFastPool);
+    for (int round = 0; round < 8 && lo < hi; ++round) {
+      const unsigned sh = fast_shift(lo, hi);
+      unsigned* h = hist[buf];
+      unsigned* co = coarse[buf];
+      for (int b = tid; b < kFastBins; b += kFastThreads) h[b] = 0;
+      __syncthreads();
+      for (unsigned i = tid; i < n; i += kFastThreads) {
+        const uint32_t k = pool[i];
+        if (k >= lo && k <= hi) atomicAdd(&h[(unsigned)((k - lo) >> sh)], 1u);
+      }
+      __syncthreads();
+      {
+        const int c = tid >> 2, part = tid & 3;   // 64 coarse bins of 32
+        unsigned sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sum += h[c * 32 + part * 8 + i];
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        if (part == 0) co[c] = sum;
+      }
+      cl.sync();   // every CTA's histogram and coarse counts are complete
+      if (tid < 64) {
+        unsigned t = 0;
+        for (int r = 0; r < kClusterCtas; ++r) t += cl.map_shared_rank(co, r)[tid];
+        sum64[tid] = t;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        int cbin;
+        unsigned long long cbelow;
+        unsigned csize;
+        warp_find64(sum64, rank, &cbin, &cbelow, &csize);
+        unsigned f = 0;
+        for (int r = 0; r < kClusterCtas; ++r) f += cl.map_shared_rank(h, r)[cbin * 32 + lane];
+        int fbin;
+        unsigned long long fbelow;
+        unsigned fsize;
+        warp_find32(f, rank - cbelow, &fbin, &fbelow, &fsize);
+        if (lane == 0) {
+          const unsigned long long nlo = lo + ((unsigned long long)(cbin * 32 + fbin) << sh);
+          sel[0] = nlo;
+          sel[1] = min(hi, nlo + ((1ull << sh) - 1));
+          sel[2] = rank - cbelow - fbelow;
+        }
+      }
+      __syncthreads();
+      lo = sel[0];
+      hi = sel[1];
+      rank = sel[2];
+      __syncthreads();   // sel is rewritten next round
+      buf ^= 1;
+    }
+    return (uint32_t)lo;
+  };
+  auto leave = [&](bool fail) {
+    if (fail && crank == 0 && tid == 0) cs[2 * g + 1] = -1.0;   // the cluster kernel takes it
+    cl.sync();   // nobody leaves while others may still read its shared memory
+  };
+
+  // ---- median bracket from the sample (the same in every CTA)
+  reset();
+  unsigned ns = sample(false, 0.f);
+  uint32_t kA = 0, kB = 0;
+  if (ns > 0) {
+    unsigned long long t[2];
+    fast_targets(ns, t);
+    fast_quantiles(pool, slots, kmin, kmax, t, 2, hist[1], wsum, res, &kA, &kB);
+  }
+  // ---- pass 1: finite count, keys below A, copies of [A, B]
+  reset();
+  unsigned long long tot[3];
+  pass([](float x) { return f32_key(x); }, kA, kA, kB, tot);
+  const unsigned long long nf = tot[0];
+  if (nf == 0) {
+    if (crank == 0 && tid == 0) {
+      cs[2 * g] = NAN;
+      cs[2 * g + 1] = 0.0;
+      if (invalid && n > 0) atomicAdd(invalid, (unsigned long long)n);
+    }
+    leave(false);
+    return;
+  }
+  const unsigned long long R = (nf - 1) / 2;
+  if (ns == 0 || tot[2] == ~0ull || R < tot[1] || R >= tot[1] + tot[2]) {
+    leave(true);
+    return;
+  }
+  const float med = f32_from_key(select(kA, kB, R - tot[1]));
+  // ---- MAD bracket from the sample of |v - median|
+  cl.sync();   // every CTA is done with its copies before they are replaced
+  reset();
+  ns = sample(true, med);
+  uint32_t mlo = 0, mhi = 0xffffffffu;
+  if (ns > 0) {
+    unsigned long long t[2];
+    fast_targets(ns, t);
+    fast_quantiles(pool, slots, kmin, kmax, t, 2, hist[buf], wsum, res, &mlo, &mhi);
+  }
+  // ---- pass 2: |v - median| <= m_lo counted, (m_lo, m_hi) copied
+  cl.sync();   // no CTA still reads the previous counts
+  if (ns == 0 || mhi <= mlo + 1u) {   // no key strictly inside: the bracket cannot hold the MAD
+    leave(true);
+    return;
+  }
+  reset();
+  pass([&](float x) { return finite_bits(x) ? f32_key(fabsf(x - med)) : kNoKey; }, mlo + 1,
+       mlo + 1, mhi - 1, tot);
+  if (ns == 0 || tot[2] == ~0ull || R < tot[1] || R >= tot[1] + tot[2]) {
+    leave(true);
+    return;
+  }
+  const float mad = f32_from_key(select((unsigned long long)mlo + 1, (unsigned long long)mhi - 1,
+                                        R - tot[1]));
+  if (crank == 0 && tid == 0) {
+    cs[2 * g] = (double)med;
+    cs[2 * g + 1] = kMadToSigma * (double)mad;
+    if (invalid && (int64_t)nf < n) atomicAdd(invalid, (unsigned long long)(n - (int64_t)nf));
+  }
+  leave(false);
+}
+
+template <bool VEC>
+static cudaError_t launch_fast_t(const float* vals, int groups, int64_t stride, int64_t n,
+                                 double* cs, unsigned long long* invalid, cudaStream_t st) {
+  for (int g0 = 0; g0 < groups; g0 += 65535) {
+    const int gb = std::min(65535, groups - g0);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kClusterCtas, gb, 1);
+    cfg.blockDim = dim3(kFastThreads, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_medmad_fast<VEC>, vals, stride, n, g0, cs, invalid);
+    count_launches(1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 static cudaError_t launch_medmad_cluster(const float* vals, int groups, int64_t stride,
                                          int64_t n, bool vec, double* cs,
-                                         unsigned long long* invalid, cudaStream_t st) {
+                                         unsigned long long* invalid, int skip_done,
+                                         cudaStream_t st) {
   for (int g0 = 0; g0 < groups; g0 += 65535) {
     const int gb = std::min(65535, groups - g0);
     cudaLaunchConfig_t cfg = {};
@@ -638,8 +1110,10 @@ static cudaError_t launch_medmad_cluster(const float* vals, int groups, int64_t 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const cudaError_t e =
-        vec ? cudaLaunchKernelEx(&cfg, k_medmad_cluster<true>, vals, stride, n, g0, cs, invalid)
-            : cudaLaunchKernelEx(&cfg, k_medmad_cluster<false>, vals, stride, n, g0, cs, invalid);
+        vec ? cudaLaunchKernelEx(&cfg, k_medmad_cluster<true>, vals, stride, n, g0, cs, invalid,
+                                 skip_done)
+            : cudaLaunchKernelEx(&cfg, k_medmad_cluster<false>, vals, stride, n, g0, cs, invalid,
+                                 skip_done);
     count_launches(1);
     if (e != cudaSuccess) return e;
   }
@@ -673,8 +1147,15 @@ cudaError_t launch_noise(const float* vals, int groups, int64_t stride, int64_t 
   }
   if (mode != FITRIG_NOISE_MEDMAD) return cudaErrorInvalidValue;
   // groups of moderate size: one cluster per group, all passes in one launch
-  if (stride <= kClusterMaxPerGroup && s.allow_cluster)
-    return launch_medmad_cluster(vals, groups, stride, n, vec, cs, s.invalid, st);
+  if (stride <= kClusterMaxPerGroup && s.allow_cluster) {
+    if (stride > kFastMaxPerGroup)
+      return launch_medmad_cluster(vals, groups, stride, n, vec, cs, s.invalid, 0, st);
+    // the bracketed form, then the cluster form for any group it leaves
+    const cudaError_t e = vec ? launch_fast_t<true>(vals, groups, stride, n, cs, s.invalid, st)
+                              : launch_fast_t<false>(vals, groups, stride, n, cs, s.invalid, st);
+    if (e != cudaSuccess) return e;
+    return launch_medmad_cluster(vals, groups, stride, n, vec, cs, s.invalid, 1, st);
+  }
   cudaError_t e = cudaMemsetAsync(s.rsel, 0, (size_t)groups * 4 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(s.hist, 0, (size_t)groups * kBins * sizeof(unsigned), st);

@@ -96,8 +96,15 @@ enum {
   FITRIG_OPT_STREAM = 8,     /* cudaStream_t cast to int64; 0 = the plan's own stream */
   FITRIG_OPT_TIMEOUT_NS = 9, /* bound of every device-side wait (default 2e9 ns)      */
   FITRIG_OPT_AUTOTUNE = 10,  /* 1: use the autotuned stack-march shape (tunes once)    */
-  FITRIG_OPT_MAX_SELECTED = 11 /* selected-tile capacity of one detect; 0 = default    */
+  FITRIG_OPT_MAX_SELECTED = 11, /* selected-tile capacity of one detect; 0 = default   */
+  FITRIG_OPT_GRAPH = 12       /* 1 (default): replay repeated detects from a graph     */
 };
+/* GRAPH: the second fitrig_detect of an unchanged plan state (same pushed
+ * snapshots count and ring position, same selection lists) captures that
+ * detect's device work into a CUDA graph, which it and later detects of the
+ * state replay with one launch instead of a few dozen.  Results are the same
+ * either way.  0 turns this off (every detect launches its kernels one by
+ * one); settable at any time. */
 /* MAX_SELECTED bounds the tiles (pixels in sliding mode) that pass the
  * threshold in one detect, over all units and both branches, and so also the
  * candidates.  0 (the default) is automatic: the lists start at 4 Mi +

@@ -156,11 +156,135 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restri
   bin[t] = bk;
 }
 
+// Even n = 2m (n <= 66): the transform splits into the two length-m DFTs of
+// the even- and odd-indexed samples, X_k = E_k + W^k O_k with W = e^(-2 pi i/n)
+// (a radix-2 decimation in time).  E and O are DFTs of real series, so only
+// their bins k = 0..floor(m/2) are formed (the others are complex conjugates,
+// E_(m-k) = conj(E_k)), each from folded pairs of samples; one shared-memory
+// twiddle then feeds four multiply-adds (both halves, real and imaginary
+// parts), half the work of the direct form.  X_m = E_0 - O_0 (Nyquist).
+// Twiddles come from the host's FP64 table of 2 pi q / n (its first row) by
+// symmetry.
+template <int KH>
+__global__ void __launch_bounds__(kDftThreads) k_dft_even(const float* __restrict__ vp, int n,
+                                                          int64_t T, int64_t vs,
+                                                          const float2* __restrict__ tw,
+                                                          const float* __restrict__ wts,
+                                                          float* eta, int* bin) {
+  extern __shared__ float2 sm2[];
+  const int m = n / 2, Hm = (m - 1) / 2, K = m / 2, H = (n - 1) / 2;
+  float2* th = sm2;                                 // [Hm][K]: 2 pi j k / m, j,k >= 1
+  float2* tk = th + (Hm > 0 ? Hm * K : 0);          // [m]: 2 pi k / n
+  float* ys = reinterpret_cast<float*>(tk + m);     // [n][kDftThreads]
+  // (cos, sin) of 2 pi a / n from the table row q = 1..H and symmetry
+  auto ang = [&](int a) -> float2 {
+    if (a == 0) return make_float2(1.f, 0.f);
+    if (2 * a == n) return make_float2(-1.f, 0.f);
+    if (a <= H) return tw[a - 1];
+    const float2 c = tw[n - a - 1];
+    return make_float2(c.x, -c.y);
+  };
+  for (int i = threadIdx.x; i < Hm * K; i += blockDim.x) {
+    const int j = i / K + 1, k = i - (i / K) * K + 1;
+    th[i] = ang((2 * j * k) % n);
+  }
+  for (int k = threadIdx.x; k < m; k += blockDim.x) tk[k] = ang(k);
+  __syncthreads();
+  const int64_t t = (int64_t)blockIdx.x * kDftThreads + threadIdx.x;
+  if (t >= T) return;
+  float* my = ys + threadIdx.x;
+  float sum = 0.f;
+  bool ok = true;
+  for (int q = 0; q < n; ++q) {
+    const float v = wts ? vp[(size_t)q * vs + t] * wts[q] : vp[(size_t)q * vs + t];
+    ok = ok && isfinite(v);
+    my[q * kDftThreads] = v;
+    sum += v;
+  }
+  if (!ok) {
+    eta[t] = NAN;
+    bin[t] = -1;
+    return;
+  }
+  const float mean = sum / (float)n;
+  auto ye = [&](int j) { return my[(2 * j) * kDftThreads] - mean; };       // y_(2j)
+  auto yo = [&](int j) { return my[(2 * j + 1) * kDftThreads] - mean; };   // y_(2j+1)
+  const float ye0 = ye(0), yo0 = yo(0);
+  const bool meven = (m & 1) == 0;
+  const float yem = meven ? ye(m / 2) : 0.f, yom = meven ? yo(m / 2) : 0.f;
+  float E0 = ye0 + yem, O0 = yo0 + yom;   // bin 0 of each half
+  float er[KH], es[KH], orr[KH], os[KH];  // bins 1..K: real parts, and the sums of
+                                          // the odd folds times sin (imag = -that)
+#pragma unroll
+  for (int k = 0; k < KH; ++k) {
+    const float sg = ((k + 1) & 1) ? -1.f : 1.f;   // (-1)^(k+1)
+    er[k] = ye0 + sg * yem;
+    orr[k] = yo0 + sg * yom;
+    es[k] = 0.f;
+    os[k] = 0.f;
+  }
+  for (int j = 1; j <= Hm; ++j) {
+    const float a = ye(j), b = ye(m - j), c = yo(j), d = yo(m - j);
+    const float ee = a + b, eo = a - b, oe = c + d, oo = c - d;
+    E0 += ee;
+    O0 += oe;
+    const float2* row = th + (j - 1) * K;
+#pragma unroll
+    for (int k = 0; k < KH; ++k) {
+      if (k < K) {
+        const float2 w = row[k];
+        er[k] = fmaf(ee, w.x, er[k]);
+        es[k] = fmaf(eo, w.y, es[k]);
+        orr[k] = fmaf(oe, w.x, orr[k]);
+        os[k] = fmaf(oo, w.y, os[k]);
+      }
+    }
+  }
+  // X_k = E_k + W^k O_k, W^k = (c, -s):  Re = Er + c Or + s Oi,  Im = Ei + c Oi - s Or
+  float best = -1.f;
+  int bk = 1;
+  auto take = [&](int k, float Er, float Ei, float Or, float Oi) {
+    const float2 w = tk[k];
+    const float re = Er + w.x * Or + w.y * Oi;
+    const float im = Ei + w.x * Oi - w.y * Or;
+    const float m2 = re * re + im * im;
+    if (m2 > best || (m2 == best && k < bk)) {
+      best = m2;
+      bk = k;
+    }
+  };
+#pragma unroll
+  for (int k = 0; k < KH; ++k) {
+    if (k < K) {
+      take(k + 1, er[k], -es[k], orr[k], -os[k]);                    // bin k+1
+      if (m - (k + 1) > K) take(m - (k + 1), er[k], es[k], orr[k], os[k]);   // its mirror
+    }
+  }
+  {
+    const float x = E0 - O0;   // bin m
+    const float m2 = x * x;
+    if (m2 > best || (m2 == best && m < bk)) {
+      best = m2;
+      bk = m;
+    }
+  }
+  eta[t] = sqrtf(best);
+  bin[t] = bk;
+}
+
 cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
                             const float2* twiddle, const float* wts, float* eta, int* bin,
                             cudaStream_t st) {
   const int64_t blocks = (T + kDftThreads - 1) / kDftThreads;
   const int H = (n - 1) / 2, K = n / 2;
+  if ((n & 1) == 0 && n <= 66) {
+    const int m = n / 2, Hm = (m - 1) / 2, Kh = m / 2;
+    const size_t sm = (size_t)(Hm > 0 ? Hm * Kh : 0) * sizeof(float2) + (size_t)m * sizeof(float2) +
+                      (size_t)n * kDftThreads * sizeof(float);
+    k_dft_even<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts, eta, bin);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   if (n <= 65 && H >= 1) {
     const size_t sm = (size_t)H * K * sizeof(float2) + (size_t)n * kDftThreads * sizeof(float);
     if (K <= 16)

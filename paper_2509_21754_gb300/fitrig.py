@@ -24,7 +24,7 @@ BRANCH_IMAGE, BRANCH_FREQ, BRANCH_BOTH = 1, 2, 3
 F32, BF16, F16 = 0, 1, 2
 OPT_STORAGE, OPT_NOISE, OPT_RMODE, OPT_MMODE, OPT_EDGE, OPT_STRIDE = 1, 2, 3, 4, 5, 6
 OPT_STREAM, OPT_TIMEOUT_NS = 8, 9
-OPT_AUTOTUNE, OPT_MAX_SELECTED = 10, 11
+OPT_AUTOTUNE, OPT_MAX_SELECTED, OPT_GRAPH = 10, 11, 12
 NOISE_MEANSTD, NOISE_MEDMAD = 0, 1
 RMODE_ABS, RMODE_SIGNED = 0, 1
 MMODE_GLOBAL, MMODE_RUNNING = 0, 1

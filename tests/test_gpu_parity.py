@@ -196,6 +196,31 @@ def test_scale_invariance_of_candidates():
     assert r2["M"] == 4.0 * r1["M"]
 
 
+def test_graph_replay_matches_eager():
+    """Repeated detects of one state replay a captured graph (the second
+    captures, the third replays); candidates, tile values, spectrum, noise,
+    stage timings and launch counts match the eager detects."""
+    spec = synth.small_spec(20, 300, 310, n_steady=10, n_pulsed=3, pulse_period=(3, 6))
+    stack, _ = synth.make_stack(spec, seed=21, device="cuda")
+    with F.Plan(310, 300, 20, 5, 4.0, F.BRANCH_BOTH, noise=F.NOISE_MEDMAD) as p:
+        p.push_stack(stack)
+        runs = []
+        for graph in (0, 1, 1, 1, 0):
+            F.fitrig_plan_set(p.h, F.OPT_GRAPH, graph)
+            n0 = F.fitrig_launch_count()
+            rc, c = p.detect()
+            launches = F.fitrig_launch_count() - n0
+            eta, kbin = F.fitrig_spectrum(p.h)
+            runs.append((rc, c.tobytes(), F.fitrig_unit_values(p.h, 7).tobytes(), eta.tobytes(),
+                         kbin.tobytes(), F.fitrig_noise_params(p.h, 3), launches))
+            for k in (F.KERNEL_STACK, F.KERNEL_NOISE, F.KERNEL_SELECT, F.KERNEL_SPECTRUM):
+                ms = F.fitrig_kernel_ms(p.h, k)
+                assert 0.0 < ms < 100.0, (graph, k, ms)
+        assert len(runs[0][1]) > 0
+        for r in runs[1:]:
+            assert r == runs[0]
+
+
 def test_determinism():
     stack, _ = synth.make_stack(synth.small_spec(20, 300, 310), seed=23, device="cuda")
     a = F.detect_stack(stack, 5, 4.0, F.BRANCH_BOTH, noise=F.NOISE_MEANSTD)

@@ -113,7 +113,8 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restri
                                                            const float* __restrict__ thr,
                                                            int64_t chunk, const int* woff,
                                                            SelItem* items, uint32_t* sbits,
-                                                           int* wbase, int64_t cap) {
+                                                           int* wbase, int64_t cap,
+                                                           unsigned* compmax, int* peak) {
   const int64_t N = (int64_t)groups * stride;
   int64_t lo, hi;
   warp_range(N, chunk, &lo, &hi);
@@ -182,6 +183,8 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_write(const float* __restri
           it.t = (int32_t)(e - (int64_t)g * stride);
           it.v = v[k];
           items[pos] = it;
+          compmax[pos] = 0u;   // component state for launch_components
+          peak[pos] = INT_MAX;
         }
         ++pos;
       }
@@ -209,14 +212,14 @@ cudaError_t launch_select(const float* vals, int groups, int64_t stride, const f
                                       s.want);
     k_sel_write<true><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk,
                                                       s.blkoff, s.items, s.bits, s.wbase,
-                                                      s.capacity);
+                                                      s.capacity, s.compmax, s.peak);
   } else {
     k_sel_count<false><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk, s.blkcnt);
     k_scan_blocks<<<1, 1024, 0, st>>>(nw, s.blkcnt, s.blkoff, s.nsel, s.capacity, status,
                                       s.want);
     k_sel_write<false><<<s.nblk, kSelThreads, 0, st>>>(vals, groups, stride, thr, chunk,
                                                        s.blkoff, s.items, s.bits, s.wbase,
-                                                       s.capacity);
+                                                       s.capacity, s.compmax, s.peak);
   }
   count_launches(3);
   return cudaGetLastError();
@@ -292,14 +295,6 @@ __device__ void unite(int* parent, int a, int b, unsigned* status) {
   atomicOr(status, kErrCcLimit);
 }
 
-__global__ void k_cc_init(const int* nsel, int* parent, unsigned* compmax, int* peak) {
-  const int n = *nsel;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    parent[i] = i;
-    compmax[i] = 0u;
-    peak[i] = INT_MAX;
-  }
-}
 
 // Horizontal runs: a selected tile whose left neighbour is selected is the next
 // list entry after it.  Each warp takes 32 consecutive entries, finds by
@@ -366,12 +361,13 @@ __global__ void k_cc_union(const SelItem* __restrict__ items, const int* nsel, i
   }
 }
 
-// After the unions every entry points straight at its root.  The roots no
-// longer change here, so each thread finds its root without writing and then
-// sets every entry on its path to that root: every store is a final value
-// (path halving here could store an intermediate ancestor over another
-// thread's root and leave an entry outside its component's root).
-__global__ void k_cc_flatten(const int* nsel, int* parent) {
+// After the unions the roots no longer change, so each thread finds its
+// entry's root without writing, then points the entry at it (a final value,
+// so other walks through it stay valid) and raises the component's largest
+// value key.  (Path halving here could store an intermediate ancestor over
+// another thread's root and leave an entry outside its component's root.)
+__global__ void k_cc_flatten_max(const SelItem* __restrict__ items, const int* nsel, int* parent,
+                                 unsigned* compmax) {
   const int n = *nsel;
   volatile int* p = parent;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -380,37 +376,32 @@ __global__ void k_cc_flatten(const int* nsel, int* parent) {
       r = y;
       y = p[r];
     }
-    int x = i;
-    while (x != r) {
-      const int nx = p[x];
-      p[x] = r;
-      x = nx;
-    }
+    p[i] = r;
+    atomicMax(&compmax[r], f32_key(items[i].v));   // a component lies in one group
   }
 }
 
+// The peak of each component: its entry of largest value, the smallest list
+// index on ties (the list is in tile order).
 __global__ void k_cc_peak(const SelItem* __restrict__ items, const int* nsel, const int* parent,
-                          unsigned* compmax, int* peak, int stage) {
+                          const unsigned* compmax, int* peak) {
   const int n = *nsel;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const unsigned k = f32_key(items[i].v);   // a component lies in one group
     const int r = parent[i];
-    if (stage == 0) atomicMax(&compmax[r], k);
-    else if (k == compmax[r]) atomicMin(&peak[r], i);
+    if (f32_key(items[i].v) == compmax[r]) atomicMin(&peak[r], i);
   }
 }
 
 cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
                               unsigned* status, cudaStream_t st) {
+  // (every entry's compmax / peak were initialised by the compaction)
   const int grid = 152 * 16, thr = 256;
-  k_cc_init<<<grid, thr, 0, st>>>(s.nsel, s.parent, s.compmax, s.peak);
   k_cc_runs<<<grid, thr, 0, st>>>(s.items, s.nsel, Tx, s.parent);
   k_cc_union<<<grid, thr, 0, st>>>(s.items, s.nsel, Tx, Ty, T, s.bits, s.wbase, s.parent,
                                    status);
-  k_cc_flatten<<<grid, thr, 0, st>>>(s.nsel, s.parent);
-  k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak, 0);
-  k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak, 1);
-  count_launches(6);
+  k_cc_flatten_max<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax);
+  k_cc_peak<<<grid, thr, 0, st>>>(s.items, s.nsel, s.parent, s.compmax, s.peak);
+  count_launches(4);
   return cudaGetLastError();
 }
 

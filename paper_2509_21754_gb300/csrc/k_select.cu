@@ -513,20 +513,6 @@ __device__ __forceinline__ fitrig_candidate image_candidate(const CandArgs& a, c
   return c;
 }
 
-// Image branch, step 1 (fused arg-max available): one thread per peak reads
-// the stack march's in-tile arg-max (index r*w + q of the first maximum of
-// Delta) and writes the candidate in peak-list order to `tmp`.
-__global__ void k_emit_image_arg(CandArgs a, const SelItem* __restrict__ items, const int* np_,
-                                 const int* __restrict__ plist, fitrig_candidate* tmp) {
-  const int np = *np_;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-    const SelItem it = items[plist[p]];
-    const int ty = it.t / a.Tx, tx = it.t - (it.t / a.Tx) * a.Tx;
-    const int idx = a.arg[(int64_t)it.group * a.stride + it.t];
-    tmp[p] = image_candidate(a, it, tx, ty, a.w, idx % a.w, idx / a.w);
-  }
-}
-
 // Image branch, step 1 (otherwise): one warp per peak computes the tile's
 // arg-max of Delta (ties: smallest row-major index, same FP32 arithmetic as the
 // stack march) and writes the candidate in peak-list order to `tmp`.
@@ -578,14 +564,26 @@ __global__ void k_emit_image(CandArgs a, const SelItem* __restrict__ items, cons
 constexpr int kGroupWarps = 8;
 constexpr int kMaxW = 128;
 
-__device__ __forceinline__ bool same_group(const fitrig_candidate* tmp, int p, int q, int w) {
-  return tmp[p].snapshot == tmp[q].snapshot && tmp[p].y / w == tmp[q].y / w;
-}
-
+// FROM_ARG: the candidates are formed here from the peak list and the
+// march's in-tile arg-max (no intermediate list); otherwise they are read
+// from `tmp`, where k_emit_image wrote them.
+template <bool FROM_ARG>
 __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, const int* np_,
                                                                  const fitrig_candidate* tmp,
+                                                                 const SelItem* __restrict__ items,
+                                                                 const int* __restrict__ plist,
                                                                  const int* base_) {
   __shared__ int counts[kGroupWarps][kMaxW];
+  auto snap_of = [&](int p) { return FROM_ARG ? items[plist[p]].group : tmp[p].snapshot; };
+  auto row_of = [&](int p) { return FROM_ARG ? items[plist[p]].t / a.Tx : tmp[p].y / a.w; };
+  auto cand_of = [&](int p) -> fitrig_candidate {
+    if (!FROM_ARG) return tmp[p];
+    const SelItem it = items[plist[p]];
+    const int ty = it.t / a.Tx, tx = it.t - ty * a.Tx;
+    const int idx = a.arg[(int64_t)it.group * a.stride + it.t];
+    return image_candidate(a, it, tx, ty, a.w, idx % a.w, idx / a.w);
+  };
+  auto same_group = [&](int p, int q) { return snap_of(p) == snap_of(q) && row_of(p) == row_of(q); };
   const int np = *np_;
   const int base = base_ ? *base_ : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -594,18 +592,18 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
   const int nw = gridDim.x * kGroupWarps;
   for (int p0 = wid * 32; p0 < np; p0 += nw * 32) {
     const int pl = p0 + lane;
-    const bool head = pl < np && (pl == 0 || !same_group(tmp, pl, pl - 1, a.w));
+    const bool head = pl < np && (pl == 0 || !same_group(pl, pl - 1));
     unsigned heads = __ballot_sync(0xffffffffu, head);
     while (heads) {
       const int p = p0 + __ffs(heads) - 1;
       heads &= heads - 1;
-      const int gty = tmp[p].y / a.w;
-      const int snap = tmp[p].snapshot;
+      const int gty = row_of(p);
+      const int snap = snap_of(p);
       // group extent
       int end = p + 1;
       for (;;) {
         const int q = end + lane;
-        const bool same = q < np && tmp[q].snapshot == snap && tmp[q].y / a.w == gty;
+        const bool same = q < np && snap_of(q) == snap && row_of(q) == gty;
         const unsigned bal = __ballot_sync(0xffffffffu, same);
         if (bal == 0xffffffffu) {
           end += 32;
@@ -616,7 +614,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
       }
       for (int k = lane; k < a.w; k += 32) cnt[k] = 0;
       __syncwarp();
-      for (int q = p + lane; q < end; q += 32) atomicAdd(&cnt[tmp[q].y - gty * a.w], 1);
+      for (int q = p + lane; q < end; q += 32) atomicAdd(&cnt[cand_of(q).y - gty * a.w], 1);
       __syncwarp();
       if (lane == 0) {
         int run = 0;
@@ -633,7 +631,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
         fitrig_candidate c;
         int dy = kMaxW;
         if (valid) {
-          c = tmp[q];
+          c = cand_of(q);
           dy = c.y - gty * a.w;
         }
         const unsigned peers = __match_any_sync(0xffffffffu, dy);
@@ -681,12 +679,16 @@ cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, in
     k_emit_freq<<<152 * 4, 256, 0, st>>>(a, s.items, s.npeak, s.plist);
     count_launches(4);
   } else {
-    if (a.arg)
-      k_emit_image_arg<<<152 * 4, 256, 0, st>>>(a, s.items, s.npeak, s.plist, tmp);
-    else
+    if (a.arg) {
+      k_group_sort<true><<<152 * 4, kGroupWarps * 32, 0, st>>>(a, s.npeak, tmp, s.items, s.plist,
+                                                               base);
+      count_launches(4);
+    } else {
       k_emit_image<<<152 * 4, 256, 0, st>>>(a, s.items, s.npeak, s.plist, tmp);
-    k_group_sort<<<152 * 4, kGroupWarps * 32, 0, st>>>(a, s.npeak, tmp, base);
-    count_launches(5);
+      k_group_sort<false><<<152 * 4, kGroupWarps * 32, 0, st>>>(a, s.npeak, tmp, s.items,
+                                                                s.plist, base);
+      count_launches(5);
+    }
   }
   // running total of candidates
   k_add_count<<<1, 1, 0, st>>>(a.nout, s.npeak);

@@ -193,12 +193,24 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_even(const float* __restric
   const int64_t t = (int64_t)blockIdx.x * kDftThreads + threadIdx.x;
   if (t >= T) return;
   float* my = ys + threadIdx.x;
+  // the series arrives by asynchronous global -> shared copies, all n of a
+  // thread in flight at once (coalesced over the CTA's tiles)
+  for (int q = 0; q < n; ++q) {
+    const uint32_t dst = smem_u32(my + q * kDftThreads);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst),
+                 "l"(vp + (size_t)q * vs + t)
+                 : "memory");
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   float sum = 0.f;
   bool ok = true;
   for (int q = 0; q < n; ++q) {
-    const float v = wts ? vp[(size_t)q * vs + t] * wts[q] : vp[(size_t)q * vs + t];
+    float v = my[q * kDftThreads];
+    if (wts) {
+      v *= wts[q];
+      my[q * kDftThreads] = v;
+    }
     ok = ok && isfinite(v);
-    my[q * kDftThreads] = v;
     sum += v;
   }
   if (!ok) {

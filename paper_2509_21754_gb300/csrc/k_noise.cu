@@ -816,7 +816,7 @@ __global__ void __launch_bounds__(kFastThreads, 4) k_medmad_fast(const float* __
       const int64_t i = (c * runs / use) * 32 + lane;
       if (i < stride) asm volatile("prefetch.global.L2 [%0];" ::"l"((const void*)(v + i)));
     }
-    constexpr int B = 6;
+    constexpr int B = 12;
     for (int64_t c0 = warp; c0 < use; c0 += B * kFastWarps) {
       float x[B];
       bool in[B];
@@ -864,33 +864,43 @@ __global__ void __launch_bounds__(kFastThreads, 4) k_medmad_fast(const float* __
   auto pass = [&](auto&& keyof, uint32_t low, uint32_t clo, uint32_t chi,
                   unsigned long long* tot) {
     unsigned nf = 0, c0 = 0;
-    constexpr int U = VEC ? 3 : 8;   // loads in flight per thread (registers allow 12 keys)
+    constexpr int U = VEC ? 3 : 8;   // vectors per batch (registers allow 12 keys)
     constexpr int E = VEC ? 4 * U : U;
+    constexpr int NV = VEC ? 4 : 1;
     const int step = kClusterCtas * kFastThreads;
     const int nvi = (int)nv;
     const uint32_t cw = chi - clo;
+    // one batch of raw values; the next batch is loaded before the current one
+    // is classified, so that two batches of loads overlap the work
+    float cur[E], nxt[E];
+    auto load = [&](float (&x)[E], int w0) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = w0 + lane + u * step;
+        if (VEC) {
+          const float4 q = i < nvi ? reinterpret_cast<const float4*>(v)[i]
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+          x[4 * u] = q.x;
+          x[4 * u + 1] = q.y;
+          x[4 * u + 2] = q.z;
+          x[4 * u + 3] = q.w;
+        } else {
+          x[u] = i < nvi ? v[i] : 0.f;
+        }
+      }
+    };
     // the trip count depends on the warp only (the shuffles below need every lane)
-    for (int w0 = (int)crank * kFastThreads + warp * 32; w0 < nvi; w0 += U * step) {
-      const int b0 = w0 + lane;
+    int w0 = (int)crank * kFastThreads + warp * 32;
+    if (w0 < nvi) load(cur, w0);
+    for (; w0 < nvi; w0 += U * step) {
+      const int wn = w0 + U * step;
+      if (wn < nvi) load(nxt, wn);
       uint32_t key[E];
       // slots past the end take kNoKey, which no class contains
-      if (VEC) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int i = b0 + u * step;
-          const bool in = i < nvi;
-          const float4 q = in ? reinterpret_cast<const float4*>(v)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-          key[4 * u] = in ? keyof(q.x) : kNoKey;
-          key[4 * u + 1] = in ? keyof(q.y) : kNoKey;
-          key[4 * u + 2] = in ? keyof(q.z) : kNoKey;
-          key[4 * u + 3] = in ? keyof(q.w) : kNoKey;
-        }
-      } else {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int i = b0 + u * step;
-          key[u] = i < nvi ? keyof(v[i]) : kNoKey;
-        }
+      for (int e = 0; e < E; ++e) {
+        const int i = w0 + lane + (e / NV) * step;
+        key[e] = i < nvi ? keyof(cur[e]) : kNoKey;
       }
       unsigned ncp = 0;
 #pragma unroll
@@ -918,6 +928,8 @@ __global__ void __launch_bounds__(kFastThreads, 4) k_medmad_fast(const float* __
           pos += cp;
         }
       }
+#pragma unroll
+      for (int e = 0; e < E; ++e) cur[e] = nxt[e];
     }
     unsigned long long nf64 = nf, c064 = c0;
 #pragma unroll

@@ -42,6 +42,9 @@ Readings where the paper is silent or ambiguous (each is an option here):
 * a sliding-window mode (not in the paper, whose tiles partition the image)
   evaluates the tile statistic over the odd w x w window centred on each pixel,
   clipped at the border, and then treats pixels as 1 x 1 tiles.
+* snapshot accumulation (Sec. 4.3.2): the paper sums adjacent snapshots
+  "progressively until there is enough difference" without a criterion; the
+  reading here sums fixed, non-overlapping blocks of K consecutive snapshots.
 
 All pins of this module live in ``tests/test_oracle_pins.py``.
 """
@@ -59,6 +62,24 @@ MAD_TO_SIGMA = 1.482602218505602   # 1 / Phi^-1(3/4)
 BRANCH_IMAGE = 1
 BRANCH_FREQ = 2
 BRANCH_BOTH = 3
+
+
+# --------------------------------------------------------------------------
+# Snapshot accumulation (Sec. 4.3.2, Fig. "Snapshots accumulation")
+# --------------------------------------------------------------------------
+def accumulate(raw: np.ndarray, k: int) -> np.ndarray:
+    """Stack of sums of K consecutive raw snapshots: snapshot j of the result
+    is the sum of raw snapshots jK .. jK+K-1 (an incomplete last block is
+    dropped).  K = 1 returns the raw stack."""
+    raw = np.asarray(raw, dtype=np.float64)
+    if k < 1:
+        raise ValueError("k must be >= 1")
+    n = raw.shape[0] // k
+    out = np.zeros((n,) + raw.shape[1:], dtype=np.float64)
+    for j in range(n):
+        for i in range(k):
+            out[j] += raw[j * k + i]
+    return out
 
 
 # --------------------------------------------------------------------------

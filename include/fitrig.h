@@ -97,8 +97,21 @@ enum {
   FITRIG_OPT_TIMEOUT_NS = 9, /* bound of every device-side wait (default 2e9 ns)      */
   FITRIG_OPT_AUTOTUNE = 10,  /* 1: use the autotuned stack-march shape (tunes once)    */
   FITRIG_OPT_MAX_SELECTED = 11, /* selected-tile capacity of one detect; 0 = default   */
-  FITRIG_OPT_GRAPH = 12       /* 1 (default): replay repeated detects from a graph     */
+  FITRIG_OPT_GRAPH = 12,      /* 1 (default): replay repeated detects from a graph     */
+  FITRIG_OPT_ACCUMULATE = 13  /* K >= 1: each K pushed snapshots are summed into one   */
 };
+/* ACCUMULATE (Sec. 4.3.2, Fig. "Snapshots accumulation"): with sampling
+ * periods so short that adjacent snapshots are nearly identical, the trigger
+ * runs on sums of adjacent snapshots.  With K > 1 every fitrig_push_snapshot
+ * adds one raw snapshot to a running FP32 sum on the device (raw snapshots
+ * added in push order, the first of a block copied); the K-th raw push of a
+ * block stores the sum, rounded to the plan's storage type, as the next
+ * snapshot of the stack.  nsnap (fitrig_plan_create) counts these stored
+ * sums, so nsnap * K raw pushes fill the stack; a detect uses the complete
+ * sums only.  The paper grows the block until adjacent sums differ enough
+ * but gives no criterion, so K is fixed by the caller.  Default 1 (no sums);
+ * only before the first push; not for serving fields.  Costs an FP32 image of
+ * device memory. */
 /* GRAPH: the second fitrig_detect of an unchanged plan state (same pushed
  * snapshots count and ring position, same selection lists) captures that
  * detect's device work into a CUDA graph, which it and later detects of the

@@ -352,6 +352,31 @@ __global__ void k_convert(const void* src, int st, int64_t sp, void* dst, int dt
   }
 }
 
+// Snapshot accumulation (Sec. 4.3.2): acc = x (first raw snapshot of a
+// block) or acc + x in FP32; the last raw snapshot of the block stores the
+// sum, in the storage type, to the stack slot instead.
+__global__ void k_accumulate(const void* src, int st, int64_t sp, float* acc, int first, int last,
+                             void* dst, int dt, int64_t dp, int ny, int nx) {
+  const int64_t total = (int64_t)ny * nx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = i / nx, x = i - (i / nx) * nx;
+    const float v = load_any(src, st, y * sp + x);
+    const float a = first ? v : acc[i] + v;
+    if (last) store_any(dst, dt, y * dp + x, a);
+    else acc[i] = a;
+  }
+}
+
+cudaError_t launch_accumulate(const void* src, int src_type, int64_t src_pitch, float* acc,
+                              bool first, bool last, void* dst, int dst_type, int64_t dst_pitch,
+                              int ny, int nx, cudaStream_t st) {
+  k_accumulate<<<152 * 8, 256, 0, st>>>(src, src_type, src_pitch, acc, first ? 1 : 0,
+                                        last ? 1 : 0, dst, dst_type, dst_pitch, ny, nx);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,
                            int dst_type, int64_t dst_pitch, int ny, int nx, cudaStream_t st) {
   k_convert<<<152 * 8, 256, 0, st>>>(src, src_type, src_pitch, dst, dst_type, dst_pitch, ny, nx);

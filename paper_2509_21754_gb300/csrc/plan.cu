@@ -62,6 +62,9 @@ struct fitrig_plan_s {
   int stride = FITRIG_STRIDE_TILE;
   int mmode = FITRIG_MMODE_GLOBAL;
   int autotune = 0;
+  int accumulate = 1;        // raw snapshots summed into one stack snapshot
+  int raw_pushed = 0;        // raw snapshots of the block being summed
+  float* d_accum = nullptr;  // [ny][nx] FP32 running sum (accumulate > 1)
   int64_t max_selected = 0;  // 0: automatic selection capacity
   int64_t auto_selected = 0; // the automatic capacity after growing (0: default)
   int64_t sel_bytes = 0;     // device bytes of the selection lists
@@ -161,7 +164,7 @@ static void free_all(fitrig_plan_t p) {
   drop_graph(p);
   void* ptrs[] = {p->d_stack, p->d_vp,  p->d_small, p->d_invalid,  p->d_cs, p->d_arg, p->d_inv,
                   p->d_thr,   p->d_noise, p->d_sel, p->d_cand,     p->d_cand_tmp,
-                  p->d_bin,   p->d_tw,  p->d_staging, p->d_report,
+                  p->d_bin,   p->d_tw,  p->d_staging, p->d_report, p->d_accum,
                   p->d_smax,  p->d_mrun, p->d_wts};   // d_eta lives inside d_vp
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -554,6 +557,11 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t p, int option, int64_t value) {
       if (value != FITRIG_F32 && value != FITRIG_BF16 && value != FITRIG_F16) return FITRIG_EINVAL;
       p->storage = (int)value;
       return FITRIG_OK;
+    case FITRIG_OPT_ACCUMULATE:
+      if (value < 1 || value > 1 << 20) return FITRIG_EINVAL;
+      if (p->ring) return FITRIG_EUNSUPPORTED;
+      p->accumulate = (int)value;
+      return FITRIG_OK;
     case FITRIG_OPT_NOISE:
       if (value != FITRIG_NOISE_MEANSTD && value != FITRIG_NOISE_MEDMAD) return FITRIG_EINVAL;
       p->noise = (int)value;
@@ -667,6 +675,31 @@ FITRIG_API int fitrig_push_snapshot(fitrig_plan_t p, const void* data, int dtype
   cudaStream_t st = plan_stream(p);
   const int eb = elem_bytes(p->storage), ib = elem_bytes(dtype);
   char* dst = p->d_stack + p->slice_bytes * p->pushed;
+  if (p->accumulate > 1) {
+    // Sec. 4.3.2: K raw snapshots summed (FP32, push order) into one
+    const void* src = data;
+    int64_t sp = rp;
+    if (!on_device) {
+      if (!p->d_staging) CK(dmalloc(p, &p->d_staging, (size_t)p->nx * p->ny * 4));
+      CK(copy_rows_h2d(p, p->d_staging, (size_t)p->nx * ib, data, (size_t)rp * ib,
+                       (size_t)p->nx * ib, st));
+      src = p->d_staging;
+      sp = p->nx;
+    }
+    if (!p->d_accum) CK(dmalloc(p, &p->d_accum, (size_t)p->nx * p->ny * 4));
+    const bool first = p->raw_pushed == 0, last = p->raw_pushed + 1 == p->accumulate;
+    CK(launch_accumulate(src, dtype, sp, p->d_accum, first, last, dst, p->storage, p->pitch,
+                         p->ny, p->nx, st));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    if (!last) {
+      p->raw_pushed += 1;
+      return FITRIG_OK;
+    }
+    p->raw_pushed = 0;
+    p->pushed += 1;
+    p->detected = false;
+    return FITRIG_OK;
+  }
   if (dtype == p->storage) {
     if (on_device)
       CK(cudaMemcpy2DAsync(dst, p->pitch * eb, data, rp * ib, (size_t)p->nx * ib, p->ny,
@@ -695,6 +728,7 @@ FITRIG_API int fitrig_push_snapshot(fitrig_plan_t p, const void* data, int dtype
 FITRIG_API int fitrig_plan_reset(fitrig_plan_t p) {
   if (!p) return FITRIG_EINVAL;
   p->pushed = 0;
+  p->raw_pushed = 0;
   p->detected = false;
   return FITRIG_OK;
 }

@@ -1,5 +1,6 @@
 """CUDA path against the FP64 oracle, element by element and candidate by
 candidate, on seeded synthetic stacks.  All calls go through the C ABI."""
+import ctypes
 import math
 
 import numpy as np
@@ -132,6 +133,50 @@ def test_zero_reference_guard(storage, w):
         stack[s + 2, y, xx] = (a + 2.0 ** -22, a, 3.0)[k % 3]
     res, det, x = run_both(stack, w, 3.0, F.BRANCH_IMAGE, storage=storage)
     assert_parity(res, det, x, w, 3.0, F.BRANCH_IMAGE)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("k", [1, 3, 4])
+def test_snapshot_accumulation(storage, k):
+    """Sec. 4.3.2: K raw snapshots pushed per stack snapshot are summed in FP32
+    in push order and stored in the plan's type; the oracle runs on those
+    stored sums."""
+    spec = synth.small_spec(7 * k, 96, 101, n_steady=6, n_pulsed=2, pulse_period=(3, 5))
+    raw, _ = synth.make_stack(spec, seed=50 + k, device="cuda")
+    rawh = raw.cpu()
+    res = F.detect_stack(raw, 5, 3.5, F.BRANCH_BOTH, STORAGE[storage][0], accumulate=k)
+    x = rawh.numpy().astype(np.float32)
+    sums = x[0::k].copy()
+    for i in range(1, k):
+        sums = (sums + x[i::k]).astype(np.float32)   # FP32, in push order
+    stored = torch.from_numpy(sums).to(STORAGE[storage][1]).to(torch.float32).numpy()
+    det = O.detect(stored, 5, 3.5, O.BRANCH_BOTH)
+    assert_parity(res, det, stored, 5, 3.5, F.BRANCH_BOTH)
+    if k > 1:
+        assert np.array_equal(O.accumulate(x.astype(np.float64), k).astype(np.float32).shape,
+                              stored.shape)
+
+
+def test_accumulation_pushes_and_reset():
+    """Raw pushes (host and device alternating) complete a stack snapshot
+    every K; pushing past the stack is refused; a reset starts a new block."""
+    k = 3
+    raw = torch.randn(3 * k + 1, 40, 44, device="cuda")
+    with F.Plan(44, 40, 3, 4, 4.0, accumulate=k) as p:
+        for r in range(3 * k):
+            F.fitrig_push_snapshot(p.h, raw[r] if r % 2 else raw[r].cpu().numpy())
+        lib = F.load()
+        rc = lib.fitrig_push_snapshot(p.h, ctypes.c_void_p(raw[3 * k].data_ptr()), F.F32, 1, 0)
+        assert rc == F.ESTATE
+        rc1, _ = p.detect()
+        assert rc1 in F.SOFT
+        v1 = F.fitrig_unit_values(p.h, 0).copy()
+        F.fitrig_plan_reset(p.h)
+        for r in range(3 * k):
+            F.fitrig_push_snapshot(p.h, raw[r])
+        p.detect()
+        assert np.array_equal(F.fitrig_unit_values(p.h, 0), v1)
+        assert F.load().fitrig_plan_set(p.h, F.OPT_ACCUMULATE, 2) == F.ESTATE
 
 
 # ---------------------------------------------------------------- properties

@@ -13,6 +13,7 @@
 // and o_s = y_s - y_{n-s}, so that Re X_k = y_0 + sum e_s cos + [n even]
 // (-1)^k y_{n/2} and Im X_k = -sum o_s sin, halving the multiply-adds.  The
 // twiddles cos/sin(2 pi k s / n) come from a table filled on the host in FP64.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.cuh"
@@ -342,14 +343,17 @@ __device__ __forceinline__ void store_any(void* p, int type, int64_t i, float v)
   }
 }
 
+// Rows over blockIdx.y, columns over the threads of blockIdx.x (no per-pixel
+// division).
 __global__ void k_convert(const void* src, int st, int64_t sp, void* dst, int dt, int64_t dp,
                           int ny, int nx) {
-  const int64_t total = (int64_t)ny * nx;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t y = i / nx, x = i - (i / nx) * nx;
-    store_any(dst, dt, y * dp + x, load_any(src, st, y * sp + x));
-  }
+  for (int y = blockIdx.y; y < ny; y += gridDim.y)
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x)
+      store_any(dst, dt, (int64_t)y * dp + x, load_any(src, st, (int64_t)y * sp + x));
+}
+
+static dim3 image_grid(int ny, int nx) {
+  return dim3((unsigned)std::min(8, (nx + 255) / 256), (unsigned)std::min(ny, 4096));
 }
 
 // Snapshot accumulation (Sec. 4.3.2): acc = x (first raw snapshot of a
@@ -357,29 +361,30 @@ __global__ void k_convert(const void* src, int st, int64_t sp, void* dst, int dt
 // sum, in the storage type, to the stack slot instead.
 __global__ void k_accumulate(const void* src, int st, int64_t sp, float* acc, int first, int last,
                              void* dst, int dt, int64_t dp, int ny, int nx) {
-  const int64_t total = (int64_t)ny * nx;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t y = i / nx, x = i - (i / nx) * nx;
-    const float v = load_any(src, st, y * sp + x);
-    const float a = first ? v : acc[i] + v;
-    if (last) store_any(dst, dt, y * dp + x, a);
-    else acc[i] = a;
+  for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+    float* arow = acc + (int64_t)y * nx;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+      const float v = load_any(src, st, (int64_t)y * sp + x);
+      const float a = first ? v : arow[x] + v;
+      if (last) store_any(dst, dt, (int64_t)y * dp + x, a);
+      else arow[x] = a;
+    }
   }
 }
 
 cudaError_t launch_accumulate(const void* src, int src_type, int64_t src_pitch, float* acc,
                               bool first, bool last, void* dst, int dst_type, int64_t dst_pitch,
                               int ny, int nx, cudaStream_t st) {
-  k_accumulate<<<152 * 8, 256, 0, st>>>(src, src_type, src_pitch, acc, first ? 1 : 0,
-                                        last ? 1 : 0, dst, dst_type, dst_pitch, ny, nx);
+  k_accumulate<<<image_grid(ny, nx), 256, 0, st>>>(src, src_type, src_pitch, acc, first ? 1 : 0,
+                                                   last ? 1 : 0, dst, dst_type, dst_pitch, ny, nx);
   count_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,
                            int dst_type, int64_t dst_pitch, int ny, int nx, cudaStream_t st) {
-  k_convert<<<152 * 8, 256, 0, st>>>(src, src_type, src_pitch, dst, dst_type, dst_pitch, ny, nx);
+  k_convert<<<image_grid(ny, nx), 256, 0, st>>>(src, src_type, src_pitch, dst, dst_type, dst_pitch,
+                                                ny, nx);
   count_launches(1);
   return cudaGetLastError();
 }

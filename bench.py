@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batched", action="store_true",
                     help="also run the 256-field batched workload (about a minute)")
+    ap.add_argument("--large", action="store_true",
+                    help="also run the 8 x 50000^2 field (generated and pushed one snapshot "
+                         "at a time; about 90 GB of device memory with FP32 storage)")
     ap.add_argument("--accumulate", type=int, default=0,
                     help="also time ingest with snapshot accumulation: K raw device "
                          "snapshots summed per stack snapshot (Sec. 4.3.2)")
@@ -386,6 +389,45 @@ def batched_run(a, F, synth, torch, wave_bytes=200e9, reps=3, seed=11):
             "generation_s": round(t_gen, 1), "per_wave": per_wave}
 
 
+# ---------------------------------------------------------------- large-field leg
+def large_run(a, F, synth, torch, storage, steps=5, seed=3030):
+    """C3: 8 snapshots of 50000 x 50000 (MeerKAT-like PSF, 10^4 steady sources,
+    50 pulsars), both branches, window 5, 6 sigma; snapshots generated on the
+    device one at a time and pushed (FP32 in, stored in the chosen type)."""
+    spec = synth.C3
+    noise = {"meanstd": F.NOISE_MEANSTD, "medmad": F.NOISE_MEDMAD}[a.noise]
+    st = torch.cuda.current_stream()
+    plan = F.Plan(spec.nx, spec.ny, spec.nsnap, 5, 6.0, F.BRANCH_BOTH, storage, noise,
+                  stream=st.cuda_stream)
+    try:
+        for _, snap in synth.iter_stack(spec, seed, "cuda"):
+            F.fitrig_push_snapshot(plan.h, snap)
+            del snap
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        F.fitrig_detect(plan.h)
+        F.fitrig_detect(plan.h)
+        ms, stack_ms = [], []
+        for _ in range(steps):
+            rc, n = F.fitrig_detect(plan.h)
+            ms.append(F.fitrig_kernel_ms(plan.h, F.KERNEL_DETECT))
+            stack_ms.append(F.fitrig_kernel_ms(plan.h, F.KERNEL_STACK))
+        Ty, Tx = F.fitrig_tile_grid(plan.h)
+    finally:
+        plan.close()
+    L, px = spec.nsnap, spec.ny * spec.nx
+    eb = 4 if storage == F.F32 else 2
+    t, ts = statistics.median(ms), statistics.median(stack_ms)
+    alg = eb * L * px + 5 * (L - 2) * Ty * Tx
+    peak, _ = hbm_peak()
+    return {"workload": "8 snapshots of 50000x50000, MeerKAT-like PSF, both branches, window 5, "
+                        f"6 sigma, {a.noise} noise", "storage": {F.F32: "f32", F.BF16: "bf16",
+                                                                F.F16: "f16"}[storage],
+            "detect_ms": t, "value": L * px / (t * 1e-3) / 1e9, "unit": UNIT,
+            "stack_ms": ts, "stack_frac_of_hbm": alg / (ts * 1e-3) / 1e9 / peak,
+            "candidates": int(n), "status": int(rc)}
+
+
 # ---------------------------------------------------------------- accumulation leg
 def accumulate_run(a, F, torch, stack, storage, reps=3):
     """Ingest with snapshot accumulation (Sec. 4.3.2): K raw device snapshots
@@ -524,15 +566,19 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(used, 2)}
 
-    accum = None
+    accum = large = None
     if rank == 0 and ws == 1 and a.accumulate > 1:
         accum = accumulate_run(a, F, torch, stack, storage)
 
     serving = batched = None
-    if rank == 0 and ws == 1 and not (a.no_serving and not a.batched):
+    legs = rank == 0 and ws == 1 and (a.large or not (a.no_serving and not a.batched))
+    if legs:   # the remaining legs need the device memory of the main workload
         plan.close()
         del stack, stack_s
         torch.cuda.empty_cache()
+    if rank == 0 and ws == 1 and a.large:
+        large = large_run(a, F, synth, torch, storage)
+    if rank == 0 and ws == 1 and not (a.no_serving and not a.batched):
         if not a.no_serving:
             serving = serving_run(a, F, synth, torch)
         if a.batched:
@@ -557,6 +603,7 @@ def main():
             "serving": serving,
             "batched": batched,
             "accumulate": accum,
+            "large": large,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
         }

@@ -545,6 +545,32 @@ def detect(stack: np.ndarray, w: int, tau: float, branch: int = BRANCH_IMAGE,
     return det
 
 
+def freq_window(stack: np.ndarray, w: int, tau: float, n: int, noise: str = "meanstd",
+                forced: Optional[Dict[Tuple[int, int], bool]] = None):
+    """Real-time image-frequency branch: the Sec. 2.4.2 statistic over the last
+    ``n`` units of the stack only (units L-2-n .. L-3), each normalised by its
+    running M_s (the real-time reading of Sec. 2.2.4).  Returns (candidates,
+    eta, kbin, z) for the window ending at the stack's last unit; the
+    candidates' snapshot is that unit.  With n = L - 2 and a running maximum
+    that is already global at the first unit this is ``detect(...,
+    BRANCH_FREQ)`` exactly."""
+    x = np.asarray(stack)
+    L, ny, nx = x.shape
+    if not 1 <= n <= L - 2:
+        raise ValueError("window longer than the units of the stack")
+    Ty, Tx, nyu, nxu = tiling(ny, nx, w)
+    region = x[:, :nyu, :nxu]
+    Ms = normaliser_M_running(region)
+    first = L - 2 - n
+    tl = np.stack([tlisi_from_tiles(unit_tiles(x, s, w), Ms[s]) for s in range(first, L - 2)])
+    eta, kbin = spectrum(tl)
+    z, _, _ = zscore_map(eta, noise)
+    cands = freq_candidates(eta, kbin, z, tau, w, nyu, nxu, forced)
+    for c in cands:
+        c.snapshot = L - 3
+    return cands, eta, kbin, z
+
+
 def threshold_count(values: np.ndarray, tau: float, noise: str = "meanstd") -> int:
     """Number of entries of a plain map whose z-score exceeds tau."""
     z, _, _ = zscore_map(np.asarray(values, dtype=np.float64), noise)

@@ -509,3 +509,45 @@ def test_accumulation_reveals_pulse_too_faint_per_snapshot():
     acc = O.detect(O.accumulate(raw, k), w, 6.0, O.BRANCH_IMAGE, "meanstd")
     units = {c.snapshot for c in acc.candidates if (c.y, c.x) == (py, px)}
     assert units <= {0, 1, 3, 4, 6, 7, 9} and len(units) >= 5
+
+
+# ---------------------------------------------------------------- real-time frequency window
+def test_freq_window_over_all_units_is_the_batch_frequency_branch():
+    """With the window covering every unit, and the stack's maximum in its
+    first three snapshots (so the running M is the global M at every unit),
+    the real-time window gives the batch frequency branch exactly."""
+    x = synth.periodic_tile_stack(26, 40, 43, 4, 4, 1, (2, 3), 6.0, seed=31)
+    x[0, 0, 0] = 10.0 * np.abs(x).max()   # the maximum comes first
+    cands, eta, kbin, z = O.freq_window(x, 4, 4.0, 24, "medmad")
+    det = O.detect(x, 4, 4.0, O.BRANCH_FREQ, "medmad")
+    assert np.array_equal(eta, det.eta) and np.array_equal(kbin, det.eta_bin)
+    assert [(c.y, c.x, c.freq_bin) for c in cands] == \
+        [(c.y, c.x, c.freq_bin) for c in det.candidates]
+    assert all(c.snapshot == 23 for c in cands)
+
+
+def test_spectrum_magnitudes_ignore_circular_time_shifts():
+    """|X_k| of a circularly shifted series equals that of the series (the
+    shift multiplies X_k by a phase): a ring of unit maps in any rotation has
+    the same eta and bin."""
+    rs = np.random.default_rng(17)
+    cube = rs.random((14, 6, 7))
+    eta, kbin = O.spectrum(cube)
+    for r in (1, 5, 13):
+        e2, k2 = O.spectrum(np.roll(cube, r, axis=0))
+        np.testing.assert_allclose(e2, eta, rtol=1e-12, atol=0)
+        assert np.array_equal(k2, kbin)
+
+
+def test_freq_window_recovers_period_of_recent_pulses():
+    """A pulse of period 4 in the last 16 units of a 30-unit stack shows at bin
+    16/4 = 4 of a 16-unit window, at its tile."""
+    rs = np.random.default_rng(3)
+    L, ny, nx, w = 32, 24, 24, 4
+    x = 5.0 + 0.01 * rs.standard_normal((L, ny, nx))
+    for s in range(L - 18, L):
+        if s % 4 == 1:
+            x[s, 10, 14] += 3.0
+    cands, eta, kbin, z = O.freq_window(x, w, 4.0, 16, "meanstd")
+    assert kbin[10 // w, 14 // w] % 4 == 0
+    assert any((c.y // w, c.x // w) == (10 // w, 14 // w) for c in cands)

@@ -341,6 +341,22 @@ FITRIG_API int fitrig_batch_destroy(fitrig_batch_t batch);
 FITRIG_API int fitrig_server_create(int64_t hbm_budget_bytes, int max_fields, fitrig_server_t* out);
 FITRIG_API int fitrig_server_admit(fitrig_server_t server, int nx, int ny, int window,
                                    double nsigma, int storage, int noise, int32_t* field_id);
+/* fitrig_server_admit_freq -- as fitrig_server_admit, and the field also runs
+ * the image-frequency branch (Sec. 2.4.2) in real time over its last
+ * `freq_units` units (2..256): the tile statistic of each completed unit is
+ * kept in a ring on the device with the weight 1 / M_s^2, M_s the maximum
+ * over every snapshot seen so far (the real-time reading of M, Sec. 2.2.4),
+ * and from the unit that fills the ring on, every unit's result also holds
+ * the frequency candidates (branch FITRIG_BRANCH_FREQ, snapshot = the unit) of
+ * the unnormalised DFT of exact length freq_units over the window ending at
+ * that unit: eta = the largest spectral magnitude, its z-score over the
+ * field's tiles, components, tile centre + parabolic refine.  A result lists
+ * its frequency candidates first, then the image candidates, each sorted by
+ * (y, x).  Reserves freq_units tile maps more than fitrig_server_admit.
+ * EINVAL for freq_units < 2, EUNSUPPORTED above 256. */
+FITRIG_API int fitrig_server_admit_freq(fitrig_server_t server, int nx, int ny, int window,
+                                        double nsigma, int storage, int noise, int freq_units,
+                                        int32_t* field_id);
 FITRIG_API int fitrig_server_push(fitrig_server_t server, int32_t field, const void* data,
                                   int dtype, int64_t t_arrival_ns);
 FITRIG_API int fitrig_server_poll(fitrig_server_t server, fitrig_result* out, int32_t cap,

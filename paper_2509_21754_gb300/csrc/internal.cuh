@@ -318,6 +318,9 @@ cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
 // Ingest conversion (fp32 <-> bf16/fp16).
 cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,
                            int dst_type, int64_t dst_pitch, int ny, int nx, cudaStream_t st);
+// w = 1 / M^2 (M from the running-maximum key, floored at C): the weight of a
+// serving unit in the real-time frequency series.
+cudaError_t launch_unit_weight(const unsigned* gmax_key, float* w, cudaStream_t st);
 // Snapshot accumulation: acc (FP32, ny x nx dense) = src (first) or acc + src;
 // with `last` the sum goes to dst (storage type, pitch dst_pitch) instead.
 cudaError_t launch_accumulate(const void* src, int src_type, int64_t src_pitch, float* acc,

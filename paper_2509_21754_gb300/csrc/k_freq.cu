@@ -381,6 +381,22 @@ cudaError_t launch_accumulate(const void* src, int src_type, int64_t src_pitch, 
   return cudaGetLastError();
 }
 
+// A serving unit's frequency-series weight 1 / M_s^2 (FP64, rounded to FP32),
+// with M_s the running maximum over every snapshot seen so far (its ordered
+// key, 0 before any finite pixel), floored at C (Eq. 5's constant).
+__global__ void k_unit_weight(const unsigned* gmax_key, float* w) {
+  const unsigned k = *gmax_key;
+  double m = k ? (double)f32_from_key(k) : 0.0;
+  if (!(m > (double)kGuardC)) m = (double)kGuardC;
+  *w = (float)(1.0 / (m * m));
+}
+
+cudaError_t launch_unit_weight(const unsigned* gmax_key, float* w, cudaStream_t st) {
+  k_unit_weight<<<1, 1, 0, st>>>(gmax_key, w);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,
                            int dst_type, int64_t dst_pitch, int ny, int nx, cudaStream_t st) {
   k_convert<<<image_grid(ny, nx), 256, 0, st>>>(src, src_type, src_pitch, dst, dst_type, dst_pitch,

@@ -62,6 +62,14 @@ struct fitrig_plan_s {
   int stride = FITRIG_STRIDE_TILE;
   int mmode = FITRIG_MMODE_GLOBAL;
   int autotune = 0;
+  // real-time frequency branch of a serving field: a ring of the last hist_n
+  // units' tile statistics, with each unit's weight 1 / M_s^2 (running M)
+  int hist_n = 0;
+  int64_t hist_units = 0;    // units written into the ring so far
+  bool freq_ready = false;   // the ring holds hist_n units
+  float* d_hist = nullptr;   // [hist_n][vstride]
+  float* d_hwts = nullptr;   // [hist_n]
+  float2* d_htw = nullptr;   // twiddles of length hist_n
   int accumulate = 1;        // raw snapshots summed into one stack snapshot
   int raw_pushed = 0;        // raw snapshots of the block being summed
   float* d_accum = nullptr;  // [ny][nx] FP32 running sum (accumulate > 1)
@@ -165,6 +173,7 @@ static void free_all(fitrig_plan_t p) {
   void* ptrs[] = {p->d_stack, p->d_vp,  p->d_small, p->d_invalid,  p->d_cs, p->d_arg, p->d_inv,
                   p->d_thr,   p->d_noise, p->d_sel, p->d_cand,     p->d_cand_tmp,
                   p->d_bin,   p->d_tw,  p->d_staging, p->d_report, p->d_accum,
+                  p->d_hist,  p->d_hwts, p->d_htw,
                   p->d_smax,  p->d_mrun, p->d_wts};   // d_eta lives inside d_vp
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -361,6 +370,21 @@ static int alloc_select(fitrig_plan_t p) {
   return FITRIG_OK;
 }
 
+// Twiddle table of the length-n transform: (cos, sin)(2 pi ((k q) mod n) / n)
+// for k = 1..n/2, q = 1..(n-1)/2, computed in FP64 on the host.
+static int make_twiddles(fitrig_plan_t p, int n, float2** out) {
+  const int H = (n - 1) / 2, K = n / 2;
+  std::vector<float2> tw((size_t)std::max(1, K * H));
+  for (int k = 1; k <= K; ++k)
+    for (int q = 1; q <= H; ++q) {
+      const double ang = 2.0 * M_PI * (double)(((int64_t)k * q) % n) / (double)n;
+      tw[(size_t)(k - 1) * H + (q - 1)] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  CK(dmalloc(p, out, sizeof(float2) * tw.size()));
+  CK(cudaMemcpy(*out, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+  return FITRIG_OK;
+}
+
 static int allocate(fitrig_plan_t p) {
   if (p->allocated) return FITRIG_OK;
   const int eb = elem_bytes(p->storage);
@@ -420,15 +444,8 @@ static int allocate(fitrig_plan_t p) {
   }
   if (p->branch & FITRIG_BRANCH_FREQ) {
     CK(dmalloc(p, &p->d_bin, sizeof(int) * p->T));
-    const int n = U, H = (n - 1) / 2, K = n / 2;
-    std::vector<float2> tw((size_t)std::max(1, K * H));
-    for (int k = 1; k <= K; ++k)
-      for (int q = 1; q <= H; ++q) {
-        const double ang = 2.0 * M_PI * (double)(((int64_t)k * q) % n) / (double)n;
-        tw[(size_t)(k - 1) * H + (q - 1)] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-      }
-    CK(dmalloc(p, &p->d_tw, sizeof(float2) * tw.size()));
-    CK(cudaMemcpy(p->d_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+    const int rc = make_twiddles(p, U, &p->d_tw);
+    if (rc != FITRIG_OK) return rc;
   }
   if (p->mmode == FITRIG_MMODE_RUNNING) {
     CK(dmalloc(p, &p->d_smax, sizeof(unsigned) * 2 * p->L));
@@ -827,10 +844,17 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
   if (p->d_smax)
     CKE(launch_running_norm(p->d_stack, p->storage, p->pushed, p->nyu, p->nxu, p->pitch, p->d_smax,
                             p->d_mrun, p->d_wts, st));
-  const bool both = (p->branch & FITRIG_BRANCH_FREQ) && (p->branch & FITRIG_BRANCH_IMAGE);
-  if (p->branch & FITRIG_BRANCH_FREQ) {
+  // a serving field's frequency branch runs once its ring of units is full
+  const bool freq = (p->branch & FITRIG_BRANCH_FREQ) && (p->hist_n == 0 || p->freq_ready);
+  const bool both = freq && (p->branch & FITRIG_BRANCH_IMAGE);
+  if (freq) {
     mark(FITRIG_KERNEL_SPECTRUM, 0);
-    CKE(launch_spectrum(p->d_vp, U, p->T, p->vstride, p->d_tw, p->d_wts, p->d_eta, p->d_bin, st));
+    if (p->hist_n > 0)   // the ring in any rotation: |X_k| ignores circular shifts
+      CKE(launch_spectrum(p->d_hist, p->hist_n, p->T, p->vstride, p->d_htw, p->d_hwts, p->d_eta,
+                          p->d_bin, st));
+    else
+      CKE(launch_spectrum(p->d_vp, U, p->T, p->vstride, p->d_tw, p->d_wts, p->d_eta, p->d_bin,
+                          st));
     mark(FITRIG_KERNEL_SPECTRUM, 1);
     double* cs = p->d_cs + 2 * U;
     if (both) {
@@ -1434,6 +1458,7 @@ struct ServerField {
   int id = 0;
   int state = kFieldQueued;
   int nx = 0, ny = 0, w = 0, storage = 0, noise = 0;
+  int nwin = 0;                     // frequency-branch window in units (0: image only)
   double tau = 0.0;
   fitrig_plan_t plan = nullptr;
   cudaStream_t stream = nullptr;
@@ -1525,7 +1550,19 @@ int activate(fitrig_server_s* s, ServerField* f) {
     return rc;
   }
   p->ring = true;
+  if (f->nwin > 0) p->branch = FITRIG_BRANCH_BOTH;   // eta takes the slot after the unit
   rc = ensure_allocated(p);
+  if (rc == FITRIG_OK && f->nwin > 0) {
+    if (cudaMalloc(&p->d_hist, sizeof(float) * (size_t)f->nwin * p->vstride) != cudaSuccess ||
+        cudaMalloc(&p->d_hwts, sizeof(float) * f->nwin) != cudaSuccess) {
+      (void)cudaGetLastError();
+      rc = FITRIG_ENOMEM;
+    } else {
+      p->bytes += (int64_t)(sizeof(float) * ((size_t)f->nwin * p->vstride + f->nwin));
+      rc = make_twiddles(p, f->nwin, &p->d_htw);
+      p->hist_n = f->nwin;
+    }
+  }
   const int64_t need = p->bytes;
   if (rc != FITRIG_OK || s->used + need > s->budget) {
     fitrig_plan_destroy(p);
@@ -1604,6 +1641,42 @@ FITRIG_API int fitrig_server_admit(fitrig_server_t s, int nx, int ny, int window
   return FITRIG_OK;
 }
 
+FITRIG_API int fitrig_server_admit_freq(fitrig_server_t s, int nx, int ny, int window,
+                                        double nsigma, int storage, int noise, int freq_units,
+                                        int32_t* field_id) {
+  if (!s || !field_id) return FITRIG_EINVAL;
+  if (freq_units < 2) return FITRIG_EINVAL;
+  if (freq_units > 256) return FITRIG_EUNSUPPORTED;
+  if (nx < 1 || ny < 1 || window < 1 || window > std::min(nx, ny) || !(nsigma > 0.0)) return FITRIG_EINVAL;
+  if (storage != FITRIG_F32 && storage != FITRIG_BF16 && storage != FITRIG_F16) return FITRIG_EINVAL;
+  if (noise != FITRIG_NOISE_MEANSTD && noise != FITRIG_NOISE_MEDMAD) return FITRIG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mtx);
+  CK(cudaSetDevice(s->device));
+  ServerField* f = new (std::nothrow) ServerField();
+  if (!f) return FITRIG_ENOMEM;
+  f->id = (int)s->fields.size();
+  f->nx = nx;
+  f->ny = ny;
+  f->w = window;
+  f->tau = nsigma;
+  f->storage = storage;
+  f->noise = noise;
+  f->nwin = freq_units;
+  s->fields.push_back(f);
+  *field_id = f->id;
+  int rc = FITRIG_EBUSY;
+  if (s->waiting.empty() && s->active < s->max_fields) rc = activate(s, f);
+  if (rc == FITRIG_EBUSY) {
+    s->waiting.push_back(f->id);
+    return FITRIG_EBUSY;
+  }
+  if (rc != FITRIG_OK) {
+    f->state = kFieldRetired;
+    return rc;
+  }
+  return FITRIG_OK;
+}
+
 FITRIG_API int fitrig_server_field_state(fitrig_server_t s, int32_t field, int32_t* state) {
   if (!s || !state) return FITRIG_EINVAL;
   std::lock_guard<std::mutex> lk(s->mtx);
@@ -1646,6 +1719,15 @@ FITRIG_API int fitrig_server_push(fitrig_server_t s, int32_t field, const void* 
       p->zrot = (int)((f->received - 3) % 3);
       CK(enqueue_clear(p, st));
       CK(enqueue_march(p, st));
+      if (p->hist_n > 0) {
+        // the unit's tile statistics and weight into the ring of the last hist_n
+        const int64_t slot = p->hist_units % p->hist_n;
+        CK(cudaMemcpyAsync(p->d_hist + slot * p->vstride, p->d_vp, sizeof(float) * p->vstride,
+                           cudaMemcpyDeviceToDevice, st));
+        CK(launch_unit_weight(p->d_small, p->d_hwts + slot, st));
+        p->hist_units += 1;
+        p->freq_ready = p->hist_units >= p->hist_n;
+      }
       CK(enqueue_post(p, st, false));
       CK(launch_export_candidates(p->d_cand, reinterpret_cast<int*>(p->d_small + 2), f->d_cands,
                                   f->cand_cap, st));

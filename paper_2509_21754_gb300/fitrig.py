@@ -88,6 +88,8 @@ SIGNATURES = {
     "fitrig_batch_create": (c_int, [POINTER(P), c_int32, POINTER(P)]),
     "fitrig_server_create": (c_int, [c_int64, c_int, POINTER(P)]),
     "fitrig_server_admit": (c_int, [P, c_int, c_int, c_int, c_double, c_int, c_int, POINTER(c_int32)]),
+    "fitrig_server_admit_freq": (c_int, [P, c_int, c_int, c_int, c_double, c_int, c_int, c_int,
+                                         POINTER(c_int32)]),
     "fitrig_server_push": (c_int, [P, c_int32, P, c_int, c_int64]),
     "fitrig_server_poll": (c_int, [P, P, c_int32, P, c_int32, POINTER(c_int32), POINTER(c_int32)]),
     "fitrig_server_drain": (c_int, [P]),
@@ -350,6 +352,17 @@ def fitrig_server_admit(server, nx, ny, window, nsigma, storage=F32, noise=NOISE
     rc = load().fitrig_server_admit(server, nx, ny, window, float(nsigma), storage, noise,
                                     byref(fid))
     _check(rc, "fitrig_server_admit", allow=(OK, EBUSY))
+    return rc, fid.value
+
+
+def fitrig_server_admit_freq(server, nx, ny, window, nsigma, storage=F32,
+                             noise=NOISE_MEANSTD, freq_units=16):
+    """Admit a field with the real-time frequency branch over its last
+    freq_units units; returns (status, field id) (EBUSY = queued)."""
+    fid = c_int32()
+    rc = load().fitrig_server_admit_freq(server, int(nx), int(ny), int(window), float(nsigma),
+                                         int(storage), int(noise), int(freq_units), byref(fid))
+    _check(rc, "fitrig_server_admit_freq", allow=(OK, EBUSY))
     return rc, fid.value
 
 

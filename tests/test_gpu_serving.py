@@ -120,3 +120,50 @@ def test_admission_is_fifo_under_the_budget():
         assert F.fitrig_server_push(srv, states[2][1], x, 0) == F.OK
     finally:
         F.fitrig_server_destroy(srv)
+
+
+@pytest.mark.parametrize("nwin,noise", [(14, F.NOISE_MEDMAD), (9, F.NOISE_MEANSTD)])
+def test_realtime_frequency_window(nwin, noise):
+    """A field admitted with the real-time frequency branch: before its ring of
+    nwin units is full a unit has image candidates only; from then on it also
+    has the frequency candidates of the last nwin units (tile statistic over
+    the running M_s^2), equal to the oracle's on that window: the same tiles
+    except where the oracle's z lies within 1e-4 tau of tau, significance to
+    1e-4.  Its image candidates equal those of an image-only field."""
+    from oracle import fitrig_oracle as O
+    L, ny, nx, w, tau = nwin + 8, 120, 131, 4, 4.0
+    x = synth.periodic_tile_stack(L, ny, nx, w, 4, 2, (11, 7), 6.0, seed=nwin)
+    stack = torch.from_numpy(x)
+    srv = F.fitrig_server_create(8 << 30, 4)
+    try:
+        rc, fid = F.fitrig_server_admit_freq(srv, nx, ny, w, tau, F.F32, noise, nwin)
+        rc2, fid2 = F.fitrig_server_admit(srv, nx, ny, w, tau, F.F32, noise)
+        assert rc == F.OK and rc2 == F.OK
+        serve(srv, fid, stack, torch.float32)
+        serve(srv, fid2, stack, torch.float32)
+        got = collect(srv)
+    finally:
+        F.fitrig_server_destroy(srv)
+    name = "medmad" if noise == F.NOISE_MEDMAD else "meanstd"
+    found_pulse = 0
+    for u in range(L - 2):
+        r, c = got[(fid, u)]
+        assert r["status"] in (F.OK, F.ENONFINITE)
+        img, fq = c[c["branch"] == F.BRANCH_IMAGE], c[c["branch"] == F.BRANCH_FREQ]
+        assert img.tobytes() == got[(fid2, u)][1].tobytes()
+        if u < nwin - 1:
+            assert fq.size == 0
+            continue
+        want, eta, kbin, z = O.freq_window(x[:u + 3], w, tau, nwin, name)
+        amb = np.abs(z - tau) <= 1e-4 * tau
+        g = {(int(a["y"]) // w, int(a["x"]) // w): a for a in fq}
+        o = {(c_.y // w, c_.x // w): c_ for c_ in want}
+        for t in set(g) ^ set(o):
+            assert amb[t], (u, t)
+        for t in set(g) & set(o):
+            assert g[t]["snapshot"] == u and o[t].snapshot == u
+            assert (int(g[t]["y"]), int(g[t]["x"])) == (o[t].y, o[t].x)
+            assert g[t]["significance"] == pytest.approx(o[t].significance, rel=1e-4)
+            assert 1 <= g[t]["freq_bin"] <= nwin // 2
+        found_pulse += (11, 7) in g
+    assert found_pulse >= 1

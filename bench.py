@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batched", action="store_true",
                     help="also run the 256-field batched workload (about a minute)")
+    ap.add_argument("--serving-freq", type=int, default=0,
+                    help="serving fields also run the real-time frequency branch over their "
+                         "last N units")
     ap.add_argument("--large", action="store_true",
                     help="also run the 8 x 50000^2 field (generated and pushed one snapshot "
                          "at a time; about 90 GB of device memory with FP32 storage)")
@@ -259,7 +262,8 @@ def _cuda():
 
 
 # ---------------------------------------------------------------- serving leg
-def serving_run(a, F, synth, torch, nfields=32, nsnap=24, compression=20.0, seed=7):
+def serving_run(a, F, synth, torch, nfields=32, nsnap=24, compression=20.0, seed=7,
+                freq_units=0):
     """C5-like serving: fields stream snapshots (Poisson arrivals, mean 2 s,
     time-compressed) through the server API; returns latency/throughput."""
     import threading
@@ -277,8 +281,12 @@ def serving_run(a, F, synth, torch, nfields=32, nsnap=24, compression=20.0, seed
     try:
         ids = []
         for side in sides:
-            rc, fid = F.fitrig_server_admit(srv, side, side, a.window, a.nsigma, F.BF16,
-                                            F.NOISE_MEDMAD)
+            if freq_units:
+                rc, fid = F.fitrig_server_admit_freq(srv, side, side, a.window, a.nsigma, F.BF16,
+                                                     F.NOISE_MEDMAD, freq_units)
+            else:
+                rc, fid = F.fitrig_server_admit(srv, side, side, a.window, a.nsigma, F.BF16,
+                                                F.NOISE_MEDMAD)
             ids.append((rc, fid))
         active = [(fid, pools[k]) for k, (rc, fid) in enumerate(ids) if rc == F.OK]
         mean_gap = 2.0 / compression
@@ -317,6 +325,7 @@ def serving_run(a, F, synth, torch, nfields=32, nsnap=24, compression=20.0, seed
             "compression": compression, "storage": "bf16", "noise": "medmad",
             "reserved_gb": used / 1e9,
             "sides": "uniform 2048..16384, seeded",
+            "freq_units": freq_units,
         }
     finally:
         F.fitrig_server_destroy(srv)
@@ -580,7 +589,7 @@ def main():
         large = large_run(a, F, synth, torch, storage)
     if rank == 0 and ws == 1 and not (a.no_serving and not a.batched):
         if not a.no_serving:
-            serving = serving_run(a, F, synth, torch)
+            serving = serving_run(a, F, synth, torch, freq_units=a.serving_freq)
         if a.batched:
             batched = batched_run(a, F, synth, torch)
 

@@ -365,6 +365,21 @@ FITRIG_API int fitrig_server_poll(fitrig_server_t server, fitrig_result* out, in
 FITRIG_API int fitrig_server_drain(fitrig_server_t server);
 FITRIG_API int fitrig_server_retire(fitrig_server_t server, int32_t field);
 FITRIG_API int fitrig_server_field_state(fitrig_server_t server, int32_t field, int32_t* state);
+/* fitrig_server_field_export -- checkpoint of an active field (no counterpart
+ * in the paper; the real-time trigger of Sec. 3.2 keeps this state on the
+ * device): its configuration, the last two snapshots as stored, the running
+ * maximum M, the frequency ring with its weights and the counters, written
+ * to `out` (host memory, `cap` bytes) after the field's pushed units have
+ * finished.  *size = the bytes needed; ETRUNC (nothing written) when cap is
+ * smaller or out is NULL; ESTATE unless the field is active.
+ * fitrig_server_field_import -- a new active field from such an image, on
+ * this or another server: its later pushes give exactly the results the
+ * exported field would have given (unit numbers continue).  EBUSY when it
+ * does not fit now (nothing is queued), EINVAL for a malformed image. */
+FITRIG_API int fitrig_server_field_export(fitrig_server_t server, int32_t field, void* out,
+                                          int64_t cap, int64_t* size);
+FITRIG_API int fitrig_server_field_import(fitrig_server_t server, const void* image, int64_t size,
+                                          int32_t* field_id);
 FITRIG_API int fitrig_server_usage(fitrig_server_t server, int64_t* used_bytes, int32_t* active,
                                    int32_t* waiting);
 FITRIG_API int fitrig_server_destroy(fitrig_server_t server);

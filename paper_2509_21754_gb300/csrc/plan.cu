@@ -1771,6 +1771,130 @@ FITRIG_API int fitrig_server_drain(fitrig_server_t s) {
   return FITRIG_OK;
 }
 
+// ---- checkpoint / resume of a serving field
+namespace {
+struct FieldImage {            // header of an exported field (host byte order)
+  char magic[8];               // "FITRIGF1"
+  int32_t nx, ny, w, storage, noise, nwin;
+  double tau;
+  int64_t received, hist_units;
+  uint32_t gmax_key, nsnaps;   // running-maximum key; snapshots that follow (0..2)
+  int64_t slice_bytes, hist_bytes;
+};
+constexpr char kFieldMagic[8] = {'F', 'I', 'T', 'R', 'I', 'G', 'F', '1'};
+
+int64_t field_image_bytes(const ServerField* f, const fitrig_plan_t p) {
+  const int64_t ns = std::min<int64_t>(2, f->received);
+  const int64_t hist = p->hist_n ? (int64_t)sizeof(float) * ((int64_t)p->hist_n * p->vstride + p->hist_n) : 0;
+  return (int64_t)sizeof(FieldImage) + ns * (int64_t)p->slice_bytes + hist;
+}
+}  // namespace
+
+FITRIG_API int fitrig_server_field_export(fitrig_server_t s, int32_t field, void* out, int64_t cap,
+                                          int64_t* size) {
+  if (!s || !size) return FITRIG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mtx);
+  if (field < 0 || field >= (int)s->fields.size()) return FITRIG_EINVAL;
+  ServerField* f = s->fields[field];
+  if (f->state != kFieldActive) return FITRIG_ESTATE;
+  fitrig_plan_t p = f->plan;
+  *size = field_image_bytes(f, p);
+  if (!out || cap < *size) return FITRIG_ETRUNC;
+  CK(cudaSetDevice(s->device));
+  CK(cudaStreamSynchronize(f->stream));   // every pushed unit is complete
+  FieldImage h{};
+  memcpy(h.magic, kFieldMagic, 8);
+  h.nx = f->nx;
+  h.ny = f->ny;
+  h.w = f->w;
+  h.storage = f->storage;
+  h.noise = f->noise;
+  h.nwin = f->nwin;
+  h.tau = f->tau;
+  h.received = f->received;
+  h.hist_units = p->hist_units;
+  h.nsnaps = (uint32_t)std::min<int64_t>(2, f->received);
+  h.slice_bytes = (int64_t)p->slice_bytes;
+  h.hist_bytes = p->hist_n ? (int64_t)sizeof(float) * ((int64_t)p->hist_n * p->vstride + p->hist_n) : 0;
+  CK(cudaMemcpy(&h.gmax_key, p->d_small, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  char* o = static_cast<char*>(out);
+  memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  for (int64_t r = f->received - h.nsnaps; r < f->received; ++r) {   // oldest first
+    CK(cudaMemcpy(o, p->d_stack + p->slice_bytes * (r % 3), p->slice_bytes, cudaMemcpyDeviceToHost));
+    o += p->slice_bytes;
+  }
+  if (p->hist_n) {
+    CK(cudaMemcpy(o, p->d_hist, sizeof(float) * (size_t)p->hist_n * p->vstride, cudaMemcpyDeviceToHost));
+    o += sizeof(float) * (size_t)p->hist_n * p->vstride;
+    CK(cudaMemcpy(o, p->d_hwts, sizeof(float) * p->hist_n, cudaMemcpyDeviceToHost));
+  }
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_server_field_import(fitrig_server_t s, const void* image, int64_t size,
+                                          int32_t* field_id) {
+  if (!s || !image || !field_id || size < (int64_t)sizeof(FieldImage)) return FITRIG_EINVAL;
+  FieldImage h;
+  memcpy(&h, image, sizeof(h));
+  if (memcmp(h.magic, kFieldMagic, 8) != 0 || h.nsnaps > 2 || h.received < 0 ||
+      h.nsnaps != (uint32_t)std::min<int64_t>(2, h.received) || h.hist_units < 0 ||
+      size != (int64_t)sizeof(h) + (int64_t)h.nsnaps * h.slice_bytes + h.hist_bytes)
+    return FITRIG_EINVAL;
+  if (h.nx < 1 || h.ny < 1 || h.w < 1 || h.w > std::min(h.nx, h.ny) || !(h.tau > 0.0) ||
+      (h.storage != FITRIG_F32 && h.storage != FITRIG_BF16 && h.storage != FITRIG_F16) ||
+      (h.noise != FITRIG_NOISE_MEANSTD && h.noise != FITRIG_NOISE_MEDMAD) || h.nwin < 0 || h.nwin > 256)
+    return FITRIG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mtx);
+  CK(cudaSetDevice(s->device));
+  if (!s->waiting.empty() || s->active >= s->max_fields) return FITRIG_EBUSY;
+  ServerField* f = new (std::nothrow) ServerField();
+  if (!f) return FITRIG_ENOMEM;
+  f->nx = h.nx;
+  f->ny = h.ny;
+  f->w = h.w;
+  f->tau = h.tau;
+  f->storage = h.storage;
+  f->noise = h.noise;
+  f->nwin = h.nwin;
+  const int rc = activate(s, f);   // nothing is queued by an import
+  if (rc != FITRIG_OK) {
+    delete f;
+    return rc;
+  }
+  fitrig_plan_t p = f->plan;
+  const int64_t hist = p->hist_n ? (int64_t)sizeof(float) * ((int64_t)p->hist_n * p->vstride + p->hist_n) : 0;
+  bool ok = h.slice_bytes == (int64_t)p->slice_bytes && h.hist_bytes == hist;
+  const char* in = static_cast<const char*>(image) + sizeof(h);
+  for (int64_t r = h.received - h.nsnaps; ok && r < h.received; ++r) {
+    ok = cudaMemcpy(p->d_stack + p->slice_bytes * (r % 3), in, p->slice_bytes,
+                    cudaMemcpyHostToDevice) == cudaSuccess;
+    in += p->slice_bytes;
+  }
+  if (ok && p->hist_n) {
+    ok = cudaMemcpy(p->d_hist, in, sizeof(float) * (size_t)p->hist_n * p->vstride,
+                    cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->d_hwts, in + sizeof(float) * (size_t)p->hist_n * p->vstride,
+                    sizeof(float) * p->hist_n, cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  ok = ok && cudaMemcpy(p->d_small, &h.gmax_key, sizeof(uint32_t), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    (void)cudaGetLastError();
+    s->used -= f->bytes;
+    --s->active;
+    free_field(f);
+    delete f;
+    return FITRIG_EINVAL;
+  }
+  f->received = h.received;
+  p->hist_units = h.hist_units;
+  p->freq_ready = p->hist_n > 0 && p->hist_units >= p->hist_n;
+  f->id = (int)s->fields.size();
+  s->fields.push_back(f);
+  *field_id = f->id;
+  return FITRIG_OK;
+}
+
 FITRIG_API int fitrig_server_retire(fitrig_server_t s, int32_t field) {
   if (!s) return FITRIG_EINVAL;
   std::lock_guard<std::mutex> lk(s->mtx);

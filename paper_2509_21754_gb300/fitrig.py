@@ -95,6 +95,8 @@ SIGNATURES = {
     "fitrig_server_drain": (c_int, [P]),
     "fitrig_server_retire": (c_int, [P, c_int32]),
     "fitrig_server_field_state": (c_int, [P, c_int32, POINTER(c_int32)]),
+    "fitrig_server_field_export": (c_int, [P, c_int32, P, c_int64, POINTER(c_int64)]),
+    "fitrig_server_field_import": (c_int, [P, P, c_int64, POINTER(c_int32)]),
     "fitrig_server_usage": (c_int, [P, POINTER(c_int64), POINTER(c_int32), POINTER(c_int32)]),
     "fitrig_server_destroy": (c_int, [P]),
     "fitrig_batch_detect": (c_int, [P, POINTER(c_int32)]),
@@ -397,6 +399,26 @@ def fitrig_server_field_state(server, field: int) -> int:
     st = c_int32()
     _check(load().fitrig_server_field_state(server, field, byref(st)), "fitrig_server_field_state")
     return st.value
+
+
+def fitrig_server_field_export(server, field: int) -> bytes:
+    """Checkpoint of an active field as bytes."""
+    size = c_int64()
+    rc = load().fitrig_server_field_export(server, int(field), None, 0, byref(size))
+    _check(rc, "fitrig_server_field_export", allow=(ETRUNC,))
+    buf = ctypes.create_string_buffer(size.value)
+    _check(load().fitrig_server_field_export(server, int(field), buf, size.value, byref(size)),
+           "fitrig_server_field_export")
+    return buf.raw
+
+
+def fitrig_server_field_import(server, image: bytes) -> Tuple[int, int]:
+    """A new active field from a checkpoint; returns (status, field id)."""
+    fid = c_int32()
+    buf = ctypes.create_string_buffer(image, len(image))
+    rc = load().fitrig_server_field_import(server, buf, len(image), byref(fid))
+    _check(rc, "fitrig_server_field_import", allow=(OK, EBUSY))
+    return rc, fid.value
 
 
 def fitrig_server_usage(server) -> Tuple[int, int, int]:

@@ -5,6 +5,7 @@
   concurrently from several threads (their work overlaps on the device);
 * admission queues fields that do not fit the HBM budget, FIFO.
 """
+import ctypes
 import threading
 import time
 
@@ -167,3 +168,43 @@ def test_realtime_frequency_window(nwin, noise):
             assert 1 <= g[t]["freq_bin"] <= nwin // 2
         found_pulse += (11, 7) in g
     assert found_pulse >= 1
+
+
+@pytest.mark.parametrize("nwin", [0, 6])
+def test_field_checkpoint_resumes_exactly(nwin):
+    """A field exported after 10 of 20 snapshots and imported into another
+    server gives, for the next snapshots, byte-identical results to the
+    original field (image and real-time frequency candidates, unit numbers)."""
+    stack = field_stack(20, 150, 161, seed=40 + nwin)
+    srv_a = F.fitrig_server_create(8 << 30, 4)
+    srv_b = F.fitrig_server_create(8 << 30, 4)
+    try:
+        admit = (lambda srv: F.fitrig_server_admit_freq(srv, 161, 150, 5, 4.0, F.F32,
+                                                        F.NOISE_MEDMAD, nwin)) if nwin else \
+                (lambda srv: F.fitrig_server_admit(srv, 161, 150, 5, 4.0, F.F32, F.NOISE_MEDMAD))
+        rc, fa = admit(srv_a)
+        assert rc == F.OK
+        serve(srv_a, fa, stack[:10], torch.float32)
+        collect(srv_a)
+        size = ctypes.c_int64()
+        lib = F.load()
+        assert lib.fitrig_server_field_export(srv_a, fa, None, 0, ctypes.byref(size)) == F.ETRUNC
+        image = F.fitrig_server_field_export(srv_a, fa)
+        assert len(image) == size.value
+        rc, fb = F.fitrig_server_field_import(srv_b, image)
+        assert rc == F.OK and F.fitrig_server_field_state(srv_b, fb) == F.FIELD_ACTIVE
+        bad = bytearray(image)
+        bad[0] ^= 1
+        assert lib.fitrig_server_field_import(srv_b, bytes(bad), len(bad),
+                                              ctypes.byref(ctypes.c_int32())) == F.EINVAL
+        serve(srv_a, fa, stack[10:], torch.float32)
+        serve(srv_b, fb, stack[10:], torch.float32)
+        ra, rb = collect(srv_a), collect(srv_b)
+        assert sorted(u for (_, u) in rb) == list(range(8, 18))
+        for u in range(8, 18):
+            (r1, c1), (r2, c2) = ra[(fa, u)], rb[(fb, u)]
+            assert c1.tobytes() == c2.tobytes(), u
+            assert r1["status"] == r2["status"]
+    finally:
+        F.fitrig_server_destroy(srv_a)
+        F.fitrig_server_destroy(srv_b)

@@ -396,6 +396,16 @@ FITRIG_API int fitrig_server_destroy(fitrig_server_t server);
 FITRIG_API int fitrig_autotune(int window, int storage, int32_t* tile_rows, int32_t* stages,
                                float* best_ms);
 
+/* fitrig_wait_probe -- failure detection without a fault (no counterpart in
+ * the paper): one device wait on an mbarrier that nothing completes, bounded
+ * by timeout_ns through the same helper as every wait of the trigger's
+ * kernels (which spin on mbarrier.try_wait and give up once %globaltimer
+ * passes their deadline).  Returns FITRIG_ETIMEOUT when the wait gave up --
+ * the expected result -- after which the context stays usable.  timeout_ns
+ * in (0, 10^10]; stream as in FITRIG_OPT_STREAM (0: legacy stream).
+ * Synchronises the stream. */
+FITRIG_API int fitrig_wait_probe(int64_t timeout_ns, int64_t stream);
+
 /* fitrig_launch_count -- number of CUDA kernels this library has launched in
  * the process so far (all plans); for accounting in benchmarks. */
 FITRIG_API int fitrig_launch_count(int64_t* count);

@@ -192,6 +192,8 @@ cudaError_t launch_stack(const CUtensorMap* tmap, const StackArgs& a, int storag
                          cudaStream_t st);
 cudaError_t launch_finite_max(const void* stack, int storage, int L, int ny, int nx,
                               int64_t pitch, unsigned* gmax, cudaStream_t st);
+// One device wait, bounded like the march's, on a barrier nothing completes.
+cudaError_t launch_wait_probe(uint64_t timeout_ns, unsigned* gave_up, cudaStream_t st);
 
 // Sliding-window mode geometry (see k_slide.cu).
 struct SlideGeom {

@@ -546,6 +546,24 @@ __global__ void k_finite_max(const T* __restrict__ x, int L, int ny, int nx, int
   if ((threadIdx.x & 31) == 0 && m > -INFINITY) atomicMax(gmax, f32_key(m));
 }
 
+// One bounded wait on an mbarrier that nothing completes (fitrig_wait_probe):
+// the same helper as the march's waits; reports whether it gave up.
+__global__ void k_wait_probe(uint64_t timeout_ns, unsigned* gave_up) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  fence_mbar_init();
+  const bool ok = mbar_wait_bounded(b, 0u, globaltimer_ns() + timeout_ns);
+  *gave_up = ok ? 0u : 1u;
+}
+
+cudaError_t launch_wait_probe(uint64_t timeout_ns, unsigned* gave_up, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(timeout_ns, gave_up);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 bool small_geometry(int w, int elem_bytes, int tby, int stages, StackGeom* g) {
   // 32 tiles across (lane = tile), TBY tile rows per CTA
   if (w < 3 || w > kSmallMaxW || tby < 1 || 32 * tby > kSmallMaxThreads || stages < 2) return false;

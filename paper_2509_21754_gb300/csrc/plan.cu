@@ -1949,6 +1949,23 @@ FITRIG_API int fitrig_server_destroy(fitrig_server_t s) {
   return FITRIG_OK;
 }
 
+FITRIG_API int fitrig_wait_probe(int64_t timeout_ns, int64_t stream) {
+  if (timeout_ns <= 0 || timeout_ns > 10000000000ll) return FITRIG_EINVAL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned* d = nullptr;
+  unsigned h = 0;
+  CK(cudaMalloc(&d, sizeof(unsigned)));
+  cudaError_t e = launch_wait_probe((uint64_t)timeout_ns, d, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return FITRIG_ECUDA;
+  }
+  return h ? FITRIG_ETIMEOUT : FITRIG_OK;
+}
+
 FITRIG_API int fitrig_launch_count(int64_t* count) {
   if (!count) return FITRIG_EINVAL;
   *count = g_launches.load(std::memory_order_relaxed);

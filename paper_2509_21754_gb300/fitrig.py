@@ -85,6 +85,7 @@ SIGNATURES = {
     "fitrig_threshold_map": (c_int, [P, c_int64, c_double, c_int, c_int64,
                                      POINTER(c_int64), POINTER(c_double), POINTER(c_double)]),
     "fitrig_launch_count": (c_int, [POINTER(c_int64)]),
+    "fitrig_wait_probe": (c_int, [c_int64, c_int64]),
     "fitrig_batch_create": (c_int, [POINTER(P), c_int32, POINTER(P)]),
     "fitrig_server_create": (c_int, [c_int64, c_int, POINTER(P)]),
     "fitrig_server_admit": (c_int, [P, c_int, c_int, c_int, c_double, c_int, c_int, POINTER(c_int32)]),
@@ -429,6 +430,12 @@ def fitrig_server_usage(server) -> Tuple[int, int, int]:
 
 def fitrig_server_destroy(server) -> None:
     _check(load().fitrig_server_destroy(server), "fitrig_server_destroy")
+
+
+def fitrig_wait_probe(timeout_ns: int, stream: int = 0) -> int:
+    """One bounded device wait that nothing completes; returns the status
+    (ETIMEOUT is the expected result)."""
+    return load().fitrig_wait_probe(int(timeout_ns), int(stream))
 
 
 def fitrig_launch_count() -> int:

@@ -2,6 +2,7 @@
 candidate, on seeded synthetic stacks.  All calls go through the C ABI."""
 import ctypes
 import math
+import time
 
 import numpy as np
 import pytest
@@ -495,3 +496,18 @@ def test_device_pushes_wait_for_their_producer():
         for k in range(L):
             got = device_view(*F.fitrig_stack_device_ptr(p.h, k), ny, torch.bfloat16)
             assert torch.equal(got[:, :nx].cpu(), kept[k]), k
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """Failure detection without a fault: one device wait, bounded exactly as
+    the trigger's TMA waits are, on an mbarrier that nothing ever completes
+    gives up after its bound and reports ETIMEOUT; the context stays usable
+    (a detect right after equals one made before)."""
+    stack, _ = synth.make_stack(synth.small_spec(8, 200, 210), seed=78, device="cuda")
+    before = F.detect_stack(stack, 5, 4.0, F.BRANCH_BOTH, dumps=False)
+    lib = F.load()
+    t0 = time.perf_counter()
+    assert lib.fitrig_wait_probe(20_000_000, 0) == F.ETIMEOUT   # 20 ms bound
+    assert time.perf_counter() - t0 < 5.0
+    after = F.detect_stack(stack, 5, 4.0, F.BRANCH_BOTH, dumps=False)
+    assert after["candidates"].tobytes() == before["candidates"].tobytes()

@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batched", action="store_true",
                     help="also run the 256-field batched workload (about a minute)")
+    ap.add_argument("--serving-compression", type=float, default=20.0,
+                    help="time compression of the serving leg's Poisson arrivals")
     ap.add_argument("--serving-freq", type=int, default=0,
                     help="serving fields also run the real-time frequency branch over their "
                          "last N units")
@@ -589,7 +591,8 @@ def main():
         large = large_run(a, F, synth, torch, storage)
     if rank == 0 and ws == 1 and not (a.no_serving and not a.batched):
         if not a.no_serving:
-            serving = serving_run(a, F, synth, torch, freq_units=a.serving_freq)
+            serving = serving_run(a, F, synth, torch, freq_units=a.serving_freq,
+                                  compression=a.serving_compression)
         if a.batched:
             batched = batched_run(a, F, synth, torch)
 

@@ -182,6 +182,23 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t plan, int option, int64_t value);
 FITRIG_API int fitrig_push_snapshot(fitrig_plan_t plan, const void* data, int dtype,
                                     int on_device, int64_t row_pitch_elems);
 
+/*
+ * fitrig_push_snapshots -- push `count` snapshots in one call, the same as
+ * `count` calls of fitrig_push_snapshot in order: snapshot i starts
+ * `snap_stride_elems` elements after snapshot i-1 (0 means row_pitch * ny) and
+ * holds ny rows of `row_pitch_elems` elements (0 means nx).  A host buffer is
+ * borrowed until the call returns (one synchronisation at the end, not one per
+ * snapshot).  When the host snapshots are contiguous rows of the storage type
+ * and the plan's rows are unpadded (nx * element size a multiple of 128 bytes),
+ * the block goes as one transfer split into four row bands on the side
+ * streams.  With FITRIG_OPT_ACCUMULATE = K they are raw snapshots (K per slot).
+ * EINVAL for count < 0 or a stride shorter than one snapshot; ESTATE (nothing
+ * pushed) when they do not fit into the remaining slots.
+ */
+FITRIG_API int fitrig_push_snapshots(fitrig_plan_t plan, const void* data, int32_t count,
+                                     int dtype, int on_device, int64_t row_pitch_elems,
+                                     int64_t snap_stride_elems);
+
 /* fitrig_plan_reset -- forget the pushed snapshots (keeps the memory) so a new
  * stack of the same shape can be pushed. */
 FITRIG_API int fitrig_plan_reset(fitrig_plan_t plan);
@@ -201,7 +218,8 @@ FITRIG_API int fitrig_detect(fitrig_plan_t plan, int32_t* ncand);
 
 /* fitrig_candidates -- copy the candidates of the last detect, sorted by
  * (snapshot, y, x), into `out` (host, `cap` entries).  ETRUNC with *n = the
- * full count when cap is too small (the first cap entries are written). */
+ * full count when cap is too small (the first cap entries are written).
+ * Pinned host memory, reused across detects, is the fastest `out`. */
 FITRIG_API int fitrig_candidates(fitrig_plan_t plan, fitrig_candidate* out, int32_t cap,
                                  int32_t* n);
 

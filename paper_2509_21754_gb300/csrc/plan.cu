@@ -640,8 +640,7 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t p, int option, int64_t value) {
 // already on `st` and `st` waits for all of them.  A copy whose rows are
 // contiguous on both sides goes as one linear copy per band.
 static cudaError_t copy_rows_h2d(fitrig_plan_t p, void* dst, size_t dpitch, const void* src,
-                                 size_t spitch, size_t width, cudaStream_t st) {
-  const int ny = p->ny;
+                                 size_t spitch, size_t width, int64_t ny, cudaStream_t st) {
   const size_t bytes = width * (size_t)ny;
   const bool linear = dpitch == width && spitch == width;
   int nb = bytes >= ((size_t)32 << 20) ? 4 : 1;
@@ -661,9 +660,9 @@ static cudaError_t copy_rows_h2d(fitrig_plan_t p, void* dst, size_t dpitch, cons
     return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, ny, cudaMemcpyHostToDevice, st);
   }
   cudaError_t e = cudaEventRecord(p->copy_ev[4], st);
-  const int band = (ny + nb - 1) / nb;
+  const int64_t band = (ny + nb - 1) / nb;
   for (int i = 0; i < nb && e == cudaSuccess; ++i) {
-    const int r0 = i * band, r1 = std::min(ny, r0 + band);
+    const int64_t r0 = i * band, r1 = std::min(ny, r0 + band);
     if (r0 >= r1) break;
     cudaStream_t cs = p->copy_st[i];
     e = cudaStreamWaitEvent(cs, p->copy_ev[4], 0);
@@ -679,16 +678,11 @@ static cudaError_t copy_rows_h2d(fitrig_plan_t p, void* dst, size_t dpitch, cons
   return e;
 }
 
-FITRIG_API int fitrig_push_snapshot(fitrig_plan_t p, const void* data, int dtype, int on_device,
-                                    int64_t row_pitch_elems) {
-  if (!p || !data) return FITRIG_EINVAL;
-  if (dtype != FITRIG_F32 && dtype != FITRIG_BF16 && dtype != FITRIG_F16) return FITRIG_EINVAL;
-  const int64_t rp = row_pitch_elems ? row_pitch_elems : p->nx;
-  if (rp < p->nx) return FITRIG_EINVAL;
-  if (p->pushed >= p->L) return FITRIG_ESTATE;
-  CK(cudaSetDevice(p->device));
-  int rc = ensure_allocated(p);
-  if (rc != FITRIG_OK) return rc;
+// One snapshot into the next slot; arguments already validated.  With `sync`
+// a host push returns only after its copy finished (the caller may then reuse
+// the buffer); without it the caller synchronises the plan's stream.
+static int push_one(fitrig_plan_t p, const void* data, int dtype, int on_device, int64_t rp,
+                    bool sync) {
   cudaStream_t st = plan_stream(p);
   const int eb = elem_bytes(p->storage), ib = elem_bytes(dtype);
   char* dst = p->d_stack + p->slice_bytes * p->pushed;
@@ -699,7 +693,7 @@ FITRIG_API int fitrig_push_snapshot(fitrig_plan_t p, const void* data, int dtype
     if (!on_device) {
       if (!p->d_staging) CK(dmalloc(p, &p->d_staging, (size_t)p->nx * p->ny * 4));
       CK(copy_rows_h2d(p, p->d_staging, (size_t)p->nx * ib, data, (size_t)rp * ib,
-                       (size_t)p->nx * ib, st));
+                       (size_t)p->nx * ib, p->ny, st));
       src = p->d_staging;
       sp = p->nx;
     }
@@ -707,7 +701,7 @@ FITRIG_API int fitrig_push_snapshot(fitrig_plan_t p, const void* data, int dtype
     const bool first = p->raw_pushed == 0, last = p->raw_pushed + 1 == p->accumulate;
     CK(launch_accumulate(src, dtype, sp, p->d_accum, first, last, dst, p->storage, p->pitch,
                          p->ny, p->nx, st));
-    if (!on_device) CK(cudaStreamSynchronize(st));
+    if (!on_device && sync) CK(cudaStreamSynchronize(st));
     if (!last) {
       p->raw_pushed += 1;
       return FITRIG_OK;
@@ -723,22 +717,82 @@ FITRIG_API int fitrig_push_snapshot(fitrig_plan_t p, const void* data, int dtype
                            cudaMemcpyDeviceToDevice, st));
     else
       CK(copy_rows_h2d(p, dst, (size_t)p->pitch * eb, data, (size_t)rp * ib, (size_t)p->nx * ib,
-                       st));
+                       p->ny, st));
   } else {
     const void* src = data;
     int64_t sp = rp;
     if (!on_device) {
       if (!p->d_staging) CK(dmalloc(p, &p->d_staging, (size_t)p->nx * p->ny * 4));
       CK(copy_rows_h2d(p, p->d_staging, (size_t)p->nx * ib, data, (size_t)rp * ib,
-                       (size_t)p->nx * ib, st));
+                       (size_t)p->nx * ib, p->ny, st));
       src = p->d_staging;
       sp = p->nx;
     }
     CK(launch_convert(src, dtype, sp, dst, p->storage, p->pitch, p->ny, p->nx, st));
   }
-  if (!on_device) CK(cudaStreamSynchronize(st));
+  if (!on_device && sync) CK(cudaStreamSynchronize(st));
   p->pushed += 1;
   p->detected = false;
+  return FITRIG_OK;
+}
+
+static int push_args(fitrig_plan_t p, const void* data, int dtype, int64_t row_pitch_elems,
+                     int64_t* rp) {
+  if (!p || !data) return FITRIG_EINVAL;
+  if (dtype != FITRIG_F32 && dtype != FITRIG_BF16 && dtype != FITRIG_F16) return FITRIG_EINVAL;
+  *rp = row_pitch_elems ? row_pitch_elems : p->nx;
+  if (*rp < p->nx) return FITRIG_EINVAL;
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_push_snapshot(fitrig_plan_t p, const void* data, int dtype, int on_device,
+                                    int64_t row_pitch_elems) {
+  int64_t rp = 0;
+  int rc = push_args(p, data, dtype, row_pitch_elems, &rp);
+  if (rc != FITRIG_OK) return rc;
+  if (p->pushed >= p->L) return FITRIG_ESTATE;
+  CK(cudaSetDevice(p->device));
+  rc = ensure_allocated(p);
+  if (rc != FITRIG_OK) return rc;
+  return push_one(p, data, dtype, on_device, rp, true);
+}
+
+FITRIG_API int fitrig_push_snapshots(fitrig_plan_t p, const void* data, int32_t count, int dtype,
+                                     int on_device, int64_t row_pitch_elems,
+                                     int64_t snap_stride_elems) {
+  int64_t rp = 0;
+  int rc = push_args(p, data, dtype, row_pitch_elems, &rp);
+  if (rc != FITRIG_OK) return rc;
+  if (count < 0) return FITRIG_EINVAL;
+  const int64_t ss = snap_stride_elems ? snap_stride_elems : rp * p->ny;
+  if (ss < rp * p->ny) return FITRIG_EINVAL;
+  // with accumulation every K raw snapshots fill one slot
+  const int64_t k = p->accumulate > 1 ? p->accumulate : 1;
+  if (p->pushed + (p->raw_pushed + (int64_t)count + k - 1) / k > p->L) return FITRIG_ESTATE;
+  if (count == 0) return FITRIG_OK;
+  CK(cudaSetDevice(p->device));
+  rc = ensure_allocated(p);
+  if (rc != FITRIG_OK) return rc;
+  cudaStream_t st = plan_stream(p);
+  const int eb = elem_bytes(p->storage);
+  const bool contiguous = !on_device && k == 1 && dtype == p->storage && rp == p->nx &&
+                          p->pitch == p->nx && ss == rp * p->ny;
+  if (contiguous) {
+    // host rows and device slots line up: one transfer of count * ny rows
+    char* dst = p->d_stack + p->slice_bytes * p->pushed;
+    const size_t row = (size_t)p->nx * eb;
+    CK(copy_rows_h2d(p, dst, row, data, row, row, (int64_t)count * p->ny, st));
+    p->pushed += count;
+    p->detected = false;
+  } else {
+    const size_t ib = (size_t)elem_bytes(dtype);
+    for (int32_t i = 0; i < count; ++i) {
+      rc = push_one(p, static_cast<const char*>(data) + (size_t)ss * ib * i, dtype, on_device,
+                    rp, false);
+      if (rc != FITRIG_OK) return rc;
+    }
+  }
+  if (!on_device) CK(cudaStreamSynchronize(st));
   return FITRIG_OK;
 }
 

@@ -70,6 +70,7 @@ SIGNATURES = {
     "fitrig_plan_create": (c_int, [c_int, c_int, c_int, c_int, c_double, c_int, POINTER(P)]),
     "fitrig_plan_set": (c_int, [P, c_int, c_int64]),
     "fitrig_push_snapshot": (c_int, [P, P, c_int, c_int, c_int64]),
+    "fitrig_push_snapshots": (c_int, [P, P, c_int32, c_int, c_int, c_int64, c_int64]),
     "fitrig_plan_reset": (c_int, [P]),
     "fitrig_detect": (c_int, [P, POINTER(c_int32)]),
     "fitrig_candidates": (c_int, [P, P, c_int32, POINTER(c_int32)]),
@@ -196,6 +197,31 @@ def fitrig_push_snapshot(plan, data, row_pitch_elems: Optional[int] = None) -> N
            "fitrig_push_snapshot")
 
 
+def fitrig_push_snapshots(plan, data) -> None:
+    """Push a (count, ny, nx) block (torch tensor or numpy array, unit column
+    stride) as `count` snapshots in one call."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(data, torch.Tensor):
+        if data.dim() != 3:
+            raise FitrigError(EINVAL, "push_snapshots: need a 3-D block")
+        ptr, code, dev, pitch = _ptr_dtype(data[0] if data.shape[0] else data.new_empty(1, 1))
+        ptr, stride = data.data_ptr(), int(data.stride(0))
+    else:
+        a = np.asarray(data)
+        if a.ndim != 3:
+            raise FitrigError(EINVAL, "push_snapshots: need a 3-D block")
+        ptr, code, dev, pitch = _ptr_dtype(a[0] if a.shape[0] else np.empty((1, 1), a.dtype))
+        ptr, stride = a.ctypes.data, a.strides[0] // a.itemsize
+    count = int(data.shape[0])
+    if count == 0:
+        stride = 0
+    _check(load().fitrig_push_snapshots(plan, c_void_p(ptr), count, code, dev, pitch, stride),
+           "fitrig_push_snapshots")
+
+
 def fitrig_plan_reset(plan) -> None:
     _check(load().fitrig_plan_reset(plan), "fitrig_plan_reset")
 
@@ -212,14 +238,23 @@ def fitrig_detect(plan) -> Tuple[int, int]:
     return rc, n.value
 
 
-def fitrig_candidates(plan, cap: Optional[int] = None) -> np.ndarray:
+def fitrig_candidates(plan, cap: Optional[int] = None,
+                      out: Optional[np.ndarray] = None) -> np.ndarray:
+    """The last detect's candidates.  `out` (a CANDIDATE_DTYPE array, e.g. a
+    view of pinned host memory that is reused across detects) receives them
+    instead of a fresh array; then cap defaults to its length."""
     n = c_int32()
     lib = load()
+    if out is not None:
+        if out.dtype != CANDIDATE_DTYPE or out.ndim != 1 or not out.flags.c_contiguous:
+            raise FitrigError(EINVAL, "fitrig_candidates: out must be a contiguous CANDIDATE_DTYPE vector")
+        cap = len(out) if cap is None else min(cap, len(out))
     if cap is None:
         lib.fitrig_candidates(plan, None, 0, byref(n))
         cap = n.value
-    out = np.zeros(max(cap, 1), dtype=CANDIDATE_DTYPE)
-    rc = lib.fitrig_candidates(plan, c_void_p(out.ctypes.data), cap, byref(n))
+    if out is None:
+        out = np.zeros(max(cap, 1), dtype=CANDIDATE_DTYPE)
+    rc = lib.fitrig_candidates(plan, c_void_p(out.ctypes.data) if cap else None, cap, byref(n))
     _check(rc, "fitrig_candidates", allow=(OK, ETRUNC))
     return out[:min(cap, n.value)]
 

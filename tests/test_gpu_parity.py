@@ -416,6 +416,73 @@ def test_large_host_pushes_land_exactly(storage, host_dtype, pad):
             assert torch.equal(got[:, :nx], want), k
 
 
+@pytest.mark.parametrize("storage,host_dtype,nx,pad,k,dev", [
+    (F.F32, torch.float32, 2048, 0, 1, 0),     # contiguous: one banded transfer
+    (F.F32, torch.float32, 2001, 0, 1, 0),     # padded device rows
+    (F.F32, torch.float32, 2048, 64, 1, 0),    # padded host rows
+    (F.BF16, torch.float32, 2048, 0, 1, 0),    # converted on the device
+    (F.F32, torch.float32, 1000, 0, 2, 0),     # accumulation, K = 2
+    (F.F16, torch.float16, 1000, 8, 1, 1)])    # device block
+def test_block_push_equals_single_pushes(storage, host_dtype, nx, pad, k, dev):
+    """fitrig_push_snapshots stores exactly what one push per snapshot stores
+    and gives the same candidates."""
+    ny, L = 1100, 6
+    x = torch.randn(L * k, ny, nx + pad, dtype=torch.float32).to(host_dtype)
+    x = x.cuda() if dev else x.pin_memory()
+    tdt = {F.F32: torch.float32, F.BF16: torch.bfloat16, F.F16: torch.float16}[storage]
+    out = []
+    for block in (False, True):
+        with F.Plan(nx, ny, L, 5, 4.0, storage=storage, accumulate=k) as p:
+            if block:
+                F.fitrig_push_snapshots(p.h, x[:2 * k + 1, :, :nx])   # ragged: one partial slot
+                F.fitrig_push_snapshots(p.h, x[2 * k + 1:, :, :nx])
+                with pytest.raises(F.FitrigError) as e:
+                    F.fitrig_push_snapshots(p.h, x[:1, :, :nx])
+                assert e.value.status == F.ESTATE
+            else:
+                for r in range(L * k):
+                    F.fitrig_push_snapshot(p.h, x[r, :, :nx])
+            torch.cuda.synchronize()
+            st = torch.stack([device_view(*F.fitrig_stack_device_ptr(p.h, s), ny, tdt)[:, :nx]
+                              for s in range(L)]).clone()
+            rc, c = p.detect()
+            out.append((st, c))
+    assert torch.equal(out[0][0], out[1][0])
+    assert out[0][1].tobytes() == out[1][1].tobytes()
+    if k == 1 and storage == F.F32 and host_dtype == torch.float32:
+        assert torch.equal(out[1][0].cpu(), x[:, :, :nx].cpu())
+
+
+def test_block_push_rejects_bad_arguments():
+    with F.Plan(64, 32, 4, 4, 3.0) as p:
+        x = torch.randn(4, 32, 64, device="cuda")
+        lib = F.load()
+        assert lib.fitrig_push_snapshots(p.h, ctypes.c_void_p(x.data_ptr()), -1, F.F32, 1, 0, 0) == F.EINVAL
+        assert lib.fitrig_push_snapshots(p.h, ctypes.c_void_p(x.data_ptr()), 2, F.F32, 1, 0, 100) == F.EINVAL
+        assert lib.fitrig_push_snapshots(p.h, ctypes.c_void_p(x.data_ptr()), 5, F.F32, 1, 0, 0) == F.ESTATE
+        assert lib.fitrig_push_snapshots(p.h, ctypes.c_void_p(x.data_ptr()), 0, F.F32, 1, 0, 0) == F.OK
+        F.fitrig_push_snapshots(p.h, x)
+        rc, _ = p.detect()
+        assert rc in (F.OK,)
+
+
+def test_candidates_into_a_caller_buffer():
+    """A reused (pinned) output buffer gets the same candidates; a short one
+    the first of them."""
+    stack, _ = synth.make_stack(synth.small_spec(8, 96, 128), seed=5, device="cuda")
+    with F.Plan(128, 96, 8, 5, 2.0, branch=F.BRANCH_BOTH) as p:
+        p.push_stack(stack)
+        rc, want = p.detect()
+        assert len(want) > 2
+        raw = torch.empty((len(want) + 3) * F.CANDIDATE_DTYPE.itemsize, dtype=torch.uint8,
+                          pin_memory=True)
+        buf = raw.numpy().view(F.CANDIDATE_DTYPE)
+        got = F.fitrig_candidates(p.h, out=buf)
+        assert got.tobytes() == want.tobytes()
+        assert got.ctypes.data == buf.ctypes.data
+        assert F.fitrig_candidates(p.h, out=buf[:2]).tobytes() == want[:2].tobytes()
+
+
 def test_selection_lists_grow_automatically():
     """A detect that selects more tiles than the starting capacity grows the
     lists and gives the same result as a plan sized for every tile."""

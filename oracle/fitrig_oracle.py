@@ -18,7 +18,9 @@ Paper sections used (arXiv 2509.21754, "FITrig"):
   {t | z_t > tau}.
 * Sec. 2.4.2 (image-frequency detection): the tLISI cube, Eq. (eta) with h =
   maximum spectral magnitude (the paper's own conservative choice in Sec. 3.4.3),
-  the z-score of eta and the selected set.
+  the z-score of eta and the selected set.  h may instead be an incoherent
+  harmonic sum (Sec. 2.4.2 names harmonic summing as a choice of h and Sec. 3.3
+  applies it to the real data, without defining it; see ``harmonic_sum``).
 
 Readings where the paper is silent or ambiguous (each is an option here):
 
@@ -39,6 +41,12 @@ Readings where the paper is silent or ambiguous (each is an option here):
   through the eta values of the neighbouring tiles.
 * the transform is the unnormalised DFT of exact length n = L - 2, bins
   k = 1..floor(n/2).
+* harmonic summing (parity with the paper unpinned: the paper gives no
+  formula): the classic incoherent sum of the magnitudes at the first m
+  harmonics of a fundamental bin k, scaled by 1/sqrt(m), maximised over
+  m = 1, 2, 4, .., m_max and over the k with m k <= floor(n/2); m_max = 1 is
+  the maximum magnitude.  The bin reported is the fundamental k.  Ties go to
+  the smaller m, then the smaller k.
 * a sliding-window mode (not in the paper, whose tiles partition the image)
   evaluates the tile statistic over the odd w x w window centred on each pixel,
   clipped at the border, and then treats pixels as 1 x 1 tiles.
@@ -388,8 +396,37 @@ def dft_magnitudes(series: np.ndarray) -> np.ndarray:
     return np.abs(X)
 
 
-def spectrum(cube: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
-    """eta_t = max_k |X_k| and its bin (smallest k on ties) per tile.
+def harmonic_sum(mags: np.ndarray, m_max: int) -> Tuple[np.ndarray, np.ndarray]:
+    """h of Eq. (eta) as an incoherent harmonic sum.
+
+    ``mags`` has shape (tiles, K) and holds |X_k| for k = 1..K.  For every
+    m = 1, 2, 4, .., m_max and every fundamental k with m k <= K,
+    S_m(k) = (|X_k| + |X_2k| + .. + |X_mk|) / sqrt(m); the result is the
+    largest S_m(k) per tile and its fundamental k (ties: smaller m, then
+    smaller k).  With m_max = 1 it is max_k |X_k| (the maximum magnitude).
+    """
+    a = np.asarray(mags, dtype=np.float64)
+    ntile, K = a.shape
+    best = np.full(ntile, -np.inf)
+    kbin = np.ones(ntile, dtype=np.int64)
+    m = 1
+    while m <= m_max:
+        for k in range(1, K // m + 1):
+            total = np.zeros(ntile)
+            for j in range(1, m + 1):
+                total = total + a[:, j * k - 1]
+            S = total / np.sqrt(m)
+            better = S > best
+            best = np.where(better, S, best)
+            kbin = np.where(better, k, kbin)
+        m *= 2
+    return best, kbin
+
+
+def spectrum(cube: np.ndarray, harmonics: int = 1) -> Tuple[np.ndarray, np.ndarray]:
+    """eta_t = h(|X_k|) and its bin per tile: h = max_k |X_k| (smallest k on
+    ties) when ``harmonics`` is 1, else ``harmonic_sum`` with m_max =
+    ``harmonics``.
 
     ``cube`` is the tLISI cube with shape (L-2, Ty, Tx); tiles with a
     non-finite entry get eta = NaN and bin = -1.
@@ -398,8 +435,11 @@ def spectrum(cube: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
     series = np.moveaxis(cube, 0, -1).reshape(Ty * Tx, U)
     ok = np.all(np.isfinite(series), axis=1)
     mags = dft_magnitudes(np.where(ok[:, None], series, 0.0))
-    eta = mags.max(axis=1)
-    kbin = mags.argmax(axis=1) + 1
+    if harmonics == 1:
+        eta = mags.max(axis=1)
+        kbin = mags.argmax(axis=1) + 1
+    else:
+        eta, kbin = harmonic_sum(mags, harmonics)
     eta = np.where(ok, eta, np.nan).reshape(Ty, Tx)
     kbin = np.where(ok, kbin, -1).reshape(Ty, Tx)
     return eta, kbin
@@ -497,7 +537,7 @@ def freq_candidates(eta: np.ndarray, kbin: np.ndarray, z: np.ndarray, tau: float
 def detect(stack: np.ndarray, w: int, tau: float, branch: int = BRANCH_IMAGE,
            noise: str = "meanstd", rmode: str = "abs", edge: str = "partial",
            forced_image=None, forced_freq=None, stride: str = "tile",
-           mmode: str = "global") -> Detection:
+           mmode: str = "global", harmonics: int = 1) -> Detection:
     """Run the trigger on a (L, ny, nx) stack and return the sorted candidates.
 
     stride "tile" is the paper's tiling; "sliding" evaluates the same statistic
@@ -506,7 +546,8 @@ def detect(stack: np.ndarray, w: int, tau: float, branch: int = BRANCH_IMAGE,
     mmode "global" normalises every unit by the one M of the whole stack;
     "running" normalises unit s by M_s over snapshots 0..s+2 (real time).
     ``Detection.M`` is the global M in both modes, ``Detection.M_units`` the
-    normaliser of each unit.
+    normaliser of each unit.  ``harmonics`` is m_max of the frequency branch's
+    h (1: maximum magnitude).
     """
     x = np.asarray(stack)
     L, ny, nx = x.shape
@@ -535,7 +576,7 @@ def detect(stack: np.ndarray, w: int, tau: float, branch: int = BRANCH_IMAGE,
         det.scale = np.array(ss)
         cands += image_candidates(units, det.z, tau, forced_image)
     if branch & BRANCH_FREQ:
-        eta, kbin = spectrum(tl)
+        eta, kbin = spectrum(tl, harmonics)
         ez, ec, es = zscore_map(eta, noise)
         det.eta, det.eta_bin, det.eta_z = eta, kbin, ez
         det.eta_centre, det.eta_scale = ec, es
@@ -546,7 +587,7 @@ def detect(stack: np.ndarray, w: int, tau: float, branch: int = BRANCH_IMAGE,
 
 
 def freq_window(stack: np.ndarray, w: int, tau: float, n: int, noise: str = "meanstd",
-                forced: Optional[Dict[Tuple[int, int], bool]] = None):
+                forced: Optional[Dict[Tuple[int, int], bool]] = None, harmonics: int = 1):
     """Real-time image-frequency branch: the Sec. 2.4.2 statistic over the last
     ``n`` units of the stack only (units L-2-n .. L-3), each normalised by its
     running M_s (the real-time reading of Sec. 2.2.4).  Returns (candidates,
@@ -563,7 +604,7 @@ def freq_window(stack: np.ndarray, w: int, tau: float, n: int, noise: str = "mea
     Ms = normaliser_M_running(region)
     first = L - 2 - n
     tl = np.stack([tlisi_from_tiles(unit_tiles(x, s, w), Ms[s]) for s in range(first, L - 2)])
-    eta, kbin = spectrum(tl)
+    eta, kbin = spectrum(tl, harmonics)
     z, _, _ = zscore_map(eta, noise)
     cands = freq_candidates(eta, kbin, z, tau, w, nyu, nxu, forced)
     for c in cands:

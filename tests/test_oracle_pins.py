@@ -551,3 +551,91 @@ def test_freq_window_recovers_period_of_recent_pulses():
     cands, eta, kbin, z = O.freq_window(x, w, 4.0, 16, "meanstd")
     assert kbin[10 // w, 14 // w] % 4 == 0
     assert any((c.y // w, c.x // w) == (10 // w, 14 // w) for c in cands)
+
+
+# ---------------------------------------------------------------- harmonic summing
+def _one_tile_cube(series):
+    return np.asarray(series, dtype=np.float64)[:, None, None]
+
+
+@pytest.mark.parametrize("amps,k0,m_max,want_eta,want_k", [
+    # y_s = sum_j a_j cos(2 pi j k0 s / n), n = 64: |X_(j k0)| = n a_j / 2 exactly
+    # (want_k None: equal sums at several bins, which rounding orders)
+    ([1, 1, 1, 1], 2, 1, 32.0, None),
+    ([1, 1, 1, 1], 2, 2, 64.0 / math.sqrt(2), None),
+    ([1, 1, 1, 1], 2, 4, 64.0, 2),
+    ([1, 1, 1, 1], 2, 16, 64.0, 2),
+    ([1.0, 0.5, 0.25, 0.0], 3, 4, 48.0 / math.sqrt(2), 3),   # S_2 = 48/sqrt 2 beats S_1, S_4
+    ([1.0, 0.3, 0.1, 0.0], 3, 4, 32.0, 3),                   # S_1 = 32 beats S_2, S_4
+    ([0.2, 1.0, 1.0, 1.0], 2, 4, (6.4 + 96.0) / 2, 2),       # the weak fundamental counts
+])
+def test_harmonic_sum_of_cosines_closed_form(amps, k0, m_max, want_eta, want_k):
+    n = 64
+    s = np.arange(n)
+    y = sum(a * np.cos(2 * np.pi * (j + 1) * k0 * s / n) for j, a in enumerate(amps))
+    eta, kbin = O.spectrum(_one_tile_cube(y), harmonics=m_max)
+    assert eta[0, 0] == pytest.approx(want_eta, rel=1e-12, abs=1e-9)
+    if want_k is not None:
+        assert kbin[0, 0] == want_k
+
+
+@pytest.mark.parametrize("m_max,want_eta,want_k", [(1, 8.0, 8), (2, 16 / math.sqrt(2), 8),
+                                                   (4, 16.0, 8), (8, 16.0, 8)])
+def test_harmonic_sum_of_pulse_comb_includes_nyquist(m_max, want_eta, want_k):
+    """A comb of period 8 over n = 64 has |X_k| = 8 at k = 8, 16, 24, 32 (32 =
+    Nyquist) and 0 elsewhere; four harmonics of k = 8 give 4 * 8 / 2 = 16."""
+    n = 64
+    y = (np.arange(n) % 8 == 0).astype(np.float64)
+    eta, kbin = O.spectrum(_one_tile_cube(y), harmonics=m_max)
+    assert eta[0, 0] == pytest.approx(want_eta, rel=1e-12)
+    assert kbin[0, 0] == want_k
+
+
+def test_harmonic_sum_with_one_harmonic_is_the_maximum_magnitude():
+    rng = np.random.default_rng(4)
+    cube = rng.standard_normal((37, 5, 6))
+    e1, k1 = O.spectrum(cube, harmonics=1)
+    mags = O.dft_magnitudes(np.moveaxis(cube, 0, -1).reshape(30, 37))
+    e, k = O.harmonic_sum(mags, 1)
+    assert np.array_equal(e.reshape(5, 6), e1) and np.array_equal(k.reshape(5, 6), k1)
+
+
+def test_harmonic_sum_grows_with_m_max_and_is_bounded():
+    """More harmonics only add candidates to the maximum, and each S_m(k) is at
+    most sqrt(m) times the largest magnitude."""
+    rng = np.random.default_rng(9)
+    cube = rng.standard_normal((126, 4, 4))
+    mags = O.dft_magnitudes(np.moveaxis(cube, 0, -1).reshape(16, 126))
+    prev = None
+    for m_max in (1, 2, 4, 8, 16, 32):
+        e, _ = O.spectrum(cube, harmonics=m_max)
+        if prev is not None:
+            assert np.all(e >= prev)
+        assert np.all(e.ravel() <= math.sqrt(m_max) * mags.max(axis=1) * (1 + 1e-12))
+        prev = e
+
+
+def test_harmonic_sum_brute_force_on_tiny_spectra():
+    """Every (m, k) written out for K = 6 against a hand enumeration."""
+    mags = np.array([[3.0, 1.0, 2.0, 4.0, 0.5, 2.5]])
+    cands = {(1, k): mags[0, k - 1] for k in range(1, 7)}
+    cands.update({(2, 1): (3 + 1) / math.sqrt(2), (2, 2): (1 + 4) / math.sqrt(2),
+                  (2, 3): (2 + 2.5) / math.sqrt(2)})
+    cands.update({(4, 1): (3 + 1 + 2 + 4) / 2.0})
+    best = max(cands.items(), key=lambda kv: (kv[1], -kv[0][0], -kv[0][1]))
+    e, k = O.harmonic_sum(mags, 8)
+    assert e[0] == pytest.approx(best[1], rel=1e-15) and k[0] == best[0][1] == 1
+    e, k = O.harmonic_sum(mags, 2)
+    assert e[0] == pytest.approx(4.0) and k[0] == 4
+
+
+def test_harmonic_summing_finds_a_pulse_train_missed_by_the_maximum():
+    """A narrow periodic pulse spreads its power over many harmonics, so the
+    harmonic sum raises the pulsar tile's eta more than a noise tile's."""
+    rng = np.random.default_rng(11)
+    n, P = 128, 16
+    cube = rng.standard_normal((n, 8, 8))
+    cube[np.arange(n) % P == 3, 2, 5] += 2.0
+    z1 = O.zscore_map(O.spectrum(cube, 1)[0])[0][2, 5]
+    z8 = O.zscore_map(O.spectrum(cube, 8)[0])[0][2, 5]
+    assert z8 > z1 + 1.0

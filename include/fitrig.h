@@ -98,8 +98,17 @@ enum {
   FITRIG_OPT_AUTOTUNE = 10,  /* 1: use the autotuned stack-march shape (tunes once)    */
   FITRIG_OPT_MAX_SELECTED = 11, /* selected-tile capacity of one detect; 0 = default   */
   FITRIG_OPT_GRAPH = 12,      /* 1 (default): replay repeated detects from a graph     */
-  FITRIG_OPT_ACCUMULATE = 13  /* K >= 1: each K pushed snapshots are summed into one   */
+  FITRIG_OPT_ACCUMULATE = 13, /* K >= 1: each K pushed snapshots are summed into one   */
+  FITRIG_OPT_HARMONICS = 14   /* m_max of the frequency branch's harmonic sum (1..32)  */
 };
+/* HARMONICS (Sec. 2.4.2 names harmonic summing as a choice of the spectral
+ * function h; Sec. 3.3 applies it to the real data; the paper gives no
+ * formula): with m_max > 1 (a power of two <= 32) eta_t is the largest
+ * incoherent harmonic sum (|X_k| + |X_2k| + .. + |X_mk|) / sqrt(m) over
+ * m = 1, 2, 4, .., m_max and the fundamentals k with m k <= floor(n/2), and
+ * the reported bin is that k (ties: smaller m, then smaller k).  1 (the
+ * default) is the maximum magnitude of Sec. 3.4.3.  Settable at any time;
+ * EINVAL for other values. */
 /* ACCUMULATE (Sec. 4.3.2, Fig. "Snapshots accumulation"): with sampling
  * periods so short that adjacent snapshots are nearly identical, the trigger
  * runs on sums of adjacent snapshots.  With K > 1 every fitrig_push_snapshot
@@ -156,14 +165,15 @@ enum { FITRIG_KERNEL_STACK = 0, FITRIG_KERNEL_NOISE = 1, FITRIG_KERNEL_SELECT = 
  * Validates: window in [1, min(nx, ny)], nsnap >= 3 (>= 4 with the frequency
  * branch, whose series has nsnap-2 >= 2 points), nsigma > 0.  Device memory
  * is allocated at the first push.  EINVAL on bad arguments, EUNSUPPORTED for a
- * window above 128.
+ * window above 128 or a frequency-branch series (nsnap - 2) above 4096 points.
  */
 FITRIG_API int fitrig_plan_create(int nx, int ny, int nsnap, int window, double nsigma,
                                   int branch, fitrig_plan_t* out);
 
 /* fitrig_plan_set -- set an option (see the enum).  STORAGE, NOISE, RMODE,
  * EDGE, STRIDE and AUTOTUNE are accepted only before the first push (ESTATE
- * after); STREAM, TIMEOUT_NS and MAX_SELECTED at any time.  EINVAL for an unknown option or value. */
+ * after); STREAM, TIMEOUT_NS, MAX_SELECTED, GRAPH and HARMONICS at any time.
+ * EINVAL for an unknown option or value. */
 FITRIG_API int fitrig_plan_set(fitrig_plan_t plan, int option, int64_t value);
 
 /*

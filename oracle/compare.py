@@ -52,8 +52,13 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
             noise: str = "meanstd", rmode: str = "abs", edge: str = "partial",
             decide_image: Optional[Callable[[int, int, int], bool]] = None,
             decide_freq: Optional[Callable[[int, int], bool]] = None,
-            det: Optional[O.Detection] = None, pixel_sample: Optional[int] = None) -> List[str]:
+            det: Optional[O.Detection] = None, pixel_sample: Optional[int] = None,
+            harmonics: int = 1) -> List[str]:
     """Return a list of parity violations (empty when the lists agree).
+
+    ``harmonics`` is m_max of the frequency branch's h (1: maximum magnitude);
+    a frequency candidate's bin must then be a fundamental whose best harmonic
+    sum is within the tolerance of the tile's largest.
 
     ``pixel_sample`` limits the arg-max pixel check (which reads the stack) to
     that many randomly chosen image candidates; everything else is checked for
@@ -63,7 +68,7 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
     L, ny, nx = stack.shape
     Ty, Tx, nyu, nxu = O.tiling(ny, nx, w, edge)
     if det is None:
-        det = O.detect(stack, w, tau, branch, noise, rmode, edge)
+        det = O.detect(stack, w, tau, branch, noise, rmode, edge, harmonics=harmonics)
     band = REL_TOL * tau
     names = cands.dtype.names
     got = [dict(zip(names, c)) for c in cands]
@@ -146,13 +151,27 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
                 errs.append(f"freq: candidate {(gc['y'], gc['x'])} is not the centre of {(ty, tx)}")
             mags = O.dft_magnitudes(series[:, ty, tx])
             k = int(gc["freq_bin"])
-            if not (1 <= k <= mags.size) or mags[k - 1] < mags.max() * (1 - REL_TOL):
+            if not bin_is_a_maximum(mags, k, harmonics):
                 errs.append(f"freq: bin {k} is not a maximum of tile {(ty, tx)}")
             oc = ref.get((ty, tx))
             if oc is not None:
                 if abs(gc["xf"] - oc.xf) > XF_TOL_TILES * w or abs(gc["yf"] - oc.yf) > XF_TOL_TILES * w:
                     errs.append(f"freq: refined {(gc['yf'], gc['xf'])} vs oracle {(oc.yf, oc.xf)}")
     return errs
+
+
+def bin_is_a_maximum(mags: np.ndarray, k: int, harmonics: int = 1) -> bool:
+    """Whether fundamental k attains, within REL_TOL, the largest value of h
+    over the magnitudes |X_1..X_K| (largest over m of the harmonic sums at k)."""
+    K = mags.size
+    if not 1 <= k <= K:
+        return False
+    top = O.harmonic_sum(mags[None, :], harmonics)[0][0]
+    val, m = -np.inf, 1
+    while m <= harmonics and m * k <= K:
+        val = max(val, sum(mags[j * k - 1] for j in range(1, m + 1)) / np.sqrt(m))
+        m *= 2
+    return bool(val >= top * (1 - REL_TOL))
 
 
 def values_close(gpu: np.ndarray, ref: np.ndarray, rel: float = 1e-5,

@@ -314,8 +314,9 @@ cudaError_t launch_export_candidates(const fitrig_candidate* src, const int* n,
 
 // Frequency branch.
 cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
-                            const float2* twiddle, const float* wts, float* eta, int* bin,
-                            cudaStream_t st);
+                            const float2* twiddle, const float* wts, int hmax, float* eta,
+                            int* bin, cudaStream_t st);
+int spectrum_max_n();   // longest series launch_spectrum takes
 
 // Ingest conversion (fp32 <-> bf16/fp16).
 cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,

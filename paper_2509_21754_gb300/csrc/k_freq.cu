@@ -2,7 +2,13 @@
 // statistic over the n = L - 2 units, its mean removed (the DC term of Eq.
 // eta), an unnormalised DFT of exact length n, and
 //   eta_t = max_{k=1..floor(n/2)} |X_k|   (h = maximum spectral magnitude)
-// with the arg-max bin (smallest k on ties).
+// with the arg-max bin (smallest k on ties), or, with hmax > 1, h = the
+// incoherent harmonic sum
+//   eta_t = max_{m = 1, 2, 4, .., hmax} max_{k: m k <= floor(n/2)}
+//           (|X_k| + |X_2k| + .. + |X_mk|) / sqrt(m)
+// with the fundamental k (ties: smaller m, then smaller k).  Sec. 2.4.2 names
+// harmonic summing as a choice of h without a formula; this is the classic
+// incoherent form.
 //
 // The series used is v_t(s) = mean(Delta) max(Delta) mean(r), i.e. the tLISI
 // complement times M^2 with one M for the stack, so |X_k| of tLISI is |X_k|/M^2
@@ -21,6 +27,27 @@
 namespace fitrig {
 
 constexpr int kDftThreads = 128;
+
+// The harmonic sum over one tile's magnitudes |X_k| = mag[(k - 1) * stride],
+// k = 1..K, in the order (m ascending, k ascending) so that ties keep the
+// smaller m, then the smaller k.
+__device__ __forceinline__ void harmonic_best(const float* mag, int stride, int K, int hmax,
+                                              float& best, int& bk) {
+  best = -1.f;
+  bk = 1;
+  for (int m = 1; m <= hmax && m <= K; m <<= 1) {
+    const float inv = 1.f / sqrtf((float)m);
+    for (int k = 1; k * m <= K; ++k) {
+      float acc = 0.f;
+      for (int j = 1; j <= m; ++j) acc += mag[(j * k - 1) * stride];
+      acc *= inv;
+      if (acc > best) {
+        best = acc;
+        bk = k;
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kDftThreads) k_dft(const float* __restrict__ vp, int n,
                                                      int64_t T, int64_t vs,
@@ -89,7 +116,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restri
                                                            int64_t T, int64_t vs,
                                                            const float2* __restrict__ tw,
                                                            const float* __restrict__ wts,
-                                                           float* eta, int* bin) {
+                                                           int hmax, float* eta, int* bin) {
   extern __shared__ float2 tws[];   // [H][K] twiddles, pair-major, then [n][threads] series
   const int H = (n - 1) / 2, K = n / 2;
   float* ys = reinterpret_cast<float*>(tws + H * K);
@@ -143,6 +170,16 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restri
   }
   float best = -1.f;
   int bk = 1;
+  if (hmax > 1) {
+    // the series is spent: its column holds the magnitudes for the harmonic sum
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+      if (k < K) my[k * kDftThreads] = sqrtf(re[k] * re[k] + im[k] * im[k]);
+    harmonic_best(my, kDftThreads, K, hmax, best, bk);
+    eta[t] = best;
+    bin[t] = bk;
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < KMAX; ++k) {
     if (k < K) {
@@ -171,7 +208,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_even(const float* __restric
                                                           int64_t T, int64_t vs,
                                                           const float2* __restrict__ tw,
                                                           const float* __restrict__ wts,
-                                                          float* eta, int* bin) {
+                                                          int hmax, float* eta, int* bin) {
   extern __shared__ float2 sm2[];
   const int m = n / 2, Hm = (m - 1) / 2, K = m / 2, H = (n - 1) / 2;
   float2* th = sm2;                                 // [Hm][K]: 2 pi j k / m, j,k >= 1
@@ -256,11 +293,14 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_even(const float* __restric
   // X_k = E_k + W^k O_k, W^k = (c, -s):  Re = Er + c Or + s Oi,  Im = Ei + c Oi - s Or
   float best = -1.f;
   int bk = 1;
+  // with harmonic summing the spent series column collects |X_k| at row k - 1
+  const bool harm = hmax > 1;
   auto take = [&](int k, float Er, float Ei, float Or, float Oi) {
     const float2 w = tk[k];
     const float re = Er + w.x * Or + w.y * Oi;
     const float im = Ei + w.x * Oi - w.y * Or;
     const float m2 = re * re + im * im;
+    if (harm) my[(k - 1) * kDftThreads] = sqrtf(m2);
     if (m2 > best || (m2 == best && k < bk)) {
       best = m2;
       bk = k;
@@ -276,36 +316,217 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_even(const float* __restric
   {
     const float x = E0 - O0;   // bin m
     const float m2 = x * x;
+    if (harm) my[(m - 1) * kDftThreads] = fabsf(x);
     if (m2 > best || (m2 == best && m < bk)) {
       best = m2;
       bk = m;
     }
   }
+  if (harm) {
+    harmonic_best(my, kDftThreads, m, hmax, best, bk);
+    eta[t] = best;
+    bin[t] = bk;
+    return;
+  }
   eta[t] = sqrtf(best);
   bin[t] = bk;
 }
 
+// Long series (n up to kLongMaxN) and harmonic sums beyond the short kernels:
+// one warp per tile, a CTA stages the series of kLongWarps consecutive tiles
+// (each cube row a 32-byte segment) and transposes them into shared memory.
+// Lane l forms bins k = l + 1 + 32 j, kLongB at a time, over the folded pairs
+// (e_q, o_q) read as broadcasts; the phasor (cos, sin)(2 pi k q / n) advances by
+// one complex multiply per step and is re-seeded from the host's FP64 table
+// every kSeed steps, so its rounding error stays that of a few dozen
+// multiplies.  The magnitudes go to shared memory for the maximum or the
+// harmonic sum, which the warp then reduces.
+constexpr int kLongWarps = 8;
+constexpr int kLongMaxN = 4096;
+constexpr int kLongB = 4;
+constexpr int kSeed = 32;
+
+__host__ __device__ constexpr int long_ldy(int n) { return (n + 27) / 32 * 32 + 4; }
+
+__global__ void __launch_bounds__(kLongWarps * 32) k_dft_long(const float* __restrict__ vp, int n,
+                                                              int64_t T, int64_t vs,
+                                                              const float2* __restrict__ tw,
+                                                              const float* __restrict__ wts,
+                                                              int hmax, float* eta, int* bin) {
+  extern __shared__ float lsm[];
+  const int K = n / 2, H = (n - 1) / 2, ldy = long_ldy(n);
+  float* ys = lsm;                                 // [kLongWarps][ldy]
+  float* mg = lsm + kLongWarps * ldy;              // [kLongWarps][K + 1]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t0 = (int64_t)blockIdx.x * kLongWarps;
+  for (int i = threadIdx.x; i < n * kLongWarps; i += blockDim.x) {
+    const int q = i / kLongWarps, c = i - q * kLongWarps;
+    const int64_t t = t0 + c;
+    float v = t < T ? vp[(size_t)q * vs + t] : 0.f;
+    if (wts) v *= wts[q];
+    ys[c * ldy + q] = v;
+  }
+  __syncthreads();
+  const int64_t t = t0 + warp;
+  if (t >= T) return;
+  float* y = ys + warp * ldy;
+  float sum = 0.f;
+  bool ok = true;
+  for (int q = lane; q < n; q += 32) {
+    const float v = y[q];
+    ok = ok && isfinite(v);
+    sum += v;
+  }
+  ok = __all_sync(0xffffffffu, ok);
+#pragma unroll
+  for (int off = 16; off; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  if (!ok) {
+    if (lane == 0) {
+      eta[t] = NAN;
+      bin[t] = -1;
+    }
+    return;
+  }
+  const float mean = sum / (float)n;
+  __syncwarp();
+  for (int q = 1 + lane; q <= H; q += 32) {
+    const float a = y[q] - mean, b = y[n - q] - mean;
+    y[q] = a + b;       // e_q
+    y[n - q] = a - b;   // o_q
+  }
+  __syncwarp();
+  const bool even = (n & 1) == 0;
+  const float y0 = y[0] - mean;
+  const float ymid = even ? y[n / 2] - mean : 0.f;
+  // (cos, sin) of 2 pi a / n, 0 <= a < n, from the table's first row and symmetry
+  auto ang = [&](int a) -> float2 {
+    if (a == 0) return make_float2(1.f, 0.f);
+    if (2 * a == n) return make_float2(-1.f, 0.f);
+    if (a <= H) return tw[a - 1];
+    const float2 c = tw[n - a - 1];
+    return make_float2(c.x, -c.y);
+  };
+  float* mk = mg + warp * (K + 1);   // |X_k|^2 at mk[k]
+  for (int kb = 1; kb <= K; kb += 32 * kLongB) {
+    int kk[kLongB];
+    float re[kLongB], im[kLongB], c[kLongB], sn[kLongB], wc[kLongB], ws[kLongB];
+#pragma unroll
+    for (int b = 0; b < kLongB; ++b) {
+      kk[b] = min(kb + lane + 32 * b, K);
+      re[b] = y0 + ((even && (kk[b] & 1)) ? -ymid : ymid);
+      im[b] = 0.f;
+      const float2 w = ang(kk[b]);
+      wc[b] = w.x;
+      ws[b] = w.y;
+    }
+    for (int q0 = 1; q0 <= H; q0 += kSeed) {
+#pragma unroll
+      for (int b = 0; b < kLongB; ++b) {
+        const float2 e = ang((int)(((int64_t)kk[b] * q0) % n));
+        c[b] = e.x;
+        sn[b] = e.y;
+      }
+      const int qe = min(H, q0 + kSeed - 1);
+      for (int q = q0; q <= qe; ++q) {
+        const float e = y[q], o = y[n - q];
+#pragma unroll
+        for (int b = 0; b < kLongB; ++b) {
+          re[b] = fmaf(e, c[b], re[b]);
+          im[b] = fmaf(o, sn[b], im[b]);
+          const float cn = fmaf(c[b], wc[b], -sn[b] * ws[b]);
+          sn[b] = fmaf(sn[b], wc[b], c[b] * ws[b]);
+          c[b] = cn;
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kLongB; ++b)
+      if (kb + lane + 32 * b <= K) mk[kk[b]] = re[b] * re[b] + im[b] * im[b];
+  }
+  __syncwarp();
+  float best = -1.f;
+  int bk = 1, bm = 1;
+  if (hmax <= 1) {
+    for (int k = 1 + lane; k <= K; k += 32) {
+      const float v = mk[k];
+      if (v > best) {
+        best = v;
+        bk = k;
+      }
+    }
+  } else {
+    for (int m = 1; m <= hmax && m <= K; m <<= 1) {
+      const float inv = 1.f / sqrtf((float)m);
+      for (int k = 1 + lane; k * m <= K; k += 32) {
+        float acc = 0.f;
+        for (int j = 1; j <= m; ++j) acc += sqrtf(mk[j * k]);
+        acc *= inv;
+        if (acc > best) {
+          best = acc;
+          bk = k;
+          bm = m;
+        }
+      }
+    }
+  }
+  // warp arg-max: larger value, then smaller m, then smaller k
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, best, off);
+    const int okk = __shfl_xor_sync(0xffffffffu, bk, off);
+    const int om = __shfl_xor_sync(0xffffffffu, bm, off);
+    if (ov > best || (ov == best && (om < bm || (om == bm && okk < bk)))) {
+      best = ov;
+      bk = okk;
+      bm = om;
+    }
+  }
+  if (lane == 0) {
+    eta[t] = hmax <= 1 ? sqrtf(best) : best;
+    bin[t] = bk;
+  }
+}
+
+int spectrum_max_n() { return kLongMaxN; }
+
 cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
-                            const float2* twiddle, const float* wts, float* eta, int* bin,
-                            cudaStream_t st) {
+                            const float2* twiddle, const float* wts, int hmax, float* eta,
+                            int* bin, cudaStream_t st) {
   const int64_t blocks = (T + kDftThreads - 1) / kDftThreads;
   const int H = (n - 1) / 2, K = n / 2;
+  if (n < 2 || n > kLongMaxN || hmax < 1) return cudaErrorInvalidValue;
   if ((n & 1) == 0 && n <= 66) {
     const int m = n / 2, Hm = (m - 1) / 2, Kh = m / 2;
     const size_t sm = (size_t)(Hm > 0 ? Hm * Kh : 0) * sizeof(float2) + (size_t)m * sizeof(float2) +
                       (size_t)n * kDftThreads * sizeof(float);
-    k_dft_even<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts, eta, bin);
+    k_dft_even<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts, hmax,
+                                                              eta, bin);
     count_launches(1);
     return cudaGetLastError();
   }
   if (n <= 65 && H >= 1) {
     const size_t sm = (size_t)H * K * sizeof(float2) + (size_t)n * kDftThreads * sizeof(float);
     if (K <= 16)
-      k_dft_short<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts, eta,
-                                                                 bin);
+      k_dft_short<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts,
+                                                                 hmax, eta, bin);
     else
-      k_dft_short<32><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts, eta,
-                                                                 bin);
+      k_dft_short<32><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts,
+                                                                 hmax, eta, bin);
+    count_launches(1);
+    return cudaGetLastError();
+  }
+  if (n > 256 || hmax > 1) {
+    const size_t sm = (size_t)kLongWarps * (long_ldy(n) + K + 1) * sizeof(float);
+    static size_t long_configured = 0;
+    if (sm > 48 * 1024 && sm > long_configured) {
+      cudaError_t e = cudaFuncSetAttribute(k_dft_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sm);
+      if (e != cudaSuccess) return e;
+      long_configured = sm;
+    }
+    const int64_t lblocks = (T + kLongWarps - 1) / kLongWarps;
+    k_dft_long<<<(unsigned)lblocks, kLongWarps * 32, sm, st>>>(vp, n, T, vs, twiddle, wts, hmax,
+                                                               eta, bin);
     count_launches(1);
     return cudaGetLastError();
   }

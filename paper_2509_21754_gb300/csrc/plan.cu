@@ -71,6 +71,7 @@ struct fitrig_plan_s {
   float* d_hwts = nullptr;   // [hist_n]
   float2* d_htw = nullptr;   // twiddles of length hist_n
   int accumulate = 1;        // raw snapshots summed into one stack snapshot
+  int hmax = 1;              // harmonics of the frequency branch's h (1: max magnitude)
   int raw_pushed = 0;        // raw snapshots of the block being summed
   float* d_accum = nullptr;  // [ny][nx] FP32 running sum (accumulate > 1)
   int64_t max_selected = 0;  // 0: automatic selection capacity
@@ -372,8 +373,11 @@ static int alloc_select(fitrig_plan_t p) {
 
 // Twiddle table of the length-n transform: (cos, sin)(2 pi ((k q) mod n) / n)
 // for k = 1..n/2, q = 1..(n-1)/2, computed in FP64 on the host.
+// (cos, sin)(2 pi (k q mod n) / n) in FP64, rounded once: [K][H] for the
+// direct kernel of series up to 256 points; longer series take only the first
+// row (k = 1), which is all the warp-per-tile kernel reads.
 static int make_twiddles(fitrig_plan_t p, int n, float2** out) {
-  const int H = (n - 1) / 2, K = n / 2;
+  const int H = (n - 1) / 2, K = n > 256 ? 1 : n / 2;
   std::vector<float2> tw((size_t)std::max(1, K * H));
   for (int k = 1; k <= K; ++k)
     for (int q = 1; q <= H; ++q) {
@@ -509,7 +513,7 @@ FITRIG_API int fitrig_plan_create(int nx, int ny, int nsnap, int window, double 
   if (nsnap < 3 || ((branch & FITRIG_BRANCH_FREQ) && nsnap < 4)) return FITRIG_EINVAL;
   if (!(nsigma > 0.0) || !std::isfinite(nsigma)) return FITRIG_EINVAL;
   if (window > 128) return FITRIG_EUNSUPPORTED;
-  if ((branch & FITRIG_BRANCH_FREQ) && nsnap - 2 > 256) return FITRIG_EUNSUPPORTED;
+  if ((branch & FITRIG_BRANCH_FREQ) && nsnap - 2 > spectrum_max_n()) return FITRIG_EUNSUPPORTED;
   fitrig_plan_t p = new (std::nothrow) fitrig_plan_s();
   if (!p) return FITRIG_ENOMEM;
   p->nx = nx;
@@ -559,6 +563,11 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t p, int option, int64_t value) {
       if (value <= 0) return FITRIG_EINVAL;
       p->timeout_ns = (uint64_t)value;
       drop_graph(p);   // the captured kernels carry the old bound
+      return FITRIG_OK;
+    case FITRIG_OPT_HARMONICS:
+      if (value < 1 || value > 32 || (value & (value - 1))) return FITRIG_EINVAL;
+      if (p->hmax != (int)value) drop_graph(p);
+      p->hmax = (int)value;
       return FITRIG_OK;
     case FITRIG_OPT_GRAPH:
       if (value != 0 && value != 1) return FITRIG_EINVAL;
@@ -904,11 +913,11 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
   if (freq) {
     mark(FITRIG_KERNEL_SPECTRUM, 0);
     if (p->hist_n > 0)   // the ring in any rotation: |X_k| ignores circular shifts
-      CKE(launch_spectrum(p->d_hist, p->hist_n, p->T, p->vstride, p->d_htw, p->d_hwts, p->d_eta,
-                          p->d_bin, st));
+      CKE(launch_spectrum(p->d_hist, p->hist_n, p->T, p->vstride, p->d_htw, p->d_hwts, p->hmax,
+                          p->d_eta, p->d_bin, st));
     else
-      CKE(launch_spectrum(p->d_vp, U, p->T, p->vstride, p->d_tw, p->d_wts, p->d_eta, p->d_bin,
-                          st));
+      CKE(launch_spectrum(p->d_vp, U, p->T, p->vstride, p->d_tw, p->d_wts, p->hmax, p->d_eta,
+                          p->d_bin, st));
     mark(FITRIG_KERNEL_SPECTRUM, 1);
     double* cs = p->d_cs + 2 * U;
     if (both) {

@@ -71,7 +71,7 @@ def test_status_strings(lib):
     ((10, 10, 5, 2, float("nan"), 1), 1),
     ((10, 10, 5, 2, 3.0, 4), 1),     # unknown branch
     ((300, 300, 5, 129, 3.0, 1), 9),  # windows above 128 are not implemented
-    ((10, 10, 300, 2, 3.0, 2), 9),   # transform longer than 256 points
+    ((10, 10, 4099, 2, 3.0, 2), 9),  # transform longer than 4096 points
 ])
 def test_plan_create_validation(lib, args, code):
     from paper_2509_21754_gb300 import fitrig as F

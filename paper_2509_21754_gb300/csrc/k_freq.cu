@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft(const float* __restrict__ v
 // Short series (n <= 2*KMAX + 1): the pair loop runs outermost and the
 // accumulators of every bin stay in registers; each twiddle is a shared-memory
 // broadcast, so one load feeds two multiply-adds.
-template <int KMAX>
+template <int KMAX, bool HARM>
 __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restrict__ vp, int n,
                                                            int64_t T, int64_t vs,
                                                            const float2* __restrict__ tw,
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restri
   }
   float best = -1.f;
   int bk = 1;
-  if (hmax > 1) {
+  if constexpr (HARM) {
     // the series is spent: its column holds the magnitudes for the harmonic sum
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
@@ -178,20 +178,20 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restri
     harmonic_best(my, kDftThreads, K, hmax, best, bk);
     eta[t] = best;
     bin[t] = bk;
-    return;
-  }
+  } else {
 #pragma unroll
-  for (int k = 0; k < KMAX; ++k) {
-    if (k < K) {
-      const float m2 = re[k] * re[k] + im[k] * im[k];
-      if (m2 > best) {
-        best = m2;
-        bk = k + 1;
+    for (int k = 0; k < KMAX; ++k) {
+      if (k < K) {
+        const float m2 = re[k] * re[k] + im[k] * im[k];
+        if (m2 > best) {
+          best = m2;
+          bk = k + 1;
+        }
       }
     }
+    eta[t] = sqrtf(best);
+    bin[t] = bk;
   }
-  eta[t] = sqrtf(best);
-  bin[t] = bk;
 }
 
 // Even n = 2m (n <= 66): the transform splits into the two length-m DFTs of
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_short(const float* __restri
 // parts), half the work of the direct form.  X_m = E_0 - O_0 (Nyquist).
 // Twiddles come from the host's FP64 table of 2 pi q / n (its first row) by
 // symmetry.
-template <int KH>
+template <int KH, bool HARM>
 __global__ void __launch_bounds__(kDftThreads) k_dft_even(const float* __restrict__ vp, int n,
                                                           int64_t T, int64_t vs,
                                                           const float2* __restrict__ tw,
@@ -294,13 +294,13 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_even(const float* __restric
   float best = -1.f;
   int bk = 1;
   // with harmonic summing the spent series column collects |X_k| at row k - 1
-  const bool harm = hmax > 1;
+  constexpr bool harm = HARM;
   auto take = [&](int k, float Er, float Ei, float Or, float Oi) {
     const float2 w = tk[k];
     const float re = Er + w.x * Or + w.y * Oi;
     const float im = Ei + w.x * Oi - w.y * Or;
     const float m2 = re * re + im * im;
-    if (harm) my[(k - 1) * kDftThreads] = sqrtf(m2);
+    if constexpr (harm) my[(k - 1) * kDftThreads] = sqrtf(m2);
     if (m2 > best || (m2 == best && k < bk)) {
       best = m2;
       bk = k;
@@ -316,20 +316,20 @@ __global__ void __launch_bounds__(kDftThreads) k_dft_even(const float* __restric
   {
     const float x = E0 - O0;   // bin m
     const float m2 = x * x;
-    if (harm) my[(m - 1) * kDftThreads] = fabsf(x);
+    if constexpr (HARM) my[(m - 1) * kDftThreads] = fabsf(x);
     if (m2 > best || (m2 == best && m < bk)) {
       best = m2;
       bk = m;
     }
   }
-  if (harm) {
+  if constexpr (HARM) {
     harmonic_best(my, kDftThreads, m, hmax, best, bk);
     eta[t] = best;
     bin[t] = bk;
-    return;
+  } else {
+    eta[t] = sqrtf(best);
+    bin[t] = bk;
   }
-  eta[t] = sqrtf(best);
-  bin[t] = bk;
 }
 
 // Long series (n up to kLongMaxN) and harmonic sums beyond the short kernels:
@@ -495,23 +495,21 @@ cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
   const int64_t blocks = (T + kDftThreads - 1) / kDftThreads;
   const int H = (n - 1) / 2, K = n / 2;
   if (n < 2 || n > kLongMaxN || hmax < 1) return cudaErrorInvalidValue;
+  const bool harm = hmax > 1;
   if ((n & 1) == 0 && n <= 66) {
     const int m = n / 2, Hm = (m - 1) / 2, Kh = m / 2;
     const size_t sm = (size_t)(Hm > 0 ? Hm * Kh : 0) * sizeof(float2) + (size_t)m * sizeof(float2) +
                       (size_t)n * kDftThreads * sizeof(float);
-    k_dft_even<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts, hmax,
-                                                              eta, bin);
+    auto kern = harm ? k_dft_even<16, true> : k_dft_even<16, false>;
+    kern<<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts, hmax, eta, bin);
     count_launches(1);
     return cudaGetLastError();
   }
   if (n <= 65 && H >= 1) {
     const size_t sm = (size_t)H * K * sizeof(float2) + (size_t)n * kDftThreads * sizeof(float);
-    if (K <= 16)
-      k_dft_short<16><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts,
-                                                                 hmax, eta, bin);
-    else
-      k_dft_short<32><<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts,
-                                                                 hmax, eta, bin);
+    auto kern = K <= 16 ? (harm ? k_dft_short<16, true> : k_dft_short<16, false>)
+                        : (harm ? k_dft_short<32, true> : k_dft_short<32, false>);
+    kern<<<(unsigned)blocks, kDftThreads, sm, st>>>(vp, n, T, vs, twiddle, wts, hmax, eta, bin);
     count_launches(1);
     return cudaGetLastError();
   }

@@ -19,7 +19,7 @@
 //     x^(s+1) and D^(s) in registers from one snapshot to the next, so Delta and
 //     r never touch memory;
 //   * per-thread partial sums go to shared memory once per snapshot, and one
-//     thread per tile combines them in a fixed order (deterministic).
+//     warp per tile combines them in a fixed order (deterministic).
 // The one __syncthreads per snapshot also guards the reuse of ring stages, so
 // no "empty" barriers are needed.
 #include <algorithm>
@@ -33,6 +33,17 @@ namespace fitrig {
 constexpr int kStackMaxThreads = 512;
 constexpr int kSmallMaxThreads = 256;   // thread-per-tile path: 32 x TBY tiles per CTA
 constexpr int kSmallMaxW = 6;
+
+// Maximum of v over the calling threads into *key.  Full warps reduce with
+// shuffles first; the threads of a trailing partial warp (a block size that is
+// not a multiple of 32) go straight to the atomic.
+__device__ __forceinline__ void max_to(float v, unsigned* key, bool full_warp) {
+  if (full_warp) {
+    warp_max_to(v, key);
+    return;
+  }
+  if (v > -INFINITY) atomicMax(key, f32_key(v));
+}
 
 template <typename T, int R, bool SIGNED>
 __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_constant__ CUtensorMap tmap,
@@ -129,7 +140,8 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
       return;
     }
     mx = fmaxf(mx, sm);
-    if (a.smax) warp_max_to(sm, a.smax + j);
+    const bool full_warp = (tid >> 5) < (g.threads >> 5);
+    if (a.smax) max_to(sm, a.smax + j, full_warp);
     if (tid == 0 && j + NS < L) {
       fence_proxy_async_smem();
       mbar_expect_tx(bar0 + 8 * stg, box_bytes);
@@ -140,37 +152,46 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
       stg = 0;
       phase ^= 1u;
     }
-    if (j >= 2 && tid < g.TBX * g.TBY) {
-      const int tb = tid / g.TBX;
-      const int tbx = tid - tb * g.TBX;
-      const int tx = blockIdx.x * g.TBX + tbx;
-      const int ty = blockIdx.y * g.TBY + tb;
-      if (tx < a.Tx && ty < a.Ty) {
-        const float4* pp = part + (j & 1) * g.threads;
+    if (j >= 2) {
+      // One full warp per tile combines the tile's nseg * w column partials:
+      // lanes stride over them, then a fixed shuffle tree (deterministic).
+      // Warps take tiles round-robin; a trailing partial warp takes none.
+      const int warp = tid >> 5, lane = tid & 31, nwf = g.threads >> 5;
+      const int NT = g.TBX * g.TBY, per = g.nseg * g.w;
+      const float4* pp = part + (j & 1) * g.threads;
+      for (int tt = warp; tt < NT && warp < nwf; tt += nwf) {
+        const int tb = tt / g.TBX;
+        const int tbx = tt - tb * g.TBX;
         float S1 = 0.f, S2 = 0.f, S3 = 0.f;
-        for (int sg = 0; sg < g.nseg; ++sg) {
-          const float4* row = pp + (tb * g.nseg + sg) * g.BW + tbx * g.w;
-          for (int cc = 0; cc < g.w; ++cc) {
-            const float4 q = row[cc];
-            S1 += q.x;
-            S2 = fmaxf(S2, q.y);
-            S3 += q.z;
-          }
+        for (int i = lane; i < per; i += 32) {
+          const int sg = i / g.w, cc = i - sg * g.w;
+          const float4 q = pp[(tb * g.nseg + sg) * g.BW + tbx * g.w + cc];
+          S1 += q.x;
+          S2 = fmaxf(S2, q.y);
+          S3 += q.z;
         }
-        const int hw = min(g.w, a.ny - ty * g.w);
-        const int ww = min(g.w, a.nx - tx * g.w);
-        const float n = (float)(hw * ww);
-        float v = (S1 / n) * S2 * (S3 / n);
-        if (!isfinite(S1) || !isfinite(v)) v = NAN;
-        a.vp[(size_t)(j - 2) * (size_t)a.vstride + (size_t)ty * a.Tx + tx] = v;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+          S2 = fmaxf(S2, __shfl_xor_sync(0xffffffffu, S2, o));
+          S3 += __shfl_xor_sync(0xffffffffu, S3, o);
+        }
+        const int tx = blockIdx.x * g.TBX + tbx;
+        const int ty = blockIdx.y * g.TBY + tb;
+        if (lane == 0 && tx < a.Tx && ty < a.Ty) {
+          const int hw = min(g.w, a.ny - ty * g.w);
+          const int ww = min(g.w, a.nx - tx * g.w);
+          const float n = (float)(hw * ww);
+          float v = (S1 / n) * S2 * (S3 / n);
+          if (!isfinite(S1) || !isfinite(v)) v = NAN;
+          a.vp[(size_t)(j - 2) * (size_t)a.vstride + (size_t)ty * a.Tx + tx] = v;
+        }
       }
     }
   }
   (void)stg;
   // Global maximum M (NaN ignored by fmaxf; +inf is resolved on the host).
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((tid & 31) == 0 && mx > -INFINITY) atomicMax(a.gmax, f32_key(mx));
+  max_to(mx, a.gmax, (tid >> 5) < (g.threads >> 5));
 }
 
 // Small windows (W <= 6): one thread owns a whole W x W tile and keeps its

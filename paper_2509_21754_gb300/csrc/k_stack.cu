@@ -34,6 +34,13 @@ constexpr int kStackMaxThreads = 512;
 constexpr int kSmallMaxThreads = 256;   // thread-per-tile path: 32 x TBY tiles per CTA
 constexpr int kSmallMaxW = 6;
 
+// Approximate reciprocal (rcp.approx.ftz: relative error below 2^-23).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Maximum of v over the calling threads into *key.  Full warps reduce with
 // shuffles first; the threads of a trailing partial warp (a block size that is
 // not a multiple of 32) go straight to the atomic.
@@ -98,6 +105,16 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
     if (ok) {
       if (j >= 2) {
         float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        // ABS reading: when none of the column's x^(s+1) is zero (its smallest
+        // |x| is not), r = sat(Delta * |1/x|) needs no guard (as in the
+        // thread-per-tile march); otherwise every pixel takes the guarded form.
+        float mn = INFINITY;
+        if (!SIGNED) {
+#pragma unroll
+          for (int i = 0; i < R; ++i)
+            if (i < rcount) mn = fminf(mn, fabsf(xp[i]));
+        }
+        const bool fast = !SIGNED && mn != 0.f;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
           if (i < rcount) {
@@ -105,9 +122,14 @@ __global__ void __launch_bounds__(kStackMaxThreads) k_stack_tile(const __grid_co
             sm = fmaxf(sm, xn);
             const float dn = fabsf(xn - xp[i]);        // D^(s+1)
             const float d = fabsf(dn - dp[i]);         // Delta
-            const float ref = SIGNED ? xp[i] : fabsf(xp[i]);
-            const float xh = (xp[i] == 0.f) ? kGuardC : ref;   // Eq. 5
-            const float r = fminf(__fdividef(d, xh), 1.f);     // Eq. 4
+            float r;
+            if (fast) {
+              r = __saturatef(d * fabsf(rcp_approx(xp[i])));
+            } else {
+              const float ref = SIGNED ? xp[i] : fabsf(xp[i]);
+              const float xh = (xp[i] == 0.f) ? kGuardC : ref;   // Eq. 5
+              r = fminf(__fdividef(d, xh), 1.f);                 // Eq. 4
+            }
             s1 += d;
             s2 = fmaxf(s2, d);
             s3 += r;
@@ -260,13 +282,6 @@ __device__ __forceinline__ float r_term(float d, float xref) {
   }
   const float xh = (xref == 0.f) ? kGuardC : fabsf(xref);
   return __saturatef(__fdividef(d, xh));
-}
-
-// Approximate reciprocal (rcp.approx.ftz: relative error below 2^-23).
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
 }
 
 // Waits for the ring's current stage (bounded); false when it never completed.
@@ -614,24 +629,35 @@ bool small_geometry(int w, int elem_bytes, int tby, int stages, StackGeom* g) {
 bool stack_geometry(int w, int elem_bytes, StackGeom* g) {
   if (w < 1 || w > 128) return false;
   if (w >= 3 && w <= kSmallMaxW && small_geometry(w, elem_bytes, 4, 4, g)) return true;
-  // rows per thread R (a template value) and row segments per tile band
-  int R, nseg;
+  // Rows per thread R (a template value) and row segments per tile band.
+  // Long columns (R = 32 or 16 rows, when padding the last segment wastes at
+  // most a quarter of the rows) spread the per-snapshot costs -- the stage
+  // wait, the barrier, the partial sums -- over many pixels and keep CTAs at
+  // about 128 threads; otherwise the tile's rows split evenly into <= 8.
+  int R = 0, nseg = 0;
+  bool wide = false;
   if (w <= 8) {
     R = w;
     nseg = 1;
-  } else if (w <= 32) {
-    nseg = (w + 7) / 8;
-    R = (w + nseg - 1) / nseg;
-  } else if (w <= 64) {
-    R = 16;
-    nseg = (w + 15) / 16;
   } else {
-    R = 32;
-    nseg = (w + 31) / 32;
+    for (int r : {32, 16}) {
+      const int ns = (w + r - 1) / r;
+      if (4 * (ns * r - w) <= ns * r) {
+        R = r;
+        nseg = ns;
+        wide = true;
+        break;
+      }
+    }
+    if (!wide) {
+      nseg = (w + 7) / 8;
+      R = (w + nseg - 1) / nseg;
+    }
   }
-  // Tiles per CTA in x: about 160 pixel columns, preferring an origin that is
-  // always a multiple of 8 elements (TMA needs 16-byte aligned x).
-  const int max_cols = std::min(160, kStackMaxThreads / nseg);
+  // Tiles per CTA in x: about 160 pixel columns (128 threads for the long
+  // columns), preferring an origin that is always a multiple of 8 elements
+  // (TMA needs 16-byte aligned x).
+  const int max_cols = wide ? std::max(w, 128 / nseg) : std::min(160, kStackMaxThreads / nseg);
   if (w > max_cols) return false;
   int tbx = 0;
   for (int t = max_cols / w; t >= 1; --t)
@@ -639,7 +665,7 @@ bool stack_geometry(int w, int elem_bytes, StackGeom* g) {
   bool aligned = tbx > 0;
   if (!aligned) tbx = max_cols / w;
   const int BW = tbx * w;
-  int tby = 320 / (BW * nseg);
+  int tby = (wide ? 128 : 320) / (BW * nseg);
   if (tby < 1) tby = 1;
   if (tby * w > 256) tby = 256 / w;
   if (tby < 1) return false;

@@ -629,35 +629,24 @@ bool small_geometry(int w, int elem_bytes, int tby, int stages, StackGeom* g) {
 bool stack_geometry(int w, int elem_bytes, StackGeom* g) {
   if (w < 1 || w > 128) return false;
   if (w >= 3 && w <= kSmallMaxW && small_geometry(w, elem_bytes, 4, 4, g)) return true;
-  // Rows per thread R (a template value) and row segments per tile band.
-  // Long columns (R = 32 or 16 rows, when padding the last segment wastes at
-  // most a quarter of the rows) spread the per-snapshot costs -- the stage
-  // wait, the barrier, the partial sums -- over many pixels and keep CTAs at
-  // about 128 threads; otherwise the tile's rows split evenly into <= 8.
-  int R = 0, nseg = 0;
-  bool wide = false;
+  // rows per thread R (a template value) and row segments per tile band
+  int R, nseg;
   if (w <= 8) {
     R = w;
     nseg = 1;
+  } else if (w <= 32) {
+    nseg = (w + 7) / 8;
+    R = (w + nseg - 1) / nseg;
+  } else if (w <= 64) {
+    R = 16;
+    nseg = (w + 15) / 16;
   } else {
-    for (int r : {32, 16}) {
-      const int ns = (w + r - 1) / r;
-      if (4 * (ns * r - w) <= ns * r) {
-        R = r;
-        nseg = ns;
-        wide = true;
-        break;
-      }
-    }
-    if (!wide) {
-      nseg = (w + 7) / 8;
-      R = (w + nseg - 1) / nseg;
-    }
+    R = 32;
+    nseg = (w + 31) / 32;
   }
-  // Tiles per CTA in x: about 160 pixel columns (128 threads for the long
-  // columns), preferring an origin that is always a multiple of 8 elements
-  // (TMA needs 16-byte aligned x).
-  const int max_cols = wide ? std::max(w, 128 / nseg) : std::min(160, kStackMaxThreads / nseg);
+  // Tiles per CTA in x: about 160 pixel columns, preferring an origin that is
+  // always a multiple of 8 elements (TMA needs 16-byte aligned x).
+  const int max_cols = std::min(160, kStackMaxThreads / nseg);
   if (w > max_cols) return false;
   int tbx = 0;
   for (int t = max_cols / w; t >= 1; --t)
@@ -665,7 +654,7 @@ bool stack_geometry(int w, int elem_bytes, StackGeom* g) {
   bool aligned = tbx > 0;
   if (!aligned) tbx = max_cols / w;
   const int BW = tbx * w;
-  int tby = (wide ? 128 : 320) / (BW * nseg);
+  int tby = 320 / (BW * nseg);
   if (tby < 1) tby = 1;
   if (tby * w > 256) tby = 256 / w;
   if (tby < 1) return false;

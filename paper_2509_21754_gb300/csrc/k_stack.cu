@@ -509,6 +509,123 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_stack_small(const __grid_c
   block_max_to(mx, a.gmax);
 }
 
+// Windows that are multiples of 4 up to 64 (8, 16, 32, 64): the thread-per-tile
+// march on 4 x 4 sub-tiles.  Each thread keeps its sub-tile's x^(s+1) and
+// D^(s) in registers (tile_unit with W = 4); a warp covers 128 columns x 4
+// rows.  A w x w tile spans w/4 lanes and w/4 warps: its lanes combine by a
+// shuffle tree, each warp leaves one partial per tile in shared memory, and
+// after the ring barrier of the snapshot one thread per tile adds the w/4
+// warp partials in order (deterministic).  The partials are double-buffered by
+// unit parity, so the next unit's partials never overwrite ones being read.
+constexpr int kSubCols = 128;   // 32 lanes x 4 columns
+
+// Partials after the ring stages and their barriers, 16-byte aligned.
+__host__ __device__ __forceinline__ size_t sub_part_offset_host(int stages, size_t stage_bytes) {
+  return ((size_t)stages * stage_bytes + 8 * (size_t)stages + 15) / 16 * 16;
+}
+__device__ __forceinline__ size_t sub_part_offset(const StackGeom& g) {
+  return sub_part_offset_host(g.stages, g.stage_bytes);
+}
+
+template <typename T, bool SIGNED>
+__device__ __forceinline__ bool march_sub(const CUtensorMap* tmap, const StackArgs& a, Ring& rg,
+                                          unsigned char* smem, uint64_t deadline, float& mx) {
+  constexpr int N = 16;
+  const StackGeom& g = a.g;
+  const int w = g.w, gl = w / 4;             // lanes (and warps) per tile side
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = g.threads >> 5;
+  const int L = a.nsnap;
+  const int x0 = blockIdx.x * kSubCols, y0 = blockIdx.y * g.BH;
+  float4* part = reinterpret_cast<float4*>(smem + sub_part_offset(g));   // [2][nw][TBX]
+  const int off = (warp * 4) * kSubCols + lane * 4;
+  if (tid == 0) {
+    int s = rg.stg;
+    for (int j = 0; j < rg.NS && j < L; ++j) {
+      mbar_expect_tx(rg.bar0 + 8 * s, rg.box_bytes);
+      tma_load_3d(rg.stage0 + s * rg.stage_bytes, tmap, x0, y0, (a.zrot + j) % L, rg.bar0 + 8 * s);
+      if (++s == rg.NS) s = 0;
+    }
+  }
+  auto stage = [&]() {
+    return reinterpret_cast<const T*>(smem + (size_t)rg.stg * rg.stage_bytes) + off;
+  };
+  // the tile this thread reduces after each barrier (one per tile of the CTA)
+  const int NT = g.TBX * g.TBY;
+  const int rtb = tid / g.TBX, rtc = tid - (tid / g.TBX) * g.TBX;
+  const int rtx = blockIdx.x * g.TBX + rtc, rty = blockIdx.y * g.TBY + rtb;
+  const bool rlive = tid < NT && rtx < a.Tx && rty < a.Ty;
+  float inv_n = 0.f;
+  if (rlive) {
+    const int hw = min(w, a.ny - rty * w), ww = min(w, a.nx - rtx * w);
+    inv_n = 1.f / (float)(hw * ww);
+  }
+  float* out = a.vp + (rlive ? (size_t)rty * a.Tx + rtx : 0);
+  float xa[N], da[N], xb[N], db[N];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (j >= L) break;
+    const bool ok = ring_wait(rg, deadline);
+    float sm = -INFINITY;
+    if (ok) {
+      if (j == 0) tile_load<T, 4>(stage(), xb, xa, da, true, sm);
+      else tile_load<T, 4>(stage(), xa, xb, db, false, sm);
+    }
+    if (!ring_release(rg, ok, tmap, a.status, j, L, x0, y0, a.zrot)) return false;
+    mx = fmaxf(mx, sm);
+    if (a.smax) warp_max_to(sm, a.smax + j);
+  }
+  auto unit = [&](int j, const float (&xp)[N], const float (&dp)[N], float (&xn)[N],
+                  float (&dn)[N]) -> bool {
+    const bool ok = ring_wait(rg, deadline);
+    float sm = -INFINITY;
+    float s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int am = 0;
+    if (ok) tile_unit<T, 4, SIGNED>(stage(), xp, dp, xn, dn, sm, s1, s2, s3, am);
+    for (int o = gl >> 1; o > 0; o >>= 1) {
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      s2 = fmaxf(s2, __shfl_xor_sync(0xffffffffu, s2, o));
+      s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+    }
+    float4* pp = part + (size_t)(j & 1) * nw * g.TBX;
+    if (lane % gl == 0) pp[warp * g.TBX + lane / gl] = make_float4(s1, s2, s3, 0.f);
+    if (!ring_release(rg, ok, tmap, a.status, j, L, x0, y0, a.zrot)) return false;
+    mx = fmaxf(mx, sm);
+    if (a.smax) warp_max_to(sm, a.smax + j);
+    if (rlive) {
+      float S1 = 0.f, S2 = 0.f, S3 = 0.f;
+      for (int k = 0; k < gl; ++k) {
+        const float4 q = pp[(rtb * gl + k) * g.TBX + rtc];
+        S1 += q.x;
+        S2 = fmaxf(S2, q.y);
+        S3 += q.z;
+      }
+      float v = (S1 * inv_n) * S2 * (S3 * inv_n);
+      if (!isfinite(S1) || !isfinite(v)) v = NAN;
+      out[(size_t)(j - 2) * (size_t)a.vstride] = v;
+    }
+    return true;
+  };
+  for (int j = 2; j < L; j += 2) {
+    if (!unit(j, xb, db, xa, da)) return false;
+    if (j + 1 < L && !unit(j + 1, xa, da, xb, db)) return false;
+  }
+  return true;
+}
+
+template <typename T, bool SIGNED>
+__global__ void __launch_bounds__(kStackMaxThreads) k_stack_sub(const __grid_constant__ CUtensorMap tmap,
+                                                                const StackArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (threadIdx.x == 0) prefetch_tmap(&tmap);
+  Ring rg;
+  ring_init(rg, smem, a.g, (int)sizeof(T));
+  float mx = -INFINITY;
+  const uint64_t deadline = globaltimer_ns() + a.timeout_ns;
+  if (!march_sub<T, SIGNED>(&tmap, a, rg, smem, deadline, mx)) return;
+  block_max_to(mx, a.gmax);
+}
+
 // Persistent form over many fields (one launch for a whole batch): each CTA
 // takes the next (field, box) item from a global counter until none is left;
 // fields are ordered largest first.  Every field has its own TMA descriptor in
@@ -626,9 +743,35 @@ bool small_geometry(int w, int elem_bytes, int tby, int stages, StackGeom* g) {
   return true;
 }
 
+// Sub-tile march (w = 8, 16, 32, 64): a CTA covers 128 columns (128 / w tiles)
+// and 32 rows (64 for w = 64) with one warp per 4 rows; about 64 KB of ring.
+static bool sub_geometry(int w, int elem_bytes, StackGeom* g) {
+  if (w != 8 && w != 16 && w != 32 && w != 64) return false;
+  const int BH = w <= 32 ? 32 : 64;
+  const int nw = BH / 4;
+  size_t stage = (size_t)kSubCols * BH * elem_bytes;
+  stage = (stage + 127) / 128 * 128;
+  const int stages = std::max(3, std::min(8, (int)(65536 / stage)));
+  g->w = w;
+  g->R = -1;   // marks the sub-tile path
+  g->nseg = 1;
+  g->TBX = kSubCols / w;
+  g->TBY = BH / w;
+  g->BW = kSubCols;
+  g->BH = BH;
+  g->boxW = kSubCols;
+  g->aligned = true;
+  g->stages = stages;
+  g->threads = 32 * nw;
+  g->stage_bytes = stage;
+  g->smem_bytes = sub_part_offset_host(stages, stage) + (size_t)2 * nw * g->TBX * sizeof(float4);
+  return g->smem_bytes <= 232448 - 1024;
+}
+
 bool stack_geometry(int w, int elem_bytes, StackGeom* g) {
   if (w < 1 || w > 128) return false;
   if (w >= 3 && w <= kSmallMaxW && small_geometry(w, elem_bytes, 4, 4, g)) return true;
+  if (sub_geometry(w, elem_bytes, g)) return true;
   // rows per thread R (a template value) and row segments per tile band
   int R, nseg;
   if (w <= 8) {
@@ -719,7 +862,24 @@ static cudaError_t launch_small(const CUtensorMap* tmap, const StackArgs& a, cud
 }
 
 template <typename T, bool SIGNED>
+static cudaError_t launch_sub(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
+  auto kern = k_stack_sub<T, SIGNED>;
+  static size_t configured = 0;
+  if (a.g.smem_bytes > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)a.g.smem_bytes);
+    if (e != cudaSuccess) return e;
+    configured = a.g.smem_bytes;
+  }
+  dim3 grid(a.g.gridX, a.g.gridY);
+  kern<<<grid, a.g.threads, a.g.smem_bytes, st>>>(*tmap, a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename T, bool SIGNED>
 static cudaError_t launch_r(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
+  if (a.g.R < 0) return launch_sub<T, SIGNED>(tmap, a, st);
   if (a.g.R == 0) {
     switch (a.g.w) {
       case 3: return launch_small<T, 3, SIGNED>(tmap, a, st);

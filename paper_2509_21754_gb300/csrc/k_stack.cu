@@ -613,8 +613,10 @@ __device__ __forceinline__ bool march_sub(const CUtensorMap* tmap, const StackAr
   return true;
 }
 
-template <typename T, bool SIGNED>
-__global__ void __launch_bounds__(kStackMaxThreads) k_stack_sub(const __grid_constant__ CUtensorMap tmap,
+// MAXT = 256 (w <= 32, eight warps) leaves room for three CTAs per SM;
+// MAXT = 512 (w = 64, sixteen warps) for one.
+template <typename T, bool SIGNED, int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_stack_sub(const __grid_constant__ CUtensorMap tmap,
                                                                 const StackArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   if (threadIdx.x == 0) prefetch_tmap(&tmap);
@@ -863,13 +865,14 @@ static cudaError_t launch_small(const CUtensorMap* tmap, const StackArgs& a, cud
 
 template <typename T, bool SIGNED>
 static cudaError_t launch_sub(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
-  auto kern = k_stack_sub<T, SIGNED>;
-  static size_t configured = 0;
-  if (a.g.smem_bytes > configured) {
+  const bool big = a.g.threads > 256;
+  auto kern = big ? k_stack_sub<T, SIGNED, 512> : k_stack_sub<T, SIGNED, 256>;
+  static size_t configured[2] = {0, 0};
+  if (a.g.smem_bytes > configured[big]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)a.g.smem_bytes);
     if (e != cudaSuccess) return e;
-    configured = a.g.smem_bytes;
+    configured[big] = a.g.smem_bytes;
   }
   dim3 grid(a.g.gridX, a.g.gridY);
   kern<<<grid, a.g.threads, a.g.smem_bytes, st>>>(*tmap, a);

@@ -325,6 +325,30 @@ __device__ __forceinline__ bool ring_release(Ring& rg, bool ok, const CUtensorMa
   return true;
 }
 
+// One tile row of W stage elements into FP32.  For W = 4 the row is one
+// 16-byte (FP32) or 8-byte (half) shared-memory load: a lane's row starts at a
+// multiple of 4 elements, and four scalar loads at a 4-word lane stride would
+// meet 4-way bank conflicts.
+template <typename T, int W>
+__device__ __forceinline__ void load_row(const T* src, float* dst) {
+  if constexpr (W == 4 && sizeof(T) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(src);
+    dst[0] = v.x;
+    dst[1] = v.y;
+    dst[2] = v.z;
+    dst[3] = v.w;
+  } else if constexpr (W == 4 && sizeof(T) == 2) {
+    const uint2 v = *reinterpret_cast<const uint2*>(src);
+    const uint16_t h[4] = {(uint16_t)(v.x & 0xffffu), (uint16_t)(v.x >> 16),
+                           (uint16_t)(v.y & 0xffffu), (uint16_t)(v.y >> 16)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dst[q] = to_f32(T{h[q]});
+  } else {
+#pragma unroll
+    for (int q = 0; q < W; ++q) dst[q] = to_f32(src[q]);
+  }
+}
+
 // One unit of the thread's W x W tile: from x^(s+1) (xp) and D^(s) (dp) and
 // the stage holding x^(s+2), writes x^(s+2) to xn and D^(s+1) to dn (separate
 // arrays, so that the caller alternates them and no value is copied), and
@@ -351,8 +375,7 @@ __device__ __forceinline__ void tile_unit(const T* st, const float (&xp)[W * W],
     float r1 = 0.f, r3 = 0.f, rm = 0.f;
     int ri = 0;
     float dd[W];
-#pragma unroll
-    for (int q = 0; q < W; ++q) xn[r * W + q] = to_f32(st[r * (32 * W) + q]);
+    load_row<T, W>(st + r * (32 * W), &xn[r * W]);
     sm = row_max<W>(sm, &xn[r * W]);
 #pragma unroll
     for (int q = 0; q < W; ++q) {
@@ -391,8 +414,7 @@ __device__ __forceinline__ void tile_load(const T* st, const float (&xp)[W * W],
                                           float& sm) {
 #pragma unroll
   for (int r = 0; r < W; ++r) {
-#pragma unroll
-    for (int q = 0; q < W; ++q) xn[r * W + q] = to_f32(st[r * (32 * W) + q]);
+    load_row<T, W>(st + r * (32 * W), &xn[r * W]);
     sm = row_max<W>(sm, &xn[r * W]);
   }
   if (!first) {

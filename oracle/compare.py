@@ -53,7 +53,7 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
             decide_image: Optional[Callable[[int, int, int], bool]] = None,
             decide_freq: Optional[Callable[[int, int], bool]] = None,
             det: Optional[O.Detection] = None, pixel_sample: Optional[int] = None,
-            harmonics: int = 1) -> List[str]:
+            harmonics: int = 1, refine: str = "parabolic") -> List[str]:
     """Return a list of parity violations (empty when the lists agree).
 
     ``harmonics`` is m_max of the frequency branch's h (1: maximum magnitude);
@@ -68,7 +68,8 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
     L, ny, nx = stack.shape
     Ty, Tx, nyu, nxu = O.tiling(ny, nx, w, edge)
     if det is None:
-        det = O.detect(stack, w, tau, branch, noise, rmode, edge, harmonics=harmonics)
+        det = O.detect(stack, w, tau, branch, noise, rmode, edge, harmonics=harmonics,
+                       refine=refine)
     band = REL_TOL * tau
     names = cands.dtype.names
     got = [dict(zip(names, c)) for c in cands]
@@ -142,7 +143,8 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
         ref = {}
         for c in O.freq_candidates(det.eta, det.eta_bin, z, tau, w, nyu, nxu,
                                    forced={(int(a), int(b)): bool(mask[a, b])
-                                           for a, b in zip(*np.nonzero(amb))}):
+                                           for a, b in zip(*np.nonzero(amb))},
+                                   refine=refine):
             ref[(c.y // w, c.x // w)] = c
         series = det.tlisi
         for gc, (ty, tx), _ in check_groups([("freq", z, comps, -1)], O.BRANCH_FREQ):

@@ -47,6 +47,10 @@ Readings where the paper is silent or ambiguous (each is an option here):
   m = 1, 2, 4, .., m_max and over the k with m k <= floor(n/2); m_max = 1 is
   the maximum magnitude.  The bin reported is the fundamental k.  Ties go to
   the smaller m, then the smaller k.
+* the spline interpolation of eta (Sec. 2.4.2, Sec. 3.3; parity with the paper
+  unpinned, no formula given): per axis, the Catmull-Rom cubic through the
+  peak tile's eta and two neighbours on each side, maximised within half a
+  tile (``cubic_offset``); the default refine is the three-point parabola.
 * a sliding-window mode (not in the paper, whose tiles partition the image)
   evaluates the tile statistic over the odd w x w window centred on each pixel,
   clipped at the border, and then treats pixels as 1 x 1 tiles.
@@ -456,6 +460,67 @@ def parabolic_offset(left: float, centre: float, right: float) -> float:
     return float(min(0.5, max(-0.5, d)))
 
 
+def cubic_offset(m2: float, m1: float, c: float, p1: float, p2: float) -> float:
+    """Peak offset (in grid steps, within [-0.5, 0.5]) of the Catmull-Rom cubic
+    spline through the samples at -2, -1, 0, +1, +2 (the "spline
+    interpolation" of eta, Sec. 2.4.2 and Sec. 3.3; our reading).
+
+    On the segment between samples a (at 0) and b (at 1) with outer neighbours
+    z (at -1) and d (at 2) the spline is
+        f(t) = a + t (b - z) / 2 + t^2 (2z - 5a + 4b - d) / 2
+               + t^3 (-z + 3a - 3b + d) / 2.
+    The maximum over [0, 0.5] (segment 0..1, t in [0, 0.5]) and [-0.5, 0]
+    (segment -1..0, t in [0.5, 1]) is taken among, in this order, the offset
+    0, the right segment's interior roots of f' (ascending) and +0.5, then the
+    left segment's interior roots (ascending) and -0.5; the first of equal
+    values is kept.  A side whose neighbour at +-1 is missing (outside the map or not
+    finite) is not searched; a missing sample at +-2 is extended linearly
+    (2 f(+-1) - f(0)).  A non-finite centre gives 0.
+    """
+    fin = np.isfinite
+    if not fin(c):
+        return 0.0
+    best_x, best_f = 0.0, float(c)
+
+    def consider(x: float, f: float):
+        nonlocal best_x, best_f
+        if f > best_f:
+            best_x, best_f = x, f
+
+    def segment(z, a, b, d, lo, hi, shift):
+        # f on t in [lo, hi]; offset x = t + shift
+        k1 = 0.5 * (b - z)
+        k2 = 0.5 * (2 * z - 5 * a + 4 * b - d)
+        k3 = 0.5 * (-z + 3 * a - 3 * b + d)
+        f = lambda t: a + t * (k1 + t * (k2 + t * k3))
+        # roots of f'(t) = A t^2 + B t + C by the cancellation-free form
+        # q = -(B + sign(B) sqrt(B^2 - 4AC)) / 2, t = q / A and C / q (a
+        # near-zero A, as for a quadratic, leaves the linear root intact)
+        A, B, C_ = 3.0 * k3, 2.0 * k2, k1
+        roots = []
+        disc = B * B - 4.0 * A * C_
+        if disc >= 0.0:
+            q = -0.5 * (B + np.copysign(np.sqrt(disc), B))
+            if A != 0.0:
+                roots.append(q / A)
+            if q != 0.0:
+                roots.append(C_ / q)
+            roots.sort()
+        for t in roots:
+            if lo < t < hi:
+                consider(t + shift, f(t))
+        end = hi if shift == 0.0 else lo
+        consider(end + shift, f(end))
+
+    if fin(p1):
+        d = p2 if fin(p2) else 2.0 * p1 - c
+        segment(m1 if fin(m1) else 2.0 * c - p1, c, p1, d, 0.0, 0.5, 0.0)
+    if fin(m1):
+        z = m2 if fin(m2) else 2.0 * m1 - c
+        segment(z, m1, c, p1 if fin(p1) else 2.0 * c - m1, 0.5, 1.0, -1.0)
+    return float(best_x)
+
+
 # --------------------------------------------------------------------------
 # Whole trigger
 # --------------------------------------------------------------------------
@@ -512,7 +577,11 @@ def image_candidates(units: List[UnitTiles], z: np.ndarray, tau: float,
 
 def freq_candidates(eta: np.ndarray, kbin: np.ndarray, z: np.ndarray, tau: float,
                     w: int, nyu: int, nxu: int,
-                    forced: Optional[Dict[Tuple[int, int], bool]] = None) -> List[Candidate]:
+                    forced: Optional[Dict[Tuple[int, int], bool]] = None,
+                    refine: str = "parabolic") -> List[Candidate]:
+    """One candidate per component of the selected eta tiles, at the peak
+    tile's centre; the refined position uses ``parabolic_offset`` (three
+    samples) or ``cubic_offset`` (the spline through five) along each axis."""
     Ty, Tx = eta.shape
     mask = select(z, tau)
     if forced:
@@ -526,8 +595,12 @@ def freq_candidates(eta: np.ndarray, kbin: np.ndarray, z: np.ndarray, tau: float
         cy = ty * w + (hy - 1) / 2.0
         gx = lambda j: eta[ty, j] if 0 <= j < Tx else np.nan
         gy = lambda j: eta[j, tx] if 0 <= j < Ty else np.nan
-        dx = parabolic_offset(gx(tx - 1), eta[ty, tx], gx(tx + 1))
-        dy = parabolic_offset(gy(ty - 1), eta[ty, tx], gy(ty + 1))
+        if refine == "cubic":
+            dx = cubic_offset(gx(tx - 2), gx(tx - 1), eta[ty, tx], gx(tx + 1), gx(tx + 2))
+            dy = cubic_offset(gy(ty - 2), gy(ty - 1), eta[ty, tx], gy(ty + 1), gy(ty + 2))
+        else:
+            dx = parabolic_offset(gx(tx - 1), eta[ty, tx], gx(tx + 1))
+            dy = parabolic_offset(gy(ty - 1), eta[ty, tx], gy(ty + 1))
         out.append(Candidate(-1, ty * w + (hy - 1) // 2, tx * w + (wx - 1) // 2,
                              float(z[ty, tx]), BRANCH_FREQ, int(kbin[ty, tx]),
                              float(cx + dx * w), float(cy + dy * w)))
@@ -537,7 +610,7 @@ def freq_candidates(eta: np.ndarray, kbin: np.ndarray, z: np.ndarray, tau: float
 def detect(stack: np.ndarray, w: int, tau: float, branch: int = BRANCH_IMAGE,
            noise: str = "meanstd", rmode: str = "abs", edge: str = "partial",
            forced_image=None, forced_freq=None, stride: str = "tile",
-           mmode: str = "global", harmonics: int = 1) -> Detection:
+           mmode: str = "global", harmonics: int = 1, refine: str = "parabolic") -> Detection:
     """Run the trigger on a (L, ny, nx) stack and return the sorted candidates.
 
     stride "tile" is the paper's tiling; "sliding" evaluates the same statistic
@@ -580,14 +653,15 @@ def detect(stack: np.ndarray, w: int, tau: float, branch: int = BRANCH_IMAGE,
         ez, ec, es = zscore_map(eta, noise)
         det.eta, det.eta_bin, det.eta_z = eta, kbin, ez
         det.eta_centre, det.eta_scale = ec, es
-        cands += freq_candidates(eta, kbin, ez, tau, w, nyu, nxu, forced_freq)
+        cands += freq_candidates(eta, kbin, ez, tau, w, nyu, nxu, forced_freq, refine)
     cands.sort(key=Candidate.key)
     det.candidates = cands
     return det
 
 
 def freq_window(stack: np.ndarray, w: int, tau: float, n: int, noise: str = "meanstd",
-                forced: Optional[Dict[Tuple[int, int], bool]] = None, harmonics: int = 1):
+                forced: Optional[Dict[Tuple[int, int], bool]] = None, harmonics: int = 1,
+                refine: str = "parabolic"):
     """Real-time image-frequency branch: the Sec. 2.4.2 statistic over the last
     ``n`` units of the stack only (units L-2-n .. L-3), each normalised by its
     running M_s (the real-time reading of Sec. 2.2.4).  Returns (candidates,
@@ -606,7 +680,7 @@ def freq_window(stack: np.ndarray, w: int, tau: float, n: int, noise: str = "mea
     tl = np.stack([tlisi_from_tiles(unit_tiles(x, s, w), Ms[s]) for s in range(first, L - 2)])
     eta, kbin = spectrum(tl, harmonics)
     z, _, _ = zscore_map(eta, noise)
-    cands = freq_candidates(eta, kbin, z, tau, w, nyu, nxu, forced)
+    cands = freq_candidates(eta, kbin, z, tau, w, nyu, nxu, forced, refine)
     for c in cands:
         c.snapshot = L - 3
     return cands, eta, kbin, z

@@ -639,3 +639,65 @@ def test_harmonic_summing_finds_a_pulse_train_missed_by_the_maximum():
     z1 = O.zscore_map(O.spectrum(cube, 1)[0])[0][2, 5]
     z8 = O.zscore_map(O.spectrum(cube, 8)[0])[0][2, 5]
     assert z8 > z1 + 1.0
+
+
+# ---------------------------------------------------------------- spline refine of eta
+@pytest.mark.parametrize("x0", [-0.5, -0.37, -0.1, 0.0, 0.23, 0.41, 0.5])
+def test_cubic_refine_reproduces_a_parabola(x0):
+    """Catmull-Rom splines reproduce quadratics, so samples of a parabola refine
+    to its vertex exactly, as the three-point parabola does."""
+    q = lambda x: 7.0 - 3.0 * (x - x0) ** 2
+    s = [q(x) for x in (-2, -1, 0, 1, 2)]
+    assert O.cubic_offset(*s) == pytest.approx(x0, abs=1e-12)
+    assert O.parabolic_offset(s[1], s[2], s[3]) == pytest.approx(x0, abs=1e-12)
+
+
+def test_cubic_refine_against_a_hermite_spline():
+    """The same spline as scipy's cubic Hermite interpolant with Catmull-Rom
+    (central-difference) tangents, maximised on a dense grid over [-0.5, 0.5]."""
+    from scipy.interpolate import CubicHermiteSpline
+    rng = np.random.default_rng(17)
+    grid = np.linspace(-0.5, 0.5, 200001)
+    checked = 0
+    for _ in range(400):
+        y = rng.standard_normal(5)
+        y[2] += 1.5                       # a peak near the centre, as for a selected tile
+        yi = y[1:4]
+        m = 0.5 * (y[2:5] - y[0:3])       # tangents at -1, 0, 1
+        f = CubicHermiteSpline([-1.0, 0.0, 1.0], yi, m)(grid)
+        top = np.sort(f)[-1]
+        # skip near ties between two separate maxima (either answer is right)
+        far = np.abs(grid - grid[np.argmax(f)]) > 0.02
+        if far.any() and f[far].max() > top - 1e-9:
+            continue
+        x = O.cubic_offset(*y)
+        assert x == pytest.approx(grid[np.argmax(f)], abs=2e-5)
+        checked += 1
+    assert checked > 350
+
+
+def test_cubic_refine_edges_and_degenerate_samples():
+    assert O.cubic_offset(1.0, 2.0, 3.0, 2.0, 1.0) == 0.0            # symmetric
+    assert O.cubic_offset(0.0, 1.0, 2.0, 3.0, 4.0) == 0.5            # rising line: right end
+    assert O.cubic_offset(4.0, 3.0, 2.0, 1.0, 0.0) == -0.5           # falling line: left end
+    assert O.cubic_offset(1.0, 5.0, 3.0, np.nan, np.nan) < 0.0       # no right neighbour
+    assert O.cubic_offset(np.nan, np.nan, 3.0, 5.0, 1.0) > 0.0       # no left neighbour
+    assert O.cubic_offset(np.nan, np.nan, 3.0, np.nan, np.nan) == 0.0
+    assert O.cubic_offset(1.0, 2.0, np.nan, 2.0, 1.0) == 0.0
+    # a missing outer sample is the linear extension 2 f(+-1) - f(0)
+    a = O.cubic_offset(0.3, 2.0, 3.0, 2.6, np.nan)
+    b = O.cubic_offset(0.3, 2.0, 3.0, 2.6, 2 * 2.6 - 3.0)
+    assert a == b
+
+
+def test_cubic_refine_moves_a_freq_candidate_towards_the_source():
+    """A pulsed source off the tile centre leaks into the neighbouring tiles;
+    both refines move the candidate from the centre towards it."""
+    w = 8
+    x = synth.periodic_tile_stack(40, 48, 48, w, 4, 1, (2, 2), 0.0, seed=3, noise=0.3)
+    x[np.arange(40) % 4 == 1, 20:26, 21:29] += 6.0     # straddles tiles (2, 2) and (2, 3)
+    for refine in ("parabolic", "cubic"):
+        det = O.detect(x, w, 4.0, O.BRANCH_FREQ, refine=refine)
+        c = [c for c in det.candidates if (c.y // w, c.x // w) == (2, 2) or (c.y // w, c.x // w) == (2, 3)]
+        assert c, refine
+        assert c[0].xf != c[0].x

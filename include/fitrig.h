@@ -99,8 +99,18 @@ enum {
   FITRIG_OPT_MAX_SELECTED = 11, /* selected-tile capacity of one detect; 0 = default   */
   FITRIG_OPT_GRAPH = 12,      /* 1 (default): replay repeated detects from a graph     */
   FITRIG_OPT_ACCUMULATE = 13, /* K >= 1: each K pushed snapshots are summed into one   */
-  FITRIG_OPT_HARMONICS = 14   /* m_max of the frequency branch's harmonic sum (1..32)  */
+  FITRIG_OPT_HARMONICS = 14,  /* m_max of the frequency branch's harmonic sum (1..32)  */
+  FITRIG_OPT_REFINE = 15      /* FITRIG_REFINE_PARABOLIC (default) | FITRIG_REFINE_CUBIC */
 };
+/* REFINE: the sub-tile position (xf, yf) of a frequency candidate.  Sec. 2.4.2
+ * and Sec. 3.3 interpolate the eta map (spline, bicubic or Makima) without a
+ * formula.  PARABOLIC (default): per axis, the vertex of the parabola through
+ * the peak tile's eta and its two neighbours.  CUBIC: per axis, the maximum of
+ * the Catmull-Rom cubic spline through the peak tile and two neighbours on
+ * each side (a missing outer sample extended linearly), within half a tile;
+ * ties keep, in order, the centre, the right side, the left side.  Settable at
+ * any time; EINVAL for other values. */
+enum { FITRIG_REFINE_PARABOLIC = 0, FITRIG_REFINE_CUBIC = 1 };
 /* HARMONICS (Sec. 2.4.2 names harmonic summing as a choice of the spectral
  * function h; Sec. 3.3 applies it to the real data; the paper gives no
  * formula): with m_max > 1 (a power of two <= 32) eta_t is the largest
@@ -172,7 +182,7 @@ FITRIG_API int fitrig_plan_create(int nx, int ny, int nsnap, int window, double 
 
 /* fitrig_plan_set -- set an option (see the enum).  STORAGE, NOISE, RMODE,
  * EDGE, STRIDE and AUTOTUNE are accepted only before the first push (ESTATE
- * after); STREAM, TIMEOUT_NS, MAX_SELECTED, GRAPH and HARMONICS at any time.
+ * after); STREAM, TIMEOUT_NS, MAX_SELECTED, GRAPH, HARMONICS and REFINE at any time.
  * EINVAL for an unknown option or value. */
 FITRIG_API int fitrig_plan_set(fitrig_plan_t plan, int option, int64_t value);
 

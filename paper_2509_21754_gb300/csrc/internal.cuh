@@ -296,6 +296,7 @@ struct CandArgs {
   // freq branch
   const float* eta;
   const int* bin;
+  int refine;          // FITRIG_REFINE_PARABOLIC or FITRIG_REFINE_CUBIC
   // significance z = (v - cs[2g]) * inv[g] in FP64 (per group g)
   const double* cs;
   const double* inv;

@@ -466,6 +466,65 @@ __device__ __forceinline__ float parabola(float l, float c, float r) {
   return fminf(0.5f, fmaxf(-0.5f, d));
 }
 
+// Peak offset within [-0.5, 0.5] of the Catmull-Rom cubic spline through the
+// samples at -2..2 (m2, m1, c, p1, p2) along one axis of the eta map.  On the
+// segment from a (at 0) to b (at 1) with outer neighbours z (at -1) and d (at
+// 2):  f(t) = a + t (k1 + t (k2 + t k3)),  k1 = (b - z)/2,
+// k2 = (2z - 5a + 4b - d)/2,  k3 = (-z + 3a - 3b + d)/2.  Candidates in order:
+// offset 0; the right segment's interior roots of f' (ascending), then +0.5;
+// the left segment's (t in [0.5, 1], offset t - 1) roots, then -0.5; strictly
+// larger values win.  A missing neighbour at +-1 leaves its side unsearched;
+// a missing outer sample is extended linearly.  Roots of f' come from the
+// cancellation-free form of the quadratic formula.
+__device__ __forceinline__ float cubic_offset(float m2, float m1, float c, float p1, float p2) {
+  if (!isfinite(c)) return 0.f;
+  float bx = 0.f, bf = c;
+  auto segment = [&](float z, float a, float b, float d, float lo, float hi, float shift) {
+    const float k1 = 0.5f * (b - z);
+    const float k2 = 0.5f * (2.f * z - 5.f * a + 4.f * b - d);
+    const float k3 = 0.5f * (-z + 3.f * a - 3.f * b + d);
+    auto f = [&](float t) { return a + t * (k1 + t * (k2 + t * k3)); };
+    const float A = 3.f * k3, B = 2.f * k2, C = k1;
+    const float disc = B * B - 4.f * A * C;
+    float r0 = 0.f, r1 = 0.f;
+    int nr = 0;
+    if (disc >= 0.f) {
+      const float q = -0.5f * (B + copysignf(sqrtf(disc), B));
+      if (A != 0.f) r0 = q / A, nr = 1;
+      if (q != 0.f) {
+        if (nr == 0) r0 = C / q;
+        else r1 = C / q;
+        ++nr;
+      }
+      if (nr == 2 && r1 < r0) {
+        const float t = r0;
+        r0 = r1;
+        r1 = t;
+      }
+    }
+    if (nr >= 1 && lo < r0 && r0 < hi) {
+      const float v = f(r0);
+      if (v > bf) bf = v, bx = r0 + shift;
+    }
+    if (nr == 2 && lo < r1 && r1 < hi) {
+      const float v = f(r1);
+      if (v > bf) bf = v, bx = r1 + shift;
+    }
+    const float e = shift == 0.f ? hi : lo;
+    const float v = f(e);
+    if (v > bf) bf = v, bx = e + shift;
+  };
+  if (isfinite(p1)) {
+    const float d = isfinite(p2) ? p2 : 2.f * p1 - c;
+    segment(isfinite(m1) ? m1 : 2.f * c - p1, c, p1, d, 0.f, 0.5f, 0.f);
+  }
+  if (isfinite(m1)) {
+    const float z = isfinite(m2) ? m2 : 2.f * m1 - c;
+    segment(z, m1, c, isfinite(p1) ? p1 : 2.f * c - m1, 0.5f, 1.f, -1.f);
+  }
+  return bx;
+}
+
 // The candidate's significance, z = (v - centre) / scale in FP64 (Sec. 2.4.1,
 // 2.4.2), rounded to FP32 for the output.
 __device__ __forceinline__ float significance(const CandArgs& a, const SelItem& it) {
@@ -493,8 +552,20 @@ __global__ void k_emit_freq(CandArgs a, const SelItem* __restrict__ items, const
     c.significance = significance(a, it);
     c.branch = FITRIG_BRANCH_FREQ;
     c.freq_bin = a.bin[it.t];
-    c.xf = (float)(tx * a.w) + 0.5f * (float)(ww - 1) + parabola(el, e, er) * (float)a.w;
-    c.yf = (float)(ty * a.w) + 0.5f * (float)(hw - 1) + parabola(eu, e, ed) * (float)a.w;
+    float dx, dy;
+    if (a.refine == FITRIG_REFINE_CUBIC) {
+      const float el2 = tx > 1 ? a.eta[it.t - 2] : NAN;
+      const float er2 = tx + 2 < a.Tx ? a.eta[it.t + 2] : NAN;
+      const float eu2 = ty > 1 ? a.eta[it.t - 2 * a.Tx] : NAN;
+      const float ed2 = ty + 2 < a.Ty ? a.eta[it.t + 2 * a.Tx] : NAN;
+      dx = cubic_offset(el2, el, e, er, er2);
+      dy = cubic_offset(eu2, eu, e, ed, ed2);
+    } else {
+      dx = parabola(el, e, er);
+      dy = parabola(eu, e, ed);
+    }
+    c.xf = (float)(tx * a.w) + 0.5f * (float)(ww - 1) + dx * (float)a.w;
+    c.yf = (float)(ty * a.w) + 0.5f * (float)(hw - 1) + dy * (float)a.w;
     if (p < a.cap) a.out[p] = c;
   }
 }

@@ -72,6 +72,7 @@ struct fitrig_plan_s {
   float2* d_htw = nullptr;   // twiddles of length hist_n
   int accumulate = 1;        // raw snapshots summed into one stack snapshot
   int hmax = 1;              // harmonics of the frequency branch's h (1: max magnitude)
+  int refine = FITRIG_REFINE_PARABOLIC;   // frequency candidates' position refine
   int raw_pushed = 0;        // raw snapshots of the block being summed
   float* d_accum = nullptr;  // [ny][nx] FP32 running sum (accumulate > 1)
   int64_t max_selected = 0;  // 0: automatic selection capacity
@@ -564,6 +565,11 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t p, int option, int64_t value) {
       p->timeout_ns = (uint64_t)value;
       drop_graph(p);   // the captured kernels carry the old bound
       return FITRIG_OK;
+    case FITRIG_OPT_REFINE:
+      if (value != FITRIG_REFINE_PARABOLIC && value != FITRIG_REFINE_CUBIC) return FITRIG_EINVAL;
+      if (p->refine != (int)value) drop_graph(p);
+      p->refine = (int)value;
+      return FITRIG_OK;
     case FITRIG_OPT_HARMONICS:
       if (value < 1 || value > 32 || (value & (value - 1))) return FITRIG_EINVAL;
       if (p->hmax != (int)value) drop_graph(p);
@@ -900,6 +906,7 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
   ca.zmod = p->ring ? p->L : 0;
   ca.eta = p->d_eta;
   ca.bin = p->d_bin;
+  ca.refine = p->refine;
   ca.out = p->d_cand;
   ca.nout = nout;
   ca.cap = p->cand_cap;

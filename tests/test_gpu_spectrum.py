@@ -105,3 +105,28 @@ def test_series_length_limit():
     assert e.value.status == F.EUNSUPPORTED
     h = F.fitrig_plan_create(16, 16, 5000, 4, 4.0, F.BRANCH_IMAGE)   # image branch: no limit
     F.fitrig_plan_destroy(h)
+
+
+@pytest.mark.parametrize("refine", ["parabolic", "cubic"])
+@pytest.mark.parametrize("seed", [3, 4])
+def test_refined_positions_follow_the_oracle(refine, seed):
+    """Frequency candidates' sub-tile positions (parabola or spline through the
+    eta map) within 0.05 tiles of the oracle's: a pulsed source that straddles
+    two tiles, one at the map edge and one off-centre inside a tile."""
+    w = 8
+    code = {"parabolic": F.REFINE_PARABOLIC, "cubic": F.REFINE_CUBIC}[refine]
+    x = synth.periodic_tile_stack(42, 128, 128, w, 4, 1, (2, 2), 0.0, seed=seed, noise=0.3)
+    x[np.arange(42) % 4 == 1, 44:50, 60:70] += 6.0
+    x[np.arange(42) % 4 == 2, 2:8, 121:127] += 5.0
+    x[np.arange(42) % 5 == 0, 90:97, 33:36] += 6.0
+    res = F.detect_stack(torch.from_numpy(x).cuda(), w, 4.0, F.BRANCH_FREQ, refine=code)
+    det = O.detect(x, w, 4.0, F.BRANCH_FREQ, refine=refine)
+    di, dfq = F.decisions(res, 4.0)
+    errs = C.compare(res["candidates"], x, w, 4.0, F.BRANCH_FREQ, decide_image=di,
+                     decide_freq=dfq, det=det, refine=refine)
+    assert not errs, errs[:10]
+    assert len(res["candidates"]) >= 3
+    with F.Plan(128, 128, 42, w, 4.0, F.BRANCH_FREQ) as p:
+        with pytest.raises(F.FitrigError) as e:
+            F.fitrig_plan_set(p.h, F.OPT_REFINE, 2)
+        assert e.value.status == F.EINVAL

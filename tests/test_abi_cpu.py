@@ -100,3 +100,22 @@ def test_binding_raises_on_errors(lib):
     with pytest.raises(F.FitrigError) as e:
         F.fitrig_plan_create(0, 10, 5, 2, 3.0)
     assert e.value.status == F.EINVAL
+
+
+def test_new_entry_points_check_their_arguments_without_a_device(lib):
+    """The block push and the caller-buffer candidates reject bad arguments
+    before any device call."""
+    import numpy as np
+    from paper_2509_21754_gb300 import fitrig as F
+    L = F.load()
+    assert L.fitrig_push_snapshots(None, None, 1, F.F32, 0, 0, 0) == F.EINVAL
+    buf = np.zeros((2, 4, 4), np.float32)
+    assert L.fitrig_push_snapshots(None, ctypes.c_void_p(buf.ctypes.data), 2, F.F32, 0, 0, 0) == F.EINVAL
+    with pytest.raises(F.FitrigError) as e:
+        F.fitrig_push_snapshots(None, np.zeros((4, 4), np.float32))   # not a block
+    assert e.value.status == F.EINVAL
+    with pytest.raises(F.FitrigError) as e:
+        F.fitrig_candidates(None, out=np.zeros(4, np.float32))         # wrong record type
+    assert e.value.status == F.EINVAL
+    assert L.fitrig_plan_set(None, F.OPT_HARMONICS, 8) == F.EINVAL
+    assert L.fitrig_plan_set(None, F.OPT_REFINE, F.REFINE_CUBIC) == F.EINVAL

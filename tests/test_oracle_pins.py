@@ -701,3 +701,19 @@ def test_cubic_refine_moves_a_freq_candidate_towards_the_source():
         c = [c for c in det.candidates if (c.y // w, c.x // w) == (2, 2) or (c.y // w, c.x // w) == (2, 3)]
         assert c, refine
         assert c[0].xf != c[0].x
+
+
+@pytest.mark.parametrize("harmonics,refine", [(4, "parabolic"), (8, "cubic"), (1, "cubic")])
+def test_freq_window_matches_the_batch_branch_with_harmonics_and_refine(harmonics, refine):
+    """The real-time window over every unit equals the batch frequency branch
+    for the harmonic sum and the spline refine too (same eta, bins, candidate
+    positions)."""
+    x = synth.periodic_tile_stack(34, 40, 43, 4, 4, 1, (2, 3), 6.0, seed=37)
+    x[0, 0, 0] = 10.0 * np.abs(x).max()
+    cands, eta, kbin, z = O.freq_window(x, 4, 4.0, 32, "meanstd", harmonics=harmonics,
+                                        refine=refine)
+    det = O.detect(x, 4, 4.0, O.BRANCH_FREQ, "meanstd", harmonics=harmonics, refine=refine)
+    assert np.array_equal(eta, det.eta) and np.array_equal(kbin, det.eta_bin)
+    assert [(c.y, c.x, c.freq_bin, c.xf, c.yf) for c in cands] == \
+        [(c.y, c.x, c.freq_bin, c.xf, c.yf) for c in det.candidates]
+    assert cands

@@ -64,7 +64,7 @@ def parse():
                          "at a time; about 90 GB of device memory with FP32 storage)")
     ap.add_argument("--accumulate", type=int, default=0,
                     help="also time ingest with snapshot accumulation: K raw device "
-                         "snapshots summed per stack snapshot (Sec. 4.3.2)")
+                         "snapshots summed per stack snapshot (Sec. 3.3.2)")
     return ap.parse_args()
 
 
@@ -443,11 +443,11 @@ def large_run(a, F, synth, torch, storage, steps=5, seed=3030):
 
 
 # ---------------------------------------------------------------- the paper's end-to-end run
-PAPER_H100_S = 6.34   # Sec. 3.3: 1500 snapshots of 4096^2, image loading to pulsar position
+PAPER_H100_S = 6.34   # Sec. 3 (real-data evaluation): 1500 snapshots of 4096^2, image loading to pulsar position
 
 
 def paper_run(a, F, synth, torch, steps=3, seed=4040, ring=64):
-    """The configuration of the paper's end-to-end timing (Sec. 3.3): 1500
+    """The configuration of the paper's end-to-end timing (the real-data evaluation of Sec. 3): 1500
     snapshots of 4096 x 4096 (MeerKAT-like PSF, the 64-snapshot workload's
     source rules), image-frequency branch with harmonic summing (m_max = 8),
     window 32, 6 sigma, mean/std noise, FP32.  Device leg: detects over the
@@ -519,7 +519,7 @@ def paper_run(a, F, synth, torch, steps=3, seed=4040, ring=64):
 
 # ---------------------------------------------------------------- accumulation leg
 def accumulate_run(a, F, torch, stack, storage, reps=3):
-    """Ingest with snapshot accumulation (Sec. 4.3.2): K raw device snapshots
+    """Ingest with snapshot accumulation (Sec. 3.3.2): K raw device snapshots
     (the stack's snapshots, cycled) pushed per stack snapshot, then a detect.
     Bytes per raw push: read the raw snapshot, read and write the FP32 sum
     (the first push of a block only writes it, the last writes the stack)."""

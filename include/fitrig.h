@@ -103,7 +103,7 @@ enum {
   FITRIG_OPT_REFINE = 15      /* FITRIG_REFINE_PARABOLIC (default) | FITRIG_REFINE_CUBIC */
 };
 /* REFINE: the sub-tile position (xf, yf) of a frequency candidate.  Sec. 2.4.2
- * and Sec. 3.3 interpolate the eta map (spline, bicubic or Makima) without a
+ * and the real-data evaluation of Sec. 3 interpolate the eta map (spline, bicubic or Makima) without a
  * formula.  PARABOLIC (default): per axis, the vertex of the parabola through
  * the peak tile's eta and its two neighbours.  CUBIC: per axis, the maximum of
  * the Catmull-Rom cubic spline through the peak tile and two neighbours on
@@ -112,14 +112,14 @@ enum {
  * any time; EINVAL for other values. */
 enum { FITRIG_REFINE_PARABOLIC = 0, FITRIG_REFINE_CUBIC = 1 };
 /* HARMONICS (Sec. 2.4.2 names harmonic summing as a choice of the spectral
- * function h; Sec. 3.3 applies it to the real data; the paper gives no
+ * function h; the real-data evaluation of Sec. 3 applies it to the real data; the paper gives no
  * formula): with m_max > 1 (a power of two <= 32) eta_t is the largest
  * incoherent harmonic sum (|X_k| + |X_2k| + .. + |X_mk|) / sqrt(m) over
  * m = 1, 2, 4, .., m_max and the fundamentals k with m k <= floor(n/2), and
  * the reported bin is that k (ties: smaller m, then smaller k).  1 (the
  * default) is the maximum magnitude of Sec. 3.4.3.  Settable at any time;
  * EINVAL for other values. */
-/* ACCUMULATE (Sec. 4.3.2, Fig. "Snapshots accumulation"): with sampling
+/* ACCUMULATE (Sec. 3.3.2, Fig. "Snapshots accumulation"): with sampling
  * periods so short that adjacent snapshots are nearly identical, the trigger
  * runs on sums of adjacent snapshots.  With K > 1 every fitrig_push_snapshot
  * adds one raw snapshot to a running FP32 sum on the device (raw snapshots
@@ -314,8 +314,11 @@ FITRIG_API int fitrig_threshold_map(const float* dev_map, int64_t n, double nsig
  * FITRIG_NOISE_STATIC_MAX_GROUPS (EINVAL beyond it) and n to INT32_MAX.
  * Every call shares that array: calls that overlap on the GPU (for example on
  * two streams at once) race and must not be issued.  The first call on a
- * device looks up the array's device address; make that first call before
- * any stream capture.
+ * device looks up the array's device address, and so does the first call
+ * after the device's context was destroyed and created again (a device
+ * reset); make such a call before any stream capture.  Each map is read by
+ * 608 / groups blocks (at least one): with many groups, large maps are read
+ * by few blocks, which is correct but slow.
  */
 #define FITRIG_NOISE_STATIC_MAX_GROUPS 64
 FITRIG_API int fitrig_noise_static(const float* dev_values, int32_t groups, int64_t n,

@@ -36,33 +36,58 @@ def _near_peak(comp, z, tol):
     return {p for p in comp if z[p] >= zmax - tol * max(1.0, abs(zmax))}
 
 
-def _pixel_ok(stack: np.ndarray, s: int, y: int, x: int, ty: int, tx: int, w: int,
-              nyu: int, nxu: int, rmode: str) -> bool:
-    y0, x0 = ty * w, tx * w
-    y1, x1 = min(y0 + w, nyu), min(x0 + w, nxu)
-    if not (y0 <= y < y1 and x0 <= x < x1):
-        return False
-    a, b, c = (np.asarray(stack[s + i, y0:y1, x0:x1], dtype=np.float64) for i in range(3))
-    d, _, _ = O.unit_terms(a, b, c, rmode)
-    bound = 8 * U32 * (np.abs(a) + 2 * np.abs(b) + np.abs(c)).max() + 1e-300
-    return d[y - y0, x - x0] >= d.max() - bound
+def _pixels_ok(stack: np.ndarray, s: np.ndarray, y: np.ndarray, x: np.ndarray,
+               ty: np.ndarray, tx: np.ndarray, w: int, nyu: int, nxu: int, rmode: str,
+               chunk: int = 65536) -> np.ndarray:
+    """For each image candidate (unit s, pixel (y, x), peak tile (ty, tx)):
+    whether the pixel lies in the tile and its oracle Delta is within the FP32
+    rounding bound of the tile's maximum Delta (so near ties may pick either
+    pixel).  Vectorised over candidates; ragged edge tiles are masked."""
+    n = len(s)
+    ok = np.zeros(n, dtype=bool)
+    off = np.arange(w)
+    for i0 in range(0, n, chunk):
+        sl = slice(i0, min(n, i0 + chunk))
+        ss, yy, xx, tyy, txx = s[sl], y[sl], x[sl], ty[sl], tx[sl]
+        rows = tyy[:, None] * w + off[None, :]                  # (m, w)
+        cols = txx[:, None] * w + off[None, :]
+        inside = (rows[:, :, None] < nyu) & (cols[:, None, :] < nxu)
+        rc = np.minimum(rows, nyu - 1)
+        cc = np.minimum(cols, nxu - 1)
+        a, b, c = (np.asarray(stack[(ss + k)[:, None, None], rc[:, :, None], cc[:, None, :]],
+                              dtype=np.float64) for k in range(3))
+        d, _, _ = O.unit_terms(a, b, c, rmode)
+        d = np.where(inside, d, -np.inf)
+        mag = np.where(inside, np.abs(a) + 2 * np.abs(b) + np.abs(c), 0.0)
+        bound = 8 * U32 * mag.reshape(len(ss), -1).max(axis=1) + 1e-300
+        dmax = d.reshape(len(ss), -1).max(axis=1)
+        iy, ix = yy - tyy * w, xx - txx * w
+        inr = (iy >= 0) & (iy < w) & (ix >= 0) & (ix < w) & (yy < nyu) & (xx < nxu)
+        m = np.arange(len(ss))
+        dv = d[m, np.clip(iy, 0, w - 1), np.clip(ix, 0, w - 1)]
+        ok[sl] = inr & (dv >= dmax - bound)
+    return ok
 
 
 def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: int,
             noise: str = "meanstd", rmode: str = "abs", edge: str = "partial",
             decide_image: Optional[Callable[[int, int, int], bool]] = None,
             decide_freq: Optional[Callable[[int, int], bool]] = None,
-            det: Optional[O.Detection] = None, pixel_sample: Optional[int] = None,
-            harmonics: int = 1, refine: str = "parabolic") -> List[str]:
+            det: Optional[O.Detection] = None,
+            harmonics: int = 1, refine: str = "parabolic",
+            cut_top: bool = False, cut_bottom: bool = False) -> List[str]:
     """Return a list of parity violations (empty when the lists agree).
 
     ``harmonics`` is m_max of the frequency branch's h (1: maximum magnitude);
     a frequency candidate's bin must then be a fundamental whose best harmonic
-    sum is within the tolerance of the tile's largest.
+    sum is within the tolerance of the tile's largest.  Every candidate is
+    checked, including the arg-max pixel of every image candidate.
 
-    ``pixel_sample`` limits the arg-max pixel check (which reads the stack) to
-    that many randomly chosen image candidates; everything else is checked for
-    every candidate.
+    ``cut_top`` / ``cut_bottom`` say that ``stack`` is a strip of whole tile
+    rows cut out of a larger field at its first / last tile row: components
+    that touch a cut row may continue beyond the strip, so they and the
+    candidates inside them are skipped; every other component and candidate
+    is checked as usual.
     """
     errs: List[str] = []
     L, ny, nx = stack.shape
@@ -72,7 +97,8 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
                        refine=refine)
     band = REL_TOL * tau
     names = cands.dtype.names
-    got = [dict(zip(names, c)) for c in cands]
+    cols = {k: cands[k].tolist() for k in names}
+    got = [dict(zip(names, row)) for row in zip(*(cols[k] for k in names))]
 
     def check_groups(groups, branch_id):
         # groups: list of (label, z_map, comps, snapshot)
@@ -87,6 +113,10 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
         for label, zmap, comps, snap in groups:
             for comp in comps:
                 hits = [by_tile[(snap,) + t] for t in comp if (snap,) + t in by_tile]
+                if any((cut_top and t[0] == 0) or (cut_bottom and t[0] == Ty - 1)
+                       for t in comp):
+                    used.update(hits)   # may continue beyond the strip
+                    continue
                 if len(hits) != 1:
                     errs.append(f"{label}: oracle component at {sorted(comp)[:4]} has "
                                 f"{len(hits)} candidates")
@@ -121,12 +151,12 @@ def compare(cands: np.ndarray, stack: np.ndarray, w: int, tau: float, branch: in
                     mask[ty, tx] = bool(decide_image(s, int(ty), int(tx)))
             groups.append((f"unit {s}", z, O.components(mask), s))
         matched = list(check_groups(groups, O.BRANCH_IMAGE))
-        if pixel_sample is not None and len(matched) > pixel_sample:
-            rng = np.random.default_rng(12345)
-            pick = rng.choice(len(matched), pixel_sample, replace=False)
-            matched = [matched[i] for i in sorted(pick)]
-        for gc, (ty, tx), s in matched:
-            if not _pixel_ok(stack, s, int(gc["y"]), int(gc["x"]), ty, tx, w, nyu, nxu, rmode):
+        if matched:
+            arr = lambda f: np.array([f(m) for m in matched], dtype=np.int64)
+            ok = _pixels_ok(stack, arr(lambda m: m[2]), arr(lambda m: int(m[0]["y"])),
+                            arr(lambda m: int(m[0]["x"])), arr(lambda m: m[1][0]),
+                            arr(lambda m: m[1][1]), w, nyu, nxu, rmode)
+            for (gc, _, s) in (matched[i] for i in np.nonzero(~ok)[0]):
                 errs.append(f"unit {s}: pixel {(gc['y'], gc['x'])} is not an arg-max of Delta")
 
     if branch & O.BRANCH_FREQ:
@@ -191,3 +221,19 @@ def values_close(gpu: np.ndarray, ref: np.ndarray, rel: float = 1e-5,
     ok = bool(np.all(err <= rel * np.abs(r[m]) + abs_scale * scale))
     worst = float(np.max(err / (np.abs(r[m]) + abs_scale * scale + 1e-300)))
     return ok, worst
+
+
+def library_decisions(res: dict, tau: float):
+    """Threshold decisions of the implementation under test, from its dumped
+    tile values and noise parameters (centre, scale): a tile is selected when
+    (double)v > centre + tau * scale.  Used only for the ambiguous tiles of
+    ``compare`` (those whose oracle z lies within the tolerance band of tau).
+    Returns (image(s, ty, tx), freq(ty, tx))."""
+    def image(s, ty, tx):
+        c, sc = res["noise"][s]
+        return sc > 0 and float(res["values"][s, ty, tx]) > c + tau * sc
+
+    def freq(ty, tx):
+        c, sc = res["eta_noise"]
+        return sc > 0 and float(res["eta"][ty, tx]) > c + tau * sc
+    return image, freq

@@ -19,7 +19,7 @@ Paper sections used (arXiv 2509.21754, "FITrig"):
 * Sec. 2.4.2 (image-frequency detection): the tLISI cube, Eq. (eta) with h =
   maximum spectral magnitude (the paper's own conservative choice in Sec. 3.4.3),
   the z-score of eta and the selected set.  h may instead be an incoherent
-  harmonic sum (Sec. 2.4.2 names harmonic summing as a choice of h and Sec. 3.3
+  harmonic sum (Sec. 2.4.2 names harmonic summing as a choice of h and the real-data evaluation of Sec. 3
   applies it to the real data, without defining it; see ``harmonic_sum``).
 
 Readings where the paper is silent or ambiguous (each is an option here):
@@ -47,14 +47,14 @@ Readings where the paper is silent or ambiguous (each is an option here):
   m = 1, 2, 4, .., m_max and over the k with m k <= floor(n/2); m_max = 1 is
   the maximum magnitude.  The bin reported is the fundamental k.  Ties go to
   the smaller m, then the smaller k.
-* the spline interpolation of eta (Sec. 2.4.2, Sec. 3.3; parity with the paper
+* the spline interpolation of eta (Sec. 2.4.2 and the real-data evaluation of Sec. 3; parity with the paper
   unpinned, no formula given): per axis, the Catmull-Rom cubic through the
   peak tile's eta and two neighbours on each side, maximised within half a
   tile (``cubic_offset``); the default refine is the three-point parabola.
 * a sliding-window mode (not in the paper, whose tiles partition the image)
   evaluates the tile statistic over the odd w x w window centred on each pixel,
   clipped at the border, and then treats pixels as 1 x 1 tiles.
-* snapshot accumulation (Sec. 4.3.2): the paper sums adjacent snapshots
+* snapshot accumulation (Sec. 3.3.2): the paper sums adjacent snapshots
   "progressively until there is enough difference" without a criterion; the
   reading here sums fixed, non-overlapping blocks of K consecutive snapshots.
 
@@ -77,7 +77,7 @@ BRANCH_BOTH = 3
 
 
 # --------------------------------------------------------------------------
-# Snapshot accumulation (Sec. 4.3.2, Fig. "Snapshots accumulation")
+# Snapshot accumulation (Sec. 3.3.2, Fig. "Snapshots accumulation")
 # --------------------------------------------------------------------------
 def accumulate(raw: np.ndarray, k: int) -> np.ndarray:
     """Stack of sums of K consecutive raw snapshots: snapshot j of the result
@@ -463,7 +463,7 @@ def parabolic_offset(left: float, centre: float, right: float) -> float:
 def cubic_offset(m2: float, m1: float, c: float, p1: float, p2: float) -> float:
     """Peak offset (in grid steps, within [-0.5, 0.5]) of the Catmull-Rom cubic
     spline through the samples at -2, -1, 0, +1, +2 (the "spline
-    interpolation" of eta, Sec. 2.4.2 and Sec. 3.3; our reading).
+    interpolation" of eta, Sec. 2.4.2 and the real-data evaluation of Sec. 3; our reading).
 
     On the segment between samples a (at 0) and b (at 1) with outer neighbours
     z (at -1) and d (at 2) the spline is

@@ -575,7 +575,7 @@ static dim3 image_grid(int ny, int nx) {
   return dim3((unsigned)std::min(8, (nx + 255) / 256), (unsigned)std::min(ny, 4096));
 }
 
-// Snapshot accumulation (Sec. 4.3.2): acc = x (first raw snapshot of a
+// Snapshot accumulation (Sec. 3.3.2): acc = x (first raw snapshot of a
 // block) or acc + x in FP32; the last raw snapshot of the block stores the
 // sum, in the storage type, to the stack slot instead.
 __global__ void k_accumulate(const void* src, int st, int64_t sp, float* acc, int first, int last,

@@ -13,9 +13,12 @@
 // exits.  Every call on a device shares it and it keeps the last call's
 // contents, so each call clears what must start at zero; calls that overlap
 // on the GPU (e.g. on two streams at once) race on it and must not be issued.
-// The first call on a device looks up the array's device address (a host-side
-// symbol is only a stand-in for it); make that first call before any stream
-// capture.
+// The first call on a device (and the first after a device reset) looks up
+// the array's device address (a host-side symbol is only a stand-in for it);
+// make that first call before any stream capture.  Each map is split over
+// 608 / groups blocks (at least one), so a call with many groups reads each
+// map with few blocks: correct, but far below the memory bandwidth for large
+// maps.
 #include <mutex>
 
 #include "internal.cuh"
@@ -42,24 +45,73 @@ constexpr size_t kScratchBytes = kOffShift + ((kMaxGroups * 4 + 255) / 256) * 25
 __device__ __align__(256) static unsigned char g_noise_scratch[kScratchBytes];
 
 std::mutex g_setup_mutex;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once).
+// The cached address belongs to one CUDA context: a device reset (or the
+// primary context being released and created again) reloads the module, and
+// the array may then sit elsewhere.  Each device's entry therefore records
+// the unique ID of the context it was looked up in (cuCtxGetId, never reused
+// within a process) and is looked up again when the current context differs.
+struct ScratchEntry {
+  unsigned long long ctx_id = 0;
+  bool valid = false;
+  unsigned char* addr = nullptr;
+};
+ScratchEntry g_scratch[kMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+template <typename Fn>
+Fn driver_fn(const char* name, int version) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, version, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return reinterpret_cast<Fn>(p);
+}
+
+// Unique ID of the calling thread's current context on device `dev`
+// (cudaSetDevice makes the device's primary context current and initialises
+// it; it allocates nothing).
+int current_context_id(int dev, unsigned long long* id) {
+  static CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent", 3020);
+  static CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId", 12000);
+  if (!get_current || !get_id) return FITRIG_EUNSUPPORTED;
+  if (cudaSetDevice(dev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return FITRIG_ECUDA;
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return FITRIG_ECUDA;
+  return get_id(ctx, id) == CUDA_SUCCESS ? FITRIG_OK : FITRIG_ECUDA;
+}
+
+// Device address of the scratch array in the current device's current
+// context (looked up once per context).
 int scratch_address(unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FITRIG_ECUDA;
   if (dev < 0 || dev >= kMaxDevices) return FITRIG_EUNSUPPORTED;
+  unsigned long long ctx = 0;
+  const int rc = current_context_id(dev, &ctx);
+  if (rc != FITRIG_OK) return rc;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
+  ScratchEntry& e = g_scratch[dev];
+  if (!e.valid || e.ctx_id != ctx) {
     void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noise_scratch);
-    if (e != cudaSuccess || !p) {
+    const cudaError_t err = cudaGetSymbolAddress(&p, g_noise_scratch);
+    if (err != cudaSuccess || !p) {
       (void)cudaGetLastError();
       return FITRIG_ECUDA;
     }
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    e.addr = static_cast<unsigned char*>(p);
+    e.ctx_id = ctx;
+    e.valid = true;
   }
-  *out = g_scratch_addr[dev];
+  *out = e.addr;
   return FITRIG_OK;
 }
 

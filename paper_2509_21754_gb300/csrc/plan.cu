@@ -702,7 +702,7 @@ static int push_one(fitrig_plan_t p, const void* data, int dtype, int on_device,
   const int eb = elem_bytes(p->storage), ib = elem_bytes(dtype);
   char* dst = p->d_stack + p->slice_bytes * p->pushed;
   if (p->accumulate > 1) {
-    // Sec. 4.3.2: K raw snapshots summed (FP32, push order) into one
+    // Sec. 3.3.2: K raw snapshots summed (FP32, push order) into one
     const void* src = data;
     int64_t sp = rp;
     if (!on_device) {

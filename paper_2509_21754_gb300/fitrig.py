@@ -580,15 +580,3 @@ def detect_stack(stack, window: int, nsigma: float, branch: int = BRANCH_IMAGE,
                 out["eta_noise"] = fitrig_noise_params(p.h, -1)
             out["kernel_ms"] = {k: fitrig_kernel_ms(p.h, k) for k in range(5)}
         return out
-
-
-def decisions(res: dict, nsigma: float):
-    """The library's own threshold decisions, (double)v > centre + tau * scale."""
-    def image(s, ty, tx):
-        c, sc = res["noise"][s]
-        return sc > 0 and float(res["values"][s, ty, tx]) > c + nsigma * sc
-
-    def freq(ty, tx):
-        c, sc = res["eta_noise"]
-        return sc > 0 and float(res["eta"][ty, tx]) > c + nsigma * sc
-    return image, freq

@@ -86,7 +86,7 @@ def test_batch_field_against_oracle():
                "noise": np.array([F.fitrig_noise_params(p.h, s) for s in range(x.shape[0] - 2)])}
         res["eta"], res["bin"] = F.fitrig_spectrum(p.h)
         res["eta_noise"] = F.fitrig_noise_params(p.h, -1)
-        di, dfq = F.decisions(res, 4.0)
+        di, dfq = C.library_decisions(res, 4.0)
         errs = C.compare(F.fitrig_candidates(p.h, int(n[k])), x, 5, 4.0, O.BRANCH_BOTH,
                          decide_image=di, decide_freq=dfq, det=det)
         assert not errs, errs[:8]

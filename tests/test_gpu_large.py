@@ -2,8 +2,16 @@
 branches, median/MAD noise, with FP32 storage (80 GB) and with BF16 / FP16
 storage (40 GB) plus FP32 accumulation.
 
-* parity: the tile statistic on sampled tiles equals the oracle's on the values
-  as stored (half storage rounds on ingest);
+* parity of the tile statistic on sampled tiles against the oracle on the
+  values as stored (half storage rounds on ingest);
+* candidate parity on three whole-width strips of 32 tile rows (the top edge,
+  the middle and the bottom edge of the field): the oracle computes every tile
+  statistic of the strip and its eta in FP64 from the stored pixels, takes the
+  z-scores with the library's noise parameters of the whole field (those are
+  bit-exact order statistics of the library's own values, checked in
+  test_gpu_noise.py and test_gpu_fullsize.py), selects, forms components and
+  candidates, and the library's candidates in the strip must match by the
+  parity rule; components cut by a strip edge are skipped;
 * accuracy: the error of each storage type against the FP64 oracle on the FP32
   originals, per statistic (tile statistic v, tLISI, eta), max and 99th
   percentile; with FITRIG_REPORT=<path> the numbers are written as JSON.
@@ -32,6 +40,8 @@ from paper_2509_21754_gb300 import synth  # noqa: E402
 
 W, TAU, SEED = 5, 6.0, 3030
 SPEC = synth.C3
+TY = -(-SPEC.ny // W)
+STRIPS = ((0, 32), (TY // 2 - 16, TY // 2 + 16), (TY - 32, TY))   # tile rows [a, b)
 STORES = {"f32": (F.F32, torch.float32), "bf16": (F.BF16, torch.bfloat16),
           "f16": (F.F16, torch.float16)}
 
@@ -46,35 +56,67 @@ def sample_tiles():
     return sorted(tiles)
 
 
+def stored(x: np.ndarray, tdt) -> np.ndarray:
+    """The values the plan holds for FP32 input x (round to nearest even)."""
+    if tdt == torch.float32:
+        return x
+    return torch.from_numpy(x).to(tdt).float().numpy()
+
+
 def run(storage_name, tiles):
     code, tdt = STORES[storage_name]
     L, ny, nx = SPEC.nsnap, SPEC.ny, SPEC.nx
     crops = [[] for _ in tiles]
+    strips = [[] for _ in STRIPS]
     with F.Plan(nx, ny, L, W, TAU, F.BRANCH_BOTH, code, F.NOISE_MEDMAD) as p:
         for k, snap in synth.iter_stack(SPEC, SEED, "cuda"):
             for j, (ty, tx) in enumerate(tiles):
                 crops[j].append(snap[ty * W:ty * W + W, tx * W:tx * W + W].cpu().numpy())
+            for j, (a, b) in enumerate(STRIPS):
+                strips[j].append(snap[a * W:b * W].cpu().numpy())
             F.fitrig_push_snapshot(p.h, snap)   # FP32 in, converted to the storage type
             del snap
         torch.cuda.synchronize()
         rc, n = F.fitrig_detect(p.h)   # the selection lists grow as needed
         ms = F.fitrig_kernel_ms(p.h, F.KERNEL_DETECT)
         stack_ms = F.fitrig_kernel_ms(p.h, F.KERNEL_STACK)
-        vals = np.stack([F.fitrig_unit_values(p.h, s)[[t[0] for t in tiles], [t[1] for t in tiles]]
-                         for s in range(L - 2)])
+        cands = F.fitrig_candidates(p.h, n)
+        rows = [t[0] for t in tiles]
+        cols = [t[1] for t in tiles]
+        vals, strip_vals = [], [[] for _ in STRIPS]
+        for s in range(L - 2):
+            full = F.fitrig_unit_values(p.h, s)
+            vals.append(full[rows, cols])
+            for j, (a, b) in enumerate(STRIPS):
+                strip_vals[j].append(full[a:b].copy())
+            del full
         noise = np.array([F.fitrig_noise_params(p.h, s) for s in range(L - 2)])
-        eta, _ = F.fitrig_spectrum(p.h)
-        eta = eta[[t[0] for t in tiles], [t[1] for t in tiles]]
+        eta_full, _ = F.fitrig_spectrum(p.h)
+        eta = eta_full[rows, cols]
+        strip_eta = [eta_full[a:b].copy() for (a, b) in STRIPS]
+        del eta_full
+        eta_noise = F.fitrig_noise_params(p.h, -1)
         M = F.fitrig_global_max(p.h)
-    return dict(rc=rc, ncand=n, ms=ms, stack_ms=stack_ms, vals=vals, noise=noise, eta=eta, M=M,
-                crops=[np.stack(c) for c in crops])
+    # the library's candidates inside each strip, in strip coordinates
+    ty_c = cands["y"] // W
+    strip_cands = []
+    for (a, b) in STRIPS:
+        c = cands[(ty_c >= a) & (ty_c < b)].copy()
+        c["y"] -= a * W
+        c["yf"] -= a * W
+        strip_cands.append(c)
+    return dict(rc=rc, ncand=n, ms=ms, stack_ms=stack_ms, vals=np.stack(vals), noise=noise,
+                eta=eta, eta_noise=eta_noise, M=M, crops=[np.stack(c) for c in crops],
+                strips=[np.stack(s) for s in strips],
+                strip_vals=[np.stack(v) for v in strip_vals], strip_eta=strip_eta,
+                strip_cands=strip_cands)
 
 
 def oracle_on(crops, tiles, quant=None):
     """Oracle tile statistics of the sampled tiles (each crop is one tile)."""
     out = np.zeros((SPEC.nsnap - 2, len(tiles)))
     for j, c in enumerate(crops):
-        x = c if quant is None else torch.from_numpy(c).to(quant).float().numpy()
+        x = c if quant is None else stored(c, quant)
         out[:, j] = O.sampled_tiles(x, W, [(0, 0)])["numerator"][:, 0]
     return out
 
@@ -99,6 +141,37 @@ def test_parity_on_stored_values(large):
         ok, worst = C.values_close(r["vals"], ref)
         assert ok, (name, worst)
         assert r["rc"] in (F.OK, F.ENONFINITE)
+
+
+@pytest.mark.parametrize("name", list(STORES))
+def test_candidates_on_strips(large, name):
+    """The library's candidates in each strip equal the oracle's (computed
+    from the stored pixels of the strip, with the field's noise parameters)."""
+    _, runs = large
+    r = runs[name]
+    tdt = STORES[name][1]
+    U = SPEC.nsnap - 2
+    checked = 0
+    for j, (a, b) in enumerate(STRIPS):
+        xs = stored(r["strips"][j], tdt)
+        units = [O.unit_tiles(xs, s, W) for s in range(U)]
+        v = np.stack([u.numerator for u in units])          # FP64, M-free
+        ok, worst = C.values_close(r["strip_vals"][j], v)
+        assert ok, (name, j, worst)
+        det = O.Detection([], r["M"], b - a, v.shape[2], tlisi=v, units=units)
+        with np.errstate(invalid="ignore"):
+            det.z = np.stack([(v[s] - r["noise"][s][0]) / r["noise"][s][1] for s in range(U)])
+            det.eta, det.eta_bin = O.spectrum(v)
+            det.eta_z = (det.eta - r["eta_noise"][0]) / r["eta_noise"][1]
+        res = {"noise": r["noise"], "values": r["strip_vals"][j],
+               "eta_noise": r["eta_noise"], "eta": r["strip_eta"][j]}
+        di, dfq = C.library_decisions(res, TAU)
+        cands = r["strip_cands"][j]
+        errs = C.compare(cands, xs, W, TAU, O.BRANCH_BOTH, "medmad", decide_image=di,
+                         decide_freq=dfq, det=det, cut_top=a > 0, cut_bottom=b < TY)
+        assert not errs, (name, j, errs[:10])
+        checked += len(cands)
+    assert checked > 1000
 
 
 def test_accuracy_against_fp32_originals(large):

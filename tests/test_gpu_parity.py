@@ -43,7 +43,7 @@ def run_both(stack_t, w, tau, branch=F.BRANCH_IMAGE, noise="meanstd", rmode="abs
 
 def assert_parity(res, det, x, w, tau, branch, noise="meanstd", rmode="abs", edge="partial",
                   rel=1e-5):
-    di, dfq = F.decisions(res, tau)
+    di, dfq = C.library_decisions(res, tau)
     errs = C.compare(res["candidates"], x, w, tau, branch, noise, rmode, edge, di, dfq, det)
     assert not errs, errs[:10]
     if branch & F.BRANCH_IMAGE:
@@ -139,7 +139,7 @@ def test_zero_reference_guard(storage, w):
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 @pytest.mark.parametrize("k", [1, 3, 4])
 def test_snapshot_accumulation(storage, k):
-    """Sec. 4.3.2: K raw snapshots pushed per stack snapshot are summed in FP32
+    """Sec. 3.3.2: K raw snapshots pushed per stack snapshot are summed in FP32
     in push order and stored in the plan's type; the oracle runs on those
     stored sums."""
     spec = synth.small_spec(7 * k, 96, 101, n_steady=6, n_pulsed=2, pulse_period=(3, 5))
@@ -526,7 +526,7 @@ def test_running_M_reading(stride):
     assert list(res["M_units"]) == list(det.M_units)
     assert len(set(det.M_units)) > 3           # the reading really differs from one M
     assert res["M"] == det.M
-    di, dfq = F.decisions(res, tau)
+    di, dfq = C.library_decisions(res, tau)
     if stride == "tile":
         errs = C.compare(res["candidates"], x, w, tau, F.BRANCH_BOTH, "medmad", "abs",
                          "partial", di, dfq, det)

@@ -20,7 +20,7 @@ def run(stack, w, tau, branch, noise="meanstd", storage=F.F32, tdt=torch.float32
                          stride=F.STRIDE_SLIDING)
     x = stack.to(tdt).float().cpu().numpy()
     det = O.detect(x, w, tau, branch, noise, stride="sliding")
-    di, dfq = F.decisions(res, tau)
+    di, dfq = C.library_decisions(res, tau)
     errs = C.compare(res["candidates"], x, 1, tau, branch, noise, decide_image=di,
                      decide_freq=dfq, det=det)
     assert not errs, errs[:8]

@@ -26,7 +26,7 @@ def run(x, w, tau, hmax, noise="meanstd"):
 
 
 def check(res, det, x, w, tau, hmax, noise):
-    di, dfq = F.decisions(res, tau)
+    di, dfq = C.library_decisions(res, tau)
     errs = C.compare(res["candidates"], x, w, tau, F.BRANCH_FREQ, noise, decide_image=di,
                      decide_freq=dfq, det=det, harmonics=hmax)
     assert not errs, errs[:10]
@@ -65,7 +65,7 @@ def test_spectrum_parity(L, side, w, period, hmax):
 def test_harmonic_sum_recovers_the_fundamental(seed):
     """A one-snapshot pulse every 16 snapshots over n = 128 units: the largest
     single magnitude sits on a high harmonic, the harmonic sum on the
-    fundamental bin n / 16 = 8 (the spin frequency, as in Sec. 3.3)."""
+    fundamental bin n / 16 = 8 (the spin frequency, as in the real-data evaluation of Sec. 3)."""
     x = synth.periodic_tile_stack(130, 64, 64, 4, 16, 3, (5, 7), 3.0, seed=seed)
     bins = {}
     for hmax in (1, 16):
@@ -121,7 +121,7 @@ def test_refined_positions_follow_the_oracle(refine, seed):
     x[np.arange(42) % 5 == 0, 90:97, 33:36] += 6.0
     res = F.detect_stack(torch.from_numpy(x).cuda(), w, 4.0, F.BRANCH_FREQ, refine=code)
     det = O.detect(x, w, 4.0, F.BRANCH_FREQ, refine=refine)
-    di, dfq = F.decisions(res, 4.0)
+    di, dfq = C.library_decisions(res, 4.0)
     errs = C.compare(res["candidates"], x, w, 4.0, F.BRANCH_FREQ, decide_image=di,
                      decide_freq=dfq, det=det, refine=refine)
     assert not errs, errs[:10]

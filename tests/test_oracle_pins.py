@@ -463,7 +463,7 @@ def test_running_M_brings_out_a_steady_tile_in_the_spectrum():
 
 # ---------------------------------------------------------------- accumulation
 def test_accumulate_block_sums_closed_form():
-    """Sec. 4.3.2: snapshot j of the accumulated stack is the sum of raw
+    """Sec. 3.3.2: snapshot j of the accumulated stack is the sum of raw
     snapshots jK .. jK+K-1; with raw snapshot r = r everywhere the sum is
     K^2 j + K(K-1)/2, and an incomplete last block is dropped."""
     raw = np.broadcast_to(np.arange(23, dtype=np.float64)[:, None, None], (23, 3, 4)).copy()
@@ -717,3 +717,63 @@ def test_freq_window_matches_the_batch_branch_with_harmonics_and_refine(harmonic
     assert [(c.y, c.x, c.freq_bin, c.xf, c.yf) for c in cands] == \
         [(c.y, c.x, c.freq_bin, c.xf, c.yf) for c in det.candidates]
     assert cands
+
+
+# ---------------------------------------------------------------- sampled tiles
+def _tile_by_pixel_loops(x, s, w, ty, tx, nyu, nxu):
+    """S1, S2, S3, n, valid and the first arg-max of Delta of one tile of unit
+    s, by a loop over its pixels (Eq. 3-5 written out per pixel)."""
+    S1 = S3 = 0.0
+    best, by, bx, cnt, valid = -1.0, -1, -1, 0, True
+    for y in range(ty * w, min(nyu, ty * w + w)):
+        for xx in range(tx * w, min(nxu, tx * w + w)):
+            a, b, c = (float(x[s + i, y, xx]) for i in range(3))
+            cnt += 1
+            if not (math.isfinite(a) and math.isfinite(b) and math.isfinite(c)):
+                valid = False
+                continue
+            dd = abs(abs(c - b) - abs(b - a))
+            xh = O.C if b == 0 else abs(b)
+            rr = dd / xh if dd / xh < 1 else 1.0
+            S1 += dd
+            S3 += rr
+            if dd > best:
+                best, by, bx = dd, y, xx
+    return S1, best, S3, cnt, valid, by, bx
+
+
+@pytest.mark.parametrize("edge", ["partial", "drop"])
+@pytest.mark.parametrize("kind", ["normal", "integers", "zeros"])
+@pytest.mark.parametrize("shape,w", [((5, 13, 17), 4), ((4, 9, 10), 3), ((6, 11, 7), 5)])
+def test_sampled_tiles_against_pixel_loops_and_unit_tiles(edge, kind, shape, w):
+    """The per-tile sampler that checks the library at full size: every tile's
+    S1, S2, S3, n, numerator, validity and absolute arg-max pixel equal a pixel
+    loop over that tile, and equal the whole-image tiling, on ragged grids
+    (the last tile row and column are partial under EDGE_PARTIAL), ties and
+    zeros, with a non-finite pixel in one tile."""
+    x = synth.random_stack(*shape, seed=sum(shape) * 7 + w, kind=kind).astype(np.float64)
+    x[2, shape[1] // 2, shape[2] - 1] = np.nan
+    L, ny, nx = shape
+    Ty, Tx, nyu, nxu = O.tiling(ny, nx, w, edge)
+    tiles = [(ty, tx) for ty in range(Ty) for tx in range(Tx)]
+    rng = np.random.default_rng(len(tiles))
+    tiles = [tiles[i] for i in rng.permutation(len(tiles))]   # order must not matter
+    got = O.sampled_tiles(x, w, tiles, edge=edge)
+    for s in range(L - 2):
+        ut = O.unit_tiles(x, s, w, edge=edge)
+        for j, (ty, tx) in enumerate(tiles):
+            S1, S2, S3, n, valid, by, bx = _tile_by_pixel_loops(x, s, w, ty, tx, nyu, nxu)
+            assert got["n"][s, j] == n == ut.n[ty, tx]
+            assert got["valid"][s, j] == valid == ut.valid[ty, tx]
+            if not valid:
+                assert np.isnan(got["numerator"][s, j])
+                continue
+            assert got["S1"][s, j] == pytest.approx(S1, rel=1e-13, abs=1e-300)
+            assert got["S2"][s, j] == S2
+            assert got["S3"][s, j] == pytest.approx(S3, rel=1e-13, abs=1e-300)
+            assert (got["arg_y"][s, j], got["arg_x"][s, j]) == (by, bx)
+            assert (got["arg_y"][s, j], got["arg_x"][s, j]) == (ut.arg_y[ty, tx], ut.arg_x[ty, tx])
+            want_v = (S1 / n) * S2 * (S3 / n)
+            assert got["numerator"][s, j] == pytest.approx(want_v, rel=1e-12, abs=1e-300)
+            assert got["numerator"][s, j] == pytest.approx(ut.numerator[ty, tx], rel=1e-12,
+                                                           abs=1e-300)

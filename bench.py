@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-spectrum", action="store_true",
+                    help="skip the transform-alone leg at power-of-two series lengths")
     ap.add_argument("--batched", action="store_true",
                     help="also run the 256-field batched workload (about a minute)")
     ap.add_argument("--serving-compression", type=float, default=20.0,
@@ -517,6 +519,32 @@ def paper_run(a, F, synth, torch, steps=3, seed=4040, ring=64):
             "candidates": int(n), "status": int(rc), "generation_s": round(gen_s, 1)}
 
 
+# ---------------------------------------------------------------- spectrum leg
+def spectrum_run(F, torch, T=16384, lengths=(256, 512, 1024, 2048, 4096), reps=5):
+    """The image-frequency transform alone at the paper's power-of-two series
+    lengths (L - 2 = 2^m), on T = 16384 series (a 4096^2 image at window 32):
+    the radix FFT against the direct O(n^2) warp kernel on the same cube.
+    Bytes per launch = the cube read once (4 n T) + eta and bin written (8 T)."""
+    out = {"tiles": T, "timing": f"median of {reps} launches, CUDA events", "lengths": {}}
+    g = torch.Generator(device="cuda").manual_seed(5)
+    for n in lengths:
+        x = torch.randn(n, T, device="cuda", generator=g).abs_().square_().add_(0.5)
+        eta = torch.empty(T, device="cuda")
+        kb = torch.empty(T, dtype=torch.int32, device="cuda")
+        row = {}
+        for name, m in (("radix", F.SPECTRUM_RADIX), ("direct", F.SPECTRUM_DIRECT)):
+            F.fitrig_spectrum_map(x, n, T, T, 1, eta, kb, m)
+            ms = statistics.median(F.fitrig_spectrum_map(x, n, T, T, 1, eta, kb, m)
+                                   for _ in range(reps))
+            row[f"{name}_ms"] = ms
+            row[f"{name}_gb_per_s"] = (4 * n * T + 8 * T) / (ms * 1e-3) / 1e9
+        row["speedup"] = row["direct_ms"] / row["radix_ms"]
+        out["lengths"][str(n)] = row
+        del x, eta, kb
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------- accumulation leg
 def accumulate_run(a, F, torch, stack, storage, reps=3):
     """Ingest with snapshot accumulation (Sec. 3.3.2): K raw device snapshots
@@ -660,9 +688,11 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                "seconds": round(used, 2)}
 
-    accum = large = None
+    accum = large = spectrum = None
     if rank == 0 and ws == 1 and a.accumulate > 1:
         accum = accumulate_run(a, F, torch, stack, storage)
+    if rank == 0 and ws == 1 and not a.no_spectrum:
+        spectrum = spectrum_run(F, torch)
 
     serving = batched = None
     legs = rank == 0 and ws == 1 and (a.large or a.paper_run or
@@ -702,6 +732,7 @@ def main():
             "serving": serving,
             "batched": batched,
             "accumulate": accum,
+            "spectrum_pow2": spectrum,
             "large": large,
             "paper_run": paper,
             "clocks": clk.summary(),

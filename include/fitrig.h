@@ -286,6 +286,30 @@ FITRIG_API int fitrig_stack_device_ptr(fitrig_plan_t plan, int32_t s, void** ptr
                                        int64_t* row_pitch_elems);
 
 /*
+ * fitrig_spectrum_map -- the image-frequency statistic of Sec. 2.4.2 (Eq.
+ * eta) alone, on a caller cube in device memory: T series of n points, point
+ * q of series t at dev_cube[q * stride + t] (FP32; stride >= T).  For each
+ * series, its mean is removed, the unnormalised DFT of exact length n is
+ * taken, and eta[t] = h(|X_1..X_(n/2)|) with bin[t] its frequency bin: h is
+ * the maximum magnitude (harmonics = 1) or the incoherent harmonic sum over
+ * m = 1, 2, 4, .., harmonics (a power of two <= 32), as in a plan's
+ * frequency branch; a series with a non-finite point gets eta = NaN, bin =
+ * -1.  Outputs go to dev_eta[T] and dev_bin[T] (device memory).  `method`
+ * picks the transform: FITRIG_SPECTRUM_AUTO (what a plan uses for this n),
+ * FITRIG_SPECTRUM_DIRECT (the direct O(n^2) sum; for n > 256 only, where the
+ * warp-per-tile direct kernel applies) or FITRIG_SPECTRUM_RADIX (the radix
+ * FFT; n a power of two from 128 to 4096, EUNSUPPORTED otherwise).  2 <= n
+ * <= 4096.  Allocates and frees a twiddle table; work is enqueued on `stream`
+ * (a cudaStream_t, 0 = legacy default) and the call synchronises it.
+ * Optional `ms` receives the transform's device time (CUDA events).  EINVAL
+ * on bad arguments.
+ */
+enum { FITRIG_SPECTRUM_AUTO = 0, FITRIG_SPECTRUM_DIRECT = 1, FITRIG_SPECTRUM_RADIX = 2 };
+FITRIG_API int fitrig_spectrum_map(const float* dev_cube, int32_t n, int64_t T, int64_t stride,
+                                   int32_t harmonics, float* dev_eta, int32_t* dev_bin,
+                                   int32_t method, int64_t stream, float* ms);
+
+/*
  * fitrig_threshold_map -- the noise + threshold stage alone (Sec. 2.4.1) on a
  * caller map of n finite-or-NaN FP32 values in device memory: centre/scale by
  * `noise_mode`, and the number of entries with z > nsigma.  `stream` is a

@@ -206,6 +206,66 @@ def bin_is_a_maximum(mags: np.ndarray, k: int, harmonics: int = 1) -> bool:
     return bool(val >= top * (1 - REL_TOL))
 
 
+def tile_value_bound(stack: np.ndarray, s: int, w: int, rmode: str = "abs",
+                     edge: str = "partial") -> np.ndarray:
+    """Per tile of unit s, an upper bound on |v - v_exact| for an implementation
+    that computes the tile statistic v = mean(Delta) max(Delta) mean(r) in
+    FP32 (unit roundoff u = 2^-24) from the stored values, where v_exact is
+    the FP64 value of the same definition on the same inputs.
+
+    Per pixel: D^(s) = fl|b - a| and D^(s+1) = fl|c - b| are each one rounding
+    and Delta one more, so |Delta - Delta_exact| <= e_D = u (D1 + D2 + Delta)
+    (1 + 1/64): the error is relative to the differences, not to Delta, which
+    can be far smaller when D1 and D2 nearly cancel (a pulse in the middle
+    snapshot).  The ratio Delta / |b| takes an approximate reciprocal (relative
+    error <= 2u) and a product (u), and min(., 1) does not enlarge errors, so
+    |r - r_exact| <= min(1, (e_D + 3u (Delta + e_D)) / |b|), and 0 where both
+    sides are certainly clipped at 1.  Tile sums of m terms add (m - 1) u times
+    the sum of magnitudes; the maximum moves by at most the largest e_D; the
+    two divisions by the pixel count and the two products add 8u.  The bound
+    on v follows from the perturbed factors."""
+    u = 2.0 ** -24
+    L, ny, nx = stack.shape
+    Ty, Tx, nyu, nxu = O.tiling(ny, nx, w, edge)
+    a, b, c = (np.asarray(stack[s + i, :nyu, :nxu], dtype=np.float64) for i in range(3))
+    delta, r, fin = O.unit_terms(a, b, c, rmode)
+    with np.errstate(invalid="ignore", over="ignore"):
+        d1 = np.abs(b - a)
+        d2 = np.abs(c - b)
+        eD = u * (d1 + d2 + delta) * (1.0 + 1.0 / 64)
+        xh = np.where(b == 0.0, O.C, np.abs(b))
+        ratio = delta / xh
+        er = (eD + 3 * u * (delta + eD)) / xh
+        er = np.where(ratio - er >= 1.0, 0.0, np.minimum(er, 1.0))
+    eD = np.where(fin, eD, 0.0)
+    er = np.where(fin, er, 0.0)
+    ut = O.tile_reduce(delta, r, fin, w, Ty, Tx)
+    eu = O.tile_reduce(eD, er, fin, w, Ty, Tx)
+    m = ut.n
+    S1 = ut.S1 + eu.S1 + (m - 1) * u * (ut.S1 + eu.S1)
+    S2 = ut.S2 + eu.S2
+    S3 = ut.S3 + eu.S3 + (m - 1) * u * (ut.S3 + eu.S3)
+    hi = (S1 / m) * S2 * (S3 / m) * (1 + 8 * u)
+    return np.where(ut.valid, hi - ut.numerator, np.nan)
+
+
+def values_within_bound(gpu: np.ndarray, ref: np.ndarray, bound: np.ndarray,
+                        slack: float = 2.0) -> Tuple[bool, float]:
+    """|gpu - ref| <= slack * bound elementwise (NaNs must coincide); returns
+    (ok, worst ratio of error to bound)."""
+    g = np.asarray(gpu, dtype=np.float64)
+    r = np.asarray(ref, dtype=np.float64)
+    if not np.array_equal(np.isnan(g), np.isnan(r)):
+        return False, float("inf")
+    m = np.isfinite(r)
+    if not m.any():
+        return True, 0.0
+    err = np.abs(g[m] - r[m])
+    b = np.asarray(bound, dtype=np.float64)[m]
+    ratio = err / np.maximum(b, 1e-300)
+    return bool(np.all(err <= slack * b)), float(ratio.max())
+
+
 def values_close(gpu: np.ndarray, ref: np.ndarray, rel: float = 1e-5,
                  abs_scale: float = 1e-6) -> Tuple[bool, float]:
     """Elementwise |gpu - ref| <= rel |ref| + abs_scale * mean|ref|, NaNs must coincide."""

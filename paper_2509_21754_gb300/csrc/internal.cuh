@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/fitrig.h"
 
 namespace fitrig {
@@ -318,6 +320,18 @@ cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
                             const float2* twiddle, const float* wts, int hmax, float* eta,
                             int* bin, cudaStream_t st);
 int spectrum_max_n();   // longest series launch_spectrum takes
+// The twiddle table launch_spectrum expects for series of n points (host
+// side, FP64 angles rounded once): the full circle (cos, sin)(2 pi a / n) for
+// the radix kernel's lengths (powers of two from 128), else the direct
+// kernels' rows.
+std::vector<float2> spectrum_twiddles(int n);
+// launch_spectrum with the transform chosen: automatic (what a plan uses),
+// the direct O(n^2) warp kernel, or the radix FFT (powers of two 128..4096,
+// cudaErrorInvalidValue otherwise).
+enum { kSpectrumAuto = 0, kSpectrumDirect = 1, kSpectrumRadix = 2 };
+cudaError_t launch_spectrum_method(const float* vp, int n, int64_t T, int64_t vs,
+                                   const float2* twiddle, const float* wts, int hmax, float* eta,
+                                   int* bin, int method, cudaStream_t st);
 
 // Ingest conversion (fp32 <-> bf16/fp16).
 cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,

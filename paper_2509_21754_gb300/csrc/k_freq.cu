@@ -346,6 +346,54 @@ constexpr int kLongMaxN = 4096;
 constexpr int kLongB = 4;
 constexpr int kSeed = 32;
 
+// Warp reduction of one tile's squared magnitudes mk[k] = |X_k|^2, k = 1..K:
+// the maximum magnitude (hmax = 1) or the largest harmonic sum, with its bin
+// (ties: smaller m, then smaller k).  Lane 0 writes eta and the bin.
+__device__ __forceinline__ void warp_spectrum_best(const float* mk, int K, int hmax, int lane,
+                                                   float* eta, int* bin) {
+  float best = -1.f;
+  int bk = 1, bm = 1;
+  if (hmax <= 1) {
+    for (int k = 1 + lane; k <= K; k += 32) {
+      const float v = mk[k];
+      if (v > best) {
+        best = v;
+        bk = k;
+      }
+    }
+  } else {
+    for (int m = 1; m <= hmax && m <= K; m <<= 1) {
+      const float inv = 1.f / sqrtf((float)m);
+      for (int k = 1 + lane; k * m <= K; k += 32) {
+        float acc = 0.f;
+        for (int j = 1; j <= m; ++j) acc += sqrtf(mk[j * k]);
+        acc *= inv;
+        if (acc > best) {
+          best = acc;
+          bk = k;
+          bm = m;
+        }
+      }
+    }
+  }
+  // warp arg-max: larger value, then smaller m, then smaller k
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, best, off);
+    const int okk = __shfl_xor_sync(0xffffffffu, bk, off);
+    const int om = __shfl_xor_sync(0xffffffffu, bm, off);
+    if (ov > best || (ov == best && (om < bm || (om == bm && okk < bk)))) {
+      best = ov;
+      bk = okk;
+      bm = om;
+    }
+  }
+  if (lane == 0) {
+    *eta = hmax <= 1 ? sqrtf(best) : best;
+    *bin = bk;
+  }
+}
+
 __host__ __device__ constexpr int long_ldy(int n) { return (n + 27) / 32 * 32 + 4; }
 
 __global__ void __launch_bounds__(kLongWarps * 32) k_dft_long(const float* __restrict__ vp, int n,
@@ -444,50 +492,226 @@ __global__ void __launch_bounds__(kLongWarps * 32) k_dft_long(const float* __res
       if (kb + lane + 32 * b <= K) mk[kk[b]] = re[b] * re[b] + im[b] * im[b];
   }
   __syncwarp();
-  float best = -1.f;
-  int bk = 1, bm = 1;
-  if (hmax <= 1) {
-    for (int k = 1 + lane; k <= K; k += 32) {
-      const float v = mk[k];
-      if (v > best) {
-        best = v;
-        bk = k;
-      }
-    }
-  } else {
-    for (int m = 1; m <= hmax && m <= K; m <<= 1) {
-      const float inv = 1.f / sqrtf((float)m);
-      for (int k = 1 + lane; k * m <= K; k += 32) {
-        float acc = 0.f;
-        for (int j = 1; j <= m; ++j) acc += sqrtf(mk[j * k]);
-        acc *= inv;
-        if (acc > best) {
-          best = acc;
-          bk = k;
-          bm = m;
-        }
-      }
+  warp_spectrum_best(mk, K, hmax, lane, eta + t, bin + t);
+}
+
+// Powers of two, kFftMinN <= n <= kLongMaxN: a radix FFT per tile instead of
+// the O(n^2) direct sum.  One warp per tile; a CTA stages the series of
+// TILES consecutive tiles by asynchronous global -> shared copies (each cube
+// row a TILES x 4-byte segment).  The real series y_0..y_(n-1), mean removed,
+// is read as the complex series z_j = y_(2j) + i y_(2j+1) of N = n/2 points
+// (the staging buffer already holds it in that order), transformed by a
+// Stockham autosort FFT (radix-4 passes, one radix-2 pass when log2 N is odd)
+// that alternates between the staging buffer and a second warp buffer, and
+// the real spectrum is recovered as
+//   X_k = (Z_k + conj Z_(N-k)) / 2 - (i/2) e^(-2 pi i k/n) (Z_k - conj Z_(N-k)),
+//   X_(n/2) = Re Z_0 - Im Z_0,
+// whose squared magnitudes feed the same maximum / harmonic-sum reduction as
+// the direct kernels.  Every twiddle is an entry of the host's FP64 table of
+// (cos, sin)(2 pi a / n), a = 0..n-1, rounded once to FP32.
+constexpr int kFftMinN = 128;
+
+__host__ __device__ constexpr bool fft_length(int n) {
+  return n >= kFftMinN && n <= kLongMaxN && (n & (n - 1)) == 0;
+}
+
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 w) {   // a * conj(w)
+  return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
+}
+
+template <int TILES>
+__global__ void __launch_bounds__(TILES * 32) k_fft_pow2(const float* __restrict__ vp, int n,
+                                                         int logN, int64_t T, int64_t vs,
+                                                         const float2* __restrict__ fw,
+                                                         const float* __restrict__ wts, int hmax,
+                                                         float* eta, int* bin) {
+  extern __shared__ float2 fsm[];
+  const int N = n >> 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t0 = (int64_t)blockIdx.x * TILES;
+  for (int i = threadIdx.x; i < n * TILES; i += TILES * 32) {
+    const int q = i / TILES, c = i - q * TILES;
+    float* dst = reinterpret_cast<float*>(fsm + (size_t)c * 2 * N) + q;
+    if (t0 + c < T) {
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)),
+                   "l"(vp + (size_t)q * vs + t0 + c)
+                   : "memory");
+    } else {
+      *dst = 0.f;
     }
   }
-  // warp arg-max: larger value, then smaller m, then smaller k
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const int64_t t = t0 + warp;
+  if (t >= T) return;
+  float2* src = fsm + (size_t)warp * 2 * N;   // z_j = (y_2j, y_2j+1)
+  float2* dst = src + N;
+  float* y = reinterpret_cast<float*>(src);
+  float sum = 0.f;
+  bool ok = true;
+  for (int q = lane; q < n; q += 32) {
+    float v = y[q];
+    if (wts) {
+      v *= wts[q];
+      y[q] = v;
+    }
+    ok = ok && isfinite(v);
+    sum += v;
+  }
+  ok = __all_sync(0xffffffffu, ok);
 #pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    const float ov = __shfl_xor_sync(0xffffffffu, best, off);
-    const int okk = __shfl_xor_sync(0xffffffffu, bk, off);
-    const int om = __shfl_xor_sync(0xffffffffu, bm, off);
-    if (ov > best || (ov == best && (om < bm || (om == bm && okk < bk)))) {
-      best = ov;
-      bk = okk;
-      bm = om;
+  for (int off = 16; off; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  if (!ok) {
+    if (lane == 0) {
+      eta[t] = NAN;
+      bin[t] = -1;
     }
+    return;
   }
-  if (lane == 0) {
-    eta[t] = hmax <= 1 ? sqrtf(best) : best;
-    bin[t] = bk;
+  const float mean = sum / (float)n;
+  for (int q = lane; q < n; q += 32) y[q] -= mean;
+  __syncwarp();
+  int Ns = 1;
+  for (int pass = 0; pass < (logN >> 1); ++pass) {
+    const int Q = N >> 2, step = n / (4 * Ns);
+    for (int j = lane; j < Q; j += 32) {
+      const int k = j & (Ns - 1);
+      const int e = k * step;   // W_(4 Ns)^(r k) = W_n^(r e), r e < 3n/4
+      const float2 a0 = src[j];
+      const float2 a1 = cmul_conj(src[j + Q], __ldg(fw + e));
+      const float2 a2 = cmul_conj(src[j + 2 * Q], __ldg(fw + 2 * e));
+      const float2 a3 = cmul_conj(src[j + 3 * Q], __ldg(fw + 3 * e));
+      const float2 b0 = make_float2(a0.x + a2.x, a0.y + a2.y);
+      const float2 b1 = make_float2(a0.x - a2.x, a0.y - a2.y);
+      const float2 b2 = make_float2(a1.x + a3.x, a1.y + a3.y);
+      const float2 b3 = make_float2(a1.y - a3.y, a3.x - a1.x);   // -i (a1 - a3)
+      const int base = ((j - k) << 2) + k;
+      dst[base] = make_float2(b0.x + b2.x, b0.y + b2.y);
+      dst[base + Ns] = make_float2(b1.x + b3.x, b1.y + b3.y);
+      dst[base + 2 * Ns] = make_float2(b0.x - b2.x, b0.y - b2.y);
+      dst[base + 3 * Ns] = make_float2(b1.x - b3.x, b1.y - b3.y);
+    }
+    __syncwarp();
+    float2* tmp = src;
+    src = dst;
+    dst = tmp;
+    Ns <<= 2;
   }
+  if (logN & 1) {   // last pass radix 2: Ns = N / 2, twiddle W_N^j = W_n^(2j)
+    for (int j = lane; j < Ns; j += 32) {
+      const float2 a0 = src[j];
+      const float2 a1 = cmul_conj(src[j + Ns], __ldg(fw + 2 * j));
+      dst[j] = make_float2(a0.x + a1.x, a0.y + a1.y);
+      dst[j + Ns] = make_float2(a0.x - a1.x, a0.y - a1.y);
+    }
+    __syncwarp();
+    float2* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  float* mk = reinterpret_cast<float*>(dst);   // |X_k|^2 at mk[k], k = 1..N
+  for (int k = 1 + lane; k <= N; k += 32) {
+    float m2;
+    if (k == N) {
+      const float2 z0 = src[0];
+      const float x = z0.x - z0.y;
+      m2 = x * x;
+    } else {
+      const float2 zk = src[k], zc = src[N - k];
+      const float er = 0.5f * (zk.x + zc.x), ei = 0.5f * (zk.y - zc.y);
+      const float orr = 0.5f * (zk.y + zc.y), oi = 0.5f * (zc.x - zk.x);
+      const float2 w = __ldg(fw + k);   // (cos, sin)(2 pi k / n); forward uses conj
+      const float xr = er + fmaf(w.x, orr, w.y * oi);
+      const float xi = ei + fmaf(w.x, oi, -w.y * orr);
+      m2 = xr * xr + xi * xi;
+    }
+    mk[k] = m2;
+  }
+  __syncwarp();
+  warp_spectrum_best(mk, N, hmax, lane, eta + t, bin + t);
+}
+
+static int fft_tiles(int n) { return n <= 1024 ? 8 : 4; }
+
+std::vector<float2> spectrum_twiddles(int n) {
+  std::vector<float2> tw;
+  if (fft_length(n)) {   // the full circle: (cos, sin)(2 pi a / n), a = 0..n-1
+    tw.resize((size_t)n);
+    for (int a = 0; a < n; ++a) {
+      const double ang = 2.0 * M_PI * (double)a / (double)n;
+      tw[(size_t)a] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    return tw;
+  }
+  // (cos, sin)(2 pi ((k q) mod n) / n) for k = 1..K, q = 1..H: [K][H] for the
+  // direct kernels of series up to 256 points; longer series take only the
+  // first row (k = 1), which is all the warp-per-tile kernel reads.
+  const int H = (n - 1) / 2, K = n > 256 ? 1 : n / 2;
+  tw.resize((size_t)std::max(1, K * H));
+  for (int k = 1; k <= K; ++k)
+    for (int q = 1; q <= H; ++q) {
+      const double ang = 2.0 * M_PI * (double)(((int64_t)k * q) % n) / (double)n;
+      tw[(size_t)(k - 1) * H + (q - 1)] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  return tw;
 }
 
 int spectrum_max_n() { return kLongMaxN; }
+
+static cudaError_t launch_long(const float* vp, int n, int64_t T, int64_t vs,
+                               const float2* tw_row, const float* wts, int hmax, float* eta,
+                               int* bin, cudaStream_t st) {
+  const int K = n / 2;
+  const size_t sm = (size_t)kLongWarps * (long_ldy(n) + K + 1) * sizeof(float);
+  static size_t long_configured = 0;
+  if (sm > 48 * 1024 && sm > long_configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_dft_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    long_configured = sm;
+  }
+  const int64_t lblocks = (T + kLongWarps - 1) / kLongWarps;
+  k_dft_long<<<(unsigned)lblocks, kLongWarps * 32, sm, st>>>(vp, n, T, vs, tw_row, wts, hmax,
+                                                             eta, bin);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+template <int TILES>
+static cudaError_t launch_fft_t(const float* vp, int n, int64_t T, int64_t vs, const float2* fw,
+                                const float* wts, int hmax, float* eta, int* bin,
+                                cudaStream_t st) {
+  const size_t sm = (size_t)TILES * n * sizeof(float2);   // two N-point buffers per tile
+  static size_t configured = 0;
+  if (sm > 48 * 1024 && sm > configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_pow2<TILES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    configured = sm;
+  }
+  int logN = 0;
+  while ((2 << logN) < n) ++logN;   // N = n / 2 = 2^logN
+  const int64_t blocks = (T + TILES - 1) / TILES;
+  k_fft_pow2<TILES><<<(unsigned)blocks, TILES * 32, sm, st>>>(vp, n, logN, T, vs, fw, wts, hmax,
+                                                             eta, bin);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum_method(const float* vp, int n, int64_t T, int64_t vs,
+                                   const float2* twiddle, const float* wts, int hmax, float* eta,
+                                   int* bin, int method, cudaStream_t st) {
+  if (n < 2 || n > kLongMaxN || hmax < 1) return cudaErrorInvalidValue;
+  if (T == 0) return cudaSuccess;
+  if (fft_length(n)) {
+    if (method == kSpectrumDirect)   // the O(n^2) warp kernel on the same table
+      return launch_long(vp, n, T, vs, twiddle + 1, wts, hmax, eta, bin, st);
+    return fft_tiles(n) == 8 ? launch_fft_t<8>(vp, n, T, vs, twiddle, wts, hmax, eta, bin, st)
+                             : launch_fft_t<4>(vp, n, T, vs, twiddle, wts, hmax, eta, bin, st);
+  }
+  if (method == kSpectrumRadix) return cudaErrorInvalidValue;
+  return launch_spectrum(vp, n, T, vs, twiddle, wts, hmax, eta, bin, st);
+}
 
 cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
                             const float2* twiddle, const float* wts, int hmax, float* eta,
@@ -495,6 +719,9 @@ cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
   const int64_t blocks = (T + kDftThreads - 1) / kDftThreads;
   const int H = (n - 1) / 2, K = n / 2;
   if (n < 2 || n > kLongMaxN || hmax < 1) return cudaErrorInvalidValue;
+  if (T == 0) return cudaSuccess;
+  if (fft_length(n))
+    return launch_spectrum_method(vp, n, T, vs, twiddle, wts, hmax, eta, bin, kSpectrumAuto, st);
   const bool harm = hmax > 1;
   if ((n & 1) == 0 && n <= 66) {
     const int m = n / 2, Hm = (m - 1) / 2, Kh = m / 2;
@@ -513,21 +740,7 @@ cudaError_t launch_spectrum(const float* vp, int n, int64_t T, int64_t vs,
     count_launches(1);
     return cudaGetLastError();
   }
-  if (n > 256 || hmax > 1) {
-    const size_t sm = (size_t)kLongWarps * (long_ldy(n) + K + 1) * sizeof(float);
-    static size_t long_configured = 0;
-    if (sm > 48 * 1024 && sm > long_configured) {
-      cudaError_t e = cudaFuncSetAttribute(k_dft_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)sm);
-      if (e != cudaSuccess) return e;
-      long_configured = sm;
-    }
-    const int64_t lblocks = (T + kLongWarps - 1) / kLongWarps;
-    k_dft_long<<<(unsigned)lblocks, kLongWarps * 32, sm, st>>>(vp, n, T, vs, twiddle, wts, hmax,
-                                                               eta, bin);
-    count_launches(1);
-    return cudaGetLastError();
-  }
+  if (n > 256 || hmax > 1) return launch_long(vp, n, T, vs, twiddle, wts, hmax, eta, bin, st);
   const size_t smem = (size_t)n * kDftThreads * sizeof(float);
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {

@@ -372,19 +372,10 @@ static int alloc_select(fitrig_plan_t p) {
   return FITRIG_OK;
 }
 
-// Twiddle table of the length-n transform: (cos, sin)(2 pi ((k q) mod n) / n)
-// for k = 1..n/2, q = 1..(n-1)/2, computed in FP64 on the host.
-// (cos, sin)(2 pi (k q mod n) / n) in FP64, rounded once: [K][H] for the
-// direct kernel of series up to 256 points; longer series take only the first
-// row (k = 1), which is all the warp-per-tile kernel reads.
+// Twiddle table of the length-n transform (layout chosen by the spectrum
+// kernels: spectrum_twiddles), computed in FP64 on the host.
 static int make_twiddles(fitrig_plan_t p, int n, float2** out) {
-  const int H = (n - 1) / 2, K = n > 256 ? 1 : n / 2;
-  std::vector<float2> tw((size_t)std::max(1, K * H));
-  for (int k = 1; k <= K; ++k)
-    for (int q = 1; q <= H; ++q) {
-      const double ang = 2.0 * M_PI * (double)(((int64_t)k * q) % n) / (double)n;
-      tw[(size_t)(k - 1) * H + (q - 1)] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-    }
+  const std::vector<float2> tw = spectrum_twiddles(n);
   CK(dmalloc(p, out, sizeof(float2) * tw.size()));
   CK(cudaMemcpy(*out, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
   return FITRIG_OK;
@@ -1276,6 +1267,51 @@ FITRIG_API int fitrig_stack_device_ptr(fitrig_plan_t p, int32_t s, void** ptr,
   if (rc != FITRIG_OK) return rc;
   *ptr = p->d_stack + p->slice_bytes * s;
   *row_pitch_elems = p->pitch;
+  return FITRIG_OK;
+}
+
+FITRIG_API int fitrig_spectrum_map(const float* dev_cube, int32_t n, int64_t T, int64_t stride,
+                                   int32_t harmonics, float* dev_eta, int32_t* dev_bin,
+                                   int32_t method, int64_t stream, float* ms) {
+  if (!dev_cube || !dev_eta || !dev_bin || T < 1 || stride < T) return FITRIG_EINVAL;
+  if (n < 2 || n > spectrum_max_n()) return FITRIG_EINVAL;
+  if (harmonics < 1 || harmonics > 32 || (harmonics & (harmonics - 1))) return FITRIG_EINVAL;
+  if (method < FITRIG_SPECTRUM_AUTO || method > FITRIG_SPECTRUM_RADIX) return FITRIG_EINVAL;
+  const bool pow2 = n >= 128 && (n & (n - 1)) == 0;
+  if (method == FITRIG_SPECTRUM_RADIX && !pow2) return FITRIG_EUNSUPPORTED;
+  if (method == FITRIG_SPECTRUM_DIRECT && n <= 256) return FITRIG_EUNSUPPORTED;
+  if (T > (int64_t)UINT32_MAX) return FITRIG_EUNSUPPORTED;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const std::vector<float2> tw = spectrum_twiddles(n);
+  float2* d_tw = nullptr;
+  CK(cudaMalloc(&d_tw, sizeof(float2) * tw.size()));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMemcpyAsync(d_tw, tw.data(), sizeof(float2) * tw.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) {
+    const int m = method == FITRIG_SPECTRUM_DIRECT ? kSpectrumDirect
+                  : method == FITRIG_SPECTRUM_RADIX ? kSpectrumRadix : kSpectrumAuto;
+    if (method == FITRIG_SPECTRUM_DIRECT && !pow2)   // the table is already the direct kernels'
+      e = launch_spectrum(dev_cube, n, T, stride, d_tw, nullptr, harmonics, dev_eta, dev_bin, st);
+    else
+      e = launch_spectrum_method(dev_cube, n, T, stride, d_tw, nullptr, harmonics, dev_eta,
+                                 dev_bin, m, st);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(d_tw);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return FITRIG_ECUDA;
+  }
+  if (ms) *ms = t;
   return FITRIG_OK;
 }
 

@@ -108,6 +108,8 @@ SIGNATURES = {
     "fitrig_batch_destroy": (c_int, [P]),
     "fitrig_autotune": (c_int, [c_int, c_int, POINTER(c_int32), POINTER(c_int32), POINTER(c_float)]),
     "fitrig_noise_static": (c_int, [P, c_int32, c_int64, c_int, P, c_int64]),
+    "fitrig_spectrum_map": (c_int, [P, c_int32, c_int64, c_int64, c_int32, P, P, c_int32,
+                                    c_int64, POINTER(c_float)]),
     "fitrig_plan_destroy": (c_int, [P]),
 }
 
@@ -330,6 +332,20 @@ def fitrig_threshold_map(dev_map, nsigma: float, noise_mode: int = NOISE_MEANSTD
                                        float(nsigma), noise_mode, int(stream), byref(n),
                                        byref(c), byref(s)), "fitrig_threshold_map")
     return n.value, c.value, s.value
+
+
+SPECTRUM_AUTO, SPECTRUM_DIRECT, SPECTRUM_RADIX = 0, 1, 2
+
+
+def fitrig_spectrum_map(dev_cube, n: int, T: int, stride: int, harmonics: int, dev_eta,
+                        dev_bin, method: int = SPECTRUM_AUTO, stream: int = 0) -> float:
+    """eta / bin of T series of n points (point q of series t at
+    dev_cube[q * stride + t]; CUDA tensors); returns the transform's ms."""
+    ms = c_float()
+    _check(load().fitrig_spectrum_map(c_void_p(dev_cube.data_ptr()), n, T, stride, harmonics,
+                                      c_void_p(dev_eta.data_ptr()), c_void_p(dev_bin.data_ptr()),
+                                      method, int(stream), byref(ms)), "fitrig_spectrum_map")
+    return ms.value
 
 
 def fitrig_autotune(window: int, storage: int = F32) -> Tuple[int, int, float]:

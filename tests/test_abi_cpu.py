@@ -119,3 +119,21 @@ def test_new_entry_points_check_their_arguments_without_a_device(lib):
     assert e.value.status == F.EINVAL
     assert L.fitrig_plan_set(None, F.OPT_HARMONICS, 8) == F.EINVAL
     assert L.fitrig_plan_set(None, F.OPT_REFINE, F.REFINE_CUBIC) == F.EINVAL
+
+
+def test_spectrum_map_checks_its_arguments_without_a_device(lib):
+    """fitrig_spectrum_map rejects bad arguments before any device call."""
+    from paper_2509_21754_gb300 import fitrig as F
+    L = F.load()
+    p = ctypes.c_void_p(16)   # never dereferenced: every call below fails validation
+    ms = ctypes.c_float()
+    assert L.fitrig_spectrum_map(None, 256, 8, 8, 1, p, p, 0, 0, ctypes.byref(ms)) == F.EINVAL
+    assert L.fitrig_spectrum_map(p, 256, 8, 4, 1, p, p, 0, 0, None) == F.EINVAL       # stride < T
+    assert L.fitrig_spectrum_map(p, 1, 8, 8, 1, p, p, 0, 0, None) == F.EINVAL         # n < 2
+    assert L.fitrig_spectrum_map(p, 4097, 8, 8, 1, p, p, 0, 0, None) == F.EINVAL      # n > 4096
+    assert L.fitrig_spectrum_map(p, 256, 8, 8, 3, p, p, 0, 0, None) == F.EINVAL       # harmonics
+    assert L.fitrig_spectrum_map(p, 256, 8, 8, 64, p, p, 0, 0, None) == F.EINVAL
+    assert L.fitrig_spectrum_map(p, 256, 8, 8, 1, p, p, 3, 0, None) == F.EINVAL       # method
+    assert L.fitrig_spectrum_map(p, 300, 8, 8, 1, p, p, F.SPECTRUM_RADIX, 0, None) == F.EUNSUPPORTED
+    assert L.fitrig_spectrum_map(p, 64, 8, 8, 1, p, p, F.SPECTRUM_RADIX, 0, None) == F.EUNSUPPORTED
+    assert L.fitrig_spectrum_map(p, 128, 8, 8, 1, p, p, F.SPECTRUM_DIRECT, 0, None) == F.EUNSUPPORTED

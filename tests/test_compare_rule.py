@@ -158,3 +158,63 @@ def test_strip_rule_passes_the_oracle_list_and_skips_cut_components(case, a, b):
     errs = C.compare(bad, xs, W, TAU, O.BRANCH_BOTH, "medmad", **kw)
     cut = (a > 0 and ty0 == 0) or (b < Ty and ty0 == b - a - 1)
     assert cut or any("significance" in e for e in errs), errs
+
+
+def _fp32_tile_statistic(x32: np.ndarray, s: int, w: int) -> np.ndarray:
+    """The tile statistic computed the way an FP32 implementation does: every
+    difference, ratio, sum (sequential over the tile) and product rounded to
+    FP32 (NumPy float32 arithmetic is IEEE round-to-nearest-even)."""
+    f = np.float32
+    a, b, c = x32[s], x32[s + 1], x32[s + 2]
+    d1 = np.abs(b - a)
+    d2 = np.abs(c - b)
+    delta = np.abs(d1 - d2)
+    xh = np.where(b == 0, f(O.C), np.abs(b)).astype(f)
+    r = np.minimum(delta * (f(1) / xh), f(1))
+    ny, nx = a.shape
+    Ty, Tx = -(-ny // w), -(-nx // w)
+    out = np.zeros((Ty, Tx), dtype=f)
+    for ty in range(Ty):
+        for tx in range(Tx):
+            sl = (slice(ty * w, ty * w + w), slice(tx * w, tx * w + w))
+            S1, S3, S2 = f(0), f(0), f(-1)
+            for dv, rv in zip(delta[sl].ravel(), r[sl].ravel()):
+                S1 = f(S1 + dv)
+                S3 = f(S3 + rv)
+                S2 = max(S2, dv)
+            n = f(delta[sl].size)
+            out[ty, tx] = f(f(f(S1 / n) * S2) * f(S3 / n))
+    return out
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_tile_value_bound_covers_fp32_arithmetic(seed):
+    """The derived FP32 error bound of the tile statistic holds for an FP32
+    emulation of the tile arithmetic on stacks with the hard cases: a pulse in
+    the middle snapshot of a unit (the two differences nearly cancel in
+    Delta), bright steady sky, faint reference pixels and exact zeros; and it
+    is tight enough to be a meaningful test (median bound ~1e-7 relative)."""
+    rng = np.random.default_rng(seed)
+    L, ny, nx, w = 6, 40, 45, 5
+    x = rng.standard_normal((L, ny, nx))
+    x[:, :10, :] += 300.0 * rng.uniform(0, 1, (1, 10, nx))   # bright steady sky
+    x[2, 10:30, :] += 25.0                                   # pulse in snapshot 2
+    x[3, 30:, :20] += 400.0                                  # brighter pulse
+    x[:, 35:, 40:] *= 1e-3                                   # faint references
+    x[1, 5, 5] = 0.0
+    x32 = x.astype(np.float32)
+    worst = 0.0
+    rels = []
+    for s in range(L - 2):
+        ref = O.unit_tiles(x32, s, w).numerator
+        bound = C.tile_value_bound(x32, s, w)
+        got = _fp32_tile_statistic(x32, s, w).astype(np.float64)
+        ok, ratio = C.values_within_bound(got, ref, bound, slack=1.0)
+        assert ok, (s, ratio)
+        worst = max(worst, ratio)
+        rels.append(np.median(bound / np.abs(ref)))
+    assert np.median(rels) < 1e-5
+    # the cancellation case needs the bound: the plain 1e-5 relative rule fails
+    ok_plain = all(C.values_close(_fp32_tile_statistic(x32, s, w), O.unit_tiles(x32, s, w).numerator,
+                                  rel=1e-7, abs_scale=0.0)[0] for s in range(L - 2))
+    assert not ok_plain

@@ -8,8 +8,8 @@ one host core), and:
 * the library's candidate list is compared with the oracle's own list by the
   parity rule (oracle/compare.py): every component, every peak tile, every
   significance and every image candidate's arg-max pixel;
-* every tile statistic of every unit, every eta and every noise parameter is
-  compared with the oracle's;
+* every tile statistic of every unit (within twice its FP32 rounding bound),
+  every eta and every noise parameter is compared with the oracle's;
 * as a second, independent check of the post-march stages, the oracle's
   z-score, selection and component steps run on the library's own tile values
   and must reproduce its candidates, and the median/MAD must be bit-exact on
@@ -60,10 +60,19 @@ def test_candidates_equal_the_oracle_list(run):
 
 
 def test_every_tile_statistic(run):
+    """Every tile of every unit within twice the FP32 rounding bound of the
+    tile arithmetic (oracle/compare.py: tile_value_bound; where the two
+    differences of a pixel nearly cancel in Delta, e.g. a pulse in the middle
+    snapshot, the bound is relative to the differences, not to Delta)."""
     res, x, truth, det = run
     ref = np.stack([u.numerator for u in det.units])
-    ok, worst = C.values_close(res["values"], ref)
-    assert ok, worst
+    worst = 0.0
+    for s in range(ref.shape[0]):
+        bound = C.tile_value_bound(x, s, W)
+        ok, ratio = C.values_within_bound(res["values"][s], ref[s], bound)
+        assert ok, (s, ratio)
+        worst = max(worst, ratio)
+    print(f"largest error / FP32 bound over all tiles: {worst:.3f}")
     assert res["M"] == det.M
     # the pulsars' tiles are among the compared ones (not only quiet sky)
     for (px, py, *_r) in truth.pulsed:

@@ -296,8 +296,7 @@ FITRIG_API int fitrig_stack_device_ptr(fitrig_plan_t plan, int32_t s, void** ptr
  * frequency branch; a series with a non-finite point gets eta = NaN, bin =
  * -1.  Outputs go to dev_eta[T] and dev_bin[T] (device memory).  `method`
  * picks the transform: FITRIG_SPECTRUM_AUTO (what a plan uses for this n),
- * FITRIG_SPECTRUM_DIRECT (the direct O(n^2) sum; for n > 256 only, where the
- * warp-per-tile direct kernel applies) or FITRIG_SPECTRUM_RADIX (the radix
+ * FITRIG_SPECTRUM_DIRECT (a direct O(n^2) sum) or FITRIG_SPECTRUM_RADIX (the radix
  * FFT; n a power of two from 128 to 4096, EUNSUPPORTED otherwise).  2 <= n
  * <= 4096.  Allocates and frees a twiddle table; work is enqueued on `stream`
  * (a cudaStream_t, 0 = legacy default) and the call synchronises it.

@@ -233,9 +233,17 @@ struct NoiseScratch {
   unsigned long long* invalid;  // device counter of non-finite values seen (may be null)
   int nblk;
   bool allow_cluster = true;    // median/MAD may use the one-launch cluster form
+  // median/MAD of groups up to 2 Mi values: per-group state and key copies of
+  // the split form (noise_split_bytes); null: the bracketed cluster form
+  void* split = nullptr;
+  int64_t split_cap = 0;        // copied keys per group
 };
 size_t noise_scratch_bytes(int groups, int nblk);
 void noise_scratch_carve(void* base, int groups, int nblk, NoiseScratch* s);
+// Scratch of the split median/MAD form for `groups` maps of `stride` values
+// (0 when maps that large take another form).
+size_t noise_split_bytes(int groups, int64_t stride);
+void noise_split_carve(void* base, int groups, int64_t stride, NoiseScratch* s);
 // Group g's values are vals[g*stride .. g*stride + stride); entries that are
 // not finite (including padding) are skipped; n = real entries per group
 // (for the count of invalid ones).

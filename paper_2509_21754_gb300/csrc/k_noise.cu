@@ -1132,6 +1132,546 @@ static cudaError_t launch_medmad_cluster(const float* vals, int groups, int64_t 
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------- MEDMAD, split form
+// For plans, which own scratch memory: the bracketed selection above with its
+// pieces in separate launches, so that the passes over the maps run on every
+// SM at memory bandwidth instead of in one 8-CTA cluster per map:
+//   1. k_split_bracket (one CTA per map): a fixed, evenly spread sample of up
+//      to kSplitRuns runs of 32 values; two histogram rounds over the sample
+//      keys give quantiles A <= B at ranks 1/2 -+ delta, which bracket the
+//      median;
+//   2. k_split_pass (many CTAs per map): counts the finite values and the
+//      keys below A, and copies the keys in [A, B] (gathered in shared memory,
+//      one global reservation per CTA) into the map's copy buffer, counting
+//      them in a 2048-bin histogram over [A, B];
+//   3. k_split_select (one CTA per map): the histogram gives the bin holding
+//      the median's rank; the copies inside that bin are gathered into shared
+//      memory and the median is selected among them exactly; the same sample
+//      as keys of |v - median| (FP32) then brackets the MAD as (m_lo, m_hi);
+//   4. k_split_pass again on the keys of |v - median| (those <= m_lo counted,
+//      those strictly inside the bracket copied) and 5. k_split_select for the
+//      MAD.
+// Every count is exact, so the results are the elements a sort gives; the
+// sample only decides how much is copied.  A map whose bracket misses its
+// rank, whose copies overflow, or whose rank bin holds too many copies is
+// marked (scale -1) and the cluster kernel, launched last, finishes it.
+constexpr int kSplitRuns = 512;
+constexpr int kSplitPool = kSplitRuns * 32;     // sample keys (64 KB of shared memory)
+constexpr int kSplitChunk = 8192;               // values per CTA of a pass
+constexpr int kSplitPassThreads = 256;
+constexpr int kSplitThreads = 512;              // bracket and select kernels
+constexpr int kSplitBins = 2048;
+constexpr int kSplitGather = 8192;              // copies of the rank's bin kept in shared memory
+
+struct SplitState {
+  uint32_t lo, hi;     // copy range of the current pass (inclusive keys)
+  uint32_t nfin;       // finite values (pass 1)
+  uint32_t nbelow;     // keys below lo (current pass)
+  uint32_t ncopy;      // keys copied (current pass; may exceed the capacity)
+  uint32_t stage;      // 0: median pass, 1: MAD pass, 2: finished, 3: left to the cluster form
+  float med;
+  uint32_t nsample;    // finite sample values
+};
+static_assert(sizeof(SplitState) == 32, "SplitState layout");
+
+static int64_t split_cap(int64_t stride) {
+  int64_t c = (stride / 8 + 1023) / 1024 * 1024;
+  c = std::max<int64_t>(c, 8192);
+  return std::min<int64_t>(c, (stride + 1023) / 1024 * 1024);
+}
+
+size_t noise_split_bytes(int groups, int64_t stride) {
+  if (stride > kFastMaxPerGroup || groups > 65535) return 0;
+  const size_t head = ((size_t)groups * (sizeof(SplitState) + kSplitBins * sizeof(unsigned)) + 255) /
+                      256 * 256;
+  return head + (size_t)groups * (size_t)split_cap(stride) * sizeof(uint32_t);
+}
+
+void noise_split_carve(void* base, int groups, int64_t stride, NoiseScratch* s) {
+  s->split = noise_split_bytes(groups, stride) ? base : nullptr;
+  s->split_cap = s->split ? split_cap(stride) : 0;
+}
+
+struct SplitPtrs {
+  SplitState* st;
+  unsigned* hist;      // [groups][kSplitBins]
+  uint32_t* copies;    // [groups][cap]
+};
+
+static SplitPtrs split_ptrs(void* base, int groups) {
+  char* p = static_cast<char*>(base);
+  SplitPtrs r;
+  r.st = reinterpret_cast<SplitState*>(p);
+  r.hist = reinterpret_cast<unsigned*>(p + (size_t)groups * sizeof(SplitState));
+  const size_t head = ((size_t)groups * (sizeof(SplitState) + kSplitBins * sizeof(unsigned)) + 255) /
+                      256 * 256;
+  r.copies = reinterpret_cast<uint32_t*>(p + head);
+  return r;
+}
+
+// Bin width (as a shift) of kSplitBins bins over the inclusive key range
+// [lo, hi] (0 for an empty range, which holds no key).
+__device__ __forceinline__ unsigned split_shift(uint32_t lo, uint32_t hi) {
+  if (hi < lo) return 0;
+  const uint32_t span = hi - lo;   // width - 1
+  unsigned s = 0;
+  while (s < 32 && (span >> s) >= (uint32_t)kSplitBins) ++s;
+  return s;
+}
+
+// Block-wide (kSplitThreads): the bin of h[0..kSplitBins) holding `rank`
+// and the count before it.  Every thread must call it; the result is in
+// every thread.  Returns false when the rank lies beyond the total.
+__device__ bool split_find(const unsigned* h, unsigned long long rank, unsigned* bin,
+                           unsigned long long* below, unsigned long long* wsum,
+                           unsigned long long* found) {
+  constexpr int per = kSplitBins / kSplitThreads;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned c[per];
+  unsigned long long mine = 0;
+#pragma unroll
+  for (int i = 0; i < per; ++i) {
+    c[i] = h[per * tid + i];
+    mine += c[i];
+  }
+  unsigned long long incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  if (tid == 0) found[0] = ~0ull;
+  __syncthreads();
+  unsigned long long before = incl - mine;
+  for (int w = 0; w < warp; ++w) before += wsum[w];
+  if (rank >= before && rank < before + mine) {
+    unsigned long long cum = before;
+#pragma unroll
+    for (int i = 0; i < per; ++i) {
+      if (rank >= cum && rank < cum + c[i]) {
+        found[0] = (unsigned long long)(per * tid + i);
+        found[1] = cum;
+      }
+      cum += c[i];
+    }
+  }
+  __syncthreads();
+  const bool ok = found[0] != ~0ull;
+  *bin = (unsigned)found[0];
+  *below = found[1];
+  __syncthreads();   // found and wsum are reused by the next call
+  return ok;
+}
+
+// The sample: up to kSplitRuns runs of 32 consecutive values, evenly spread
+// over the map (the same runs in every call), as keys of v (mad = false) or
+// of |v - med| in FP32.  A value that is not finite leaves key 0, below every
+// finite key.  Returns the number of finite sample values; kminmax gets their
+// smallest and largest key.  Every thread must call it.
+__device__ unsigned split_sample(const float* v, int64_t stride, bool mad, float med,
+                                 uint32_t* pool, unsigned* slots, uint32_t* kminmax,
+                                 unsigned* nfin_sh) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int nwarps = kSplitThreads / 32;
+  const int64_t runs = (stride + 31) / 32;
+  const int64_t use = runs < kSplitRuns ? runs : kSplitRuns;
+  if (tid == 0) {
+    kminmax[0] = 0xffffffffu;
+    kminmax[1] = 0u;
+    *nfin_sh = 0;
+    *slots = (unsigned)(use * 32);
+  }
+  for (int64_t c = warp; c < use; c += nwarps) {   // every run into L2 first
+    const int64_t i = (c * runs / use) * 32 + lane;
+    if (i < stride) asm volatile("prefetch.global.L2 [%0];" ::"l"((const void*)(v + i)));
+  }
+  __syncthreads();
+  uint32_t lmin = 0xffffffffu, lmax = 0u;
+  unsigned nf = 0;
+  constexpr int B = 8;
+  for (int64_t c0 = warp; c0 < use; c0 += B * nwarps) {
+    float x[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int64_t c = c0 + (int64_t)b * nwarps;
+      const int64_t i = (c * runs / use) * 32 + lane;
+      x[b] = (c < use && i < stride) ? v[i] : NAN;
+    }
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int64_t c = c0 + (int64_t)b * nwarps;
+      if (c >= use) break;
+      uint32_t key = 0;
+      if (finite_bits(x[b])) {
+        key = mad ? f32_key(fabsf(x[b] - med)) : f32_key(x[b]);
+        lmin = min(lmin, key);
+        lmax = max(lmax, key);
+        ++nf;
+      }
+      pool[c * 32 + lane] = key;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    lmin = min(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+    lmax = max(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    nf += __shfl_xor_sync(0xffffffffu, nf, o);
+  }
+  if (lane == 0) {
+    atomicMin(&kminmax[0], lmin);
+    atomicMax(&kminmax[1], lmax);
+    atomicAdd(nfin_sh, nf);
+  }
+  __syncthreads();
+  return *nfin_sh;
+}
+
+// Sample ranks 1/2 -+ delta of ns sample values (delta = 4.5 standard errors of
+// a sample median, a run of 32 values counting as half as informative).
+__device__ __forceinline__ void split_targets(unsigned ns, unsigned long long* t) {
+  const double d = 4.5 * 0.5 / sqrt(0.5 * (double)ns) + 1.0 / (double)ns;
+  const double m = (double)(ns - 1);
+  const double a = floor((0.5 - d) * m), b = ceil((0.5 + d) * m);
+  t[0] = a < 0.0 ? 0ull : (unsigned long long)a;
+  t[1] = b > m ? (unsigned long long)m : (unsigned long long)b;
+}
+
+// Sample quantiles at ranks t[0] <= t[1] among the finite sample keys (range
+// [kmin, kmax]): one histogram over the range, one over the bins holding the
+// two targets; returns the lower edge of t[0]'s final bin and the upper edge
+// of t[1]'s.  Every thread must call it.
+__device__ void split_quantiles(const uint32_t* pool, unsigned slots, uint32_t kmin, uint32_t kmax,
+                                const unsigned long long* t, unsigned* hist,
+                                unsigned long long* wsum, unsigned long long* found,
+                                uint32_t* qlo, uint32_t* qhi) {
+  uint32_t lo = kmin, hi = kmax;
+  unsigned long long r0 = t[0], r1 = t[1];
+  for (int round = 0; round < 2; ++round) {
+    const unsigned sh = split_shift(lo, hi);
+    for (int b = threadIdx.x; b < kSplitBins; b += kSplitThreads) hist[b] = 0;
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < slots; i += kSplitThreads) {
+      const uint32_t k = pool[i];
+      if (k >= lo && k <= hi) atomicAdd(&hist[(k - lo) >> sh], 1u);
+    }
+    __syncthreads();
+    unsigned b0, b1;
+    unsigned long long w0, w1;
+    split_find(hist, r0, &b0, &w0, wsum, found);
+    split_find(hist, r1, &b1, &w1, wsum, found);
+    const uint32_t nlo = lo + (b0 << sh);
+    const unsigned long long top = (unsigned long long)lo + ((unsigned long long)(b1 + 1) << sh) - 1;
+    const uint32_t nhi = top < hi ? (uint32_t)top : hi;
+    r0 -= w0;
+    r1 -= w0;
+    lo = nlo;
+    hi = nhi;
+    __syncthreads();
+  }
+  *qlo = lo;
+  *qhi = hi;
+}
+
+// 1. The median's bracket from the sample; clears the map's counters and
+// histogram.
+__global__ void __launch_bounds__(kSplitThreads) k_split_bracket(const float* __restrict__ vals,
+                                                                 int64_t stride, SplitState* st,
+                                                                 unsigned* hist_g) {
+  extern __shared__ uint32_t spool[];   // kSplitPool
+  __shared__ unsigned hist[kSplitBins];
+  __shared__ unsigned long long wsum[kSplitThreads / 32], found[2];
+  __shared__ uint32_t kmm[2];
+  __shared__ unsigned slots, nfin;
+  const int g = blockIdx.x;
+  const float* v = vals + (size_t)g * stride;
+  unsigned* hg = hist_g + (size_t)g * kSplitBins;
+  for (int b = threadIdx.x; b < kSplitBins; b += kSplitThreads) hg[b] = 0;
+  const unsigned ns = split_sample(v, stride, false, 0.f, spool, &slots, kmm, &nfin);
+  uint32_t A = 1, B = 0;   // empty range when the sample has no finite value
+  if (ns > 0) {
+    unsigned long long t[2];
+    split_targets(ns, t);
+    split_quantiles(spool, slots, kmm[0], kmm[1], t, hist, wsum, found, &A, &B);
+  }
+  if (threadIdx.x == 0) {
+    SplitState s;
+    s.lo = A;
+    s.hi = B;
+    s.nfin = 0;
+    s.nbelow = 0;
+    s.ncopy = 0;
+    s.stage = 0;
+    s.med = 0.f;
+    s.nsample = ns;
+    st[g] = s;
+  }
+}
+
+// 2./4. One chunk of one map: counts and copies (see above).
+template <bool VEC, bool MAD>
+__global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* __restrict__ vals,
+                                                                  int64_t stride, SplitState* st,
+                                                                  unsigned* hist_g,
+                                                                  uint32_t* copies, int64_t cap) {
+  __shared__ uint32_t buf[kSplitChunk];
+  __shared__ unsigned nbuf, base_sh;
+  __shared__ unsigned red[2][kSplitPassThreads / 32];
+  const int g = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const SplitState s = st[g];
+  if (s.stage != (MAD ? 1u : 0u)) return;   // finished, degenerate or handed on
+  const int64_t c0 = (int64_t)blockIdx.x * kSplitChunk;
+  if (c0 >= stride) return;
+  const int64_t c1 = c0 + kSplitChunk < stride ? c0 + kSplitChunk : stride;
+  const uint32_t lo = s.lo, hi = s.hi;
+  const unsigned sh = split_shift(lo, hi);
+  const float med = s.med;
+  const float* v = vals + (size_t)g * stride;
+  if (tid == 0) nbuf = 0;
+  __syncthreads();
+  unsigned below = 0, fin = 0;
+  auto take = [&](float x) {
+    const bool f = finite_bits(x);
+    const uint32_t key = f ? (MAD ? f32_key(fabsf(x - med)) : f32_key(x)) : kNoKey;
+    fin += f;
+    below += key < lo;
+    const bool cp = key >= lo && key <= hi;   // never a non-finite value (hi < kNoKey)
+    const unsigned m = __ballot_sync(0xffffffffu, cp);
+    if (m) {
+      unsigned b = 0;
+      if (lane == __ffs(m) - 1) b = atomicAdd(&nbuf, (unsigned)__popc(m));
+      b = __shfl_sync(0xffffffffu, b, __ffs(m) - 1);
+      if (cp) buf[b + __popc(m & ((1u << lane) - 1u))] = key;
+    }
+  };
+  if (VEC) {
+    // chunk starts are multiples of 8192 values and stride % 4 == 0
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    constexpr int U = kSplitChunk / 4 / kSplitPassThreads;   // float4 per thread
+    float4 q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = c0 / 4 + (int64_t)u * kSplitPassThreads + tid;
+      q[u] = i < c1 / 4 ? v4[i] : make_float4(NAN, NAN, NAN, NAN);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      take(q[u].x);
+      take(q[u].y);
+      take(q[u].z);
+      take(q[u].w);
+    }
+  } else {
+    for (int64_t b = c0; b < c1; b += kSplitPassThreads) {
+      const int64_t i = b + tid;
+      take(i < c1 ? v[i] : NAN);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    below += __shfl_xor_sync(0xffffffffu, below, o);
+    fin += __shfl_xor_sync(0xffffffffu, fin, o);
+  }
+  if (lane == 0) {
+    red[0][warp] = below;
+    red[1][warp] = fin;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned tb = 0, tf = 0;
+    for (int w = 0; w < kSplitPassThreads / 32; ++w) {
+      tb += red[0][w];
+      tf += red[1][w];
+    }
+    if (tb) atomicAdd(&st[g].nbelow, tb);
+    if (!MAD && tf) atomicAdd(&st[g].nfin, tf);
+    base_sh = nbuf ? atomicAdd(&st[g].ncopy, nbuf) : 0u;
+  }
+  __syncthreads();
+  const unsigned nb = nbuf, base = base_sh;
+  if ((int64_t)base + nb <= cap) {
+    uint32_t* out = copies + (size_t)g * cap + base;
+    unsigned* hg = hist_g + (size_t)g * kSplitBins;
+    for (unsigned j = tid; j < nb; j += kSplitPassThreads) {
+      const uint32_t k = buf[j];
+      out[j] = k;
+      atomicAdd(&hg[(k - lo) >> sh], 1u);
+    }
+  }
+}
+
+// 3./5. Exact selection among the copies; after the median, the MAD's bracket.
+template <bool MAD>
+__global__ void __launch_bounds__(kSplitThreads) k_split_select(const float* __restrict__ vals,
+                                                                int64_t stride, int64_t n,
+                                                                SplitState* st, unsigned* hist_g,
+                                                                const uint32_t* __restrict__ copies,
+                                                                int64_t cap, double* cs,
+                                                                unsigned long long* invalid) {
+  extern __shared__ uint32_t spool[];   // kSplitPool (the sample, median stage), the gathered bin
+  __shared__ unsigned hist[kSplitBins];
+  __shared__ unsigned long long wsum[kSplitThreads / 32], found[2];
+  __shared__ uint32_t kmm[2];
+  __shared__ unsigned slots, nfin_sh, ngather;
+  const int g = blockIdx.x;
+  const int tid = threadIdx.x;
+  const SplitState s = st[g];
+  if (s.stage != (MAD ? 1u : 0u)) return;
+  unsigned* hg = hist_g + (size_t)g * kSplitBins;
+  auto hand_on = [&]() {   // the cluster kernel computes this map
+    if (tid == 0) {
+      cs[2 * g + 1] = -1.0;
+      st[g].stage = 3;
+    }
+  };
+  if (!MAD && s.nfin == 0) {
+    if (tid == 0) {
+      cs[2 * g] = NAN;
+      cs[2 * g + 1] = 0.0;
+      if (invalid && n > 0) atomicAdd(invalid, (unsigned long long)n);
+      st[g].stage = 2;
+    }
+    return;
+  }
+  const unsigned long long R = (s.nfin - 1) / 2;
+  if (s.nsample == 0 || (int64_t)s.ncopy > cap || R < s.nbelow ||
+      R >= (unsigned long long)s.nbelow + s.ncopy) {
+    hand_on();
+    return;
+  }
+  // the bin of the pass histogram holding the rank, then its copies
+  unsigned long long rank = R - s.nbelow;
+  const unsigned sh = split_shift(s.lo, s.hi);
+  for (int b = tid; b < kSplitBins; b += kSplitThreads) hist[b] = hg[b];
+  __syncthreads();
+  unsigned bin;
+  unsigned long long below;
+  if (!split_find(hist, rank, &bin, &below, wsum, found)) {
+    hand_on();
+    return;
+  }
+  rank -= below;
+  uint32_t lo = s.lo + (bin << sh);
+  const unsigned long long top = (unsigned long long)lo + (1ull << sh) - 1;
+  uint32_t hi = top < s.hi ? (uint32_t)top : s.hi;
+  if (tid == 0) ngather = 0;
+  __syncthreads();
+  const uint32_t* cp = copies + (size_t)g * cap;
+  constexpr int GB = 8;   // loads in flight per thread
+  for (unsigned i0 = tid; i0 < s.ncopy; i0 += GB * kSplitThreads) {
+    uint32_t k[GB];
+#pragma unroll
+    for (int b = 0; b < GB; ++b) {
+      const unsigned i = i0 + b * kSplitThreads;
+      k[b] = i < s.ncopy ? cp[i] : 1u;
+    }
+#pragma unroll
+    for (int b = 0; b < GB; ++b) {
+      const unsigned i = i0 + b * kSplitThreads;
+      if (i < s.ncopy && k[b] >= lo && k[b] <= hi) {
+        const unsigned j = atomicAdd(&ngather, 1u);
+        if (j < kSplitGather) spool[j] = k[b];
+      }
+    }
+  }
+  __syncthreads();
+  const unsigned ng = ngather;
+  if (ng > kSplitGather) {
+    hand_on();
+    return;
+  }
+  // rounds of histograms over the gathered keys until one key remains
+  while (lo < hi) {
+    const unsigned s2 = split_shift(lo, hi);
+    for (int b = tid; b < kSplitBins; b += kSplitThreads) hist[b] = 0;
+    __syncthreads();
+    for (unsigned i = tid; i < ng; i += kSplitThreads) {
+      const uint32_t k = spool[i];
+      if (k >= lo && k <= hi) atomicAdd(&hist[(k - lo) >> s2], 1u);
+    }
+    __syncthreads();
+    if (!split_find(hist, rank, &bin, &below, wsum, found)) {
+      hand_on();
+      return;
+    }
+    rank -= below;
+    const uint32_t nlo = lo + (bin << s2);
+    const unsigned long long t2 = (unsigned long long)nlo + (1ull << s2) - 1;
+    hi = t2 < hi ? (uint32_t)t2 : hi;
+    lo = nlo;
+  }
+  const float val = f32_from_key(lo);
+  if (MAD) {
+    if (tid == 0) {
+      cs[2 * g] = (double)s.med;
+      cs[2 * g + 1] = kMadToSigma * (double)val;
+      if (invalid && (int64_t)s.nfin < n) atomicAdd(invalid, (unsigned long long)(n - (int64_t)s.nfin));
+      st[g].stage = 2;
+    }
+    return;
+  }
+  // the MAD's bracket from the same sample as keys of |v - median|
+  __syncthreads();   // the gathered keys are replaced by the sample
+  const float* v = vals + (size_t)g * stride;
+  const unsigned ns = split_sample(v, stride, true, val, spool, &slots, kmm, &nfin_sh);
+  uint32_t mlo = 0, mhi = 0;
+  if (ns > 0) {
+    unsigned long long t[2];
+    split_targets(ns, t);
+    split_quantiles(spool, slots, kmm[0], kmm[1], t, hist, wsum, found, &mlo, &mhi);
+  }
+  if (ns == 0 || mhi <= mlo + 1u) {   // no key strictly inside the bracket
+    hand_on();
+    return;
+  }
+  for (int b = tid; b < kSplitBins; b += kSplitThreads) hg[b] = 0;
+  if (tid == 0) {
+    SplitState n2 = s;
+    n2.lo = mlo + 1;       // keys <= m_lo are counted below
+    n2.hi = mhi - 1;       // keys strictly inside the bracket are copied
+    n2.nbelow = 0;
+    n2.ncopy = 0;
+    n2.stage = 1;
+    n2.med = val;
+    st[g] = n2;
+  }
+}
+
+template <bool VEC>
+static cudaError_t launch_split_t(const float* vals, int groups, int64_t stride, int64_t n,
+                                  const NoiseScratch& ns, double* cs, cudaStream_t st) {
+  const SplitPtrs sp = split_ptrs(ns.split, groups);
+  const size_t dyn = (size_t)kSplitPool * sizeof(uint32_t);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_split_bracket,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_split_select<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)dyn);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_split_select<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)dyn);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const dim3 pgrid((unsigned)((stride + kSplitChunk - 1) / kSplitChunk), (unsigned)groups);
+  k_split_bracket<<<groups, kSplitThreads, dyn, st>>>(vals, stride, sp.st, sp.hist);
+  k_split_pass<VEC, false><<<pgrid, kSplitPassThreads, 0, st>>>(vals, stride, sp.st, sp.hist,
+                                                                 sp.copies, ns.split_cap);
+  k_split_select<false><<<groups, kSplitThreads, dyn, st>>>(vals, stride, n, sp.st, sp.hist,
+                                                            sp.copies, ns.split_cap, cs,
+                                                            ns.invalid);
+  k_split_pass<VEC, true><<<pgrid, kSplitPassThreads, 0, st>>>(vals, stride, sp.st, sp.hist,
+                                                                sp.copies, ns.split_cap);
+  k_split_select<true><<<groups, kSplitThreads, dyn, st>>>(vals, stride, n, sp.st, sp.hist,
+                                                           sp.copies, ns.split_cap, cs,
+                                                           ns.invalid);
+  count_launches(5);
+  return cudaGetLastError();
+}
+
 static int noise_blocks(int groups, const NoiseScratch& s) {
   (void)groups;
   return s.nblk;
@@ -1158,6 +1698,15 @@ cudaError_t launch_noise(const float* vals, int groups, int64_t stride, int64_t 
     return cudaGetLastError();
   }
   if (mode != FITRIG_NOISE_MEDMAD) return cudaErrorInvalidValue;
+  // groups of up to 2 Mi values with split scratch: the split form, then the
+  // cluster form for any group it leaves
+  if (s.split && s.allow_cluster && stride <= kFastMaxPerGroup && groups <= 65535 &&
+      stride <= (int64_t)INT32_MAX) {
+    const cudaError_t e = vec ? launch_split_t<true>(vals, groups, stride, n, s, cs, st)
+                              : launch_split_t<false>(vals, groups, stride, n, s, cs, st);
+    if (e != cudaSuccess) return e;
+    return launch_medmad_cluster(vals, groups, stride, n, vec, cs, s.invalid, 1, st);
+  }
   // groups of moderate size: one cluster per group, all passes in one launch
   if (stride <= kClusterMaxPerGroup && s.allow_cluster) {
     if (stride > kFastMaxPerGroup)

@@ -77,7 +77,7 @@ Fn driver_fn(const char* name, int version) {
 // (cudaSetDevice makes the device's primary context current and initialises
 // it; it allocates nothing).
 int current_context_id(int dev, unsigned long long* id) {
-  static CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent", 3020);
+  static CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent", 12000);
   static CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId", 12000);
   if (!get_current || !get_id) return FITRIG_EUNSUPPORTED;
   if (cudaSetDevice(dev) != cudaSuccess) {

@@ -109,6 +109,7 @@ struct fitrig_plan_s {
   double* d_cs = nullptr;        // (units + 1) x (centre, scale)
   float* d_thr = nullptr;        // units + 1
   void* d_noise = nullptr;
+  void* d_split = nullptr;       // split median/MAD scratch (NoiseScratch::split)
   NoiseScratch ns_img{}, ns_freq{};
   void* d_sel = nullptr;
   SelectScratch sel{};
@@ -173,7 +174,7 @@ static void drop_graph(fitrig_plan_t p);
 static void free_all(fitrig_plan_t p) {
   drop_graph(p);
   void* ptrs[] = {p->d_stack, p->d_vp,  p->d_small, p->d_invalid,  p->d_cs, p->d_arg, p->d_inv,
-                  p->d_thr,   p->d_noise, p->d_sel, p->d_cand,     p->d_cand_tmp,
+                  p->d_thr,   p->d_noise, p->d_split, p->d_sel, p->d_cand, p->d_cand_tmp,
                   p->d_bin,   p->d_tw,  p->d_staging, p->d_report, p->d_accum,
                   p->d_hist,  p->d_hwts, p->d_htw,
                   p->d_smax,  p->d_mrun, p->d_wts};   // d_eta lives inside d_vp
@@ -434,6 +435,16 @@ static int allocate(fitrig_plan_t p) {
   noise_scratch_carve(p->d_noise, 1, nblk_freq, &p->ns_freq);
   p->ns_img.invalid = p->d_invalid;
   p->ns_freq.invalid = p->d_invalid;
+  if (p->noise == FITRIG_NOISE_MEDMAD) {
+    // the split median/MAD form; the image maps (with eta) and the eta-only
+    // estimate never run at once, so they share one buffer
+    const size_t sb = std::max(noise_split_bytes(U + 1, p->vstride), noise_split_bytes(1, p->vstride));
+    if (sb > 0) {
+      CK(dmalloc(p, &p->d_split, sb));
+      noise_split_carve(p->d_split, U + 1, p->vstride, &p->ns_img);
+      noise_split_carve(p->d_split, 1, p->vstride, &p->ns_freq);
+    }
+  }
   {
     const int rc = alloc_select(p);
     if (rc != FITRIG_OK) return rc;
@@ -1279,7 +1290,6 @@ FITRIG_API int fitrig_spectrum_map(const float* dev_cube, int32_t n, int64_t T, 
   if (method < FITRIG_SPECTRUM_AUTO || method > FITRIG_SPECTRUM_RADIX) return FITRIG_EINVAL;
   const bool pow2 = n >= 128 && (n & (n - 1)) == 0;
   if (method == FITRIG_SPECTRUM_RADIX && !pow2) return FITRIG_EUNSUPPORTED;
-  if (method == FITRIG_SPECTRUM_DIRECT && n <= 256) return FITRIG_EUNSUPPORTED;
   if (T > (int64_t)UINT32_MAX) return FITRIG_EUNSUPPORTED;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const std::vector<float2> tw = spectrum_twiddles(n);
@@ -1326,9 +1336,12 @@ FITRIG_API int fitrig_threshold_map(const float* dev_map, int64_t n, double nsig
   void* scratch = nullptr;
   const size_t nb = (noise_scratch_bytes(1, nblk) + 255) / 256 * 256;   // keeps the tail 8-byte aligned
   const size_t extra = 256 + sizeof(int) * (nblk * 8 + 2) + sizeof(long long) * 2 + 64;
-  CK(cudaMalloc(&scratch, nb + extra));
+  const size_t ntail = (extra + 255) / 256 * 256;
+  const size_t nsplit = noise_mode == FITRIG_NOISE_MEDMAD ? noise_split_bytes(1, n) : 0;
+  CK(cudaMalloc(&scratch, nb + ntail + nsplit));
   NoiseScratch ns;
   noise_scratch_carve(scratch, 1, nblk, &ns);
+  if (nsplit) noise_split_carve(static_cast<char*>(scratch) + nb + ntail, 1, n, &ns);
   char* tail = static_cast<char*>(scratch) + nb;
   double* cs = reinterpret_cast<double*>(tail);
   float* thr = reinterpret_cast<float*>(tail + 16);

@@ -136,4 +136,3 @@ def test_spectrum_map_checks_its_arguments_without_a_device(lib):
     assert L.fitrig_spectrum_map(p, 256, 8, 8, 1, p, p, 3, 0, None) == F.EINVAL       # method
     assert L.fitrig_spectrum_map(p, 300, 8, 8, 1, p, p, F.SPECTRUM_RADIX, 0, None) == F.EUNSUPPORTED
     assert L.fitrig_spectrum_map(p, 64, 8, 8, 1, p, p, F.SPECTRUM_RADIX, 0, None) == F.EUNSUPPORTED
-    assert L.fitrig_spectrum_map(p, 128, 8, 8, 1, p, p, F.SPECTRUM_DIRECT, 0, None) == F.EUNSUPPORTED

@@ -291,6 +291,38 @@ cudaError_t launch_clamp_count(int* n, int cap, unsigned* status, cudaStream_t s
 cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
                               unsigned* status, cudaStream_t st);
 
+// Block-tiled selection and components: each CTA takes a kBlkY x kBlkX block
+// of one group's tile map.  Components that touch a block edge are merged
+// through a global union-find over "boundary components"; every peak ends up
+// as a bit in a dense per-group bitmap, compacted in (group, t) order.
+constexpr int kBlkY = 32, kBlkX = 64;
+struct BlockScratch {
+  int* glab;                  // [groups * stride] boundary-component id of edge tiles (never cleared)
+  int* bpar;                  // [cap] union-find parents of boundary components
+  int* bgrp;                  // [cap] group of each boundary component
+  unsigned long long* bkey;   // [cap] block-local peak key (value key << 32 | ~t)
+  unsigned long long* rkey;   // [cap] merged peak key (roots)
+  uint32_t* pbits;            // [groups][Ty][words] peak bitmap
+  int* counters;              // [0] boundary components, [1] selected tiles, [2] peaks
+  int64_t cap;                // boundary components one detect can hold
+  int words;                  // bitmap words per tile row
+  int nblk;                   // grid of the ordered compaction
+  int* blkcnt;                // [nblk]
+  int* blkoff;                // [nblk + 1]
+};
+// Bytes of BlockScratch for `groups` maps of Ty x Tx tiles at group stride
+// `stride` (carved by block_scratch_carve in the same order).
+size_t block_scratch_bytes(int groups, int Tx, int Ty, int64_t stride);
+void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride, BlockScratch* b);
+// Threshold (v > thr[g]), 8-connected components and their peaks over groups
+// x Ty x Tx tiles at vals[g * stride + ty * Tx + tx]; writes the peaks, in
+// (group, t) order, as SelItem{g, t, v} to peaks[0..min(n, cap)) with n in
+// b.counters[2]; flags kErrCapacity (and *want = selected count) when more
+// than `cap` tiles are selected.
+cudaError_t launch_block_select(const float* vals, int groups, int64_t stride, int Tx, int Ty,
+                                const float* thr, const BlockScratch& b, SelItem* peaks,
+                                int64_t cap, unsigned* status, unsigned* want, cudaStream_t st);
+
 struct CandArgs {
   int nx, ny, w, Tx, Ty;
   int64_t T;
@@ -320,6 +352,10 @@ struct CandArgs {
 cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, int* base,
                                    fitrig_candidate* tmp, unsigned* status, cudaStream_t st);
 
+// The candidates of an ordered peak list (launch_block_select), as
+// launch_emit_candidates does from its own list.
+cudaError_t launch_emit_peaks(const CandArgs& a, const SelItem* peaks, const int* npeak,
+                              int* base, fitrig_candidate* tmp, cudaStream_t st);
 cudaError_t launch_export_candidates(const fitrig_candidate* src, const int* n,
                                      fitrig_candidate* dst, int cap, cudaStream_t st);
 

@@ -405,6 +405,413 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- block-tiled components
+// A CTA thresholds one kBlkY x kBlkX block of one group's tile map (with a
+// one-tile halo), labels the block's 8-connected components with a
+// shared-memory union-find, and finds each component's peak (largest value,
+// smallest tile index on ties) as the largest key (value key << 32) | ~t.  A
+// component that reaches a selected tile outside the block is a boundary
+// component: it gets a global id, its edge tiles get that id in a dense label
+// map, and a second kernel unites the ids of selected neighbours across block
+// edges.  Every other component's peak is set in the block's bits of the
+// dense peak bitmap directly; the merged boundary components' peaks are
+// OR'ed in afterwards, and an ordered compaction of the bitmap gives the peak
+// list in (group, t) order.
+constexpr int kBlkT = kBlkY * kBlkX;
+constexpr int kBlkThreads = 256;
+constexpr int kBlkPer = kBlkT / kBlkThreads;
+constexpr int kBlkRing = 2 * kBlkX + 2 * (kBlkY - 2);   // edge tiles of a block
+
+__device__ __forceinline__ int find_s(const int* par, int x) {
+  const volatile int* p = par;
+  int y = p[x];
+  while (y != x) {
+    x = y;
+    y = p[x];
+  }
+  return x;
+}
+
+// Shared-memory union (roots always link the larger index to the smaller).
+__device__ void unite_s(int* par, int a, int b, unsigned* status) {
+  for (int it = 0; it < (1 << 16); ++it) {
+    a = find_s(par, a);
+    b = find_s(par, b);
+    if (a == b) return;
+    const int hi = a > b ? a : b, lo = a > b ? b : a;
+    const int old = atomicCAS(&par[hi], hi, lo);
+    if (old == hi) return;
+    a = old;
+    b = lo;
+  }
+  atomicOr(status, kErrCcLimit);
+}
+
+__device__ __forceinline__ int find_g(const int* par, int x) {
+  const volatile int* p = par;
+  int y = p[x];
+  while (y != x) {
+    x = y;
+    y = p[x];
+  }
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long peak_key(float v, uint32_t t) {
+  return ((unsigned long long)f32_key(v) << 32) | (unsigned long long)(0xffffffffu - t);
+}
+
+// The ring position r (0 <= r < kBlkRing) of a block's edge as (ly, lx).
+__device__ __forceinline__ void ring_pos(int r, int* ly, int* lx) {
+  if (r < kBlkX) {
+    *ly = 0;
+    *lx = r;
+  } else if (r < 2 * kBlkX) {
+    *ly = kBlkY - 1;
+    *lx = r - kBlkX;
+  } else {
+    const int q = r - 2 * kBlkX;   // the side columns without the corners
+    *ly = 1 + (q >> 1);
+    *lx = (q & 1) ? kBlkX - 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict__ vals,
+                                                        int64_t stride, int Tx, int Ty,
+                                                        const float* __restrict__ thr,
+                                                        BlockScratch b, unsigned* status) {
+  __shared__ uint8_t msk[kBlkY + 2][kBlkX + 2];
+  __shared__ int par[kBlkT];
+  __shared__ float val[kBlkT];
+  __shared__ unsigned long long pkey[kBlkT];
+  __shared__ uint8_t bnd[kBlkT];
+  __shared__ int bid[kBlkT];
+  __shared__ uint32_t pw[kBlkY][kBlkX / 32];
+  __shared__ int nsel_sh;
+  const int g = blockIdx.z;
+  const int tid = threadIdx.x;
+  const int tx0 = blockIdx.x * kBlkX, ty0 = blockIdx.y * kBlkY;
+  const float th = thr[g];
+  const float* v = vals + (size_t)g * stride;
+  if (tid == 0) nsel_sh = 0;
+  for (int i = tid; i < kBlkY * (kBlkX / 32); i += kBlkThreads) (&pw[0][0])[i] = 0u;
+  // 1. the mask with its halo, and the block's values
+  for (int i = tid; i < (kBlkY + 2) * (kBlkX + 2); i += kBlkThreads) {
+    const int ly = i / (kBlkX + 2) - 1, lx = i - (i / (kBlkX + 2)) * (kBlkX + 2) - 1;
+    const int ty = ty0 + ly, tx = tx0 + lx;
+    float x = 0.f;
+    bool sel = false;
+    if (ty >= 0 && ty < Ty && tx >= 0 && tx < Tx) {
+      x = v[(int64_t)ty * Tx + tx];
+      sel = x > th;
+    }
+    msk[ly + 1][lx + 1] = sel;
+    if (ly >= 0 && ly < kBlkY && lx >= 0 && lx < kBlkX) {
+      const int li = ly * kBlkX + lx;
+      val[li] = x;
+      par[li] = sel ? li : -1;
+      pkey[li] = 0ull;
+      bnd[li] = 0;
+    }
+  }
+  __syncthreads();
+  // 2. unions inside the block (left, up-left, up, up-right)
+  int mine = 0;
+  for (int li = tid; li < kBlkT; li += kBlkThreads) {
+    const int ly = li / kBlkX, lx = li - (li / kBlkX) * kBlkX;
+    if (!msk[ly + 1][lx + 1]) continue;
+    ++mine;
+    if (lx > 0 && msk[ly + 1][lx]) unite_s(par, li, li - 1, status);
+    if (ly > 0) {
+      if (msk[ly][lx + 1]) unite_s(par, li, li - kBlkX, status);
+      if (lx > 0 && msk[ly][lx]) unite_s(par, li, li - kBlkX - 1, status);
+      if (lx + 1 < kBlkX && msk[ly][lx + 2]) unite_s(par, li, li - kBlkX + 1, status);
+    }
+  }
+  __syncthreads();
+  // 3. roots (read-only finds, then one write each), boundary flags, peak keys
+  int root[kBlkPer];
+#pragma unroll
+  for (int k = 0; k < kBlkPer; ++k) {
+    const int li = tid + k * kBlkThreads;
+    root[k] = par[li] >= 0 ? find_s(par, li) : -1;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kBlkPer; ++k) {
+    const int li = tid + k * kBlkThreads;
+    if (root[k] < 0) continue;
+    par[li] = root[k];
+    const int ly = li / kBlkX, lx = li - (li / kBlkX) * kBlkX;
+    const uint32_t t = (uint32_t)((ty0 + ly) * Tx + (tx0 + lx));
+    atomicMax(&pkey[root[k]], peak_key(val[li], t));
+    if (ly == 0 || ly == kBlkY - 1 || lx == 0 || lx == kBlkX - 1) {
+      bool out = false;
+#pragma unroll
+      for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int ny = ly + dy, nx = lx + dx;
+          const bool outside = ny < 0 || ny >= kBlkY || nx < 0 || nx >= kBlkX;
+          out = out || (outside && msk[ny + 1][nx + 1]);
+        }
+      if (out) bnd[root[k]] = 1;
+    }
+  }
+  __syncthreads();
+  // 4. roots: an interior component's peak bit; a boundary component's id
+#pragma unroll
+  for (int k = 0; k < kBlkPer; ++k) {
+    const int li = tid + k * kBlkThreads;
+    if (root[k] != li) continue;
+    const unsigned long long key = pkey[li];
+    if (!bnd[li]) {
+      const uint32_t t = 0xffffffffu - (uint32_t)key;
+      const int pty = (int)(t / (uint32_t)Tx), ptx = (int)(t - (uint32_t)pty * (uint32_t)Tx);
+      const int ply = pty - ty0, plx = ptx - tx0;
+      atomicOr(&pw[ply][plx >> 5], 1u << (plx & 31));
+    } else {
+      const int id = atomicAdd(&b.counters[0], 1);
+      if (id < b.cap) {
+        b.bpar[id] = id;
+        b.bgrp[id] = g;
+        b.bkey[id] = key;
+        b.rkey[id] = key;
+        bid[li] = id;
+      } else {
+        bid[li] = -1;
+        atomicOr(status, kErrCapacity);
+      }
+    }
+  }
+  __syncthreads();
+  // 5. labels of the edge tiles of boundary components; the block's peak
+  // words (a row of the block covers kBlkX / 32 whole words); the count
+  for (int r = tid; r < kBlkRing; r += kBlkThreads) {
+    int ly, lx;
+    ring_pos(r, &ly, &lx);
+    const int li = ly * kBlkX + lx;
+    if (!msk[ly + 1][lx + 1] || !bnd[par[li]]) continue;
+    b.glab[(size_t)g * stride + (int64_t)(ty0 + ly) * Tx + (tx0 + lx)] = bid[par[li]];
+  }
+  for (int i = tid; i < kBlkY * (kBlkX / 32); i += kBlkThreads) {
+    const int ly = i / (kBlkX / 32), wx = i - ly * (kBlkX / 32);
+    const int ty = ty0 + ly, w = tx0 / 32 + wx;
+    if (ty < Ty && w < b.words) b.pbits[((size_t)g * Ty + ty) * b.words + w] = pw[ly][wx];
+  }
+  for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((tid & 31) == 0 && mine) atomicAdd(&nsel_sh, mine);
+  __syncthreads();
+  if (tid == 0 && nsel_sh) atomicAdd(&b.counters[1], nsel_sh);
+}
+
+// Unions of boundary components across block edges: every selected edge tile
+// with a selected neighbour outside its block joins the two ids.
+__global__ void __launch_bounds__(kBlkThreads) k_blk_merge(const float* __restrict__ vals,
+                                                           int64_t stride, int Tx, int Ty,
+                                                           const float* __restrict__ thr,
+                                                           BlockScratch b, unsigned* status) {
+  const int g = blockIdx.z;
+  const int tx0 = blockIdx.x * kBlkX, ty0 = blockIdx.y * kBlkY;
+  const float th = thr[g];
+  const float* v = vals + (size_t)g * stride;
+  const int* lab = b.glab + (size_t)g * stride;
+  // ids of this detect only (the label map is never cleared; every label read
+  // here was written by k_blk_cc, and the range check keeps it so)
+  const int nid = min(b.counters[0], (int)b.cap);
+  for (int r = threadIdx.x; r < kBlkRing; r += kBlkThreads) {
+    int ly, lx;
+    ring_pos(r, &ly, &lx);
+    const int ty = ty0 + ly, tx = tx0 + lx;
+    if (ty >= Ty || tx >= Tx) continue;
+    const int64_t t = (int64_t)ty * Tx + tx;
+    if (!(v[t] > th)) continue;
+    const int me = lab[t];
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ny = ly + dy, nx = lx + dx;
+        if (ny >= 0 && ny < kBlkY && nx >= 0 && nx < kBlkX) continue;   // inside the block
+        const int gy = ty + dy, gx = tx + dx;
+        if (gy < 0 || gy >= Ty || gx < 0 || gx >= Tx) continue;
+        const int64_t tn = (int64_t)gy * Tx + gx;
+        if (!(v[tn] > th)) continue;
+        const int other = lab[tn];
+        if (me >= 0 && me < nid && other >= 0 && other < nid) unite(b.bpar, me, other, status);
+      }
+  }
+}
+
+// Merged peak keys: every boundary component raises its root's key.
+__global__ void k_blk_resolve(BlockScratch b) {
+  const int n = min(b.counters[0], (int)b.cap);
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+    const int r = find_g(b.bpar, id);
+    if (r != id) atomicMax(&b.rkey[r], b.bkey[id]);
+  }
+}
+
+// Each merged component's peak bit.
+__global__ void k_blk_mark(int Tx, int Ty, BlockScratch b) {
+  const int n = min(b.counters[0], (int)b.cap);
+  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+    if (b.bpar[id] != id) continue;   // roots never change after the unions
+    const uint32_t t = 0xffffffffu - (uint32_t)b.rkey[id];
+    const int ty = (int)(t / (uint32_t)Tx), tx = (int)(t - (uint32_t)ty * (uint32_t)Tx);
+    atomicOr(&b.pbits[((size_t)b.bgrp[id] * Ty + ty) * b.words + (tx >> 5)], 1u << (tx & 31));
+  }
+}
+
+// Ordered compaction of the peak bitmap: per-block counts, then the writes.
+__global__ void __launch_bounds__(kSelThreads) k_pbits_count(int64_t nwords, BlockScratch b) {
+  __shared__ int wsum[kSelThreads / 32];
+  int64_t lo, hi;
+  chunk_range(nwords, b.nblk, blockIdx.x, &lo, &hi);
+  int cnt = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += kSelThreads) cnt += __popc(b.pbits[i]);
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kSelThreads / 32; ++w) t += wsum[w];
+    b.blkcnt[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_pbits_write(int64_t nwords, int Tx, int Ty,
+                                                             const float* __restrict__ vals,
+                                                             int64_t stride, BlockScratch b,
+                                                             SelItem* peaks, int64_t cap) {
+  __shared__ int wcnt[kSelThreads / 32];
+  int64_t lo, hi;
+  chunk_range(nwords, b.nblk, blockIdx.x, &lo, &hi);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t run = b.blkoff[blockIdx.x];
+  const int64_t per_group = (int64_t)Ty * b.words;
+  for (int64_t base = lo; base < hi; base += kSelThreads) {
+    const int64_t i = base + threadIdx.x;
+    const uint32_t w = i < hi ? b.pbits[i] : 0u;
+    const int c = __popc(w);
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wcnt[warp] = incl;
+    __syncthreads();
+    int before = 0, tile = 0;
+    for (int k = 0; k < kSelThreads / 32; ++k) {
+      before += k < warp ? wcnt[k] : 0;
+      tile += wcnt[k];
+    }
+    if (w) {
+      const int g = (int)(i / per_group);
+      const int64_t r = i - (int64_t)g * per_group;
+      const int ty = (int)(r / b.words), wx = (int)(r - (int64_t)ty * b.words);
+      int64_t pos = run + before + incl - c;
+      uint32_t m = w;
+      while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        const int t = ty * Tx + wx * 32 + bit;
+        if (pos < cap) peaks[pos] = SelItem{g, t, vals[(size_t)g * stride + t]};
+        ++pos;
+      }
+    }
+    run += tile;
+    __syncthreads();
+  }
+}
+
+__global__ void k_blk_check(BlockScratch b, int64_t cap, unsigned* status, unsigned* want) {
+  const int n = b.counters[1];
+  if ((int64_t)n > cap) {
+    atomicOr(status, kErrCapacity);
+    if (want) atomicMax(want, (unsigned)n);
+  }
+}
+
+static int64_t block_edge_tiles(int Tx, int Ty) {
+  // edge tiles over all blocks of one map (an exact upper bound on boundary
+  // components: each owns at least one edge tile)
+  int64_t e = 0;
+  for (int by = 0; by < (Ty + kBlkY - 1) / kBlkY; ++by) {
+    const int h = std::min(kBlkY, Ty - by * kBlkY);
+    for (int bx = 0; bx < (Tx + kBlkX - 1) / kBlkX; ++bx) {
+      const int w = std::min(kBlkX, Tx - bx * kBlkX);
+      e += (h <= 2 || w <= 2) ? (int64_t)h * w : 2 * (int64_t)(h + w) - 4;
+    }
+  }
+  return e;
+}
+
+static int block_words(int Tx) { return (Tx + 31) / 32; }
+
+size_t block_scratch_bytes(int groups, int Tx, int Ty, int64_t stride) {
+  const int64_t cap = std::max<int64_t>(1, block_edge_tiles(Tx, Ty) * groups);
+  const int64_t nw = (int64_t)groups * Ty * block_words(Tx);
+  const int nblk = 152 * 8;
+  size_t bytes = 0;
+  auto add = [&](size_t n) { bytes += (n + 255) / 256 * 256; };
+  add(sizeof(int) * (size_t)groups * stride);    // glab
+  add(sizeof(int) * cap);                        // bpar
+  add(sizeof(int) * cap);                        // bgrp
+  add(sizeof(unsigned long long) * cap);         // bkey
+  add(sizeof(unsigned long long) * cap);         // rkey
+  add(sizeof(uint32_t) * nw);                    // pbits
+  add(sizeof(int) * 4);                          // counters
+  add(sizeof(int) * nblk);                       // blkcnt
+  add(sizeof(int) * (nblk + 1));                 // blkoff
+  return bytes;
+}
+
+void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride, BlockScratch* b) {
+  const int64_t cap = std::max<int64_t>(1, block_edge_tiles(Tx, Ty) * groups);
+  const int64_t nw = (int64_t)groups * Ty * block_words(Tx);
+  char* p = static_cast<char*>(base);
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    char* q = p + off;
+    off += (n + 255) / 256 * 256;
+    return q;
+  };
+  b->glab = reinterpret_cast<int*>(take(sizeof(int) * (size_t)groups * stride));
+  b->bpar = reinterpret_cast<int*>(take(sizeof(int) * cap));
+  b->bgrp = reinterpret_cast<int*>(take(sizeof(int) * cap));
+  b->bkey = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * cap));
+  b->rkey = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * cap));
+  b->pbits = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
+  b->counters = reinterpret_cast<int*>(take(sizeof(int) * 4));
+  b->nblk = 152 * 8;
+  b->blkcnt = reinterpret_cast<int*>(take(sizeof(int) * b->nblk));
+  b->blkoff = reinterpret_cast<int*>(take(sizeof(int) * (b->nblk + 1)));
+  b->cap = cap;
+  b->words = block_words(Tx);
+}
+
+cudaError_t launch_block_select(const float* vals, int groups, int64_t stride, int Tx, int Ty,
+                                const float* thr, const BlockScratch& b, SelItem* peaks,
+                                int64_t cap, unsigned* status, unsigned* want, cudaStream_t st) {
+  if (groups < 1 || groups > 65535 || (Ty + kBlkY - 1) / kBlkY > 65535 ||
+      (int64_t)Tx * Ty > 0xffffffffll || b.cap > INT_MAX)
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(b.counters, 0, sizeof(int) * 4, st);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((Tx + kBlkX - 1) / kBlkX, (Ty + kBlkY - 1) / kBlkY, groups);
+  k_blk_cc<<<grid, kBlkThreads, 0, st>>>(vals, stride, Tx, Ty, thr, b, status);
+  k_blk_merge<<<grid, kBlkThreads, 0, st>>>(vals, stride, Tx, Ty, thr, b, status);
+  k_blk_resolve<<<152 * 4, 256, 0, st>>>(b);
+  k_blk_mark<<<152 * 4, 256, 0, st>>>(Tx, Ty, b);
+  const int64_t nwords = (int64_t)groups * Ty * b.words;
+  k_pbits_count<<<b.nblk, kSelThreads, 0, st>>>(nwords, b);
+  k_scan_blocks<<<1, 1024, 0, st>>>(b.nblk, b.blkcnt, b.blkoff, &b.counters[2], cap, status,
+                                    nullptr);
+  k_pbits_write<<<b.nblk, kSelThreads, 0, st>>>(nwords, Tx, Ty, vals, stride, b, peaks, cap);
+  k_blk_check<<<1, 1, 0, st>>>(b, cap, status, want);
+  count_launches(8);
+  return cudaGetLastError();
+}
+
 // ---- ordered list of component peaks (sorted by (group, t) like the items)
 __global__ void __launch_bounds__(kSelThreads) k_peak_count(const int* nsel, const int* parent,
                                                             const int* peak, int nblk,
@@ -450,6 +857,11 @@ __global__ void __launch_bounds__(kSelThreads) k_peak_write(const int* nsel, con
 }
 
 // ---- candidates
+// Peak p of an ordered peak list: items[plist[p]], or items[p] without plist.
+__device__ __forceinline__ SelItem peak_item(const SelItem* items, const int* plist, int p) {
+  return plist ? items[plist[p]] : items[p];
+}
+
 __device__ __forceinline__ float load_px(const void* base, int storage, int64_t idx) {
   switch (storage) {
     case FITRIG_BF16: return to_f32(static_cast<const bf16_t*>(base)[idx]);
@@ -537,7 +949,7 @@ __global__ void k_emit_freq(CandArgs a, const SelItem* __restrict__ items, const
                             const int* __restrict__ plist) {
   const int np = *np_;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-    const SelItem it = items[plist[p]];
+    const SelItem it = peak_item(items, plist, p);
     const int ty = it.t / a.Tx, tx = it.t - (it.t / a.Tx) * a.Tx;
     const int hw = min(a.w, a.ny - ty * a.w), ww = min(a.w, a.nx - tx * a.w);
     const float e = a.eta[it.t];
@@ -594,7 +1006,7 @@ __global__ void k_emit_image(CandArgs a, const SelItem* __restrict__ items, cons
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int p = wid; p < np; p += nw) {
-    const SelItem it = items[plist[p]];
+    const SelItem it = peak_item(items, plist, p);
     const int ty = it.t / a.Tx, tx = it.t - (it.t / a.Tx) * a.Tx;
     const int hw = min(a.w, a.ny - ty * a.w), ww = min(a.w, a.nx - tx * a.w);
     int64_t sl[3];   // the unit's three snapshots in the stack
@@ -645,11 +1057,11 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
                                                                  const int* __restrict__ plist,
                                                                  const int* base_) {
   __shared__ int counts[kGroupWarps][kMaxW];
-  auto snap_of = [&](int p) { return FROM_ARG ? items[plist[p]].group : tmp[p].snapshot; };
-  auto row_of = [&](int p) { return FROM_ARG ? items[plist[p]].t / a.Tx : tmp[p].y / a.w; };
+  auto snap_of = [&](int p) { return FROM_ARG ? peak_item(items, plist, p).group : tmp[p].snapshot; };
+  auto row_of = [&](int p) { return FROM_ARG ? peak_item(items, plist, p).t / a.Tx : tmp[p].y / a.w; };
   auto cand_of = [&](int p) -> fitrig_candidate {
     if (!FROM_ARG) return tmp[p];
-    const SelItem it = items[plist[p]];
+    const SelItem it = peak_item(items, plist, p);
     const int ty = it.t / a.Tx, tx = it.t - ty * a.Tx;
     const int idx = a.arg[(int64_t)it.group * a.stride + it.t];
     return image_candidate(a, it, tx, ty, a.w, idx % a.w, idx / a.w);
@@ -734,6 +1146,24 @@ __global__ void k_export(const fitrig_candidate* __restrict__ src, const int* n,
 cudaError_t launch_export_candidates(const fitrig_candidate* src, const int* n,
                                      fitrig_candidate* dst, int cap, cudaStream_t st) {
   k_export<<<64, 256, 0, st>>>(src, n, dst, cap);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit_peaks(const CandArgs& a, const SelItem* peaks, const int* npeak,
+                              int* base, fitrig_candidate* tmp, cudaStream_t st) {
+  if (a.branch == FITRIG_BRANCH_FREQ) {
+    k_emit_freq<<<152 * 4, 256, 0, st>>>(a, peaks, npeak, nullptr);
+    count_launches(1);
+  } else if (a.arg) {
+    k_group_sort<true><<<152 * 4, kGroupWarps * 32, 0, st>>>(a, npeak, tmp, peaks, nullptr, base);
+    count_launches(1);
+  } else {
+    k_emit_image<<<152 * 4, 256, 0, st>>>(a, peaks, npeak, nullptr, tmp);
+    k_group_sort<false><<<152 * 4, kGroupWarps * 32, 0, st>>>(a, npeak, tmp, peaks, nullptr, base);
+    count_launches(2);
+  }
+  k_add_count<<<1, 1, 0, st>>>(a.nout, npeak);
   count_launches(1);
   return cudaGetLastError();
 }

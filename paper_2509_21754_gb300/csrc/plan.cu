@@ -110,6 +110,8 @@ struct fitrig_plan_s {
   float* d_thr = nullptr;        // units + 1
   void* d_noise = nullptr;
   void* d_split = nullptr;       // split median/MAD scratch (NoiseScratch::split)
+  void* d_blk = nullptr;         // block-tiled components (BlockScratch), both branches
+  BlockScratch blk{};
   NoiseScratch ns_img{}, ns_freq{};
   void* d_sel = nullptr;
   SelectScratch sel{};
@@ -174,7 +176,7 @@ static void drop_graph(fitrig_plan_t p);
 static void free_all(fitrig_plan_t p) {
   drop_graph(p);
   void* ptrs[] = {p->d_stack, p->d_vp,  p->d_small, p->d_invalid,  p->d_cs, p->d_arg, p->d_inv,
-                  p->d_thr,   p->d_noise, p->d_split, p->d_sel, p->d_cand, p->d_cand_tmp,
+                  p->d_thr,   p->d_noise, p->d_split, p->d_blk, p->d_sel, p->d_cand, p->d_cand_tmp,
                   p->d_bin,   p->d_tw,  p->d_staging, p->d_report, p->d_accum,
                   p->d_hist,  p->d_hwts, p->d_htw,
                   p->d_smax,  p->d_mrun, p->d_wts};   // d_eta lives inside d_vp
@@ -444,6 +446,12 @@ static int allocate(fitrig_plan_t p) {
       noise_split_carve(p->d_split, U + 1, p->vstride, &p->ns_img);
       noise_split_carve(p->d_split, 1, p->vstride, &p->ns_freq);
     }
+  }
+  {
+    // the image branch's U maps and eta's one map run in turn: one buffer
+    const int gmax = std::max(U, 1);
+    CK(dmalloc(p, &p->d_blk, block_scratch_bytes(gmax, p->Tx, p->Ty, p->vstride)));
+    block_scratch_carve(p->d_blk, gmax, p->Tx, p->Ty, p->vstride, &p->blk);
   }
   {
     const int rc = alloc_select(p);
@@ -939,12 +947,12 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
       CKE(launch_noise(p->d_eta, 1, p->vstride, p->T, p->noise, p->ns_freq, cs, st));
       CKE(launch_thresholds(cs, 1, p->tau, p->d_thr + U, p->d_inv + U, st));
     }
-    CKE(launch_select(p->d_eta, 1, p->vstride, p->d_thr + U, p->sel, status, st));
-    CKE(launch_components(p->Tx, p->Ty, p->vstride, p->sel, status, st));
+    CKE(launch_block_select(p->d_eta, 1, p->vstride, p->Tx, p->Ty, p->d_thr + U, p->blk,
+                            p->sel.items, p->sel.capacity, status, p->sel.want, st));
     ca.branch = FITRIG_BRANCH_FREQ;
     ca.cs = cs;              // eta's estimate (group 0 of its selection)
     ca.inv = p->d_inv + U;
-    CKE(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
+    CKE(launch_emit_peaks(ca, p->sel.items, &p->blk.counters[2], nout, p->d_cand_tmp, st));
   }
   if (p->branch & FITRIG_BRANCH_IMAGE) {
     if (!both) {
@@ -954,13 +962,13 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
       mark(FITRIG_KERNEL_NOISE, 1);
     }
     mark(FITRIG_KERNEL_SELECT, 0);
-    CKE(launch_select(p->d_vp, U, p->vstride, p->d_thr, p->sel, status, st));
-    CKE(launch_components(p->Tx, p->Ty, p->vstride, p->sel, status, st));
+    CKE(launch_block_select(p->d_vp, U, p->vstride, p->Tx, p->Ty, p->d_thr, p->blk,
+                            p->sel.items, p->sel.capacity, status, p->sel.want, st));
     ca.branch = FITRIG_BRANCH_IMAGE;
     ca.arg = p->d_arg;
     ca.cs = p->d_cs;
     ca.inv = p->d_inv;
-    CKE(launch_emit_candidates(ca, p->sel, nout, p->d_cand_tmp, status, st));
+    CKE(launch_emit_peaks(ca, p->sel.items, &p->blk.counters[2], nout, p->d_cand_tmp, st));
     mark(FITRIG_KERNEL_SELECT, 1);
   }
   CKE(launch_clamp_count(nout, (int)p->cand_cap, status, st));

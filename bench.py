@@ -51,19 +51,21 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-spectrum", action="store_true",
                     help="skip the transform-alone leg at power-of-two series lengths")
-    ap.add_argument("--batched", action="store_true",
-                    help="also run the 256-field batched workload (about a minute)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 256-field batched workload (a few minutes)")
     ap.add_argument("--serving-compression", type=float, default=20.0,
                     help="time compression of the serving leg's Poisson arrivals")
+    ap.add_argument("--serving-snapshots", type=int, default=600,
+                    help="snapshots each serving field streams (the serving workload's 600)")
     ap.add_argument("--serving-freq", type=int, default=0,
                     help="serving fields also run the real-time frequency branch over their "
                          "last N units")
     ap.add_argument("--paper-run", action="store_true",
                     help="add the paper's end-to-end configuration: 1500 x 4096^2, frequency "
                          "branch with harmonic summing, window 32 (about 110 GB of HBM)")
-    ap.add_argument("--large", action="store_true",
-                    help="also run the 8 x 50000^2 field (generated and pushed one snapshot "
-                         "at a time; about 90 GB of device memory with FP32 storage)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 8 x 50000^2 field with FP32 and BF16 storage (generated and "
+                         "pushed one snapshot at a time; about 90 GB of device memory)")
     ap.add_argument("--accumulate", type=int, default=0,
                     help="also time ingest with snapshot accumulation: K raw device "
                          "snapshots summed per stack snapshot (Sec. 3.3.2)")
@@ -223,6 +225,58 @@ def oracle_sample(a, stack_np, budget_s=12.0):
     return done_px / t_used / 1e9, desc, t_used
 
 
+def _oracle_strip(args):
+    """Worker of the all-cores oracle leg (a spawned process): one strip."""
+    strip, window, nsigma, noise = args
+    from oracle import fitrig_oracle as O
+    t0 = time.perf_counter()
+    O.detect(strip, window, nsigma, O.BRANCH_BOTH, noise)
+    return time.perf_counter() - t0
+
+
+def host_cpu():
+    """(logical cores, model name) of the host."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_all_cores(a, stack_np, budget_s=12.0):
+    """The same oracle on every host core at once: one spawned process per core
+    (NumPy single-threaded in each), each taking whole-width strips of the
+    stack, for about ``budget_s`` of wall time; returns (Gpx/s, desc, cores)."""
+    import multiprocessing as mp
+    cores, _ = host_cpu()
+    L, ny, nx = stack_np.shape
+    rows = 8 * a.window
+    nstrip = max(1, ny // rows)
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    ctx = mp.get_context("spawn")   # a fork after CUDA work would hang
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_strip, [(stack_np[:, :rows, :], a.window, a.nsigma, a.noise)] * cores)
+        done_px, jobs, t0 = 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < budget_s and jobs < 8 * nstrip:
+            batch = []
+            for _ in range(cores):
+                y0 = ((jobs * 13) % nstrip) * rows
+                batch.append((stack_np[:, y0:y0 + rows, :], a.window, a.nsigma, a.noise))
+                jobs += 1
+            pool.map(_oracle_strip, batch)
+            done_px += len(batch) * L * rows * nx
+        wall = time.perf_counter() - t0
+    desc = (f"{jobs} strips of {L} snapshots x {rows} rows x {nx} columns "
+            f"({done_px / 1e6:.0f} Mpixel), {cores} processes, FP64 NumPy oracle")
+    return done_px / wall / 1e9, desc, cores
+
+
 def reference_arm(a, ws, rank):
     if rank != 0:
         return 0
@@ -323,6 +377,22 @@ def serving_run(a, F, synth, torch, nfields=32, nsnap=24, compression=20.0, seed
         res, _ = F.fitrig_server_poll(srv, cap=1 << 20, cand_cap=1 << 24)
         lat = (res["t_done_ns"] - res["t_arrival_ns"]) / 1e6
         used, nact, nwait = F.fitrig_server_usage(srv)
+        # where the latency went, per unit: the feeder's delay before the push,
+        # the host enqueue, the device copy and trigger (GPU timer), and the
+        # rest (waiting behind earlier work on the field's stream, callback)
+        feeder = (res["t_push_ns"] - res["t_arrival_ns"]) / 1e6
+        host = (res["t_enqueued_ns"] - res["t_push_ns"]) / 1e6
+        copy = res["copy_ms"].astype(np.float64)
+        trig = res["trigger_ms"].astype(np.float64)
+        rest = lat - feeder - host - copy - trig
+        pct = lambda a: {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)),
+                         "max": float(a.max())}
+        slow = lat >= np.percentile(lat, 99)
+        stages = {"feeder_ms": pct(feeder), "host_enqueue_ms": pct(host), "copy_ms": pct(copy),
+                  "trigger_ms": pct(trig), "rest_ms": pct(rest),
+                  "slowest_1pct_mean_ms": {k: float(np.mean(a[slow])) for k, a in
+                                           (("latency", lat), ("feeder", feeder), ("host", host),
+                                            ("copy", copy), ("trigger", trig), ("rest", rest))}}
         return {
             "fields": len(sides), "admitted": len(active), "queued": nwait,
             "snapshots_per_field": nsnap, "units": int(res.size),
@@ -333,6 +403,7 @@ def serving_run(a, F, synth, torch, nfields=32, nsnap=24, compression=20.0, seed
             "reserved_gb": used / 1e9,
             "sides": "uniform 2048..16384, seeded",
             "freq_units": freq_units,
+            "stages": stages,
         }
     finally:
         F.fitrig_server_destroy(srv)
@@ -684,9 +755,12 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not a.no_cpu:
         x = stack.to(tdt).float().cpu().numpy()
-        v, desc, used = oracle_sample(a, x)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": round(used, 2)}
+        v1, desc1, used = oracle_sample(a, x)
+        vall, descall, cores = oracle_all_cores(a, x)
+        _, model = host_cpu()
+        cpu = {"value": vall, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": descall,
+               "single_core": {"value": v1, "cores": 1, "sample": desc1, "seconds": round(used, 2)},
+               "host_cpu": model}
 
     accum = large = spectrum = None
     if rank == 0 and ws == 1 and a.accumulate > 1:
@@ -695,8 +769,8 @@ def main():
         spectrum = spectrum_run(F, torch)
 
     serving = batched = None
-    legs = rank == 0 and ws == 1 and (a.large or a.paper_run or
-                                      not (a.no_serving and not a.batched))
+    legs = rank == 0 and ws == 1 and (not a.no_large or a.paper_run or not a.no_serving or
+                                      not a.no_batched)
     if legs:   # the remaining legs need the device memory of the main workload
         plan.close()
         del stack, stack_s
@@ -704,14 +778,14 @@ def main():
     paper = None
     if rank == 0 and ws == 1 and a.paper_run:
         paper = paper_run(a, F, synth, torch)
-    if rank == 0 and ws == 1 and a.large:
-        large = large_run(a, F, synth, torch, storage)
-    if rank == 0 and ws == 1 and not (a.no_serving and not a.batched):
-        if not a.no_serving:
-            serving = serving_run(a, F, synth, torch, freq_units=a.serving_freq,
-                                  compression=a.serving_compression)
-        if a.batched:
-            batched = batched_run(a, F, synth, torch)
+    if rank == 0 and ws == 1 and not a.no_large:
+        large = {"f32": large_run(a, F, synth, torch, F.F32),
+                 "bf16": large_run(a, F, synth, torch, F.BF16)}
+    if rank == 0 and ws == 1 and not a.no_serving:
+        serving = serving_run(a, F, synth, torch, freq_units=a.serving_freq,
+                              compression=a.serving_compression, nsnap=a.serving_snapshots)
+    if rank == 0 and ws == 1 and not a.no_batched:
+        batched = batched_run(a, F, synth, torch)
 
     if rank == 0:
         line = {

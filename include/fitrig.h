@@ -57,6 +57,15 @@ typedef struct {
   int64_t t_arrival_ns;  /* the caller's stamp of snapshot s+2 (CLOCK_MONOTONIC ns)  */
   int64_t t_done_ns;     /* CLOCK_MONOTONIC ns when the result reached host memory   */
   int64_t cand_offset;   /* index of its first candidate in the poll's candidates    */
+  /* where the latency t_done_ns - t_arrival_ns went (64-byte record):           */
+  int64_t t_push_ns;     /* CLOCK_MONOTONIC ns when fitrig_server_push was entered   */
+  int64_t t_enqueued_ns; /* ... when the unit's device work had been enqueued        */
+  float copy_ms;         /* device: the snapshot's copy into the ring, from the time
+                            the field's stream reached it (includes waiting for a
+                            copy engine) to its end (GPU global timer)              */
+  float trigger_ms;      /* device: the unit's trigger, from the end of the copy to
+                            the candidates in host memory (includes SM sharing with
+                            other fields' streams)                                   */
 } fitrig_result;
 
 /* One trigger candidate (32 bytes). */

@@ -207,7 +207,7 @@ def bin_is_a_maximum(mags: np.ndarray, k: int, harmonics: int = 1) -> bool:
 
 
 def tile_value_bound(stack: np.ndarray, s: int, w: int, rmode: str = "abs",
-                     edge: str = "partial") -> np.ndarray:
+                     edge: str = "partial", stride: str = "tile") -> np.ndarray:
     """Per tile of unit s, an upper bound on |v - v_exact| for an implementation
     that computes the tile statistic v = mean(Delta) max(Delta) mean(r) in
     FP32 (unit roundoff u = 2^-24) from the stored values, where v_exact is
@@ -223,10 +223,11 @@ def tile_value_bound(stack: np.ndarray, s: int, w: int, rmode: str = "abs",
     sides are certainly clipped at 1.  Tile sums of m terms add (m - 1) u times
     the sum of magnitudes; the maximum moves by at most the largest e_D; the
     two divisions by the pixel count and the two products add 8u.  The bound
-    on v follows from the perturbed factors."""
+    on v follows from the perturbed factors.  With stride "sliding" the sums
+    run over the window centred on each pixel instead of over tiles."""
     u = 2.0 ** -24
     L, ny, nx = stack.shape
-    Ty, Tx, nyu, nxu = O.tiling(ny, nx, w, edge)
+    Ty, Tx, nyu, nxu = O.tiling(ny, nx, w, edge) if stride == "tile" else (ny, nx, ny, nx)
     a, b, c = (np.asarray(stack[s + i, :nyu, :nxu], dtype=np.float64) for i in range(3))
     delta, r, fin = O.unit_terms(a, b, c, rmode)
     with np.errstate(invalid="ignore", over="ignore"):
@@ -239,8 +240,12 @@ def tile_value_bound(stack: np.ndarray, s: int, w: int, rmode: str = "abs",
         er = np.where(ratio - er >= 1.0, 0.0, np.minimum(er, 1.0))
     eD = np.where(fin, eD, 0.0)
     er = np.where(fin, er, 0.0)
-    ut = O.tile_reduce(delta, r, fin, w, Ty, Tx)
-    eu = O.tile_reduce(eD, er, fin, w, Ty, Tx)
+    if stride == "tile":
+        ut = O.tile_reduce(delta, r, fin, w, Ty, Tx)
+        eu = O.tile_reduce(eD, er, fin, w, Ty, Tx)
+    else:
+        ut = O.window_stats(delta, r, fin, w)
+        eu = O.window_stats(eD, er, fin, w)
     m = ut.n
     S1 = ut.S1 + eu.S1 + (m - 1) * u * (ut.S1 + eu.S1)
     S2 = ut.S2 + eu.S2

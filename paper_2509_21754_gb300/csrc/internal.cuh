@@ -303,7 +303,9 @@ struct BlockScratch {
   unsigned long long* bkey;   // [cap] block-local peak key (value key << 32 | ~t)
   unsigned long long* rkey;   // [cap] merged peak key (roots)
   uint32_t* pbits;            // [groups][Ty][words] peak bitmap
-  int* counters;              // [0] boundary components, [1] selected tiles, [2] peaks
+  unsigned long long* pairs;  // [pcap] selected neighbours across block edges (g, t, direction)
+  int64_t pcap;
+  int* counters;              // [0] boundary components, [1] selected tiles, [2] peaks, [3] pairs
   int64_t cap;                // boundary components one detect can hold
   int words;                  // bitmap words per tile row
   int nblk;                   // grid of the ordered compaction
@@ -390,6 +392,8 @@ cudaError_t launch_accumulate(const void* src, int src_type, int64_t src_pitch, 
                               int ny, int nx, cudaStream_t st);
 
 // Small helpers.
+// The GPU's global nanosecond timer into *dst when the stream reaches it.
+cudaError_t launch_stamp(long long* dst, cudaStream_t st);
 cudaError_t launch_fill_probe(void* dst, int type, int64_t n, uint32_t seed, cudaStream_t st);
 cudaError_t launch_tlisi_from_values(const float* vp, int64_t n, const unsigned* gmax,
                                      const double* m_unit, float* out, cudaStream_t st);

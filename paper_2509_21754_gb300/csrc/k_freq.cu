@@ -837,6 +837,22 @@ cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, voi
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- timestamps
+// The GPU's global nanosecond timer, written when the stream reaches this
+// point (serving: per-stage device times of a unit, read by the host without
+// a CUDA call).
+__global__ void k_stamp(long long* dst) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *dst = (long long)t;
+}
+
+cudaError_t launch_stamp(long long* dst, cudaStream_t st) {
+  k_stamp<<<1, 1, 0, st>>>(dst);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- autotuner probe data
 // Deterministic pseudo-random values in [-4, 4) (an integer hash of the index),
 // used only as timing input for the autotuner.

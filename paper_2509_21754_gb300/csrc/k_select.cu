@@ -418,9 +418,11 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
 // OR'ed in afterwards, and an ordered compaction of the bitmap gives the peak
 // list in (group, t) order.
 constexpr int kBlkT = kBlkY * kBlkX;
-constexpr int kBlkThreads = 256;
-constexpr int kBlkPer = kBlkT / kBlkThreads;
+constexpr int kBlkThreads = 512;
+constexpr int kBlkPer = kBlkT / kBlkThreads;            // tiles per thread
+constexpr int kBlkRowsPer = kBlkThreads / kBlkX;        // block rows per pass of the threads
 constexpr int kBlkRing = 2 * kBlkX + 2 * (kBlkY - 2);   // edge tiles of a block
+constexpr int kBlkHalo = 2 * (kBlkX + 2) + 2 * kBlkY;   // halo tiles of a block
 
 __device__ __forceinline__ int find_s(const int* par, int x) {
   const volatile int* p = par;
@@ -461,6 +463,22 @@ __device__ __forceinline__ unsigned long long peak_key(float v, uint32_t t) {
   return ((unsigned long long)f32_key(v) << 32) | (unsigned long long)(0xffffffffu - t);
 }
 
+// Halo position q (0 <= q < kBlkHalo) of a block as (ly, lx), -1 <= ly <= kBlkY,
+// -1 <= lx <= kBlkX: the row above, the row below, then the two side columns.
+__device__ __forceinline__ void halo_pos(int q, int* ly, int* lx) {
+  if (q < kBlkX + 2) {
+    *ly = -1;
+    *lx = q - 1;
+  } else if (q < 2 * (kBlkX + 2)) {
+    *ly = kBlkY;
+    *lx = q - (kBlkX + 2) - 1;
+  } else {
+    const int r = q - 2 * (kBlkX + 2);
+    *ly = r >> 1;
+    *lx = (r & 1) ? kBlkX : -1;
+  }
+}
+
 // The ring position r (0 <= r < kBlkRing) of a block's edge as (ly, lx).
 __device__ __forceinline__ void ring_pos(int r, int* ly, int* lx) {
   if (r < kBlkX) {
@@ -476,13 +494,20 @@ __device__ __forceinline__ void ring_pos(int r, int* ly, int* lx) {
   }
 }
 
+// Cross-block neighbour pair: group, tile and the direction (0..7) of the
+// neighbour, packed as (g << 40) | (t << 3) | dir.
+__device__ __forceinline__ void dir_offset(int d, int* dy, int* dx) {
+  const int k = d < 4 ? d : d + 1;   // skip the centre of the 3 x 3
+  *dy = k / 3 - 1;
+  *dx = k % 3 - 1;
+}
+
 __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict__ vals,
                                                         int64_t stride, int Tx, int Ty,
                                                         const float* __restrict__ thr,
                                                         BlockScratch b, unsigned* status) {
   __shared__ uint8_t msk[kBlkY + 2][kBlkX + 2];
   __shared__ int par[kBlkT];
-  __shared__ float val[kBlkT];
   __shared__ unsigned long long pkey[kBlkT];
   __shared__ uint8_t bnd[kBlkT];
   __shared__ int bid[kBlkT];
@@ -493,34 +518,43 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
   const int tx0 = blockIdx.x * kBlkX, ty0 = blockIdx.y * kBlkY;
   const float th = thr[g];
   const float* v = vals + (size_t)g * stride;
-  if (tid == 0) nsel_sh = 0;
-  for (int i = tid; i < kBlkY * (kBlkX / 32); i += kBlkThreads) (&pw[0][0])[i] = 0u;
-  // 1. the mask with its halo, and the block's values
-  for (int i = tid; i < (kBlkY + 2) * (kBlkX + 2); i += kBlkThreads) {
-    const int ly = i / (kBlkX + 2) - 1, lx = i - (i / (kBlkX + 2)) * (kBlkX + 2) - 1;
-    const int ty = ty0 + ly, tx = tx0 + lx;
-    float x = 0.f;
-    bool sel = false;
-    if (ty >= 0 && ty < Ty && tx >= 0 && tx < Tx) {
-      x = v[(int64_t)ty * Tx + tx];
-      sel = x > th;
-    }
-    msk[ly + 1][lx + 1] = sel;
-    if (ly >= 0 && ly < kBlkY && lx >= 0 && lx < kBlkX) {
-      const int li = ly * kBlkX + lx;
-      val[li] = x;
-      par[li] = sel ? li : -1;
-      pkey[li] = 0ull;
-      bnd[li] = 0;
-    }
+  // 1. every load first: the thread's kBlkPer tiles (column tid % kBlkX, rows
+  // tid / kBlkX + kBlkRowsPer k) and one halo tile
+  const int lx0 = tid % kBlkX, ly0 = tid / kBlkX;
+  const int gx = tx0 + lx0;
+  float x[kBlkPer];
+#pragma unroll
+  for (int k = 0; k < kBlkPer; ++k) {
+    const int gy = ty0 + ly0 + kBlkRowsPer * k;
+    x[k] = (gx < Tx && gy < Ty) ? v[(int64_t)gy * Tx + gx] : NAN;
   }
+  float xh = NAN;
+  int hy = 0, hx = 0;
+  if (tid < kBlkHalo) {
+    halo_pos(tid, &hy, &hx);
+    const int gy = ty0 + hy, gxh = tx0 + hx;
+    if (gy >= 0 && gy < Ty && gxh >= 0 && gxh < Tx) xh = v[(int64_t)gy * Tx + gxh];
+  }
+  if (tid == 0) nsel_sh = 0;
+  if (tid < kBlkY * (kBlkX / 32)) (&pw[0][0])[tid] = 0u;
+  int mine = 0;
+#pragma unroll
+  for (int k = 0; k < kBlkPer; ++k) {
+    const int ly = ly0 + kBlkRowsPer * k, li = ly * kBlkX + lx0;
+    const bool sel = x[k] > th;   // NaN (invalid tile, or beyond the map) is never selected
+    mine += sel;
+    msk[ly + 1][lx0 + 1] = sel;
+    par[li] = sel ? li : -1;
+    pkey[li] = 0ull;
+    bnd[li] = 0;
+  }
+  if (tid < kBlkHalo) msk[hy + 1][hx + 1] = xh > th;
   __syncthreads();
   // 2. unions inside the block (left, up-left, up, up-right)
-  int mine = 0;
-  for (int li = tid; li < kBlkT; li += kBlkThreads) {
-    const int ly = li / kBlkX, lx = li - (li / kBlkX) * kBlkX;
+#pragma unroll
+  for (int k = 0; k < kBlkPer; ++k) {
+    const int ly = ly0 + kBlkRowsPer * k, lx = lx0, li = ly * kBlkX + lx;
     if (!msk[ly + 1][lx + 1]) continue;
-    ++mine;
     if (lx > 0 && msk[ly + 1][lx]) unite_s(par, li, li - 1, status);
     if (ly > 0) {
       if (msk[ly][lx + 1]) unite_s(par, li, li - kBlkX, status);
@@ -533,18 +567,17 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
   int root[kBlkPer];
 #pragma unroll
   for (int k = 0; k < kBlkPer; ++k) {
-    const int li = tid + k * kBlkThreads;
+    const int li = (ly0 + kBlkRowsPer * k) * kBlkX + lx0;
     root[k] = par[li] >= 0 ? find_s(par, li) : -1;
   }
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kBlkPer; ++k) {
-    const int li = tid + k * kBlkThreads;
     if (root[k] < 0) continue;
+    const int ly = ly0 + kBlkRowsPer * k, lx = lx0, li = ly * kBlkX + lx;
     par[li] = root[k];
-    const int ly = li / kBlkX, lx = li - (li / kBlkX) * kBlkX;
     const uint32_t t = (uint32_t)((ty0 + ly) * Tx + (tx0 + lx));
-    atomicMax(&pkey[root[k]], peak_key(val[li], t));
+    atomicMax(&pkey[root[k]], peak_key(x[k], t));
     if (ly == 0 || ly == kBlkY - 1 || lx == 0 || lx == kBlkX - 1) {
       bool out = false;
 #pragma unroll
@@ -562,7 +595,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
   // 4. roots: an interior component's peak bit; a boundary component's id
 #pragma unroll
   for (int k = 0; k < kBlkPer; ++k) {
-    const int li = tid + k * kBlkThreads;
+    const int li = (ly0 + kBlkRowsPer * k) * kBlkX + lx0;
     if (root[k] != li) continue;
     const unsigned long long key = pkey[li];
     if (!bnd[li]) {
@@ -585,17 +618,34 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
     }
   }
   __syncthreads();
-  // 5. labels of the edge tiles of boundary components; the block's peak
-  // words (a row of the block covers kBlkX / 32 whole words); the count
-  for (int r = tid; r < kBlkRing; r += kBlkThreads) {
+  // 5. edge tiles of boundary components: their label, and each selected
+  // neighbour across the block edge with a larger tile index as a pair; the
+  // block's peak words (a row of the block covers kBlkX / 32 whole words)
+  if (tid < kBlkRing) {
     int ly, lx;
-    ring_pos(r, &ly, &lx);
+    ring_pos(tid, &ly, &lx);
     const int li = ly * kBlkX + lx;
-    if (!msk[ly + 1][lx + 1] || !bnd[par[li]]) continue;
-    b.glab[(size_t)g * stride + (int64_t)(ty0 + ly) * Tx + (tx0 + lx)] = bid[par[li]];
+    if (msk[ly + 1][lx + 1] && bnd[par[li]]) {
+      const int64_t t = (int64_t)(ty0 + ly) * Tx + (tx0 + lx);
+      b.glab[(size_t)g * stride + t] = bid[par[li]];
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        int dy, dx;
+        dir_offset(d, &dy, &dx);
+        const int ny = ly + dy, nx = lx + dx;
+        const bool outside = ny < 0 || ny >= kBlkY || nx < 0 || nx >= kBlkX;
+        if (!outside || !msk[ny + 1][nx + 1]) continue;
+        if (dy * Tx + dx <= 0) continue;   // the other tile records it
+        const int pi = atomicAdd(&b.counters[3], 1);
+        if (pi < b.pcap)
+          b.pairs[pi] = ((unsigned long long)g << 40) | ((unsigned long long)t << 3) | (unsigned)d;
+        else
+          atomicOr(status, kErrCapacity);
+      }
+    }
   }
-  for (int i = tid; i < kBlkY * (kBlkX / 32); i += kBlkThreads) {
-    const int ly = i / (kBlkX / 32), wx = i - ly * (kBlkX / 32);
+  if (tid < kBlkY * (kBlkX / 32)) {
+    const int ly = tid / (kBlkX / 32), wx = tid - ly * (kBlkX / 32);
     const int ty = ty0 + ly, w = tx0 / 32 + wx;
     if (ty < Ty && w < b.words) b.pbits[((size_t)g * Ty + ty) * b.words + w] = pw[ly][wx];
   }
@@ -605,39 +655,23 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
   if (tid == 0 && nsel_sh) atomicAdd(&b.counters[1], nsel_sh);
 }
 
-// Unions of boundary components across block edges: every selected edge tile
-// with a selected neighbour outside its block joins the two ids.
-__global__ void __launch_bounds__(kBlkThreads) k_blk_merge(const float* __restrict__ vals,
-                                                           int64_t stride, int Tx, int Ty,
-                                                           const float* __restrict__ thr,
-                                                           BlockScratch b, unsigned* status) {
-  const int g = blockIdx.z;
-  const int tx0 = blockIdx.x * kBlkX, ty0 = blockIdx.y * kBlkY;
-  const float th = thr[g];
-  const float* v = vals + (size_t)g * stride;
-  const int* lab = b.glab + (size_t)g * stride;
+// Unions of boundary components across block edges: one thread per recorded
+// neighbour pair joins the two tiles' component ids.
+__global__ void k_blk_merge(int64_t stride, int Tx, BlockScratch b, unsigned* status) {
+  const int np = min(b.counters[3], (int)b.pcap);
   // ids of this detect only (the label map is never cleared; every label read
   // here was written by k_blk_cc, and the range check keeps it so)
   const int nid = min(b.counters[0], (int)b.cap);
-  for (int r = threadIdx.x; r < kBlkRing; r += kBlkThreads) {
-    int ly, lx;
-    ring_pos(r, &ly, &lx);
-    const int ty = ty0 + ly, tx = tx0 + lx;
-    if (ty >= Ty || tx >= Tx) continue;
-    const int64_t t = (int64_t)ty * Tx + tx;
-    if (!(v[t] > th)) continue;
-    const int me = lab[t];
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int ny = ly + dy, nx = lx + dx;
-        if (ny >= 0 && ny < kBlkY && nx >= 0 && nx < kBlkX) continue;   // inside the block
-        const int gy = ty + dy, gx = tx + dx;
-        if (gy < 0 || gy >= Ty || gx < 0 || gx >= Tx) continue;
-        const int64_t tn = (int64_t)gy * Tx + gx;
-        if (!(v[tn] > th)) continue;
-        const int other = lab[tn];
-        if (me >= 0 && me < nid && other >= 0 && other < nid) unite(b.bpar, me, other, status);
-      }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+    const unsigned long long pk = b.pairs[i];
+    const int g = (int)(pk >> 40);
+    const int64_t t = (int64_t)((pk >> 3) & ((1ull << 37) - 1));
+    int dy, dx;
+    dir_offset((int)(pk & 7u), &dy, &dx);
+    const int64_t tn = t + (int64_t)dy * Tx + dx;
+    const int* lab = b.glab + (size_t)g * stride;
+    const int me = lab[t], other = lab[tn];
+    if (me >= 0 && me < nid && other >= 0 && other < nid) unite(b.bpar, me, other, status);
   }
 }
 
@@ -759,6 +793,7 @@ size_t block_scratch_bytes(int groups, int Tx, int Ty, int64_t stride) {
   add(sizeof(unsigned long long) * cap);         // bkey
   add(sizeof(unsigned long long) * cap);         // rkey
   add(sizeof(uint32_t) * nw);                    // pbits
+  add(sizeof(unsigned long long) * 4 * cap);     // pairs
   add(sizeof(int) * 4);                          // counters
   add(sizeof(int) * nblk);                       // blkcnt
   add(sizeof(int) * (nblk + 1));                 // blkoff
@@ -781,6 +816,8 @@ void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride,
   b->bkey = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * cap));
   b->rkey = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * cap));
   b->pbits = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
+  b->pairs = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * 4 * cap));
+  b->pcap = 4 * cap;
   b->counters = reinterpret_cast<int*>(take(sizeof(int) * 4));
   b->nblk = 152 * 8;
   b->blkcnt = reinterpret_cast<int*>(take(sizeof(int) * b->nblk));
@@ -793,13 +830,13 @@ cudaError_t launch_block_select(const float* vals, int groups, int64_t stride, i
                                 const float* thr, const BlockScratch& b, SelItem* peaks,
                                 int64_t cap, unsigned* status, unsigned* want, cudaStream_t st) {
   if (groups < 1 || groups > 65535 || (Ty + kBlkY - 1) / kBlkY > 65535 ||
-      (int64_t)Tx * Ty > 0xffffffffll || b.cap > INT_MAX)
+      (int64_t)Tx * Ty > 0xffffffffll || b.pcap > INT_MAX)
     return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(b.counters, 0, sizeof(int) * 4, st);
   if (e != cudaSuccess) return e;
   const dim3 grid((Tx + kBlkX - 1) / kBlkX, (Ty + kBlkY - 1) / kBlkY, groups);
   k_blk_cc<<<grid, kBlkThreads, 0, st>>>(vals, stride, Tx, Ty, thr, b, status);
-  k_blk_merge<<<grid, kBlkThreads, 0, st>>>(vals, stride, Tx, Ty, thr, b, status);
+  k_blk_merge<<<152 * 8, 256, 0, st>>>(stride, Tx, b, status);
   k_blk_resolve<<<152 * 4, 256, 0, st>>>(b);
   k_blk_mark<<<152 * 4, 256, 0, st>>>(Tx, Ty, b);
   const int64_t nwords = (int64_t)groups * Ty * b.words;

@@ -1595,6 +1595,11 @@ struct ServerField {
   fitrig_candidate* h_cands = nullptr;   // mapped pinned host buffer
   fitrig_candidate* d_cands = nullptr;   // its device alias
   int32_t cand_cap = 0;
+  // GPU timestamps of the current unit (mapped, after the candidates): the
+  // copy's start and end and the trigger's end; the unit's callback reads
+  // them before the next unit's stamps run (stream order)
+  long long* h_stamps = nullptr;
+  long long* d_stamps = nullptr;
 };
 
 struct ServerResult {
@@ -1623,6 +1628,8 @@ struct UnitTicket {
   ServerField* f;
   int32_t unit;
   int64_t t_arrival;
+  int64_t t_push;
+  int64_t t_enqueued;
 };
 
 constexpr int32_t kServeCandCap = 1 << 16;
@@ -1650,6 +1657,11 @@ void CUDART_CB unit_done(void* arg) {
   res.r.t_arrival_ns = t->t_arrival;
   res.r.t_done_ns = monotonic_ns();
   res.r.cand_offset = 0;
+  res.r.t_push_ns = t->t_push;
+  res.r.t_enqueued_ns = t->t_enqueued;
+  const volatile long long* gs = f->h_stamps;
+  res.r.copy_ms = (float)((double)(gs[1] - gs[0]) * 1e-6);
+  res.r.trigger_ms = (float)((double)(gs[2] - gs[1]) * 1e-6);
   {
     std::lock_guard<std::mutex> lk(t->srv->rmtx);
     t->srv->results.push_back(std::move(res));
@@ -1698,7 +1710,7 @@ int activate(fitrig_server_s* s, ServerField* f) {
   f->plan = p;
   f->stream = plan_stream(p);
   f->cand_cap = kServeCandCap;
-  if (cudaHostAlloc(&f->h_cands, sizeof(fitrig_candidate) * f->cand_cap, cudaHostAllocMapped) != cudaSuccess ||
+  if (cudaHostAlloc(&f->h_cands, sizeof(fitrig_candidate) * f->cand_cap + 64, cudaHostAllocMapped) != cudaSuccess ||
       cudaHostGetDevicePointer(&f->d_cands, f->h_cands, 0) != cudaSuccess ||
       cudaEventCreateWithFlags(&f->copied, cudaEventDisableTiming) != cudaSuccess ||
       cudaMemsetAsync(p->d_small, 0, 16, f->stream) != cudaSuccess) {
@@ -1706,6 +1718,8 @@ int activate(fitrig_server_s* s, ServerField* f) {
     free_field(f);
     return FITRIG_ENOMEM;
   }
+  f->h_stamps = reinterpret_cast<long long*>(f->h_cands + f->cand_cap);
+  f->d_stamps = reinterpret_cast<long long*>(f->d_cands + f->cand_cap);
   f->bytes = need;
   s->used += need;
   f->state = kFieldActive;
@@ -1816,6 +1830,7 @@ FITRIG_API int fitrig_server_push(fitrig_server_t s, int32_t field, const void* 
                                   int64_t t_arrival_ns) {
   if (!s || !data) return FITRIG_EINVAL;
   if (dtype != FITRIG_F32 && dtype != FITRIG_BF16 && dtype != FITRIG_F16) return FITRIG_EINVAL;
+  const int64_t t_push = monotonic_ns();
   cudaEvent_t copied = nullptr;
   {
     std::lock_guard<std::mutex> lk(s->mtx);
@@ -1829,6 +1844,8 @@ FITRIG_API int fitrig_server_push(fitrig_server_t s, int32_t field, const void* 
     const int slot = (int)(f->received % 3);
     const int eb = elem_bytes(p->storage), ib = elem_bytes(dtype);
     char* dst = p->d_stack + p->slice_bytes * slot;
+    const bool unit = f->received + 1 >= 3;   // this snapshot completes a unit
+    if (unit) CK(launch_stamp(f->d_stamps + 0, st));
     if (dtype == p->storage) {
       CK(cudaMemcpy2DAsync(dst, p->pitch * eb, data, (size_t)p->nx * ib, (size_t)p->nx * ib, p->ny,
                            cudaMemcpyDefault, st));
@@ -1837,6 +1854,7 @@ FITRIG_API int fitrig_server_push(fitrig_server_t s, int32_t field, const void* 
       CK(cudaMemcpyAsync(p->d_staging, data, (size_t)p->nx * p->ny * ib, cudaMemcpyDefault, st));
       CK(launch_convert(p->d_staging, dtype, p->nx, dst, p->storage, p->pitch, p->ny, p->nx, st));
     }
+    if (unit) CK(launch_stamp(f->d_stamps + 1, st));
     CK(cudaEventRecord(f->copied, st));
     copied = f->copied;
     f->received += 1;
@@ -1858,7 +1876,9 @@ FITRIG_API int fitrig_server_push(fitrig_server_t s, int32_t field, const void* 
       CK(enqueue_post(p, st, false));
       CK(launch_export_candidates(p->d_cand, reinterpret_cast<int*>(p->d_small + 2), f->d_cands,
                                   f->cand_cap, st));
-      UnitTicket* t = new (std::nothrow) UnitTicket{s, f, (int32_t)(f->received - 3), t_arrival_ns};
+      CK(launch_stamp(f->d_stamps + 2, st));
+      UnitTicket* t = new (std::nothrow)
+          UnitTicket{s, f, (int32_t)(f->received - 3), t_arrival_ns, t_push, monotonic_ns()};
       if (!t) return FITRIG_ENOMEM;
       CK(cudaLaunchHostFunc(st, unit_done, t));
     }

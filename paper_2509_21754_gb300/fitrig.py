@@ -51,7 +51,9 @@ class Result(ctypes.Structure):
 
 RESULT_DTYPE = np.dtype([("field", np.int32), ("unit", np.int32), ("ncand", np.int32),
                          ("status", np.int32), ("t_arrival_ns", np.int64),
-                         ("t_done_ns", np.int64), ("cand_offset", np.int64)])
+                         ("t_done_ns", np.int64), ("cand_offset", np.int64),
+                         ("t_push_ns", np.int64), ("t_enqueued_ns", np.int64),
+                         ("copy_ms", np.float32), ("trigger_ms", np.float32)])
 
 CANDIDATE_DTYPE = np.dtype([("x", np.int32), ("y", np.int32), ("snapshot", np.int32),
                             ("significance", np.float32), ("branch", np.int32),

@@ -136,3 +136,10 @@ def test_spectrum_map_checks_its_arguments_without_a_device(lib):
     assert L.fitrig_spectrum_map(p, 256, 8, 8, 1, p, p, 3, 0, None) == F.EINVAL       # method
     assert L.fitrig_spectrum_map(p, 300, 8, 8, 1, p, p, F.SPECTRUM_RADIX, 0, None) == F.EUNSUPPORTED
     assert L.fitrig_spectrum_map(p, 64, 8, 8, 1, p, p, F.SPECTRUM_RADIX, 0, None) == F.EUNSUPPORTED
+
+
+def test_result_and_candidate_records_match_the_header():
+    """The binding's record types have the sizes fitrig.h documents."""
+    from paper_2509_21754_gb300 import fitrig as F
+    assert F.RESULT_DTYPE.itemsize == 64
+    assert F.CANDIDATE_DTYPE.itemsize == 32

@@ -63,6 +63,10 @@ def test_units_equal_batch_trigger(storage, tdt, noise, w):
             assert r["status"] in (F.OK, F.ENONFINITE)
             assert c.tobytes() == want.tobytes(), s
             assert r["t_done_ns"] >= r["t_arrival_ns"]
+            # the latency accounting is ordered and its device times are sane
+            assert r["t_arrival_ns"] <= r["t_push_ns"] <= r["t_enqueued_ns"] <= r["t_done_ns"]
+            assert 0.0 <= r["copy_ms"] < 1e3 and 0.0 < r["trigger_ms"] < 1e3
+            assert r["copy_ms"] + r["trigger_ms"] <= (r["t_done_ns"] - r["t_push_ns"]) / 1e6 + 1.0
     finally:
         F.fitrig_server_destroy(srv)
 

@@ -1159,7 +1159,7 @@ constexpr int kSplitRuns = 512;
 constexpr int kSplitPool = kSplitRuns * 32;     // sample keys (64 KB of shared memory)
 constexpr int kSplitChunk = 8192;               // values per CTA of a pass
 constexpr int kSplitPassThreads = 256;
-constexpr int kSplitThreads = 512;              // bracket and select kernels
+constexpr int kSplitThreads = 1024;             // bracket and select kernels
 constexpr int kSplitBins = 2048;
 constexpr int kSplitGather = 8192;              // copies of the rank's bin kept in shared memory
 
@@ -1408,7 +1408,10 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_bracket(const float* __
   }
 }
 
-// 2./4. One chunk of one map: counts and copies (see above).
+// 2./4. One chunk of one map: counts and copies (see above).  Each thread
+// handles 32 values (eight float4 loads issued together), counts in
+// registers, and notes which of its values are copies in a bit mask; the
+// copies (a few percent) are appended once per thread after a warp scan.
 template <bool VEC, bool MAD>
 __global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* __restrict__ vals,
                                                                   int64_t stride, SplitState* st,
@@ -1429,53 +1432,69 @@ __global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* _
   const float med = s.med;
   const float* v = vals + (size_t)g * stride;
   if (tid == 0) nbuf = 0;
-  __syncthreads();
-  unsigned below = 0, fin = 0;
-  auto take = [&](float x) {
-    const bool f = finite_bits(x);
-    const uint32_t key = f ? (MAD ? f32_key(fabsf(x - med)) : f32_key(x)) : kNoKey;
-    fin += f;
-    below += key < lo;
-    const bool cp = key >= lo && key <= hi;   // never a non-finite value (hi < kNoKey)
-    const unsigned m = __ballot_sync(0xffffffffu, cp);
-    if (m) {
-      unsigned b = 0;
-      if (lane == __ffs(m) - 1) b = atomicAdd(&nbuf, (unsigned)__popc(m));
-      b = __shfl_sync(0xffffffffu, b, __ffs(m) - 1);
-      if (cp) buf[b + __popc(m & ((1u << lane) - 1u))] = key;
-    }
-  };
+  constexpr int U = kSplitChunk / kSplitPassThreads;   // values per thread (32)
+  float x[U];
   if (VEC) {
-    // chunk starts are multiples of 8192 values and stride % 4 == 0
+    // chunk starts are multiples of kSplitChunk values and stride % 4 == 0
     const float4* v4 = reinterpret_cast<const float4*>(v);
-    constexpr int U = kSplitChunk / 4 / kSplitPassThreads;   // float4 per thread
-    float4 q[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
+    for (int u = 0; u < U / 4; ++u) {
       const int64_t i = c0 / 4 + (int64_t)u * kSplitPassThreads + tid;
-      q[u] = i < c1 / 4 ? v4[i] : make_float4(NAN, NAN, NAN, NAN);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      take(q[u].x);
-      take(q[u].y);
-      take(q[u].z);
-      take(q[u].w);
+      const float4 q = i < c1 / 4 ? v4[i] : make_float4(NAN, NAN, NAN, NAN);
+      x[4 * u] = q.x;
+      x[4 * u + 1] = q.y;
+      x[4 * u + 2] = q.z;
+      x[4 * u + 3] = q.w;
     }
   } else {
-    for (int64_t b = c0; b < c1; b += kSplitPassThreads) {
-      const int64_t i = b + tid;
-      take(i < c1 ? v[i] : NAN);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = c0 + (int64_t)u * kSplitPassThreads + tid;
+      x[u] = i < c1 ? v[i] : NAN;
     }
   }
+  auto key_of = [&](float e) -> uint32_t {
+    return finite_bits(e) ? (MAD ? f32_key(fabsf(e - med)) : f32_key(e)) : kNoKey;
+  };
+  unsigned below = 0, fin = 0;
+  uint32_t cmask = 0;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const uint32_t key = key_of(x[u]);
+    fin += key != kNoKey;
+    below += key < lo;
+    cmask |= (uint32_t)(key >= lo && key <= hi) << u;   // never a non-finite value
+  }
+  // this thread's copies, appended after a warp scan of the counts
+  const int nc = __popc(cmask);
+  int incl = nc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int wtot = __shfl_sync(0xffffffffu, incl, 31);
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     below += __shfl_xor_sync(0xffffffffu, below, o);
     fin += __shfl_xor_sync(0xffffffffu, fin, o);
   }
+  __syncthreads();   // nbuf is initialised
+  unsigned wbase = 0;
   if (lane == 0) {
     red[0][warp] = below;
     red[1][warp] = fin;
+    if (wtot) wbase = atomicAdd(&nbuf, (unsigned)wtot);
+  }
+  wbase = __shfl_sync(0xffffffffu, wbase, 0);
+  unsigned pos = wbase + incl - nc;
+  for (uint32_t m = cmask; m; m &= m - 1) {
+    const int u = __ffs(m) - 1;
+    float e = 0.f;
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (k == u) e = x[k];   // register array: select without local memory
+    buf[pos++] = key_of(e);
   }
   __syncthreads();
   if (tid == 0) {

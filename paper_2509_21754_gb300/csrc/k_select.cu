@@ -418,9 +418,7 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
 // OR'ed in afterwards, and an ordered compaction of the bitmap gives the peak
 // list in (group, t) order.
 constexpr int kBlkT = kBlkY * kBlkX;
-constexpr int kBlkThreads = 512;
-constexpr int kBlkPer = kBlkT / kBlkThreads;            // tiles per thread
-constexpr int kBlkRowsPer = kBlkThreads / kBlkX;        // block rows per pass of the threads
+constexpr int kBlkThreads = 256;
 constexpr int kBlkRing = 2 * kBlkX + 2 * (kBlkY - 2);   // edge tiles of a block
 constexpr int kBlkHalo = 2 * (kBlkX + 2) + 2 * kBlkY;   // halo tiles of a block
 
@@ -502,31 +500,56 @@ __device__ __forceinline__ void dir_offset(int d, int* dy, int* dx) {
   *dx = k % 3 - 1;
 }
 
+// Run-based labelling on bit masks.  Row y of the block is a 64-bit mask; a
+// run is a maximal sequence of set bits, identified by its first bit, and is a
+// node of the shared-memory union-find (node y * 64 + start).  Runs of
+// adjacent rows are joined when they touch 8-connectedly (overlap after
+// dilating one by a bit on each side).
+__device__ __forceinline__ uint64_t run_starts(uint64_t m) { return m & ~(m << 1); }
+
+// First bit of the run of m that contains bit b (b set in m).
+__device__ __forceinline__ int run_of(uint64_t m, int b) {
+  const uint64_t st = run_starts(m) & (b == 63 ? ~0ull : ((2ull << b) - 1ull));
+  return 63 - __clzll((long long)st);
+}
+
+// Bits s.. of the run of m starting at s.
+__device__ __forceinline__ uint64_t run_bits(uint64_t m, int s) {
+  const uint64_t from = m >> s;
+  const int len = __ffsll((long long)~from) - 1;   // < 64 unless the run reaches bit 63
+  const uint64_t ones = (len <= 0 || len >= 64) ? ~0ull : ((1ull << len) - 1ull);
+  return (len == 0 ? 0ull : ones) << s;
+}
+
 __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict__ vals,
                                                         int64_t stride, int Tx, int Ty,
                                                         const float* __restrict__ thr,
                                                         BlockScratch b, unsigned* status) {
-  __shared__ uint8_t msk[kBlkY + 2][kBlkX + 2];
-  __shared__ int par[kBlkT];
+  __shared__ unsigned long long mrow[kBlkY];   // the block's rows
+  __shared__ unsigned long long htop, hbot;   // halo rows above / below (block columns)
+  __shared__ uint32_t hleft, hright;        // halo columns (bit = block row)
+  __shared__ uint32_t hcorner;              // bits: 0 top-left, 1 top-right, 2 bottom-left, 3 bottom-right
+  __shared__ int par[kBlkT];                // union-find over run starts
   __shared__ unsigned long long pkey[kBlkT];
   __shared__ uint8_t bnd[kBlkT];
   __shared__ int bid[kBlkT];
-  __shared__ uint32_t pw[kBlkY][kBlkX / 32];
+  __shared__ uint32_t pw[kBlkY][2];
   __shared__ int nsel_sh;
   const int g = blockIdx.z;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tx0 = blockIdx.x * kBlkX, ty0 = blockIdx.y * kBlkY;
   const float th = thr[g];
   const float* v = vals + (size_t)g * stride;
-  // 1. every load first: the thread's kBlkPer tiles (column tid % kBlkX, rows
-  // tid / kBlkX + kBlkRowsPer k) and one halo tile
-  const int lx0 = tid % kBlkX, ly0 = tid / kBlkX;
-  const int gx = tx0 + lx0;
-  float x[kBlkPer];
+  // 1. every load first: warp w takes rows w + 8 j (j < 4), both 32-column
+  // halves; threads below kBlkHalo also take one halo tile
+  constexpr int NW = kBlkThreads / 32;
+  constexpr int NL = 2 * kBlkY / NW;   // loads per lane
+  float x[NL];
 #pragma unroll
-  for (int k = 0; k < kBlkPer; ++k) {
-    const int gy = ty0 + ly0 + kBlkRowsPer * k;
-    x[k] = (gx < Tx && gy < Ty) ? v[(int64_t)gy * Tx + gx] : NAN;
+  for (int i = 0; i < NL; ++i) {
+    const int row = warp + NW * (i >> 1), col = (i & 1) * 32 + lane;
+    const int gy = ty0 + row, gx = tx0 + col;
+    x[i] = (gx < Tx && gy < Ty) ? v[(int64_t)gy * Tx + gx] : NAN;
   }
   float xh = NAN;
   int hy = 0, hx = 0;
@@ -535,122 +558,172 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
     const int gy = ty0 + hy, gxh = tx0 + hx;
     if (gy >= 0 && gy < Ty && gxh >= 0 && gxh < Tx) xh = v[(int64_t)gy * Tx + gxh];
   }
-  if (tid == 0) nsel_sh = 0;
-  if (tid < kBlkY * (kBlkX / 32)) (&pw[0][0])[tid] = 0u;
+  if (tid == 0) {
+    htop = hbot = 0ull;
+    hleft = hright = hcorner = 0u;
+    nsel_sh = 0;
+  }
+  __syncthreads();
+  // 2. masks (NaN -- an invalid tile or one beyond the map -- is never selected)
   int mine = 0;
 #pragma unroll
-  for (int k = 0; k < kBlkPer; ++k) {
-    const int ly = ly0 + kBlkRowsPer * k, li = ly * kBlkX + lx0;
-    const bool sel = x[k] > th;   // NaN (invalid tile, or beyond the map) is never selected
-    mine += sel;
-    msk[ly + 1][lx0 + 1] = sel;
-    par[li] = sel ? li : -1;
-    pkey[li] = 0ull;
-    bnd[li] = 0;
-  }
-  if (tid < kBlkHalo) msk[hy + 1][hx + 1] = xh > th;
-  __syncthreads();
-  // 2. unions inside the block (left, up-left, up, up-right)
-#pragma unroll
-  for (int k = 0; k < kBlkPer; ++k) {
-    const int ly = ly0 + kBlkRowsPer * k, lx = lx0, li = ly * kBlkX + lx;
-    if (!msk[ly + 1][lx + 1]) continue;
-    if (lx > 0 && msk[ly + 1][lx]) unite_s(par, li, li - 1, status);
-    if (ly > 0) {
-      if (msk[ly][lx + 1]) unite_s(par, li, li - kBlkX, status);
-      if (lx > 0 && msk[ly][lx]) unite_s(par, li, li - kBlkX - 1, status);
-      if (lx + 1 < kBlkX && msk[ly][lx + 2]) unite_s(par, li, li - kBlkX + 1, status);
+  for (int i = 0; i < NL; i += 2) {
+    const int row = warp + NW * (i >> 1);
+    const uint32_t lo = __ballot_sync(0xffffffffu, x[i] > th);
+    const uint32_t hi = __ballot_sync(0xffffffffu, x[i + 1] > th);
+    if (lane == 0) {
+      mrow[row] = ((uint64_t)hi << 32) | lo;
+      mine += __popc(lo) + __popc(hi);
     }
   }
-  __syncthreads();
-  // 3. roots (read-only finds, then one write each), boundary flags, peak keys
-  int root[kBlkPer];
-#pragma unroll
-  for (int k = 0; k < kBlkPer; ++k) {
-    const int li = (ly0 + kBlkRowsPer * k) * kBlkX + lx0;
-    root[k] = par[li] >= 0 ? find_s(par, li) : -1;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < kBlkPer; ++k) {
-    if (root[k] < 0) continue;
-    const int ly = ly0 + kBlkRowsPer * k, lx = lx0, li = ly * kBlkX + lx;
-    par[li] = root[k];
-    const uint32_t t = (uint32_t)((ty0 + ly) * Tx + (tx0 + lx));
-    atomicMax(&pkey[root[k]], peak_key(x[k], t));
-    if (ly == 0 || ly == kBlkY - 1 || lx == 0 || lx == kBlkX - 1) {
-      bool out = false;
-#pragma unroll
-      for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int ny = ly + dy, nx = lx + dx;
-          const bool outside = ny < 0 || ny >= kBlkY || nx < 0 || nx >= kBlkX;
-          out = out || (outside && msk[ny + 1][nx + 1]);
-        }
-      if (out) bnd[root[k]] = 1;
-    }
-  }
-  __syncthreads();
-  // 4. roots: an interior component's peak bit; a boundary component's id
-#pragma unroll
-  for (int k = 0; k < kBlkPer; ++k) {
-    const int li = (ly0 + kBlkRowsPer * k) * kBlkX + lx0;
-    if (root[k] != li) continue;
-    const unsigned long long key = pkey[li];
-    if (!bnd[li]) {
-      const uint32_t t = 0xffffffffu - (uint32_t)key;
-      const int pty = (int)(t / (uint32_t)Tx), ptx = (int)(t - (uint32_t)pty * (uint32_t)Tx);
-      const int ply = pty - ty0, plx = ptx - tx0;
-      atomicOr(&pw[ply][plx >> 5], 1u << (plx & 31));
+  if (tid < kBlkHalo && xh > th) {
+    if (hy == -1 || hy == kBlkY) {
+      if (hx == -1 || hx == kBlkX)
+        atomicOr(&hcorner, 1u << ((hy == kBlkY ? 2 : 0) + (hx == kBlkX ? 1 : 0)));
+      else
+        atomicOr(hy == -1 ? &htop : &hbot, 1ull << hx);
     } else {
-      const int id = atomicAdd(&b.counters[0], 1);
-      if (id < b.cap) {
-        b.bpar[id] = id;
-        b.bgrp[id] = g;
-        b.bkey[id] = key;
-        b.rkey[id] = key;
-        bid[li] = id;
-      } else {
-        bid[li] = -1;
-        atomicOr(status, kErrCapacity);
+      atomicOr(hx == -1 ? &hleft : &hright, 1u << hy);
+    }
+  }
+  __syncthreads();
+  // 3. runs: one thread per row initialises its run nodes, then joins them
+  // with the touching runs of the row above
+  const int y = tid;   // row of this thread in the run steps (tid < kBlkY)
+  uint64_t m = 0ull;
+  if (y < kBlkY) {
+    m = mrow[y];
+    for (uint64_t st = run_starts(m); st; st &= st - 1) {
+      const int sb = __ffsll((long long)st) - 1;
+      par[y * kBlkX + sb] = y * kBlkX + sb;
+      pkey[y * kBlkX + sb] = 0ull;
+      bnd[y * kBlkX + sb] = 0;
+    }
+  }
+  __syncthreads();
+  if (y > 0 && y < kBlkY) {
+    const uint64_t u = mrow[y - 1];
+    for (uint64_t st = run_starts(m); st; st &= st - 1) {
+      const int sb = __ffsll((long long)st) - 1;
+      const uint64_t rb = run_bits(m, sb);
+      uint64_t nb = (rb | (rb << 1) | (rb >> 1)) & u;
+      while (nb) {
+        const int ub = __ffsll((long long)nb) - 1;
+        const int us = run_of(u, ub);
+        unite_s(par, y * kBlkX + sb, (y - 1) * kBlkX + us, status);
+        nb &= ~run_bits(u, us);
       }
     }
   }
   __syncthreads();
-  // 5. edge tiles of boundary components: their label, and each selected
+  // 4. roots of the runs (read-only finds, then one write each) and the
+  // boundary flag: a run touching a selected tile outside the block
+  if (y < kBlkY) {
+    for (uint64_t st = run_starts(m); st; st &= st - 1) {
+      const int sb = __ffsll((long long)st) - 1;
+      const int r = find_s(par, y * kBlkX + sb);
+      const uint64_t rb = run_bits(m, sb);
+      const uint64_t dil = rb | (rb << 1) | (rb >> 1);
+      bool out = false;
+      if (y == 0) out = out || (dil & htop) || ((rb & 1ull) && (hcorner & 1u)) ||
+                          ((rb >> 63) && (hcorner & 2u));
+      if (y == kBlkY - 1) out = out || (dil & hbot) || ((rb & 1ull) && (hcorner & 4u)) ||
+                                  ((rb >> 63) && (hcorner & 8u));
+      const uint32_t near = (uint32_t)((7ull << y) >> 1);   // block rows y-1..y+1 as halo-column bits
+      if (rb & 1ull) out = out || (hleft & near);
+      if (rb >> 63) out = out || (hright & near);
+      if (out) bnd[r] = 1;   // benign: every writer stores 1
+    }
+  }
+  __syncthreads();
+  if (y < kBlkY) {   // point every run straight at its root (roots no longer change)
+    for (uint64_t st = run_starts(m); st; st &= st - 1) {
+      const int sb = __ffsll((long long)st) - 1;
+      par[y * kBlkX + sb] = find_s(par, y * kBlkX + sb);
+    }
+  }
+  __syncthreads();
+  // 5. peak keys: every selected tile raises its component's key
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    const int row = warp + NW * (i >> 1), col = (i & 1) * 32 + lane;
+    if (!(x[i] > th)) continue;
+    const int r = par[row * kBlkX + run_of(mrow[row], col)];
+    const uint32_t t = (uint32_t)((ty0 + row) * Tx + (tx0 + col));
+    atomicMax(&pkey[r], peak_key(x[i], t));
+  }
+  if (tid < kBlkY) pw[tid][0] = pw[tid][1] = 0u;
+  __syncthreads();
+  // 6. roots: an interior component's peak bit; a boundary component's id
+  if (y < kBlkY) {
+    for (uint64_t st = run_starts(m); st; st &= st - 1) {
+      const int sb = __ffsll((long long)st) - 1;
+      const int li = y * kBlkX + sb;
+      if (par[li] != li) continue;
+      const unsigned long long key = pkey[li];
+      if (!bnd[li]) {
+        const uint32_t t = 0xffffffffu - (uint32_t)key;
+        const int pty = (int)(t / (uint32_t)Tx), ptx = (int)(t - (uint32_t)pty * (uint32_t)Tx);
+        const int ply = pty - ty0, plx = ptx - tx0;
+        atomicOr(&pw[ply][plx >> 5], 1u << (plx & 31));
+      } else {
+        const int id = atomicAdd(&b.counters[0], 1);
+        if (id < b.cap) {
+          b.bpar[id] = id;
+          b.bgrp[id] = g;
+          b.bkey[id] = key;
+          b.rkey[id] = key;
+          bid[li] = id;
+        } else {
+          bid[li] = -1;
+          atomicOr(status, kErrCapacity);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // 7. edge tiles of boundary components: their label, and each selected
   // neighbour across the block edge with a larger tile index as a pair; the
-  // block's peak words (a row of the block covers kBlkX / 32 whole words)
+  // block's peak words; the selected count
+  auto selected = [&](int ly, int lx) -> bool {   // -1 <= ly <= kBlkY, -1 <= lx <= kBlkX
+    if (ly >= 0 && ly < kBlkY) {
+      if (lx >= 0 && lx < kBlkX) return (mrow[ly] >> lx) & 1ull;
+      return ((lx < 0 ? hleft : hright) >> ly) & 1u;
+    }
+    if (lx >= 0 && lx < kBlkX) return ((ly < 0 ? htop : hbot) >> lx) & 1ull;
+    return (hcorner >> ((ly < 0 ? 0 : 2) + (lx < 0 ? 0 : 1))) & 1u;
+  };
   if (tid < kBlkRing) {
     int ly, lx;
     ring_pos(tid, &ly, &lx);
-    const int li = ly * kBlkX + lx;
-    if (msk[ly + 1][lx + 1] && bnd[par[li]]) {
-      const int64_t t = (int64_t)(ty0 + ly) * Tx + (tx0 + lx);
-      b.glab[(size_t)g * stride + t] = bid[par[li]];
+    if (selected(ly, lx)) {
+      const int r = par[ly * kBlkX + run_of(mrow[ly], lx)];
+      if (bnd[r]) {
+        const int64_t t = (int64_t)(ty0 + ly) * Tx + (tx0 + lx);
+        b.glab[(size_t)g * stride + t] = bid[r];
 #pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        int dy, dx;
-        dir_offset(d, &dy, &dx);
-        const int ny = ly + dy, nx = lx + dx;
-        const bool outside = ny < 0 || ny >= kBlkY || nx < 0 || nx >= kBlkX;
-        if (!outside || !msk[ny + 1][nx + 1]) continue;
-        if (dy * Tx + dx <= 0) continue;   // the other tile records it
-        const int pi = atomicAdd(&b.counters[3], 1);
-        if (pi < b.pcap)
-          b.pairs[pi] = ((unsigned long long)g << 40) | ((unsigned long long)t << 3) | (unsigned)d;
-        else
-          atomicOr(status, kErrCapacity);
+        for (int d = 0; d < 8; ++d) {
+          int dy, dx;
+          dir_offset(d, &dy, &dx);
+          const int ny = ly + dy, nx = lx + dx;
+          const bool outside = ny < 0 || ny >= kBlkY || nx < 0 || nx >= kBlkX;
+          if (!outside || !selected(ny, nx)) continue;
+          if (dy * Tx + dx <= 0) continue;   // the other tile records it
+          const int pi = atomicAdd(&b.counters[3], 1);
+          if (pi < b.pcap)
+            b.pairs[pi] = ((unsigned long long)g << 40) | ((unsigned long long)t << 3) | (unsigned)d;
+          else
+            atomicOr(status, kErrCapacity);
+        }
       }
     }
   }
-  if (tid < kBlkY * (kBlkX / 32)) {
-    const int ly = tid / (kBlkX / 32), wx = tid - ly * (kBlkX / 32);
+  if (tid < 2 * kBlkY) {
+    const int ly = tid >> 1, wx = tid & 1;
     const int ty = ty0 + ly, w = tx0 / 32 + wx;
     if (ty < Ty && w < b.words) b.pbits[((size_t)g * Ty + ty) * b.words + w] = pw[ly][wx];
   }
-  for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-  if ((tid & 31) == 0 && mine) atomicAdd(&nsel_sh, mine);
+  if (lane == 0 && mine) atomicAdd(&nsel_sh, mine);
   __syncthreads();
   if (tid == 0 && nsel_sh) atomicAdd(&b.counters[1], nsel_sh);
 }
@@ -695,65 +768,63 @@ __global__ void k_blk_mark(int Tx, int Ty, BlockScratch b) {
   }
 }
 
-// Ordered compaction of the peak bitmap: per-block counts, then the writes.
-__global__ void __launch_bounds__(kSelThreads) k_pbits_count(int64_t nwords, BlockScratch b) {
-  __shared__ int wsum[kSelThreads / 32];
-  int64_t lo, hi;
-  chunk_range(nwords, b.nblk, blockIdx.x, &lo, &hi);
-  int cnt = 0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += kSelThreads) cnt += __popc(b.pbits[i]);
+// Ordered compaction of the peak bitmap: one thread per word; per-block
+// counts, their scan, then each block's words in order.
+constexpr int kPbThreads = 256;
+
+__global__ void __launch_bounds__(kPbThreads) k_pbits_count(int64_t nwords, BlockScratch b) {
+  __shared__ int wsum[kPbThreads / 32];
+  const int64_t i = (int64_t)blockIdx.x * kPbThreads + threadIdx.x;
+  int cnt = i < nwords ? __popc(b.pbits[i]) : 0;
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
   __syncthreads();
   if (threadIdx.x == 0) {
     int t = 0;
-    for (int w = 0; w < kSelThreads / 32; ++w) t += wsum[w];
+    for (int w = 0; w < kPbThreads / 32; ++w) t += wsum[w];
     b.blkcnt[blockIdx.x] = t;
   }
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_pbits_write(int64_t nwords, int Tx, int Ty,
-                                                             const float* __restrict__ vals,
-                                                             int64_t stride, BlockScratch b,
-                                                             SelItem* peaks, int64_t cap) {
-  __shared__ int wcnt[kSelThreads / 32];
-  int64_t lo, hi;
-  chunk_range(nwords, b.nblk, blockIdx.x, &lo, &hi);
+__global__ void __launch_bounds__(kPbThreads) k_pbits_write(int64_t nwords, int Tx, int Ty,
+                                                            const float* __restrict__ vals,
+                                                            int64_t stride, BlockScratch b,
+                                                            SelItem* peaks, int64_t cap) {
+  __shared__ int wcnt[kPbThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int64_t run = b.blkoff[blockIdx.x];
+  const int64_t i = (int64_t)blockIdx.x * kPbThreads + threadIdx.x;
+  const uint32_t w = i < nwords ? b.pbits[i] : 0u;
+  const int c = __popc(w);
+  int incl = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wcnt[warp] = incl;
+  __syncthreads();
+  int before = 0;
+  for (int k = 0; k < warp; ++k) before += wcnt[k];
+  if (!w) return;
   const int64_t per_group = (int64_t)Ty * b.words;
-  for (int64_t base = lo; base < hi; base += kSelThreads) {
-    const int64_t i = base + threadIdx.x;
-    const uint32_t w = i < hi ? b.pbits[i] : 0u;
-    const int c = __popc(w);
-    int incl = c;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+  const int g = (int)(i / per_group);
+  const int64_t r = i - (int64_t)g * per_group;
+  const int ty = (int)(r / b.words), wx = (int)(r - (int64_t)ty * b.words);
+  int64_t pos = (int64_t)b.blkoff[blockIdx.x] + before + incl - c;
+  // every value load of the word first, then the writes
+  constexpr int kMaxBits = 8;
+  float val[kMaxBits];
+  int tt[kMaxBits];
+  uint32_t m = w;
+  while (m) {
+    int nb = 0;
+    for (; m && nb < kMaxBits; ++nb) {
+      const int bit = __ffs(m) - 1;
+      m &= m - 1;
+      tt[nb] = ty * Tx + wx * 32 + bit;
+      val[nb] = vals[(size_t)g * stride + tt[nb]];
     }
-    if (lane == 31) wcnt[warp] = incl;
-    __syncthreads();
-    int before = 0, tile = 0;
-    for (int k = 0; k < kSelThreads / 32; ++k) {
-      before += k < warp ? wcnt[k] : 0;
-      tile += wcnt[k];
-    }
-    if (w) {
-      const int g = (int)(i / per_group);
-      const int64_t r = i - (int64_t)g * per_group;
-      const int ty = (int)(r / b.words), wx = (int)(r - (int64_t)ty * b.words);
-      int64_t pos = run + before + incl - c;
-      uint32_t m = w;
-      while (m) {
-        const int bit = __ffs(m) - 1;
-        m &= m - 1;
-        const int t = ty * Tx + wx * 32 + bit;
-        if (pos < cap) peaks[pos] = SelItem{g, t, vals[(size_t)g * stride + t]};
-        ++pos;
-      }
-    }
-    run += tile;
-    __syncthreads();
+    for (int k = 0; k < nb; ++k, ++pos)
+      if (pos < cap) peaks[pos] = SelItem{g, tt[k], val[k]};
   }
 }
 
@@ -784,7 +855,7 @@ static int block_words(int Tx) { return (Tx + 31) / 32; }
 size_t block_scratch_bytes(int groups, int Tx, int Ty, int64_t stride) {
   const int64_t cap = std::max<int64_t>(1, block_edge_tiles(Tx, Ty) * groups);
   const int64_t nw = (int64_t)groups * Ty * block_words(Tx);
-  const int nblk = 152 * 8;
+  const int64_t nblk = (nw + kPbThreads - 1) / kPbThreads;
   size_t bytes = 0;
   auto add = [&](size_t n) { bytes += (n + 255) / 256 * 256; };
   add(sizeof(int) * (size_t)groups * stride);    // glab
@@ -819,7 +890,7 @@ void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride,
   b->pairs = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * 4 * cap));
   b->pcap = 4 * cap;
   b->counters = reinterpret_cast<int*>(take(sizeof(int) * 4));
-  b->nblk = 152 * 8;
+  b->nblk = (int)((nw + kPbThreads - 1) / kPbThreads);
   b->blkcnt = reinterpret_cast<int*>(take(sizeof(int) * b->nblk));
   b->blkoff = reinterpret_cast<int*>(take(sizeof(int) * (b->nblk + 1)));
   b->cap = cap;
@@ -840,10 +911,12 @@ cudaError_t launch_block_select(const float* vals, int groups, int64_t stride, i
   k_blk_resolve<<<152 * 4, 256, 0, st>>>(b);
   k_blk_mark<<<152 * 4, 256, 0, st>>>(Tx, Ty, b);
   const int64_t nwords = (int64_t)groups * Ty * b.words;
-  k_pbits_count<<<b.nblk, kSelThreads, 0, st>>>(nwords, b);
-  k_scan_blocks<<<1, 1024, 0, st>>>(b.nblk, b.blkcnt, b.blkoff, &b.counters[2], cap, status,
+  const int64_t nb = (nwords + kPbThreads - 1) / kPbThreads;
+  if (nb > b.nblk) return cudaErrorInvalidValue;   // sized by block_scratch_carve
+  k_pbits_count<<<(unsigned)nb, kPbThreads, 0, st>>>(nwords, b);
+  k_scan_blocks<<<1, 1024, 0, st>>>((int)nb, b.blkcnt, b.blkoff, &b.counters[2], cap, status,
                                     nullptr);
-  k_pbits_write<<<b.nblk, kSelThreads, 0, st>>>(nwords, Tx, Ty, vals, stride, b, peaks, cap);
+  k_pbits_write<<<(unsigned)nb, kPbThreads, 0, st>>>(nwords, Tx, Ty, vals, stride, b, peaks, cap);
   k_blk_check<<<1, 1, 0, st>>>(b, cap, status, want);
   count_launches(8);
   return cudaGetLastError();

@@ -298,15 +298,16 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
 constexpr int kBlkY = 32, kBlkX = 64;
 struct BlockScratch {
   int* glab;                  // [groups * stride] boundary-component id of edge tiles (never cleared)
-  int* bpar;                  // [cap] union-find parents of boundary components
+  int* bpar;                  // [cap] union-find parents of boundary components (block slots)
   int* bgrp;                  // [cap] group of each boundary component
   unsigned long long* bkey;   // [cap] block-local peak key (value key << 32 | ~t)
   unsigned long long* rkey;   // [cap] merged peak key (roots)
   uint32_t* pbits;            // [groups][Ty][words] peak bitmap
-  unsigned long long* pairs;  // [pcap] selected neighbours across block edges (g, t, direction)
+  unsigned long long* pairs;  // [blocks][pairs per block] selected neighbours across block edges
   int64_t pcap;
-  int* counters;              // [0] boundary components, [1] selected tiles, [2] peaks, [3] pairs
-  int64_t cap;                // boundary components one detect can hold
+  int4* bstat;                // [blocks] boundary components, pairs, selected tiles of each block
+  int* counters;              // [2] peaks
+  int64_t cap;                // boundary-component slots (blocks x slots per block)
   int words;                  // bitmap words per tile row
   int nblk;                   // grid of the ordered compaction
   int* blkcnt;                // [nblk]

@@ -419,6 +419,8 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
 // list in (group, t) order.
 constexpr int kBlkT = kBlkY * kBlkX;
 constexpr int kBlkThreads = 256;
+constexpr int kBlkIds = 2 * kBlkX + 2 * (kBlkY - 2);   // boundary components a block can have
+constexpr int kBlkPairs = 4 * kBlkIds;                  // cross-edge pairs a block can record
 constexpr int kBlkRing = 2 * kBlkX + 2 * (kBlkY - 2);   // edge tiles of a block
 constexpr int kBlkHalo = 2 * (kBlkX + 2) + 2 * kBlkY;   // halo tiles of a block
 
@@ -534,9 +536,11 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
   __shared__ uint8_t bnd[kBlkT];
   __shared__ int bid[kBlkT];
   __shared__ uint32_t pw[kBlkY][2];
-  __shared__ int nsel_sh;
+  __shared__ int nsel_sh, nbnd_sh, npair_sh;
   const int g = blockIdx.z;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // this block's slots: boundary ids bidx * kBlkIds + k, pairs bidx * kBlkPairs + k
+  const int64_t bidx = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   const int tx0 = blockIdx.x * kBlkX, ty0 = blockIdx.y * kBlkY;
   const float th = thr[g];
   const float* v = vals + (size_t)g * stride;
@@ -561,7 +565,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
   if (tid == 0) {
     htop = hbot = 0ull;
     hleft = hright = hcorner = 0u;
-    nsel_sh = 0;
+    nsel_sh = nbnd_sh = npair_sh = 0;
   }
   __syncthreads();
   // 2. masks (NaN -- an invalid tile or one beyond the map -- is never selected)
@@ -667,17 +671,13 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
         const int ply = pty - ty0, plx = ptx - tx0;
         atomicOr(&pw[ply][plx >> 5], 1u << (plx & 31));
       } else {
-        const int id = atomicAdd(&b.counters[0], 1);
-        if (id < b.cap) {
-          b.bpar[id] = id;
-          b.bgrp[id] = g;
-          b.bkey[id] = key;
-          b.rkey[id] = key;
-          bid[li] = id;
-        } else {
-          bid[li] = -1;
-          atomicOr(status, kErrCapacity);
-        }
+        const int k = atomicAdd(&nbnd_sh, 1);   // < kBlkIds: each owns a ring tile
+        const int id = (int)(bidx * kBlkIds + k);
+        b.bpar[id] = id;
+        b.bgrp[id] = g;
+        b.bkey[id] = key;
+        b.rkey[id] = key;
+        bid[li] = id;
       }
     }
   }
@@ -709,11 +709,9 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
           const bool outside = ny < 0 || ny >= kBlkY || nx < 0 || nx >= kBlkX;
           if (!outside || !selected(ny, nx)) continue;
           if (dy * Tx + dx <= 0) continue;   // the other tile records it
-          const int pi = atomicAdd(&b.counters[3], 1);
-          if (pi < b.pcap)
-            b.pairs[pi] = ((unsigned long long)g << 40) | ((unsigned long long)t << 3) | (unsigned)d;
-          else
-            atomicOr(status, kErrCapacity);
+          const int k = atomicAdd(&npair_sh, 1);   // < kBlkPairs: at most 4 per ring tile
+          b.pairs[bidx * kBlkPairs + k] =
+              ((unsigned long long)g << 40) | ((unsigned long long)t << 3) | (unsigned)d;
         }
       }
     }
@@ -725,46 +723,69 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
   }
   if (lane == 0 && mine) atomicAdd(&nsel_sh, mine);
   __syncthreads();
-  if (tid == 0 && nsel_sh) atomicAdd(&b.counters[1], nsel_sh);
+  if (tid == 0) b.bstat[bidx] = make_int4(nbnd_sh, npair_sh, nsel_sh, 0);
 }
 
-// Unions of boundary components across block edges: one thread per recorded
-// neighbour pair joins the two tiles' component ids.
-__global__ void k_blk_merge(int64_t stride, int Tx, BlockScratch b, unsigned* status) {
-  const int np = min(b.counters[3], (int)b.pcap);
-  // ids of this detect only (the label map is never cleared; every label read
-  // here was written by k_blk_cc, and the range check keeps it so)
-  const int nid = min(b.counters[0], (int)b.cap);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
-    const unsigned long long pk = b.pairs[i];
-    const int g = (int)(pk >> 40);
-    const int64_t t = (int64_t)((pk >> 3) & ((1ull << 37) - 1));
-    int dy, dx;
-    dir_offset((int)(pk & 7u), &dy, &dx);
-    const int64_t tn = t + (int64_t)dy * Tx + dx;
-    const int* lab = b.glab + (size_t)g * stride;
-    const int me = lab[t], other = lab[tn];
-    if (me >= 0 && me < nid && other >= 0 && other < nid) unite(b.bpar, me, other, status);
+// Unions of boundary components across block edges: one warp per block joins
+// the component ids of the block's recorded neighbour pairs.
+__device__ __forceinline__ bool valid_id(const BlockScratch& b, int64_t nblocks, int id) {
+  if (id < 0) return false;
+  const int64_t blk = id / kBlkIds;
+  return blk < nblocks && (id - blk * kBlkIds) < b.bstat[blk].x;
+}
+
+__global__ void k_blk_merge(int64_t stride, int Tx, int64_t nblocks, BlockScratch b,
+                            unsigned* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; blk < nblocks;
+       blk += nw) {
+    const int np = b.bstat[blk].y;
+    for (int k = lane; k < np; k += 32) {
+      const unsigned long long pk = b.pairs[blk * kBlkPairs + k];
+      const int g = (int)(pk >> 40);
+      const int64_t t = (int64_t)((pk >> 3) & ((1ull << 37) - 1));
+      int dy, dx;
+      dir_offset((int)(pk & 7u), &dy, &dx);
+      const int64_t tn = t + (int64_t)dy * Tx + dx;
+      const int* lab = b.glab + (size_t)g * stride;
+      // the label map is never cleared: every label read here was written by
+      // k_blk_cc of this detect, and the check keeps a stale one harmless
+      const int me = lab[t], other = lab[tn];
+      if (valid_id(b, nblocks, me) && valid_id(b, nblocks, other)) unite(b.bpar, me, other, status);
+    }
   }
 }
 
 // Merged peak keys: every boundary component raises its root's key.
-__global__ void k_blk_resolve(BlockScratch b) {
-  const int n = min(b.counters[0], (int)b.cap);
-  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
-    const int r = find_g(b.bpar, id);
-    if (r != id) atomicMax(&b.rkey[r], b.bkey[id]);
+__global__ void k_blk_resolve(int64_t nblocks, BlockScratch b) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; blk < nblocks;
+       blk += nw) {
+    const int n = b.bstat[blk].x;
+    for (int k = lane; k < n; k += 32) {
+      const int id = (int)(blk * kBlkIds + k);
+      const int r = find_g(b.bpar, id);
+      if (r != id) atomicMax(&b.rkey[r], b.bkey[id]);
+    }
   }
 }
 
 // Each merged component's peak bit.
-__global__ void k_blk_mark(int Tx, int Ty, BlockScratch b) {
-  const int n = min(b.counters[0], (int)b.cap);
-  for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
-    if (b.bpar[id] != id) continue;   // roots never change after the unions
-    const uint32_t t = 0xffffffffu - (uint32_t)b.rkey[id];
-    const int ty = (int)(t / (uint32_t)Tx), tx = (int)(t - (uint32_t)ty * (uint32_t)Tx);
-    atomicOr(&b.pbits[((size_t)b.bgrp[id] * Ty + ty) * b.words + (tx >> 5)], 1u << (tx & 31));
+__global__ void k_blk_mark(int Tx, int Ty, int64_t nblocks, BlockScratch b) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; blk < nblocks;
+       blk += nw) {
+    const int n = b.bstat[blk].x;
+    for (int k = lane; k < n; k += 32) {
+      const int id = (int)(blk * kBlkIds + k);
+      if (b.bpar[id] != id) continue;   // roots never change after the unions
+      const uint32_t t = 0xffffffffu - (uint32_t)b.rkey[id];
+      const int ty = (int)(t / (uint32_t)Tx), tx = (int)(t - (uint32_t)ty * (uint32_t)Tx);
+      atomicOr(&b.pbits[((size_t)b.bgrp[id] * Ty + ty) * b.words + (tx >> 5)], 1u << (tx & 31));
+    }
   }
 }
 
@@ -828,32 +849,33 @@ __global__ void __launch_bounds__(kPbThreads) k_pbits_write(int64_t nwords, int 
   }
 }
 
-__global__ void k_blk_check(BlockScratch b, int64_t cap, unsigned* status, unsigned* want) {
-  const int n = b.counters[1];
-  if ((int64_t)n > cap) {
-    atomicOr(status, kErrCapacity);
-    if (want) atomicMax(want, (unsigned)n);
-  }
-}
-
-static int64_t block_edge_tiles(int Tx, int Ty) {
-  // edge tiles over all blocks of one map (an exact upper bound on boundary
-  // components: each owns at least one edge tile)
-  int64_t e = 0;
-  for (int by = 0; by < (Ty + kBlkY - 1) / kBlkY; ++by) {
-    const int h = std::min(kBlkY, Ty - by * kBlkY);
-    for (int bx = 0; bx < (Tx + kBlkX - 1) / kBlkX; ++bx) {
-      const int w = std::min(kBlkX, Tx - bx * kBlkX);
-      e += (h <= 2 || w <= 2) ? (int64_t)h * w : 2 * (int64_t)(h + w) - 4;
+// The selected count (the blocks' sum) against the selection capacity.
+__global__ void __launch_bounds__(1024) k_blk_check(int64_t nblocks, BlockScratch b, int64_t cap,
+                                                    unsigned* status, unsigned* want) {
+  __shared__ long long part[32];
+  long long n = 0;
+  for (int64_t i = threadIdx.x; i < nblocks; i += 1024) n += b.bstat[i].z;
+  for (int o = 16; o; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = n;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long tot = 0;
+    for (int w = 0; w < 32; ++w) tot += part[w];
+    if (tot > cap) {
+      atomicOr(status, kErrCapacity);
+      if (want) atomicMax(want, (unsigned)(tot < 0xffffffffll ? tot : 0xffffffffll));
     }
   }
-  return e;
 }
 
 static int block_words(int Tx) { return (Tx + 31) / 32; }
 
+static int64_t block_count(int groups, int Tx, int Ty) {
+  return (int64_t)groups * ((Ty + kBlkY - 1) / kBlkY) * ((Tx + kBlkX - 1) / kBlkX);
+}
+
 size_t block_scratch_bytes(int groups, int Tx, int Ty, int64_t stride) {
-  const int64_t cap = std::max<int64_t>(1, block_edge_tiles(Tx, Ty) * groups);
+  const int64_t cap = block_count(groups, Tx, Ty) * kBlkIds;
   const int64_t nw = (int64_t)groups * Ty * block_words(Tx);
   const int64_t nblk = (nw + kPbThreads - 1) / kPbThreads;
   size_t bytes = 0;
@@ -864,7 +886,8 @@ size_t block_scratch_bytes(int groups, int Tx, int Ty, int64_t stride) {
   add(sizeof(unsigned long long) * cap);         // bkey
   add(sizeof(unsigned long long) * cap);         // rkey
   add(sizeof(uint32_t) * nw);                    // pbits
-  add(sizeof(unsigned long long) * 4 * cap);     // pairs
+  add(sizeof(unsigned long long) * block_count(groups, Tx, Ty) * kBlkPairs);   // pairs
+  add(sizeof(int4) * block_count(groups, Tx, Ty));   // bstat
   add(sizeof(int) * 4);                          // counters
   add(sizeof(int) * nblk);                       // blkcnt
   add(sizeof(int) * (nblk + 1));                 // blkoff
@@ -872,7 +895,7 @@ size_t block_scratch_bytes(int groups, int Tx, int Ty, int64_t stride) {
 }
 
 void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride, BlockScratch* b) {
-  const int64_t cap = std::max<int64_t>(1, block_edge_tiles(Tx, Ty) * groups);
+  const int64_t cap = block_count(groups, Tx, Ty) * kBlkIds;
   const int64_t nw = (int64_t)groups * Ty * block_words(Tx);
   char* p = static_cast<char*>(base);
   size_t off = 0;
@@ -887,8 +910,10 @@ void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride,
   b->bkey = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * cap));
   b->rkey = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * cap));
   b->pbits = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
-  b->pairs = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * 4 * cap));
-  b->pcap = 4 * cap;
+  b->pairs = reinterpret_cast<unsigned long long*>(
+      take(sizeof(unsigned long long) * block_count(groups, Tx, Ty) * kBlkPairs));
+  b->bstat = reinterpret_cast<int4*>(take(sizeof(int4) * block_count(groups, Tx, Ty)));
+  b->pcap = block_count(groups, Tx, Ty) * kBlkPairs;
   b->counters = reinterpret_cast<int*>(take(sizeof(int) * 4));
   b->nblk = (int)((nw + kPbThreads - 1) / kPbThreads);
   b->blkcnt = reinterpret_cast<int*>(take(sizeof(int) * b->nblk));
@@ -900,16 +925,19 @@ void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride,
 cudaError_t launch_block_select(const float* vals, int groups, int64_t stride, int Tx, int Ty,
                                 const float* thr, const BlockScratch& b, SelItem* peaks,
                                 int64_t cap, unsigned* status, unsigned* want, cudaStream_t st) {
+  const int64_t nblocks = block_count(groups, Tx, Ty);
   if (groups < 1 || groups > 65535 || (Ty + kBlkY - 1) / kBlkY > 65535 ||
-      (int64_t)Tx * Ty > 0xffffffffll || b.pcap > INT_MAX)
+      (int64_t)Tx * Ty > 0xffffffffll || nblocks * kBlkIds > INT_MAX ||
+      nblocks * kBlkIds > b.cap)
     return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(b.counters, 0, sizeof(int) * 4, st);
   if (e != cudaSuccess) return e;
   const dim3 grid((Tx + kBlkX - 1) / kBlkX, (Ty + kBlkY - 1) / kBlkY, groups);
   k_blk_cc<<<grid, kBlkThreads, 0, st>>>(vals, stride, Tx, Ty, thr, b, status);
-  k_blk_merge<<<152 * 8, 256, 0, st>>>(stride, Tx, b, status);
-  k_blk_resolve<<<152 * 4, 256, 0, st>>>(b);
-  k_blk_mark<<<152 * 4, 256, 0, st>>>(Tx, Ty, b);
+  const unsigned wgrid = (unsigned)std::min<int64_t>((nblocks + 7) / 8, 152 * 16);   // a warp per block
+  k_blk_merge<<<wgrid, 256, 0, st>>>(stride, Tx, nblocks, b, status);
+  k_blk_resolve<<<wgrid, 256, 0, st>>>(nblocks, b);
+  k_blk_mark<<<wgrid, 256, 0, st>>>(Tx, Ty, nblocks, b);
   const int64_t nwords = (int64_t)groups * Ty * b.words;
   const int64_t nb = (nwords + kPbThreads - 1) / kPbThreads;
   if (nb > b.nblk) return cudaErrorInvalidValue;   // sized by block_scratch_carve
@@ -917,7 +945,7 @@ cudaError_t launch_block_select(const float* vals, int groups, int64_t stride, i
   k_scan_blocks<<<1, 1024, 0, st>>>((int)nb, b.blkcnt, b.blkoff, &b.counters[2], cap, status,
                                     nullptr);
   k_pbits_write<<<(unsigned)nb, kPbThreads, 0, st>>>(nwords, Tx, Ty, vals, stride, b, peaks, cap);
-  k_blk_check<<<1, 1, 0, st>>>(b, cap, status, want);
+  k_blk_check<<<1, 1024, 0, st>>>(nblocks, b, cap, status, want);
   count_launches(8);
   return cudaGetLastError();
 }

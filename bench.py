@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-sliding", action="store_true",
+                    help="skip the sliding-window leg on the main workload's stack")
     ap.add_argument("--no-spectrum", action="store_true",
                     help="skip the transform-alone leg at power-of-two series lengths")
     ap.add_argument("--no-batched", action="store_true",
@@ -616,6 +618,41 @@ def spectrum_run(F, torch, T=16384, lengths=(256, 512, 1024, 2048, 4096), reps=5
     return out
 
 
+# ---------------------------------------------------------------- sliding-window leg
+def sliding_run(a, F, torch, stack, storage, reps=5):
+    """The sliding-window mode (the odd w x w window centred on every pixel) on
+    the main workload's stack: the detect and its march (k_slide).  Bytes of
+    the march per launch: the stack read once (b L px) and v written per pixel
+    and unit (4 (L - 2) px)."""
+    L, ny, nx = stack.shape
+    eb = 4 if a.storage == "f32" else 2
+    st = torch.cuda.current_stream()
+    plan = F.Plan(nx, ny, L, a.window, a.nsigma, F.BRANCH_IMAGE, storage,
+                  {"meanstd": F.NOISE_MEANSTD, "medmad": F.NOISE_MEDMAD}[a.noise],
+                  stream=st.cuda_stream, stride=F.STRIDE_SLIDING)
+    try:
+        plan.push_stack(stack)
+        torch.cuda.synchronize()
+        F.fitrig_detect(plan.h)
+        F.fitrig_detect(plan.h)
+        ms, mms = [], []
+        for _ in range(reps):
+            rc, n = F.fitrig_detect(plan.h)
+            ms.append(F.fitrig_kernel_ms(plan.h, F.KERNEL_DETECT))
+            mms.append(F.fitrig_kernel_ms(plan.h, F.KERNEL_STACK))
+    finally:
+        plan.close()
+    px = L * ny * nx
+    t, tm = statistics.median(ms), statistics.median(mms)
+    alg = eb * px + 4 * (L - 2) * ny * nx
+    peak, kind = hbm_peak()
+    return {"workload": f"{L} snapshots of {nx}x{ny}, sliding {a.window}x{a.window} window, image "
+                        f"branch, {a.nsigma:g} sigma, {a.noise} noise",
+            "detect_ms": t, "value": px / (t * 1e-3) / 1e9, "unit": UNIT, "march_ms": tm,
+            "march_gb_per_s": alg / (tm * 1e-3) / 1e9, "march_frac_of_hbm": alg / (tm * 1e-3) / 1e9 / peak,
+            "candidates": int(n), "status": int(rc)}
+
+
 # ---------------------------------------------------------------- accumulation leg
 def accumulate_run(a, F, torch, stack, storage, reps=3):
     """Ingest with snapshot accumulation (Sec. 3.3.2): K raw device snapshots
@@ -767,6 +804,9 @@ def main():
         accum = accumulate_run(a, F, torch, stack, storage)
     if rank == 0 and ws == 1 and not a.no_spectrum:
         spectrum = spectrum_run(F, torch)
+    sliding = None
+    if rank == 0 and ws == 1 and not a.no_sliding:
+        sliding = sliding_run(a, F, torch, stack_s, storage)
 
     serving = batched = None
     legs = rank == 0 and ws == 1 and (not a.no_large or a.paper_run or not a.no_serving or
@@ -807,6 +847,7 @@ def main():
             "batched": batched,
             "accumulate": accum,
             "spectrum_pow2": spectrum,
+            "sliding": sliding,
             "large": large,
             "paper_run": paper,
             "clocks": clk.summary(),

@@ -523,18 +523,23 @@ __device__ __forceinline__ uint64_t run_bits(uint64_t m, int s) {
   return (len == 0 ? 0ull : ones) << s;
 }
 
+constexpr int kBlkMaxRuns = kBlkT / 2;   // runs of a block (alternating bits at most)
+
 __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict__ vals,
                                                         int64_t stride, int Tx, int Ty,
                                                         const float* __restrict__ thr,
                                                         BlockScratch b, unsigned* status) {
   __shared__ unsigned long long mrow[kBlkY];   // the block's rows
   __shared__ unsigned long long htop, hbot;   // halo rows above / below (block columns)
-  __shared__ uint32_t hleft, hright;        // halo columns (bit = block row)
-  __shared__ uint32_t hcorner;              // bits: 0 top-left, 1 top-right, 2 bottom-left, 3 bottom-right
-  __shared__ int par[kBlkT];                // union-find over run starts
-  __shared__ unsigned long long pkey[kBlkT];
-  __shared__ uint8_t bnd[kBlkT];
-  __shared__ int bid[kBlkT];
+  __shared__ uint32_t hleft, hright;          // halo columns (bit = block row)
+  __shared__ uint32_t hcorner;                // bits: 0 top-left, 1 top-right, 2 bottom-left, 3 bottom-right
+  __shared__ float val[kBlkT];                // the block's values
+  __shared__ int runbase[kBlkY + 1];          // first run of each row; runbase[kBlkY] = runs
+  __shared__ uint32_t rinfo[kBlkMaxRuns];     // run: row << 16 | start << 8 | end
+  __shared__ __align__(16) short par[kBlkMaxRuns];   // union-find over runs (CAS on aligned words)
+  __shared__ unsigned long long pkey[kBlkMaxRuns];
+  __shared__ uint8_t bnd[kBlkMaxRuns];
+  __shared__ int bid[kBlkMaxRuns];
   __shared__ uint32_t pw[kBlkY][2];
   __shared__ int nsel_sh, nbnd_sh, npair_sh;
   const int g = blockIdx.z;
@@ -567,16 +572,20 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
     hleft = hright = hcorner = 0u;
     nsel_sh = nbnd_sh = npair_sh = 0;
   }
+  if (tid < kBlkY) pw[tid][0] = pw[tid][1] = 0u;
   __syncthreads();
-  // 2. masks (NaN -- an invalid tile or one beyond the map -- is never selected)
+  // 2. masks (NaN -- an invalid tile or one beyond the map -- is never
+  // selected) and the values
   int mine = 0;
 #pragma unroll
   for (int i = 0; i < NL; i += 2) {
     const int row = warp + NW * (i >> 1);
+    val[row * kBlkX + lane] = x[i];
+    val[row * kBlkX + 32 + lane] = x[i + 1];
     const uint32_t lo = __ballot_sync(0xffffffffu, x[i] > th);
     const uint32_t hi = __ballot_sync(0xffffffffu, x[i + 1] > th);
     if (lane == 0) {
-      mrow[row] = ((uint64_t)hi << 32) | lo;
+      mrow[row] = ((unsigned long long)hi << 32) | lo;
       mine += __popc(lo) + __popc(hi);
     }
   }
@@ -591,100 +600,130 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
     }
   }
   __syncthreads();
-  // 3. runs: one thread per row initialises its run nodes, then joins them
-  // with the touching runs of the row above
-  const int y = tid;   // row of this thread in the run steps (tid < kBlkY)
-  uint64_t m = 0ull;
-  if (y < kBlkY) {
-    m = mrow[y];
-    for (uint64_t st = run_starts(m); st; st &= st - 1) {
-      const int sb = __ffsll((long long)st) - 1;
-      par[y * kBlkX + sb] = y * kBlkX + sb;
-      pkey[y * kBlkX + sb] = 0ull;
-      bnd[y * kBlkX + sb] = 0;
-    }
-  }
-  __syncthreads();
-  if (y > 0 && y < kBlkY) {
-    const uint64_t u = mrow[y - 1];
-    for (uint64_t st = run_starts(m); st; st &= st - 1) {
-      const int sb = __ffsll((long long)st) - 1;
-      const uint64_t rb = run_bits(m, sb);
-      uint64_t nb = (rb | (rb << 1) | (rb >> 1)) & u;
-      while (nb) {
-        const int ub = __ffsll((long long)nb) - 1;
-        const int us = run_of(u, ub);
-        unite_s(par, y * kBlkX + sb, (y - 1) * kBlkX + us, status);
-        nb &= ~run_bits(u, us);
-      }
-    }
-  }
-  __syncthreads();
-  // 4. roots of the runs (read-only finds, then one write each) and the
-  // boundary flag: a run touching a selected tile outside the block
-  if (y < kBlkY) {
-    for (uint64_t st = run_starts(m); st; st &= st - 1) {
-      const int sb = __ffsll((long long)st) - 1;
-      const int r = find_s(par, y * kBlkX + sb);
-      const uint64_t rb = run_bits(m, sb);
-      const uint64_t dil = rb | (rb << 1) | (rb >> 1);
-      bool out = false;
-      if (y == 0) out = out || (dil & htop) || ((rb & 1ull) && (hcorner & 1u)) ||
-                          ((rb >> 63) && (hcorner & 2u));
-      if (y == kBlkY - 1) out = out || (dil & hbot) || ((rb & 1ull) && (hcorner & 4u)) ||
-                                  ((rb >> 63) && (hcorner & 8u));
-      const uint32_t near = (uint32_t)((7ull << y) >> 1);   // block rows y-1..y+1 as halo-column bits
-      if (rb & 1ull) out = out || (hleft & near);
-      if (rb >> 63) out = out || (hright & near);
-      if (out) bnd[r] = 1;   // benign: every writer stores 1
-    }
-  }
-  __syncthreads();
-  if (y < kBlkY) {   // point every run straight at its root (roots no longer change)
-    for (uint64_t st = run_starts(m); st; st &= st - 1) {
-      const int sb = __ffsll((long long)st) - 1;
-      par[y * kBlkX + sb] = find_s(par, y * kBlkX + sb);
-    }
-  }
-  __syncthreads();
-  // 5. peak keys: every selected tile raises its component's key
+  // 3. the run list: counts per row, their scan (warp 0), then each row's runs
+  if (warp == 0) {
+    const int c = __popcll((long long)run_starts(mrow[lane]));
+    int incl = c;
 #pragma unroll
-  for (int i = 0; i < NL; ++i) {
-    const int row = warp + NW * (i >> 1), col = (i & 1) * 32 + lane;
-    if (!(x[i] > th)) continue;
-    const int r = par[row * kBlkX + run_of(mrow[row], col)];
-    const uint32_t t = (uint32_t)((ty0 + row) * Tx + (tx0 + col));
-    atomicMax(&pkey[r], peak_key(x[i], t));
-  }
-  if (tid < kBlkY) pw[tid][0] = pw[tid][1] = 0u;
-  __syncthreads();
-  // 6. roots: an interior component's peak bit; a boundary component's id
-  if (y < kBlkY) {
-    for (uint64_t st = run_starts(m); st; st &= st - 1) {
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    runbase[lane] = incl - c;
+    if (lane == 31) runbase[kBlkY] = incl;
+    __syncwarp();
+    const unsigned long long m = mrow[lane];
+    int k = incl - c;
+    for (unsigned long long st = run_starts(m); st; st &= st - 1, ++k) {
       const int sb = __ffsll((long long)st) - 1;
-      const int li = y * kBlkX + sb;
-      if (par[li] != li) continue;
-      const unsigned long long key = pkey[li];
-      if (!bnd[li]) {
-        const uint32_t t = 0xffffffffu - (uint32_t)key;
-        const int pty = (int)(t / (uint32_t)Tx), ptx = (int)(t - (uint32_t)pty * (uint32_t)Tx);
-        const int ply = pty - ty0, plx = ptx - tx0;
-        atomicOr(&pw[ply][plx >> 5], 1u << (plx & 31));
-      } else {
-        const int k = atomicAdd(&nbnd_sh, 1);   // < kBlkIds: each owns a ring tile
-        const int id = (int)(bidx * kBlkIds + k);
-        b.bpar[id] = id;
-        b.bgrp[id] = g;
-        b.bkey[id] = key;
-        b.rkey[id] = key;
-        bid[li] = id;
-      }
+      const int eb = 63 - __clzll((long long)run_bits(m, sb));
+      rinfo[k] = ((uint32_t)lane << 16) | ((uint32_t)sb << 8) | (uint32_t)eb;
+    }
+  }
+  __syncthreads();
+  const int nr = runbase[kBlkY];
+  auto run_index = [&](int row, int sb) {   // run of `row` starting at bit sb
+    const unsigned long long st = run_starts(mrow[row]);
+    return runbase[row] + __popcll((long long)(st & ((1ull << sb) - 1ull)));
+  };
+  for (int k = tid; k < nr; k += kBlkThreads) {
+    par[k] = (short)k;
+    pkey[k] = 0ull;
+    bnd[k] = 0;
+  }
+  __syncthreads();
+  // 4. unions: each run with the touching runs of the row above
+  const volatile short* vpar = par;
+  auto unite_r = [&](int a, int c) {
+    for (int it = 0; it < (1 << 16); ++it) {
+      while (vpar[a] != a) a = vpar[a];
+      while (vpar[c] != c) c = vpar[c];
+      if (a == c) return;
+      const int hi = a > c ? a : c, lo = a > c ? c : a;
+      // 16-bit compare-and-swap through the aligned 32-bit word
+      unsigned* w = reinterpret_cast<unsigned*>(&par[hi & ~1]);
+      const unsigned sh = (hi & 1) ? 16u : 0u;
+      const unsigned old = *reinterpret_cast<volatile unsigned*>(w);
+      if ((int)(short)(old >> sh) != hi) continue;
+      const unsigned nw = (old & ~(0xffffu << sh)) | ((unsigned)(unsigned short)lo << sh);
+      if (atomicCAS(w, old, nw) == old) return;
+    }
+    atomicOr(status, kErrCcLimit);
+  };
+  for (int k = tid; k < nr; k += kBlkThreads) {
+    const uint32_t ri = rinfo[k];
+    const int row = ri >> 16, sb = (ri >> 8) & 255, eb = ri & 255;
+    if (row == 0) continue;
+    const unsigned long long rb = (eb == 63 ? ~0ull : ((2ull << eb) - 1ull)) & ~((1ull << sb) - 1ull);
+    const unsigned long long u = mrow[row - 1];
+    unsigned long long nb = (rb | (rb << 1) | (rb >> 1)) & u;
+    while (nb) {
+      const int ub = __ffsll((long long)nb) - 1;
+      const int us = run_of(u, ub);
+      unite_r(k, run_index(row - 1, us));
+      nb &= ~run_bits(u, us);
+    }
+  }
+  __syncthreads();
+  // 5. per run: its root (read-only), boundary flag, peak key
+  int rootv[(kBlkMaxRuns + kBlkThreads - 1) / kBlkThreads];
+#pragma unroll
+  for (int j = 0; j < (kBlkMaxRuns + kBlkThreads - 1) / kBlkThreads; ++j) {
+    const int k = tid + j * kBlkThreads;
+    rootv[j] = -1;
+    if (k >= nr) continue;
+    int r = k;
+    while (par[r] != r) r = par[r];
+    rootv[j] = r;
+    const uint32_t ri = rinfo[k];
+    const int row = ri >> 16, sb = (ri >> 8) & 255, eb = ri & 255;
+    const unsigned long long rb = (eb == 63 ? ~0ull : ((2ull << eb) - 1ull)) & ~((1ull << sb) - 1ull);
+    const unsigned long long dil = rb | (rb << 1) | (rb >> 1);
+    bool out = false;
+    if (row == 0) out = out || (dil & htop) || (sb == 0 && (hcorner & 1u)) || (eb == 63 && (hcorner & 2u));
+    if (row == kBlkY - 1)
+      out = out || (dil & hbot) || (sb == 0 && (hcorner & 4u)) || (eb == 63 && (hcorner & 8u));
+    const uint32_t near = (uint32_t)((7ull << row) >> 1);   // block rows row-1..row+1
+    if (sb == 0) out = out || (hleft & near);
+    if (eb == 63) out = out || (hright & near);
+    if (out) bnd[r] = 1;   // benign: every writer stores 1
+    unsigned long long key = 0ull;
+    for (int c = sb; c <= eb; ++c) {
+      const uint32_t t = (uint32_t)((ty0 + row) * Tx + (tx0 + c));
+      const unsigned long long kc = peak_key(val[row * kBlkX + c], t);
+      key = kc > key ? kc : key;
+    }
+    atomicMax(&pkey[r], key);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < (kBlkMaxRuns + kBlkThreads - 1) / kBlkThreads; ++j)
+    if (rootv[j] >= 0) par[tid + j * kBlkThreads] = (short)rootv[j];   // straight to the root
+  // 6. roots: an interior component's peak bit; a boundary component's id
+#pragma unroll
+  for (int j = 0; j < (kBlkMaxRuns + kBlkThreads - 1) / kBlkThreads; ++j) {
+    const int k = tid + j * kBlkThreads;
+    if (rootv[j] != k) continue;
+    const unsigned long long key = pkey[k];
+    if (!bnd[k]) {
+      const uint32_t t = 0xffffffffu - (uint32_t)key;
+      const int pty = (int)(t / (uint32_t)Tx), ptx = (int)(t - (uint32_t)pty * (uint32_t)Tx);
+      const int ply = pty - ty0, plx = ptx - tx0;
+      atomicOr(&pw[ply][plx >> 5], 1u << (plx & 31));
+    } else {
+      const int slot = atomicAdd(&nbnd_sh, 1);   // < kBlkIds: each owns a ring tile
+      const int id = (int)(bidx * kBlkIds + slot);
+      b.bpar[id] = id;
+      b.bgrp[id] = g;
+      b.bkey[id] = key;
+      b.rkey[id] = key;
+      bid[k] = id;
     }
   }
   __syncthreads();
   // 7. edge tiles of boundary components: their label, and each selected
   // neighbour across the block edge with a larger tile index as a pair; the
-  // block's peak words; the selected count
+  // block's peak words; the counts
   auto selected = [&](int ly, int lx) -> bool {   // -1 <= ly <= kBlkY, -1 <= lx <= kBlkX
     if (ly >= 0 && ly < kBlkY) {
       if (lx >= 0 && lx < kBlkX) return (mrow[ly] >> lx) & 1ull;
@@ -697,7 +736,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
     int ly, lx;
     ring_pos(tid, &ly, &lx);
     if (selected(ly, lx)) {
-      const int r = par[ly * kBlkX + run_of(mrow[ly], lx)];
+      const int r = par[run_index(ly, run_of(mrow[ly], lx))];
       if (bnd[r]) {
         const int64_t t = (int64_t)(ty0 + ly) * Tx + (tx0 + lx);
         b.glab[(size_t)g * stride + t] = bid[r];

@@ -368,6 +368,25 @@ def serving_run(a, F, synth, torch, nfields=32, nsnap=24, compression=20.0, seed
                 with lock:
                     pushed[0] += pool.shape[1] * pool.shape[2]
 
+        # results are collected while the fields stream (the records are kept,
+        # the candidates counted and dropped, so host memory stays bounded)
+        parts, ncand, done = [], [0], threading.Event()
+
+        def collect():
+            while True:
+                last = done.is_set()
+                while True:
+                    r, c = F.fitrig_server_poll(srv, cap=1 << 14, cand_cap=1 << 22)
+                    if r.size == 0:
+                        break
+                    parts.append(r)
+                    ncand[0] += c.size
+                if last:
+                    return
+                time.sleep(0.05)
+
+        poller = threading.Thread(target=collect)
+        poller.start()
         threads = [threading.Thread(target=feed, args=(fid, pool, np.random.default_rng(seed + i)))
                    for i, (fid, pool) in enumerate(active)]
         for th in threads:
@@ -376,7 +395,10 @@ def serving_run(a, F, synth, torch, nfields=32, nsnap=24, compression=20.0, seed
             th.join()
         F.fitrig_server_drain(srv)
         t_end = time.monotonic()
-        res, _ = F.fitrig_server_poll(srv, cap=1 << 20, cand_cap=1 << 24)
+        done.set()
+        poller.join()
+        res = np.concatenate(parts) if parts else np.zeros(0, dtype=F.RESULT_DTYPE)
+        ncand = ncand[0]
         lat = (res["t_done_ns"] - res["t_arrival_ns"]) / 1e6
         used, nact, nwait = F.fitrig_server_usage(srv)
         # where the latency went, per unit: the feeder's delay before the push,
@@ -397,7 +419,8 @@ def serving_run(a, F, synth, torch, nfields=32, nsnap=24, compression=20.0, seed
                                             ("copy", copy), ("trigger", trig), ("rest", rest))}}
         return {
             "fields": len(sides), "admitted": len(active), "queued": nwait,
-            "snapshots_per_field": nsnap, "units": int(res.size),
+            "snapshots_per_field": nsnap, "units": int(res.size), "candidates": int(ncand),
+            "units_truncated": int(np.count_nonzero(res["status"] == F.ETRUNC)),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat.max()),
             "gpx_per_s": pushed[0] / (t_end - t0) / 1e9,

@@ -1453,9 +1453,21 @@ __global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* _
       x[u] = i < c1 ? v[i] : NAN;
     }
   }
+  // order-preserving key from the bits (the same map as f32_key), kNoKey for
+  // a value that is not finite; |v - med| is never negative, so its key is
+  // its bits with the sign bit set
   auto key_of = [&](float e) -> uint32_t {
-    return finite_bits(e) ? (MAD ? f32_key(fabsf(e - med)) : f32_key(e)) : kNoKey;
+    const uint32_t bits = __float_as_uint(e);
+    const bool f = (bits & 0x7f800000u) != 0x7f800000u;
+    uint32_t key;
+    if (MAD) key = __float_as_uint(fabsf(e - med)) | 0x80000000u;
+    else key = bits ^ ((uint32_t)((int32_t)bits >> 31) | 0x80000000u);
+    return f ? key : kNoKey;
   };
+  // copies: lo <= key <= hi as one unsigned compare; an empty bracket (no
+  // finite sample value: lo > hi) copies nothing
+  const bool any = hi >= lo;
+  const uint32_t span = any ? hi - lo : 0u;
   unsigned below = 0, fin = 0;
   uint32_t cmask = 0;
 #pragma unroll
@@ -1463,7 +1475,7 @@ __global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* _
     const uint32_t key = key_of(x[u]);
     fin += key != kNoKey;
     below += key < lo;
-    cmask |= (uint32_t)(key >= lo && key <= hi) << u;   // never a non-finite value
+    cmask |= (uint32_t)(any && key - lo <= span) << u;   // never a non-finite value (hi < kNoKey)
   }
   // this thread's copies, appended after a warp scan of the counts
   const int nc = __popc(cmask);

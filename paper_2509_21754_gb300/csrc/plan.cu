@@ -421,7 +421,9 @@ static int allocate(fitrig_plan_t p) {
   CK(dmalloc(p, &p->d_vp, sizeof(float) * (size_t)vslots * p->vstride));
   CK(cudaMemset(p->d_vp, 0xff, sizeof(float) * (size_t)vslots * p->vstride));   // NaN padding
   if (p->branch & FITRIG_BRANCH_FREQ) p->d_eta = p->d_vp + (size_t)U * p->vstride;
-  if (p->stride == FITRIG_STRIDE_TILE && p->geom.R == 0)
+  // the thread-per-tile march writes the in-tile arg-max for FP32 storage
+  // only (half storage recomputes it for the component peaks)
+  if (p->stride == FITRIG_STRIDE_TILE && p->geom.R == 0 && p->storage == FITRIG_F32)
     CK(dmalloc(p, &p->d_arg, (size_t)U * p->vstride));
   CK(dmalloc(p, &p->d_inv, sizeof(double) * (U + 1)));
   CK(dmalloc(p, &p->d_small, 64));

@@ -377,23 +377,15 @@ __device__ __forceinline__ void tile_unit(const T* st, const float (&xp)[W * W],
     float dd[W];
     load_row<T, W>(st + r * (32 * W), &xn[r * W]);
     sm = row_max<W>(sm, &xn[r * W]);
-    // FP32 storage tracks the in-tile arg-max here (the march is bound by
-    // memory); half storage is bound by instruction issue, so it keeps the
-    // maximum only and the candidate kernel recomputes the arg-max of peaks
-    constexpr bool kArg = sizeof(T) == 4;
 #pragma unroll
     for (int q = 0; q < W; ++q) {
       const int i = r * W + q;
       dn[i] = fabsf(xn[i] - xp[i]);       // D^(s+1)
       dd[q] = fabsf(dn[i] - dp[i]);       // Delta
       r1 += dd[q];
-      if (kArg) {
-        if (dd[q] > rm) {
-          rm = dd[q];
-          ri = q;
-        }
-      } else {
-        rm = fmaxf(rm, dd[q]);
+      if (dd[q] > rm) {
+        rm = dd[q];
+        ri = q;
       }
     }
     float pz = xp[r * W];
@@ -408,13 +400,9 @@ __device__ __forceinline__ void tile_unit(const T* st, const float (&xp)[W * W],
     }
     s1 += r1;
     s3 += r3;
-    if (kArg) {
-      if (rm > s2) {
-        s2 = rm;
-        am = r * W + ri;
-      }
-    } else {
-      s2 = fmaxf(s2, rm);
+    if (rm > s2) {
+      s2 = rm;
+      am = r * W + ri;
     }
   }
 }

@@ -110,8 +110,17 @@ struct fitrig_plan_s {
   float* d_thr = nullptr;        // units + 1
   void* d_noise = nullptr;
   void* d_split = nullptr;       // split median/MAD scratch (NoiseScratch::split)
-  void* d_blk = nullptr;         // block-tiled components (BlockScratch), both branches
+  void* d_blk = nullptr;         // block-tiled components (BlockScratch) of the image branch
   BlockScratch blk{};
+  // the frequency branch runs beside the image branch (its own stream), so
+  // it has its own noise, split, components and peak buffers
+  void* d_noise_f = nullptr;
+  void* d_split_f = nullptr;
+  void* d_blk_f = nullptr;
+  BlockScratch blk_f{};
+  SelItem* d_fpeaks = nullptr;   // [T] eta's component peaks
+  cudaStream_t side_st = nullptr;   // the image branch's post-march work
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   NoiseScratch ns_img{}, ns_freq{};
   void* d_sel = nullptr;
   SelectScratch sel{};
@@ -176,7 +185,8 @@ static void drop_graph(fitrig_plan_t p);
 static void free_all(fitrig_plan_t p) {
   drop_graph(p);
   void* ptrs[] = {p->d_stack, p->d_vp,  p->d_small, p->d_invalid,  p->d_cs, p->d_arg, p->d_inv,
-                  p->d_thr,   p->d_noise, p->d_split, p->d_blk, p->d_sel, p->d_cand, p->d_cand_tmp,
+                  p->d_thr,   p->d_noise, p->d_split, p->d_blk, p->d_noise_f, p->d_split_f,
+                  p->d_blk_f, p->d_fpeaks, p->d_sel, p->d_cand, p->d_cand_tmp,
                   p->d_bin,   p->d_tw,  p->d_staging, p->d_report, p->d_accum,
                   p->d_hist,  p->d_hwts, p->d_htw,
                   p->d_smax,  p->d_mrun, p->d_wts};   // d_eta lives inside d_vp
@@ -421,9 +431,7 @@ static int allocate(fitrig_plan_t p) {
   CK(dmalloc(p, &p->d_vp, sizeof(float) * (size_t)vslots * p->vstride));
   CK(cudaMemset(p->d_vp, 0xff, sizeof(float) * (size_t)vslots * p->vstride));   // NaN padding
   if (p->branch & FITRIG_BRANCH_FREQ) p->d_eta = p->d_vp + (size_t)U * p->vstride;
-  // the thread-per-tile march writes the in-tile arg-max for FP32 storage
-  // only (half storage recomputes it for the component peaks)
-  if (p->stride == FITRIG_STRIDE_TILE && p->geom.R == 0 && p->storage == FITRIG_F32)
+  if (p->stride == FITRIG_STRIDE_TILE && p->geom.R == 0)
     CK(dmalloc(p, &p->d_arg, (size_t)U * p->vstride));
   CK(dmalloc(p, &p->d_inv, sizeof(double) * (U + 1)));
   CK(dmalloc(p, &p->d_small, 64));
@@ -432,28 +440,41 @@ static int allocate(fitrig_plan_t p) {
   CK(dmalloc(p, &p->d_thr, sizeof(float) * (U + 1)));
   const int nblk_img = std::max(1, std::min(1024, (152 * 4 + U - 1) / U));
   const int nblk_freq = 152 * 4;
-  const size_t nb =
-      std::max(noise_scratch_bytes(U + 1, nblk_img), noise_scratch_bytes(1, nblk_freq));
-  CK(dmalloc(p, &p->d_noise, nb));
-  noise_scratch_carve(p->d_noise, U + 1, nblk_img, &p->ns_img);
-  noise_scratch_carve(p->d_noise, 1, nblk_freq, &p->ns_freq);
+  // the image branch's estimates (U maps) and eta's (one map) run on two
+  // streams at once, so each has its own scratch
+  CK(dmalloc(p, &p->d_noise, noise_scratch_bytes(U, nblk_img)));
+  noise_scratch_carve(p->d_noise, U, nblk_img, &p->ns_img);
   p->ns_img.invalid = p->d_invalid;
-  p->ns_freq.invalid = p->d_invalid;
   if (p->noise == FITRIG_NOISE_MEDMAD) {
-    // the split median/MAD form; the image maps (with eta) and the eta-only
-    // estimate never run at once, so they share one buffer
-    const size_t sb = std::max(noise_split_bytes(U + 1, p->vstride), noise_split_bytes(1, p->vstride));
+    const size_t sb = noise_split_bytes(U, p->vstride);
     if (sb > 0) {
       CK(dmalloc(p, &p->d_split, sb));
-      noise_split_carve(p->d_split, U + 1, p->vstride, &p->ns_img);
-      noise_split_carve(p->d_split, 1, p->vstride, &p->ns_freq);
+      noise_split_carve(p->d_split, U, p->vstride, &p->ns_img);
     }
   }
-  {
-    // the image branch's U maps and eta's one map run in turn: one buffer
-    const int gmax = std::max(U, 1);
-    CK(dmalloc(p, &p->d_blk, block_scratch_bytes(gmax, p->Tx, p->Ty, p->vstride)));
-    block_scratch_carve(p->d_blk, gmax, p->Tx, p->Ty, p->vstride, &p->blk);
+  if (p->branch & FITRIG_BRANCH_FREQ) {
+    CK(dmalloc(p, &p->d_noise_f, noise_scratch_bytes(1, nblk_freq)));
+    noise_scratch_carve(p->d_noise_f, 1, nblk_freq, &p->ns_freq);
+    p->ns_freq.invalid = p->d_invalid;
+    if (p->noise == FITRIG_NOISE_MEDMAD) {
+      const size_t sb = noise_split_bytes(1, p->vstride);
+      if (sb > 0) {
+        CK(dmalloc(p, &p->d_split_f, sb));
+        noise_split_carve(p->d_split_f, 1, p->vstride, &p->ns_freq);
+      }
+    }
+    CK(dmalloc(p, &p->d_blk_f, block_scratch_bytes(1, p->Tx, p->Ty, p->vstride)));
+    block_scratch_carve(p->d_blk_f, 1, p->Tx, p->Ty, p->vstride, &p->blk_f);
+    CK(dmalloc(p, &p->d_fpeaks, sizeof(SelItem) * (size_t)std::max<int64_t>(1, p->T)));
+  }
+  if (p->branch & FITRIG_BRANCH_IMAGE) {
+    CK(dmalloc(p, &p->d_blk, block_scratch_bytes(std::max(U, 1), p->Tx, p->Ty, p->vstride)));
+    block_scratch_carve(p->d_blk, std::max(U, 1), p->Tx, p->Ty, p->vstride, &p->blk);
+  }
+  if (!p->side_st) {
+    CK(cudaStreamCreateWithFlags(&p->side_st, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming));
   }
   {
     const int rc = alloc_select(p);
@@ -922,13 +943,32 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
   ca.out = p->d_cand;
   ca.nout = nout;
   ca.cap = p->cand_cap;
-  // frequency branch first: its candidates (snapshot -1) lead the sorted list
+  // a serving field's frequency branch runs once its ring of units is full
+  const bool freq = (p->branch & FITRIG_BRANCH_FREQ) && (p->hist_n == 0 || p->freq_ready);
+  const bool image = (p->branch & FITRIG_BRANCH_IMAGE) != 0;
+  // The image branch's noise, thresholds and components need only the tile
+  // statistics, so they run on the side stream beside the spectrum and the
+  // frequency branch; the two join before the image candidates are written
+  // (frequency candidates, snapshot -1, lead the sorted list).
+  cudaStream_t is = st;
+  if (image && freq) {
+    CKE(cudaEventRecord(p->fork_ev, st));
+    CKE(cudaStreamWaitEvent(p->side_st, p->fork_ev, 0));
+    is = p->side_st;
+  }
+  if (image) {
+    if (timed) rec(p, FITRIG_KERNEL_NOISE, 0, is);
+    CKE(launch_noise(p->d_vp, U, p->vstride, p->T, p->noise, p->ns_img, p->d_cs, is));
+    CKE(launch_thresholds(p->d_cs, U, p->tau, p->d_thr, p->d_inv, is));
+    if (timed) rec(p, FITRIG_KERNEL_NOISE, 1, is);
+    if (timed) rec(p, FITRIG_KERNEL_SELECT, 0, is);
+    CKE(launch_block_select(p->d_vp, U, p->vstride, p->Tx, p->Ty, p->d_thr, p->blk,
+                            p->sel.items, p->sel.capacity, status, p->sel.want, is));
+    if (is != st) CKE(cudaEventRecord(p->join_ev, is));
+  }
   if (p->d_smax)
     CKE(launch_running_norm(p->d_stack, p->storage, p->pushed, p->nyu, p->nxu, p->pitch, p->d_smax,
                             p->d_mrun, p->d_wts, st));
-  // a serving field's frequency branch runs once its ring of units is full
-  const bool freq = (p->branch & FITRIG_BRANCH_FREQ) && (p->hist_n == 0 || p->freq_ready);
-  const bool both = freq && (p->branch & FITRIG_BRANCH_IMAGE);
   if (freq) {
     mark(FITRIG_KERNEL_SPECTRUM, 0);
     if (p->hist_n > 0)   // the ring in any rotation: |X_k| ignores circular shifts
@@ -939,33 +979,17 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
                           p->d_bin, st));
     mark(FITRIG_KERNEL_SPECTRUM, 1);
     double* cs = p->d_cs + 2 * U;
-    if (both) {
-      // both branches' estimates in one launch: the U units, then eta
-      mark(FITRIG_KERNEL_NOISE, 0);
-      CKE(launch_noise(p->d_vp, U + 1, p->vstride, p->T, p->noise, p->ns_img, p->d_cs, st));
-      CKE(launch_thresholds(p->d_cs, U + 1, p->tau, p->d_thr, p->d_inv, st));
-      mark(FITRIG_KERNEL_NOISE, 1);
-    } else {
-      CKE(launch_noise(p->d_eta, 1, p->vstride, p->T, p->noise, p->ns_freq, cs, st));
-      CKE(launch_thresholds(cs, 1, p->tau, p->d_thr + U, p->d_inv + U, st));
-    }
-    CKE(launch_block_select(p->d_eta, 1, p->vstride, p->Tx, p->Ty, p->d_thr + U, p->blk,
-                            p->sel.items, p->sel.capacity, status, p->sel.want, st));
+    CKE(launch_noise(p->d_eta, 1, p->vstride, p->T, p->noise, p->ns_freq, cs, st));
+    CKE(launch_thresholds(cs, 1, p->tau, p->d_thr + U, p->d_inv + U, st));
+    CKE(launch_block_select(p->d_eta, 1, p->vstride, p->Tx, p->Ty, p->d_thr + U, p->blk_f,
+                            p->d_fpeaks, p->T, status, p->sel.want, st));
     ca.branch = FITRIG_BRANCH_FREQ;
     ca.cs = cs;              // eta's estimate (group 0 of its selection)
     ca.inv = p->d_inv + U;
-    CKE(launch_emit_peaks(ca, p->sel.items, &p->blk.counters[2], nout, p->d_cand_tmp, st));
+    CKE(launch_emit_peaks(ca, p->d_fpeaks, &p->blk_f.counters[2], nout, p->d_cand_tmp, st));
   }
-  if (p->branch & FITRIG_BRANCH_IMAGE) {
-    if (!both) {
-      mark(FITRIG_KERNEL_NOISE, 0);
-      CKE(launch_noise(p->d_vp, U, p->vstride, p->T, p->noise, p->ns_img, p->d_cs, st));
-      CKE(launch_thresholds(p->d_cs, U, p->tau, p->d_thr, p->d_inv, st));
-      mark(FITRIG_KERNEL_NOISE, 1);
-    }
-    mark(FITRIG_KERNEL_SELECT, 0);
-    CKE(launch_block_select(p->d_vp, U, p->vstride, p->Tx, p->Ty, p->d_thr, p->blk,
-                            p->sel.items, p->sel.capacity, status, p->sel.want, st));
+  if (image) {
+    if (is != st) CKE(cudaStreamWaitEvent(st, p->join_ev, 0));
     ca.branch = FITRIG_BRANCH_IMAGE;
     ca.arg = p->d_arg;
     ca.cs = p->d_cs;
@@ -2135,6 +2159,9 @@ FITRIG_API int fitrig_plan_destroy(fitrig_plan_t p) {
   for (cudaEvent_t c : p->copy_ev)
     if (c) cudaEventDestroy(c);
   if (p->own_stream) cudaStreamDestroy(p->own_stream);
+  if (p->side_st) cudaStreamDestroy(p->side_st);
+  if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+  if (p->join_ev) cudaEventDestroy(p->join_ev);
   delete p;
   return FITRIG_OK;
 }

@@ -295,7 +295,7 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
 // of one group's tile map.  Components that touch a block edge are merged
 // through a global union-find over "boundary components"; every peak ends up
 // as a bit in a dense per-group bitmap, compacted in (group, t) order.
-constexpr int kBlkY = 32, kBlkX = 64;
+constexpr int kBlkY = 64, kBlkX = 64;
 struct BlockScratch {
   int* glab;                  // [groups * stride] boundary-component id of edge tiles (never cleared)
   int* bpar;                  // [cap] union-find parents of boundary components (block slots)

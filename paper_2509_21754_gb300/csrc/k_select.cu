@@ -418,7 +418,8 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
 // OR'ed in afterwards, and an ordered compaction of the bitmap gives the peak
 // list in (group, t) order.
 constexpr int kBlkT = kBlkY * kBlkX;
-constexpr int kBlkThreads = 256;
+constexpr int kBlkThreads = 512;
+static_assert(kBlkY % 32 == 0 && kBlkY <= 64 && kBlkX == 64, "block geometry");
 constexpr int kBlkIds = 2 * kBlkX + 2 * (kBlkY - 2);   // boundary components a block can have
 constexpr int kBlkPairs = 4 * kBlkIds;                  // cross-edge pairs a block can record
 constexpr int kBlkRing = 2 * kBlkX + 2 * (kBlkY - 2);   // edge tiles of a block
@@ -531,15 +532,14 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
                                                         BlockScratch b, unsigned* status) {
   __shared__ unsigned long long mrow[kBlkY];   // the block's rows
   __shared__ unsigned long long htop, hbot;   // halo rows above / below (block columns)
-  __shared__ uint32_t hleft, hright;          // halo columns (bit = block row)
+  __shared__ unsigned long long hleft, hright;   // halo columns (bit = block row)
   __shared__ uint32_t hcorner;                // bits: 0 top-left, 1 top-right, 2 bottom-left, 3 bottom-right
   __shared__ float val[kBlkT];                // the block's values
   __shared__ int runbase[kBlkY + 1];          // first run of each row; runbase[kBlkY] = runs
   __shared__ uint32_t rinfo[kBlkMaxRuns];     // run: row << 16 | start << 8 | end
   __shared__ __align__(16) short par[kBlkMaxRuns];   // union-find over runs (CAS on aligned words)
-  __shared__ unsigned long long pkey[kBlkMaxRuns];
-  __shared__ uint8_t bnd[kBlkMaxRuns];
-  __shared__ int bid[kBlkMaxRuns];
+  __shared__ unsigned long long pkey[kBlkMaxRuns];   // peak key of each root; its id once known
+  __shared__ uint32_t bnd[kBlkMaxRuns / 32];         // boundary flag of each root (bit mask)
   __shared__ uint32_t pw[kBlkY][2];
   __shared__ int nsel_sh, nbnd_sh, npair_sh;
   const int g = blockIdx.z;
@@ -569,7 +569,8 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
   }
   if (tid == 0) {
     htop = hbot = 0ull;
-    hleft = hright = hcorner = 0u;
+    hleft = hright = 0ull;
+    hcorner = 0u;
     nsel_sh = nbnd_sh = npair_sh = 0;
   }
   if (tid < kBlkY) pw[tid][0] = pw[tid][1] = 0u;
@@ -596,28 +597,37 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
       else
         atomicOr(hy == -1 ? &htop : &hbot, 1ull << hx);
     } else {
-      atomicOr(hx == -1 ? &hleft : &hright, 1u << hy);
+      atomicOr(hx == -1 ? &hleft : &hright, 1ull << hy);
     }
   }
   __syncthreads();
-  // 3. the run list: counts per row, their scan (warp 0), then each row's runs
-  if (warp == 0) {
-    const int c = __popcll((long long)run_starts(mrow[lane]));
-    int incl = c;
+  // 3. the run list: counts per row, their scan (one thread per row, the
+  // first kBlkY / 32 warps), then each row's runs
+  __shared__ int wrun[kBlkY / 32];
+  int rc = 0, rincl = 0;
+  if (tid < kBlkY) {
+    rc = __popcll((long long)run_starts(mrow[tid]));
+    rincl = rc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+      const int y = __shfl_up_sync(0xffffffffu, rincl, o);
+      if (lane >= o) rincl += y;
     }
-    runbase[lane] = incl - c;
-    if (lane == 31) runbase[kBlkY] = incl;
-    __syncwarp();
-    const unsigned long long m = mrow[lane];
-    int k = incl - c;
+    if (lane == 31) wrun[warp] = rincl;
+  }
+  __syncthreads();
+  if (tid < kBlkY) {
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wrun[w];
+    const int k0 = before + rincl - rc;
+    runbase[tid] = k0;
+    if (tid == kBlkY - 1) runbase[kBlkY] = before + rincl;
+    const unsigned long long m = mrow[tid];
+    int k = k0;
     for (unsigned long long st = run_starts(m); st; st &= st - 1, ++k) {
       const int sb = __ffsll((long long)st) - 1;
       const int eb = 63 - __clzll((long long)run_bits(m, sb));
-      rinfo[k] = ((uint32_t)lane << 16) | ((uint32_t)sb << 8) | (uint32_t)eb;
+      rinfo[k] = ((uint32_t)tid << 16) | ((uint32_t)sb << 8) | (uint32_t)eb;
     }
   }
   __syncthreads();
@@ -629,8 +639,8 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
   for (int k = tid; k < nr; k += kBlkThreads) {
     par[k] = (short)k;
     pkey[k] = 0ull;
-    bnd[k] = 0;
   }
+  for (int k = tid; k < kBlkMaxRuns / 32; k += kBlkThreads) bnd[k] = 0u;
   __syncthreads();
   // 4. unions: each run with the touching runs of the row above
   const volatile short* vpar = par;
@@ -683,10 +693,11 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
     if (row == 0) out = out || (dil & htop) || (sb == 0 && (hcorner & 1u)) || (eb == 63 && (hcorner & 2u));
     if (row == kBlkY - 1)
       out = out || (dil & hbot) || (sb == 0 && (hcorner & 4u)) || (eb == 63 && (hcorner & 8u));
-    const uint32_t near = (uint32_t)((7ull << row) >> 1);   // block rows row-1..row+1
+    // block rows row-1..row+1 as halo-column bits
+    const unsigned long long near = row == 0 ? 3ull : (7ull << (row - 1));
     if (sb == 0) out = out || (hleft & near);
     if (eb == 63) out = out || (hright & near);
-    if (out) bnd[r] = 1;   // benign: every writer stores 1
+    if (out) atomicOr(&bnd[r >> 5], 1u << (r & 31));
     unsigned long long key = 0ull;
     for (int c = sb; c <= eb; ++c) {
       const uint32_t t = (uint32_t)((ty0 + row) * Tx + (tx0 + c));
@@ -705,7 +716,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
     const int k = tid + j * kBlkThreads;
     if (rootv[j] != k) continue;
     const unsigned long long key = pkey[k];
-    if (!bnd[k]) {
+    if (!((bnd[k >> 5] >> (k & 31)) & 1u)) {
       const uint32_t t = 0xffffffffu - (uint32_t)key;
       const int pty = (int)(t / (uint32_t)Tx), ptx = (int)(t - (uint32_t)pty * (uint32_t)Tx);
       const int ply = pty - ty0, plx = ptx - tx0;
@@ -717,7 +728,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
       b.bgrp[id] = g;
       b.bkey[id] = key;
       b.rkey[id] = key;
-      bid[k] = id;
+      pkey[k] = (unsigned long long)id;   // only this thread reads or writes a root's slot here
     }
   }
   __syncthreads();
@@ -727,7 +738,7 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
   auto selected = [&](int ly, int lx) -> bool {   // -1 <= ly <= kBlkY, -1 <= lx <= kBlkX
     if (ly >= 0 && ly < kBlkY) {
       if (lx >= 0 && lx < kBlkX) return (mrow[ly] >> lx) & 1ull;
-      return ((lx < 0 ? hleft : hright) >> ly) & 1u;
+      return ((lx < 0 ? hleft : hright) >> ly) & 1ull;
     }
     if (lx >= 0 && lx < kBlkX) return ((ly < 0 ? htop : hbot) >> lx) & 1ull;
     return (hcorner >> ((ly < 0 ? 0 : 2) + (lx < 0 ? 0 : 1))) & 1u;
@@ -737,9 +748,9 @@ __global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict_
     ring_pos(tid, &ly, &lx);
     if (selected(ly, lx)) {
       const int r = par[run_index(ly, run_of(mrow[ly], lx))];
-      if (bnd[r]) {
+      if ((bnd[r >> 5] >> (r & 31)) & 1u) {
         const int64_t t = (int64_t)(ty0 + ly) * Tx + (tx0 + lx);
-        b.glab[(size_t)g * stride + t] = bid[r];
+        b.glab[(size_t)g * stride + t] = (int)pkey[r];
 #pragma unroll
         for (int d = 0; d < 8; ++d) {
           int dy, dx;

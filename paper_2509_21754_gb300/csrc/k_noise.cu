@@ -1351,9 +1351,15 @@ __device__ void split_quantiles(const uint32_t* pool, unsigned slots, uint32_t k
     const unsigned sh = split_shift(lo, hi);
     for (int b = threadIdx.x; b < kSplitBins; b += kSplitThreads) hist[b] = 0;
     __syncthreads();
+    // slots is a multiple of 32, so every lane of a warp takes the same
+    // trips; lanes with the same bin add once (the first round's bins are
+    // concentrated)
     for (unsigned i = threadIdx.x; i < slots; i += kSplitThreads) {
       const uint32_t k = pool[i];
-      if (k >= lo && k <= hi) atomicAdd(&hist[(k - lo) >> sh], 1u);
+      const unsigned bin = (k >= lo && k <= hi) ? ((k - lo) >> sh) : 0xffffffffu;
+      const unsigned peers = __match_any_sync(0xffffffffu, bin);
+      if (bin != 0xffffffffu && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
+        atomicAdd(&hist[bin], (unsigned)__popc(peers));
     }
     __syncthreads();
     unsigned b0, b1;

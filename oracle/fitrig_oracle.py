@@ -57,6 +57,12 @@ Readings where the paper is silent or ambiguous (each is an option here):
 * snapshot accumulation (Sec. 3.3.2): the paper sums adjacent snapshots
   "progressively until there is enough difference" without a criterion; the
   reading here sums fixed, non-overlapping blocks of K consecutive snapshots.
+* difference-coded half storage (not in the paper; the precision form of the
+  trigger): snapshot 0 is kept in FP32 and every later snapshot as the
+  BF16/FP16-rounded difference from the previous *decoded* snapshot, so that
+  the steady sky, which cancels in Eq. 3, is not rounded to 8 or 11
+  significant bits.  ``delta_encode`` and ``delta_decode`` define the stored
+  form; the trigger then runs on the decoded FP32 stack.
 
 All pins of this module live in ``tests/test_oracle_pins.py``.
 """
@@ -91,6 +97,64 @@ def accumulate(raw: np.ndarray, k: int) -> np.ndarray:
     for j in range(n):
         for i in range(k):
             out[j] += raw[j * k + i]
+    return out
+
+
+# --------------------------------------------------------------------------
+# Half-precision storage: rounding and difference coding
+# --------------------------------------------------------------------------
+def round_half(x: np.ndarray, fmt: str) -> np.ndarray:
+    """FP32 values rounded to the nearest BF16 ("bf16") or IEEE binary16
+    ("f16") number, ties to even, returned as FP32.  BF16 keeps the upper 16
+    bits of the FP32 pattern: adding 0x7FFF plus the lowest kept bit and
+    truncating rounds to nearest with ties to the even pattern (an overflow
+    carries into the infinity pattern); NaN stays NaN."""
+    x = np.asarray(x, dtype=np.float32)
+    if fmt == "f16":
+        with np.errstate(over="ignore"):
+            return x.astype(np.float16).astype(np.float32)
+    if fmt != "bf16":
+        raise ValueError(fmt)
+    bits = x.view(np.uint32).astype(np.uint64)
+    kept = ((bits + 0x7FFF + ((bits >> 16) & 1)) >> 16) << 16
+    out = (kept & 0xFFFFFFFF).astype(np.uint32).view(np.float32)
+    return np.where(np.isnan(x), np.float32(np.nan), out)
+
+
+def delta_encode(stack: np.ndarray, fmt: str) -> Tuple[np.ndarray, np.ndarray]:
+    """Difference coding of a (L, ny, nx) FP32 stack, closed loop.
+
+    key = x^(0) in FP32.  The coder keeps the decoded previous snapshot xt
+    (FP32, starting at key); for s >= 1 it stores
+        q^(s)  = round_half(fl32(x^(s) - xt), fmt)
+        xt     = fl32(xt + q^(s))
+    so each decoded snapshot carries the rounding of one difference only, which
+    does not accumulate.  A non-finite input (or a difference that overflows
+    the half format) makes q non-finite, and then xt and every later decoded
+    value of that pixel are NaN or infinite: a difference stream has nothing
+    to restart from without a new key frame.  Returns (key, q) with q[0] = 0
+    and q holding half values as FP32."""
+    x = np.asarray(stack, dtype=np.float32)
+    key = x[0].copy()
+    q = np.zeros_like(x)
+    xt = key.copy()
+    with np.errstate(invalid="ignore", over="ignore"):
+        for s in range(1, x.shape[0]):
+            q[s] = round_half(x[s] - xt, fmt)          # FP32 difference, then rounded
+            xt = xt + q[s]                             # FP32 sum (numpy float32)
+    return key, q
+
+
+def delta_decode(key: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """The decoded FP32 stack of a difference-coded one: snapshot 0 is the key,
+    snapshot s the FP32 sum of snapshot s-1 and q^(s), in order."""
+    key = np.asarray(key, dtype=np.float32)
+    q = np.asarray(q, dtype=np.float32)
+    out = np.empty(q.shape, dtype=np.float32)
+    out[0] = key
+    with np.errstate(invalid="ignore", over="ignore"):
+        for s in range(1, q.shape[0]):
+            out[s] = out[s - 1] + q[s]
     return out
 
 

@@ -777,3 +777,122 @@ def test_sampled_tiles_against_pixel_loops_and_unit_tiles(edge, kind, shape, w):
             assert got["numerator"][s, j] == pytest.approx(want_v, rel=1e-12, abs=1e-300)
             assert got["numerator"][s, j] == pytest.approx(ut.numerator[ty, tx], rel=1e-12,
                                                            abs=1e-300)
+
+
+# ---------------------------------------------------------------- difference-coded half storage
+_UH = {"bf16": 2.0 ** -8, "f16": 2.0 ** -11}   # half unit roundoff (8 / 11 significant bits)
+_U32 = 2.0 ** -24
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_round_half_is_torch_round_to_nearest_even(fmt):
+    """round_half equals torch's FP32 -> BF16/FP16 conversion (round to
+    nearest, ties to even) on random values, exact ties, the largest finite
+    values, subnormals, infinities and NaN."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    x = np.concatenate([
+        rng.normal(size=20000) * 10.0 ** rng.uniform(-8, 8, size=20000),
+        # halfway between neighbouring BF16 numbers (odd and even kept patterns)
+        (np.arange(1, 200, dtype=np.uint32) << 16 | 0x8000).view(np.float32),
+        # halfway between neighbouring FP16 numbers near 1
+        1.0 + (np.arange(1, 200) + 0.5) * 2.0 ** -10,
+        [65504.0, 65519.0, 65520.0, 3.3e38, 3.4028235e38, 1e-40, -1e-42, 6e-8, 3e-8,
+         np.inf, -np.inf, 0.0, -0.0],
+    ]).astype(np.float32)
+    tdt = torch.bfloat16 if fmt == "bf16" else torch.float16
+    want = torch.from_numpy(x).to(tdt).to(torch.float32).numpy()
+    got = O.round_half(x, fmt)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    assert np.isnan(O.round_half(np.array([np.nan], np.float32), fmt)[0])
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_delta_coding_exact_when_differences_are_representable(fmt):
+    """Integer snapshots whose frame-to-frame differences fit in the half
+    format (|d| <= 256) decode to themselves bit for bit, whatever the
+    absolute level (up to 2^20 here, far beyond the half formats)."""
+    rng = np.random.default_rng(4)
+    base = rng.integers(-2 ** 20, 2 ** 20, size=(1, 9, 11))
+    steps = rng.integers(-256, 257, size=(12, 9, 11))
+    steps[0] = 0
+    x = (base + np.cumsum(steps, axis=0)).astype(np.float32)
+    key, q = O.delta_encode(x, fmt)
+    assert np.array_equal(key, x[0])
+    assert np.array_equal(q[1:], np.diff(x, axis=0))
+    assert np.array_equal(O.delta_decode(key, q), x)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_delta_coding_error_is_one_rounding_per_snapshot(fmt):
+    """Closed loop: every decoded snapshot is within one half rounding of its
+    own frame-to-frame difference (plus FP32 roundings) of the original, on a
+    300-snapshot random walk on a 500-sigma sky, so the error does not grow
+    with the snapshot index (an open-loop coder of x^(s) - x^(s-1) drifts)."""
+    rng = np.random.default_rng(5)
+    L = 300
+    sky = rng.uniform(-20, 500, size=(16, 16))
+    x = (sky + np.cumsum(rng.normal(size=(L, 16, 16)), axis=0) * 0.1
+         + rng.normal(size=(L, 16, 16))).astype(np.float32)
+    key, q = O.delta_encode(x, fmt)
+    xt = O.delta_decode(key, q)
+    assert np.array_equal(xt[0], x[0])
+    prev = xt[0].astype(np.float64)
+    for s in range(1, L):
+        d = x[s].astype(np.float64) - prev
+        bound = (_UH[fmt] + _U32) * np.abs(d) * 1.0001 + _U32 * np.abs(xt[s]) * 1.0001
+        err = np.abs(xt[s].astype(np.float64) - x[s].astype(np.float64))
+        assert np.all(err <= bound), (s, float((err / bound).max()))
+        prev = xt[s].astype(np.float64)
+    # the open-loop alternative (rounding x^(s) - x^(s-1) itself) does drift
+    qo = np.zeros_like(x)
+    qo[1:] = O.round_half(np.diff(x, axis=0), fmt)
+    drift = np.abs(O.delta_decode(key, qo).astype(np.float64) - x).max()
+    assert drift > 4 * np.abs(xt.astype(np.float64) - x).max()
+
+
+def test_delta_coding_of_a_steady_stack_stores_zeros():
+    x = np.repeat(np.random.default_rng(6).normal(size=(1, 7, 9)).astype(np.float32) * 300, 6, 0)
+    for fmt in ("bf16", "f16"):
+        key, q = O.delta_encode(x, fmt)
+        assert not q.any()
+        assert np.array_equal(O.delta_decode(key, q), x)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "f16"])
+def test_delta_coding_non_finite_pixel_poisons_only_its_later_snapshots(fmt):
+    rng = np.random.default_rng(7)
+    x = (rng.normal(size=(8, 5, 6)) + 40).astype(np.float32)
+    y = x.copy()
+    y[3, 2, 4] = np.nan
+    y[5, 0, 1] = np.inf
+    dx = O.delta_decode(*O.delta_encode(x, fmt))
+    ky = O.delta_decode(*O.delta_encode(y, fmt))
+    bad = np.zeros(x.shape, dtype=bool)
+    bad[3:, 2, 4] = True
+    bad[5:, 0, 1] = True
+    assert np.all(~np.isfinite(ky[bad]))
+    assert np.array_equal(ky[~bad], dx[~bad])
+
+
+@pytest.mark.parametrize("fmt,p99_max", [("bf16", 2e-2), ("f16", 3e-3)])
+def test_delta_coding_keeps_the_tile_statistic_accurate(fmt, p99_max):
+    """On a dirty-image stack with steady sources up to 500 sigma, the tile
+    statistic of the decoded stack stays within a fraction of a percent of
+    the FP32 original's (p99 of the relative error), while rounding the
+    values themselves to the half format is off by whole multiples."""
+    spec = synth.small_spec(10, 200, 200, n_steady=40, n_pulsed=3, pulse_period=(3, 5))
+    x, _ = synth.make_stack(spec, seed=8, device="cpu")
+    x = x.numpy().astype(np.float32)
+
+    def v(stack):
+        return np.stack([O.unit_tiles(stack.astype(np.float64), s, 5).numerator
+                         for s in range(stack.shape[0] - 2)])
+
+    ref = v(x)
+    key, q = O.delta_encode(x, fmt)
+    rel_delta = np.abs(v(O.delta_decode(key, q)) - ref) / np.abs(ref)
+    rel_value = np.abs(v(O.round_half(x, fmt)) - ref) / np.abs(ref)
+    p99d, p99v = np.percentile(rel_delta, 99), np.percentile(rel_value, 99)
+    assert p99d < p99_max, p99d
+    assert p99v > 10 * p99d, (p99v, p99d)

@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--paper-run", action="store_true",
                     help="add the paper's end-to-end configuration: 1500 x 4096^2, frequency "
                          "branch with harmonic summing, window 32 (about 110 GB of HBM)")
+    ap.add_argument("--no-delta", action="store_true",
+                    help="skip the difference-coded half-storage leg on the main workload")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 8 x 50000^2 field with FP32 and BF16 storage (generated and "
                          "pushed one snapshot at a time; about 90 GB of device memory)")
@@ -676,6 +678,96 @@ def sliding_run(a, F, torch, stack, storage, reps=5):
             "candidates": int(n), "status": int(rc)}
 
 
+# ---------------------------------------------------------------- difference-coded half storage
+class _DevArr:
+    """A borrowed device buffer seen through the CUDA array interface."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"data": (ptr, False), "shape": shape,
+                                         "typestr": typestr, "version": 2, "strides": None}
+
+
+def delta_run(a, F, torch, stack, steps=20, e2e_steps=5):
+    """The main workload with difference-coded half storage (FP32 key frame,
+    BF16 or FP16 differences; FITRIG_OPT_CODING): device detect over the
+    resident stack, its march against the algorithmic bytes (key 4 B/px once,
+    differences 2 B/px per later snapshot, v and arg-max per tile and unit),
+    and for BF16 end to end from pinned host buffers that already hold the
+    coded form (the key frame as FP32, the differences as BF16: a producer
+    that runs the same coder), with the candidates read back every step."""
+    L, ny, nx = stack.shape
+    st = torch.cuda.current_stream()
+    noise = {"meanstd": F.NOISE_MEANSTD, "medmad": F.NOISE_MEDMAD}[a.noise]
+    peak, kind = hbm_peak()
+    out = {"workload": workload_name(a).replace(f"{a.storage.upper()} storage",
+                                                "difference-coded storage"),
+           "timing": f"CUDA events around {steps} detects"}
+    for name, code, tdt in (("bf16", F.BF16, torch.bfloat16), ("f16", F.F16, torch.float16)):
+        plan = F.Plan(nx, ny, L, a.window, a.nsigma, F.BRANCH_BOTH, code, noise,
+                      stream=st.cuda_stream, coding=F.CODING_DELTA)
+        try:
+            plan.push_stack(stack)           # FP32 on the device, coded there
+            torch.cuda.synchronize()
+            for _ in range(3):
+                F.fitrig_detect(plan.h)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            sms = []
+            e0.record(st)
+            for _ in range(steps):
+                rc, n = F.fitrig_detect(plan.h)
+                sms.append(F.fitrig_kernel_ms(plan.h, F.KERNEL_STACK))
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            Ty, Tx = F.fitrig_tile_grid(plan.h)
+            alg = 4 * ny * nx + 2 * (L - 1) * ny * nx + (4 + (1 if a.window <= 6 else 0)) * (L - 2) * Ty * Tx
+            k_ms = statistics.mean(sms)
+            leg = {"detect_ms": ms, "value": L * ny * nx / (ms * 1e-3) / 1e9, "unit": UNIT,
+                   "march_ms": k_ms, "march_alg_bytes": alg,
+                   "march_frac_of_hbm": alg / (k_ms * 1e-3) / 1e9 / peak,
+                   "candidates": int(n), "status": int(rc)}
+            if name == "bf16" and not a.no_e2e:
+                # the coded form as a producer would send it, read back once
+                key = torch.empty((ny, nx), dtype=torch.float32, pin_memory=True)
+                qh = torch.empty((L - 1, ny, nx), dtype=tdt, pin_memory=True)
+                for s_ in range(L):
+                    ptr, pitch = F.fitrig_stack_device_ptr(plan.h, s_)
+                    view = torch.as_tensor(_DevArr(ptr, (ny, pitch), "<f4" if s_ == 0 else "<i2"),
+                                           device="cuda")
+                    if s_ == 0:
+                        key.copy_(view[:, :nx])
+                    else:
+                        qh[s_ - 1].copy_(view[:, :nx].view(tdt))
+                torch.cuda.synchronize()
+                tim, cbuf, ecands = [], None, 0
+                for i in range(1 + e2e_steps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    F.fitrig_plan_reset(plan.h)
+                    F.fitrig_push_snapshot(plan.h, key)
+                    F.fitrig_push_snapshots(plan.h, qh)
+                    rc2, n2 = F.fitrig_detect(plan.h)
+                    if cbuf is None or len(cbuf) < n2:
+                        craw = torch.empty(max(n2, 1) * F.CANDIDATE_DTYPE.itemsize,
+                                           dtype=torch.uint8, pin_memory=True)
+                        cbuf = craw.numpy().view(F.CANDIDATE_DTYPE)
+                    c = F.fitrig_candidates(plan.h, n2, out=cbuf)
+                    dt = time.perf_counter() - t0
+                    if i > 0:
+                        tim.append(dt)
+                    ecands = len(c)
+                e_ms = 1e3 * statistics.mean(tim)
+                leg["e2e"] = {"value": L * ny * nx / (e_ms * 1e-3) / 1e9, "unit": UNIT,
+                              "h2d_bytes_per_step": 4 * ny * nx + 2 * (L - 1) * ny * nx,
+                              "d2h_bytes_per_step": 32 * ecands + 24, "ms_per_step": e_ms,
+                              "steps": len(tim), "candidates": int(n2)}
+                del key, qh, cbuf
+            out[name] = leg
+        finally:
+            plan.close()
+    return out
+
+
 # ---------------------------------------------------------------- accumulation leg
 def accumulate_run(a, F, torch, stack, storage, reps=3):
     """Ingest with snapshot accumulation (Sec. 3.3.2): K raw device snapshots
@@ -830,6 +922,9 @@ def main():
     sliding = None
     if rank == 0 and ws == 1 and not a.no_sliding:
         sliding = sliding_run(a, F, torch, stack_s, storage)
+    delta = None
+    if rank == 0 and ws == 1 and not a.no_delta:
+        delta = delta_run(a, F, torch, stack)
 
     serving = batched = None
     legs = rank == 0 and ws == 1 and (not a.no_large or a.paper_run or not a.no_serving or
@@ -871,6 +966,7 @@ def main():
             "accumulate": accum,
             "spectrum_pow2": spectrum,
             "sliding": sliding,
+            "delta": delta,
             "large": large,
             "paper_run": paper,
             "clocks": clk.summary(),

@@ -109,8 +109,35 @@ enum {
   FITRIG_OPT_GRAPH = 12,      /* 1 (default): replay repeated detects from a graph     */
   FITRIG_OPT_ACCUMULATE = 13, /* K >= 1: each K pushed snapshots are summed into one   */
   FITRIG_OPT_HARMONICS = 14,  /* m_max of the frequency branch's harmonic sum (1..32)  */
-  FITRIG_OPT_REFINE = 15      /* FITRIG_REFINE_PARABOLIC (default) | FITRIG_REFINE_CUBIC */
+  FITRIG_OPT_REFINE = 15,     /* FITRIG_REFINE_PARABOLIC (default) | FITRIG_REFINE_CUBIC */
+  FITRIG_OPT_CODING = 16      /* FITRIG_CODING_VALUE (default) | FITRIG_CODING_DELTA    */
 };
+/* CODING (not in the paper; half-precision storage that keeps the statistic
+ * accurate): with FITRIG_CODING_DELTA and BF16 or F16 storage the plan keeps
+ * snapshot 0 in FP32 (the key frame) and stores every later snapshot s as the
+ * half-rounded difference from the previous *decoded* snapshot:
+ *   q^(s)  = round_to_nearest_even_half(fl32(x^(s) - xt^(s-1)))
+ *   xt^(s) = fl32(xt^(s-1) + q^(s)),      xt^(0) = x^(0)
+ * The trigger runs on the decoded FP32 snapshots xt (the stack march decodes
+ * them in registers, so D, Delta and r of Eq. 3-5 see steady sky that is
+ * exact to FP32 instead of rounded to 8 or 11 significant bits).  The coder is
+ * closed-loop: each decoded snapshot carries the rounding of one difference
+ * only.  A non-finite input pixel (or a difference that overflows the half
+ * format) makes that pixel NaN/inf in every later decoded snapshot (there is
+ * no key frame to restart from).  F16 differences below 2^-14 are subnormal:
+ * scale the data so that pixel differences are well above that.
+ * Pushes: the first pushed snapshot (any dtype) becomes the key frame; a
+ * later push of FP32 (or the other half type) is encoded on the device; a
+ * later push of the storage's own half type is taken as already-encoded
+ * differences q (a producer that ran the same coder), after which FP32 pushes
+ * return ESTATE until fitrig_plan_reset (the device coder's running xt is
+ * not updated by them).  Requires FITRIG_STRIDE_TILE, a window of 3..6 or
+ * 8, 16, 32 or 64, ACCUMULATE = 1 and BF16/F16 storage (EUNSUPPORTED on the
+ * first push otherwise); not in batches or serving fields.
+ * fitrig_stack_device_ptr(plan, 0, ..) returns the FP32 key frame and its
+ * pitch in FP32 elements; slots 1.. hold the differences.  Settable before
+ * the first push; EINVAL for other values. */
+enum { FITRIG_CODING_VALUE = 0, FITRIG_CODING_DELTA = 1 };
 /* REFINE: the sub-tile position (xf, yf) of a frequency candidate.  Sec. 2.4.2
  * and the real-data evaluation of Sec. 3 interpolate the eta map (spline, bicubic or Makima) without a
  * formula.  PARABOLIC (default): per axis, the vertex of the parabola through
@@ -290,7 +317,9 @@ FITRIG_API int fitrig_tile_grid(fitrig_plan_t plan, int32_t* ty, int32_t* tx);
 FITRIG_API int fitrig_kernel_ms(fitrig_plan_t plan, int kernel, float* ms);
 
 /* fitrig_stack_device_ptr -- device address of snapshot slot s of the stack
- * and its row pitch in elements (for zero-copy producers on the same device). */
+ * and its row pitch in elements (for zero-copy producers on the same device).
+ * With FITRIG_CODING_DELTA slot 0 is the FP32 key frame (its own pitch) and
+ * slots 1.. hold the half-precision differences. */
 FITRIG_API int fitrig_stack_device_ptr(fitrig_plan_t plan, int32_t s, void** ptr,
                                        int64_t* row_pitch_elems);
 

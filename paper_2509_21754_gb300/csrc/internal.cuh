@@ -165,6 +165,8 @@ struct StackArgs {
   unsigned* status;    // error flags
   uint64_t timeout_ns;
   StackGeom g;
+  const float* key = nullptr;   // difference-coded stack: FP32 snapshot 0 ([ny][kpitch]),
+  int64_t kpitch = 0;           // the stack slots 1.. then hold half differences
 };
 
 // One field of a batched (persistent, multi-field) stack march.  The TMA
@@ -194,6 +196,15 @@ cudaError_t launch_stack(const CUtensorMap* tmap, const StackArgs& a, int storag
                          cudaStream_t st);
 cudaError_t launch_finite_max(const void* stack, int storage, int L, int ny, int nx,
                               int64_t pitch, unsigned* gmax, cudaStream_t st);
+// The same for a difference-coded stack (decoded in snapshot order): the
+// finite maximum over every snapshot into *gmax (if set), and with smax (2L
+// words, as launch_running_norm's) the finite maximum of each snapshot whose
+// fused maximum smax[k] was +inf into smax[L + k].  L <= kDeltaMaxSnaps when
+// smax is set.
+constexpr int kDeltaMaxSnaps = 8192;
+cudaError_t launch_delta_finite_max(const float* key, int64_t kpitch, const void* stack,
+                                    int storage, int L, int ny, int nx, int64_t pitch,
+                                    unsigned* gmax, unsigned* smax, cudaStream_t st);
 // One device wait, bounded like the march's, on a barrier nothing completes.
 cudaError_t launch_wait_probe(uint64_t timeout_ns, unsigned* gave_up, cudaStream_t st);
 
@@ -338,6 +349,8 @@ struct CandArgs {
   int64_t pitch;       // elements per row
   int64_t slice;       // elements per snapshot
   int zrot, zmod;      // snapshot j of unit 0 is slot (zrot + j) % zmod (zmod 0: slot = unit + j)
+  const float* key = nullptr;   // difference-coded stack: FP32 snapshot 0 (slots 1.. hold
+  int64_t kpitch = 0;           // half differences, decoded in snapshot order)
   // freq branch
   const float* eta;
   const int* bin;
@@ -383,6 +396,14 @@ cudaError_t launch_spectrum_method(const float* vp, int n, int64_t T, int64_t vs
 // Ingest conversion (fp32 <-> bf16/fp16).
 cudaError_t launch_convert(const void* src, int src_type, int64_t src_pitch, void* dst,
                            int dst_type, int64_t dst_pitch, int ny, int nx, cudaStream_t st);
+// Difference coding of one pushed snapshot (FITRIG_CODING_DELTA): with
+// `first` the snapshot goes to the FP32 key frame (pitch key_pitch) and to the
+// coder's running decoded snapshot `state` (ny x nx dense); otherwise
+// q = half(fl32(x - state)) goes to dst (dst_type, dst_pitch) and state
+// becomes fl32(state + q).
+cudaError_t launch_delta_encode(const void* src, int src_type, int64_t src_pitch, float* state,
+                                float* key, int64_t key_pitch, void* dst, int dst_type,
+                                int64_t dst_pitch, bool first, int ny, int nx, cudaStream_t st);
 // w = 1 / M^2 (M from the running-maximum key, floored at C): the weight of a
 // serving unit in the real-time frequency series.
 cudaError_t launch_unit_weight(const unsigned* gmax_key, float* w, cudaStream_t st);
@@ -399,7 +420,9 @@ cudaError_t launch_fill_probe(void* dst, int type, int64_t n, uint32_t seed, cud
 cudaError_t launch_tlisi_from_values(const float* vp, int64_t n, const unsigned* gmax,
                                      const double* m_unit, float* out, cudaStream_t st);
 // Running normalisers (real-time M): smax holds 2 * nsnap keys (the march's
-// per-snapshot maxima, then finite maxima where those were +inf).
+// per-snapshot maxima, then finite maxima where those were +inf).  A null
+// stack skips the finite maxima (a difference-coded stack: the caller runs
+// launch_delta_finite_max first).
 cudaError_t launch_running_norm(const void* stack, int storage, int L, int ny, int nx,
                                 int64_t pitch, unsigned* smax, double* m_unit, float* wts,
                                 cudaStream_t st);

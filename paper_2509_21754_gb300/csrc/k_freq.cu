@@ -761,18 +761,25 @@ __device__ __forceinline__ float load_any(const void* p, int type, int64_t i) {
   return static_cast<const float*>(p)[i];
 }
 
-__device__ __forceinline__ void store_any(void* p, int type, int64_t i, float v) {
+// Stores v in `type` (half types: round to nearest even) and returns the
+// stored value as FP32.
+__device__ __forceinline__ float store_any(void* p, int type, int64_t i, float v) {
   if (type == FITRIG_BF16) {
     unsigned short h;
     asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(v));
     static_cast<uint16_t*>(p)[i] = h;
-  } else if (type == FITRIG_F16) {
+    return __uint_as_float((uint32_t)h << 16);
+  }
+  if (type == FITRIG_F16) {
     unsigned short h;
     asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(v));
     static_cast<uint16_t*>(p)[i] = h;
-  } else {
-    static_cast<float*>(p)[i] = v;
+    float r;
+    asm("cvt.f32.f16 %0, %1;" : "=f"(r) : "h"(h));
+    return r;
   }
+  static_cast<float*>(p)[i] = v;
+  return v;
 }
 
 // Rows over blockIdx.y, columns over the threads of blockIdx.x (no per-pixel
@@ -786,6 +793,40 @@ __global__ void k_convert(const void* src, int st, int64_t sp, void* dst, int dt
 
 static dim3 image_grid(int ny, int nx) {
   return dim3((unsigned)std::min(8, (nx + 255) / 256), (unsigned)std::min(ny, 4096));
+}
+
+// Difference coding, closed loop (FITRIG_CODING_DELTA): the first snapshot is
+// kept in FP32 (key frame) and starts the coder's decoded snapshot `state`;
+// each later one stores q = round-to-nearest-even half of the FP32 difference
+// x - state, and state advances by the decoded difference, fl32(state + q),
+// exactly as the stack march decodes it.  NaN and infinities propagate.
+__global__ void k_delta_encode(const void* src, int st, int64_t sp, float* state, float* key,
+                               int64_t kp, void* dst, int dt, int64_t dp, int first, int ny,
+                               int nx) {
+  for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+    float* srow = state + (int64_t)y * nx;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+      const float v = load_any(src, st, (int64_t)y * sp + x);
+      if (first) {
+        key[(int64_t)y * kp + x] = v;
+        srow[x] = v;
+      } else {
+        const float prev = srow[x];
+        const float q = store_any(dst, dt, (int64_t)y * dp + x, __fsub_rn(v, prev));
+        srow[x] = __fadd_rn(prev, q);   // the decoded difference
+      }
+    }
+  }
+}
+
+cudaError_t launch_delta_encode(const void* src, int src_type, int64_t src_pitch, float* state,
+                                float* key, int64_t key_pitch, void* dst, int dst_type,
+                                int64_t dst_pitch, bool first, int ny, int nx, cudaStream_t st) {
+  k_delta_encode<<<image_grid(ny, nx), 256, 0, st>>>(src, src_type, src_pitch, state, key,
+                                                     key_pitch, dst, dst_type, dst_pitch,
+                                                     first ? 1 : 0, ny, nx);
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 // Snapshot accumulation (Sec. 3.3.2): acc = x (first raw snapshot of a
@@ -951,7 +992,10 @@ cudaError_t launch_running_norm(const void* stack, int storage, int L, int ny, i
                                 int64_t pitch, unsigned* smax, double* m_unit, float* wts,
                                 cudaStream_t st) {
   const size_t slice = (size_t)pitch * ny;
-  if (storage == FITRIG_F32)
+  int n = 1;
+  if (!stack) {
+    // a difference-coded stack: the caller ran launch_delta_finite_max
+  } else if (storage == FITRIG_F32)
     k_snap_finite_max<float><<<152 * 2, 256, 0, st>>>(static_cast<const float*>(stack), L, ny, nx,
                                                        pitch, slice, smax);
   else if (storage == FITRIG_BF16)
@@ -960,8 +1004,9 @@ cudaError_t launch_running_norm(const void* stack, int storage, int L, int ny, i
   else
     k_snap_finite_max<f16_t><<<152 * 2, 256, 0, st>>>(static_cast<const f16_t*>(stack), L, ny, nx,
                                                        pitch, slice, smax);
+  if (stack) n = 2;
   k_running_norm<<<1, 32, 0, st>>>(smax, L, m_unit, wts);
-  count_launches(2);
+  count_launches(n);
   return cudaGetLastError();
 }
 

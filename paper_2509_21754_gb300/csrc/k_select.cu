@@ -1205,9 +1205,20 @@ __global__ void k_emit_image(CandArgs a, const SelItem* __restrict__ items, cons
     for (int q = lane; q < hw * ww; q += 32) {
       const int dy = q / ww, dx = q - (q / ww) * ww;
       const int64_t off = (int64_t)(ty * a.w + dy) * a.pitch + (tx * a.w + dx);
-      const float x0 = load_px(a.stack, a.storage, sl[0] + off);
-      const float x1 = load_px(a.stack, a.storage, sl[1] + off);
-      const float x2 = load_px(a.stack, a.storage, sl[2] + off);
+      float x0, x1, x2;
+      if (a.key) {
+        // difference-coded stack (plans only: slot = snapshot): decode the
+        // pixel in snapshot order with the march's FP32 sums
+        x0 = a.key[(int64_t)(ty * a.w + dy) * a.kpitch + (tx * a.w + dx)];
+        for (int k = 1; k <= it.group; ++k)
+          x0 = __fadd_rn(x0, load_px(a.stack, a.storage, (int64_t)k * a.slice + off));
+        x1 = __fadd_rn(x0, load_px(a.stack, a.storage, sl[1] + off));
+        x2 = __fadd_rn(x1, load_px(a.stack, a.storage, sl[2] + off));
+      } else {
+        x0 = load_px(a.stack, a.storage, sl[0] + off);
+        x1 = load_px(a.stack, a.storage, sl[1] + off);
+        x2 = load_px(a.stack, a.storage, sl[2] + off);
+      }
       const float d = fabsf(fabsf(x2 - x1) - fabsf(x1 - x0));
       if (d > best) {
         best = d;

@@ -22,6 +22,12 @@
 //     warp per tile combines them in a fixed order (deterministic).
 // The one __syncthreads per snapshot also guards the reuse of ring stages, so
 // no "empty" barriers are needed.
+//
+// Difference-coded half storage (FITRIG_CODING_DELTA): the stack holds an FP32
+// key frame (snapshot 0, outside the TMA ring) and half-rounded differences
+// q^(s); the thread-per-tile marches decode xt^(s) = fl32(xt^(s-1) + q^(s)) in
+// the registers that already carry x^(s+1), so the rest of the arithmetic is
+// the FP32 march on the decoded values.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
@@ -238,6 +244,8 @@ struct Ring {
 struct FieldView {
   int nx, ny, L, Tx, Ty;
   int zrot;
+  const float* key = nullptr;   // FP32 key frame of a difference-coded stack
+  int64_t kpitch = 0;
   int64_t vstride;
   float* vp;
   uint8_t* arg;
@@ -361,7 +369,9 @@ __device__ __forceinline__ void load_row(const T* src, float* dst) {
 // takes that form; any other row (a zero pixel, the zero fill outside the
 // image, or a product that underflows) takes the guarded form of Eq. 5.  Both
 // give the same r for a non-zero x.
-template <typename T, int W, bool SIGNED>
+// With DELTA the stage holds the differences q^(s+2) and the row is decoded
+// first: x^(s+2) = fl32(x^(s+1) + q^(s+2)), the coder's own sum.
+template <typename T, int W, bool SIGNED, bool DELTA = false>
 __device__ __forceinline__ void tile_unit(const T* st, const float (&xp)[W * W],
                                           const float (&dp)[W * W], float (&xn)[W * W],
                                           float (&dn)[W * W], float& sm, float& s1, float& s2,
@@ -376,6 +386,10 @@ __device__ __forceinline__ void tile_unit(const T* st, const float (&xp)[W * W],
     int ri = 0;
     float dd[W];
     load_row<T, W>(st + r * (32 * W), &xn[r * W]);
+    if (DELTA) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) xn[r * W + q] = __fadd_rn(xp[r * W + q], xn[r * W + q]);
+    }
     sm = row_max<W>(sm, &xn[r * W]);
 #pragma unroll
     for (int q = 0; q < W; ++q) {
@@ -407,14 +421,19 @@ __device__ __forceinline__ void tile_unit(const T* st, const float (&xp)[W * W],
   }
 }
 
-// Snapshots 0 and 1 of a tile: x^(j) into xn, and D^(0) once j == 1.
-template <typename T, int W>
+// Snapshots 0 and 1 of a tile: x^(j) into xn, and D^(0) once j == 1.  With
+// DELTA (snapshot 1 only) the stage holds q^(1), decoded against x^(0) in xp.
+template <typename T, int W, bool DELTA = false>
 __device__ __forceinline__ void tile_load(const T* st, const float (&xp)[W * W],
                                           float (&xn)[W * W], float (&dn)[W * W], bool first,
                                           float& sm) {
 #pragma unroll
   for (int r = 0; r < W; ++r) {
     load_row<T, W>(st + r * (32 * W), &xn[r * W]);
+    if (DELTA) {
+#pragma unroll
+      for (int q = 0; q < W; ++q) xn[r * W + q] = __fadd_rn(xp[r * W + q], xn[r * W + q]);
+    }
     sm = row_max<W>(sm, &xn[r * W]);
   }
   if (!first) {
@@ -423,10 +442,30 @@ __device__ __forceinline__ void tile_load(const T* st, const float (&xp)[W * W],
   }
 }
 
+// The FP32 key frame of an H x W pixel block at (px, py) (plain loads: a warp
+// reads whole rows of adjacent tiles), zero outside the analysed nx x ny
+// region like the TMA fill of the differences.
+template <int H, int W>
+__device__ __forceinline__ void key_load(const float* key, int64_t kpitch, int px, int py, int nx,
+                                         int ny, float (&xn)[H * W], float& sm) {
+#pragma unroll
+  for (int r = 0; r < H; ++r) {
+    const int y = py + r;
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const int x = px + q;
+      xn[r * W + q] = (y < ny && x < nx) ? __ldg(key + (int64_t)y * kpitch + x) : 0.f;
+    }
+    sm = row_max<W>(sm, &xn[r * W]);
+  }
+}
+
 // Marches box (bx, by) of a field through its snapshots; mx collects the
 // running maximum.  Returns false (after flagging and draining, bounded) if a
 // stage never completed; the caller must then leave.
-template <typename T, int W, bool SIGNED>
+// With DELTA, snapshot 0 is the key frame (no ring stage) and the ring
+// carries the differences of snapshots 1..L-1.
+template <typename T, int W, bool SIGNED, bool DELTA = false>
 __device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const FieldView& f, int bx,
                                             int by, int tby, Ring& rg, unsigned char* smem,
                                             uint64_t deadline, float& mx) {
@@ -444,9 +483,10 @@ __device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const Field
   const int ww = live ? min(W, f.nx - tx * W) : 1;
   const float inv_n2 = 1.f / ((float)(hw * ww) * (float)(hw * ww));
   const int off = (tb * W) * (32 * W) + tbx * W;
+  const int j0 = DELTA ? 1 : 0;   // first snapshot that comes through the ring
   if (tid == 0) {
     int s = rg.stg;
-    for (int j = 0; j < rg.NS && j < L; ++j) {
+    for (int j = j0; j < j0 + rg.NS && j < L; ++j) {
       mbar_expect_tx(rg.bar0 + 8 * s, rg.box_bytes);
       tma_load_3d(rg.stage0 + s * rg.stage_bytes, tmap, x0, y0, (f.zrot + j) % L, rg.bar0 + 8 * s);
       if (++s == rg.NS) s = 0;
@@ -460,14 +500,20 @@ __device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const Field
   };
   // Two register sets alternate between x^(s+1), D^(s) and x^(s+2), D^(s+1).
   float xa[N], da[N], xb[N], db[N];
+  if (DELTA) {
+    float sm = -INFINITY;
+    key_load<W, W>(f.key, f.kpitch, x0 + tbx * W, y0 + tb * W, f.nx, f.ny, xa, sm);
+    mx = fmaxf(mx, sm);
+    if (f.smax) warp_max_to(sm, f.smax);
+  }
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
+  for (int j = j0; j < 2; ++j) {
     if (j >= L) break;
     const bool ok = ring_wait(rg, deadline);
     float sm = -INFINITY;
     if (ok) {
       if (j == 0) tile_load<T, W>(stage(), xb, xa, da, true, sm);
-      else tile_load<T, W>(stage(), xa, xb, db, false, sm);
+      else tile_load<T, W, DELTA>(stage(), xa, xb, db, false, sm);
     }
     if (!ring_release(rg, ok, tmap, f.status, j, L, x0, y0, f.zrot)) return false;
     mx = fmaxf(mx, sm);
@@ -480,7 +526,7 @@ __device__ __forceinline__ bool march_small(const CUtensorMap* tmap, const Field
     float sm = -INFINITY;
     float s1 = 0.f, s2 = 0.f, s3 = 0.f;
     int am = 0;
-    if (ok) tile_unit<T, W, SIGNED>(stage(), xp, dp, xn, dn, sm, s1, s2, s3, am);
+    if (ok) tile_unit<T, W, SIGNED, DELTA>(stage(), xp, dp, xn, dn, sm, s1, s2, s3, am);
     if (!ring_release(rg, ok, tmap, f.status, j, L, x0, y0, f.zrot)) return false;
     mx = fmaxf(mx, sm);
     if (f.smax) warp_max_to(sm, f.smax + j);
@@ -505,7 +551,7 @@ __device__ __forceinline__ void block_max_to(float mx, unsigned* gmax) {
   if ((threadIdx.x & 31) == 0 && mx > -INFINITY) atomicMax(gmax, f32_key(mx));
 }
 
-template <typename T, int W, bool SIGNED>
+template <typename T, int W, bool SIGNED, bool DELTA>
 __global__ void __launch_bounds__(kSmallMaxThreads) k_stack_small(const __grid_constant__ CUtensorMap tmap,
                                                                const StackArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -524,9 +570,12 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_stack_small(const __grid_c
   f.arg = a.arg;
   f.smax = a.smax;
   f.status = a.status;
+  f.key = a.key;
+  f.kpitch = a.kpitch;
   float mx = -INFINITY;
   const uint64_t deadline = globaltimer_ns() + a.timeout_ns;
-  if (!march_small<T, W, SIGNED>(&tmap, f, blockIdx.x, blockIdx.y, a.g.TBY, rg, smem, deadline, mx))
+  if (!march_small<T, W, SIGNED, DELTA>(&tmap, f, blockIdx.x, blockIdx.y, a.g.TBY, rg, smem,
+                                        deadline, mx))
     return;
   block_max_to(mx, a.gmax);
 }
@@ -549,7 +598,7 @@ __device__ __forceinline__ size_t sub_part_offset(const StackGeom& g) {
   return sub_part_offset_host(g.stages, g.stage_bytes);
 }
 
-template <typename T, bool SIGNED>
+template <typename T, bool SIGNED, bool DELTA>
 __device__ __forceinline__ bool march_sub(const CUtensorMap* tmap, const StackArgs& a, Ring& rg,
                                           unsigned char* smem, uint64_t deadline, float& mx) {
   constexpr int N = 16;
@@ -561,9 +610,10 @@ __device__ __forceinline__ bool march_sub(const CUtensorMap* tmap, const StackAr
   const int x0 = blockIdx.x * kSubCols, y0 = blockIdx.y * g.BH;
   float4* part = reinterpret_cast<float4*>(smem + sub_part_offset(g));   // [2][nw][TBX]
   const int off = (warp * 4) * kSubCols + lane * 4;
+  const int j0 = DELTA ? 1 : 0;   // first snapshot that comes through the ring
   if (tid == 0) {
     int s = rg.stg;
-    for (int j = 0; j < rg.NS && j < L; ++j) {
+    for (int j = j0; j < j0 + rg.NS && j < L; ++j) {
       mbar_expect_tx(rg.bar0 + 8 * s, rg.box_bytes);
       tma_load_3d(rg.stage0 + s * rg.stage_bytes, tmap, x0, y0, (a.zrot + j) % L, rg.bar0 + 8 * s);
       if (++s == rg.NS) s = 0;
@@ -584,14 +634,20 @@ __device__ __forceinline__ bool march_sub(const CUtensorMap* tmap, const StackAr
   }
   float* out = a.vp + (rlive ? (size_t)rty * a.Tx + rtx : 0);
   float xa[N], da[N], xb[N], db[N];
+  if (DELTA) {
+    float sm = -INFINITY;
+    key_load<4, 4>(a.key, a.kpitch, x0 + lane * 4, y0 + warp * 4, a.nx, a.ny, xa, sm);
+    mx = fmaxf(mx, sm);
+    if (a.smax) warp_max_to(sm, a.smax);
+  }
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
+  for (int j = j0; j < 2; ++j) {
     if (j >= L) break;
     const bool ok = ring_wait(rg, deadline);
     float sm = -INFINITY;
     if (ok) {
       if (j == 0) tile_load<T, 4>(stage(), xb, xa, da, true, sm);
-      else tile_load<T, 4>(stage(), xa, xb, db, false, sm);
+      else tile_load<T, 4, DELTA>(stage(), xa, xb, db, false, sm);
     }
     if (!ring_release(rg, ok, tmap, a.status, j, L, x0, y0, a.zrot)) return false;
     mx = fmaxf(mx, sm);
@@ -603,7 +659,7 @@ __device__ __forceinline__ bool march_sub(const CUtensorMap* tmap, const StackAr
     float sm = -INFINITY;
     float s1 = 0.f, s2 = 0.f, s3 = 0.f;
     int am = 0;
-    if (ok) tile_unit<T, 4, SIGNED>(stage(), xp, dp, xn, dn, sm, s1, s2, s3, am);
+    if (ok) tile_unit<T, 4, SIGNED, DELTA>(stage(), xp, dp, xn, dn, sm, s1, s2, s3, am);
     for (int o = gl >> 1; o > 0; o >>= 1) {
       s1 += __shfl_xor_sync(0xffffffffu, s1, o);
       s2 = fmaxf(s2, __shfl_xor_sync(0xffffffffu, s2, o));
@@ -637,7 +693,7 @@ __device__ __forceinline__ bool march_sub(const CUtensorMap* tmap, const StackAr
 
 // MAXT = 256 (w <= 32, eight warps) leaves room for three CTAs per SM;
 // MAXT = 512 (w = 64, sixteen warps) for one.
-template <typename T, bool SIGNED, int MAXT>
+template <typename T, bool SIGNED, int MAXT, bool DELTA>
 __global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_stack_sub(const __grid_constant__ CUtensorMap tmap,
                                                                 const StackArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -646,7 +702,7 @@ __global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1) k_stack_sub(const _
   ring_init(rg, smem, a.g, (int)sizeof(T));
   float mx = -INFINITY;
   const uint64_t deadline = globaltimer_ns() + a.timeout_ns;
-  if (!march_sub<T, SIGNED>(&tmap, a, rg, smem, deadline, mx)) return;
+  if (!march_sub<T, SIGNED, DELTA>(&tmap, a, rg, smem, deadline, mx)) return;
   block_max_to(mx, a.gmax);
 }
 
@@ -721,6 +777,86 @@ __global__ void k_finite_max(const T* __restrict__ x, int L, int ny, int nx, int
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0 && m > -INFINITY) atomicMax(gmax, f32_key(m));
+}
+
+// Finite maxima of a difference-coded stack, each pixel decoded in snapshot
+// order (xt^(0) = key, xt^(s) = fl32(xt^(s-1) + q^(s)), as the march does);
+// used only when a fused maximum saw +inf.  With smax, shared memory holds one
+// flag (smax[k] was +inf) and one running key per snapshot.
+template <typename T>
+__global__ void k_delta_finite_max(const float* __restrict__ key, int64_t kpitch,
+                                   const T* __restrict__ q, size_t slice, int L, int ny, int nx,
+                                   int64_t pitch, unsigned* gmax, unsigned* smax) {
+  extern __shared__ unsigned sk[];   // [L] flags, [L] keys (only with smax)
+  const unsigned inf_key = f32_key(INFINITY);
+  if (smax) {
+    int any = 0;
+    for (int k = threadIdx.x; k < L; k += blockDim.x) {
+      sk[k] = smax[k] == inf_key ? 1u : 0u;
+      sk[L + k] = 0u;
+      any |= (int)sk[k];
+    }
+    // nothing to do unless a snapshot's fused maximum was +inf (the usual
+    // case for the per-snapshot maxima of the running reading)
+    if (!__syncthreads_or(any) && !gmax) return;
+  }
+  float m = -INFINITY;
+  const int64_t total = (int64_t)ny * nx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t yy = i / nx, xx = i - yy * nx;
+    float x = key[yy * kpitch + xx];
+    for (int k = 0; k < L; ++k) {
+      if (k > 0) x = __fadd_rn(x, to_f32(q[(size_t)k * slice + yy * pitch + xx]));
+      if (isfinite(x)) {
+        m = fmaxf(m, x);
+        if (smax && sk[k]) atomicMax(&sk[L + k], f32_key(x));
+      }
+    }
+  }
+  if (gmax) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > -INFINITY) atomicMax(gmax, f32_key(m));
+  }
+  if (smax) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < L; k += blockDim.x)
+      if (sk[k] && sk[L + k]) atomicMax(&smax[L + k], sk[L + k]);
+  }
+}
+
+cudaError_t launch_delta_finite_max(const float* key, int64_t kpitch, const void* stack,
+                                    int storage, int L, int ny, int nx, int64_t pitch,
+                                    unsigned* gmax, unsigned* smax, cudaStream_t st) {
+  if (smax && L > kDeltaMaxSnaps) return cudaErrorInvalidValue;
+  const size_t slice = (size_t)pitch * ny;
+  const size_t sm = smax ? sizeof(unsigned) * 2 * (size_t)L : 0;
+  const int64_t total = (int64_t)ny * nx;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(152 * 4, (total + 255) / 256));
+  if (storage == FITRIG_BF16) {
+    auto kern = k_delta_finite_max<bf16_t>;
+    if (sm > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<blocks, 256, sm, st>>>(key, kpitch, static_cast<const bf16_t*>(stack), slice, L, ny, nx,
+                                  pitch, gmax, smax);
+  } else if (storage == FITRIG_F16) {
+    auto kern = k_delta_finite_max<f16_t>;
+    if (sm > 48 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<blocks, 256, sm, st>>>(key, kpitch, static_cast<const f16_t*>(stack), slice, L, ny, nx,
+                                  pitch, gmax, smax);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  count_launches(1);
+  return cudaGetLastError();
 }
 
 // One bounded wait on an mbarrier that nothing completes (fitrig_wait_probe):
@@ -869,9 +1005,9 @@ static cudaError_t launch_one(const CUtensorMap* tmap, const StackArgs& a, cudaS
   return cudaGetLastError();
 }
 
-template <typename T, int W, bool SIGNED>
+template <typename T, int W, bool SIGNED, bool DELTA>
 static cudaError_t launch_small(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
-  auto kern = k_stack_small<T, W, SIGNED>;
+  auto kern = k_stack_small<T, W, SIGNED, DELTA>;
   static size_t configured = 0;
   if (a.g.smem_bytes > configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -885,10 +1021,10 @@ static cudaError_t launch_small(const CUtensorMap* tmap, const StackArgs& a, cud
   return cudaGetLastError();
 }
 
-template <typename T, bool SIGNED>
+template <typename T, bool SIGNED, bool DELTA>
 static cudaError_t launch_sub(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
   const bool big = a.g.threads > 256;
-  auto kern = big ? k_stack_sub<T, SIGNED, 512> : k_stack_sub<T, SIGNED, 256>;
+  auto kern = big ? k_stack_sub<T, SIGNED, 512, DELTA> : k_stack_sub<T, SIGNED, 256, DELTA>;
   static size_t configured[2] = {0, 0};
   if (a.g.smem_bytes > configured[big]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -902,15 +1038,36 @@ static cudaError_t launch_sub(const CUtensorMap* tmap, const StackArgs& a, cudaS
   return cudaGetLastError();
 }
 
+// Difference-coded half stacks (a.key set): the thread-per-tile and sub-tile
+// marches only.
+template <typename T, bool SIGNED>
+static cudaError_t launch_delta(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
+  if constexpr (sizeof(T) == 2) {
+    if (a.zrot != 0) return cudaErrorInvalidValue;
+    if (a.g.R < 0) return launch_sub<T, SIGNED, true>(tmap, a, st);
+    if (a.g.R == 0) {
+      switch (a.g.w) {
+        case 3: return launch_small<T, 3, SIGNED, true>(tmap, a, st);
+        case 4: return launch_small<T, 4, SIGNED, true>(tmap, a, st);
+        case 5: return launch_small<T, 5, SIGNED, true>(tmap, a, st);
+        case 6: return launch_small<T, 6, SIGNED, true>(tmap, a, st);
+        default: break;
+      }
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <typename T, bool SIGNED>
 static cudaError_t launch_r(const CUtensorMap* tmap, const StackArgs& a, cudaStream_t st) {
-  if (a.g.R < 0) return launch_sub<T, SIGNED>(tmap, a, st);
+  if (a.key) return launch_delta<T, SIGNED>(tmap, a, st);
+  if (a.g.R < 0) return launch_sub<T, SIGNED, false>(tmap, a, st);
   if (a.g.R == 0) {
     switch (a.g.w) {
-      case 3: return launch_small<T, 3, SIGNED>(tmap, a, st);
-      case 4: return launch_small<T, 4, SIGNED>(tmap, a, st);
-      case 5: return launch_small<T, 5, SIGNED>(tmap, a, st);
-      case 6: return launch_small<T, 6, SIGNED>(tmap, a, st);
+      case 3: return launch_small<T, 3, SIGNED, false>(tmap, a, st);
+      case 4: return launch_small<T, 4, SIGNED, false>(tmap, a, st);
+      case 5: return launch_small<T, 5, SIGNED, false>(tmap, a, st);
+      case 6: return launch_small<T, 6, SIGNED, false>(tmap, a, st);
       default: return cudaErrorInvalidValue;
     }
   }

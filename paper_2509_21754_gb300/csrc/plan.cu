@@ -71,6 +71,13 @@ struct fitrig_plan_s {
   float* d_hwts = nullptr;   // [hist_n]
   float2* d_htw = nullptr;   // twiddles of length hist_n
   int accumulate = 1;        // raw snapshots summed into one stack snapshot
+  // difference-coded half storage: FP32 key frame (snapshot 0) and the
+  // device coder's running decoded snapshot
+  int coding = FITRIG_CODING_VALUE;
+  float* d_key = nullptr;    // [ny][kpitch]
+  float* d_dstate = nullptr; // [ny][nx]
+  int64_t kpitch = 0;
+  bool dstate_stale = false; // already-encoded differences were pushed
   int hmax = 1;              // harmonics of the frequency branch's h (1: max magnitude)
   int refine = FITRIG_REFINE_PARABOLIC;   // frequency candidates' position refine
   int raw_pushed = 0;        // raw snapshots of the block being summed
@@ -189,7 +196,7 @@ static void free_all(fitrig_plan_t p) {
                   p->d_blk_f, p->d_fpeaks, p->d_sel, p->d_cand, p->d_cand_tmp,
                   p->d_bin,   p->d_tw,  p->d_staging, p->d_report, p->d_accum,
                   p->d_hist,  p->d_hwts, p->d_htw,
-                  p->d_smax,  p->d_mrun, p->d_wts};   // d_eta lives inside d_vp
+                  p->d_smax,  p->d_mrun, p->d_wts, p->d_key, p->d_dstate};   // d_eta lives inside d_vp
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->h_pinned) cudaFreeHost(p->h_pinned);
@@ -397,6 +404,10 @@ static int make_twiddles(fitrig_plan_t p, int n, float2** out) {
 static int allocate(fitrig_plan_t p) {
   if (p->allocated) return FITRIG_OK;
   const int eb = elem_bytes(p->storage);
+  const bool delta = p->coding == FITRIG_CODING_DELTA;
+  if (delta && (p->storage == FITRIG_F32 || p->stride != FITRIG_STRIDE_TILE || p->accumulate != 1 ||
+                p->ring))
+    return FITRIG_EUNSUPPORTED;
   p->pitch = ((int64_t)p->nx * eb + 127) / 128 * 128 / eb;
   p->slice_bytes = (size_t)p->pitch * p->ny * eb;
   int boxW, boxH;
@@ -416,6 +427,9 @@ static int allocate(fitrig_plan_t p) {
     } else if (!stack_geometry(p->w, eb, &p->geom)) {
       return FITRIG_EUNSUPPORTED;
     }
+    // the difference-coded march exists for the thread-per-tile and sub-tile
+    // paths (windows 3..6, 8, 16, 32, 64)
+    if (delta && p->geom.R > 0) return FITRIG_EUNSUPPORTED;
     p->geom.gridX = (p->Tx + p->geom.TBX - 1) / p->geom.TBX;
     p->geom.gridY = (p->Ty + p->geom.TBY - 1) / p->geom.TBY;
     if (p->geom.gridY > 65535) return FITRIG_EUNSUPPORTED;
@@ -425,6 +439,11 @@ static int allocate(fitrig_plan_t p) {
   const int U = p->units;
   p->vstride = (p->T + 3) / 4 * 4;
   CK(dmalloc(p, &p->d_stack, p->slice_bytes * p->L));
+  if (delta) {
+    p->kpitch = ((int64_t)p->nx + 31) / 32 * 32;
+    CK(dmalloc(p, &p->d_key, sizeof(float) * (size_t)p->kpitch * p->ny));
+    CK(dmalloc(p, &p->d_dstate, sizeof(float) * (size_t)p->nx * p->ny));
+  }
   // with the frequency branch, eta is one more slot after the U units, so that
   // both branches' noise estimates run as one launch over U + 1 groups
   const int vslots = (p->branch & FITRIG_BRANCH_FREQ) ? U + 1 : U;
@@ -622,6 +641,11 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t p, int option, int64_t value) {
       if (value != FITRIG_F32 && value != FITRIG_BF16 && value != FITRIG_F16) return FITRIG_EINVAL;
       p->storage = (int)value;
       return FITRIG_OK;
+    case FITRIG_OPT_CODING:
+      if (value != FITRIG_CODING_VALUE && value != FITRIG_CODING_DELTA) return FITRIG_EINVAL;
+      if (p->ring) return FITRIG_EUNSUPPORTED;
+      p->coding = (int)value;
+      return FITRIG_OK;
     case FITRIG_OPT_ACCUMULATE:
       if (value < 1 || value > 1 << 20) return FITRIG_EINVAL;
       if (p->ring) return FITRIG_EUNSUPPORTED;
@@ -734,6 +758,27 @@ static int push_one(fitrig_plan_t p, const void* data, int dtype, int on_device,
   cudaStream_t st = plan_stream(p);
   const int eb = elem_bytes(p->storage), ib = elem_bytes(dtype);
   char* dst = p->d_stack + p->slice_bytes * p->pushed;
+  if (p->coding == FITRIG_CODING_DELTA && (p->pushed == 0 || dtype != p->storage)) {
+    // the key frame, or a snapshot the device coder encodes against its
+    // running decoded snapshot (which already-encoded pushes do not advance)
+    if (p->pushed > 0 && p->dstate_stale) return FITRIG_ESTATE;
+    const void* src = data;
+    int64_t sp = rp;
+    if (!on_device) {
+      if (!p->d_staging) CK(dmalloc(p, &p->d_staging, (size_t)p->nx * p->ny * 4));
+      CK(copy_rows_h2d(p, p->d_staging, (size_t)p->nx * ib, data, (size_t)rp * ib,
+                       (size_t)p->nx * ib, p->ny, st));
+      src = p->d_staging;
+      sp = p->nx;
+    }
+    CK(launch_delta_encode(src, dtype, sp, p->d_dstate, p->d_key, p->kpitch, dst, p->storage,
+                           p->pitch, p->pushed == 0, p->ny, p->nx, st));
+    if (!on_device && sync) CK(cudaStreamSynchronize(st));
+    p->pushed += 1;
+    p->detected = false;
+    return FITRIG_OK;
+  }
+  if (p->coding == FITRIG_CODING_DELTA) p->dstate_stale = true;   // already-encoded differences
   if (p->accumulate > 1) {
     // Sec. 3.3.2: K raw snapshots summed (FP32, push order) into one
     const void* src = data;
@@ -823,8 +868,10 @@ FITRIG_API int fitrig_push_snapshots(fitrig_plan_t p, const void* data, int32_t 
   if (rc != FITRIG_OK) return rc;
   cudaStream_t st = plan_stream(p);
   const int eb = elem_bytes(p->storage);
+  // (a difference-coded plan takes its first snapshot as the key frame)
   const bool contiguous = !on_device && k == 1 && dtype == p->storage && rp == p->nx &&
-                          p->pitch == p->nx && ss == rp * p->ny;
+                          p->pitch == p->nx && ss == rp * p->ny &&
+                          !(p->coding == FITRIG_CODING_DELTA && p->pushed == 0);
   if (contiguous) {
     // host rows and device slots line up: one transfer of count * ny rows
     char* dst = p->d_stack + p->slice_bytes * p->pushed;
@@ -832,6 +879,7 @@ FITRIG_API int fitrig_push_snapshots(fitrig_plan_t p, const void* data, int32_t 
     CK(copy_rows_h2d(p, dst, row, data, row, row, (int64_t)count * p->ny, st));
     p->pushed += count;
     p->detected = false;
+    if (p->coding == FITRIG_CODING_DELTA) p->dstate_stale = true;
   } else {
     const size_t ib = (size_t)elem_bytes(dtype);
     for (int32_t i = 0; i < count; ++i) {
@@ -848,6 +896,7 @@ FITRIG_API int fitrig_plan_reset(fitrig_plan_t p) {
   if (!p) return FITRIG_EINVAL;
   p->pushed = 0;
   p->raw_pushed = 0;
+  p->dstate_stale = false;
   p->detected = false;
   return FITRIG_OK;
 }
@@ -891,6 +940,10 @@ static cudaError_t enqueue_march(fitrig_plan_t p, cudaStream_t st) {
   a.status = p->d_small + 1;
   a.timeout_ns = p->timeout_ns;
   a.g = p->geom;
+  if (p->coding == FITRIG_CODING_DELTA) {
+    a.key = p->d_key;
+    a.kpitch = p->kpitch;
+  }
   if (p->stride == FITRIG_STRIDE_SLIDING) {
     SlideArgs sa{};
     sa.zrot = p->zrot;
@@ -937,6 +990,10 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
   ca.slice = (int64_t)p->pitch * p->ny;
   ca.zrot = p->zrot;
   ca.zmod = p->ring ? p->L : 0;
+  if (p->coding == FITRIG_CODING_DELTA) {
+    ca.key = p->d_key;
+    ca.kpitch = p->kpitch;
+  }
   ca.eta = p->d_eta;
   ca.bin = p->d_bin;
   ca.refine = p->refine;
@@ -966,9 +1023,15 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
                             p->sel.items, p->sel.capacity, status, p->sel.want, is));
     if (is != st) CKE(cudaEventRecord(p->join_ev, is));
   }
-  if (p->d_smax)
+  if (p->d_smax && p->coding == FITRIG_CODING_DELTA) {
+    CKE(launch_delta_finite_max(p->d_key, p->kpitch, p->d_stack, p->storage, p->pushed, p->nyu,
+                                p->nxu, p->pitch, nullptr, p->d_smax, st));
+    CKE(launch_running_norm(nullptr, p->storage, p->pushed, p->nyu, p->nxu, p->pitch, p->d_smax,
+                            p->d_mrun, p->d_wts, st));
+  } else if (p->d_smax) {
     CKE(launch_running_norm(p->d_stack, p->storage, p->pushed, p->nyu, p->nxu, p->pitch, p->d_smax,
                             p->d_mrun, p->d_wts, st));
+  }
   if (freq) {
     mark(FITRIG_KERNEL_SPECTRUM, 0);
     if (p->hist_n > 0)   // the ring in any rotation: |X_k| ignores circular shifts
@@ -1208,8 +1271,12 @@ static int resolve_max(fitrig_plan_t p, double* M) {
   if (key && std::isinf(f32_from_key(key))) {
     // the fused maximum saw +inf: recompute over finite pixels only
     CK(cudaMemsetAsync(p->d_small, 0, 4, st));
-    CK(launch_finite_max(p->d_stack, p->storage, p->pushed, p->nyu, p->nxu, p->pitch, p->d_small,
-                         st));
+    if (p->coding == FITRIG_CODING_DELTA)
+      CK(launch_delta_finite_max(p->d_key, p->kpitch, p->d_stack, p->storage, p->pushed, p->nyu,
+                                 p->nxu, p->pitch, p->d_small, nullptr, st));
+    else
+      CK(launch_finite_max(p->d_stack, p->storage, p->pushed, p->nyu, p->nxu, p->pitch,
+                           p->d_small, st));
     CK(cudaMemcpyAsync(p->h_pinned + 8, p->d_small, 4, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     key = p->h_pinned[8];
@@ -1310,6 +1377,11 @@ FITRIG_API int fitrig_stack_device_ptr(fitrig_plan_t p, int32_t s, void** ptr,
   CK(cudaSetDevice(p->device));
   int rc = ensure_allocated(p);
   if (rc != FITRIG_OK) return rc;
+  if (s == 0 && p->coding == FITRIG_CODING_DELTA) {   // the FP32 key frame
+    *ptr = p->d_key;
+    *row_pitch_elems = p->kpitch;
+    return FITRIG_OK;
+  }
   *ptr = p->d_stack + p->slice_bytes * s;
   *row_pitch_elems = p->pitch;
   return FITRIG_OK;
@@ -1452,10 +1524,12 @@ FITRIG_API int fitrig_batch_create(const fitrig_plan_t* plans, int32_t nplans,
     b->plans.push_back(plans[i]);
     b->order.push_back(i);
   }
-  // one persistent launch needs the same thread-per-tile march for all
+  // one persistent launch needs the same thread-per-tile march for all (and
+  // plain stored values: difference-coded plans march one by one)
   b->multi = true;
   for (fitrig_plan_t p : b->plans)
     if (p->stride != FITRIG_STRIDE_TILE || p->geom.R != 0 || p->w != p0->w ||
+        p->coding != FITRIG_CODING_VALUE ||
         p->storage != p0->storage || p->rmode != p0->rmode || p->geom.TBY != p0->geom.TBY ||
         p->geom.stages != p0->geom.stages)
       b->multi = false;

@@ -26,6 +26,8 @@ OPT_STORAGE, OPT_NOISE, OPT_RMODE, OPT_MMODE, OPT_EDGE, OPT_STRIDE = 1, 2, 3, 4,
 OPT_STREAM, OPT_TIMEOUT_NS = 8, 9
 OPT_AUTOTUNE, OPT_MAX_SELECTED, OPT_GRAPH, OPT_ACCUMULATE, OPT_HARMONICS, OPT_REFINE = \
     10, 11, 12, 13, 14, 15
+OPT_CODING = 16
+CODING_VALUE, CODING_DELTA = 0, 1
 REFINE_PARABOLIC, REFINE_CUBIC = 0, 1
 NOISE_MEANSTD, NOISE_MEDMAD = 0, 1
 RMODE_ABS, RMODE_SIGNED = 0, 1
@@ -510,9 +512,11 @@ class Plan:
     def __init__(self, nx, ny, nsnap, window, nsigma, branch=BRANCH_IMAGE, storage=F32,
                  noise=NOISE_MEANSTD, rmode=RMODE_ABS, edge=EDGE_PARTIAL, stream=None,
                  stride=STRIDE_TILE, autotune=False, max_selected=0, mmode=MMODE_GLOBAL,
-                 accumulate=1, harmonics=1, refine=REFINE_PARABOLIC):
+                 accumulate=1, harmonics=1, refine=REFINE_PARABOLIC, coding=CODING_VALUE):
         self.h = fitrig_plan_create(nx, ny, nsnap, window, nsigma, branch)
         try:
+            if coding != CODING_VALUE:
+                fitrig_plan_set(self.h, OPT_CODING, coding)
             if accumulate != 1:
                 fitrig_plan_set(self.h, OPT_ACCUMULATE, accumulate)
             if harmonics != 1:
@@ -574,14 +578,14 @@ def detect_stack(stack, window: int, nsigma: float, branch: int = BRANCH_IMAGE,
                  edge: int = EDGE_PARTIAL, dumps: bool = True,
                  stride: int = STRIDE_TILE, autotune: bool = False,
                  mmode: int = MMODE_GLOBAL, accumulate: int = 1, harmonics: int = 1,
-                 refine: int = REFINE_PARABOLIC) -> dict:
+                 refine: int = REFINE_PARABOLIC, coding: int = CODING_VALUE) -> dict:
     """Push an (L*accumulate, ny, nx) stack of raw snapshots, detect (on the
     L sums of `accumulate` raw snapshots), and read back candidates and dumps."""
     Lr, ny, nx = (int(d) for d in stack.shape)
     L = Lr // accumulate
     with Plan(nx, ny, L, window, nsigma, branch, storage, noise, rmode, edge,
               stride=stride, autotune=autotune, mmode=mmode, accumulate=accumulate,
-              harmonics=harmonics, refine=refine) as p:
+              harmonics=harmonics, refine=refine, coding=coding) as p:
         p.push_stack(stack)
         rc, cands = p.detect()
         out = {"status": rc, "candidates": cands}

@@ -1,6 +1,7 @@
 """Large field: 8 snapshots of 50000 x 50000 pixels, window 5, 6 sigma, both
-branches, median/MAD noise, with FP32 storage (80 GB) and with BF16 / FP16
-storage (40 GB) plus FP32 accumulation.
+branches, median/MAD noise, with FP32 storage (80 GB), with BF16 / FP16
+storage (40 GB) plus FP32 accumulation, and with difference-coded BF16 / FP16
+storage (an FP32 key frame plus half differences, 50 GB).
 
 * parity of the tile statistic on sampled tiles against the oracle on the
   values as stored (half storage rounds on ingest), within twice the FP32
@@ -43,8 +44,11 @@ W, TAU, SEED = 5, 6.0, 3030
 SPEC = synth.C3
 TY = -(-SPEC.ny // W)
 STRIPS = ((0, 32), (TY // 2 - 16, TY // 2 + 16), (TY - 32, TY))   # tile rows [a, b)
-STORES = {"f32": (F.F32, torch.float32), "bf16": (F.BF16, torch.bfloat16),
-          "f16": (F.F16, torch.float16)}
+STORES = {"f32": (F.F32, torch.float32, F.CODING_VALUE),
+          "bf16": (F.BF16, torch.bfloat16, F.CODING_VALUE),
+          "f16": (F.F16, torch.float16, F.CODING_VALUE),
+          "bf16_delta": (F.BF16, torch.bfloat16, F.CODING_DELTA),
+          "f16_delta": (F.F16, torch.float16, F.CODING_DELTA)}
 
 
 def sample_tiles():
@@ -57,19 +61,25 @@ def sample_tiles():
     return sorted(tiles)
 
 
-def stored(x: np.ndarray, tdt) -> np.ndarray:
-    """The values the plan holds for FP32 input x (round to nearest even)."""
+def stored(x: np.ndarray, name: str) -> np.ndarray:
+    """The values the plan's march sees for FP32 input x: as given (FP32),
+    rounded to nearest even (half storage), or the decoded stack of the
+    oracle's difference coder (every pixel is coded on its own, so a crop
+    codes like the whole field)."""
+    code, tdt, coding = STORES[name]
     if tdt == torch.float32:
         return x
+    if coding == F.CODING_DELTA:
+        return O.delta_decode(*O.delta_encode(x, "bf16" if code == F.BF16 else "f16"))
     return torch.from_numpy(x).to(tdt).float().numpy()
 
 
 def run(storage_name, tiles):
-    code, tdt = STORES[storage_name]
+    code, tdt, coding = STORES[storage_name]
     L, ny, nx = SPEC.nsnap, SPEC.ny, SPEC.nx
     crops = [[] for _ in tiles]
     strips = [[] for _ in STRIPS]
-    with F.Plan(nx, ny, L, W, TAU, F.BRANCH_BOTH, code, F.NOISE_MEDMAD) as p:
+    with F.Plan(nx, ny, L, W, TAU, F.BRANCH_BOTH, code, F.NOISE_MEDMAD, coding=coding) as p:
         for k, snap in synth.iter_stack(SPEC, SEED, "cuda"):
             for j, (ty, tx) in enumerate(tiles):
                 crops[j].append(snap[ty * W:ty * W + W, tx * W:tx * W + W].cpu().numpy())
@@ -113,14 +123,14 @@ def run(storage_name, tiles):
                 strip_cands=strip_cands)
 
 
-def oracle_on(crops, tiles, quant=None, bounds=False):
+def oracle_on(crops, tiles, name=None, bounds=False):
     """Oracle tile statistics of the sampled tiles (each crop is one tile),
     and with `bounds` the FP32 rounding bound of each."""
     U = SPEC.nsnap - 2
     out = np.zeros((U, len(tiles)))
     bnd = np.zeros((U, len(tiles)))
     for j, c in enumerate(crops):
-        x = c if quant is None else stored(c, quant)
+        x = c if name is None else stored(c, name)
         out[:, j] = O.sampled_tiles(x, W, [(0, 0)])["numerator"][:, 0]
         if bounds:
             bnd[:, j] = [C.tile_value_bound(x, s, W)[0, 0] for s in range(U)]
@@ -141,9 +151,9 @@ def large():
 
 def test_parity_on_stored_values(large):
     tiles, runs = large
-    for name, (code, tdt) in STORES.items():
+    for name in STORES:
         r = runs[name]
-        ref, bound = oracle_on(r["crops"], tiles, None if name == "f32" else tdt, bounds=True)
+        ref, bound = oracle_on(r["crops"], tiles, name, bounds=True)
         ok, worst = C.values_within_bound(r["vals"], ref, bound)
         assert ok, (name, worst)
         assert r["rc"] in (F.OK, F.ENONFINITE)
@@ -155,11 +165,10 @@ def test_candidates_on_strips(large, name):
     from the stored pixels of the strip, with the field's noise parameters)."""
     _, runs = large
     r = runs[name]
-    tdt = STORES[name][1]
     U = SPEC.nsnap - 2
     checked = 0
     for j, (a, b) in enumerate(STRIPS):
-        xs = stored(r["strips"][j], tdt)
+        xs = stored(r["strips"][j], name)
         units = [O.unit_tiles(xs, s, W) for s in range(U)]
         v = np.stack([u.numerator for u in units])          # FP64, M-free
         for s in range(U):
@@ -202,7 +211,9 @@ def test_accuracy_against_fp32_originals(large):
             "median_v_unit0": float(r["noise"][0][0]), "scale_v_unit0": float(r["noise"][0][1]),
             "detect_ms": r["ms"], "stack_ms": r["stack_ms"],
             "gpixel_per_s": px / (r["ms"] * 1e-3) / 1e9,
-            "stack_gb_per_s": (px * (4 if name == "f32" else 2)) / (r["stack_ms"] * 1e-3) / 1e9,
+            "stack_gb_per_s": (px * (4 if name == "f32" else 2)
+                               + (2 * SPEC.ny * SPEC.nx if "delta" in name else 0))
+                              / (r["stack_ms"] * 1e-3) / 1e9,
             "candidates": int(r["ncand"]),
         }
     out = os.environ.get("FITRIG_REPORT")
@@ -212,3 +223,8 @@ def test_accuracy_against_fp32_originals(large):
     s = report["storage"]
     assert s["f32"]["tile_statistic_v"]["max"] < 1e-5
     assert s["f16"]["tile_statistic_v"]["p99"] < s["bf16"]["tile_statistic_v"]["p99"]
+    # difference coding keeps the statistic within a few tenths of a percent
+    # (FP16) or a few percent (BF16) where rounding the values does not
+    for h in ("bf16", "f16"):
+        assert s[h + "_delta"]["tile_statistic_v"]["p99"] < 0.1 * s[h]["tile_statistic_v"]["p99"]
+        assert s[h + "_delta"]["eta"]["p99"] < 0.1 * s[h]["eta"]["p99"]

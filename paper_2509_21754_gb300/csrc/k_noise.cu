@@ -1211,12 +1211,11 @@ static SplitPtrs split_ptrs(void* base, int groups) {
 
 // Bin width (as a shift) of kSplitBins bins over the inclusive key range
 // [lo, hi] (0 for an empty range, which holds no key).
+static_assert(kSplitBins == 2048, "split_shift assumes 11-bit bins");
 __device__ __forceinline__ unsigned split_shift(uint32_t lo, uint32_t hi) {
   if (hi < lo) return 0;
-  const uint32_t span = hi - lo;   // width - 1
-  unsigned s = 0;
-  while (s < 32 && (span >> s) >= (uint32_t)kSplitBins) ++s;
-  return s;
+  const uint32_t top = (hi - lo) >> 11;   // span >> s < 2048  <=>  s >= bit length of (span >> 11)
+  return top ? 32u - (unsigned)__clz(top) : 0u;
 }
 
 // Block-wide (kSplitThreads): the bin of h[0..kSplitBins) holding `rank`
@@ -1243,8 +1242,11 @@ __device__ bool split_find(const unsigned* h, unsigned long long rank, unsigned*
   if (lane == 31) wsum[warp] = incl;
   if (tid == 0) found[0] = ~0ull;
   __syncthreads();
-  unsigned long long before = incl - mine;
-  for (int w = 0; w < warp; ++w) before += wsum[w];
+  // the warps before this one, summed across the lanes
+  unsigned long long ws = lane < warp ? wsum[lane] : 0ull;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) ws += __shfl_xor_sync(0xffffffffu, ws, o);
+  const unsigned long long before = incl - mine + ws;
   if (rank >= before && rank < before + mine) {
     unsigned long long cum = before;
 #pragma unroll
@@ -1274,28 +1276,37 @@ __device__ unsigned split_sample(const float* v, int64_t stride, bool mad, float
                                  unsigned* nfin_sh) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int nwarps = kSplitThreads / 32;
-  const int64_t runs = (stride + 31) / 32;
-  const int64_t use = runs < kSplitRuns ? runs : kSplitRuns;
+  constexpr int per_warp = kSplitRuns / nwarps;   // runs a warp reads (16)
+  static_assert(per_warp <= 32, "one run start per lane");
+  // the split form takes maps of at most 2 Mi values, so 32-bit arithmetic
+  // holds c * runs; lane l of warp w computes the start of run w + 32 l once
+  // (no division per run)
+  const uint32_t runs = (uint32_t)((stride + 31) / 32);
+  const uint32_t use = runs < (uint32_t)kSplitRuns ? runs : (uint32_t)kSplitRuns;
+  const uint32_t cl = (uint32_t)warp + (uint32_t)nwarps * (uint32_t)lane;
+  const uint32_t start = cl < use ? cl * runs / use * 32u : 0u;
   if (tid == 0) {
     kminmax[0] = 0xffffffffu;
     kminmax[1] = 0u;
     *nfin_sh = 0;
-    *slots = (unsigned)(use * 32);
+    *slots = use * 32u;
   }
-  for (int64_t c = warp; c < use; c += nwarps) {   // every run into L2 first
-    const int64_t i = (c * runs / use) * 32 + lane;
-    if (i < stride) asm volatile("prefetch.global.L2 [%0];" ::"l"((const void*)(v + i)));
+  for (int k = 0; k < per_warp; ++k) {   // every run into L2 first
+    const uint32_t c = (uint32_t)warp + (uint32_t)nwarps * (uint32_t)k;
+    const int64_t i = (int64_t)__shfl_sync(0xffffffffu, start, k) + lane;
+    if (c < use && i < stride) asm volatile("prefetch.global.L2 [%0];" ::"l"((const void*)(v + i)));
   }
   __syncthreads();
   uint32_t lmin = 0xffffffffu, lmax = 0u;
   unsigned nf = 0;
   constexpr int B = 8;
-  for (int64_t c0 = warp; c0 < use; c0 += B * nwarps) {
+  for (int k0 = 0; k0 < per_warp; k0 += B) {
+    const int64_t c0 = warp + (int64_t)nwarps * k0;
     float x[B];
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int64_t c = c0 + (int64_t)b * nwarps;
-      const int64_t i = (c * runs / use) * 32 + lane;
+      const int64_t i = (int64_t)__shfl_sync(0xffffffffu, start, k0 + b) + lane;
       x[b] = (c < use && i < stride) ? v[i] : NAN;
     }
 #pragma unroll
@@ -1329,12 +1340,14 @@ __device__ unsigned split_sample(const float* v, int64_t stride, bool mad, float
 
 // Sample ranks 1/2 -+ delta of ns sample values (delta = 4.5 standard errors of
 // a sample median, a run of 32 values counting as half as informative).
+// The ranks only decide how much the passes copy, so FP32 is enough (FP64 is
+// slow on this part, and every thread evaluates this).
 __device__ __forceinline__ void split_targets(unsigned ns, unsigned long long* t) {
-  const double d = 4.5 * 0.5 / sqrt(0.5 * (double)ns) + 1.0 / (double)ns;
-  const double m = (double)(ns - 1);
-  const double a = floor((0.5 - d) * m), b = ceil((0.5 + d) * m);
-  t[0] = a < 0.0 ? 0ull : (unsigned long long)a;
-  t[1] = b > m ? (unsigned long long)m : (unsigned long long)b;
+  const float d = 4.5f * 0.5f * rsqrtf(0.5f * (float)ns) + 1.0f / (float)ns;
+  const float m = (float)(ns - 1);
+  const float a = floorf((0.5f - d) * m), b = ceilf((0.5f + d) * m);
+  t[0] = a < 0.f ? 0ull : (unsigned long long)a;
+  t[1] = b > m ? (unsigned long long)(ns - 1) : (unsigned long long)b;
 }
 
 // Sample quantiles at ranks t[0] <= t[1] among the finite sample keys (range

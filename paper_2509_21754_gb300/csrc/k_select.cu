@@ -526,7 +526,7 @@ __device__ __forceinline__ uint64_t run_bits(uint64_t m, int s) {
 
 constexpr int kBlkMaxRuns = kBlkT / 2;   // runs of a block (alternating bits at most)
 
-__global__ void __launch_bounds__(kBlkThreads) k_blk_cc(const float* __restrict__ vals,
+__global__ void __launch_bounds__(kBlkThreads, 4) k_blk_cc(const float* __restrict__ vals,
                                                         int64_t stride, int Tx, int Ty,
                                                         const float* __restrict__ thr,
                                                         BlockScratch b, unsigned* status) {

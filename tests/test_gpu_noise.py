@@ -2,10 +2,13 @@
 definition (lower median of the finite values; lower median of |v - median|
 in FP32; scale = 1.482602218505602 MAD) evaluated by sorting in NumPy.
 
-The maps cover both ways the library selects the order statistics: the
-bracketed two-pass form (maps of up to 2 Mi values, including ones whose
-bracket cannot hold the copies and fall back to the multi-pass cluster form)
-and the multi-pass form alone (larger maps)."""
+The maps cover every way the library selects the order statistics: the
+bracketed cluster form of fitrig_noise_static (maps of up to 2 Mi values,
+including ones whose bracket cannot hold the copies and fall back to the
+multi-pass cluster form), the multi-pass form alone (larger maps), and the
+split form that plans and fitrig_threshold_map use (a sample bracket, a
+counting and copying pass and an exact selection for the median, then the
+same for the MAD; its misses fall back to the cluster form too)."""
 import numpy as np
 import pytest
 
@@ -38,15 +41,26 @@ def run(v: torch.Tensor, groups: int, n: int):
     return out.cpu().numpy().reshape(groups, 2)
 
 
-def check(v: torch.Tensor, groups: int, n: int):
-    got = run(v, groups, n)
-    host = v.cpu().numpy().reshape(groups, n)
+def run_split(v: torch.Tensor, groups: int, n: int):
+    """The allocating single-map entry point (the split form up to 2 Mi
+    values), one map at a time."""
+    stream = torch.cuda.current_stream().cuda_stream
+    out = np.zeros((groups, 2))
     for g in range(groups):
-        med, sc = definition(host[g])
-        if np.isnan(med):
-            assert np.isnan(got[g, 0]) and got[g, 1] == 0.0
-        else:
-            assert got[g, 0] == med and got[g, 1] == sc, (g, got[g], med, sc)
+        _, c, s = F.fitrig_threshold_map(v[g * n:(g + 1) * n], 3.0, F.NOISE_MEDMAD, stream)
+        out[g] = (c, s)
+    return out
+
+
+def check(v: torch.Tensor, groups: int, n: int):
+    host = v.cpu().numpy().reshape(groups, n)
+    for got in (run(v, groups, n), run_split(v, groups, n)):
+        for g in range(groups):
+            med, sc = definition(host[g])
+            if np.isnan(med):
+                assert np.isnan(got[g, 0]) and got[g, 1] == 0.0
+            else:
+                assert got[g, 0] == med and got[g, 1] == sc, (g, got[g], med, sc)
 
 
 def gen(seed):
@@ -95,3 +109,23 @@ def test_constant_and_empty_groups():
     v[n:2 * n] = float("nan")                 # no finite value: (nan, 0)
     v[2 * n:] = torch.linspace(-1.0, 1.0, n, device="cuda")
     check(v, 3, n)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_split_form_on_shifted_and_asymmetric_maps(seed):
+    """Maps whose median and MAD sit where a sample bracket is easily wrong
+    (a cluster of values just above the median, a long one-sided tail, a gap
+    at the median, quantised values with many ties): every count stays
+    exact, whichever form finishes the map."""
+    n = 672_401
+    g = gen(100 + seed)
+    v = torch.randn(n, device="cuda", generator=g)
+    if seed == 0:
+        v[: n // 40] = 0.0312                      # a spike just above the median
+    elif seed == 1:
+        v = torch.exp(3.0 * v)                     # heavy right tail
+    elif seed == 2:
+        v = torch.where(v.abs() < 0.05, v + 0.1 * torch.sign(v), v)   # a gap at the median
+    else:
+        v = torch.round(v * 64.0) / 64.0          # quantised values: many ties
+    check(v.contiguous(), 1, n)

@@ -1216,6 +1216,14 @@ struct fitrig_batch_s {
   int device = 0;
   float last_ms = 0.f;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // the plans' post-march work (noise, selection, candidates) runs on these
+  // streams, plan k on post_st[k % npost]: most of its kernels are bound by
+  // latency, so several fields' chains overlap on the device
+  static constexpr int kMaxPost = 8;
+  int npost = 0;
+  cudaStream_t post_st[kMaxPost] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kMaxPost] = {};
 };
 
 static cudaError_t enqueue_batch(fitrig_batch_t b, cudaStream_t st) {
@@ -1227,7 +1235,18 @@ static cudaError_t enqueue_batch(fitrig_batch_t b, cudaStream_t st) {
   } else {
     for (fitrig_plan_t p : b->plans) CKE(enqueue_march(p, st));
   }
-  for (fitrig_plan_t p : b->plans) CKE(enqueue_post(p, st, false));
+  if (b->npost <= 1) {
+    for (fitrig_plan_t p : b->plans) CKE(enqueue_post(p, st, false));
+    return cudaSuccess;
+  }
+  CKE(cudaEventRecord(b->fork_ev, st));
+  for (int k = 0; k < b->npost; ++k) CKE(cudaStreamWaitEvent(b->post_st[k], b->fork_ev, 0));
+  for (size_t i = 0; i < b->plans.size(); ++i)
+    CKE(enqueue_post(b->plans[i], b->post_st[i % b->npost], false));
+  for (int k = 0; k < b->npost; ++k) {
+    CKE(cudaEventRecord(b->join_ev[k], b->post_st[k]));
+    CKE(cudaStreamWaitEvent(st, b->join_ev[k], 0));
+  }
   return cudaSuccess;
 }
 
@@ -1576,6 +1595,18 @@ FITRIG_API int fitrig_batch_create(const fitrig_plan_t* plans, int32_t nplans,
     fitrig_batch_destroy(b);
     return FITRIG_ECUDA;
   }
+  b->npost = (int)std::min<size_t>(b->plans.size(), fitrig_batch_s::kMaxPost);
+  if (b->npost > 1) {
+    bool ok = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < b->npost; ++k)
+      ok = cudaStreamCreateWithFlags(&b->post_st[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      (void)cudaGetLastError();
+      fitrig_batch_destroy(b);
+      return FITRIG_ECUDA;
+    }
+  }
   *out = b;
   return FITRIG_OK;
 }
@@ -1658,6 +1689,12 @@ FITRIG_API int fitrig_batch_destroy(fitrig_batch_t b) {
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  for (int k = 0; k < fitrig_batch_s::kMaxPost; ++k) {
+    if (b->post_st[k]) cudaStreamSynchronize(b->post_st[k]);
+    if (b->post_st[k]) cudaStreamDestroy(b->post_st[k]);
+    if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+  }
   delete b;
   return FITRIG_OK;
 }

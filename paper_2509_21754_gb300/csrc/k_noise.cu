@@ -160,11 +160,23 @@ __device__ __forceinline__ bool rs_key(float v, int mad, float med, uint32_t* ke
 __device__ __forceinline__ void rs_count(unsigned* sh, int pass, unsigned prefix, bool ok,
                                          uint32_t key) {
   if (pass == 0) {
-    // the leading digit is concentrated (exponent bits): aggregate per warp
+    // the leading digit is concentrated (exponent bits): up to two leader
+    // rounds add the lanes that share a leader's bin with one atomic each
+    // (ballots, not match instructions, whose unit is slow), the rest add
+    // their own
+    const unsigned lane = threadIdx.x & 31;
     const unsigned bin = ok ? (key >> 21) : 0xffffffffu;
-    const unsigned peers = __match_any_sync(0xffffffffu, bin);
-    if (ok && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
-      atomicAdd(&sh[bin], (unsigned)__popc(peers));
+    unsigned left = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int round = 0; round < 2; ++round) {
+      if (!left) break;
+      const int lead = __ffs(left) - 1;
+      const unsigned lb = __shfl_sync(0xffffffffu, bin, lead);
+      const unsigned same = __ballot_sync(0xffffffffu, ok && bin == lb) & left;
+      if ((int)lane == lead) atomicAdd(&sh[lb], (unsigned)__popc(same));
+      left &= ~same;
+    }
+    if ((left >> lane) & 1u) atomicAdd(&sh[bin], 1u);
   } else if (pass == 1) {
     if (ok && (key >> 21) == prefix) atomicAdd(&sh[(key >> 10) & 2047u], 1u);
   } else {
@@ -187,7 +199,7 @@ __global__ void __launch_bounds__(kNoiseThreads) k_rs_hist(const float* __restri
   const float* v = vals + (size_t)g * stride;
   if (!degenerate) {
     // Trip counts depend only on the block, so every lane of a warp reaches the
-    // warp-wide match in rs_count together.
+    // warp-wide ballots in rs_count together.
     const int64_t nv = VEC ? stride / 4 : stride;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nv;
          base += (int64_t)nblk * blockDim.x) {
@@ -1364,15 +1376,9 @@ __device__ void split_quantiles(const uint32_t* pool, unsigned slots, uint32_t k
     const unsigned sh = split_shift(lo, hi);
     for (int b = threadIdx.x; b < kSplitBins; b += kSplitThreads) hist[b] = 0;
     __syncthreads();
-    // slots is a multiple of 32, so every lane of a warp takes the same
-    // trips; lanes with the same bin add once (the first round's bins are
-    // concentrated)
     for (unsigned i = threadIdx.x; i < slots; i += kSplitThreads) {
       const uint32_t k = pool[i];
-      const unsigned bin = (k >= lo && k <= hi) ? ((k - lo) >> sh) : 0xffffffffu;
-      const unsigned peers = __match_any_sync(0xffffffffu, bin);
-      if (bin != 0xffffffffu && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
-        atomicAdd(&hist[bin], (unsigned)__popc(peers));
+      if (k >= lo && k <= hi) atomicAdd(&hist[(k - lo) >> sh], 1u);
     }
     __syncthreads();
     unsigned b0, b1;

@@ -1498,7 +1498,7 @@ __global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* _
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const uint32_t key = key_of(x[u]);
-    fin += key != kNoKey;
+    if (!MAD) fin += key != kNoKey;   // the MAD pass keeps the median pass's count
     below += key < lo;
     cmask |= (uint32_t)(any && key - lo <= span) << u;   // never a non-finite value (hi < kNoKey)
   }
@@ -1514,7 +1514,7 @@ __global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* _
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     below += __shfl_xor_sync(0xffffffffu, below, o);
-    fin += __shfl_xor_sync(0xffffffffu, fin, o);
+    if (!MAD) fin += __shfl_xor_sync(0xffffffffu, fin, o);
   }
   __syncthreads();   // nbuf is initialised
   unsigned wbase = 0;
@@ -1525,13 +1525,13 @@ __global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* _
   }
   wbase = __shfl_sync(0xffffffffu, wbase, 0);
   unsigned pos = wbase + incl - nc;
+  // a copied value is read again (an L1 hit: its line was just loaded)
+  // rather than picked out of the register array by 32 compares
   for (uint32_t m = cmask; m; m &= m - 1) {
     const int u = __ffs(m) - 1;
-    float e = 0.f;
-#pragma unroll
-    for (int k = 0; k < U; ++k)
-      if (k == u) e = x[k];   // register array: select without local memory
-    buf[pos++] = key_of(e);
+    const int64_t i = VEC ? c0 + ((int64_t)(u >> 2) * kSplitPassThreads + tid) * 4 + (u & 3)
+                          : c0 + (int64_t)u * kSplitPassThreads + tid;
+    buf[pos++] = key_of(v[i]);
   }
   __syncthreads();
   if (tid == 0) {

@@ -1316,7 +1316,18 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
           c = cand_of(q);
           dy = c.y - gty * a.w;
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, dy);
+        // lanes with the same in-tile row: a ballot per row for small
+        // windows (the match instruction's unit is slow), a match otherwise;
+        // lanes past the group (dy = kMaxW) use none of it
+        unsigned peers = 0;
+        if (a.w <= 8) {
+          for (int d = 0; d < a.w; ++d) {
+            const unsigned b = __ballot_sync(0xffffffffu, dy == d);
+            if (dy == d) peers = b;
+          }
+        } else {
+          peers = __match_any_sync(0xffffffffu, dy);
+        }
         const int rank = __popc(peers & ((1u << lane) - 1u));
         const int off = valid ? cnt[dy] : 0;
         __syncwarp();

@@ -285,9 +285,13 @@ __global__ void __launch_bounds__(kShfWarps * 32, 4) k_slide_shf(const __grid_co
               S3 += rq[(oy + k) % W];
             }
             if (outcol && y < a.ny) {
+              // 1 / n_p^2: a constant inside the image, one division at its
+              // border (the tile march's form of the product)
               const int nyw = min(y + H, a.ny - 1) - max(y - H, 0) + 1;
-              const float n = (float)(nyw * nxw);
-              float v = (S1 / n) * S2 * (S3 / n);
+              constexpr float kInvFull = 1.f / (float)(W * W * W * W);
+              const float np = (float)(nyw * nxw);
+              const float inv = (nyw == W && nxw == W) ? kInvFull : 1.f / (np * np);
+              float v = S1 * S2 * S3 * inv;
               if (!isfinite(S1) || !isfinite(v)) v = NAN;
               a.vp[(size_t)(j - 2) * (size_t)a.vstride + (size_t)y * a.nx + ox] = v;
             }

@@ -119,6 +119,7 @@ def test_new_entry_points_check_their_arguments_without_a_device(lib):
     assert e.value.status == F.EINVAL
     assert L.fitrig_plan_set(None, F.OPT_HARMONICS, 8) == F.EINVAL
     assert L.fitrig_plan_set(None, F.OPT_REFINE, F.REFINE_CUBIC) == F.EINVAL
+    assert L.fitrig_plan_set(None, F.OPT_CODING, F.CODING_DELTA) == F.EINVAL
 
 
 def test_spectrum_map_checks_its_arguments_without_a_device(lib):

@@ -54,13 +54,13 @@ def run_split(v: torch.Tensor, groups: int, n: int):
 
 def check(v: torch.Tensor, groups: int, n: int):
     host = v.cpu().numpy().reshape(groups, n)
-    for got in (run(v, groups, n), run_split(v, groups, n)):
+    for form, got in (("static", run(v, groups, n)), ("split", run_split(v, groups, n))):
         for g in range(groups):
             med, sc = definition(host[g])
             if np.isnan(med):
-                assert np.isnan(got[g, 0]) and got[g, 1] == 0.0
+                assert np.isnan(got[g, 0]) and got[g, 1] == 0.0, (form, g)
             else:
-                assert got[g, 0] == med and got[g, 1] == sc, (g, got[g], med, sc)
+                assert got[g, 0] == med and got[g, 1] == sc, (form, g, got[g], med, sc)
 
 
 def gen(seed):

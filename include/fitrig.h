@@ -227,7 +227,9 @@ FITRIG_API int fitrig_plan_set(fitrig_plan_t plan, int option, int64_t value);
  * into the plan's device stack.  `data` holds ny rows of `row_pitch_elems`
  * elements (0 means nx) of type `dtype`; it is a device pointer when
  * `on_device` is non-zero, else host memory.  A dtype different from the
- * storage type is converted on the device (round to nearest even).  The
+ * storage type is converted on the device (round to nearest even); with
+ * FITRIG_CODING_DELTA it is coded on the device instead (see
+ * FITRIG_OPT_CODING).  The
  * buffer is borrowed: a host buffer may be reused when the call returns; a
  * device buffer once the plan's stream has passed this point.  ESTATE when
  * nsnap snapshots were already pushed.  Host snapshots of 32 MB or more are

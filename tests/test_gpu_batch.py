@@ -93,3 +93,48 @@ def test_batch_field_against_oracle():
     finally:
         for p in plans:
             p.close()
+
+
+def test_batch_of_c4_sized_fields_against_oracle():
+    """The batched workload's recipe at a size the oracle finishes in seconds:
+    six SKA-AA2-like fields of 1024..4096 pixels square and 16..40 snapshots,
+    BF16 storage, both branches, median/MAD, window 5, 6 sigma, in one
+    persistent march and graph; every field's candidate list equals the
+    oracle's on the stored values by the parity rule."""
+    rng = np.random.default_rng(44)
+    shapes = [(16, 4096), (40, 1024), (24, 1536), (16, 2048), (33, 1280), (20, 1100)]
+    stacks, plans = [], []
+    try:
+        for k, (L, side) in enumerate(shapes):
+            spec = synth.small_spec(L, side, side + int(rng.integers(-16, 17)),
+                                    layout="ska_aa2_like", n_ant=68)
+            st, _ = synth.make_stack(spec, seed=4400 + k, device="cuda")
+            st = st.to(torch.bfloat16)
+            p = F.Plan(st.shape[2], st.shape[1], L, 5, 6.0, F.BRANCH_BOTH, F.BF16, F.NOISE_MEDMAD)
+            p.push_stack(st)
+            stacks.append(st)
+            plans.append(p)
+        b = F.fitrig_batch_create(plans)
+        try:
+            F.fitrig_batch_detect(b, len(plans))
+            rc, n = F.fitrig_batch_detect(b, len(plans))   # the captured graph
+            assert rc in (F.OK, F.ENONFINITE)
+        finally:
+            F.fitrig_batch_destroy(b)
+        for k, p in enumerate(plans):
+            x = stacks[k].float().cpu().numpy()
+            L = x.shape[0]
+            det = O.detect(x, 5, 6.0, O.BRANCH_BOTH, "medmad")
+            res = {"values": np.stack([F.fitrig_unit_values(p.h, s) for s in range(L - 2)]),
+                   "noise": np.array([F.fitrig_noise_params(p.h, s) for s in range(L - 2)])}
+            res["eta"], res["bin"] = F.fitrig_spectrum(p.h)
+            res["eta_noise"] = F.fitrig_noise_params(p.h, -1)
+            di, dfq = C.library_decisions(res, 6.0)
+            cands = F.fitrig_candidates(p.h, int(n[k]))
+            errs = C.compare(cands, x, 5, 6.0, O.BRANCH_BOTH, "medmad", decide_image=di,
+                             decide_freq=dfq, det=det)
+            assert not errs, (k, errs[:8])
+            assert len(cands) > 0
+    finally:
+        for p in plans:
+            p.close()

@@ -188,3 +188,31 @@ def test_unsupported_combinations_are_refused(kw, status):
         with pytest.raises(F.FitrigError) as e:
             F.fitrig_plan_set(p.h, F.OPT_CODING, 7)
         assert e.value.status == F.EINVAL
+
+
+def test_batch_with_a_difference_coded_plan_equals_single_plans():
+    """A batch that holds a difference-coded plan beside plain ones marches
+    plan by plan (no persistent launch) and gives every plan its own detect
+    result, bit for bit."""
+    specs = [(8, 300, 280, F.CODING_DELTA), (7, 256, 256, F.CODING_VALUE),
+             (9, 200, 230, F.CODING_DELTA)]
+    plans, single = [], []
+    try:
+        for k, (L, ny, nx, coding) in enumerate(specs):
+            st = make(L, ny, nx, seed=70 + k)
+            p = F.Plan(nx, ny, L, 5, 3.5, F.BRANCH_BOTH, F.BF16, F.NOISE_MEDMAD, coding=coding)
+            p.push_stack(st)
+            plans.append(p)
+            single.append(p.detect()[1].tobytes())
+        b = F.fitrig_batch_create([p.h for p in plans])
+        try:
+            for _ in range(2):
+                rc, n = F.fitrig_batch_detect(b, len(plans))
+                assert rc in (F.OK, F.ENONFINITE)
+                for k, p in enumerate(plans):
+                    assert F.fitrig_candidates(p.h, int(n[k])).tobytes() == single[k]
+        finally:
+            F.fitrig_batch_destroy(b)
+    finally:
+        for p in plans:
+            p.close()

@@ -130,9 +130,36 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Programmatic dependent launch.  A kernel launched by launch_pdl may be set
+// up while the kernel ahead of it in the stream is finishing, so that a chain
+// of short kernels does not pay a full launch gap at every step.  Every
+// kernel that may be launched that way begins with pdl_begin(), which waits
+// (in hardware, not a spin) until the grids this one depends on have
+// completed and their writes are visible; launched normally, it is a no-op.
+// No kernel signals its dependents early: CTAs parked in that wait would hold
+// SM resources that the other stream's kernels of a detect use.
+__device__ __forceinline__ void pdl_begin() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------- host-side launchers
 // Adds n to the process-wide count of kernel launches (fitrig_launch_count).
 void count_launches(int n);
+// Launches kernel k with programmatic stream serialisation allowed (the kernel
+// must start with pdl_begin()).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
 
 // Stack-march geometry chosen on the host (see k_stack.cu).
 struct StackGeom {
@@ -314,6 +341,7 @@ struct BlockScratch {
   unsigned long long* bkey;   // [cap] block-local peak key (value key << 32 | ~t)
   unsigned long long* rkey;   // [cap] merged peak key (roots)
   uint32_t* pbits;            // [groups][Ty][words] peak bitmap
+  uint32_t* sbits;            // [groups][Ty][words] selected-tile bitmap (v > thr)
   unsigned long long* pairs;  // [blocks][pairs per block] selected neighbours across block edges
   int64_t pcap;
   int4* bstat;                // [blocks] boundary components, pairs, selected tiles of each block

@@ -395,6 +395,7 @@ __global__ void __launch_bounds__(kClusterThreads, 4) k_medmad_cluster(const flo
                                                                     int g0, double* cs,
                                                                     unsigned long long* invalid,
                                                                     int skip_done) {
+  pdl_begin();
   __shared__ unsigned hist[2][kClusterBins];
   __shared__ unsigned coarse[2][kCoarse];
   __shared__ uint32_t keep[kCollectPerCta];
@@ -1101,13 +1102,15 @@ static cudaError_t launch_fast_t(const float* vals, int groups, int64_t stride, 
     cfg.blockDim = dim3(kFastThreads, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = kClusterCtas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // starts with pdl_begin()
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, k_medmad_fast<VEC>, vals, stride, n, g0, cs, invalid);
     count_launches(1);
     if (e != cudaSuccess) return e;
@@ -1126,13 +1129,15 @@ static cudaError_t launch_medmad_cluster(const float* vals, int groups, int64_t 
     cfg.blockDim = dim3(kClusterThreads, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = kClusterCtas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // starts with pdl_begin()
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     const cudaError_t e =
         vec ? cudaLaunchKernelEx(&cfg, k_medmad_cluster<true>, vals, stride, n, g0, cs, invalid,
                                  skip_done)
@@ -1152,72 +1157,82 @@ static cudaError_t launch_medmad_cluster(const float* vals, int groups, int64_t 
 //      to kSplitRuns runs of 32 values; two histogram rounds over the sample
 //      keys give quantiles A <= B at ranks 1/2 -+ delta, which bracket the
 //      median;
-//   2. k_split_pass (many CTAs per map): counts the finite values and the
-//      keys below A, and copies the keys in [A, B] (gathered in shared memory,
-//      one global reservation per CTA) into the map's copy buffer, counting
-//      them in a 2048-bin histogram over [A, B];
-//   3. k_split_select (one CTA per map): the histogram gives the bin holding
-//      the median's rank; the copies inside that bin are gathered into shared
-//      memory and the median is selected among them exactly; the same sample
-//      as keys of |v - median| (FP32) then brackets the MAD as (m_lo, m_hi);
+//   2. k_split_pass (one CTA per chunk of kSplitChunk values): counts the
+//      finite values and the keys below A, and writes the keys in [A, B] into
+//      the chunk's own slot of the copy buffer, counting them in a 2048-bin
+//      histogram over [A, B].  A chunk's counts go to its own entry of a count
+//      array, so a CTA waits on no global atomic: its loads are issued first
+//      (beside the read of the map's state) and one barrier places its warps'
+//      copies;
+//   3. k_split_select (one CTA per map): sums the chunks' counts; the
+//      histogram gives the bin holding the median's rank; the copies inside
+//      that bin are gathered into shared memory and the median is selected
+//      among them exactly; the same sample as keys of |v - median| (FP32)
+//      then brackets the MAD as (m_lo, m_hi);
 //   4. k_split_pass again on the keys of |v - median| (those <= m_lo counted,
 //      those strictly inside the bracket copied) and 5. k_split_select for the
 //      MAD.
 // Every count is exact, so the results are the elements a sort gives; the
 // sample only decides how much is copied.  A map whose bracket misses its
-// rank, whose copies overflow, or whose rank bin holds too many copies is
-// marked (scale -1) and the cluster kernel, launched last, finishes it.
+// rank, a chunk of which has more copies than its slot holds, or whose rank
+// bin holds too many copies is marked (scale -1) and the cluster kernel,
+// launched last, finishes it.
 constexpr int kSplitRuns = 512;
 constexpr int kSplitPool = kSplitRuns * 32;     // sample keys (64 KB of shared memory)
 constexpr int kSplitChunk = 8192;               // values per CTA of a pass
+constexpr int kSplitSlot = 2048;                // copies a chunk keeps (a quarter of its values)
+constexpr int kSplitMaxChunks = (int)(kFastMaxPerGroup / kSplitChunk);
 constexpr int kSplitPassThreads = 256;
 constexpr int kSplitThreads = 1024;             // bracket and select kernels
 constexpr int kSplitBins = 2048;
 constexpr int kSplitGather = 8192;              // copies of the rank's bin kept in shared memory
+static_assert(kSplitMaxChunks <= kSplitThreads, "one chunk count per select thread");
 
 struct SplitState {
   uint32_t lo, hi;     // copy range of the current pass (inclusive keys)
-  uint32_t nfin;       // finite values (pass 1)
-  uint32_t nbelow;     // keys below lo (current pass)
-  uint32_t ncopy;      // keys copied (current pass; may exceed the capacity)
+  uint32_t nfin;       // finite values (set by the median's select)
   uint32_t stage;      // 0: median pass, 1: MAD pass, 2: finished, 3: left to the cluster form
   float med;
   uint32_t nsample;    // finite sample values
+  uint32_t pad[2];
 };
 static_assert(sizeof(SplitState) == 32, "SplitState layout");
 
-static int64_t split_cap(int64_t stride) {
-  int64_t c = (stride / 8 + 1023) / 1024 * 1024;
-  c = std::max<int64_t>(c, 8192);
-  return std::min<int64_t>(c, (stride + 1023) / 1024 * 1024);
+static int split_chunks(int64_t stride) { return (int)((stride + kSplitChunk - 1) / kSplitChunk); }
+
+static size_t split_head(int groups) {
+  return ((size_t)groups * (sizeof(SplitState) + kSplitBins * sizeof(unsigned)) + 255) / 256 * 256;
 }
 
 size_t noise_split_bytes(int groups, int64_t stride) {
   if (stride > kFastMaxPerGroup || groups > 65535) return 0;
-  const size_t head = ((size_t)groups * (sizeof(SplitState) + kSplitBins * sizeof(unsigned)) + 255) /
-                      256 * 256;
-  return head + (size_t)groups * (size_t)split_cap(stride) * sizeof(uint32_t);
+  const size_t nc = (size_t)groups * (size_t)split_chunks(stride);
+  return split_head(groups) + nc * sizeof(uint4) + nc * kSplitSlot * sizeof(uint32_t);
 }
 
 void noise_split_carve(void* base, int groups, int64_t stride, NoiseScratch* s) {
   s->split = noise_split_bytes(groups, stride) ? base : nullptr;
-  s->split_cap = s->split ? split_cap(stride) : 0;
+  s->split_cap = s->split ? (int64_t)split_chunks(stride) * kSplitSlot : 0;
 }
 
 struct SplitPtrs {
   SplitState* st;
   unsigned* hist;      // [groups][kSplitBins]
-  uint32_t* copies;    // [groups][cap]
+  uint4* cnt;          // [groups][nchunk]: keys below lo, finite values, copies (unclipped)
+  uint32_t* copies;    // [groups][nchunk][kSplitSlot]
+  int nchunk;
 };
 
-static SplitPtrs split_ptrs(void* base, int groups) {
+static SplitPtrs split_ptrs(void* base, int groups, int64_t stride) {
   char* p = static_cast<char*>(base);
   SplitPtrs r;
+  r.nchunk = split_chunks(stride);
   r.st = reinterpret_cast<SplitState*>(p);
   r.hist = reinterpret_cast<unsigned*>(p + (size_t)groups * sizeof(SplitState));
-  const size_t head = ((size_t)groups * (sizeof(SplitState) + kSplitBins * sizeof(unsigned)) + 255) /
-                      256 * 256;
-  r.copies = reinterpret_cast<uint32_t*>(p + head);
+  p += split_head(groups);
+  r.cnt = reinterpret_cast<uint4*>(p);
+  p += (size_t)groups * r.nchunk * sizeof(uint4);
+  r.copies = reinterpret_cast<uint32_t*>(p);
   return r;
 }
 
@@ -1403,6 +1418,7 @@ __device__ void split_quantiles(const uint32_t* pool, unsigned slots, uint32_t k
 __global__ void __launch_bounds__(kSplitThreads) k_split_bracket(const float* __restrict__ vals,
                                                                  int64_t stride, SplitState* st,
                                                                  unsigned* hist_g) {
+  pdl_begin();
   extern __shared__ uint32_t spool[];   // kSplitPool
   __shared__ unsigned hist[kSplitBins];
   __shared__ unsigned long long wsum[kSplitThreads / 32], found[2];
@@ -1424,60 +1440,75 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_bracket(const float* __
     s.lo = A;
     s.hi = B;
     s.nfin = 0;
-    s.nbelow = 0;
-    s.ncopy = 0;
     s.stage = 0;
     s.med = 0.f;
     s.nsample = ns;
+    s.pad[0] = s.pad[1] = 0u;
     st[g] = s;
   }
 }
 
-// 2./4. One chunk of one map: counts and copies (see above).  Each thread
-// handles 32 values (eight float4 loads issued together), counts in
-// registers, and notes which of its values are copies in a bit mask; the
-// copies (a few percent) are appended once per thread after a warp scan.
+// 2./4. One chunk of one map: counts and copies (see above).  The chunk goes
+// into shared memory by asynchronous copies (each thread its own 32 values,
+// as eight 16-byte copies when VEC), so that a CTA holds its whole chunk in
+// flight without registers and several CTAs per SM stream at once; the map's
+// state is read while they land.  Each thread counts in registers and notes
+// which of its values are copies in a bit mask; after a warp scan and one
+// barrier it writes its copies into the chunk's slot.  Nothing is written
+// for a map whose stage is not this pass's.
 template <bool VEC, bool MAD>
-__global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* __restrict__ vals,
-                                                                  int64_t stride, SplitState* st,
-                                                                  unsigned* hist_g,
-                                                                  uint32_t* copies, int64_t cap) {
-  __shared__ uint32_t buf[kSplitChunk];
-  __shared__ unsigned nbuf, base_sh;
-  __shared__ unsigned red[2][kSplitPassThreads / 32];
-  const int g = blockIdx.y;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const SplitState s = st[g];
-  if (s.stage != (MAD ? 1u : 0u)) return;   // finished, degenerate or handed on
-  const int64_t c0 = (int64_t)blockIdx.x * kSplitChunk;
-  if (c0 >= stride) return;
-  const int64_t c1 = c0 + kSplitChunk < stride ? c0 + kSplitChunk : stride;
-  const uint32_t lo = s.lo, hi = s.hi;
-  const unsigned sh = split_shift(lo, hi);
-  const float med = s.med;
-  const float* v = vals + (size_t)g * stride;
-  if (tid == 0) nbuf = 0;
+__global__ void __launch_bounds__(kSplitPassThreads, 6) k_split_pass(const float* __restrict__ vals,
+                                                                     int64_t stride,
+                                                                     const SplitState* __restrict__ st,
+                                                                     unsigned* hist_g, uint4* cnt,
+                                                                     uint32_t* copies, int nchunk) {
+  pdl_begin();
+  constexpr int NW = kSplitPassThreads / 32;
   constexpr int U = kSplitChunk / kSplitPassThreads;   // values per thread (32)
-  float x[U];
+  __shared__ __align__(16) float buf[kSplitChunk];
+  __shared__ unsigned wsh[3][NW];   // per warp: copies, keys below lo, finite values
+  const int g = blockIdx.y, c = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t c0 = (int64_t)c * kSplitChunk;
+  const int64_t c1 = c0 + kSplitChunk < stride ? c0 + kSplitChunk : stride;
+  const float* v = vals + (size_t)g * stride + c0;
+  const int nv = (int)(c1 - c0);
+  // value j of this thread sits at chunk offset off(j); the copy of an
+  // offset past the map's end is a NaN written here instead
+  auto off = [&](int j) -> int {
+    return VEC ? ((j >> 2) * kSplitPassThreads + tid) * 4 + (j & 3) : j * kSplitPassThreads + tid;
+  };
   if (VEC) {
-    // chunk starts are multiples of kSplitChunk values and stride % 4 == 0
-    const float4* v4 = reinterpret_cast<const float4*>(v);
+    // chunk starts are multiples of kSplitChunk values and stride % 4 == 0,
+    // so every 16-byte copy is aligned and lies wholly inside or outside
 #pragma unroll
     for (int u = 0; u < U / 4; ++u) {
-      const int64_t i = c0 / 4 + (int64_t)u * kSplitPassThreads + tid;
-      const float4 q = i < c1 / 4 ? v4[i] : make_float4(NAN, NAN, NAN, NAN);
-      x[4 * u] = q.x;
-      x[4 * u + 1] = q.y;
-      x[4 * u + 2] = q.z;
-      x[4 * u + 3] = q.w;
+      const int o = off(4 * u);
+      if (o < nv) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(buf + o)),
+                     "l"(v + o)
+                     : "memory");
+      } else {
+        *reinterpret_cast<float4*>(buf + o) = make_float4(NAN, NAN, NAN, NAN);
+      }
     }
   } else {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t i = c0 + (int64_t)u * kSplitPassThreads + tid;
-      x[u] = i < c1 ? v[i] : NAN;
+      const int o = off(u);
+      if (o < nv) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(buf + o)), "l"(v + o)
+                     : "memory");
+      } else {
+        buf[o] = NAN;
+      }
     }
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  const SplitState s = st[g];   // read while the copies land
+  const uint32_t lo = s.lo, hi = s.hi;
+  const unsigned sh = split_shift(lo, hi);
+  const float med = s.med;
   // order-preserving key from the bits (the same map as f32_key), kNoKey for
   // a value that is not finite; |v - med| is never negative, so its key is
   // its bits with the sign bit set
@@ -1495,14 +1526,26 @@ __global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* _
   const uint32_t span = any ? hi - lo : 0u;
   unsigned below = 0, fin = 0;
   uint32_t cmask = 0;
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const uint32_t key = key_of(x[u]);
+  asm volatile("cp.async.wait_all;" ::: "memory");   // this thread's own copies
+  auto classify = [&](float e, int j) {
+    const uint32_t key = key_of(e);
     if (!MAD) fin += key != kNoKey;   // the MAD pass keeps the median pass's count
     below += key < lo;
-    cmask |= (uint32_t)(any && key - lo <= span) << u;   // never a non-finite value (hi < kNoKey)
+    cmask |= (uint32_t)(any && key - lo <= span) << j;   // never a non-finite value (hi < kNoKey)
+  };
+  if (VEC) {
+#pragma unroll
+    for (int u = 0; u < U / 4; ++u) {
+      const float4 q = *reinterpret_cast<const float4*>(buf + off(4 * u));
+      classify(q.x, 4 * u);
+      classify(q.y, 4 * u + 1);
+      classify(q.z, 4 * u + 2);
+      classify(q.w, 4 * u + 3);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < U; ++u) classify(buf[off(u)], u);
   }
-  // this thread's copies, appended after a warp scan of the counts
   const int nc = __popc(cmask);
   int incl = nc;
 #pragma unroll
@@ -1510,50 +1553,42 @@ __global__ void __launch_bounds__(kSplitPassThreads) k_split_pass(const float* _
     const int y = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += y;
   }
-  const int wtot = __shfl_sync(0xffffffffu, incl, 31);
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
     below += __shfl_xor_sync(0xffffffffu, below, o);
     if (!MAD) fin += __shfl_xor_sync(0xffffffffu, fin, o);
   }
-  __syncthreads();   // nbuf is initialised
-  unsigned wbase = 0;
+  if (lane == 31) wsh[0][warp] = (unsigned)incl;
   if (lane == 0) {
-    red[0][warp] = below;
-    red[1][warp] = fin;
-    if (wtot) wbase = atomicAdd(&nbuf, (unsigned)wtot);
-  }
-  wbase = __shfl_sync(0xffffffffu, wbase, 0);
-  unsigned pos = wbase + incl - nc;
-  // a copied value is read again (an L1 hit: its line was just loaded)
-  // rather than picked out of the register array by 32 compares
-  for (uint32_t m = cmask; m; m &= m - 1) {
-    const int u = __ffs(m) - 1;
-    const int64_t i = VEC ? c0 + ((int64_t)(u >> 2) * kSplitPassThreads + tid) * 4 + (u & 3)
-                          : c0 + (int64_t)u * kSplitPassThreads + tid;
-    buf[pos++] = key_of(v[i]);
+    wsh[1][warp] = below;
+    wsh[2][warp] = fin;
   }
   __syncthreads();
+  if (s.stage != (MAD ? 1u : 0u)) return;   // finished, degenerate or handed on
+  unsigned wbase = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const unsigned t = wsh[0][w];
+    wbase += w < warp ? t : 0u;
+    tot += t;
+  }
   if (tid == 0) {
     unsigned tb = 0, tf = 0;
-    for (int w = 0; w < kSplitPassThreads / 32; ++w) {
-      tb += red[0][w];
-      tf += red[1][w];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      tb += wsh[1][w];
+      tf += wsh[2][w];
     }
-    if (tb) atomicAdd(&st[g].nbelow, tb);
-    if (!MAD && tf) atomicAdd(&st[g].nfin, tf);
-    base_sh = nbuf ? atomicAdd(&st[g].ncopy, nbuf) : 0u;
+    cnt[(size_t)g * nchunk + c] = make_uint4(tb, tf, tot, 0u);
   }
-  __syncthreads();
-  const unsigned nb = nbuf, base = base_sh;
-  if ((int64_t)base + nb <= cap) {
-    uint32_t* out = copies + (size_t)g * cap + base;
-    unsigned* hg = hist_g + (size_t)g * kSplitBins;
-    for (unsigned j = tid; j < nb; j += kSplitPassThreads) {
-      const uint32_t k = buf[j];
-      out[j] = k;
-      atomicAdd(&hg[(k - lo) >> sh], 1u);
-    }
+  if (tot > (unsigned)kSplitSlot) return;   // the select hands this map on
+  uint32_t* out = copies + ((size_t)g * nchunk + c) * kSplitSlot;
+  unsigned* hg = hist_g + (size_t)g * kSplitBins;
+  unsigned pos = wbase + (unsigned)(incl - nc);
+  for (uint32_t m = cmask; m; m &= m - 1) {
+    const uint32_t key = key_of(buf[off(__ffs(m) - 1)]);
+    out[pos++] = key;
+    atomicAdd(&hg[(key - lo) >> sh], 1u);
   }
 }
 
@@ -1562,16 +1597,21 @@ template <bool MAD>
 __global__ void __launch_bounds__(kSplitThreads) k_split_select(const float* __restrict__ vals,
                                                                 int64_t stride, int64_t n,
                                                                 SplitState* st, unsigned* hist_g,
+                                                                const uint4* __restrict__ cnt,
                                                                 const uint32_t* __restrict__ copies,
-                                                                int64_t cap, double* cs,
+                                                                int nchunk, double* cs,
                                                                 unsigned long long* invalid) {
+  pdl_begin();
   extern __shared__ uint32_t spool[];   // kSplitPool (the sample, median stage), the gathered bin
   __shared__ unsigned hist[kSplitBins];
   __shared__ unsigned long long wsum[kSplitThreads / 32], found[2];
   __shared__ uint32_t kmm[2];
   __shared__ unsigned slots, nfin_sh, ngather;
+  __shared__ unsigned ccount[kSplitMaxChunks];   // copies of each chunk (unclipped)
+  __shared__ unsigned long long tsum[3];         // keys below lo, finite values, copies
+  __shared__ unsigned tover;                     // a chunk overflowed its slot
   const int g = blockIdx.x;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const SplitState s = st[g];
   if (s.stage != (MAD ? 1u : 0u)) return;
   unsigned* hg = hist_g + (size_t)g * kSplitBins;
@@ -1581,7 +1621,38 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_select(const float* __r
       st[g].stage = 3;
     }
   };
-  if (!MAD && s.nfin == 0) {
+  // the chunks' counts (and the pass histogram, read beside them)
+  if (tid == 0) {
+    tsum[0] = tsum[1] = tsum[2] = 0ull;
+    tover = 0u;
+    ngather = 0u;
+  }
+  for (int b = tid; b < kSplitBins; b += kSplitThreads) hist[b] = hg[b];
+  uint4 q = make_uint4(0u, 0u, 0u, 0u);
+  if (tid < nchunk) {
+    q = cnt[(size_t)g * nchunk + tid];
+    ccount[tid] = q.z;
+  }
+  unsigned long long cb = q.x, cf = q.y, cc = q.z;
+  unsigned over = q.z > (unsigned)kSplitSlot;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    cb += __shfl_xor_sync(0xffffffffu, cb, o);
+    cf += __shfl_xor_sync(0xffffffffu, cf, o);
+    cc += __shfl_xor_sync(0xffffffffu, cc, o);
+    over |= __shfl_xor_sync(0xffffffffu, over, o);
+  }
+  __syncthreads();   // tsum and tover are initialised
+  if (lane == 0 && warp * 32 < nchunk) {
+    atomicAdd(&tsum[0], cb);
+    atomicAdd(&tsum[1], cf);
+    atomicAdd(&tsum[2], cc);
+    if (over) atomicOr(&tover, 1u);
+  }
+  __syncthreads();
+  const unsigned long long nbelow = tsum[0], ncopy = tsum[2];
+  const unsigned nfin = MAD ? s.nfin : (unsigned)tsum[1];
+  if (!MAD && nfin == 0) {
     if (tid == 0) {
       cs[2 * g] = NAN;
       cs[2 * g + 1] = 0.0;
@@ -1590,17 +1661,14 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_select(const float* __r
     }
     return;
   }
-  const unsigned long long R = (s.nfin - 1) / 2;
-  if (s.nsample == 0 || (int64_t)s.ncopy > cap || R < s.nbelow ||
-      R >= (unsigned long long)s.nbelow + s.ncopy) {
+  const unsigned long long R = (nfin - 1) / 2;
+  if (s.nsample == 0 || tover || R < nbelow || R >= nbelow + ncopy) {
     hand_on();
     return;
   }
   // the bin of the pass histogram holding the rank, then its copies
-  unsigned long long rank = R - s.nbelow;
+  unsigned long long rank = R - nbelow;
   const unsigned sh = split_shift(s.lo, s.hi);
-  for (int b = tid; b < kSplitBins; b += kSplitThreads) hist[b] = hg[b];
-  __syncthreads();
   unsigned bin;
   unsigned long long below;
   if (!split_find(hist, rank, &bin, &below, wsum, found)) {
@@ -1611,23 +1679,25 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_select(const float* __r
   uint32_t lo = s.lo + (bin << sh);
   const unsigned long long top = (unsigned long long)lo + (1ull << sh) - 1;
   uint32_t hi = top < s.hi ? (uint32_t)top : s.hi;
-  if (tid == 0) ngather = 0;
-  __syncthreads();
-  const uint32_t* cp = copies + (size_t)g * cap;
-  constexpr int GB = 8;   // loads in flight per thread
-  for (unsigned i0 = tid; i0 < s.ncopy; i0 += GB * kSplitThreads) {
-    uint32_t k[GB];
+  // one warp per chunk slot, eight loads in flight per lane
+  constexpr int GB = 8;
+  for (int c = warp; c < nchunk; c += kSplitThreads / 32) {
+    const unsigned nc = ccount[c];
+    const uint32_t* cp = copies + ((size_t)g * nchunk + c) * kSplitSlot;
+    for (unsigned j0 = lane; j0 < nc; j0 += GB * 32) {
+      uint32_t k[GB];
 #pragma unroll
-    for (int b = 0; b < GB; ++b) {
-      const unsigned i = i0 + b * kSplitThreads;
-      k[b] = i < s.ncopy ? cp[i] : 1u;
-    }
+      for (int b = 0; b < GB; ++b) {
+        const unsigned j = j0 + b * 32;
+        k[b] = j < nc ? cp[j] : 1u;
+      }
 #pragma unroll
-    for (int b = 0; b < GB; ++b) {
-      const unsigned i = i0 + b * kSplitThreads;
-      if (i < s.ncopy && k[b] >= lo && k[b] <= hi) {
-        const unsigned j = atomicAdd(&ngather, 1u);
-        if (j < kSplitGather) spool[j] = k[b];
+      for (int b = 0; b < GB; ++b) {
+        const unsigned j = j0 + b * 32;
+        if (j < nc && k[b] >= lo && k[b] <= hi) {
+          const unsigned i = atomicAdd(&ngather, 1u);
+          if (i < kSplitGather) spool[i] = k[b];
+        }
       }
     }
   }
@@ -1686,8 +1756,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_select(const float* __r
     SplitState n2 = s;
     n2.lo = mlo + 1;       // keys <= m_lo are counted below
     n2.hi = mhi - 1;       // keys strictly inside the bracket are copied
-    n2.nbelow = 0;
-    n2.ncopy = 0;
+    n2.nfin = nfin;
     n2.stage = 1;
     n2.med = val;
     st[g] = n2;
@@ -1697,7 +1766,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_select(const float* __r
 template <bool VEC>
 static cudaError_t launch_split_t(const float* vals, int groups, int64_t stride, int64_t n,
                                   const NoiseScratch& ns, double* cs, cudaStream_t st) {
-  const SplitPtrs sp = split_ptrs(ns.split, groups);
+  const SplitPtrs sp = split_ptrs(ns.split, groups, stride);
+  if ((int64_t)sp.nchunk * kSplitSlot != ns.split_cap) return cudaErrorInvalidValue;   // carved for another stride
   const size_t dyn = (size_t)kSplitPool * sizeof(uint32_t);
   static bool configured = false;
   if (!configured) {
@@ -1712,18 +1782,22 @@ static cudaError_t launch_split_t(const float* vals, int groups, int64_t stride,
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const dim3 pgrid((unsigned)((stride + kSplitChunk - 1) / kSplitChunk), (unsigned)groups);
-  k_split_bracket<<<groups, kSplitThreads, dyn, st>>>(vals, stride, sp.st, sp.hist);
-  k_split_pass<VEC, false><<<pgrid, kSplitPassThreads, 0, st>>>(vals, stride, sp.st, sp.hist,
-                                                                 sp.copies, ns.split_cap);
-  k_split_select<false><<<groups, kSplitThreads, dyn, st>>>(vals, stride, n, sp.st, sp.hist,
-                                                            sp.copies, ns.split_cap, cs,
-                                                            ns.invalid);
-  k_split_pass<VEC, true><<<pgrid, kSplitPassThreads, 0, st>>>(vals, stride, sp.st, sp.hist,
-                                                                sp.copies, ns.split_cap);
-  k_split_select<true><<<groups, kSplitThreads, dyn, st>>>(vals, stride, n, sp.st, sp.hist,
-                                                           sp.copies, ns.split_cap, cs,
-                                                           ns.invalid);
+  const dim3 pgrid((unsigned)sp.nchunk, (unsigned)groups);
+  cudaError_t e = launch_pdl(k_split_bracket, dim3(groups), dim3(kSplitThreads), dyn, st, vals,
+                             stride, sp.st, sp.hist);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_split_pass<VEC, false>, pgrid, dim3(kSplitPassThreads), 0, st, vals, stride,
+                   sp.st, sp.hist, sp.cnt, sp.copies, sp.nchunk);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_split_select<false>, dim3(groups), dim3(kSplitThreads), dyn, st, vals, stride,
+                   n, sp.st, sp.hist, sp.cnt, sp.copies, sp.nchunk, cs, ns.invalid);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_split_pass<VEC, true>, pgrid, dim3(kSplitPassThreads), 0, st, vals, stride,
+                   sp.st, sp.hist, sp.cnt, sp.copies, sp.nchunk);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_split_select<true>, dim3(groups), dim3(kSplitThreads), dyn, st, vals, stride,
+                   n, sp.st, sp.hist, sp.cnt, sp.copies, sp.nchunk, cs, ns.invalid);
+  if (e != cudaSuccess) return e;
   count_launches(5);
   return cudaGetLastError();
 }
@@ -1795,6 +1869,7 @@ cudaError_t launch_noise(const float* vals, int groups, int64_t stride, int64_t 
 
 __global__ void k_thresholds(const double* cs, int groups, double tau, float* thr,
                              double* inv_scale) {
+  pdl_begin();
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= groups) return;
   const double c = cs[2 * g], s = cs[2 * g + 1];
@@ -1810,7 +1885,9 @@ __global__ void k_thresholds(const double* cs, int groups, double tau, float* th
 
 cudaError_t launch_thresholds(const double* cs, int groups, double tau, float* thr,
                               double* inv_scale, cudaStream_t st) {
-  k_thresholds<<<(groups + 127) / 128, 128, 0, st>>>(cs, groups, tau, thr, inv_scale);
+  const cudaError_t e = launch_pdl(k_thresholds, dim3((groups + 127) / 128), dim3(128), 0, st, cs,
+                                   groups, tau, thr, inv_scale);
+  if (e != cudaSuccess) return e;
   count_launches(1);
   return cudaGetLastError();
 }

@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_count(const float* __restri
 __global__ void __launch_bounds__(1024) k_scan_blocks(int nblk, const int* blkcnt, int* blkoff,
                                                       int* total, int64_t cap,
                                                       unsigned* status, unsigned* want) {
+  pdl_begin();
   __shared__ long long sh[1024];
   const int per = (nblk + 1023) / 1024;
   const int b0 = threadIdx.x * per;
@@ -252,6 +253,7 @@ cudaError_t launch_count_selected(const float* vals, int groups, int64_t stride,
 }
 
 __global__ void k_clamp_count(int* n, int cap, unsigned* status) {
+  pdl_begin();
   if (*n > cap) {
     *n = cap;
     atomicOr(status, kErrCapacity);
@@ -259,7 +261,8 @@ __global__ void k_clamp_count(int* n, int cap, unsigned* status) {
 }
 
 cudaError_t launch_clamp_count(int* n, int cap, unsigned* status, cudaStream_t st) {
-  k_clamp_count<<<1, 1, 0, st>>>(n, cap, status);
+  const cudaError_t e = launch_pdl(k_clamp_count, dim3(1), dim3(1), 0, st, n, cap, status);
+  if (e != cudaSuccess) return e;
   count_launches(1);
   return cudaGetLastError();
 }
@@ -406,10 +409,12 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
 }
 
 // ---------------------------------------------------------------- block-tiled components
-// A CTA thresholds one kBlkY x kBlkX block of one group's tile map (with a
-// one-tile halo), labels the block's 8-connected components with a
+// A streaming kernel first thresholds every tile map into a bitmap (one bit
+// per tile).  A CTA then takes one kBlkY x kBlkX block of one group's bitmap
+// (with a one-tile halo), labels the block's 8-connected components with a
 // shared-memory union-find, and finds each component's peak (largest value,
-// smallest tile index on ties) as the largest key (value key << 32) | ~t.  A
+// smallest tile index on ties) as the largest key (value key << 32) | ~t,
+// reading the values of the selected tiles only.  A
 // component that reaches a selected tile outside the block is a boundary
 // component: it gets a global id, its edge tiles get that id in a dense label
 // map, and a second kernel unites the ids of selected neighbours across block
@@ -418,12 +423,11 @@ cudaError_t launch_components(int Tx, int Ty, int64_t T, const SelectScratch& s,
 // OR'ed in afterwards, and an ordered compaction of the bitmap gives the peak
 // list in (group, t) order.
 constexpr int kBlkT = kBlkY * kBlkX;
-constexpr int kBlkThreads = 512;
+constexpr int kBlkThreads = 256;
 static_assert(kBlkY % 32 == 0 && kBlkY <= 64 && kBlkX == 64, "block geometry");
 constexpr int kBlkIds = 2 * kBlkX + 2 * (kBlkY - 2);   // boundary components a block can have
 constexpr int kBlkPairs = 4 * kBlkIds;                  // cross-edge pairs a block can record
 constexpr int kBlkRing = 2 * kBlkX + 2 * (kBlkY - 2);   // edge tiles of a block
-constexpr int kBlkHalo = 2 * (kBlkX + 2) + 2 * kBlkY;   // halo tiles of a block
 
 __device__ __forceinline__ int find_s(const int* par, int x) {
   const volatile int* p = par;
@@ -462,22 +466,6 @@ __device__ __forceinline__ int find_g(const int* par, int x) {
 
 __device__ __forceinline__ unsigned long long peak_key(float v, uint32_t t) {
   return ((unsigned long long)f32_key(v) << 32) | (unsigned long long)(0xffffffffu - t);
-}
-
-// Halo position q (0 <= q < kBlkHalo) of a block as (ly, lx), -1 <= ly <= kBlkY,
-// -1 <= lx <= kBlkX: the row above, the row below, then the two side columns.
-__device__ __forceinline__ void halo_pos(int q, int* ly, int* lx) {
-  if (q < kBlkX + 2) {
-    *ly = -1;
-    *lx = q - 1;
-  } else if (q < 2 * (kBlkX + 2)) {
-    *ly = kBlkY;
-    *lx = q - (kBlkX + 2) - 1;
-  } else {
-    const int r = q - 2 * (kBlkX + 2);
-    *ly = r >> 1;
-    *lx = (r & 1) ? kBlkX : -1;
-  }
 }
 
 // The ring position r (0 <= r < kBlkRing) of a block's edge as (ly, lx).
@@ -526,15 +514,50 @@ __device__ __forceinline__ uint64_t run_bits(uint64_t m, int s) {
 
 constexpr int kBlkMaxRuns = kBlkT / 2;   // runs of a block (alternating bits at most)
 
-__global__ void __launch_bounds__(kBlkThreads, 4) k_blk_cc(const float* __restrict__ vals,
+// Selected-tile bitmap: bit (tx & 31) of word tx / 32 of row (g, ty) is
+// v > thr[g] (never for NaN: an invalid tile); bits past the row's end are 0.
+// One warp per row: all of the row's loads (coalesced, up to 32 per lane) are
+// issued before its ballots.
+constexpr int kMaskThreads = 256;
+__global__ void __launch_bounds__(kMaskThreads) k_blk_mask(const float* __restrict__ vals,
+                                                           int64_t stride, int Tx, int Ty,
+                                                           int64_t nrows,
+                                                           const float* __restrict__ thr,
+                                                           BlockScratch b) {
+  pdl_begin();
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * kMaskThreads + threadIdx.x) >> 5;
+  if (r >= nrows) return;
+  const int g = (int)(r / Ty), ty = (int)(r - (int64_t)g * Ty);
+  const float th = thr[g];
+  const float* row = vals + (size_t)g * stride + (int64_t)ty * Tx;
+  uint32_t* out = b.sbits + (size_t)r * b.words;
+  for (int w0 = 0; w0 < b.words; w0 += 32) {
+    float x[32];
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const int tx = (w0 + u) * 32 + lane;
+      x[u] = tx < Tx ? row[tx] : NAN;
+    }
+    uint32_t mine = 0;
+#pragma unroll
+    for (int u = 0; u < 32; ++u) {
+      const uint32_t bal = __ballot_sync(0xffffffffu, x[u] > th);
+      if (lane == u) mine = bal;
+    }
+    if (w0 + lane < b.words) out[w0 + lane] = mine;
+  }
+}
+
+__global__ void __launch_bounds__(kBlkThreads, 6) k_blk_cc(const float* __restrict__ vals,
                                                         int64_t stride, int Tx, int Ty,
-                                                        const float* __restrict__ thr,
                                                         BlockScratch b, unsigned* status) {
+  pdl_begin();
+  __shared__ uint32_t wsh[kBlkY + 2][4];      // bitmap words: rows ty0-1 .. ty0+kBlkY, words w0-1 .. w0+2
   __shared__ unsigned long long mrow[kBlkY];   // the block's rows
   __shared__ unsigned long long htop, hbot;   // halo rows above / below (block columns)
   __shared__ unsigned long long hleft, hright;   // halo columns (bit = block row)
   __shared__ uint32_t hcorner;                // bits: 0 top-left, 1 top-right, 2 bottom-left, 3 bottom-right
-  __shared__ float val[kBlkT];                // the block's values
   __shared__ int runbase[kBlkY + 1];          // first run of each row; runbase[kBlkY] = runs
   __shared__ uint32_t rinfo[kBlkMaxRuns];     // run: row << 16 | start << 8 | end
   __shared__ __align__(16) short par[kBlkMaxRuns];   // union-find over runs (CAS on aligned words)
@@ -547,57 +570,40 @@ __global__ void __launch_bounds__(kBlkThreads, 4) k_blk_cc(const float* __restri
   // this block's slots: boundary ids bidx * kBlkIds + k, pairs bidx * kBlkPairs + k
   const int64_t bidx = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   const int tx0 = blockIdx.x * kBlkX, ty0 = blockIdx.y * kBlkY;
-  const float th = thr[g];
-  const float* v = vals + (size_t)g * stride;
-  // 1. every load first: warp w takes rows w + 8 j (j < 4), both 32-column
-  // halves; threads below kBlkHalo also take one halo tile
-  constexpr int NW = kBlkThreads / 32;
-  constexpr int NL = 2 * kBlkY / NW;   // loads per lane
-  float x[NL];
-#pragma unroll
-  for (int i = 0; i < NL; ++i) {
-    const int row = warp + NW * (i >> 1), col = (i & 1) * 32 + lane;
-    const int gy = ty0 + row, gx = tx0 + col;
-    x[i] = (gx < Tx && gy < Ty) ? v[(int64_t)gy * Tx + gx] : NAN;
-  }
-  float xh = NAN;
-  int hy = 0, hx = 0;
-  if (tid < kBlkHalo) {
-    halo_pos(tid, &hy, &hx);
-    const int gy = ty0 + hy, gxh = tx0 + hx;
-    if (gy >= 0 && gy < Ty && gxh >= 0 && gxh < Tx) xh = v[(int64_t)gy * Tx + gxh];
+  const int w0 = tx0 / 32;
+  // 1. the bitmap words of the block's rows and of the halo rows (the words
+  // on either side hold the halo columns' bits); outside the map: 0
+  const uint32_t* sb = b.sbits + (size_t)g * Ty * b.words;
+  for (int q = tid; q < (kBlkY + 2) * 4; q += kBlkThreads) {
+    const int r = q >> 2, k = q & 3;
+    const int ty = ty0 - 1 + r, w = w0 - 1 + k;
+    uint32_t word = 0u;
+    if (ty >= 0 && ty < Ty && w >= 0 && w < b.words) word = sb[(size_t)ty * b.words + w];
+    wsh[r][k] = word;
   }
   if (tid == 0) {
-    htop = hbot = 0ull;
     hleft = hright = 0ull;
     hcorner = 0u;
     nsel_sh = nbnd_sh = npair_sh = 0;
   }
   if (tid < kBlkY) pw[tid][0] = pw[tid][1] = 0u;
   __syncthreads();
-  // 2. masks (NaN -- an invalid tile or one beyond the map -- is never
-  // selected) and the values
-  int mine = 0;
-#pragma unroll
-  for (int i = 0; i < NL; i += 2) {
-    const int row = warp + NW * (i >> 1);
-    val[row * kBlkX + lane] = x[i];
-    val[row * kBlkX + 32 + lane] = x[i + 1];
-    const uint32_t lo = __ballot_sync(0xffffffffu, x[i] > th);
-    const uint32_t hi = __ballot_sync(0xffffffffu, x[i + 1] > th);
-    if (lane == 0) {
-      mrow[row] = ((unsigned long long)hi << 32) | lo;
-      mine += __popc(lo) + __popc(hi);
-    }
-  }
-  if (tid < kBlkHalo && xh > th) {
-    if (hy == -1 || hy == kBlkY) {
-      if (hx == -1 || hx == kBlkX)
-        atomicOr(&hcorner, 1u << ((hy == kBlkY ? 2 : 0) + (hx == kBlkX ? 1 : 0)));
-      else
-        atomicOr(hy == -1 ? &htop : &hbot, 1ull << hx);
+  // 2. rows as 64-bit masks, the halo rows, columns and corners
+  if (tid < kBlkY + 2) {
+    const int r = tid - 1;   // block row -1 .. kBlkY
+    const unsigned long long m = ((unsigned long long)wsh[tid][2] << 32) | wsh[tid][1];
+    const bool left = (wsh[tid][0] >> 31) != 0u, right = (wsh[tid][3] & 1u) != 0u;
+    if (r < 0) {
+      htop = m;
+      if (left || right) atomicOr(&hcorner, (left ? 1u : 0u) | (right ? 2u : 0u));
+    } else if (r >= kBlkY) {
+      hbot = m;
+      if (left || right) atomicOr(&hcorner, (left ? 4u : 0u) | (right ? 8u : 0u));
     } else {
-      atomicOr(hx == -1 ? &hleft : &hright, 1ull << hy);
+      mrow[r] = m;
+      if (m) atomicAdd(&nsel_sh, __popcll((long long)m));
+      if (left) atomicOr(&hleft, 1ull << r);
+      if (right) atomicOr(&hright, 1ull << r);
     }
   }
   __syncthreads();
@@ -699,9 +705,11 @@ __global__ void __launch_bounds__(kBlkThreads, 4) k_blk_cc(const float* __restri
     if (eb == 63) out = out || (hright & near);
     if (out) atomicOr(&bnd[r >> 5], 1u << (r & 31));
     unsigned long long key = 0ull;
+    const uint32_t t0 = (uint32_t)((ty0 + row) * Tx + tx0);
+    const float* vr = vals + (size_t)g * stride + t0;
+#pragma unroll 4
     for (int c = sb; c <= eb; ++c) {
-      const uint32_t t = (uint32_t)((ty0 + row) * Tx + (tx0 + c));
-      const unsigned long long kc = peak_key(val[row * kBlkX + c], t);
+      const unsigned long long kc = peak_key(vr[c], t0 + (uint32_t)c);
       key = kc > key ? kc : key;
     }
     atomicMax(&pkey[r], key);
@@ -771,7 +779,6 @@ __global__ void __launch_bounds__(kBlkThreads, 4) k_blk_cc(const float* __restri
     const int ty = ty0 + ly, w = tx0 / 32 + wx;
     if (ty < Ty && w < b.words) b.pbits[((size_t)g * Ty + ty) * b.words + w] = pw[ly][wx];
   }
-  if (lane == 0 && mine) atomicAdd(&nsel_sh, mine);
   __syncthreads();
   if (tid == 0) b.bstat[bidx] = make_int4(nbnd_sh, npair_sh, nsel_sh, 0);
 }
@@ -786,6 +793,7 @@ __device__ __forceinline__ bool valid_id(const BlockScratch& b, int64_t nblocks,
 
 __global__ void k_blk_merge(int64_t stride, int Tx, int64_t nblocks, BlockScratch b,
                             unsigned* status) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; blk < nblocks;
@@ -809,6 +817,7 @@ __global__ void k_blk_merge(int64_t stride, int Tx, int64_t nblocks, BlockScratc
 
 // Merged peak keys: every boundary component raises its root's key.
 __global__ void k_blk_resolve(int64_t nblocks, BlockScratch b) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; blk < nblocks;
@@ -824,6 +833,7 @@ __global__ void k_blk_resolve(int64_t nblocks, BlockScratch b) {
 
 // Each merged component's peak bit.
 __global__ void k_blk_mark(int Tx, int Ty, int64_t nblocks, BlockScratch b) {
+  pdl_begin();
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t blk = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; blk < nblocks;
@@ -844,6 +854,7 @@ __global__ void k_blk_mark(int Tx, int Ty, int64_t nblocks, BlockScratch b) {
 constexpr int kPbThreads = 256;
 
 __global__ void __launch_bounds__(kPbThreads) k_pbits_count(int64_t nwords, BlockScratch b) {
+  pdl_begin();
   __shared__ int wsum[kPbThreads / 32];
   const int64_t i = (int64_t)blockIdx.x * kPbThreads + threadIdx.x;
   int cnt = i < nwords ? __popc(b.pbits[i]) : 0;
@@ -861,6 +872,7 @@ __global__ void __launch_bounds__(kPbThreads) k_pbits_write(int64_t nwords, int 
                                                             const float* __restrict__ vals,
                                                             int64_t stride, BlockScratch b,
                                                             SelItem* peaks, int64_t cap) {
+  pdl_begin();
   __shared__ int wcnt[kPbThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * kPbThreads + threadIdx.x;
@@ -902,6 +914,7 @@ __global__ void __launch_bounds__(kPbThreads) k_pbits_write(int64_t nwords, int 
 // The selected count (the blocks' sum) against the selection capacity.
 __global__ void __launch_bounds__(1024) k_blk_check(int64_t nblocks, BlockScratch b, int64_t cap,
                                                     unsigned* status, unsigned* want) {
+  pdl_begin();
   __shared__ long long part[32];
   long long n = 0;
   for (int64_t i = threadIdx.x; i < nblocks; i += 1024) n += b.bstat[i].z;
@@ -936,6 +949,7 @@ size_t block_scratch_bytes(int groups, int Tx, int Ty, int64_t stride) {
   add(sizeof(unsigned long long) * cap);         // bkey
   add(sizeof(unsigned long long) * cap);         // rkey
   add(sizeof(uint32_t) * nw);                    // pbits
+  add(sizeof(uint32_t) * nw);                    // sbits
   add(sizeof(unsigned long long) * block_count(groups, Tx, Ty) * kBlkPairs);   // pairs
   add(sizeof(int4) * block_count(groups, Tx, Ty));   // bstat
   add(sizeof(int) * 4);                          // counters
@@ -960,6 +974,7 @@ void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride,
   b->bkey = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * cap));
   b->rkey = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * cap));
   b->pbits = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
+  b->sbits = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
   b->pairs = reinterpret_cast<unsigned long long*>(
       take(sizeof(unsigned long long) * block_count(groups, Tx, Ty) * kBlkPairs));
   b->bstat = reinterpret_cast<int4*>(take(sizeof(int4) * block_count(groups, Tx, Ty)));
@@ -980,23 +995,35 @@ cudaError_t launch_block_select(const float* vals, int groups, int64_t stride, i
       (int64_t)Tx * Ty > 0xffffffffll || nblocks * kBlkIds > INT_MAX ||
       nblocks * kBlkIds > b.cap)
     return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(b.counters, 0, sizeof(int) * 4, st);
-  if (e != cudaSuccess) return e;
+  // (counters[2], the peak count, is written by the scan below; nothing else
+  // is read, so no clearing launch sits between the noise and this chain)
+  const int64_t nrows = (int64_t)groups * Ty;
+  cudaError_t e = launch_pdl(k_blk_mask, dim3((unsigned)((nrows * 32 + kMaskThreads - 1) / kMaskThreads)),
+                             dim3(kMaskThreads), 0, st, vals, stride, Tx, Ty, nrows, thr, b);
   const dim3 grid((Tx + kBlkX - 1) / kBlkX, (Ty + kBlkY - 1) / kBlkY, groups);
-  k_blk_cc<<<grid, kBlkThreads, 0, st>>>(vals, stride, Tx, Ty, thr, b, status);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_blk_cc, grid, dim3(kBlkThreads), 0, st, vals, stride, Tx, Ty, b, status);
   const unsigned wgrid = (unsigned)std::min<int64_t>((nblocks + 7) / 8, 152 * 16);   // a warp per block
-  k_blk_merge<<<wgrid, 256, 0, st>>>(stride, Tx, nblocks, b, status);
-  k_blk_resolve<<<wgrid, 256, 0, st>>>(nblocks, b);
-  k_blk_mark<<<wgrid, 256, 0, st>>>(Tx, Ty, nblocks, b);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_blk_merge, dim3(wgrid), dim3(256), 0, st, stride, Tx, nblocks, b, status);
+  if (e == cudaSuccess) e = launch_pdl(k_blk_resolve, dim3(wgrid), dim3(256), 0, st, nblocks, b);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_blk_mark, dim3(wgrid), dim3(256), 0, st, Tx, Ty, nblocks, b);
+  if (e != cudaSuccess) return e;
   const int64_t nwords = (int64_t)groups * Ty * b.words;
   const int64_t nb = (nwords + kPbThreads - 1) / kPbThreads;
   if (nb > b.nblk) return cudaErrorInvalidValue;   // sized by block_scratch_carve
-  k_pbits_count<<<(unsigned)nb, kPbThreads, 0, st>>>(nwords, b);
-  k_scan_blocks<<<1, 1024, 0, st>>>((int)nb, b.blkcnt, b.blkoff, &b.counters[2], cap, status,
-                                    nullptr);
-  k_pbits_write<<<(unsigned)nb, kPbThreads, 0, st>>>(nwords, Tx, Ty, vals, stride, b, peaks, cap);
-  k_blk_check<<<1, 1024, 0, st>>>(nblocks, b, cap, status, want);
-  count_launches(8);
+  e = launch_pdl(k_pbits_count, dim3((unsigned)nb), dim3(kPbThreads), 0, st, nwords, b);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_scan_blocks, dim3(1), dim3(1024), 0, st, (int)nb, (const int*)b.blkcnt,
+                   b.blkoff, &b.counters[2], cap, status, (unsigned*)nullptr);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_pbits_write, dim3((unsigned)nb), dim3(kPbThreads), 0, st, nwords, Tx, Ty, vals,
+                   stride, b, peaks, cap);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_blk_check, dim3(1), dim3(1024), 0, st, nblocks, b, cap, status, want);
+  if (e != cudaSuccess) return e;
+  count_launches(9);
   return cudaGetLastError();
 }
 
@@ -1135,6 +1162,7 @@ __device__ __forceinline__ float significance(const CandArgs& a, const SelItem& 
 // so the peaks' list order is already the output order.
 __global__ void k_emit_freq(CandArgs a, const SelItem* __restrict__ items, const int* np_,
                             const int* __restrict__ plist) {
+  pdl_begin();
   const int np = *np_;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
     const SelItem it = peak_item(items, plist, p);
@@ -1189,6 +1217,7 @@ __device__ __forceinline__ fitrig_candidate image_candidate(const CandArgs& a, c
 // stack march) and writes the candidate in peak-list order to `tmp`.
 __global__ void k_emit_image(CandArgs a, const SelItem* __restrict__ items, const int* np_,
                              const int* __restrict__ plist, fitrig_candidate* tmp) {
+  pdl_begin();
   const int np = *np_;
   const int lane = threadIdx.x & 31;
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1242,7 +1271,9 @@ __global__ void k_emit_image(CandArgs a, const SelItem* __restrict__ items, cons
 // positions once sorted by (y, x); inside a group the order is (dy, tx), so a
 // stable counting sort on the in-tile row dy finishes it.  A warp scans 32
 // consecutive peaks, finds the group heads among them by ballot, and sorts
-// each of those groups (which may run past its 32 entries).
+// each of those groups (which may run past its 32 entries).  A group's first
+// 32 peaks are read once and kept in registers between the count and the
+// write (most groups are no longer); later ones are read again.
 constexpr int kGroupWarps = 8;
 constexpr int kMaxW = 128;
 
@@ -1255,17 +1286,48 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
                                                                  const SelItem* __restrict__ items,
                                                                  const int* __restrict__ plist,
                                                                  const int* base_) {
+  pdl_begin();
   __shared__ int counts[kGroupWarps][kMaxW];
-  auto snap_of = [&](int p) { return FROM_ARG ? peak_item(items, plist, p).group : tmp[p].snapshot; };
-  auto row_of = [&](int p) { return FROM_ARG ? peak_item(items, plist, p).t / a.Tx : tmp[p].y / a.w; };
-  auto cand_of = [&](int p) -> fitrig_candidate {
-    if (!FROM_ARG) return tmp[p];
-    const SelItem it = peak_item(items, plist, p);
-    const int ty = it.t / a.Tx, tx = it.t - ty * a.Tx;
-    const int idx = a.arg[(int64_t)it.group * a.stride + it.t];
-    return image_candidate(a, it, tx, ty, a.w, idx % a.w, idx / a.w);
+  // one peak: its group (snapshot, tile row) and, for the count and the
+  // write, its candidate
+  struct Peak {
+    SelItem it;   // FROM_ARG
+    fitrig_candidate c;
+    int snap, row;
   };
-  auto same_group = [&](int p, int q) { return snap_of(p) == snap_of(q) && row_of(p) == row_of(q); };
+  auto head_of = [&](int p, int* snap, int* row) {
+    if (FROM_ARG) {
+      const SelItem it = peak_item(items, plist, p);
+      *snap = it.group;
+      *row = it.t / a.Tx;
+    } else {
+      const fitrig_candidate c = tmp[p];
+      *snap = c.snapshot;
+      *row = c.y / a.w;
+    }
+  };
+  auto load = [&](int p) -> Peak {
+    Peak k;
+    if (FROM_ARG) {
+      k.it = peak_item(items, plist, p);
+      k.snap = k.it.group;
+      k.row = k.it.t / a.Tx;
+    } else {
+      k.c = tmp[p];
+      k.snap = k.c.snapshot;
+      k.row = k.c.y / a.w;
+    }
+    return k;
+  };
+  // the candidate and its in-tile row (FROM_ARG: from the march's arg-max)
+  auto finish = [&](Peak& k) -> int {
+    if (FROM_ARG) {
+      const int ty = k.row, tx = k.it.t - ty * a.Tx;
+      const int idx = a.arg[(int64_t)k.it.group * a.stride + k.it.t];
+      k.c = image_candidate(a, k.it, tx, ty, a.w, idx % a.w, idx / a.w);
+    }
+    return k.c.y - k.row * a.w;
+  };
   const int np = *np_;
   const int base = base_ ? *base_ : 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1274,29 +1336,49 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
   const int nw = gridDim.x * kGroupWarps;
   for (int p0 = wid * 32; p0 < np; p0 += nw * 32) {
     const int pl = p0 + lane;
-    const bool head = pl < np && (pl == 0 || !same_group(pl, pl - 1));
+    int sn = -1, rw = -1, psn = -2, prw = -2;
+    if (pl < np) head_of(pl, &sn, &rw);
+    if (lane == 0 && pl > 0 && pl < np) head_of(pl - 1, &psn, &prw);
+    const int usn = __shfl_up_sync(0xffffffffu, sn, 1), urw = __shfl_up_sync(0xffffffffu, rw, 1);
+    if (lane > 0) {
+      psn = usn;
+      prw = urw;
+    }
+    const bool head = pl < np && (sn != psn || rw != prw);
     unsigned heads = __ballot_sync(0xffffffffu, head);
     while (heads) {
-      const int p = p0 + __ffs(heads) - 1;
+      const int hl = __ffs(heads) - 1;
       heads &= heads - 1;
-      const int gty = row_of(p);
-      const int snap = snap_of(p);
-      // group extent
-      int end = p + 1;
-      for (;;) {
-        const int q = end + lane;
-        const bool same = q < np && snap_of(q) == snap && row_of(q) == gty;
-        const unsigned bal = __ballot_sync(0xffffffffu, same);
-        if (bal == 0xffffffffu) {
-          end += 32;
-          continue;
-        }
-        end += __ffs(~bal) - 1;
-        break;
-      }
+      const int p = p0 + hl;
+      const int snap = __shfl_sync(0xffffffffu, sn, hl), gty = __shfl_sync(0xffffffffu, rw, hl);
       for (int k = lane; k < a.w; k += 32) cnt[k] = 0;
       __syncwarp();
-      for (int q = p + lane; q < end; q += 32) atomicAdd(&cnt[cand_of(q).y - gty * a.w], 1);
+      // the group's extent and its count per in-tile row; the first 32 peaks
+      // stay in registers
+      Peak first;
+      int dy0 = kMaxW;
+      int end = p;
+      for (int q0 = p;; q0 += 32) {
+        const int q = q0 + lane;
+        Peak k;
+        bool in = false;
+        if (q < np) {
+          k = load(q);
+          in = k.snap == snap && k.row == gty;
+        }
+        int dy = kMaxW;
+        if (in) {
+          dy = finish(k);
+          atomicAdd(&cnt[dy], 1);
+        }
+        if (q0 == p) {
+          first = k;
+          dy0 = dy;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, in);   // a prefix of the lanes
+        end = q0 + __popc(bal);
+        if (bal != 0xffffffffu) break;
+      }
       __syncwarp();
       if (lane == 0) {
         int run = 0;
@@ -1310,12 +1392,16 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
       for (int q0 = p; q0 < end; q0 += 32) {
         const int q = q0 + lane;
         const bool valid = q < end;
-        fitrig_candidate c;
-        int dy = kMaxW;
-        if (valid) {
-          c = cand_of(q);
-          dy = c.y - gty * a.w;
+        Peak k = first;
+        int dy = dy0;
+        if (q0 != p) {
+          dy = kMaxW;
+          if (valid) {
+            k = load(q);
+            dy = finish(k);
+          }
         }
+        if (!valid) dy = kMaxW;
         // lanes with the same in-tile row: a ballot per row for small
         // windows (the match instruction's unit is slow), a match otherwise;
         // lanes past the group (dy = kMaxW) use none of it
@@ -1333,7 +1419,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
         __syncwarp();
         if (valid) {
           const int pos = base + p + off + rank;
-          if (pos < a.cap) a.out[pos] = c;
+          if (pos < a.cap) a.out[pos] = k.c;
           if (lane == __ffs(peers) - 1) cnt[dy] = off + __popc(peers);
         }
         __syncwarp();
@@ -1342,7 +1428,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
   }
 }
 
-__global__ void k_add_count(int* total, const int* part) { *total += *part; }
+__global__ void k_add_count(int* total, const int* part) {
+  pdl_begin(); *total += *part; }
 
 // Copies the first min(*n, cap) candidates to mapped host memory, so only the
 // candidates that exist cross the host link.
@@ -1362,20 +1449,26 @@ cudaError_t launch_export_candidates(const fitrig_candidate* src, const int* n,
 
 cudaError_t launch_emit_peaks(const CandArgs& a, const SelItem* peaks, const int* npeak,
                               int* base, fitrig_candidate* tmp, cudaStream_t st) {
+  cudaError_t e;
   if (a.branch == FITRIG_BRANCH_FREQ) {
-    k_emit_freq<<<152 * 4, 256, 0, st>>>(a, peaks, npeak, nullptr);
+    e = launch_pdl(k_emit_freq, dim3(152 * 4), dim3(256), 0, st, a, peaks, npeak,
+                   (const int*)nullptr);
     count_launches(1);
   } else if (a.arg) {
-    k_group_sort<true><<<152 * 4, kGroupWarps * 32, 0, st>>>(a, npeak, tmp, peaks, nullptr, base);
+    e = launch_pdl(k_group_sort<true>, dim3(152 * 4), dim3(kGroupWarps * 32), 0, st, a, npeak,
+                   (const fitrig_candidate*)tmp, peaks, (const int*)nullptr, (const int*)base);
     count_launches(1);
   } else {
-    k_emit_image<<<152 * 4, 256, 0, st>>>(a, peaks, npeak, nullptr, tmp);
-    k_group_sort<false><<<152 * 4, kGroupWarps * 32, 0, st>>>(a, npeak, tmp, peaks, nullptr, base);
+    e = launch_pdl(k_emit_image, dim3(152 * 4), dim3(256), 0, st, a, peaks, npeak,
+                   (const int*)nullptr, tmp);
+    if (e == cudaSuccess)
+      e = launch_pdl(k_group_sort<false>, dim3(152 * 4), dim3(kGroupWarps * 32), 0, st, a, npeak,
+                     (const fitrig_candidate*)tmp, peaks, (const int*)nullptr, (const int*)base);
     count_launches(2);
   }
-  k_add_count<<<1, 1, 0, st>>>(a.nout, npeak);
+  if (e == cudaSuccess) e = launch_pdl(k_add_count, dim3(1), dim3(1), 0, st, a.nout, npeak);
   count_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, int* base,

@@ -348,9 +348,10 @@ struct BlockScratch {
   int* counters;              // [2] peaks
   int64_t cap;                // boundary-component slots (blocks x slots per block)
   int words;                  // bitmap words per tile row
-  int nblk;                   // grid of the ordered compaction
-  int* blkcnt;                // [nblk]
-  int* blkoff;                // [nblk + 1]
+  int nblk;                   // CTAs of the ordered compaction (kRowsPerCta tile rows each)
+  int* blkcnt;                // [nblk] peaks of each CTA's rows
+  int* blkoff;                // [nblk + 1] their exclusive scan
+  int* rowcnt;                // [groups * Ty] peaks of each tile row
 };
 // Bytes of BlockScratch for `groups` maps of Ty x Tx tiles at group stride
 // `stride` (carved by block_scratch_carve in the same order).
@@ -359,8 +360,9 @@ void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride,
 // Threshold (v > thr[g]), 8-connected components and their peaks over groups
 // x Ty x Tx tiles at vals[g * stride + ty * Tx + tx]; writes the peaks, in
 // (group, t) order, as SelItem{g, t, v} to peaks[0..min(n, cap)) with n in
-// b.counters[2]; flags kErrCapacity (and *want = selected count) when more
-// than `cap` tiles are selected.
+// b.counters[2] (with peaks == nullptr the list is left to launch_emit_rows:
+// the peak bitmap and the rows' offsets stay in b); flags kErrCapacity (and
+// *want = selected count) when more than `cap` tiles are selected.
 cudaError_t launch_block_select(const float* vals, int groups, int64_t stride, int Tx, int Ty,
                                 const float* thr, const BlockScratch& b, SelItem* peaks,
                                 int64_t cap, unsigned* status, unsigned* want, cudaStream_t st);
@@ -400,6 +402,13 @@ cudaError_t launch_emit_candidates(const CandArgs& a, const SelectScratch& s, in
 // launch_emit_candidates does from its own list.
 cudaError_t launch_emit_peaks(const CandArgs& a, const SelItem* peaks, const int* npeak,
                               int* base, fitrig_candidate* tmp, cudaStream_t st);
+// The image candidates of a launch_block_select run without a peak list
+// (peaks == nullptr), from its peak bitmap: needs a.arg, a.w <= 8 and
+// Tx <= 1024 (one bitmap word per lane of a row's warp); the
+// same candidates, in the same places, as launch_emit_peaks on the list.
+// Adds the peak count to *a.nout.
+cudaError_t launch_emit_rows(const CandArgs& a, const float* vals, int groups, const BlockScratch& b,
+                             int64_t cap, int* base, cudaStream_t st);
 cudaError_t launch_export_candidates(const fitrig_candidate* src, const int* n,
                                      fitrig_candidate* dst, int cap, cudaStream_t st);
 

@@ -1179,10 +1179,10 @@ static cudaError_t launch_medmad_cluster(const float* vals, int groups, int64_t 
 // launched last, finishes it.
 constexpr int kSplitRuns = 512;
 constexpr int kSplitPool = kSplitRuns * 32;     // sample keys (64 KB of shared memory)
-constexpr int kSplitChunk = 8192;               // values per CTA of a pass
-constexpr int kSplitSlot = 2048;                // copies a chunk keeps (a quarter of its values)
+constexpr int kSplitChunk = 4096;               // values per CTA of a pass
+constexpr int kSplitSlot = 1024;                // copies a chunk keeps (a quarter of its values)
 constexpr int kSplitMaxChunks = (int)(kFastMaxPerGroup / kSplitChunk);
-constexpr int kSplitPassThreads = 256;
+constexpr int kSplitPassThreads = 128;
 constexpr int kSplitThreads = 1024;             // bracket and select kernels
 constexpr int kSplitBins = 2048;
 constexpr int kSplitGather = 8192;              // copies of the rank's bin kept in shared memory
@@ -1457,7 +1457,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_bracket(const float* __
 // barrier it writes its copies into the chunk's slot.  Nothing is written
 // for a map whose stage is not this pass's.
 template <bool VEC, bool MAD>
-__global__ void __launch_bounds__(kSplitPassThreads, 6) k_split_pass(const float* __restrict__ vals,
+__global__ void __launch_bounds__(kSplitPassThreads, 12) k_split_pass(const float* __restrict__ vals,
                                                                      int64_t stride,
                                                                      const SplitState* __restrict__ st,
                                                                      unsigned* hist_g, uint4* cnt,

@@ -849,65 +849,84 @@ __global__ void k_blk_mark(int Tx, int Ty, int64_t nblocks, BlockScratch b) {
   }
 }
 
-// Ordered compaction of the peak bitmap: one thread per word; per-block
-// counts, their scan, then each block's words in order.
+// Ordered compaction of the peak bitmap, one warp per tile row and
+// kRowsPerCta rows per CTA: each row's peak count and each CTA's sum, the
+// scan of the CTAs' sums, then each row's peaks in order.  A row's offset is
+// its CTA's offset plus the counts of the CTA's rows before it.
 constexpr int kPbThreads = 256;
+constexpr int kRowsPerCta = kPbThreads / 32;
 
-__global__ void __launch_bounds__(kPbThreads) k_pbits_count(int64_t nwords, BlockScratch b) {
+__device__ __forceinline__ int64_t row_offset(const BlockScratch& b, int64_t r) {
+  const int64_t r0 = r & ~(int64_t)(kRowsPerCta - 1);
+  int64_t off = b.blkoff[r0 / kRowsPerCta];
+#pragma unroll
+  for (int k = 0; k < kRowsPerCta - 1; ++k)
+    if (r0 + k < r) off += b.rowcnt[r0 + k];
+  return off;
+}
+
+__global__ void __launch_bounds__(kPbThreads) k_pbits_count(int64_t nrows, BlockScratch b) {
   pdl_begin();
-  __shared__ int wsum[kPbThreads / 32];
-  const int64_t i = (int64_t)blockIdx.x * kPbThreads + threadIdx.x;
-  int cnt = i < nwords ? __popc(b.pbits[i]) : 0;
-  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+  __shared__ int wc[kRowsPerCta];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t r = (int64_t)blockIdx.x * kRowsPerCta + warp;
+  int c = 0;
+  if (r < nrows) {
+    const uint32_t* row = b.pbits + (size_t)r * b.words;
+    for (int w = lane; w < b.words; w += 32) c += __popc(row[w]);
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) {
+    wc[warp] = c;
+    if (r < nrows) b.rowcnt[r] = c;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     int t = 0;
-    for (int w = 0; w < kPbThreads / 32; ++w) t += wsum[w];
+    for (int w = 0; w < kRowsPerCta; ++w) t += wc[w];
     b.blkcnt[blockIdx.x] = t;
   }
 }
 
-__global__ void __launch_bounds__(kPbThreads) k_pbits_write(int64_t nwords, int Tx, int Ty,
+__global__ void __launch_bounds__(kPbThreads) k_pbits_write(int64_t nrows, int Tx, int Ty,
                                                             const float* __restrict__ vals,
                                                             int64_t stride, BlockScratch b,
                                                             SelItem* peaks, int64_t cap) {
   pdl_begin();
-  __shared__ int wcnt[kPbThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t i = (int64_t)blockIdx.x * kPbThreads + threadIdx.x;
-  const uint32_t w = i < nwords ? b.pbits[i] : 0u;
-  const int c = __popc(w);
-  int incl = c;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) wcnt[warp] = incl;
-  __syncthreads();
-  int before = 0;
-  for (int k = 0; k < warp; ++k) before += wcnt[k];
-  if (!w) return;
-  const int64_t per_group = (int64_t)Ty * b.words;
-  const int g = (int)(i / per_group);
-  const int64_t r = i - (int64_t)g * per_group;
-  const int ty = (int)(r / b.words), wx = (int)(r - (int64_t)ty * b.words);
-  int64_t pos = (int64_t)b.blkoff[blockIdx.x] + before + incl - c;
-  // every value load of the word first, then the writes
-  constexpr int kMaxBits = 8;
-  float val[kMaxBits];
-  int tt[kMaxBits];
-  uint32_t m = w;
-  while (m) {
-    int nb = 0;
-    for (; m && nb < kMaxBits; ++nb) {
-      const int bit = __ffs(m) - 1;
-      m &= m - 1;
-      tt[nb] = ty * Tx + wx * 32 + bit;
-      val[nb] = vals[(size_t)g * stride + tt[nb]];
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * kPbThreads + threadIdx.x) >> 5;
+  if (r >= nrows) return;
+  const int g = (int)(r / Ty), ty = (int)(r - (int64_t)g * Ty);
+  const uint32_t* row = b.pbits + (size_t)r * b.words;
+  const float* vg = vals + (size_t)g * stride;
+  int64_t run = row_offset(b, r);
+  for (int w0 = 0; w0 < b.words; w0 += 32) {
+    const int wx = w0 + lane;
+    const uint32_t w = wx < b.words ? row[wx] : 0u;
+    const int c = __popc(w);
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    for (int k = 0; k < nb; ++k, ++pos)
-      if (pos < cap) peaks[pos] = SelItem{g, tt[k], val[k]};
+    int64_t pos = run + incl - c;
+    run += __shfl_sync(0xffffffffu, incl, 31);
+    // every value load of the word first, then the writes
+    constexpr int kMaxBits = 8;
+    float val[kMaxBits];
+    int tt[kMaxBits];
+    uint32_t m = w;
+    while (m) {
+      int nb = 0;
+      for (; m && nb < kMaxBits; ++nb) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        tt[nb] = ty * Tx + wx * 32 + bit;
+        val[nb] = vg[tt[nb]];
+      }
+      for (int k = 0; k < nb; ++k, ++pos)
+        if (pos < cap) peaks[pos] = SelItem{g, tt[k], val[k]};
+    }
   }
 }
 
@@ -940,7 +959,8 @@ static int64_t block_count(int groups, int Tx, int Ty) {
 size_t block_scratch_bytes(int groups, int Tx, int Ty, int64_t stride) {
   const int64_t cap = block_count(groups, Tx, Ty) * kBlkIds;
   const int64_t nw = (int64_t)groups * Ty * block_words(Tx);
-  const int64_t nblk = (nw + kPbThreads - 1) / kPbThreads;
+  const int64_t nrows = (int64_t)groups * Ty;
+  const int64_t nblk = (nrows + kRowsPerCta - 1) / kRowsPerCta;
   size_t bytes = 0;
   auto add = [&](size_t n) { bytes += (n + 255) / 256 * 256; };
   add(sizeof(int) * (size_t)groups * stride);    // glab
@@ -955,6 +975,7 @@ size_t block_scratch_bytes(int groups, int Tx, int Ty, int64_t stride) {
   add(sizeof(int) * 4);                          // counters
   add(sizeof(int) * nblk);                       // blkcnt
   add(sizeof(int) * (nblk + 1));                 // blkoff
+  add(sizeof(int) * nrows);                      // rowcnt
   return bytes;
 }
 
@@ -980,9 +1001,11 @@ void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride,
   b->bstat = reinterpret_cast<int4*>(take(sizeof(int4) * block_count(groups, Tx, Ty)));
   b->pcap = block_count(groups, Tx, Ty) * kBlkPairs;
   b->counters = reinterpret_cast<int*>(take(sizeof(int) * 4));
-  b->nblk = (int)((nw + kPbThreads - 1) / kPbThreads);
+  const int64_t nrows = (int64_t)groups * Ty;
+  b->nblk = (int)((nrows + kRowsPerCta - 1) / kRowsPerCta);
   b->blkcnt = reinterpret_cast<int*>(take(sizeof(int) * b->nblk));
   b->blkoff = reinterpret_cast<int*>(take(sizeof(int) * (b->nblk + 1)));
+  b->rowcnt = reinterpret_cast<int*>(take(sizeof(int) * nrows));
   b->cap = cap;
   b->words = block_words(Tx);
 }
@@ -990,6 +1013,7 @@ void block_scratch_carve(void* base, int groups, int Tx, int Ty, int64_t stride,
 cudaError_t launch_block_select(const float* vals, int groups, int64_t stride, int Tx, int Ty,
                                 const float* thr, const BlockScratch& b, SelItem* peaks,
                                 int64_t cap, unsigned* status, unsigned* want, cudaStream_t st) {
+  // peaks == nullptr: the caller emits straight from the rows (launch_emit_rows)
   const int64_t nblocks = block_count(groups, Tx, Ty);
   if (groups < 1 || groups > 65535 || (Ty + kBlkY - 1) / kBlkY > 65535 ||
       (int64_t)Tx * Ty > 0xffffffffll || nblocks * kBlkIds > INT_MAX ||
@@ -1010,20 +1034,20 @@ cudaError_t launch_block_select(const float* vals, int groups, int64_t stride, i
   if (e == cudaSuccess)
     e = launch_pdl(k_blk_mark, dim3(wgrid), dim3(256), 0, st, Tx, Ty, nblocks, b);
   if (e != cudaSuccess) return e;
-  const int64_t nwords = (int64_t)groups * Ty * b.words;
-  const int64_t nb = (nwords + kPbThreads - 1) / kPbThreads;
-  if (nb > b.nblk) return cudaErrorInvalidValue;   // sized by block_scratch_carve
-  e = launch_pdl(k_pbits_count, dim3((unsigned)nb), dim3(kPbThreads), 0, st, nwords, b);
+  const int64_t ncta = (nrows + kRowsPerCta - 1) / kRowsPerCta;
+  if (ncta > b.nblk) return cudaErrorInvalidValue;   // sized by block_scratch_carve
+  const unsigned rgrid = (unsigned)ncta;   // a warp per row
+  e = launch_pdl(k_pbits_count, dim3(rgrid), dim3(kPbThreads), 0, st, nrows, b);
   if (e == cudaSuccess)
-    e = launch_pdl(k_scan_blocks, dim3(1), dim3(1024), 0, st, (int)nb, (const int*)b.blkcnt,
+    e = launch_pdl(k_scan_blocks, dim3(1), dim3(1024), 0, st, (int)ncta, (const int*)b.blkcnt,
                    b.blkoff, &b.counters[2], cap, status, (unsigned*)nullptr);
-  if (e == cudaSuccess)
-    e = launch_pdl(k_pbits_write, dim3((unsigned)nb), dim3(kPbThreads), 0, st, nwords, Tx, Ty, vals,
-                   stride, b, peaks, cap);
+  if (e == cudaSuccess && peaks)
+    e = launch_pdl(k_pbits_write, dim3(rgrid), dim3(kPbThreads), 0, st, nrows, Tx, Ty, vals, stride,
+                   b, peaks, cap);
   if (e == cudaSuccess)
     e = launch_pdl(k_blk_check, dim3(1), dim3(1024), 0, st, nblocks, b, cap, status, want);
   if (e != cudaSuccess) return e;
-  count_launches(9);
+  count_launches(peaks ? 9 : 8);
   return cudaGetLastError();
 }
 
@@ -1428,8 +1452,105 @@ __global__ void __launch_bounds__(kGroupWarps * 32) k_group_sort(CandArgs a, con
   }
 }
 
+// Image branch with the march's in-tile arg-max, w <= kRowsMaxW and rows of at
+// most 32 bitmap words (Tx <= 1024), straight from the peak bitmap: one warp
+// per tile row, one word per lane, writes the row's candidates in (snapshot,
+// y, x) order.  Inside a tile row that order is (dy, tx), so a peak's place is
+// the row's offset (from the scan of the rows' peak counts), the row's peaks
+// in lower in-tile rows, and the peaks of its own in-tile row at smaller tx
+// (warp scans of each lane's count per in-tile row).  Each lane reads the
+// arg-max byte and value of its first kRowsBatch peaks together and keeps
+// them; a lane with more reads the rest again.  The same candidates as
+// k_group_sort<true> on the compacted peak list, without that list.
+constexpr int kRowsMaxW = 8;
+constexpr int kRowsBatch = 4;
+__global__ void __launch_bounds__(kPbThreads, 4) k_emit_rows(CandArgs a, const float* __restrict__ vals,
+                                                          int64_t nrows, BlockScratch b,
+                                                          int64_t cap, const int* base_) {
+  pdl_begin();
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * kPbThreads + threadIdx.x) >> 5;
+  if (r >= nrows) return;
+  const int w = a.w;
+  const int g = (int)(r / a.Ty), ty = (int)(r - (int64_t)g * a.Ty);
+  const int t0 = ty * a.Tx;
+  const uint32_t* row = b.pbits + (size_t)r * b.words;
+  const uint8_t* ag = a.arg + (size_t)g * a.stride + t0;
+  const float* vg = vals + (size_t)g * a.stride + t0;
+  const int64_t roff = row_offset(b, r);
+  const int64_t base = *base_;
+  // one word per lane: each lane's first kRowsBatch peaks are read once
+  // (arg-max byte and value together) and kept; a lane with more reads the
+  // rest again
+  const uint32_t word = lane < b.words ? row[lane] : 0u;
+  int idx[kRowsBatch], tx[kRowsBatch];
+  float v[kRowsBatch];
+  uint32_t m = word;
+#pragma unroll
+  for (int k = 0; k < kRowsBatch; ++k) {
+    idx[k] = -1;
+    tx[k] = 0;
+    v[k] = 0.f;
+    if (m) {
+      tx[k] = lane * 32 + __ffs(m) - 1;
+      m &= m - 1;
+      idx[k] = ag[tx[k]];
+      v[k] = vg[tx[k]];
+    }
+  }
+  const uint32_t rest = m;
+  int mine[kRowsMaxW];
+#pragma unroll
+  for (int d = 0; d < kRowsMaxW; ++d) mine[d] = 0;
+#pragma unroll
+  for (int k = 0; k < kRowsBatch; ++k) {
+    const int dy = idx[k] >= 0 ? idx[k] / w : -1;
+#pragma unroll
+    for (int d = 0; d < kRowsMaxW; ++d) mine[d] += dy == d;
+  }
+  for (uint32_t q = rest; q; q &= q - 1) {
+    const int dy = ag[lane * 32 + __ffs(q) - 1] / w;
+#pragma unroll
+    for (int d = 0; d < kRowsMaxW; ++d) mine[d] += dy == d;
+  }
+  // place of this lane's first peak of each in-tile row: the row's peaks
+  // in lower in-tile rows, then the lower lanes' peaks of that row
+  int excl[kRowsMaxW];
+  int run = 0;
+#pragma unroll
+  for (int d = 0; d < kRowsMaxW; ++d) {
+    int incl = mine[d];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    excl[d] = run + incl - mine[d];
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  auto put = [&](int t, int i, float val) {
+    const int dy = i / w, dx = i - dy * w;
+    int j = 0;
+#pragma unroll
+    for (int d = 0; d < kRowsMaxW; ++d)
+      if (dy == d) j = excl[d]++;
+    const int64_t n = roff + j;   // place among the image candidates
+    const int64_t pos = base + n;
+    if (n < cap && pos < a.cap) a.out[pos] = image_candidate(a, SelItem{g, t0 + t, val}, t, ty, w, dx, dy);
+  };
+#pragma unroll
+  for (int k = 0; k < kRowsBatch; ++k)
+    if (idx[k] >= 0) put(tx[k], idx[k], v[k]);
+  for (uint32_t q = rest; q; q &= q - 1) {
+    const int t = lane * 32 + __ffs(q) - 1;
+    put(t, ag[t], vg[t]);
+  }
+}
+
 __global__ void k_add_count(int* total, const int* part) {
-  pdl_begin(); *total += *part; }
+  pdl_begin();
+  *total += *part;
+}
 
 // Copies the first min(*n, cap) candidates to mapped host memory, so only the
 // candidates that exist cross the host link.
@@ -1468,6 +1589,20 @@ cudaError_t launch_emit_peaks(const CandArgs& a, const SelItem* peaks, const int
   }
   if (e == cudaSuccess) e = launch_pdl(k_add_count, dim3(1), dim3(1), 0, st, a.nout, npeak);
   count_launches(1);
+  return e;
+}
+
+cudaError_t launch_emit_rows(const CandArgs& a, const float* vals, int groups, const BlockScratch& b,
+                             int64_t cap, int* base, cudaStream_t st) {
+  if (!a.arg || a.w < 1 || a.w > kRowsMaxW || b.words > 32 ||
+      ((int64_t)groups * a.Ty + kRowsPerCta - 1) / kRowsPerCta > b.nblk)
+    return cudaErrorInvalidValue;
+  const int64_t nrows = (int64_t)groups * a.Ty;
+  cudaError_t e = launch_pdl(k_emit_rows, dim3((unsigned)((nrows * 32 + kPbThreads - 1) / kPbThreads)),
+                             dim3(kPbThreads), 0, st, a, vals, nrows, b, cap, (const int*)base);
+  if (e == cudaSuccess)
+    e = launch_pdl(k_add_count, dim3(1), dim3(1), 0, st, a.nout, (const int*)&b.counters[2]);
+  count_launches(2);
   return e;
 }
 

@@ -1007,6 +1007,10 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
   // statistics, so they run on the side stream beside the spectrum and the
   // frequency branch; the two join before the image candidates are written
   // (frequency candidates, snapshot -1, lead the sorted list).
+  // with the march's in-tile arg-max, a small window and tile rows of at most
+  // 1024 tiles the image candidates come straight from the peak bitmap,
+  // already in (snapshot, y, x) order
+  const bool rows_emit = image && p->d_arg && ca.w <= 8 && p->Tx <= 1024;
   cudaStream_t is = st;
   if (image && freq) {
     CKE(cudaEventRecord(p->fork_ev, st));
@@ -1020,7 +1024,8 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
     if (timed) rec(p, FITRIG_KERNEL_NOISE, 1, is);
     if (timed) rec(p, FITRIG_KERNEL_SELECT, 0, is);
     CKE(launch_block_select(p->d_vp, U, p->vstride, p->Tx, p->Ty, p->d_thr, p->blk,
-                            p->sel.items, p->sel.capacity, status, p->sel.want, is));
+                            rows_emit ? nullptr : p->sel.items, p->sel.capacity, status,
+                            p->sel.want, is));
     if (is != st) CKE(cudaEventRecord(p->join_ev, is));
   }
   if (p->d_smax && p->coding == FITRIG_CODING_DELTA) {
@@ -1057,7 +1062,10 @@ static cudaError_t enqueue_post(fitrig_plan_t p, cudaStream_t st, bool timed) {
     ca.arg = p->d_arg;
     ca.cs = p->d_cs;
     ca.inv = p->d_inv;
-    CKE(launch_emit_peaks(ca, p->sel.items, &p->blk.counters[2], nout, p->d_cand_tmp, st));
+    if (rows_emit)
+      CKE(launch_emit_rows(ca, p->d_vp, U, p->blk, p->sel.capacity, nout, st));
+    else
+      CKE(launch_emit_peaks(ca, p->sel.items, &p->blk.counters[2], nout, p->d_cand_tmp, st));
     mark(FITRIG_KERNEL_SELECT, 1);
   }
   CKE(launch_clamp_count(nout, (int)p->cand_cap, status, st));

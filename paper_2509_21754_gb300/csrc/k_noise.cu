@@ -1102,15 +1102,13 @@ static cudaError_t launch_fast_t(const float* vals, int groups, int64_t stride, 
     cfg.blockDim = dim3(kFastThreads, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = kClusterCtas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // starts with pdl_begin()
-    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 2;
+    cfg.numAttrs = 1;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, k_medmad_fast<VEC>, vals, stride, n, g0, cs, invalid);
     count_launches(1);
     if (e != cudaSuccess) return e;
